@@ -1,0 +1,236 @@
+"""Pins for the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test is chosen so that a plausible mistake in the oracle (a dropped term,
+a wrong sign, a wrong index map, a transposed operand) fails at least one of
+them.  None of them compares the oracle with itself.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import elm_oracle as O
+from paper_2406_15959_gb300 import workload as wl
+
+
+def tiny(gx=2, gy=2, n=12, mi=6, p=5, seed=3, theta="paper", source="sinsin", c=0.5):
+    return wl.build(gx, gy, n, mi, mi, p, p, theta=theta, theta_seed=seed,
+                    source=source, source_seed=seed, c=c, n_test_side=20)
+
+
+# ----------------------------------------------------------------- assembly
+
+def test_features_match_symbolic_derivatives():
+    """K^s / A^s rows (Section 3) against sympy's own derivatives of tanh(w.x+b):
+    -Laplacian at interior rows, value at boundary/interface rows, outward normal
+    derivative for A^s.  Pins the sign of L, the factor 2 and the normal."""
+    sympy = pytest.importorskip("sympy")
+    x, y, w1, w2, b = sympy.symbols("x y w1 w2 b", real=True)
+    phi = sympy.tanh(w1 * x + w2 * y + b)
+    lap = sympy.lambdify((x, y, w1, w2, b), -(sympy.diff(phi, x, 2) + sympy.diff(phi, y, 2)))
+    dx = sympy.lambdify((x, y, w1, w2, b), sympy.diff(phi, x))
+    dy = sympy.lambdify((x, y, w1, w2, b), sympy.diff(phi, y))
+    val = sympy.lambdify((x, y, w1, w2, b), phi)
+    w = tiny(gx=2, gy=1, n=5, mi=3, p=2, seed=11)
+    g = w.geom
+    for s in range(g.n_sub):
+        K, A = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s])
+        ri, rb, rg = g.rows(s)
+        for j in range(w.n_neurons):
+            pj = (w.W[s, j, 0], w.W[s, j, 1], w.b[s, j])
+            for r in range(ri.start, ri.stop):
+                assert K[r, j] == pytest.approx(float(lap(*g.xy[s, r], *pj)), rel=1e-12, abs=1e-12)
+            for r in range(rb.start, rg.stop):
+                assert K[r, j] == pytest.approx(float(val(*g.xy[s, r], *pj)), rel=1e-13, abs=1e-14)
+            for k, r in enumerate(range(rg.start, rg.stop)):
+                nx, ny = g.nrm[s, r]
+                ref = nx * dx(*g.xy[s, r], *pj) + ny * dy(*g.xy[s, r], *pj)
+                assert A[k, j] == pytest.approx(float(ref), rel=1e-12, abs=1e-14)
+
+
+def test_features_match_finite_differences():
+    """Second, library-free pin of the same rows: central differences of tanh."""
+    w = tiny(gx=2, gy=2, n=7, mi=4, p=3, seed=5)
+    g = w.geom
+    h = 1e-4
+    for s in range(g.n_sub):
+        K, A = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s])
+        ri, _, rg = g.rows(s)
+        W, b = w.W[s], w.b[s]
+
+        def phi(p):
+            return np.tanh(p @ W.T + b)
+        for r in range(ri.start, ri.stop):
+            p0 = g.xy[s, r]
+            ex, ey = np.array([h, 0.0]), np.array([0.0, h])
+            lap = (phi(p0 + ex) + phi(p0 - ex) + phi(p0 + ey) + phi(p0 - ey) - 4 * phi(p0)) / h ** 2
+            np.testing.assert_allclose(K[r], -lap, rtol=2e-5, atol=1e-4)
+        for k, r in enumerate(range(rg.start, rg.stop)):
+            p0, n = g.xy[s, r], g.nrm[s, r]
+            dn = (phi(p0 + h * n) - phi(p0 - h * n)) / (2 * h)
+            np.testing.assert_allclose(A[k], dn, rtol=1e-6, atol=1e-8)
+
+
+def test_geometry_invariants():
+    """Every interface unknown is shared by exactly two subdomains at the same
+    point with opposite outward normals (the transmission conditions of Eq. (2.2))."""
+    for gx, gy in [(2, 2), (3, 2), (4, 4)]:
+        g = wl.make_geometry(gx, gy, 3, 4, 5, 6)
+        seen = {}
+        for s in range(g.n_sub):
+            _, _, rg = g.rows(s)
+            for r in range(rg.start, rg.stop):
+                seen.setdefault(int(g.dof[s, r]), []).append((s, g.xy[s, r], g.nrm[s, r]))
+        assert sorted(seen) == list(range(g.n_gamma))
+        for d, lst in seen.items():
+            assert len(lst) == 2
+            (s0, x0, n0), (s1, x1, n1) = lst
+            assert s0 != s1
+            assert np.array_equal(x0, x1)
+            assert np.array_equal(n0, -n1)
+
+
+# ----------------------------------------------------------------- the three routes
+
+@pytest.mark.parametrize("gx,gy,seed", [(2, 2, 3), (3, 2, 4), (2, 3, 6)])
+def test_ddm_route_matches_monolithic_and_normal_equations(gx, gy, seed):
+    """Route 1 (Schur system Eq. (3.5) + back-solve) equals the dense LS solution of
+    the eliminated system Eq. (3.3) and the dense normal equations Eq. (3.4)."""
+    w = tiny(gx=gx, gy=gy, seed=seed)
+    res = O.solve(w.geom, w.W, w.b, w.rhs)
+    assert res.rdiag_ratio.min() > 1e-3           # well-conditioned, so c itself is pinned
+    c2, u2 = O.monolithic_ls(w.geom, w.W, w.b, w.rhs)
+    c3, u3 = O.normal_equations(w.geom, w.W, w.b, w.rhs)
+    for c, u in [(c2, u2), (c3, u3)]:
+        assert np.linalg.norm(res.u_gamma - u) <= 1e-10 * np.linalg.norm(u)
+        assert np.linalg.norm(res.c - c) <= 1e-9 * np.linalg.norm(c)
+
+
+def test_eliminated_ls_differs_from_original_ls():
+    """The paper solves the LS problem of Eq. (3.3), not of Eq. (3.1); for an
+    inconsistent system the two minimisers differ, and the oracle follows Eq. (3.3)."""
+    w = tiny(gx=2, gy=2, seed=9)
+    K, A, B, F = O.global_blocks(w.geom, w.W, w.b, w.rhs)
+    Z = np.block([[K, B], [A, np.zeros((A.shape[0], B.shape[1]))]])
+    x = np.linalg.lstsq(Z, np.concatenate([F, np.zeros(A.shape[0])]), rcond=None)[0]
+    res = O.solve(w.geom, w.W, w.b, w.rhs)
+    u_orig = x[K.shape[1]:]
+    assert np.linalg.norm(res.u_gamma - u_orig) > 1e-8 * np.linalg.norm(u_orig)
+
+
+def test_single_subdomain_is_classical_elm():
+    """N = 1: no interface, Algorithm 1 reduces to the classical ELM c = K^+ F."""
+    w = tiny(gx=1, gy=1, n=15, mi=7, p=6, seed=2)
+    assert w.geom.n_gamma == 0
+    res = O.solve(w.geom, w.W, w.b, w.rhs)
+    g = w.geom
+    c_ref = O.classical_elm(g.xy[0], g.counts[0], w.W[0], w.b[0], w.rhs[0])
+    np.testing.assert_allclose(res.c[0], c_ref, rtol=1e-9, atol=1e-9 * np.abs(c_ref).max())
+
+
+@pytest.mark.parametrize("gx,gy", [(2, 2), (3, 2)])
+def test_consistent_system_is_recovered_exactly(gx, gy):
+    """If the local networks c* are continuous across Gamma (values and normal
+    fluxes) and F^s = K^s c*^s away from Gamma, then (c*, u* = traces of the
+    networks on Gamma) solves Eq. (3.1) exactly and so minimises Eq. (3.3) with
+    zero residual: the oracle must return it."""
+    w = tiny(gx=gx, gy=gy, n=14, mi=6, p=3, seed=17)
+    g = w.geom
+    N, n = g.n_sub, w.n_neurons
+    Ks, As = [], []
+    for s in range(N):
+        K, A = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s])
+        Ks.append(K); As.append(A)
+    # Constraints on the stacked c: value jump and flux sum at every interface point.
+    C = np.zeros((2 * g.n_gamma, N * n))
+    sign = {}
+    for s in range(N):
+        _, _, rg = g.rows(s)
+        for k, r in enumerate(range(rg.start, rg.stop)):
+            d = int(g.dof[s, r])
+            sg = sign.setdefault(d, 1.0)
+            sign[d] = -1.0
+            C[d, s * n:(s + 1) * n] += sg * Ks[s][r]
+            C[g.n_gamma + d, s * n:(s + 1) * n] += As[s][k]
+    Nul = sla.null_space(C)
+    assert Nul.shape[1] > 0
+    cstar = (Nul @ np.random.default_rng(0).standard_normal(Nul.shape[1])).reshape(N, n)
+    rhs = np.zeros_like(w.rhs)
+    ustar = np.zeros(g.n_gamma)
+    for s in range(N):
+        ri, rb, rg = g.rows(s)
+        v = Ks[s] @ cstar[s]
+        rhs[s, :rb.stop] = v[:rb.stop]
+        ustar[g.dof[s, rg]] = v[rg]
+    res = O.solve(g, w.W, w.b, rhs)
+    assert np.linalg.norm(res.u_gamma - ustar) <= 1e-9 * np.linalg.norm(ustar)
+    assert np.linalg.norm(res.c - cstar) <= 1e-7 * np.linalg.norm(cstar)
+
+
+# ----------------------------------------------------------------- invariants
+
+def test_schur_matrix_is_spd_and_backsolve_is_optimal():
+    """S is symmetric positive definite (Section 3, before Algorithm 1), and each
+    c^s satisfies the local normal equations K^T K c = K^T (F - B u) (Algorithm 1)."""
+    w = wl.build(3, 3, 40, 9, 8, 11, 10, theta="paper", theta_seed=4, source="fourier",
+                 source_seed=4, n_test_side=10)
+    res = O.solve(w.geom, w.W, w.b, w.rhs)
+    S = res.S
+    assert np.abs(S - S.T).max() <= 1e-14 * np.abs(S).max()
+    assert np.linalg.eigvalsh(S).min() > 0
+    g = w.geom
+    for s in range(g.n_sub):
+        K, _ = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s])
+        F = O.rhs_local(w.rhs[s], g.counts[s])
+        _, _, rg = g.rows(s)
+        r = K @ res.c[s] - F
+        r[rg] -= res.u_gamma[g.dof[s, rg]]           # K c + B u - F with B = [0; 0; -E]
+        assert np.linalg.norm(K.T @ r) <= 1e-9 * np.linalg.norm(K.T @ F)
+
+
+def test_schur_pieces_project_onto_range():
+    """[K K^+]_GG = Q_G Q_G^T is a block of an orthogonal projector:
+    eigenvalues of D_s = I - Q_G Q_G^T lie in [0, 1]."""
+    w = tiny(gx=3, gy=3, n=20, mi=7, p=4, seed=8)
+    res = O.solve(w.geom, w.W, w.b, w.rhs)
+    for L in res.locs:
+        ev = np.linalg.eigvalsh(L.D)
+        assert ev.min() > -1e-12 and ev.max() < 1 + 1e-12
+        np.testing.assert_allclose(L.Q.T @ L.Q, np.eye(L.Q.shape[1]), atol=1e-12)
+
+
+def test_evaluation_matches_collocation_rows():
+    """u(x) at boundary/interface collocation points equals the corresponding rows of K c."""
+    w = tiny(gx=2, gy=2, n=10, mi=5, p=4, seed=12)
+    res = O.solve(w.geom, w.W, w.b, w.rhs)
+    g = w.geom
+    for s in range(g.n_sub):
+        _, rb, rg = g.rows(s)
+        K, _ = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s])
+        pts = g.xy[s, rb.start:rg.stop]
+        u, _ = O.evaluate(w.W, w.b, res.c, pts, np.full(len(pts), s))
+        np.testing.assert_allclose(u, K[rb.start:rg.stop] @ res.c[s], rtol=1e-12, atol=1e-12)
+
+
+def test_error_falls_with_neurons_and_points():
+    """Manufactured solution sin(pi x) sin(pi y): the relative L2 error at the test
+    points falls as the networks and the point sets grow (Theorem 2.1, Table 2)."""
+    errs = []
+    for n, mi, p in [(10, 5, 5), (40, 10, 10), (120, 18, 18)]:
+        w = wl.build(2, 2, n, mi, mi, p, p, theta="paper", theta_seed=1, source="sinsin",
+                     n_test_side=40)
+        res = O.solve(w.geom, w.W, w.b, w.rhs)
+        u, gr = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
+        errs.append(O.rel_errors(u, gr, w.src.u(w.test_xy), w.src.grad_u(w.test_xy))[0])
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-5
+
+
+def test_fourier_source_has_the_stated_exact_solution():
+    """The sine-mode source and its closed-form u satisfy -Laplacian u = f (checked by FD)."""
+    src = wl.make_source("fourier", seed=5, modes=4)
+    rng = np.random.default_rng(1)
+    p = rng.uniform(0.1, 0.9, size=(50, 2))
+    h = 1e-4
+    ex, ey = np.array([h, 0.0]), np.array([0.0, h])
+    lap = (src.u(p + ex) + src.u(p - ex) + src.u(p + ey) + src.u(p - ey) - 4 * src.u(p)) / h ** 2
+    np.testing.assert_allclose(-lap, src.f(p), rtol=1e-5, atol=1e-6)
