@@ -1,0 +1,177 @@
+/*
+ * elm_ddm.h -- C ABI of the GB300 nonoverlapping domain-decomposition ELM solver.
+ *
+ * The method (arxiv 2406.15959, Section 3 and Algorithm 1) solves a 2-D elliptic
+ * problem L u = f in Omega, u = g on the boundary (Eq. (2.1)) with one random-feature
+ * network per subdomain, u_s(x) = sum_j c^s_j tanh(w^s_j . x + b^s_j), joined by an
+ * interface unknown u_Gamma.  The entry points follow Algorithm 1:
+ *
+ *   elm_ddm_setup     geometry of the decomposition (points, normals, interface map)
+ *   elm_ddm_assemble  step (a): K^s, A^s of Eq. (3.1) from the hidden parameters theta^s
+ *   elm_ddm_schur     step (b): local Householder QR of K^s, and the RHS-independent
+ *                     part of step (c): assembly and Cholesky factorisation of the
+ *                     Schur matrix of Eq. (3.5)
+ *   elm_ddm_solve     the RHS part of step (c) (right-hand side of Eq. (3.5), triangular
+ *                     solves for u_Gamma) and step (d): the local back-solves
+ *                     c^s = K^{s+}(F^s - B^s u_Gamma) (Algorithm 1, last loop)
+ *   elm_ddm_eval      u and grad u of the trained networks at arbitrary points
+ *
+ * Conventions
+ * -----------
+ * - All floating point is IEEE binary64.  Matrices are column-major.
+ * - Subdomain s has rows ordered [interior | boundary | interface] (the row blocks of
+ *   K^s in Section 3); counts[s] = {m_i, m_b, m_Gamma}; per-row arrays have a row
+ *   stride of desc->m_max.
+ * - Every interface unknown must be shared by exactly two subdomains.  Interface rows
+ *   are grouped into "edges": maximal runs of a subdomain's interface rows with
+ *   consecutive global unknowns and the same neighbouring subdomain.  Each edge must
+ *   appear, with the same unknowns in the same order, in both subdomains.
+ * - Pointers documented "host" are read during the call only.  Pointers documented
+ *   "device" are borrowed for the duration of the call (the kernels they feed are
+ *   enqueued on the handle's stream; the caller keeps them alive and unmodified until
+ *   that stream reaches the point of the call).  The handle owns all workspace.
+ * - Compute entry points are asynchronous: they enqueue work on the stream given to
+ *   elm_ddm_setup and return.  Numerical failures found by the kernels (non-SPD
+ *   Schur matrix, exactly zero R diagonal, non-finite data) are recorded in a device
+ *   status word and reported by elm_ddm_check, which synchronises the stream.
+ * - Nothing in this library allocates or frees memory outside elm_ddm_setup and
+ *   elm_ddm_destroy.
+ */
+#ifndef ELM_DDM_H
+#define ELM_DDM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define ELM_DDM_OK            0
+#define ELM_DDM_ERR_ARG       1  /* invalid argument or geometry */
+#define ELM_DDM_ERR_STATE     2  /* entry points called out of order */
+#define ELM_DDM_ERR_CUDA      3  /* a CUDA runtime call failed */
+#define ELM_DDM_ERR_OOM       4  /* device allocation failed */
+#define ELM_DDM_ERR_NONFINITE 5  /* NaN or Inf in theta, f/g or an intermediate */
+#define ELM_DDM_ERR_RANK      6  /* some R^s has an exactly zero diagonal entry */
+#define ELM_DDM_ERR_NOT_SPD   7  /* a Cholesky pivot of the Schur matrix was <= 0 */
+
+/* Differential operators. */
+#define ELM_DDM_OP_POISSON 0  /* L = -Laplacian (Eq. (4.4)) */
+
+typedef struct elm_ddm_handle elm_ddm_handle;
+
+typedef struct elm_ddm_desc {
+  int32_t n_sub;      /* N, number of subdomains (>= 1) */
+  int32_t n_neurons;  /* n_N, hidden neurons per subdomain (>= 1) */
+  int32_t m_max;      /* row stride of the per-row arrays; >= m_i + m_b + m_Gamma of every s */
+  int32_t n_gamma;    /* number of global interface unknowns (0 when N == 1) */
+  int32_t op;         /* ELM_DDM_OP_* */
+  int32_t max_rhs;    /* largest nrhs elm_ddm_solve will be given, 1..64 (0 means 1) */
+} elm_ddm_desc;
+
+/*
+ * Geometry of the decomposition (Section 3: the point sets x^s_i, x^s_b, x^s_Gamma,
+ * the outward normals n_s on Gamma, and the map B^s = [0; 0; -E_s] of interface rows
+ * onto u_Gamma).
+ *   counts  host int32  [N][3]        {m_i, m_b, m_Gamma}; each subdomain needs
+ *                                     m_i + m_b + m_Gamma >= n_neurons (the premise of
+ *                                     the full-rank proposition in Section 3)
+ *   xy      host double [N][m_max][2] collocation points
+ *   nrm     host double [N][m_max][2] outward unit normal of interface rows (other rows ignored)
+ *   dof     host int32  [N][m_max]    global interface unknown of interface rows, in
+ *                                     [0, n_gamma) (other rows ignored)
+ *   stream  cudaStream_t to enqueue all work on (NULL = legacy default stream)
+ * Returns ELM_DDM_OK and a new handle in *out, or an error code (no handle is
+ * created).  Allocates every device workspace the solver needs.
+ */
+int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double* xy,
+                  const double* nrm, const int32_t* dof, void* stream, elm_ddm_handle** out);
+
+/*
+ * Step (a) of Algorithm 1 (Section 3, definitions of K^s and A^s): with
+ * t = tanh(w.x + b), interior rows get L phi = 2|w|^2 t (1 - t^2), boundary and
+ * interface rows get phi = t, and A^s rows get d phi/d n = (w.n)(1 - t^2).
+ *   W  device double [N][n_neurons][2]  hidden weights w^s_j (global coordinates)
+ *   b  device double [N][n_neurons]     hidden biases b^s_j
+ * theta is copied into the handle (elm_ddm_eval uses it).
+ */
+int elm_ddm_assemble(elm_ddm_handle* h, const double* W, const double* b);
+
+/*
+ * Step (b) and the RHS-independent part of step (c): Householder QR K^s = Q_s R_s
+ * (reflectors kept for elm_ddm_solve), Q_G = interface rows of Q_s,
+ * Y_s = A^s R_s^{-1}, D_s = I - Q_G Q_G^T, M_s = -Y_s Q_G^T, the Schur matrix
+ * S = sum_s E_s^T D_s E_s + M^T M of Eq. (3.5) with M = sum_s E_s^T M_s E_s, and its
+ * Cholesky factor S = L L^T.  Requires elm_ddm_assemble.
+ */
+int elm_ddm_schur(elm_ddm_handle* h);
+
+/*
+ * RHS part of step (c) and step (d), for nrhs right-hand sides at once:
+ * q_s = Q_s^T F^s, rhs = sum_s E_s^T Q_G q_s + M^T h with h = sum_s E_s^T Y_s q_s,
+ * u_Gamma = S^{-1} rhs, c^s = R_s^{-1}(q_s + Q_G^T E_s u_Gamma).
+ *   rhs      device double [nrhs][N][m_max]  f at interior rows, g at boundary rows;
+ *                                           interface rows and padding are ignored (F^s
+ *                                           is zero there, Section 3)
+ *   u_gamma  device double [nrhs][n_gamma]   output (may be NULL)
+ *   c        device double [nrhs][N][n_neurons] output weights c^s (must not be NULL)
+ * Requires elm_ddm_schur.  1 <= nrhs <= desc->max_rhs.
+ */
+int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c);
+
+/*
+ * u(x) = sum_j c^s_j tanh(w^s_j . x + b^s_j) and grad u at npts points, s = owner[i].
+ *   xy     device double [npts][2]
+ *   owner  device int32  [npts]   subdomain index of each point, in [0, N)
+ *   c      device double [N][n_neurons]
+ *   u      device double [npts]   output
+ *   grad   device double [npts][2] output (may be NULL)
+ * Requires elm_ddm_assemble (for theta).
+ */
+int elm_ddm_eval(elm_ddm_handle* h, int npts, const double* xy, const int32_t* owner,
+                 const double* c, double* u, double* grad);
+
+/*
+ * Synchronises the handle's stream and returns the first failure the kernels
+ * recorded since the previous check (ELM_DDM_ERR_NOT_SPD, _RANK, _NONFINITE), a
+ * pending CUDA error (ELM_DDM_ERR_CUDA), or ELM_DDM_OK.  Clears the status word.
+ */
+int elm_ddm_check(elm_ddm_handle* h);
+
+/* Internal matrices that elm_ddm_export can copy out (for inspection and tests). */
+#define ELM_DDM_BUF_K 0  /* m_s x (n_N + m_Gamma): [K^s | J] after assemble; after schur the
+                            Householder factors: R on and above the diagonal, reflectors
+                            below it, Q_G^T in rows 0..n_N-1 of the last m_Gamma columns */
+#define ELM_DDM_BUF_A 1  /* m_Gamma x n_N: A^s after assemble, Y_s = A^s R_s^{-1} after schur */
+#define ELM_DDM_BUF_D 2  /* m_Gamma x m_Gamma: D_s = I - Q_G Q_G^T (after schur) */
+#define ELM_DDM_BUF_M 3  /* m_Gamma x m_Gamma: M_s = -Y_s Q_G^T (after schur) */
+#define ELM_DDM_BUF_L 4  /* n_gamma x n_gamma: lower Cholesky factor of S (after schur; s ignored;
+                            the strict upper triangle is unspecified) */
+
+/*
+ * Copies internal matrix `what` (ELM_DDM_BUF_*) of subdomain s, column-major, into the
+ * device buffer dst with leading dimension ld_dst (>= its row count).  Enqueued on the
+ * handle's stream.
+ */
+int elm_ddm_export(elm_ddm_handle* h, int what, int s, double* dst, int ld_dst);
+
+/*
+ * Queries.  key: 0 = n_gamma, 1 = device workspace bytes, 2 = number of kernel
+ * launches enqueued since setup, 3 = number of Schur-matrix edges (interface blocks),
+ * 4 = m_max, 5 = n_neurons, 6 = n_sub.
+ */
+int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value);
+
+/* Frees all device workspace and the handle.  Synchronises the stream first. */
+int elm_ddm_destroy(elm_ddm_handle* h);
+
+/* Message of the last failure on this handle ("" if none).  h may be NULL, in which
+ * case the message of the last failed elm_ddm_setup in this process is returned. */
+const char* elm_ddm_last_error(const elm_ddm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELM_DDM_H */

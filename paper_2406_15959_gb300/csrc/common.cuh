@@ -1,0 +1,118 @@
+// Internal declarations shared by the CUDA translation units of libelmddm.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace elmddm {
+
+constexpr int QR_NB = 32;     // panel width of the blocked Householder QR
+constexpr int CHOL_NB = 64;   // block size of the Schur-matrix Cholesky
+constexpr int TRSV_MAX_N = 8192;  // largest n_neurons the back-solve keeps in shared memory
+
+// Bits of the device status word.
+enum : unsigned { ST_RANK = 1u, ST_NOT_SPD = 2u, ST_NONFINITE = 4u };
+
+// C(m x n) = alpha * op(A) op(B) + beta * C, column-major; op = transpose or not.
+struct GemmDesc {
+  const double* A;
+  const double* B;
+  double* C;
+  int m, n, k, lda, ldb, ldc;
+};
+enum : int { GEMM_LOWER = 1, GEMM_ADD_IDENTITY = 2 };
+
+// dst(rows x cols) += src, column-major.
+struct AddDesc {
+  const double* src;
+  double* dst;
+  int rows, cols, lds, ldd;
+};
+
+// ---- launchers (return cudaGetLastError after the launch) ----
+cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_tiles,
+                        double alpha, double beta, int flags, cudaStream_t st);
+cudaError_t launch_add_blocks(const AddDesc* d, int count, int max_elems, cudaStream_t st);
+
+cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, double* Amat,
+                            long long astride, int mgld, const double* xy, const double* nrm,
+                            int m_max, const int* cnt, const double* W, const double* b, int N,
+                            int n, unsigned* status, cudaStream_t st);
+cudaError_t launch_eval(const double* W, const double* b, int N, int n, int npts,
+                        const double* xy, const int* owner, const double* c, double* u,
+                        double* grad, cudaStream_t st);
+
+cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
+                            int nbe, double* tau, int n, double* T, long long tstride,
+                            double* Vp, long long vstride, unsigned* status, cudaStream_t st);
+cudaError_t launch_trsm_y(double* Y, long long ystride, int mgld, const double* K,
+                          long long kstride, int ld, const int* mg, int mgmax, int N, int n,
+                          cudaStream_t st);
+cudaError_t launch_load_rhs(double* X, const double* rhs, int N, int m_max, int ld,
+                            const int* cnt, int nrhs, unsigned* status, cudaStream_t st);
+cudaError_t launch_apply_qt(double* X, const double* K, long long kstride, int ld,
+                            const int* ms, int N, int n, const double* T, long long tstride,
+                            int nrhs, cudaStream_t st);
+cudaError_t launch_iface_vecs(const double* X, const double* K, long long kstride, int ld,
+                              const double* Y, long long ystride, int mgld, const int* mg,
+                              int N, int n, int nrhs, double* gq, double* hq, cudaStream_t st);
+cudaError_t launch_gather2(const int* dofmap, int n_gamma, int mgld, int N, const double* a,
+                           double* out, int accumulate, int nrhs, cudaStream_t st);
+cudaError_t launch_mt_h(const double* M, long long mstride, int mgld, const int* mg,
+                        const int* ifc_dof, const double* h, int n_gamma, int N, int nrhs,
+                        double* z, cudaStream_t st);
+cudaError_t launch_backsolve(const double* X, const double* K, long long kstride, int ld,
+                             const int* mg, const int* ifc_dof, int mgld, const double* u,
+                             int n_gamma, int N, int n, int nrhs, double* c, cudaStream_t st);
+
+cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, unsigned* status,
+                              cudaStream_t st);
+cudaError_t launch_trsm_chol(double* S, int ld, int n, int k, int nb, cudaStream_t st);
+cudaError_t launch_chol_fwd(const double* L, int ld, int n, int k, int nb, double* r,
+                            double* y, int nrhs, cudaStream_t st);
+cudaError_t launch_chol_bwd(const double* L, int ld, int n, int k, int nb, double* y,
+                            double* u, int nrhs, cudaStream_t st);
+
+// ---- device helpers ----
+#ifdef __CUDACC__
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block (blockDim.x a multiple of 32, <= 1024); result in every thread.
+// `red` must hold at least 33 doubles.  Contains __syncthreads.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// 32 partial sums per lane -> lane L returns the warp-wide sum of entry L.
+// Recursive halving: 31 shuffles instead of 32 x 5.
+__device__ __forceinline__ double warp_transpose_sum32(double (&a)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      const double send = up ? a[i] : a[i + off];
+      const double keep = up ? a[i + off] : a[i];
+      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return a[0];
+}
+#endif
+
+}  // namespace elmddm

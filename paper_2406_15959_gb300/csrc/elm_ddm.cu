@@ -1,0 +1,641 @@
+// Host side of the C ABI (include/elm_ddm.h): handle lifecycle, validation of the
+// decomposition, the interface-edge structure of the Schur matrix, and the launch
+// plans of Algorithm 1.  All launch descriptors are built once at setup, so the
+// compute entry points only enqueue kernels.
+#include "elm_ddm.h"
+#include "common.cuh"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+using namespace elmddm;
+
+namespace {
+
+struct LaunchRec {
+  int kind;  // 0 = gemm, 1 = add_blocks
+  int off, count, max_tiles;
+  bool ta, tb;
+  double alpha, beta;
+  int flags;
+};
+
+struct Edge {
+  int g0, len;
+  int s[2], i[2];  // owning subdomains and local interface-row offsets
+};
+
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+inline int tiles64(int m, int n) { return ((m + 63) / 64) * ((n + 63) / 64); }
+
+std::string g_setup_error;
+
+}  // namespace
+
+struct elm_ddm_handle {
+  elm_ddm_desc desc{};
+  cudaStream_t st = nullptr;
+  int N = 0, n = 0, m_max = 0, ld = 0, ncap = 0, mgmax = 0, mgld = 0, ng = 0, nblk = 0;
+  int max_rhs = 1;
+  long long kstride = 0, astride = 0, mstride = 0, tstride = 0, vstride = 0, wstride = 0;
+  std::vector<int> cnt_h, ms_h, mg_h;
+  std::vector<Edge> edges;
+  // device buffers
+  double *K = nullptr, *Am = nullptr, *tau = nullptr, *T = nullptr, *Vp = nullptr;
+  double *W1 = nullptr, *W2 = nullptr, *D = nullptr, *M = nullptr, *S = nullptr;
+  double *Mdiag = nullptr, *thW = nullptr, *thb = nullptr, *xy = nullptr, *nrm = nullptr;
+  double *X = nullptr, *gq = nullptr, *hq = nullptr, *zv = nullptr;
+  double *rv = nullptr, *hv = nullptr, *yv = nullptr, *uv = nullptr;
+  int *cnt = nullptr, *ms = nullptr, *mg = nullptr, *dofmap = nullptr, *ifc_dof = nullptr;
+  unsigned* status = nullptr;
+  GemmDesc* gd = nullptr;
+  AddDesc* ad = nullptr;
+  size_t mdiag_elems = 0;
+  // plans
+  std::vector<LaunchRec> qr_recs;    // 3 per panel
+  std::vector<LaunchRec> dm_recs;    // D and M
+  std::vector<LaunchRec> s_recs;     // Mdiag adds, D adds, M^T M gemms
+  std::vector<LaunchRec> syrk_recs;  // one per Cholesky block step
+  int state = 0;
+  long long launches = 0;
+  size_t bytes = 0;
+  std::string err;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(elm_ddm_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_setup_error = msg;
+  return code;
+}
+
+int cuda_fail(elm_ddm_handle* h, cudaError_t e, const char* where) {
+  return fail(h, ELM_DDM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+bool dev_alloc(elm_ddm_handle* h, T** p, size_t count) {
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  h->allocs.push_back(q);
+  h->bytes += count * sizeof(T);
+  *p = static_cast<T*>(q);
+  return true;
+}
+
+void free_all(elm_ddm_handle* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+}
+
+#define ELM_LAUNCH(h, expr, where)                       \
+  do {                                                   \
+    cudaError_t e_ = (expr);                             \
+    (h)->launches++;                                     \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, where); \
+  } while (0)
+
+int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first, size_t cnt) {
+  for (size_t r = first; r < first + cnt && r < recs.size(); ++r) {
+    const LaunchRec& L = recs[r];
+    if (L.count <= 0) continue;
+    if (L.kind == 0)
+      ELM_LAUNCH(h, launch_gemm(L.ta, L.tb, h->gd + L.off, L.count, L.max_tiles, L.alpha, L.beta,
+                                L.flags, h->st), "gemm");
+    else
+      ELM_LAUNCH(h, launch_add_blocks(h->ad + L.off, L.count, L.max_tiles, h->st), "add_blocks");
+  }
+  return ELM_DDM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double* xy,
+                  const double* nrm, const int32_t* dof, void* stream, elm_ddm_handle** out) {
+  if (!out) return fail(nullptr, ELM_DDM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!desc || !counts || !xy || !nrm || !dof)
+    return fail(nullptr, ELM_DDM_ERR_ARG, "NULL descriptor or geometry array");
+  const int N = desc->n_sub, n = desc->n_neurons, m_max = desc->m_max, ng = desc->n_gamma;
+  if (N < 1 || n < 1 || m_max < 1 || ng < 0)
+    return fail(nullptr, ELM_DDM_ERR_ARG, "n_sub, n_neurons, m_max must be >= 1 and n_gamma >= 0");
+  if (desc->op != ELM_DDM_OP_POISSON) return fail(nullptr, ELM_DDM_ERR_ARG, "unsupported operator");
+  const int max_rhs = desc->max_rhs == 0 ? 1 : desc->max_rhs;
+  if (max_rhs < 1 || max_rhs > 64) return fail(nullptr, ELM_DDM_ERR_ARG, "max_rhs must be in 1..64");
+  if (n > TRSV_MAX_N) return fail(nullptr, ELM_DDM_ERR_ARG, "n_neurons > 8192 is not supported");
+  if ((long long)N * m_max > (1ll << 31)) return fail(nullptr, ELM_DDM_ERR_ARG, "geometry too large");
+
+  auto h = new elm_ddm_handle();
+  h->desc = *desc;
+  h->st = static_cast<cudaStream_t>(stream);
+  h->N = N; h->n = n; h->m_max = m_max; h->ng = ng; h->max_rhs = max_rhs;
+  h->cnt_h.assign(counts, counts + 3 * N);
+  h->ms_h.resize(N); h->mg_h.resize(N);
+  int msmax = 0, mgmax = 0;
+  for (int s = 0; s < N; ++s) {
+    const int mi = counts[3 * s], mb = counts[3 * s + 1], mgs = counts[3 * s + 2];
+    if (mi < 0 || mb < 0 || mgs < 0 || mi + mb + mgs > m_max) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_ARG, "counts of subdomain " + std::to_string(s) + " invalid");
+    }
+    if (mi + mb + mgs < n) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_ARG,
+                  "subdomain " + std::to_string(s) + " has fewer rows than neurons");
+    }
+    if ((ng == 0) != (mgs == 0) && N > 1) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_ARG, "interface rows inconsistent with n_gamma");
+    }
+    if (N == 1 && mgs != 0) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_ARG, "a single subdomain cannot have interface rows");
+    }
+    h->ms_h[s] = mi + mb + mgs;
+    h->mg_h[s] = mgs;
+    msmax = std::max(msmax, mi + mb + mgs);
+    mgmax = std::max(mgmax, mgs);
+  }
+  for (size_t i = 0; i < (size_t)N * m_max * 2; ++i) {
+    if (!std::isfinite(xy[i])) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_NONFINITE, "non-finite collocation point");
+    }
+  }
+
+  // ---- interface unknowns: owners, edges ----
+  std::vector<std::vector<std::pair<int, int>>> owners(ng);
+  for (int s = 0; s < N; ++s) {
+    const int r0 = counts[3 * s] + counts[3 * s + 1];
+    for (int i = 0; i < h->mg_h[s]; ++i) {
+      const int g = dof[(size_t)s * m_max + r0 + i];
+      if (g < 0 || g >= ng) {
+        delete h;
+        return fail(nullptr, ELM_DDM_ERR_ARG, "interface unknown index out of range");
+      }
+      owners[g].push_back({s, i});
+    }
+  }
+  for (int g = 0; g < ng; ++g) {
+    if (owners[g].size() != 2 || owners[g][0].first == owners[g][1].first) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_ARG,
+                  "interface unknown " + std::to_string(g) + " is not shared by exactly two subdomains");
+    }
+  }
+  auto other = [&](int g, int s) {
+    return owners[g][0].first == s ? owners[g][1].first : owners[g][0].first;
+  };
+  // segments: maximal runs with consecutive unknowns and the same neighbour
+  std::map<int, std::vector<std::array<int, 3>>> segs;  // g0 -> list of {s, i0, len}
+  for (int s = 0; s < N; ++s) {
+    const int r0 = counts[3 * s] + counts[3 * s + 1];
+    const int* d = dof + (size_t)s * m_max + r0;
+    int i = 0;
+    while (i < h->mg_h[s]) {
+      int j = i + 1;
+      while (j < h->mg_h[s] && d[j] == d[j - 1] + 1 && other(d[j], s) == other(d[i], s)) ++j;
+      segs[d[i]].push_back({s, i, j - i});
+      i = j;
+    }
+  }
+  int covered = 0;
+  for (auto& kv : segs) {
+    if (kv.second.size() != 2 || kv.second[0][2] != kv.second[1][2]) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_ARG, "interface rows do not form matching edges");
+    }
+    Edge e;
+    e.g0 = kv.first;
+    e.len = kv.second[0][2];
+    for (int q = 0; q < 2; ++q) { e.s[q] = kv.second[q][0]; e.i[q] = kv.second[q][1]; }
+    if (e.g0 != covered) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_ARG, "interface edges overlap or leave gaps");
+    }
+    covered += e.len;
+    h->edges.push_back(e);
+  }
+  if (covered != ng) {
+    delete h;
+    return fail(nullptr, ELM_DDM_ERR_ARG, "interface edges do not cover all unknowns");
+  }
+
+  // ---- sizes ----
+  h->ld = round_up(std::max(msmax, 1), 32);
+  h->mgmax = mgmax;
+  h->mgld = round_up(std::max(mgmax, 1), 32);
+  h->ncap = n + mgmax;
+  h->nblk = (n + QR_NB - 1) / QR_NB;
+  h->kstride = (long long)h->ld * h->ncap;
+  h->astride = (long long)h->mgld * n;
+  h->mstride = (long long)h->mgld * h->mgld;
+  h->tstride = (long long)h->nblk * QR_NB * QR_NB;
+  h->vstride = (long long)h->ld * QR_NB;
+  h->wstride = (long long)QR_NB * h->ncap;
+  for (const Edge& e : h->edges) h->mdiag_elems += (size_t)e.len * e.len;
+
+  // ---- allocation ----
+  bool ok = dev_alloc(h, &h->K, (size_t)N * h->kstride) &&
+            dev_alloc(h, &h->Am, (size_t)N * h->astride) &&
+            dev_alloc(h, &h->tau, (size_t)N * n) && dev_alloc(h, &h->T, (size_t)N * h->tstride) &&
+            dev_alloc(h, &h->Vp, (size_t)N * h->vstride) &&
+            dev_alloc(h, &h->W1, (size_t)N * h->wstride) &&
+            dev_alloc(h, &h->W2, (size_t)N * h->wstride) &&
+            dev_alloc(h, &h->D, (size_t)N * h->mstride) &&
+            dev_alloc(h, &h->M, (size_t)N * h->mstride) &&
+            dev_alloc(h, &h->S, (size_t)ng * ng) && dev_alloc(h, &h->Mdiag, h->mdiag_elems) &&
+            dev_alloc(h, &h->thW, (size_t)N * n * 2) && dev_alloc(h, &h->thb, (size_t)N * n) &&
+            dev_alloc(h, &h->xy, (size_t)N * m_max * 2) &&
+            dev_alloc(h, &h->nrm, (size_t)N * m_max * 2) &&
+            dev_alloc(h, &h->X, (size_t)max_rhs * N * h->ld) &&
+            dev_alloc(h, &h->gq, (size_t)max_rhs * N * h->mgld) &&
+            dev_alloc(h, &h->hq, (size_t)max_rhs * N * h->mgld) &&
+            dev_alloc(h, &h->zv, (size_t)max_rhs * N * h->mgld) &&
+            dev_alloc(h, &h->rv, (size_t)max_rhs * ng) && dev_alloc(h, &h->hv, (size_t)max_rhs * ng) &&
+            dev_alloc(h, &h->yv, (size_t)max_rhs * ng) && dev_alloc(h, &h->uv, (size_t)max_rhs * ng) &&
+            dev_alloc(h, &h->cnt, (size_t)N * 3) && dev_alloc(h, &h->ms, (size_t)N) &&
+            dev_alloc(h, &h->mg, (size_t)N) && dev_alloc(h, &h->dofmap, (size_t)ng * 4) &&
+            dev_alloc(h, &h->ifc_dof, (size_t)N * h->mgld) && dev_alloc(h, &h->status, 1);
+  if (!ok) {
+    free_all(h);
+    delete h;
+    return fail(nullptr, ELM_DDM_ERR_OOM, "device allocation failed");
+  }
+
+  // ---- geometry tables ----
+  std::vector<int> dofmap((size_t)ng * 4), ifc((size_t)N * h->mgld, -1);
+  for (int g = 0; g < ng; ++g) {
+    auto a = owners[g][0], b = owners[g][1];
+    if (a.first > b.first) std::swap(a, b);
+    dofmap[4 * g] = a.first; dofmap[4 * g + 1] = a.second;
+    dofmap[4 * g + 2] = b.first; dofmap[4 * g + 3] = b.second;
+  }
+  for (int s = 0; s < N; ++s) {
+    const int r0 = counts[3 * s] + counts[3 * s + 1];
+    for (int i = 0; i < h->mg_h[s]; ++i) ifc[(size_t)s * h->mgld + i] = dof[(size_t)s * m_max + r0 + i];
+  }
+
+  // ---- launch plans ----
+  std::vector<GemmDesc> gds;
+  std::vector<AddDesc> ads;
+  auto add_gemm_rec = [&](std::vector<LaunchRec>& recs, const std::vector<GemmDesc>& batch, bool ta,
+                          bool tb, double alpha, double beta, int flags) {
+    LaunchRec L{0, (int)gds.size(), 0, 0, ta, tb, alpha, beta, flags};
+    for (const GemmDesc& d : batch) {
+      if (d.m <= 0 || d.n <= 0) continue;
+      gds.push_back(d);
+      L.count++;
+      L.max_tiles = std::max(L.max_tiles, tiles64(d.m, d.n));
+    }
+    recs.push_back(L);
+  };
+  auto add_add_rec = [&](std::vector<LaunchRec>& recs, const std::vector<AddDesc>& batch) {
+    LaunchRec L{1, (int)ads.size(), 0, 0, false, false, 0, 0, 0};
+    for (const AddDesc& d : batch) {
+      if (d.rows <= 0 || d.cols <= 0) continue;
+      ads.push_back(d);
+      L.count++;
+      L.max_tiles = std::max(L.max_tiles, d.rows * d.cols);
+    }
+    recs.push_back(L);
+  };
+  const int ld = h->ld;
+  // QR trailing updates, panel b: W1 = V^T A2, W2 = T^T W1, A2 -= V W2.
+  for (int b = 0; b < h->nblk; ++b) {
+    const int k0 = b * QR_NB, nbe = std::min(QR_NB, n - k0);
+    std::vector<GemmDesc> g1, g2, g3;
+    for (int s = 0; s < N; ++s) {
+      const int n2 = n + h->mg_h[s] - (k0 + nbe), mp = h->ms_h[s] - k0;
+      if (n2 <= 0 || mp <= 0) continue;
+      double* Ks = h->K + (size_t)s * h->kstride;
+      const double* V = h->Vp + (size_t)s * h->vstride + k0;
+      double* A2 = Ks + k0 + (size_t)(k0 + nbe) * ld;
+      double* w1 = h->W1 + (size_t)s * h->wstride;
+      double* w2 = h->W2 + (size_t)s * h->wstride;
+      const double* Tb = h->T + (size_t)s * h->tstride + (size_t)b * QR_NB * QR_NB;
+      g1.push_back({V, A2, w1, nbe, n2, mp, ld, ld, QR_NB});
+      g2.push_back({Tb, w1, w2, nbe, n2, nbe, QR_NB, QR_NB, QR_NB});
+      g3.push_back({V, w2, A2, mp, n2, nbe, ld, QR_NB, ld});
+    }
+    add_gemm_rec(h->qr_recs, g1, true, false, 1.0, 0.0, 0);
+    add_gemm_rec(h->qr_recs, g2, true, false, 1.0, 0.0, 0);
+    add_gemm_rec(h->qr_recs, g3, false, false, -1.0, 1.0, 0);
+  }
+  // D_s = I - (Q_G^T)^T Q_G^T and M_s = -Y_s Q_G^T.
+  {
+    std::vector<GemmDesc> gD, gM;
+    for (int s = 0; s < N; ++s) {
+      const int mgs = h->mg_h[s];
+      if (mgs == 0) continue;
+      const double* QGt = h->K + (size_t)s * h->kstride + (size_t)n * ld;
+      gD.push_back({QGt, QGt, h->D + (size_t)s * h->mstride, mgs, mgs, n, ld, ld, h->mgld});
+      gM.push_back({h->Am + (size_t)s * h->astride, QGt, h->M + (size_t)s * h->mstride, mgs, mgs, n,
+                    h->mgld, ld, h->mgld});
+    }
+    add_gemm_rec(h->dm_recs, gD, true, false, -1.0, 0.0, GEMM_ADD_IDENTITY);
+    add_gemm_rec(h->dm_recs, gM, false, false, -1.0, 0.0, 0);
+  }
+  // Schur matrix (lower edge blocks): S[e1,e2] = sum D-blocks + sum_e Mblk(e,e1)^T Mblk(e,e2).
+  if (ng > 0) {
+    const int ne = (int)h->edges.size();
+    std::vector<size_t> mdoff(ne);
+    size_t acc = 0;
+    for (int e = 0; e < ne; ++e) { mdoff[e] = acc; acc += (size_t)h->edges[e].len * h->edges[e].len; }
+    auto local = [&](int e, int s) -> int {
+      const Edge& E = h->edges[e];
+      return E.s[0] == s ? E.i[0] : (E.s[1] == s ? E.i[1] : -1);
+    };
+    // edges of each subdomain
+    std::vector<std::vector<int>> sub_edges(N);
+    for (int e = 0; e < ne; ++e) for (int q = 0; q < 2; ++q) sub_edges[h->edges[e].s[q]].push_back(e);
+    // Mdiag[e] = M_{s0}[e,e] + M_{s1}[e,e]
+    for (int q = 0; q < 2; ++q) {
+      std::vector<AddDesc> batch;
+      for (int e = 0; e < ne; ++e) {
+        const Edge& E = h->edges[e];
+        const double* src = h->M + (size_t)E.s[q] * h->mstride + E.i[q] + (size_t)E.i[q] * h->mgld;
+        batch.push_back({src, h->Mdiag + mdoff[e], E.len, E.len, h->mgld, E.len});
+      }
+      add_add_rec(h->s_recs, batch);
+    }
+    auto mblk = [&](int e, int e2, const double** p, int* ldp) {
+      if (e == e2) { *p = h->Mdiag + mdoff[e]; *ldp = h->edges[e].len; return; }
+      const Edge& E = h->edges[e];
+      for (int q = 0; q < 2; ++q) {
+        const int s = E.s[q], l2 = local(e2, s);
+        if (l2 >= 0) {
+          *p = h->M + (size_t)s * h->mstride + E.i[q] + (size_t)l2 * h->mgld;
+          *ldp = h->mgld;
+          return;
+        }
+      }
+      *p = nullptr;
+    };
+    // neighbour lists (edges sharing a subdomain, including the edge itself)
+    std::vector<std::vector<int>> nbr(ne);
+    for (int e = 0; e < ne; ++e) {
+      std::vector<int> v;
+      for (int q = 0; q < 2; ++q) for (int e2 : sub_edges[h->edges[e].s[q]]) v.push_back(e2);
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+      nbr[e] = v;
+    }
+    std::vector<std::vector<AddDesc>> drounds;
+    std::vector<std::vector<GemmDesc>> mrounds;
+    for (int e1 = 0; e1 < ne; ++e1) {
+      // candidate e2: neighbours of neighbours
+      std::vector<int> cand;
+      for (int e : nbr[e1]) for (int e2 : nbr[e]) if (h->edges[e2].g0 <= h->edges[e1].g0) cand.push_back(e2);
+      std::sort(cand.begin(), cand.end());
+      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+      const Edge& E1 = h->edges[e1];
+      for (int e2 : cand) {
+        const Edge& E2 = h->edges[e2];
+        double* dst = h->S + E1.g0 + (size_t)E2.g0 * ng;
+        int r = 0;
+        for (int q = 0; q < 2; ++q) {
+          const int s = E1.s[q], l2 = local(e2, s);
+          if (l2 < 0) continue;
+          if ((int)drounds.size() <= r) drounds.emplace_back();
+          drounds[r++].push_back({h->D + (size_t)s * h->mstride + E1.i[q] + (size_t)l2 * h->mgld, dst,
+                                  E1.len, E2.len, h->mgld, ng});
+        }
+        r = 0;
+        for (int e : nbr[e1]) {
+          if (!std::binary_search(nbr[e].begin(), nbr[e].end(), e2)) continue;
+          const double *pa, *pb;
+          int la, lb;
+          mblk(e, e1, &pa, &la);
+          mblk(e, e2, &pb, &lb);
+          if (!pa || !pb) continue;
+          if ((int)mrounds.size() <= r) mrounds.emplace_back();
+          mrounds[r++].push_back({pa, pb, dst, E1.len, E2.len, h->edges[e].len, la, lb, ng});
+        }
+      }
+    }
+    for (auto& b : drounds) add_add_rec(h->s_recs, b);
+    for (auto& b : mrounds) add_gemm_rec(h->s_recs, b, true, false, 1.0, 1.0, 0);
+    // Cholesky trailing updates
+    for (int k = 0; k < ng; k += CHOL_NB) {
+      const int nb = std::min(CHOL_NB, ng - k), rest = ng - k - nb;
+      std::vector<GemmDesc> g;
+      if (rest > 0) {
+        double* L21 = h->S + (k + nb) + (size_t)k * ng;
+        g.push_back({L21, L21, h->S + (k + nb) + (size_t)(k + nb) * ng, rest, rest, nb, ng, ng, ng});
+      }
+      add_gemm_rec(h->syrk_recs, g, false, true, -1.0, 1.0, GEMM_LOWER);
+    }
+  }
+  ok = dev_alloc(h, &h->gd, gds.size()) && dev_alloc(h, &h->ad, ads.size());
+  if (!ok) {
+    free_all(h);
+    delete h;
+    return fail(nullptr, ELM_DDM_ERR_OOM, "device allocation failed");
+  }
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  cp(h->gd, gds.data(), gds.size() * sizeof(GemmDesc));
+  cp(h->ad, ads.data(), ads.size() * sizeof(AddDesc));
+  cp(h->xy, xy, (size_t)N * m_max * 2 * sizeof(double));
+  cp(h->nrm, nrm, (size_t)N * m_max * 2 * sizeof(double));
+  cp(h->cnt, counts, (size_t)N * 3 * sizeof(int));
+  cp(h->ms, h->ms_h.data(), (size_t)N * sizeof(int));
+  cp(h->mg, h->mg_h.data(), (size_t)N * sizeof(int));
+  cp(h->dofmap, dofmap.data(), dofmap.size() * sizeof(int));
+  cp(h->ifc_dof, ifc.data(), ifc.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    std::string msg = std::string("setup copy: ") + cudaGetErrorString(e);
+    free_all(h);
+    delete h;
+    return fail(nullptr, ELM_DDM_ERR_CUDA, msg);
+  }
+  *out = h;
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_assemble(elm_ddm_handle* h, const double* W, const double* b) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  if (!W || !b) return fail(h, ELM_DDM_ERR_ARG, "assemble: NULL theta");
+  const size_t nw = (size_t)h->N * h->n;
+  cudaError_t e = cudaMemcpyAsync(h->thW, W, nw * 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->thb, b, nw * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Am, 0, (size_t)h->N * h->astride * sizeof(double), h->st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "assemble: copy theta");
+  ELM_LAUNCH(h, launch_assemble(h->K, h->kstride, h->ld, h->ncap, h->Am, h->astride, h->mgld, h->xy,
+                                h->nrm, h->m_max, h->cnt, h->thW, h->thb, h->N, h->n, h->status, h->st),
+             "assemble");
+  h->state = 1;
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_schur(elm_ddm_handle* h) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  if (h->state != 1) return fail(h, ELM_DDM_ERR_STATE, "schur: call elm_ddm_assemble first");
+  // (b) blocked Householder QR of [K^s | J]
+  for (int b = 0; b < h->nblk; ++b) {
+    const int k0 = b * QR_NB, nbe = std::min(QR_NB, h->n - k0);
+    ELM_LAUNCH(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->T +
+                                  (size_t)b * QR_NB * QR_NB, h->tstride, h->Vp, h->vstride, h->status,
+                                  h->st), "panel_qr");
+    int rc = run_recs(h, h->qr_recs, 3 * (size_t)b, 3);
+    if (rc) return rc;
+  }
+  h->state = 0;  // K is factored in place: assemble again before another schur
+  if (h->ng > 0) {
+    ELM_LAUNCH(h, launch_trsm_y(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg, h->mgmax,
+                                h->N, h->n, h->st), "trsm_y");
+    int rc = run_recs(h, h->dm_recs, 0, h->dm_recs.size());
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(h->S, 0, (size_t)h->ng * h->ng * sizeof(double), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->Mdiag, 0, h->mdiag_elems * sizeof(double), h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "schur: memset");
+    rc = run_recs(h, h->s_recs, 0, h->s_recs.size());
+    if (rc) return rc;
+    for (int k = 0, step = 0; k < h->ng; k += CHOL_NB, ++step) {
+      const int nb = std::min(CHOL_NB, h->ng - k);
+      ELM_LAUNCH(h, launch_potrf_diag(h->S, h->ng, k, nb, h->status, h->st), "potrf");
+      if (h->ng - k - nb > 0) {
+        ELM_LAUNCH(h, launch_trsm_chol(h->S, h->ng, h->ng, k, nb, h->st), "trsm_chol");
+        rc = run_recs(h, h->syrk_recs, step, 1);
+        if (rc) return rc;
+      }
+    }
+  }
+  h->state = 2;
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  if (h->state != 2) return fail(h, ELM_DDM_ERR_STATE, "solve: call elm_ddm_schur first");
+  if (!rhs || !c) return fail(h, ELM_DDM_ERR_ARG, "solve: NULL rhs or c");
+  if (nrhs < 1 || nrhs > h->max_rhs) return fail(h, ELM_DDM_ERR_ARG, "solve: nrhs out of range");
+  const int N = h->N, n = h->n, ng = h->ng;
+  ELM_LAUNCH(h, launch_load_rhs(h->X, rhs, N, h->m_max, h->ld, h->cnt, nrhs, h->status, h->st),
+             "load_rhs");
+  ELM_LAUNCH(h, launch_apply_qt(h->X, h->K, h->kstride, h->ld, h->ms, N, n, h->T, h->tstride, nrhs,
+                                h->st), "apply_qt");
+  if (ng > 0) {
+    ELM_LAUNCH(h, launch_iface_vecs(h->X, h->K, h->kstride, h->ld, h->Am, h->astride, h->mgld, h->mg,
+                                    N, n, nrhs, h->gq, h->hq, h->st), "iface_vecs");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->gq, h->rv, 0, nrhs, h->st), "gather_r");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->hq, h->hv, 0, nrhs, h->st), "gather_h");
+    ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, h->mgld, h->mg, h->ifc_dof, h->hv, ng, N, nrhs, h->zv,
+                              h->st), "mt_h");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
+    for (int k = 0; k < ng; k += CHOL_NB) {
+      const int nb = std::min(CHOL_NB, ng - k);
+      ELM_LAUNCH(h, launch_chol_fwd(h->S, ng, ng, k, nb, h->rv, h->yv, nrhs, h->st), "chol_fwd");
+    }
+    for (int k = ((ng - 1) / CHOL_NB) * CHOL_NB; k >= 0; k -= CHOL_NB) {
+      const int nb = std::min(CHOL_NB, ng - k);
+      ELM_LAUNCH(h, launch_chol_bwd(h->S, ng, ng, k, nb, h->yv, h->uv, nrhs, h->st), "chol_bwd");
+    }
+  }
+  ELM_LAUNCH(h, launch_backsolve(h->X, h->K, h->kstride, h->ld, h->mg, h->ifc_dof, h->mgld,
+                                 ng > 0 ? h->uv : h->rv, ng, N, n, nrhs, c, h->st), "backsolve");
+  if (u_gamma && ng > 0) {
+    cudaError_t e = cudaMemcpyAsync(u_gamma, h->uv, (size_t)nrhs * ng * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "solve: copy u_gamma");
+  }
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_eval(elm_ddm_handle* h, int npts, const double* xy, const int32_t* owner,
+                 const double* c, double* u, double* grad) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  if (npts < 0) return fail(h, ELM_DDM_ERR_ARG, "eval: npts < 0");
+  if (npts == 0) return ELM_DDM_OK;
+  if (!xy || !owner || !c || !u) return fail(h, ELM_DDM_ERR_ARG, "eval: NULL pointer");
+  ELM_LAUNCH(h, launch_eval(h->thW, h->thb, h->N, h->n, npts, xy, owner, c, u, grad, h->st), "eval");
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_export(elm_ddm_handle* h, int what, int s, double* dst, int ld_dst) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  if (!dst) return fail(h, ELM_DDM_ERR_ARG, "export: NULL dst");
+  if (what != ELM_DDM_BUF_L && (s < 0 || s >= h->N)) return fail(h, ELM_DDM_ERR_ARG, "export: bad s");
+  const double* src = nullptr;
+  int rows = 0, cols = 0, lds = 0;
+  switch (what) {
+    case ELM_DDM_BUF_K:
+      src = h->K + (size_t)s * h->kstride; rows = h->ms_h[s]; cols = h->n + h->mg_h[s]; lds = h->ld; break;
+    case ELM_DDM_BUF_A:
+      src = h->Am + (size_t)s * h->astride; rows = h->mg_h[s]; cols = h->n; lds = h->mgld; break;
+    case ELM_DDM_BUF_D:
+      src = h->D + (size_t)s * h->mstride; rows = cols = h->mg_h[s]; lds = h->mgld; break;
+    case ELM_DDM_BUF_M:
+      src = h->M + (size_t)s * h->mstride; rows = cols = h->mg_h[s]; lds = h->mgld; break;
+    case ELM_DDM_BUF_L:
+      src = h->S; rows = cols = h->ng; lds = h->ng; break;
+    default: return fail(h, ELM_DDM_ERR_ARG, "export: unknown buffer");
+  }
+  if (rows == 0 || cols == 0) return ELM_DDM_OK;
+  if (ld_dst < rows) return fail(h, ELM_DDM_ERR_ARG, "export: ld_dst too small");
+  cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)ld_dst * sizeof(double), src, (size_t)lds * sizeof(double),
+                                    (size_t)rows * sizeof(double), cols, cudaMemcpyDeviceToDevice, h->st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "export");
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_check(elm_ddm_handle* h) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "check: stream");
+  unsigned bits = 0;
+  e = cudaMemcpy(&bits, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(h, e, "check: status");
+  if (bits & ST_NONFINITE) return fail(h, ELM_DDM_ERR_NONFINITE, "non-finite value in theta, f/g or R");
+  if (bits & ST_RANK) return fail(h, ELM_DDM_ERR_RANK, "a local R has an exactly zero diagonal entry");
+  if (bits & ST_NOT_SPD) return fail(h, ELM_DDM_ERR_NOT_SPD, "Schur matrix is not positive definite");
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value) {
+  if (!h || !value) return ELM_DDM_ERR_ARG;
+  switch (key) {
+    case 0: *value = h->ng; break;
+    case 1: *value = (double)h->bytes; break;
+    case 2: *value = (double)h->launches; break;
+    case 3: *value = (double)h->edges.size(); break;
+    case 4: *value = h->m_max; break;
+    case 5: *value = h->n; break;
+    case 6: *value = h->N; break;
+    default: return ELM_DDM_ERR_ARG;
+  }
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_destroy(elm_ddm_handle* h) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  cudaStreamSynchronize(h->st);
+  free_all(h);
+  delete h;
+  return ELM_DDM_OK;
+}
+
+const char* elm_ddm_last_error(const elm_ddm_handle* h) {
+  return h ? h->err.c_str() : g_setup_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+// Step (c): blocked right-looking Cholesky S = L L^T of the Schur matrix of Eq. (3.5)
+// (the paper states the system is SPD), and the blocked triangular solves that give
+// u_Gamma.  The trailing SYRK update of the factorisation goes through launch_gemm.
+#include "common.cuh"
+
+namespace elmddm {
+
+namespace {
+
+constexpr int NB = CHOL_NB;
+
+// Unblocked Cholesky of the nb x nb diagonal block at (k, k), in shared memory.
+__global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ S, int ld, int k, int nb,
+                                                    unsigned* status) {
+  __shared__ double a[NB][NB + 1];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += 256) {
+    const int i = e % nb, j = e / nb;
+    a[i][j] = (i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : 0.0;
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int j = 0; j < nb; ++j) {
+    if (tid == 0) {
+      double dj = a[j][j];
+      if (!(dj > 0.0) || !isfinite(dj)) { bad = true; dj = 1.0; }
+      a[j][j] = sqrt(dj);
+    }
+    __syncthreads();
+    const double piv = a[j][j];
+    for (int i = j + 1 + tid; i < nb; i += 256) a[i][j] /= piv;
+    __syncthreads();
+    const int w = nb - j - 1;
+    for (int e = tid; e < w * w; e += 256) {
+      const int ii = j + 1 + e % w, kk = j + 1 + e / w;
+      if (kk <= ii) a[ii][kk] = fma(-a[ii][j], a[kk][j], a[ii][kk]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += 256) {
+    const int i = e % nb, j = e / nb;
+    if (i >= j) S[(k + i) + (size_t)(k + j) * ld] = a[i][j];
+  }
+  if (bad) atomicOr(status, ST_NOT_SPD);
+}
+
+// L21 = A21 L11^{-T}: one thread per row below the diagonal block.
+__global__ void __launch_bounds__(64) k_trsm_chol(double* __restrict__ S, int ld, int n, int k,
+                                                  int nb) {
+  extern __shared__ double smem_trsm[];
+  double (*L)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(smem_trsm);
+  double (*X)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(smem_trsm + NB * (NB + 1));
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += 64) {
+    const int i = e % nb, j = e / nb;
+    L[i][j] = (i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : 0.0;
+  }
+  const int i = k + nb + blockIdx.x * 64 + tid;
+  for (int j = 0; j < nb; ++j) X[tid][j] = (i < n) ? S[i + (size_t)(k + j) * ld] : 0.0;
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    double x = X[tid][j];
+    for (int l = 0; l < j; ++l) x = fma(-X[tid][l], L[j][l], x);
+    X[tid][j] = x / L[j][j];
+  }
+  if (i < n)
+    for (int j = 0; j < nb; ++j) S[i + (size_t)(k + j) * ld] = X[tid][j];
+}
+
+// Forward substitution step for block k: y_k = L_kk^{-1} r_k, r_rest -= L_rest,k y_k.
+// Every block solves the small triangle itself, so one launch covers the step.
+__global__ void __launch_bounds__(256) k_chol_fwd(const double* __restrict__ L, int ld, int n, int k,
+                                                  int nb, double* __restrict__ r,
+                                                  double* __restrict__ y) {
+  __shared__ double Ls[NB][NB + 1];
+  __shared__ double ys[NB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* rr = r + (size_t)blockIdx.y * n;
+  double* yy = y + (size_t)blockIdx.y * n;
+  for (int e = tid; e < nb * nb; e += 256) {
+    const int i = e % nb, j = e / nb;
+    Ls[i][j] = (i >= j) ? L[(k + i) + (size_t)(k + j) * ld] : 0.0;
+  }
+  if (tid < nb) ys[tid] = rr[k + tid];
+  __syncthreads();
+  if (warp == 0) {
+    for (int i = 0; i < nb; ++i) {
+      double p = 0.0;
+      for (int l = lane; l < i; l += 32) p = fma(Ls[i][l], ys[l], p);
+      p = warp_sum(p);
+      const double yi = (ys[i] - p) / Ls[i][i];
+      __syncwarp();
+      if (lane == 0) ys[i] = yi;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && tid < nb) yy[k + tid] = ys[tid];
+  const int i = k + nb + blockIdx.x * 256 + tid;
+  if (i < n) {
+    double t = rr[i];
+    for (int l = 0; l < nb; ++l) t = fma(-L[i + (size_t)(k + l) * ld], ys[l], t);
+    rr[i] = t;
+  }
+}
+
+// Backward substitution step for block k: u_k = L_kk^{-T} y_k, y_j -= L_k,j^T u_k (j < k).
+__global__ void __launch_bounds__(256) k_chol_bwd(const double* __restrict__ L, int ld, int n, int k,
+                                                  int nb, double* __restrict__ y,
+                                                  double* __restrict__ u) {
+  __shared__ double Ls[NB][NB + 1];
+  __shared__ double us[NB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* yy = y + (size_t)blockIdx.y * n;
+  double* uu = u + (size_t)blockIdx.y * n;
+  for (int e = tid; e < nb * nb; e += 256) {
+    const int i = e % nb, j = e / nb;
+    Ls[i][j] = (i >= j) ? L[(k + i) + (size_t)(k + j) * ld] : 0.0;
+  }
+  if (tid < nb) us[tid] = yy[k + tid];
+  __syncthreads();
+  if (warp == 0) {
+    for (int i = nb - 1; i >= 0; --i) {
+      double p = 0.0;
+      for (int l = i + 1 + lane; l < nb; l += 32) p = fma(Ls[l][i], us[l], p);
+      p = warp_sum(p);
+      const double ui = (us[i] - p) / Ls[i][i];
+      __syncwarp();
+      if (lane == 0) us[i] = ui;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && tid < nb) uu[k + tid] = us[tid];
+  for (int j = blockIdx.x * 8 + warp; j < k; j += gridDim.x * 8) {
+    double p = 0.0;
+    for (int l = lane; l < nb; l += 32) p = fma(L[(k + l) + (size_t)j * ld], us[l], p);
+    p = warp_sum(p);
+    if (lane == 0) yy[j] -= p;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, unsigned* status,
+                              cudaStream_t st) {
+  k_potrf_diag<<<1, 256, 0, st>>>(S, ld, k, nb, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_chol(double* S, int ld, int n, int k, int nb, cudaStream_t st) {
+  const int rows = n - k - nb;
+  if (rows <= 0) return cudaSuccess;
+  const int smem = 2 * NB * (NB + 1) * (int)sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_trsm_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_trsm_chol<<<(rows + 63) / 64, 64, smem, st>>>(S, ld, n, k, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_fwd(const double* L, int ld, int n, int k, int nb, double* r,
+                            double* y, int nrhs, cudaStream_t st) {
+  const int rows = n - k - nb;
+  const int gx = rows > 0 ? (rows + 255) / 256 : 1;
+  k_chol_fwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, r, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_bwd(const double* L, int ld, int n, int k, int nb, double* y,
+                            double* u, int nrhs, cudaStream_t st) {
+  int gx = (k + 7) / 8;
+  if (gx < 1) gx = 1;
+  if (gx > 1024) gx = 1024;
+  k_chol_bwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, y, u);
+  return cudaGetLastError();
+}
+
+}  // namespace elmddm

@@ -1,0 +1,436 @@
+// Step (b): batched blocked Householder QR of the local matrices [K^s | J], the
+// triangular solve Y_s = A^s R_s^{-1}, and the per-subdomain kernels of the RHS path
+// and of step (d) (q_s = Q_s^T F^s, interface vectors, back-solve).
+//
+// Householder QR (not the normal equations the paper writes for K^+, Section 3) is
+// used because the tanh feature matrices are numerically rank deficient
+// (min|R_ii|/max|R_ii| ~ 1e-19 on the 8x8 Poisson workload); Q_G must come from the
+// reflectors themselves, since forming it as K_G R^{-1} loses all accuracy.
+//
+// Reflectors follow the LAPACK convention: H_j = I - tau_j v_j v_j^T, v_j(j) = 1,
+// stored below the diagonal of K; each panel of QR_NB columns keeps the upper
+// triangular T with H_1 ... H_nb = I - V T V^T, so Q^T = I - V T^T V^T per panel.
+#include "common.cuh"
+
+namespace elmddm {
+
+namespace {
+
+// One block per subdomain: factor the panel of columns [k0, k0+nbe) over rows [k0, m_s).
+__global__ void __launch_bounds__(256) k_panel_qr(double* __restrict__ K, long long kstride, int ld,
+                                                  const int* __restrict__ ms_arr, int k0, int nbe,
+                                                  double* __restrict__ tau_out, int n,
+                                                  double* __restrict__ Tout, long long tstride,
+                                                  double* __restrict__ Vp, long long vstride,
+                                                  unsigned* status) {
+  const int s = blockIdx.x;
+  double* A = K + (size_t)s * kstride;
+  const int m = ms_arr[s];
+  __shared__ double red[33];
+  __shared__ double wred[8][32];
+  __shared__ double d[32];
+  __shared__ double T[32][33];
+  __shared__ double stau[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < 32 * 33; e += 256) (&T[0][0])[e] = 0.0;
+  unsigned bits = 0;
+  __syncthreads();
+
+  for (int j = 0; j < nbe; ++j) {
+    const int c = k0 + j;
+    double* ac = A + (size_t)c * ld;
+    // Norm of the part below the diagonal.
+    double p = 0.0;
+    for (int r = c + 1 + tid; r < m; r += 256) {
+      const double v = ac[r];
+      p = fma(v, v, p);
+    }
+    p = block_sum(p, red);
+    const double alpha = (c < m) ? ac[c] : 0.0;
+    double beta, tau, scal;
+    if (p == 0.0) {
+      tau = 0.0; beta = alpha; scal = 1.0;
+    } else {
+      beta = -copysign(sqrt(fma(alpha, alpha, p)), alpha);
+      tau = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    if (tid == 0) {
+      if (beta == 0.0) bits |= ST_RANK;
+      if (!isfinite(beta)) bits |= ST_NONFINITE;
+    }
+    if (p != 0.0)
+      for (int r = c + 1 + tid; r < m; r += 256) ac[r] *= scal;
+    __syncthreads();
+
+    // d_k = v_j . (column k0+k) over rows >= c, for every other panel column:
+    // for k > j it is the w of H_j applied to column k; for k < j it is v_k . v_j,
+    // the entry the T recurrence needs.
+    double acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+    for (int r = c + 1 + tid; r < m; r += 256) {
+      const double v = ac[r];
+      const double* row = A + r + (size_t)k0 * ld;
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (k < nbe && k != j) acc[k] = fma(v, row[(size_t)k * ld], acc[k]);
+    }
+    const double ws = warp_transpose_sum32(acc);
+    wred[warp][lane] = ws;
+    __syncthreads();
+    if (tid < 32) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += wred[w][tid];
+      if (tid < nbe && tid != j && c < m) t += A[c + (size_t)(k0 + tid) * ld];
+      d[tid] = t;
+    }
+    __syncthreads();
+
+    if (tau != 0.0) {
+      for (int r = c + tid; r < m; r += 256) {
+        const double tv = tau * ((r == c) ? 1.0 : ac[r]);
+        double* row = A + r + (size_t)k0 * ld;
+        for (int k = j + 1; k < nbe; ++k) row[(size_t)k * ld] = fma(-tv, d[k], row[(size_t)k * ld]);
+      }
+    }
+    if (tid < j) {
+      double t = 0.0;
+      for (int l = tid; l < j; ++l) t = fma(T[tid][l], d[l], t);
+      T[tid][j] = -tau * t;
+    }
+    if (tid == 0) {
+      T[j][j] = tau;
+      stau[j] = tau;
+      if (c < m) ac[c] = beta;
+    }
+    __syncthreads();
+  }
+
+  if (tid < nbe) tau_out[(size_t)s * n + k0 + tid] = stau[tid];
+  double* Ts = Tout + (size_t)s * tstride;
+  for (int e = tid; e < 32 * 32; e += 256) Ts[e] = T[e & 31][e >> 5];
+  double* V = Vp + (size_t)s * vstride;
+  const int rows = m - k0;
+  if (rows > 0) {
+    for (int e = tid; e < rows * nbe; e += 256) {
+      const int r = k0 + e % rows, j = e / rows;
+      const double v = r < k0 + j ? 0.0 : (r == k0 + j ? 1.0 : A[r + (size_t)(k0 + j) * ld]);
+      V[r + (size_t)j * ld] = v;
+    }
+  }
+  if (tid == 0 && bits) atomicOr(status, bits);
+}
+
+// Y = A R^{-1} for a tile of 32 rows of Y (one subdomain), in place over A.
+__global__ void __launch_bounds__(256) k_trsm_y(double* __restrict__ Y, long long ystride, int mgld,
+                                                const double* __restrict__ K, long long kstride,
+                                                int ld, const int* __restrict__ mg_arr, int n) {
+  const int s = blockIdx.y, i0 = blockIdx.x * 32;
+  const int mg = mg_arr[s];
+  if (i0 >= mg) return;
+  double* Ys = Y + (size_t)s * ystride;
+  const double* R = K + (size_t)s * kstride;
+  __shared__ double sY[32][33];
+  __shared__ double sR[32][33];
+  const int t = threadIdx.x, ri = t & 31, cg = (t >> 5) * 4;
+  const bool row_ok = (i0 + ri) < mg;
+  for (int jb = 0; jb < n; jb += 32) {
+    const int nbj = min(32, n - jb);
+    double acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int cc = jb + cg + q;
+      acc[q] = (row_ok && cc < n) ? Ys[(i0 + ri) + (size_t)cc * mgld] : 0.0;
+    }
+    for (int l0 = 0; l0 < jb; l0 += 32) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = t + 256 * q, r = e & 31, cc = e >> 5;
+        sY[r][cc] = (i0 + r < mg) ? Ys[(i0 + r) + (size_t)(l0 + cc) * mgld] : 0.0;
+        sR[r][cc] = (jb + cc < n) ? R[(l0 + r) + (size_t)(jb + cc) * ld] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) {
+        const double y = sY[ri][l];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fma(-y, sR[l][cg + q], acc[q]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sY[ri][cg + q] = acc[q];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + 256 * q, r = e & 31, cc = e >> 5;
+      sR[r][cc] = (r <= cc && cc < nbj) ? R[(jb + r) + (size_t)(jb + cc) * ld] : 0.0;
+    }
+    __syncthreads();
+    if (t < 32) {
+      for (int c2 = 0; c2 < nbj; ++c2) {
+        double x = sY[ri][c2];
+        for (int l = 0; l < c2; ++l) x = fma(-sY[ri][l], sR[l][c2], x);
+        sY[ri][c2] = x / sR[c2][c2];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int cc = jb + cg + q;
+      if (row_ok && cc < n) Ys[(i0 + ri) + (size_t)cc * mgld] = sY[ri][cg + q];
+    }
+    __syncthreads();
+  }
+}
+
+// X[r][s][row] = F^s: f/g on interior and boundary rows, zero elsewhere.
+__global__ void k_load_rhs(double* __restrict__ X, const double* __restrict__ rhs, int N,
+                           int m_max, int ld, const int* __restrict__ cnt, unsigned* status) {
+  const int s = blockIdx.y, rh = blockIdx.z;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= ld) return;
+  const int mb_end = cnt[3 * s] + cnt[3 * s + 1];
+  double v = 0.0;
+  if (row < mb_end) {
+    v = rhs[((size_t)rh * N + s) * m_max + row];
+    if (!isfinite(v)) atomicOr(status, ST_NONFINITE);
+  }
+  X[((size_t)rh * N + s) * ld + row] = v;
+}
+
+// x <- Q^T x for one subdomain and one right-hand side, panel by panel.
+__global__ void __launch_bounds__(256) k_apply_qt(double* __restrict__ X, const double* __restrict__ K,
+                                                  long long kstride, int ld,
+                                                  const int* __restrict__ ms_arr, int N, int n,
+                                                  const double* __restrict__ Tb, long long tstride) {
+  const int s = blockIdx.x, rh = blockIdx.y;
+  const int m = ms_arr[s];
+  double* x = X + ((size_t)rh * N + s) * ld;
+  const double* A = K + (size_t)s * kstride;
+  const double* Ts = Tb + (size_t)s * tstride;
+  __shared__ double wred[8][32];
+  __shared__ double w[32], w2[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int nbe = min(32, n - k0);
+    double acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+    for (int r = k0 + tid; r < m; r += 256) {
+      const double xr = x[r];
+      const double* row = A + r + (size_t)k0 * ld;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        if (k < nbe) {
+          if (r > k0 + k) acc[k] = fma(row[(size_t)k * ld], xr, acc[k]);
+          else if (r == k0 + k) acc[k] += xr;
+        }
+      }
+    }
+    const double ws = warp_transpose_sum32(acc);
+    wred[warp][lane] = ws;
+    __syncthreads();
+    if (tid < 32) {
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t += wred[q][tid];
+      w[tid] = tid < nbe ? t : 0.0;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const double* Tk = Ts + (size_t)(k0 / 32) * 1024;
+      double t = 0.0;
+      for (int i = 0; i <= tid; ++i) t = fma(Tk[i + 32 * tid], w[i], t);
+      w2[tid] = t;
+    }
+    __syncthreads();
+    for (int r = k0 + tid; r < m; r += 256) {
+      double xr = x[r];
+      const double* row = A + r + (size_t)k0 * ld;
+      for (int k = 0; k < nbe; ++k) {
+        const double v = r > k0 + k ? row[(size_t)k * ld] : (r == k0 + k ? 1.0 : 0.0);
+        xr = fma(-v, w2[k], xr);
+      }
+      x[r] = xr;
+    }
+    __syncthreads();
+  }
+}
+
+// gq = Q_G q and hq = Y q for one subdomain / right-hand side (warp per interface row).
+__global__ void __launch_bounds__(256) k_iface_vecs(const double* __restrict__ X,
+                                                    const double* __restrict__ K, long long kstride,
+                                                    int ld, const double* __restrict__ Y,
+                                                    long long ystride, int mgld,
+                                                    const int* __restrict__ mg_arr, int N, int n,
+                                                    double* __restrict__ gq,
+                                                    double* __restrict__ hq) {
+  const int s = blockIdx.x, rh = blockIdx.y;
+  const int mg = mg_arr[s];
+  const double* q = X + ((size_t)rh * N + s) * ld;
+  const double* QGt = K + (size_t)s * kstride + (size_t)n * ld;
+  const double* Ys = Y + (size_t)s * ystride;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < mg; i += 8) {
+    double a = 0.0, b = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      const double qj = q[j];
+      a = fma(QGt[j + (size_t)i * ld], qj, a);
+      b = fma(Ys[i + (size_t)j * mgld], qj, b);
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+      gq[((size_t)rh * N + s) * mgld + i] = a;
+      hq[((size_t)rh * N + s) * mgld + i] = b;
+    }
+  }
+}
+
+// out[g] (+)= a[s0][l0] + a[s1][l1] for every interface unknown g.
+__global__ void k_gather2(const int* __restrict__ dofmap, int n_gamma, int mgld, int N,
+                          const double* __restrict__ a, double* __restrict__ out, int accumulate) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, rh = blockIdx.y;
+  if (g >= n_gamma) return;
+  const int s0 = dofmap[4 * g], l0 = dofmap[4 * g + 1], s1 = dofmap[4 * g + 2], l1 = dofmap[4 * g + 3];
+  const double v = a[((size_t)rh * N + s0) * mgld + l0] + a[((size_t)rh * N + s1) * mgld + l1];
+  double* o = out + (size_t)rh * n_gamma + g;
+  *o = accumulate ? *o + v : v;
+}
+
+// z_s = M_s^T (E_s h) (warp per column of M_s).
+__global__ void __launch_bounds__(256) k_mt_h(const double* __restrict__ M, long long mstride, int mgld,
+                                              const int* __restrict__ mg_arr,
+                                              const int* __restrict__ ifc_dof,
+                                              const double* __restrict__ h, int n_gamma, int N,
+                                              double* __restrict__ z) {
+  const int s = blockIdx.x, rh = blockIdx.y;
+  const int mg = mg_arr[s];
+  const double* Ms = M + (size_t)s * mstride;
+  const int* dofs = ifc_dof + (size_t)s * mgld;
+  const double* hh = h + (size_t)rh * n_gamma;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < mg; i += 8) {
+    double a = 0.0;
+    for (int k = lane; k < mg; k += 32) a = fma(Ms[k + (size_t)i * mgld], hh[dofs[k]], a);
+    a = warp_sum(a);
+    if (lane == 0) z[((size_t)rh * N + s) * mgld + i] = a;
+  }
+}
+
+// c^s = R^{-1} (q + Q_G^T E_s u), one block per (subdomain, right-hand side).
+__global__ void __launch_bounds__(256) k_backsolve(const double* __restrict__ X,
+                                                   const double* __restrict__ K, long long kstride,
+                                                   int ld, const int* __restrict__ mg_arr,
+                                                   const int* __restrict__ ifc_dof, int mgld,
+                                                   const double* __restrict__ u, int n_gamma, int N,
+                                                   int n, double* __restrict__ cout) {
+  extern __shared__ double v[];
+  const int s = blockIdx.x, rh = blockIdx.y;
+  const int mg = mg_arr[s];
+  const double* q = X + ((size_t)rh * N + s) * ld;
+  const double* A = K + (size_t)s * kstride;
+  const double* QGt = A + (size_t)n * ld;
+  const int* dofs = ifc_dof + (size_t)s * mgld;
+  const double* uu = u + (size_t)rh * n_gamma;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = tid; j < n; j += 256) {
+    double a = q[j];
+    for (int i = 0; i < mg; ++i) a = fma(QGt[j + (size_t)i * ld], uu[dofs[i]], a);
+    v[j] = a;
+  }
+  __syncthreads();
+  for (int jb = ((n - 1) / 32) * 32; jb >= 0; jb -= 32) {
+    const int nbj = min(32, n - jb);
+    if (warp == 0) {
+      for (int j = jb + nbj - 1; j >= jb; --j) {
+        const double cj = v[j] / A[j + (size_t)j * ld];
+        __syncwarp();
+        if (lane == 0) v[j] = cj;
+        if (lane < j - jb) v[jb + lane] = fma(-A[(jb + lane) + (size_t)j * ld], cj, v[jb + lane]);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < jb; i += 256) {
+      double t = v[i];
+      for (int l = 0; l < nbj; ++l) t = fma(-A[i + (size_t)(jb + l) * ld], v[jb + l], t);
+      v[i] = t;
+    }
+    __syncthreads();
+  }
+  double* co = cout + ((size_t)rh * N + s) * n;
+  for (int j = tid; j < n; j += 256) co[j] = v[j];
+}
+
+}  // namespace
+
+cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
+                            int nbe, double* tau, int n, double* T, long long tstride,
+                            double* Vp, long long vstride, unsigned* status, cudaStream_t st) {
+  k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride, Vp, vstride,
+                                status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_y(double* Y, long long ystride, int mgld, const double* K,
+                          long long kstride, int ld, const int* mg, int mgmax, int N, int n,
+                          cudaStream_t st) {
+  if (mgmax <= 0) return cudaSuccess;
+  k_trsm_y<<<dim3((mgmax + 31) / 32, N), 256, 0, st>>>(Y, ystride, mgld, K, kstride, ld, mg, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_rhs(double* X, const double* rhs, int N, int m_max, int ld,
+                            const int* cnt, int nrhs, unsigned* status, cudaStream_t st) {
+  k_load_rhs<<<dim3((ld + 255) / 256, N, nrhs), 256, 0, st>>>(X, rhs, N, m_max, ld, cnt, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_qt(double* X, const double* K, long long kstride, int ld,
+                            const int* ms, int N, int n, const double* T, long long tstride,
+                            int nrhs, cudaStream_t st) {
+  k_apply_qt<<<dim3(N, nrhs), 256, 0, st>>>(X, K, kstride, ld, ms, N, n, T, tstride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iface_vecs(const double* X, const double* K, long long kstride, int ld,
+                              const double* Y, long long ystride, int mgld, const int* mg,
+                              int N, int n, int nrhs, double* gq, double* hq, cudaStream_t st) {
+  k_iface_vecs<<<dim3(N, nrhs), 256, 0, st>>>(X, K, kstride, ld, Y, ystride, mgld, mg, N, n, gq,
+                                              hq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather2(const int* dofmap, int n_gamma, int mgld, int N, const double* a,
+                           double* out, int accumulate, int nrhs, cudaStream_t st) {
+  if (n_gamma <= 0) return cudaSuccess;
+  k_gather2<<<dim3((n_gamma + 255) / 256, nrhs), 256, 0, st>>>(dofmap, n_gamma, mgld, N, a, out,
+                                                               accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mt_h(const double* M, long long mstride, int mgld, const int* mg,
+                        const int* ifc_dof, const double* h, int n_gamma, int N, int nrhs,
+                        double* z, cudaStream_t st) {
+  k_mt_h<<<dim3(N, nrhs), 256, 0, st>>>(M, mstride, mgld, mg, ifc_dof, h, n_gamma, N, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backsolve(const double* X, const double* K, long long kstride, int ld,
+                             const int* mg, const int* ifc_dof, int mgld, const double* u,
+                             int n_gamma, int N, int n, int nrhs, double* c, cudaStream_t st) {
+  const size_t smem = (size_t)n * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_backsolve<<<dim3(N, nrhs), 256, smem, st>>>(X, K, kstride, ld, mg, ifc_dof, mgld, u, n_gamma,
+                                                N, n, c);
+  return cudaGetLastError();
+}
+
+}  // namespace elmddm

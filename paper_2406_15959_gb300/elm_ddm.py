@@ -1,0 +1,235 @@
+"""Python binding of libelmddm (include/elm_ddm.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; PyTorch provides device
+memory and the stream.  If the library cannot be loaded this module raises; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_RANK, ERR_NOT_SPD = range(8)
+ERROR_NAMES = {ERR_ARG: "ERR_ARG", ERR_STATE: "ERR_STATE", ERR_CUDA: "ERR_CUDA",
+               ERR_OOM: "ERR_OOM", ERR_NONFINITE: "ERR_NONFINITE", ERR_RANK: "ERR_RANK",
+               ERR_NOT_SPD: "ERR_NOT_SPD"}
+
+# Every symbol the header declares.
+SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve",
+           "elm_ddm_eval", "elm_ddm_export", "elm_ddm_check", "elm_ddm_get_info",
+           "elm_ddm_destroy", "elm_ddm_last_error")
+BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
+
+
+class ElmDdmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("n_sub", ctypes.c_int32), ("n_neurons", ctypes.c_int32),
+                ("m_max", ctypes.c_int32), ("n_gamma", ctypes.c_int32),
+                ("op", ctypes.c_int32), ("max_rhs", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libelmddm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libelmddm.so not found at {path}")
+    lib = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    lib.elm_ddm_setup.argtypes = [ctypes.POINTER(Desc), P, P, P, P, P, ctypes.POINTER(P)]
+    lib.elm_ddm_assemble.argtypes = [P, P, P]
+    lib.elm_ddm_schur.argtypes = [P]
+    lib.elm_ddm_solve.argtypes = [P, P, I, P, P]
+    lib.elm_ddm_eval.argtypes = [P, I, P, P, P, P, P]
+    lib.elm_ddm_export.argtypes = [P, I, I, P, I]
+    lib.elm_ddm_check.argtypes = [P]
+    lib.elm_ddm_get_info.argtypes = [P, I, D]
+    lib.elm_ddm_destroy.argtypes = [P]
+    lib.elm_ddm_last_error.argtypes = [P]
+    lib.elm_ddm_last_error.restype = ctypes.c_char_p
+    for name in SYMBOLS:
+        if name != "elm_ddm_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+@dataclass
+class GeometryArrays:
+    counts: np.ndarray   # int32 [N, 3]
+    xy: np.ndarray       # float64 [N, m_max, 2]
+    nrm: np.ndarray      # float64 [N, m_max, 2]
+    dof: np.ndarray      # int32 [N, m_max]
+    n_gamma: int
+
+    @classmethod
+    def from_geometry(cls, g):
+        return cls(np.ascontiguousarray(g.counts, np.int32), np.ascontiguousarray(g.xy, np.float64),
+                   np.ascontiguousarray(g.nrm, np.float64), np.ascontiguousarray(g.dof, np.int32),
+                   int(g.n_gamma))
+
+
+class Solver:
+    """One decomposition on one GPU: setup -> assemble(theta) -> schur() -> solve(rhs)."""
+
+    def __init__(self, geom, n_neurons: int, max_rhs: int = 1, stream=None):
+        import torch
+        self.lib = load()
+        ga = geom if isinstance(geom, GeometryArrays) else GeometryArrays.from_geometry(geom)
+        N, m_max = ga.xy.shape[0], ga.xy.shape[1]
+        self.N, self.n, self.m_max, self.n_gamma = N, int(n_neurons), m_max, ga.n_gamma
+        self.max_rhs = max_rhs
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        desc = Desc(N, self.n, m_max, ga.n_gamma, 0, max_rhs)
+        h = ctypes.c_void_p()
+        self._keep = ga
+        rc = self.lib.elm_ddm_setup(ctypes.byref(desc), ga.counts.ctypes.data, ga.xy.ctypes.data,
+                                    ga.nrm.ctypes.data, ga.dof.ctypes.data,
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != OK:
+            raise ElmDdmError(rc, self.lib.elm_ddm_last_error(None).decode())
+        self.h = h
+
+    # -- helpers
+    def _check_rc(self, rc):
+        if rc != OK:
+            raise ElmDdmError(rc, self.lib.elm_ddm_last_error(self.h).decode())
+
+    def info(self, key: int) -> float:
+        v = ctypes.c_double()
+        self._check_rc(self.lib.elm_ddm_get_info(self.h, key, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def launches(self) -> int:
+        return int(self.info(2))
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self.info(1))
+
+    # -- Algorithm 1
+    def assemble(self, W, b):
+        self._check_rc(self.lib.elm_ddm_assemble(self.h, _ptr(W), _ptr(b)))
+
+    def schur(self):
+        self._check_rc(self.lib.elm_ddm_schur(self.h))
+
+    def solve(self, rhs, u_gamma=None, c=None):
+        """rhs: CUDA float64 [nrhs, N, m_max] or [N, m_max].  Returns (u_gamma, c)."""
+        import torch
+        squeeze = rhs.dim() == 2
+        r = rhs.unsqueeze(0) if squeeze else rhs
+        nrhs = r.shape[0]
+        if c is None:
+            c = torch.empty((nrhs, self.N, self.n), dtype=torch.float64, device=rhs.device)
+        if u_gamma is None and self.n_gamma > 0:
+            u_gamma = torch.empty((nrhs, self.n_gamma), dtype=torch.float64, device=rhs.device)
+        self._check_rc(self.lib.elm_ddm_solve(self.h, _ptr(r.contiguous()), nrhs,
+                                              _ptr(u_gamma) if self.n_gamma > 0 else None, _ptr(c)))
+        if squeeze:
+            return (u_gamma[0] if u_gamma is not None else None), c[0]
+        return u_gamma, c
+
+    def eval(self, xy, owner, c, u=None, grad=None):
+        import torch
+        npts = xy.shape[0]
+        if u is None:
+            u = torch.empty(npts, dtype=torch.float64, device=xy.device)
+        if grad is None:
+            grad = torch.empty((npts, 2), dtype=torch.float64, device=xy.device)
+        self._check_rc(self.lib.elm_ddm_eval(self.h, npts, _ptr(xy), _ptr(owner), _ptr(c), _ptr(u),
+                                             _ptr(grad)))
+        return u, grad
+
+    def export(self, what: int, s: int = 0):
+        """Copy of an internal matrix (BUF_*) as a CUDA tensor [rows, cols] (column-major
+        data, returned transposed into row-major indexing)."""
+        import torch
+        rows, cols = self._export_shape(what, s)
+        out = torch.empty((max(cols, 1), max(rows, 1)), dtype=torch.float64, device="cuda")
+        self._check_rc(self.lib.elm_ddm_export(self.h, what, s, _ptr(out), max(rows, 1)))
+        return out.t()[:rows, :cols]
+
+    def _export_shape(self, what, s):
+        mi, mb, mg = (int(v) for v in self._keep.counts[s])
+        if what == BUF_K:
+            return mi + mb + mg, self.n + mg
+        if what == BUF_A:
+            return mg, self.n
+        if what in (BUF_D, BUF_M):
+            return mg, mg
+        if what == BUF_L:
+            return self.n_gamma, self.n_gamma
+        raise ValueError(what)
+
+    def check(self):
+        self._check_rc(self.lib.elm_ddm_check(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.elm_ddm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def run_workload(w, device="cuda", max_rhs=1):
+    """Convenience: full solve of a :class:`workload.Workload` on the GPU.
+    Returns dict with u_gamma, c, u and grad at the test points (torch CUDA tensors)."""
+    import torch
+    dev = torch.device(device)
+    s = Solver(w.geom, w.n_neurons, max_rhs=max_rhs)
+    W = torch.as_tensor(w.W, device=dev).contiguous()
+    b = torch.as_tensor(w.b, device=dev).contiguous()
+    rhs = torch.as_tensor(w.rhs, device=dev).contiguous()
+    txy = torch.as_tensor(w.test_xy, device=dev).contiguous()
+    own = torch.as_tensor(w.test_owner, device=dev).contiguous()
+    s.assemble(W, b)
+    s.schur()
+    ug, c = s.solve(rhs)
+    u, g = s.eval(txy, own, c)
+    s.check()
+    out = {"u_gamma": ug, "c": c, "u": u, "grad": g, "solver": s}
+    return out

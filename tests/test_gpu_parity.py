@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances.  Assembly is elementwise (one tanh per entry, a few roundings):
+rtol 1e-13.  The solution u at the test points and u_Gamma: relative L2 <= 1e-8 (the
+target for the FP64 path).  Factor-level quantities (R, D_s, M_s, S) and the output
+weights c are compared only on well-conditioned cases (min|R_ii|/max|R_ii| > 1e-6):
+for numerically rank-deficient K^s, two backward-stable QRs legitimately disagree in
+c (the test points still agree to ~1e-12, see the oracle's sensitivity note).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import elm_oracle as O
+from paper_2406_15959_gb300 import elm_ddm as E
+from paper_2406_15959_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+DEV = torch.device("cuda:0")
+
+CASES = {
+    "2x2_n200": wl.poisson_2x2_n200,
+    "3x3_ragged": lambda: wl.build(3, 3, 150, 17, 13, 23, 21, theta="paper", theta_seed=5,
+                                   source="fourier", source_seed=5, n_test_side=60),
+    "3x2_nonsquare": lambda: wl.build(3, 2, 70, 9, 11, 7, 6, theta="paper", theta_seed=6,
+                                      source="sin2pi_exp", n_test_side=50),
+    "1x1_classical": lambda: wl.build(1, 1, 90, 12, 11, 15, 1, theta="paper", theta_seed=7,
+                                      source="sinsin", n_test_side=40),
+    "4x4_wellcond": lambda: wl.build(4, 4, 40, 10, 10, 12, 12, theta="paper", theta_seed=8,
+                                     source="fourier", source_seed=8, c=0.5, n_test_side=40),
+    "5x3_edges70": lambda: wl.build(5, 3, 97, 14, 12, 30, 70, theta="paper", theta_seed=9,
+                                    source="fourier", source_seed=9, n_test_side=50),
+}
+
+_cache = {}
+
+
+def get(name):
+    if name not in _cache:
+        w = CASES[name]()
+        res = O.solve(w.geom, w.W, w.b, w.rhs)
+        u, g = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
+        _cache[name] = (w, res, u, g)
+    return _cache[name]
+
+
+def t(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV, dtype=dtype)
+
+
+def gpu_run(w, max_rhs=1, rhs=None):
+    s = E.Solver(w.geom, w.n_neurons, max_rhs=max_rhs)
+    s.assemble(t(w.W), t(w.b))
+    s.schur()
+    ug, c = s.solve(t(w.rhs if rhs is None else rhs))
+    u, g = s.eval(t(w.test_xy), t(w.test_owner, torch.int32), c)
+    s.check()
+    return s, ug, c, u, g
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_assembly_matches_oracle(name):
+    w, _, _, _ = get(name)
+    s = E.Solver(w.geom, w.n_neurons)
+    s.assemble(t(w.W), t(w.b))
+    g = w.geom
+    for sd in range(g.n_sub):
+        K, A = O.assemble_local(g.xy[sd], g.nrm[sd], g.counts[sd], w.W[sd], w.b[sd])
+        Kg = s.export(E.BUF_K, sd).cpu().numpy()
+        n = w.n_neurons
+        np.testing.assert_allclose(Kg[:, :n], K, rtol=1e-13, atol=1e-14 * np.abs(K).max())
+        mi, mb, mg = (int(v) for v in g.counts[sd])
+        J = np.zeros((K.shape[0], mg))
+        J[mi + mb + np.arange(mg), np.arange(mg)] = 1.0
+        assert np.array_equal(Kg[:, n:], J)
+        if mg:
+            Ag = s.export(E.BUF_A, sd).cpu().numpy()
+            np.testing.assert_allclose(Ag, A, rtol=1e-13, atol=1e-14 * np.abs(A).max())
+    s.check()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solution_matches_oracle(name):
+    w, res, u_or, g_or = get(name)
+    s, ug, c, u, g = gpu_run(w)
+    assert rel(u.cpu().numpy(), u_or) <= 1e-8
+    assert rel(g.cpu().numpy(), g_or) <= 1e-7
+    if w.geom.n_gamma:
+        assert rel(ug.cpu().numpy(), res.u_gamma) <= 1e-8
+    if res.rdiag_ratio.min() > 1e-6:
+        assert rel(c.cpu().numpy(), res.c) <= 1e-8
+
+
+def test_factor_pieces_match_oracle_when_well_conditioned():
+    w, res, _, _ = get("4x4_wellcond")
+    assert res.rdiag_ratio.min() > 1e-6
+    s, *_ = gpu_run(w)
+    n = w.n_neurons
+    for sd, L in enumerate(res.locs):
+        F = s.export(E.BUF_K, sd).cpu().numpy()
+        R = np.triu(F[:n, :n])
+        # same Householder sign convention as LAPACK's geqrf: R agrees entrywise
+        assert np.abs(R - L.R).max() <= 1e-11 * np.abs(L.R).max()
+        QGt = F[:n, n:]
+        assert np.abs(QGt - L.QG.T).max() <= 1e-11
+        D = s.export(E.BUF_D, sd).cpu().numpy()
+        M = s.export(E.BUF_M, sd).cpu().numpy()
+        assert np.abs(D - L.D).max() <= 1e-11
+        assert np.abs(M - L.M).max() <= 1e-10 * max(1.0, np.abs(L.M).max())
+    Lg = np.tril(s.export(E.BUF_L).cpu().numpy())
+    S = Lg @ Lg.T
+    assert np.abs(S - res.S).max() <= 1e-11 * np.abs(res.S).max()
+
+
+def test_full_size_8x8_n1000_matches_oracle():
+    """The benchmark workload itself (8x8 subdomains, 1000 neurons, 2400 rows each,
+    n_Gamma = 11200) in the launch configuration the benchmark times."""
+    w = wl.poisson_8x8_n1000()
+    res = O.solve(w.geom, w.W, w.b, w.rhs, keep=False)
+    u_or, g_or = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
+    s, ug, c, u, g = gpu_run(w)
+    assert rel(u.cpu().numpy(), u_or) <= 1e-8
+    assert rel(ug.cpu().numpy(), res.u_gamma) <= 1e-8
+    # and the method itself is accurate on this manufactured solution
+    l2, _ = O.rel_errors(u.cpu().numpy(), g.cpu().numpy(), w.src.u(w.test_xy), w.src.grad_u(w.test_xy))
+    assert l2 < 1e-9
+
+
+def test_multiple_rhs_equal_single_solves():
+    w, _, _, _ = get("3x3_ragged")
+    srcs = [wl.make_source("fourier", seed=k, modes=3) for k in range(3)]
+    rhs = np.stack([wl.rhs_rows(w.geom, sr) for sr in srcs])
+    s = E.Solver(w.geom, w.n_neurons, max_rhs=3)
+    s.assemble(t(w.W), t(w.b))
+    s.schur()
+    ug3, c3 = s.solve(t(rhs))
+    s.check()
+    for k in range(3):
+        ug1, c1 = s.solve(t(rhs[k]))
+        s.check()
+        assert torch.equal(c1, c3[k]) and torch.equal(ug1, ug3[k])
+        res = O.solve(w.geom, w.W, w.b, rhs[k], keep=False)
+        assert rel(ug1.cpu().numpy(), res.u_gamma) <= 1e-8
+
+
+def test_results_are_bitwise_repeatable():
+    w, _, _, _ = get("5x3_edges70")
+    _, ug1, c1, u1, _ = gpu_run(w)
+    _, ug2, c2, u2, _ = gpu_run(w)
+    assert torch.equal(c1, c2) and torch.equal(ug1, ug2) and torch.equal(u1, u2)
+
+
+@pytest.mark.parametrize("name", ["4x4_wellcond", "3x2_nonsquare"])
+def test_eval_matches_oracle_evaluate(name):
+    """u = sum_j c_j tanh(w_j.x + b_j) with the oracle's c.  The error bound of a sum is
+    eps * sum_j |c_j t_j| (ill-conditioned c has |c| >> |u|, so the bound is per point)."""
+    w, res, u_or, g_or = get(name)
+    s = E.Solver(w.geom, w.n_neurons)
+    s.assemble(t(w.W), t(w.b))
+    u, g = s.eval(t(w.test_xy), t(w.test_owner, torch.int32), t(res.c))
+    s.check()
+    mag = np.zeros(len(w.test_xy))
+    gmag = np.zeros(len(w.test_xy))
+    for sd in range(w.geom.n_sub):
+        idx = np.nonzero(w.test_owner == sd)[0]
+        tt = O.hidden(w.W[sd], w.b[sd], w.test_xy[idx])
+        mag[idx] = np.abs(tt * res.c[sd]).sum(1)
+        gmag[idx] = (np.abs((1 - tt * tt) * res.c[sd]) @ np.abs(w.W[sd])).sum(1)
+    assert np.all(np.abs(u.cpu().numpy() - u_or) <= 1e-14 * len(w.b[0]) * mag + 1e-300)
+    assert np.all(np.abs(g.cpu().numpy() - g_or).max(1) <= 1e-14 * len(w.b[0]) * gmag + 1e-300)
+
+
+def test_call_order_and_numerical_failures_are_reported():
+    w, _, _, _ = get("3x2_nonsquare")
+    s = E.Solver(w.geom, w.n_neurons)
+    with pytest.raises(E.ElmDdmError) as ei:
+        s.schur()
+    assert ei.value.code == E.ERR_STATE
+    s.assemble(t(w.W), t(w.b))
+    with pytest.raises(E.ElmDdmError) as ei:
+        s.solve(t(w.rhs))
+    assert ei.value.code == E.ERR_STATE
+    s.schur()
+    with pytest.raises(E.ElmDdmError) as ei:
+        s.schur()
+    assert ei.value.code == E.ERR_STATE
+    with pytest.raises(E.ElmDdmError) as ei:
+        s.solve(t(np.stack([w.rhs, w.rhs])))
+    assert ei.value.code == E.ERR_ARG
+    bad = w.rhs.copy()
+    bad[1, 0] = np.nan
+    s.solve(t(bad))
+    with pytest.raises(E.ElmDdmError) as ei:
+        s.check()
+    assert ei.value.code == E.ERR_NONFINITE
+    s.solve(t(w.rhs))
+    s.check()                       # status word was cleared
+    # a neuron with w = 0, b = 0 gives an all-zero column of K: R has a zero pivot
+    W = w.W.copy(); b = w.b.copy()
+    W[2, 5] = 0.0; b[2, 5] = 0.0
+    s.assemble(t(W), t(b))
+    s.schur()
+    with pytest.raises(E.ElmDdmError) as ei:
+        s.check()
+    assert ei.value.code == E.ERR_RANK
