@@ -24,6 +24,14 @@ struct LaunchRec {
   bool ta, tb;
   double alpha, beta;
   int flags;
+  double flops;  // algorithmic flops of the launch (2mnk per GEMM; m(m+1)k for a lower SYRK)
+};
+
+// One profiled launch: events around it, its class and algorithmic flops.
+struct ProfRec {
+  cudaEvent_t a, b;
+  const char* name;
+  double flops;
 };
 
 struct Edge {
@@ -63,6 +71,11 @@ struct elm_ddm_handle {
   std::vector<LaunchRec> s_recs;     // Mdiag adds, D adds, M^T M gemms
   std::vector<LaunchRec> syrk_recs;  // one per Cholesky block step
   int state = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<ProfRec> prof;
+  int prof_dropped = 0;
   long long launches = 0;
   size_t bytes = 0;
   std::string err;
@@ -100,20 +113,57 @@ void free_all(elm_ddm_handle* h) {
   h->allocs.clear();
 }
 
-#define ELM_LAUNCH(h, expr, where)                       \
-  do {                                                   \
-    cudaError_t e_ = (expr);                             \
-    (h)->launches++;                                     \
+cudaEvent_t next_event(elm_ddm_handle* h) {
+  if (h->ev_used < h->ev_pool.size()) return h->ev_pool[h->ev_used++];
+  if (h->ev_pool.size() >= 65536) return nullptr;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  h->ev_pool.push_back(e);
+  h->ev_used++;
+  return e;
+}
+
+// Records an event pair around one launch when profiling is enabled.
+struct ProfScope {
+  elm_ddm_handle* h;
+  cudaEvent_t a = nullptr;
+  const char* name;
+  double flops;
+  ProfScope(elm_ddm_handle* h_, const char* n, double f) : h(h_), name(n), flops(f) {
+    if (h->profiling) {
+      a = next_event(h);
+      if (a) cudaEventRecord(a, h->st);
+    }
+  }
+  ~ProfScope() {
+    if (!h->profiling) return;
+    cudaEvent_t b = a ? next_event(h) : nullptr;
+    if (!b) { h->prof_dropped++; return; }
+    cudaEventRecord(b, h->st);
+    h->prof.push_back({a, b, name, flops});
+  }
+};
+
+#define ELM_LAUNCH_F(h, expr, where, flops)                  \
+  do {                                                       \
+    cudaError_t e_;                                          \
+    {                                                        \
+      ProfScope ps_((h), (where), (flops));                  \
+      e_ = (expr);                                           \
+    }                                                        \
+    (h)->launches++;                                         \
     if (e_ != cudaSuccess) return cuda_fail((h), e_, where); \
   } while (0)
+#define ELM_LAUNCH(h, expr, where) ELM_LAUNCH_F(h, expr, where, 0.0)
 
-int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first, size_t cnt) {
+int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first, size_t cnt,
+             const char* gemm_name) {
   for (size_t r = first; r < first + cnt && r < recs.size(); ++r) {
     const LaunchRec& L = recs[r];
     if (L.count <= 0) continue;
     if (L.kind == 0)
-      ELM_LAUNCH(h, launch_gemm(L.ta, L.tb, h->gd + L.off, L.count, L.max_tiles, L.alpha, L.beta,
-                                L.flags, h->st), "gemm");
+      ELM_LAUNCH_F(h, launch_gemm(L.ta, L.tb, h->gd + L.off, L.count, L.max_tiles, L.alpha, L.beta,
+                                  L.flags, h->st), gemm_name, L.flops);
     else
       ELM_LAUNCH(h, launch_add_blocks(h->ad + L.off, L.count, L.max_tiles, h->st), "add_blocks");
   }
@@ -295,17 +345,18 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   std::vector<AddDesc> ads;
   auto add_gemm_rec = [&](std::vector<LaunchRec>& recs, const std::vector<GemmDesc>& batch, bool ta,
                           bool tb, double alpha, double beta, int flags) {
-    LaunchRec L{0, (int)gds.size(), 0, 0, ta, tb, alpha, beta, flags};
+    LaunchRec L{0, (int)gds.size(), 0, 0, ta, tb, alpha, beta, flags, 0.0};
     for (const GemmDesc& d : batch) {
       if (d.m <= 0 || d.n <= 0) continue;
       gds.push_back(d);
       L.count++;
       L.max_tiles = std::max(L.max_tiles, tiles64(d.m, d.n));
+      L.flops += (flags & GEMM_LOWER) ? (double)d.m * (d.m + 1) * d.k : 2.0 * d.m * d.n * d.k;
     }
     recs.push_back(L);
   };
   auto add_add_rec = [&](std::vector<LaunchRec>& recs, const std::vector<AddDesc>& batch) {
-    LaunchRec L{1, (int)ads.size(), 0, 0, false, false, 0, 0, 0};
+    LaunchRec L{1, (int)ads.size(), 0, 0, false, false, 0, 0, 0, 0.0};
     for (const AddDesc& d : batch) {
       if (d.rows <= 0 || d.cols <= 0) continue;
       ads.push_back(d);
@@ -495,26 +546,26 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     ELM_LAUNCH(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->T +
                                   (size_t)b * QR_NB * QR_NB, h->tstride, h->Vp, h->vstride, h->status,
                                   h->st), "panel_qr");
-    int rc = run_recs(h, h->qr_recs, 3 * (size_t)b, 3);
+    int rc = run_recs(h, h->qr_recs, 3 * (size_t)b, 3, "gemm_qr");
     if (rc) return rc;
   }
   h->state = 0;  // K is factored in place: assemble again before another schur
   if (h->ng > 0) {
     ELM_LAUNCH(h, launch_trsm_y(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg, h->mgmax,
                                 h->N, h->n, h->st), "trsm_y");
-    int rc = run_recs(h, h->dm_recs, 0, h->dm_recs.size());
+    int rc = run_recs(h, h->dm_recs, 0, h->dm_recs.size(), "gemm_dm");
     if (rc) return rc;
     cudaError_t e = cudaMemsetAsync(h->S, 0, (size_t)h->ng * h->ng * sizeof(double), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->Mdiag, 0, h->mdiag_elems * sizeof(double), h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "schur: memset");
-    rc = run_recs(h, h->s_recs, 0, h->s_recs.size());
+    rc = run_recs(h, h->s_recs, 0, h->s_recs.size(), "gemm_schur");
     if (rc) return rc;
     for (int k = 0, step = 0; k < h->ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, h->ng - k);
       ELM_LAUNCH(h, launch_potrf_diag(h->S, h->ng, k, nb, h->status, h->st), "potrf");
       if (h->ng - k - nb > 0) {
         ELM_LAUNCH(h, launch_trsm_chol(h->S, h->ng, h->ng, k, nb, h->st), "trsm_chol");
-        rc = run_recs(h, h->syrk_recs, step, 1);
+        rc = run_recs(h, h->syrk_recs, step, 1, "gemm_syrk");
         if (rc) return rc;
       }
     }
@@ -611,6 +662,44 @@ int elm_ddm_check(elm_ddm_handle* h) {
   return ELM_DDM_OK;
 }
 
+int elm_ddm_profile(elm_ddm_handle* h, int enable) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  h->profiling = enable != 0;
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_profile_report(elm_ddm_handle* h, char* buf, int buflen) {
+  if (!h || !buf || buflen < 2) return ELM_DDM_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "profile_report");
+  struct Acc { long long n = 0; double ms = 0, flops = 0; };
+  std::map<std::string, Acc> acc;
+  for (const ProfRec& r : h->prof) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) { cudaGetLastError(); continue; }
+    Acc& a = acc[r.name];
+    a.n++; a.ms += ms; a.flops += r.flops;
+  }
+  std::string out = "{";
+  bool first = true;
+  for (auto& kv : acc) {
+    char tmp[256];
+    snprintf(tmp, sizeof tmp, "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e}",
+             first ? "" : ", ", kv.first.c_str(), kv.second.n, kv.second.ms, kv.second.flops);
+    out += tmp;
+    first = false;
+  }
+  char tail[64];
+  snprintf(tail, sizeof tail, "%s\"_dropped\": %d}", first ? "" : ", ", h->prof_dropped);
+  out += tail;
+  h->prof.clear();
+  h->ev_used = 0;
+  h->prof_dropped = 0;
+  if ((int)out.size() + 1 > buflen) return fail(h, ELM_DDM_ERR_ARG, "profile_report: buffer too small");
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return ELM_DDM_OK;
+}
+
 int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value) {
   if (!h || !value) return ELM_DDM_ERR_ARG;
   switch (key) {
@@ -629,6 +718,7 @@ int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value) {
 int elm_ddm_destroy(elm_ddm_handle* h) {
   if (!h) return ELM_DDM_ERR_ARG;
   cudaStreamSynchronize(h->st);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   free_all(h);
   delete h;
   return ELM_DDM_OK;

@@ -22,7 +22,8 @@ ERROR_NAMES = {ERR_ARG: "ERR_ARG", ERR_STATE: "ERR_STATE", ERR_CUDA: "ERR_CUDA",
 # Every symbol the header declares.
 SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve",
            "elm_ddm_eval", "elm_ddm_export", "elm_ddm_check", "elm_ddm_get_info",
-           "elm_ddm_destroy", "elm_ddm_last_error")
+           "elm_ddm_profile", "elm_ddm_profile_report", "elm_ddm_destroy",
+           "elm_ddm_last_error")
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
 
 
@@ -62,6 +63,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_eval.argtypes = [P, I, P, P, P, P, P]
     lib.elm_ddm_export.argtypes = [P, I, I, P, I]
     lib.elm_ddm_check.argtypes = [P]
+    lib.elm_ddm_profile.argtypes = [P, I]
+    lib.elm_ddm_profile_report.argtypes = [P, ctypes.c_char_p, I]
     lib.elm_ddm_get_info.argtypes = [P, I, D]
     lib.elm_ddm_destroy.argtypes = [P]
     lib.elm_ddm_last_error.argtypes = [P]
@@ -193,6 +196,15 @@ class Solver:
         if what == BUF_L:
             return self.n_gamma, self.n_gamma
         raise ValueError(what)
+
+    def profile(self, enable: bool = True):
+        self._check_rc(self.lib.elm_ddm_profile(self.h, int(enable)))
+
+    def profile_report(self) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check_rc(self.lib.elm_ddm_profile_report(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def check(self):
         self._check_rc(self.lib.elm_ddm_check(self.h))
