@@ -55,6 +55,7 @@ extern "C" {
 #define ELM_DDM_ERR_NONFINITE 5  /* NaN or Inf in theta, f/g or an intermediate */
 #define ELM_DDM_ERR_RANK      6  /* some R^s has an exactly zero diagonal entry */
 #define ELM_DDM_ERR_NOT_SPD   7  /* a Cholesky pivot of the Schur matrix was <= 0 */
+#define ELM_DDM_ERR_CAPACITY  8  /* request larger than a no-allocation entry point's fixed scratch */
 
 /* Differential operators. */
 #define ELM_DDM_OP_POISSON 0  /* L = -Laplacian (Eq. (4.4)) */
@@ -174,6 +175,36 @@ int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value);
  */
 int elm_ddm_profile(elm_ddm_handle* h, int enable);
 int elm_ddm_profile_report(elm_ddm_handle* h, char* buf, int buflen);
+
+/*
+ * No-allocation Cholesky solve.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc -- code running while a CUDA graph is being
+ * captured in global mode, hosts that route all device memory through their own pool
+ * and forbid hidden allocations, real-time loops.  It solves L L^T u = b for nrhs
+ * right-hand sides with the same blocked substitution kernels as elm_ddm_solve's
+ * interface solve, needs no handle, and calls no cudaMalloc, cudaFree or allocating
+ * library routine: its working vectors live in one fixed device array of
+ * 2 * ELM_DDM_NOALLOC_MAX_ELEMS doubles (2 MiB) that every GPU loading the library holds
+ * until the process exits.
+ *   L     device double, lower Cholesky factor (n x n, column-major, leading dimension
+ *         ld >= n; the strict upper triangle is not read) -- e.g. elm_ddm_export's
+ *         ELM_DDM_BUF_L
+ *   b     device double [nrhs][n] right-hand sides (read only; may alias u)
+ *   u     device double [nrhs][n] solutions
+ *   stream cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Returns ELM_DDM_ERR_ARG for NULL pointers, n < 1, nrhs < 1 or ld < n;
+ * ELM_DDM_ERR_CAPACITY if n * nrhs > ELM_DDM_NOALLOC_MAX_ELEMS (nothing is enqueued);
+ * ELM_DDM_ERR_CUDA if a launch or copy fails.  Asynchronous otherwise.
+ * The first call on each device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture begins.
+ * All calls share the array and it keeps the previous call's contents (nothing in it
+ * needs to start at zero: each call overwrites what it reads).  Calls whose work
+ * overlaps on the GPU -- on different streams, or from different host threads without
+ * ordering -- race on the array; order them on one stream.
+ */
+#define ELM_DDM_NOALLOC_MAX_ELEMS 131072
+int elm_ddm_chol_solve_noalloc(const double* L, int n, int ld, const double* b, int nrhs,
+                               double* u, void* stream);
 
 /* Frees all device workspace and the handle.  Synchronises the stream first. */
 int elm_ddm_destroy(elm_ddm_handle* h);

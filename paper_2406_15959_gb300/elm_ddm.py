@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_RANK, ERR_NOT_SPD = range(8)
+OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_RANK, ERR_NOT_SPD, ERR_CAPACITY = range(9)
 ERROR_NAMES = {ERR_ARG: "ERR_ARG", ERR_STATE: "ERR_STATE", ERR_CUDA: "ERR_CUDA",
                ERR_OOM: "ERR_OOM", ERR_NONFINITE: "ERR_NONFINITE", ERR_RANK: "ERR_RANK",
                ERR_NOT_SPD: "ERR_NOT_SPD"}
@@ -23,7 +23,7 @@ ERROR_NAMES = {ERR_ARG: "ERR_ARG", ERR_STATE: "ERR_STATE", ERR_CUDA: "ERR_CUDA",
 SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve",
            "elm_ddm_eval", "elm_ddm_export", "elm_ddm_check", "elm_ddm_get_info",
            "elm_ddm_profile", "elm_ddm_profile_report", "elm_ddm_destroy",
-           "elm_ddm_last_error")
+           "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc")
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
 
 
