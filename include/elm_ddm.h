@@ -147,8 +147,17 @@ int elm_ddm_check(elm_ddm_handle* h);
 #define ELM_DDM_BUF_A 1  /* m_Gamma x n_N: A^s after assemble, Y_s = A^s R_s^{-1} after schur */
 #define ELM_DDM_BUF_D 2  /* m_Gamma x m_Gamma: D_s = I - Q_G Q_G^T (after schur) */
 #define ELM_DDM_BUF_M 3  /* m_Gamma x m_Gamma: M_s = -Y_s Q_G^T (after schur) */
-#define ELM_DDM_BUF_L 4  /* n_gamma x n_gamma: lower Cholesky factor of S (after schur; s ignored;
-                            the strict upper triangle is unspecified) */
+#define ELM_DDM_BUF_L 4  /* n_gamma x n_gamma: lower Cholesky factor of S in the internal
+                            interface order (elm_ddm_interface_order), after schur; s ignored;
+                            the strict upper triangle is unspecified */
+
+/*
+ * The Schur matrix is assembled and factored with its interface unknowns renumbered
+ * (reverse Cuthill-McKee on the interface edges, so the Cholesky factor stays inside a
+ * narrow envelope).  order (host int32 [n_gamma]) receives, for every caller unknown g,
+ * its internal index.  elm_ddm_solve's u_gamma is always in the caller's numbering.
+ */
+int elm_ddm_interface_order(const elm_ddm_handle* h, int32_t* order);
 
 /*
  * Copies internal matrix `what` (ELM_DDM_BUF_*) of subdomain s, column-major, into the

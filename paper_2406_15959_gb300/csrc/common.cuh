@@ -19,7 +19,12 @@ struct GemmDesc {
   double* C;
   int m, n, k, lda, ldb, ldc;
 };
-enum : int { GEMM_LOWER = 1, GEMM_ADD_IDENTITY = 2 };
+// GEMM_SKINNY selects the 32 x 128 tile (every m <= 32); tile counts then use that shape.
+enum : int { GEMM_LOWER = 1, GEMM_ADD_IDENTITY = 2, GEMM_SKINNY = 4 };
+inline int gemm_tiles(int m, int n, int flags) {
+  return (flags & GEMM_SKINNY) ? ((m + 31) / 32) * ((n + 127) / 128)
+                               : ((m + 63) / 64) * ((n + 63) / 64);
+}
 
 // dst(rows x cols) += src, column-major.
 struct AddDesc {
@@ -67,10 +72,13 @@ cudaError_t launch_backsolve(const double* X, const double* K, long long kstride
 cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, unsigned* status,
                               cudaStream_t st);
 cudaError_t launch_trsm_chol(double* S, int ld, int n, int k, int nb, cudaStream_t st);
+// row_end < 0 means n; j_begin 0 means all rows above the block.
 cudaError_t launch_chol_fwd(const double* L, int ld, int n, int k, int nb, double* r,
-                            double* y, int nrhs, cudaStream_t st);
+                            double* y, int nrhs, cudaStream_t st, int row_end = -1);
 cudaError_t launch_chol_bwd(const double* L, int ld, int n, int k, int nb, double* y,
-                            double* u, int nrhs, cudaStream_t st);
+                            double* u, int nrhs, cudaStream_t st, int j_begin = 0);
+cudaError_t launch_gather_perm(const int* idx, int n, const double* src, double* dst, int nrhs,
+                               cudaStream_t st);
 
 // ---- device helpers ----
 #ifdef __CUDACC__

@@ -40,9 +40,52 @@ struct Edge {
 };
 
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
-inline int tiles64(int m, int n) { return ((m + 63) / 64) * ((n + 63) / 64); }
 
 std::string g_setup_error;
+
+// Reverse Cuthill-McKee ordering of a graph given by adjacency lists (self loops
+// ignored): breadth-first from a pseudo-peripheral vertex of each component, neighbours
+// in order of increasing degree, then reversed.  Keeps the Schur matrix's nonzero
+// blocks close to the diagonal, so Cholesky fill stays inside a narrow envelope.
+std::vector<int> rcm_order(const std::vector<std::vector<int>>& adj) {
+  const int n = (int)adj.size();
+  std::vector<int> deg(n);
+  for (int i = 0; i < n; ++i) deg[i] = (int)adj[i].size();
+  std::vector<char> done(n, 0);
+  std::vector<int> order;
+  order.reserve(n);
+  auto farthest = [&](int start) {
+    std::vector<int> dist(n, -1), q{start};
+    dist[start] = 0;
+    int best = start;
+    for (size_t h = 0; h < q.size(); ++h) {
+      const int v = q[h];
+      if (dist[v] > dist[best] || (dist[v] == dist[best] && deg[v] < deg[best])) best = v;
+      for (int w : adj[v])
+        if (w != v && !done[w] && dist[w] < 0) { dist[w] = dist[v] + 1; q.push_back(w); }
+    }
+    return best;
+  };
+  while ((int)order.size() < n) {
+    int start = -1;
+    for (int i = 0; i < n; ++i)
+      if (!done[i] && (start < 0 || deg[i] < deg[start])) start = i;
+    start = farthest(farthest(start));
+    std::vector<int> q{start};
+    done[start] = 1;
+    for (size_t h = 0; h < q.size(); ++h) {
+      const int v = q[h];
+      order.push_back(v);
+      std::vector<int> nb;
+      for (int w : adj[v])
+        if (w != v && !done[w]) { done[w] = 1; nb.push_back(w); }
+      std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
+      q.insert(q.end(), nb.begin(), nb.end());
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  return order;
+}
 
 }  // namespace
 
@@ -54,6 +97,10 @@ struct elm_ddm_handle {
   long long kstride = 0, astride = 0, mstride = 0, tstride = 0, vstride = 0, wstride = 0;
   std::vector<int> cnt_h, ms_h, mg_h;
   std::vector<Edge> edges;
+  std::vector<int> newoff;      // internal offset of each edge's first unknown
+  std::vector<int> perm_h;      // caller interface unknown -> internal index
+  std::vector<int> chol_rend;   // per Cholesky block step: end of the envelope rows
+  std::vector<int> chol_jbeg;   // per Cholesky block step: first column the block rows touch
   // device buffers
   double *K = nullptr, *Am = nullptr, *tau = nullptr, *T = nullptr, *Vp = nullptr;
   double *W1 = nullptr, *W2 = nullptr, *D = nullptr, *M = nullptr, *S = nullptr;
@@ -61,6 +108,7 @@ struct elm_ddm_handle {
   double *X = nullptr, *gq = nullptr, *hq = nullptr, *zv = nullptr;
   double *rv = nullptr, *hv = nullptr, *yv = nullptr, *uv = nullptr;
   int *cnt = nullptr, *ms = nullptr, *mg = nullptr, *dofmap = nullptr, *ifc_dof = nullptr;
+  int* perm = nullptr;
   unsigned* status = nullptr;
   GemmDesc* gd = nullptr;
   AddDesc* ad = nullptr;
@@ -285,6 +333,47 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     return fail(nullptr, ELM_DDM_ERR_ARG, "interface edges do not cover all unknowns");
   }
 
+  // ---- Schur-matrix block pattern, interface ordering and Cholesky envelope ----
+  // Edges e1, e2 couple in S when some edge shares a subdomain with both (the M^T M term);
+  // that includes every pair sharing a subdomain (the D term).
+  const int ne = (int)h->edges.size();
+  std::vector<std::vector<int>> sub_edges(N), nbr(ne), spat(ne);
+  for (int e = 0; e < ne; ++e) for (int q = 0; q < 2; ++q) sub_edges[h->edges[e].s[q]].push_back(e);
+  for (int e = 0; e < ne; ++e) {
+    for (int q = 0; q < 2; ++q) for (int e2 : sub_edges[h->edges[e].s[q]]) nbr[e].push_back(e2);
+    std::sort(nbr[e].begin(), nbr[e].end());
+    nbr[e].erase(std::unique(nbr[e].begin(), nbr[e].end()), nbr[e].end());
+  }
+  for (int e1 = 0; e1 < ne; ++e1) {
+    for (int e : nbr[e1]) for (int e2 : nbr[e]) spat[e1].push_back(e2);
+    std::sort(spat[e1].begin(), spat[e1].end());
+    spat[e1].erase(std::unique(spat[e1].begin(), spat[e1].end()), spat[e1].end());
+  }
+  {
+    const std::vector<int> order = rcm_order(spat);
+    h->newoff.assign(ne, 0);
+    int off = 0;
+    for (int pos = 0; pos < ne; ++pos) { h->newoff[order[pos]] = off; off += h->edges[order[pos]].len; }
+    h->perm_h.assign(ng, 0);
+    for (int e = 0; e < ne; ++e)
+      for (int k = 0; k < h->edges[e].len; ++k) h->perm_h[h->edges[e].g0 + k] = h->newoff[e] + k;
+    // first nonzero column of every internal row (fill stays right of it)
+    std::vector<int> first_col(ng, 0);
+    for (int e1 = 0; e1 < ne; ++e1) {
+      int f = h->newoff[e1];
+      for (int e2 : spat[e1]) f = std::min(f, h->newoff[e2]);
+      for (int k = 0; k < h->edges[e1].len; ++k) first_col[h->newoff[e1] + k] = f;
+    }
+    for (int k = 0; k < ng; k += CHOL_NB) {
+      const int nb = std::min(CHOL_NB, ng - k);
+      int rend = k + nb, jb = k;
+      for (int i = k; i < ng; ++i) if (first_col[i] < k + nb) rend = i + 1;
+      for (int i = k; i < k + nb; ++i) jb = std::min(jb, first_col[i]);
+      h->chol_rend.push_back(rend);
+      h->chol_jbeg.push_back(jb);
+    }
+  }
+
   // ---- sizes ----
   h->ld = round_up(std::max(msmax, 1), 32);
   h->mgmax = mgmax;
@@ -320,7 +409,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->yv, (size_t)max_rhs * ng) && dev_alloc(h, &h->uv, (size_t)max_rhs * ng) &&
             dev_alloc(h, &h->cnt, (size_t)N * 3) && dev_alloc(h, &h->ms, (size_t)N) &&
             dev_alloc(h, &h->mg, (size_t)N) && dev_alloc(h, &h->dofmap, (size_t)ng * 4) &&
-            dev_alloc(h, &h->ifc_dof, (size_t)N * h->mgld) && dev_alloc(h, &h->status, 1);
+            dev_alloc(h, &h->ifc_dof, (size_t)N * h->mgld) && dev_alloc(h, &h->perm, (size_t)ng) &&
+            dev_alloc(h, &h->status, 1);
   if (!ok) {
     free_all(h);
     delete h;
@@ -332,12 +422,14 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   for (int g = 0; g < ng; ++g) {
     auto a = owners[g][0], b = owners[g][1];
     if (a.first > b.first) std::swap(a, b);
-    dofmap[4 * g] = a.first; dofmap[4 * g + 1] = a.second;
-    dofmap[4 * g + 2] = b.first; dofmap[4 * g + 3] = b.second;
+    const size_t gi = (size_t)h->perm_h[g];
+    dofmap[4 * gi] = a.first; dofmap[4 * gi + 1] = a.second;
+    dofmap[4 * gi + 2] = b.first; dofmap[4 * gi + 3] = b.second;
   }
   for (int s = 0; s < N; ++s) {
     const int r0 = counts[3 * s] + counts[3 * s + 1];
-    for (int i = 0; i < h->mg_h[s]; ++i) ifc[(size_t)s * h->mgld + i] = dof[(size_t)s * m_max + r0 + i];
+    for (int i = 0; i < h->mg_h[s]; ++i)
+      ifc[(size_t)s * h->mgld + i] = h->perm_h[dof[(size_t)s * m_max + r0 + i]];
   }
 
   // ---- launch plans ----
@@ -345,12 +437,15 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   std::vector<AddDesc> ads;
   auto add_gemm_rec = [&](std::vector<LaunchRec>& recs, const std::vector<GemmDesc>& batch, bool ta,
                           bool tb, double alpha, double beta, int flags) {
+    bool skinny = !(flags & GEMM_LOWER);
+    for (const GemmDesc& d : batch) skinny = skinny && d.m <= 32;
+    if (skinny) flags |= GEMM_SKINNY;
     LaunchRec L{0, (int)gds.size(), 0, 0, ta, tb, alpha, beta, flags, 0.0};
     for (const GemmDesc& d : batch) {
       if (d.m <= 0 || d.n <= 0) continue;
       gds.push_back(d);
       L.count++;
-      L.max_tiles = std::max(L.max_tiles, tiles64(d.m, d.n));
+      L.max_tiles = std::max(L.max_tiles, gemm_tiles(d.m, d.n, flags));
       L.flops += (flags & GEMM_LOWER) ? (double)d.m * (d.m + 1) * d.k : 2.0 * d.m * d.n * d.k;
     }
     recs.push_back(L);
@@ -401,9 +496,9 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     add_gemm_rec(h->dm_recs, gD, true, false, -1.0, 0.0, GEMM_ADD_IDENTITY);
     add_gemm_rec(h->dm_recs, gM, false, false, -1.0, 0.0, 0);
   }
-  // Schur matrix (lower edge blocks): S[e1,e2] = sum D-blocks + sum_e Mblk(e,e1)^T Mblk(e,e2).
+  // Schur matrix (lower edge blocks, internal order): S[e1,e2] = sum of D blocks +
+  // sum_e Mblk(e,e1)^T Mblk(e,e2), each output block written once per round.
   if (ng > 0) {
-    const int ne = (int)h->edges.size();
     std::vector<size_t> mdoff(ne);
     size_t acc = 0;
     for (int e = 0; e < ne; ++e) { mdoff[e] = acc; acc += (size_t)h->edges[e].len * h->edges[e].len; }
@@ -411,9 +506,6 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       const Edge& E = h->edges[e];
       return E.s[0] == s ? E.i[0] : (E.s[1] == s ? E.i[1] : -1);
     };
-    // edges of each subdomain
-    std::vector<std::vector<int>> sub_edges(N);
-    for (int e = 0; e < ne; ++e) for (int q = 0; q < 2; ++q) sub_edges[h->edges[e].s[q]].push_back(e);
     // Mdiag[e] = M_{s0}[e,e] + M_{s1}[e,e]
     for (int q = 0; q < 2; ++q) {
       std::vector<AddDesc> batch;
@@ -437,27 +529,14 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       }
       *p = nullptr;
     };
-    // neighbour lists (edges sharing a subdomain, including the edge itself)
-    std::vector<std::vector<int>> nbr(ne);
-    for (int e = 0; e < ne; ++e) {
-      std::vector<int> v;
-      for (int q = 0; q < 2; ++q) for (int e2 : sub_edges[h->edges[e].s[q]]) v.push_back(e2);
-      std::sort(v.begin(), v.end());
-      v.erase(std::unique(v.begin(), v.end()), v.end());
-      nbr[e] = v;
-    }
     std::vector<std::vector<AddDesc>> drounds;
     std::vector<std::vector<GemmDesc>> mrounds;
     for (int e1 = 0; e1 < ne; ++e1) {
-      // candidate e2: neighbours of neighbours
-      std::vector<int> cand;
-      for (int e : nbr[e1]) for (int e2 : nbr[e]) if (h->edges[e2].g0 <= h->edges[e1].g0) cand.push_back(e2);
-      std::sort(cand.begin(), cand.end());
-      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
       const Edge& E1 = h->edges[e1];
-      for (int e2 : cand) {
+      for (int e2 : spat[e1]) {
+        if (h->newoff[e2] > h->newoff[e1]) continue;
         const Edge& E2 = h->edges[e2];
-        double* dst = h->S + E1.g0 + (size_t)E2.g0 * ng;
+        double* dst = h->S + h->newoff[e1] + (size_t)h->newoff[e2] * ng;
         int r = 0;
         for (int q = 0; q < 2; ++q) {
           const int s = E1.s[q], l2 = local(e2, s);
@@ -481,9 +560,9 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
     for (auto& b : drounds) add_add_rec(h->s_recs, b);
     for (auto& b : mrounds) add_gemm_rec(h->s_recs, b, true, false, 1.0, 1.0, 0);
-    // Cholesky trailing updates
-    for (int k = 0; k < ng; k += CHOL_NB) {
-      const int nb = std::min(CHOL_NB, ng - k), rest = ng - k - nb;
+    // Cholesky trailing updates, restricted to the envelope rows [k+nb, rend)
+    for (int k = 0, step = 0; k < ng; k += CHOL_NB, ++step) {
+      const int nb = std::min(CHOL_NB, ng - k), rest = h->chol_rend[step] - k - nb;
       std::vector<GemmDesc> g;
       if (rest > 0) {
         double* L21 = h->S + (k + nb) + (size_t)k * ng;
@@ -511,6 +590,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   cp(h->mg, h->mg_h.data(), (size_t)N * sizeof(int));
   cp(h->dofmap, dofmap.data(), dofmap.size() * sizeof(int));
   cp(h->ifc_dof, ifc.data(), ifc.size() * sizeof(int));
+  cp(h->perm, h->perm_h.data(), h->perm_h.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
     std::string msg = std::string("setup copy: ") + cudaGetErrorString(e);
@@ -563,8 +643,8 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     for (int k = 0, step = 0; k < h->ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, h->ng - k);
       ELM_LAUNCH(h, launch_potrf_diag(h->S, h->ng, k, nb, h->status, h->st), "potrf");
-      if (h->ng - k - nb > 0) {
-        ELM_LAUNCH(h, launch_trsm_chol(h->S, h->ng, h->ng, k, nb, h->st), "trsm_chol");
+      if (h->chol_rend[step] - k - nb > 0) {
+        ELM_LAUNCH(h, launch_trsm_chol(h->S, h->ng, h->chol_rend[step], k, nb, h->st), "trsm_chol");
         rc = run_recs(h, h->syrk_recs, step, 1, "gemm_syrk");
         if (rc) return rc;
       }
@@ -592,22 +672,21 @@ int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
     ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, h->mgld, h->mg, h->ifc_dof, h->hv, ng, N, nrhs, h->zv,
                               h->st), "mt_h");
     ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
-    for (int k = 0; k < ng; k += CHOL_NB) {
+    for (int k = 0, step = 0; k < ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, ng - k);
-      ELM_LAUNCH(h, launch_chol_fwd(h->S, ng, ng, k, nb, h->rv, h->yv, nrhs, h->st), "chol_fwd");
+      ELM_LAUNCH(h, launch_chol_fwd(h->S, ng, ng, k, nb, h->rv, h->yv, nrhs, h->st,
+                                    h->chol_rend[step]), "chol_fwd");
     }
     for (int k = ((ng - 1) / CHOL_NB) * CHOL_NB; k >= 0; k -= CHOL_NB) {
       const int nb = std::min(CHOL_NB, ng - k);
-      ELM_LAUNCH(h, launch_chol_bwd(h->S, ng, ng, k, nb, h->yv, h->uv, nrhs, h->st), "chol_bwd");
+      ELM_LAUNCH(h, launch_chol_bwd(h->S, ng, ng, k, nb, h->yv, h->uv, nrhs, h->st,
+                                    h->chol_jbeg[k / CHOL_NB]), "chol_bwd");
     }
   }
   ELM_LAUNCH(h, launch_backsolve(h->X, h->K, h->kstride, h->ld, h->mg, h->ifc_dof, h->mgld,
                                  ng > 0 ? h->uv : h->rv, ng, N, n, nrhs, c, h->st), "backsolve");
-  if (u_gamma && ng > 0) {
-    cudaError_t e = cudaMemcpyAsync(u_gamma, h->uv, (size_t)nrhs * ng * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, h->st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "solve: copy u_gamma");
-  }
+  if (u_gamma && ng > 0)
+    ELM_LAUNCH(h, launch_gather_perm(h->perm, ng, h->uv, u_gamma, nrhs, h->st), "gather_u");
   return ELM_DDM_OK;
 }
 
@@ -659,6 +738,12 @@ int elm_ddm_check(elm_ddm_handle* h) {
   if (bits & ST_NONFINITE) return fail(h, ELM_DDM_ERR_NONFINITE, "non-finite value in theta, f/g or R");
   if (bits & ST_RANK) return fail(h, ELM_DDM_ERR_RANK, "a local R has an exactly zero diagonal entry");
   if (bits & ST_NOT_SPD) return fail(h, ELM_DDM_ERR_NOT_SPD, "Schur matrix is not positive definite");
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_interface_order(const elm_ddm_handle* h, int32_t* order) {
+  if (!h || (!order && h->ng > 0)) return ELM_DDM_ERR_ARG;
+  for (int g = 0; g < h->ng; ++g) order[g] = h->perm_h[g];
   return ELM_DDM_OK;
 }
 

@@ -67,10 +67,11 @@ __global__ void __launch_bounds__(64) k_trsm_chol(double* __restrict__ S, int ld
     for (int j = 0; j < nb; ++j) S[i + (size_t)(k + j) * ld] = X[tid][j];
 }
 
-// Forward substitution step for block k: y_k = L_kk^{-1} r_k, r_rest -= L_rest,k y_k.
+// Forward substitution step for block k: y_k = L_kk^{-1} r_k, r_i -= L_ik y_k for the
+// rows k+nb <= i < row_end that can hold nonzeros of the block column (the envelope).
 // Every block solves the small triangle itself, so one launch covers the step.
 __global__ void __launch_bounds__(256) k_chol_fwd(const double* __restrict__ L, int ld, int n, int k,
-                                                  int nb, double* __restrict__ r,
+                                                  int nb, int row_end, double* __restrict__ r,
                                                   double* __restrict__ y) {
   __shared__ double Ls[NB][NB + 1];
   __shared__ double ys[NB];
@@ -97,16 +98,17 @@ __global__ void __launch_bounds__(256) k_chol_fwd(const double* __restrict__ L, 
   __syncthreads();
   if (blockIdx.x == 0 && tid < nb) yy[k + tid] = ys[tid];
   const int i = k + nb + blockIdx.x * 256 + tid;
-  if (i < n) {
+  if (i < row_end) {
     double t = rr[i];
     for (int l = 0; l < nb; ++l) t = fma(-L[i + (size_t)(k + l) * ld], ys[l], t);
     rr[i] = t;
   }
 }
 
-// Backward substitution step for block k: u_k = L_kk^{-T} y_k, y_j -= L_k,j^T u_k (j < k).
+// Backward substitution step for block k: u_k = L_kk^{-T} y_k, y_j -= L_k,j^T u_k for
+// j_begin <= j < k (L_k,j is zero left of the envelope's first column j_begin).
 __global__ void __launch_bounds__(256) k_chol_bwd(const double* __restrict__ L, int ld, int n, int k,
-                                                  int nb, double* __restrict__ y,
+                                                  int nb, int j_begin, double* __restrict__ y,
                                                   double* __restrict__ u) {
   __shared__ double Ls[NB][NB + 1];
   __shared__ double us[NB];
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(256) k_chol_bwd(const double* __restrict__ L, 
   }
   __syncthreads();
   if (blockIdx.x == 0 && tid < nb) uu[k + tid] = us[tid];
-  for (int j = blockIdx.x * 8 + warp; j < k; j += gridDim.x * 8) {
+  for (int j = j_begin + blockIdx.x * 8 + warp; j < k; j += gridDim.x * 8) {
     double p = 0.0;
     for (int l = lane; l < nb; l += 32) p = fma(L[(k + l) + (size_t)j * ld], us[l], p);
     p = warp_sum(p);
@@ -163,19 +165,21 @@ cudaError_t launch_trsm_chol(double* S, int ld, int n, int k, int nb, cudaStream
 }
 
 cudaError_t launch_chol_fwd(const double* L, int ld, int n, int k, int nb, double* r,
-                            double* y, int nrhs, cudaStream_t st) {
-  const int rows = n - k - nb;
+                            double* y, int nrhs, cudaStream_t st, int row_end) {
+  if (row_end < 0 || row_end > n) row_end = n;
+  const int rows = row_end - k - nb;
   const int gx = rows > 0 ? (rows + 255) / 256 : 1;
-  k_chol_fwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, r, y);
+  k_chol_fwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, row_end, r, y);
   return cudaGetLastError();
 }
 
 cudaError_t launch_chol_bwd(const double* L, int ld, int n, int k, int nb, double* y,
-                            double* u, int nrhs, cudaStream_t st) {
-  int gx = (k + 7) / 8;
+                            double* u, int nrhs, cudaStream_t st, int j_begin) {
+  if (j_begin < 0 || j_begin > k) j_begin = 0;
+  int gx = (k - j_begin + 7) / 8;
   if (gx < 1) gx = 1;
   if (gx > 1024) gx = 1024;
-  k_chol_bwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, y, u);
+  k_chol_bwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, j_begin, y, u);
   return cudaGetLastError();
 }
 

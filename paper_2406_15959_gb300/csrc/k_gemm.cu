@@ -12,21 +12,28 @@ namespace elmddm {
 
 namespace {
 
-constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int TK = 16;
 
-template <bool TA, bool TB>
+// Tile TM x TN per block of 256 threads; every thread owns a 4 x 4 register block
+// (rows tx + TX*a, columns ty + TY*b), so TM * TN = 4096.  64 x 64 is the general tile;
+// 32 x 128 serves the skinny products of the QR panels (m = panel width 32), which a
+// 64-row tile would half waste.
+template <bool TA, bool TB, int TM, int TN>
 __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ descs, double alpha,
                                               double beta, int flags) {
+  static_assert(TM * TN == 4096, "tile must hold 256 x 16 outputs");
+  constexpr int TX = TM / 4, TY = TN / 4;
+  constexpr int A_PER = TK * TM / 256, B_PER = TK * TN / 256;
   const GemmDesc d = descs[blockIdx.y];
   const int tiles_m = (d.m + TM - 1) / TM, tiles_n = (d.n + TN - 1) / TN;
   if ((int)blockIdx.x >= tiles_m * tiles_n) return;
   const int bi = blockIdx.x % tiles_m, bj = blockIdx.x / tiles_m;
-  if ((flags & GEMM_LOWER) && bj > bi) return;
+  if ((flags & GEMM_LOWER) && bj * TN > bi * TM + TM - 1) return;
   const int i0 = bi * TM, j0 = bj * TN;
 
   __shared__ double As[TK][TM + 1];
   __shared__ double Bs[TK][TN + 1];
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int t = threadIdx.x, tx = t % TX, ty = t / TX;
   double acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -35,17 +42,21 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ descs
 
   for (int kk0 = 0; kk0 < d.k; kk0 += TK) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < A_PER; ++q) {
       const int e = t + 256 * q;
       int i, kk;
-      if (TA) { kk = e & 15; i = e >> 4; } else { i = e & 63; kk = e >> 6; }
+      if (TA) { kk = e % TK; i = e / TK; } else { i = e % TM; kk = e / TM; }
       const int gi = i0 + i, gk = kk0 + kk;
       double v = 0.0;
       if (gi < d.m && gk < d.k)
         v = TA ? d.A[gk + (size_t)gi * d.lda] : d.A[gi + (size_t)gk * d.lda];
       As[kk][i] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < B_PER; ++q) {
+      const int e = t + 256 * q;
       int j, kb;
-      if (TB) { j = e & 63; kb = e >> 6; } else { kb = e & 15; j = e >> 4; }
+      if (TB) { j = e % TN; kb = e / TN; } else { kb = e % TK; j = e / TK; }
       const int gj = j0 + j, gk2 = kk0 + kb;
       double w = 0.0;
       if (gj < d.n && gk2 < d.k)
@@ -57,9 +68,9 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ descs
     for (int kk = 0; kk < TK; ++kk) {
       double av[4], bv[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + TX * a];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + TY * b];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -69,11 +80,11 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc* __restrict__ descs
   }
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const int gj = j0 + ty + 16 * b;
+    const int gj = j0 + ty + TY * b;
     if (gj >= d.n) continue;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const int gi = i0 + tx + 16 * a;
+      const int gi = i0 + tx + TX * a;
       if (gi >= d.m) continue;
       double* cp = d.C + gi + (size_t)gj * d.ldc;
       double v = alpha * acc[a][b];
@@ -95,16 +106,24 @@ __global__ void __launch_bounds__(256) k_add_blocks(const AddDesc* __restrict__ 
 
 }  // namespace
 
+template <int TM, int TN>
+void gemm_dispatch(bool ta, bool tb, dim3 grid, cudaStream_t st, const GemmDesc* d, double alpha,
+                   double beta, int flags) {
+  if (ta && tb) k_gemm<true, true, TM, TN><<<grid, 256, 0, st>>>(d, alpha, beta, flags);
+  else if (ta) k_gemm<true, false, TM, TN><<<grid, 256, 0, st>>>(d, alpha, beta, flags);
+  else if (tb) k_gemm<false, true, TM, TN><<<grid, 256, 0, st>>>(d, alpha, beta, flags);
+  else k_gemm<false, false, TM, TN><<<grid, 256, 0, st>>>(d, alpha, beta, flags);
+}
+
 cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_tiles,
                         double alpha, double beta, int flags, cudaStream_t st) {
   if (count <= 0 || max_tiles <= 0) return cudaSuccess;
+  const bool skinny = (flags & GEMM_SKINNY) != 0;
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
     dim3 grid(max_tiles, c);
-    if (ta && tb) k_gemm<true, true><<<grid, 256, 0, st>>>(d + off, alpha, beta, flags);
-    else if (ta) k_gemm<true, false><<<grid, 256, 0, st>>>(d + off, alpha, beta, flags);
-    else if (tb) k_gemm<false, true><<<grid, 256, 0, st>>>(d + off, alpha, beta, flags);
-    else k_gemm<false, false><<<grid, 256, 0, st>>>(d + off, alpha, beta, flags);
+    if (skinny) gemm_dispatch<32, 128>(ta, tb, grid, st, d + off, alpha, beta, flags);
+    else gemm_dispatch<64, 64>(ta, tb, grid, st, d + off, alpha, beta, flags);
   }
   return cudaGetLastError();
 }

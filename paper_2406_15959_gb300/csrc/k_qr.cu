@@ -300,6 +300,13 @@ __global__ void k_gather2(const int* __restrict__ dofmap, int n_gamma, int mgld,
   *o = accumulate ? *o + v : v;
 }
 
+// dst[r][g] = src[r][idx[g]].
+__global__ void k_gather_perm(const int* __restrict__ idx, int n, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, rh = blockIdx.y;
+  if (g < n) dst[(size_t)rh * n + g] = src[(size_t)rh * n + idx[g]];
+}
+
 // z_s = M_s^T (E_s h) (warp per column of M_s).
 __global__ void __launch_bounds__(256) k_mt_h(const double* __restrict__ M, long long mstride, int mgld,
                                               const int* __restrict__ mg_arr,
@@ -409,6 +416,13 @@ cudaError_t launch_gather2(const int* dofmap, int n_gamma, int mgld, int N, cons
   if (n_gamma <= 0) return cudaSuccess;
   k_gather2<<<dim3((n_gamma + 255) / 256, nrhs), 256, 0, st>>>(dofmap, n_gamma, mgld, N, a, out,
                                                                accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_perm(const int* idx, int n, const double* src, double* dst, int nrhs,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_gather_perm<<<dim3((n + 255) / 256, nrhs), 256, 0, st>>>(idx, n, src, dst);
   return cudaGetLastError();
 }
 

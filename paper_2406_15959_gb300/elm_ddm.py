@@ -23,7 +23,7 @@ ERROR_NAMES = {ERR_ARG: "ERR_ARG", ERR_STATE: "ERR_STATE", ERR_CUDA: "ERR_CUDA",
 SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve",
            "elm_ddm_eval", "elm_ddm_export", "elm_ddm_check", "elm_ddm_get_info",
            "elm_ddm_profile", "elm_ddm_profile_report", "elm_ddm_destroy",
-           "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc")
+           "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order")
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
 
 
@@ -63,6 +63,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_eval.argtypes = [P, I, P, P, P, P, P]
     lib.elm_ddm_export.argtypes = [P, I, I, P, I]
     lib.elm_ddm_check.argtypes = [P]
+    lib.elm_ddm_interface_order.argtypes = [P, P]
     lib.elm_ddm_profile.argtypes = [P, I]
     lib.elm_ddm_profile_report.argtypes = [P, ctypes.c_char_p, I]
     lib.elm_ddm_get_info.argtypes = [P, I, D]
@@ -196,6 +197,12 @@ class Solver:
         if what == BUF_L:
             return self.n_gamma, self.n_gamma
         raise ValueError(what)
+
+    def interface_order(self) -> np.ndarray:
+        """Internal index of every interface unknown (the order of BUF_L's rows)."""
+        order = np.zeros(max(self.n_gamma, 1), np.int32)
+        self._check_rc(self.lib.elm_ddm_interface_order(self.h, order.ctypes.data))
+        return order[:self.n_gamma]
 
     def profile(self, enable: bool = True):
         self._check_rc(self.lib.elm_ddm_profile(self.h, int(enable)))

@@ -118,8 +118,10 @@ def test_factor_pieces_match_oracle_when_well_conditioned():
         assert np.abs(D - L.D).max() <= 1e-11
         assert np.abs(M - L.M).max() <= 1e-10 * max(1.0, np.abs(L.M).max())
     Lg = np.tril(s.export(E.BUF_L).cpu().numpy())
-    S = Lg @ Lg.T
-    assert np.abs(S - res.S).max() <= 1e-11 * np.abs(res.S).max()
+    S = Lg @ Lg.T                                  # internal (envelope) ordering
+    inv = np.argsort(s.interface_order())          # internal index -> caller unknown
+    S_or = res.S[np.ix_(inv, inv)]
+    assert np.abs(S - S_or).max() <= 1e-11 * np.abs(res.S).max()
 
 
 def test_full_size_8x8_n1000_matches_oracle():

@@ -49,12 +49,14 @@ def test_noalloc_solve_matches_elm_ddm_solve_on_two_calls():
     s.check()
     n = w.geom.n_gamma
     L = s.export(E.BUF_L)                        # the factor, indexed L[i, j]
+    inv = torch.as_tensor(np.argsort(s.interface_order()), device=dev)  # internal -> caller
     Lcm = L.t().contiguous()                     # its column-major buffer
     Ltri = torch.tril(L)
     stream = torch.cuda.current_stream(dev)
     f = _fn()
     free = []
-    for k, u_ref in enumerate(ref):
+    for k, u_user in enumerate(ref):
+        u_ref = u_user[inv].contiguous()           # u_Gamma in the factor's internal order
         b = (Ltri @ (Ltri.t() @ u_ref)).contiguous()   # S u_Gamma with S = L L^T
         u = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
         torch.cuda.synchronize(dev)
