@@ -57,6 +57,11 @@ extern "C" {
 #define ELM_DDM_ERR_NOT_SPD   7  /* a Cholesky pivot of the Schur matrix was <= 0 */
 #define ELM_DDM_ERR_CAPACITY  8  /* request larger than a no-allocation entry point's fixed scratch */
 
+/* elm_ddm_desc.flags */
+#define ELM_DDM_FLAG_FP64_SIMT 1  /* run every dense update on the FP64 pipe (default: the
+                                     large ones as FP64-accurate digit-split products on the
+                                     BF16 tensor cores) */
+
 /* Differential operators. */
 #define ELM_DDM_OP_POISSON 0  /* L = -Laplacian (Eq. (4.4)) */
 
@@ -69,6 +74,7 @@ typedef struct elm_ddm_desc {
   int32_t n_gamma;    /* number of global interface unknowns (0 when N == 1) */
   int32_t op;         /* ELM_DDM_OP_* */
   int32_t max_rhs;    /* largest nrhs elm_ddm_solve will be given, 1..64 (0 means 1) */
+  int32_t flags;      /* ELM_DDM_FLAG_* */
 } elm_ddm_desc;
 
 /*

@@ -10,7 +10,9 @@ constexpr int CHOL_NB = 64;   // block size of the Schur-matrix Cholesky
 constexpr int TRSV_MAX_N = 8192;  // largest n_neurons the back-solve keeps in shared memory
 
 // Bits of the device status word.
-enum : unsigned { ST_RANK = 1u, ST_NOT_SPD = 2u, ST_NONFINITE = 4u };
+// ST_TIMEOUT: a bounded wait inside a kernel gave up; ST_INTERNAL: a launch violated a
+// kernel's documented limits.  Both are reported as ELM_DDM_ERR_CUDA.
+enum : unsigned { ST_RANK = 1u, ST_NOT_SPD = 2u, ST_NONFINITE = 4u, ST_TIMEOUT = 8u, ST_INTERNAL = 16u };
 
 // C(m x n) = alpha * op(A) op(B) + beta * C, column-major; op = transpose or not.
 struct GemmDesc {
@@ -33,7 +35,35 @@ struct AddDesc {
   int rows, cols, lds, ldd;
 };
 
+// Digit split of one FP64 operand (k_ozaki.cu): the logical R x K matrix with element
+// (r, k) at X[r * rs + k * ks] becomes 7 BF16 digit planes in row tiles of row_tile rows
+// (128 for the A side, the GEMM's NT for the B side); E receives per-row exponent bounds.
+struct SplitDesc {
+  const double* X;
+  long long rs, ks;
+  int R, K;
+  int* E;
+  void* tiles;
+  int row_tile;
+};
+// C[i * c_rs + j * c_cs] = alpha * sum_k A[i, k] B[j, k] + beta * C (A, B split as above).
+struct OzDesc {
+  const void* At;
+  const int* Ae;
+  const void* Bt;
+  const int* Be;
+  double* C;
+  long long c_rs, c_cs;
+  int M, N, K;
+};
+
 // ---- launchers (return cudaGetLastError after the launch) ----
+int oz_tiles(int m, int n, int nt);
+size_t oz_split_elems(int R, int K, int row_tile);
+cudaError_t launch_split(const SplitDesc* d, int count, int max_rows, int max_split_blocks,
+                         cudaStream_t st);
+cudaError_t launch_ozaki(int nt, const OzDesc* d, int count, int max_tiles, double alpha,
+                         double beta, int flags, unsigned* status, cudaStream_t st);
 cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_tiles,
                         double alpha, double beta, int flags, cudaStream_t st);
 cudaError_t launch_add_blocks(const AddDesc* d, int count, int max_elems, cudaStream_t st);

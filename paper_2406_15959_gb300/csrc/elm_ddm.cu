@@ -19,12 +19,13 @@ using namespace elmddm;
 namespace {
 
 struct LaunchRec {
-  int kind;  // 0 = gemm, 1 = add_blocks
-  int off, count, max_tiles;
+  int kind;  // 0 = FP64 gemm, 1 = add_blocks, 2 = digit split, 3 = tensor-core digit GEMM
+  int off, count, max_tiles;  // split: max_tiles = blocks of k_split, nt = max rows
   bool ta, tb;
   double alpha, beta;
   int flags;
   double flops;  // algorithmic flops of the launch (2mnk per GEMM; m(m+1)k for a lower SYRK)
+  int nt;        // tensor-core GEMM: tile width (32 or 64); split: largest row count
 };
 
 // One profiled launch: events around it, its class and algorithmic flops.
@@ -112,9 +113,15 @@ struct elm_ddm_handle {
   unsigned* status = nullptr;
   GemmDesc* gd = nullptr;
   AddDesc* ad = nullptr;
+  SplitDesc* sd = nullptr;
+  OzDesc* od = nullptr;
+  bool emulated = true;          // FP64 products on the tensor cores (digit split)
+  void* sp_buf = nullptr;        // digit tiles and row exponents of the split operands
+  std::vector<int> qr_first;     // first record of each panel in qr_recs
+  std::vector<int> syrk_first;   // first record of each Cholesky step in syrk_recs
   size_t mdiag_elems = 0;
   // plans
-  std::vector<LaunchRec> qr_recs;    // 3 per panel
+  std::vector<LaunchRec> qr_recs;    // per panel: the trailing-update launches
   std::vector<LaunchRec> dm_recs;    // D and M
   std::vector<LaunchRec> s_recs;     // Mdiag adds, D adds, M^T M gemms
   std::vector<LaunchRec> syrk_recs;  // one per Cholesky block step
@@ -212,8 +219,13 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
     if (L.kind == 0)
       ELM_LAUNCH_F(h, launch_gemm(L.ta, L.tb, h->gd + L.off, L.count, L.max_tiles, L.alpha, L.beta,
                                   L.flags, h->st), gemm_name, L.flops);
-    else
+    else if (L.kind == 1)
       ELM_LAUNCH(h, launch_add_blocks(h->ad + L.off, L.count, L.max_tiles, h->st), "add_blocks");
+    else if (L.kind == 2)
+      ELM_LAUNCH(h, launch_split(h->sd + L.off, L.count, L.nt, L.max_tiles, h->st), "split");
+    else
+      ELM_LAUNCH_F(h, launch_ozaki(L.nt, h->od + L.off, L.count, L.max_tiles, L.alpha, L.beta,
+                                   L.flags, h->status, h->st), gemm_name, L.flops);
   }
   return ELM_DDM_OK;
 }
@@ -235,12 +247,14 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const int max_rhs = desc->max_rhs == 0 ? 1 : desc->max_rhs;
   if (max_rhs < 1 || max_rhs > 64) return fail(nullptr, ELM_DDM_ERR_ARG, "max_rhs must be in 1..64");
   if (n > TRSV_MAX_N) return fail(nullptr, ELM_DDM_ERR_ARG, "n_neurons > 8192 is not supported");
+  if (desc->flags & ~ELM_DDM_FLAG_FP64_SIMT) return fail(nullptr, ELM_DDM_ERR_ARG, "unknown flags");
   if ((long long)N * m_max > (1ll << 31)) return fail(nullptr, ELM_DDM_ERR_ARG, "geometry too large");
 
   auto h = new elm_ddm_handle();
   h->desc = *desc;
   h->st = static_cast<cudaStream_t>(stream);
   h->N = N; h->n = n; h->m_max = m_max; h->ng = ng; h->max_rhs = max_rhs;
+  h->emulated = !(desc->flags & ELM_DDM_FLAG_FP64_SIMT);
   h->cnt_h.assign(counts, counts + 3 * N);
   h->ms_h.resize(N); h->mg_h.resize(N);
   int msmax = 0, mgmax = 0;
@@ -416,6 +430,37 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     delete h;
     return fail(nullptr, ELM_DDM_ERR_OOM, "device allocation failed");
   }
+  // Split workspace (tensor-core FP64 products): per subdomain the digit tiles of the
+  // trailing block A2^T, of V^T, of V and of W2^T, then for the Cholesky the panel L21 as
+  // both operands.  Each region is 256-byte aligned.
+  const int n2max = h->ncap - std::min(QR_NB, n), mpmax = msmax;
+  int restmax = 0;
+  for (int k = 0, st = 0; k < ng; k += CHOL_NB, ++st)
+    restmax = std::max(restmax, h->chol_rend[st] - k - std::min(CHOL_NB, ng - k));
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t s1 = al(oz_split_elems(n2max, mpmax, 128) * 2), e1 = al((size_t)n2max * 4);
+  const size_t s2 = al(oz_split_elems(QR_NB, mpmax, 32) * 2), e2 = al((size_t)QR_NB * 4);
+  const size_t s3 = al(oz_split_elems(mpmax, QR_NB, 128) * 2), e3 = al((size_t)mpmax * 4);
+  const size_t s4 = al(oz_split_elems(n2max, QR_NB, 64) * 2), e4 = al((size_t)n2max * 4);
+  const size_t per_sub = s1 + e1 + s2 + e2 + s3 + e3 + s4 + e4;
+  const size_t c1 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 128) * 2);
+  const size_t c2 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 64) * 2);
+  const size_t ce = al((size_t)std::max(restmax, 1) * 4);
+  if (h->emulated) {
+    char* base = nullptr;
+    if (!dev_alloc(h, &base, per_sub * N + c1 + c2 + 2 * ce)) {
+      free_all(h);
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_OOM, "device allocation failed (split workspace)");
+    }
+    h->sp_buf = base;
+  }
+  auto sub_region = [&](int s, int which) -> char* {
+    const size_t off[8] = {0, s1, s1 + e1, s1 + e1 + s2, s1 + e1 + s2 + e2, s1 + e1 + s2 + e2 + s3,
+                           s1 + e1 + s2 + e2 + s3 + e3, s1 + e1 + s2 + e2 + s3 + e3 + s4};
+    return (char*)h->sp_buf + (size_t)s * per_sub + off[which];
+  };
+  char* chol_region = (char*)h->sp_buf + per_sub * N;
 
   // ---- geometry tables ----
   std::vector<int> dofmap((size_t)ng * 4), ifc((size_t)N * h->mgld, -1);
@@ -440,7 +485,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     bool skinny = !(flags & GEMM_LOWER);
     for (const GemmDesc& d : batch) skinny = skinny && d.m <= 32;
     if (skinny) flags |= GEMM_SKINNY;
-    LaunchRec L{0, (int)gds.size(), 0, 0, ta, tb, alpha, beta, flags, 0.0};
+    LaunchRec L{0, (int)gds.size(), 0, 0, ta, tb, alpha, beta, flags, 0.0, 0};
     for (const GemmDesc& d : batch) {
       if (d.m <= 0 || d.n <= 0) continue;
       gds.push_back(d);
@@ -451,7 +496,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     recs.push_back(L);
   };
   auto add_add_rec = [&](std::vector<LaunchRec>& recs, const std::vector<AddDesc>& batch) {
-    LaunchRec L{1, (int)ads.size(), 0, 0, false, false, 0, 0, 0, 0.0};
+    LaunchRec L{1, (int)ads.size(), 0, 0, false, false, 0, 0, 0, 0.0, 0};
     for (const AddDesc& d : batch) {
       if (d.rows <= 0 || d.cols <= 0) continue;
       ads.push_back(d);
@@ -461,10 +506,39 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     recs.push_back(L);
   };
   const int ld = h->ld;
-  // QR trailing updates, panel b: W1 = V^T A2, W2 = T^T W1, A2 -= V W2.
+  // QR trailing updates, panel b: W1 = V^T A2, W2 = T^T W1, A2 -= V W2.  With the
+  // tensor-core path, W1^T = A2^T V and A2 -= V W2 are digit-split products and only the
+  // small T^T W1 stays on the FP64 pipe.
+  std::vector<SplitDesc> sds;
+  std::vector<OzDesc> ods;
+  auto add_split_rec = [&](std::vector<LaunchRec>& recs, const std::vector<SplitDesc>& batch) {
+    LaunchRec L{2, (int)sds.size(), 0, 0, false, false, 0, 0, 0, 0.0, 0};
+    for (const SplitDesc& d : batch) {
+      if (d.R <= 0 || d.K <= 0) continue;
+      sds.push_back(d);
+      L.count++;
+      L.nt = std::max(L.nt, d.R);
+      L.max_tiles = std::max(L.max_tiles, (d.R + d.row_tile - 1) / d.row_tile * ((d.K + 31) / 32));
+    }
+    recs.push_back(L);
+  };
+  auto add_oz_rec = [&](std::vector<LaunchRec>& recs, const std::vector<OzDesc>& batch, int nt,
+                        double alpha, double beta, int flags) {
+    LaunchRec L{3, (int)ods.size(), 0, 0, false, false, alpha, beta, flags, 0.0, nt};
+    for (const OzDesc& d : batch) {
+      if (d.M <= 0 || d.N <= 0) continue;
+      ods.push_back(d);
+      L.count++;
+      L.max_tiles = std::max(L.max_tiles, oz_tiles(d.M, d.N, nt));
+      L.flops += (flags & GEMM_LOWER) ? (double)d.M * (d.M + 1) * d.K : 2.0 * d.M * d.N * d.K;
+    }
+    recs.push_back(L);
+  };
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, n - k0);
     std::vector<GemmDesc> g1, g2, g3;
+    std::vector<SplitDesc> sp1, sp3;
+    std::vector<OzDesc> o1, o3;
     for (int s = 0; s < N; ++s) {
       const int n2 = n + h->mg_h[s] - (k0 + nbe), mp = h->ms_h[s] - k0;
       if (n2 <= 0 || mp <= 0) continue;
@@ -477,11 +551,33 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       g1.push_back({V, A2, w1, nbe, n2, mp, ld, ld, QR_NB});
       g2.push_back({Tb, w1, w2, nbe, n2, nbe, QR_NB, QR_NB, QR_NB});
       g3.push_back({V, w2, A2, mp, n2, nbe, ld, QR_NB, ld});
+      if (h->emulated) {
+        void* t1 = sub_region(s, 0); int* x1 = (int*)sub_region(s, 1);
+        void* t2 = sub_region(s, 2); int* x2 = (int*)sub_region(s, 3);
+        void* t3 = sub_region(s, 4); int* x3 = (int*)sub_region(s, 5);
+        void* t4 = sub_region(s, 6); int* x4 = (int*)sub_region(s, 7);
+        sp1.push_back({A2, ld, 1, n2, mp, x1, t1, 128});     // A2^T: rows = trailing columns
+        sp1.push_back({V, ld, 1, nbe, mp, x2, t2, 32});      // V^T: rows = panel columns
+        o1.push_back({t1, x1, t2, x2, w1, QR_NB, 1, n2, nbe, mp});
+        sp3.push_back({V, 1, ld, mp, nbe, x3, t3, 128});     // V: rows = matrix rows
+        sp3.push_back({w2, QR_NB, 1, n2, nbe, x4, t4, 64});  // W2^T: rows = trailing columns
+        o3.push_back({t3, x3, t4, x4, A2, 1, ld, mp, n2, nbe});
+      }
     }
-    add_gemm_rec(h->qr_recs, g1, true, false, 1.0, 0.0, 0);
-    add_gemm_rec(h->qr_recs, g2, true, false, 1.0, 0.0, 0);
-    add_gemm_rec(h->qr_recs, g3, false, false, -1.0, 1.0, 0);
+    h->qr_first.push_back((int)h->qr_recs.size());
+    if (h->emulated) {
+      add_split_rec(h->qr_recs, sp1);
+      add_oz_rec(h->qr_recs, o1, 32, 1.0, 0.0, 0);
+      add_gemm_rec(h->qr_recs, g2, true, false, 1.0, 0.0, 0);
+      add_split_rec(h->qr_recs, sp3);
+      add_oz_rec(h->qr_recs, o3, 64, -1.0, 1.0, 0);
+    } else {
+      add_gemm_rec(h->qr_recs, g1, true, false, 1.0, 0.0, 0);
+      add_gemm_rec(h->qr_recs, g2, true, false, 1.0, 0.0, 0);
+      add_gemm_rec(h->qr_recs, g3, false, false, -1.0, 1.0, 0);
+    }
   }
+  h->qr_first.push_back((int)h->qr_recs.size());
   // D_s = I - (Q_G^T)^T Q_G^T and M_s = -Y_s Q_G^T.
   {
     std::vector<GemmDesc> gD, gM;
@@ -563,15 +659,27 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     // Cholesky trailing updates, restricted to the envelope rows [k+nb, rend)
     for (int k = 0, step = 0; k < ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, ng - k), rest = h->chol_rend[step] - k - nb;
-      std::vector<GemmDesc> g;
-      if (rest > 0) {
-        double* L21 = h->S + (k + nb) + (size_t)k * ng;
-        g.push_back({L21, L21, h->S + (k + nb) + (size_t)(k + nb) * ng, rest, rest, nb, ng, ng, ng});
+      h->syrk_first.push_back((int)h->syrk_recs.size());
+      if (rest <= 0) continue;
+      double* L21 = h->S + (k + nb) + (size_t)k * ng;
+      double* S22 = h->S + (k + nb) + (size_t)(k + nb) * ng;
+      if (h->emulated) {
+        int* xa = (int*)(chol_region + c1 + c2);
+        int* xb = (int*)(chol_region + c1 + c2 + ce);
+        std::vector<SplitDesc> sp{{L21, 1, ng, rest, nb, xa, chol_region, 128},
+                                  {L21, 1, ng, rest, nb, xb, chol_region + c1, 64}};
+        add_split_rec(h->syrk_recs, sp);
+        add_oz_rec(h->syrk_recs, {{chol_region, xa, chol_region + c1, xb, S22, 1, ng, rest, rest, nb}},
+                   64, -1.0, 1.0, GEMM_LOWER);
+      } else {
+        add_gemm_rec(h->syrk_recs, {{L21, L21, S22, rest, rest, nb, ng, ng, ng}}, false, true, -1.0,
+                     1.0, GEMM_LOWER);
       }
-      add_gemm_rec(h->syrk_recs, g, false, true, -1.0, 1.0, GEMM_LOWER);
     }
+    h->syrk_first.push_back((int)h->syrk_recs.size());
   }
-  ok = dev_alloc(h, &h->gd, gds.size()) && dev_alloc(h, &h->ad, ads.size());
+  ok = dev_alloc(h, &h->gd, gds.size()) && dev_alloc(h, &h->ad, ads.size()) &&
+       dev_alloc(h, &h->sd, sds.size()) && dev_alloc(h, &h->od, ods.size());
   if (!ok) {
     free_all(h);
     delete h;
@@ -583,6 +691,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   };
   cp(h->gd, gds.data(), gds.size() * sizeof(GemmDesc));
   cp(h->ad, ads.data(), ads.size() * sizeof(AddDesc));
+  cp(h->sd, sds.data(), sds.size() * sizeof(SplitDesc));
+  cp(h->od, ods.data(), ods.size() * sizeof(OzDesc));
   cp(h->xy, xy, (size_t)N * m_max * 2 * sizeof(double));
   cp(h->nrm, nrm, (size_t)N * m_max * 2 * sizeof(double));
   cp(h->cnt, counts, (size_t)N * 3 * sizeof(int));
@@ -626,7 +736,8 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     ELM_LAUNCH(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->T +
                                   (size_t)b * QR_NB * QR_NB, h->tstride, h->Vp, h->vstride, h->status,
                                   h->st), "panel_qr");
-    int rc = run_recs(h, h->qr_recs, 3 * (size_t)b, 3, "gemm_qr");
+    int rc = run_recs(h, h->qr_recs, h->qr_first[b], h->qr_first[b + 1] - h->qr_first[b],
+                      "gemm_qr");
     if (rc) return rc;
   }
   h->state = 0;  // K is factored in place: assemble again before another schur
@@ -645,7 +756,8 @@ int elm_ddm_schur(elm_ddm_handle* h) {
       ELM_LAUNCH(h, launch_potrf_diag(h->S, h->ng, k, nb, h->status, h->st), "potrf");
       if (h->chol_rend[step] - k - nb > 0) {
         ELM_LAUNCH(h, launch_trsm_chol(h->S, h->ng, h->chol_rend[step], k, nb, h->st), "trsm_chol");
-        rc = run_recs(h, h->syrk_recs, step, 1, "gemm_syrk");
+        rc = run_recs(h, h->syrk_recs, h->syrk_first[step],
+                      h->syrk_first[step + 1] - h->syrk_first[step], "gemm_syrk");
         if (rc) return rc;
       }
     }
@@ -738,6 +850,8 @@ int elm_ddm_check(elm_ddm_handle* h) {
   if (bits & ST_NONFINITE) return fail(h, ELM_DDM_ERR_NONFINITE, "non-finite value in theta, f/g or R");
   if (bits & ST_RANK) return fail(h, ELM_DDM_ERR_RANK, "a local R has an exactly zero diagonal entry");
   if (bits & ST_NOT_SPD) return fail(h, ELM_DDM_ERR_NOT_SPD, "Schur matrix is not positive definite");
+  if (bits & ST_TIMEOUT) return fail(h, ELM_DDM_ERR_CUDA, "a device-side wait timed out");
+  if (bits & ST_INTERNAL) return fail(h, ELM_DDM_ERR_CUDA, "a kernel was launched outside its limits");
   return ELM_DDM_OK;
 }
 

@@ -1,0 +1,509 @@
+// FP64-accurate GEMM on the BF16 tensor cores (tcgen05), by exact digit splitting.
+//
+// GB300 runs FP64 at ~1/60 of FP32 and has no fast FP64 tensor path, while every large
+// dense update of the solver (QR trailing updates, the Schur Cholesky's SYRK) needs
+// FP64 accuracy.  Each FP64 operand row r is written as x = 2^E_r * sum_p d_p 2^(-8p),
+// p = 1..7, with integer digits |d_1| <= 256, |d_p| <= 128 (p >= 2), exactly
+// representable in BF16 (E_r: exponent bound of the row, truncation error < 2^(E_r-56)).
+// Then
+//     (A B^T)_ij = 2^(E_i + F_j) * sum_g 2^(-8g) * sum_{p+q=g} sum_k dA_p(i,k) dB_q(j,k),
+// and for g = 2..8 the inner integer sums over 64 consecutive k are exact in the
+// FP32 accumulators of the tensor core (|sum| < 2.25 * 2^22 < 2^24).  Each K chunk of 64
+// is drained from TMEM into float-float registers (error-free TwoSum); the result meets
+// the FP64 rounding level and is combined into the FP64 output with two FP64 ops per
+// element instead of 2K.
+//
+// Splitting uses only integer operations on the FP64 bit pattern (no FP64 arithmetic).
+// Kernels:
+//   k_rowexp  exponent bound (max biased exponent) of each operand row
+//   k_split   7 BF16 digit planes per (row tile, 32-wide K chunk), written directly in
+//             the tcgen05 K-major no-swizzle canonical layout (8x8 core matrices)
+//   k_ozaki   one CTA per 128 x NT output tile: warp 0 streams the digit tiles with
+//             cp.async.bulk, warp 1 issues the 28 digit-pair MMAs per 16-wide k-step
+//             into 7 TMEM accumulators (one per g), warps 2..5 drain TMEM and write C.
+#include "common.cuh"
+
+#include <cuda_bf16.h>
+
+namespace elmddm {
+
+namespace {
+
+constexpr int OZ_S = 7;        // digit planes per operand
+constexpr int OZ_G = 7;        // groups g = p + q = 2..8
+constexpr int OZ_KC = 32;      // K per shared-memory stage (two 16-wide MMA k-steps)
+constexpr int OZ_M = 128;      // MMA M = rows of an A tile
+constexpr int OZ_THREADS = 192;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // every wait gives up after 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a));
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase with the given parity; false if it has not completed within 2 s
+// of wall time (each try_wait may itself suspend, so the bound is on the clock).
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity));
+    if (ok) return true;
+    if ((it & 63) == 63 && global_ns() - t0 > kWaitNs) return false;
+  }
+}
+// Warp-uniform wait: lane 0 waits, the outcome is broadcast to the whole warp (the
+// tcgen05.ld that follow are warp-collective and must be executed by all 32 lanes).
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t a, uint32_t parity) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(a, parity) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+// Shared-memory matrix descriptor, K-major, no swizzle: LBO = byte step between core
+// matrices along K, SBO = byte step between core matrices along M/N.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      mbar));
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                 "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+
+// Element offset of (r, k) inside an R x 32 tile in the canonical K-major layout
+// [r/8][k/8][r%8][k%8].
+__device__ __forceinline__ int tile_off32(int r, int k) {
+  return (((r >> 3) * 4 + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+__device__ __forceinline__ unsigned biased_exp(double x) {
+  return (unsigned)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// Balanced base-256 digits of x relative to the row bound 2^(emax-1022).
+__device__ __forceinline__ void digits7(double x, unsigned emax, int (&d)[OZ_S]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7FF);
+#pragma unroll
+  for (int p = 0; p < OZ_S; ++p) d[p] = 0;
+  if (e == 0 || emax == 0) return;  // zero (subnormals are below the digits' reach)
+  const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int shift = (int)emax - e - 3;  // >= -3 because e <= emax
+  unsigned long long F;
+  if (shift >= 64) F = 0;
+  else if (shift >= 0) F = M >> shift;
+  else F = M << (-shift);
+  int carry = 0;
+#pragma unroll
+  for (int p = OZ_S - 1; p >= 1; --p) {
+    int t = (int)((F >> (56 - 8 * (p + 1))) & 0xFF) + carry;
+    carry = t >= 128;
+    d[p] = t - (carry << 8);
+  }
+  d[0] = (int)((F >> 48) & 0xFF) + carry;
+  if (bits >> 63) {
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) d[p] = -d[p];
+  }
+}
+
+// Warp per row: E[r] = largest biased exponent in row r (0 for an all-zero row).
+__global__ void __launch_bounds__(256) k_rowexp(const SplitDesc* __restrict__ descs) {
+  const SplitDesc d = descs[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (r >= d.R) return;
+  unsigned mx = 0;
+  for (int k = lane; k < d.K; k += 32)
+    mx = max(mx, biased_exp(d.X[(long long)r * d.rs + (long long)k * d.ks]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) d.E[r] = (int)mx;
+}
+
+// One block per (row tile, 32-wide K chunk): the 7 digit planes of that tile.
+__global__ void __launch_bounds__(256) k_split(const SplitDesc* __restrict__ descs) {
+  const SplitDesc d = descs[blockIdx.y];
+  const int TR = d.row_tile;
+  const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
+  const int ntr = (d.R + TR - 1) / TR;
+  if ((int)blockIdx.x >= ntr * nkc) return;
+  const int rt = blockIdx.x / nkc, kc = blockIdx.x % nkc;
+  __nv_bfloat16* out =
+      static_cast<__nv_bfloat16*>(d.tiles) + (size_t)(rt * nkc + kc) * OZ_S * TR * OZ_KC;
+  for (int it = threadIdx.x; it < 4 * TR; it += blockDim.x) {
+    int r, kg;
+    if (d.ks == 1) { r = it >> 2; kg = it & 3; } else { r = it % TR; kg = it / TR; }
+    const int gr = rt * TR + r;
+    const unsigned emax = gr < d.R ? (unsigned)d.E[gr] : 0u;
+    uint32_t w[OZ_S][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = kc * OZ_KC + kg * 8 + j;
+      double x = 0.0;
+      if (gr < d.R && k < d.K) x = d.X[(long long)gr * d.rs + (long long)k * d.ks];
+      int dg[OZ_S];
+      digits7(x, emax, dg);
+#pragma unroll
+      for (int p = 0; p < OZ_S; ++p) {
+        const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn((float)dg[p]));
+        if (j & 1) w[p][j >> 1] |= b << 16;
+        else w[p][j >> 1] = b;
+      }
+    }
+    const int off = tile_off32(r, kg * 8);
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p)
+      *reinterpret_cast<uint4*>(out + (size_t)p * TR * OZ_KC + off) =
+          make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+  }
+}
+
+// 2^k as a double for any integer k (0 below the subnormal range).
+__device__ __forceinline__ double pow2i(int k) {
+  if (k >= -1022 && k <= 1023) return __longlong_as_double((long long)(k + 1023) << 52);
+  if (k > 1023) return __longlong_as_double(0x7FF0000000000000ll);
+  if (k >= -1074) return __longlong_as_double(1ll << (k + 1074));
+  return 0.0;
+}
+
+// x * 2^k (x an integer with |x| < 2^53, sign flipped when neg) built from its bit
+// pattern with integer operations only; exact whenever the result is a normal double.
+__device__ __forceinline__ double i64_to_double_pow2(long long x, int k, bool neg) {
+  if (x == 0) return 0.0;
+  unsigned long long sgn = (x < 0) != neg ? (1ull << 63) : 0ull;
+  const unsigned long long a = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+  const int msb = 63 - __clzll((long long)a);
+  const long long e = (long long)msb + k + 1023;
+  if (e <= 0 || e >= 2047) return (neg ? -1.0 : 1.0) * (double)x * pow2i(k);
+  const unsigned long long mant = (a << (52 - msb)) & 0xFFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | mant));
+}
+
+template <int NT>
+struct OzSmem {
+  static constexpr int A_BYTES = OZ_S * OZ_M * OZ_KC * 2;  // one stage of A digit tiles
+  static constexpr int B_BYTES = OZ_S * NT * OZ_KC * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int NSTAGE = 2;
+  static constexpr int BAR_OFF = NSTAGE * STAGE;             // 6 mbarriers
+  static constexpr int EXP_OFF = BAR_OFF + 64;               // NT column exponents
+  static constexpr int SLOT_OFF = EXP_OFF + NT * 4;          // TMEM address
+  static constexpr int FLAG_OFF = SLOT_OFF + 16;             // abort flag
+  static constexpr int TOTAL = FLAG_OFF + 16 + 1024;         // + alignment slack
+  static constexpr int TMEM_COLS = (OZ_G * NT <= 256) ? 256 : 512;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restrict__ descs, double alpha,
+                                                        double beta, int flags, unsigned* status) {
+  using L = OzSmem<NT>;
+  const OzDesc d = descs[blockIdx.y];
+  const int tiles_m = (d.M + OZ_M - 1) / OZ_M, tiles_n = (d.N + NT - 1) / NT;
+  if ((int)blockIdx.x >= tiles_m * tiles_n) return;
+  const int bi = blockIdx.x % tiles_m, bj = blockIdx.x / tiles_m;
+  if ((flags & GEMM_LOWER) && bj * NT > bi * OZ_M + OZ_M - 1) return;
+
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar = sbase + L::BAR_OFF;  // full0 full1 empty0 empty1 tfull tempty
+  int* sexp = reinterpret_cast<int*>(smem + L::EXP_OFF);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + L::SLOT_OFF);
+  volatile int* abort_flag = reinterpret_cast<int*>(smem + L::FLAG_OFF);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
+  const int nchunk = (nkc + 1) / 2;  // exact-accumulation chunks of 64
+  if (NT > 32 && nchunk > 1) {       // the wide tile keeps no accumulators across chunks
+    if (tid == 0) atomicOr(status, ST_INTERNAL);
+    return;
+  }
+
+  if (tid == 0) {
+    mbar_init(bar + 0, 1); mbar_init(bar + 8, 1);
+    mbar_init(bar + 16, 1); mbar_init(bar + 24, 1);
+    mbar_init(bar + 32, 1); mbar_init(bar + 40, 128);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  for (int j = tid; j < NT; j += OZ_THREADS) {
+    const int col = bj * NT + j;
+    sexp[j] = col < d.N ? d.Be[col] : 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(L::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *slot;
+
+  if (warp == 0) {
+    // ---------------- producer: digit tiles of A (128 rows) and B (NT rows) per stage
+    if (lane == 0) {
+      int issued = 0;
+      for (int kc = 0; kc < nkc && !*abort_flag; ++kc) {
+        const int s = kc & 1, use = kc >> 1;
+        if (!mbar_wait(bar + 16 + 8 * s, (use & 1) ^ 1)) { *abort_flag = 1; break; }
+        const uint32_t fb = bar + 8 * s;
+        mbar_expect_tx(fb, L::STAGE);
+        const __nv_bfloat16* srcA =
+            static_cast<const __nv_bfloat16*>(d.At) + (size_t)(bi * nkc + kc) * OZ_S * OZ_M * OZ_KC;
+        const __nv_bfloat16* srcB =
+            static_cast<const __nv_bfloat16*>(d.Bt) + (size_t)(bj * nkc + kc) * OZ_S * NT * OZ_KC;
+        const uint32_t dst = sbase + s * L::STAGE;
+#pragma unroll 1
+        for (int p = 0; p < OZ_S; ++p) {
+          bulk_g2s(dst + p * (OZ_M * OZ_KC * 2), srcA + (size_t)p * OZ_M * OZ_KC, OZ_M * OZ_KC * 2, fb);
+          bulk_g2s(dst + L::A_BYTES + p * (NT * OZ_KC * 2), srcB + (size_t)p * NT * OZ_KC, NT * OZ_KC * 2,
+                   fb);
+        }
+        issued = kc + 1;
+      }
+      // never leave copies in flight: wait (bounded) for the last issued stages to land
+      for (int kc = (issued > 2 ? issued - 2 : 0); kc < issued; ++kc)
+        mbar_wait(bar + 8 * (kc & 1), (kc >> 1) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(OZ_M, NT);
+      for (int kc = 0; kc < nkc && !*abort_flag; ++kc) {
+        const int s = kc & 1, use = kc >> 1, chunk = kc >> 1;
+        const bool chunk_start = (kc & 1) == 0;
+        if (chunk_start && !mbar_wait(bar + 40, (chunk & 1) ^ 1)) { *abort_flag = 1; break; }
+        if (!mbar_wait(bar + 8 * s, use & 1)) { *abort_flag = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = sbase + s * L::STAGE, b0 = a0 + L::A_BYTES;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+#pragma unroll
+          for (int g = 2; g <= OZ_S + 1; ++g) {
+#pragma unroll
+            for (int p = 1; p <= OZ_S; ++p) {
+              const int q = g - p;
+              if (q < 1 || q > OZ_S) continue;
+              const uint32_t first = (chunk_start && t == 0 && p == (g - 1 < OZ_S ? 1 : g - OZ_S));
+              const uint64_t ad = sdesc(a0 + (p - 1) * (OZ_M * OZ_KC * 2) + t * 256, 128, 512);
+              const uint64_t bd = sdesc(b0 + (q - 1) * (NT * OZ_KC * 2) + t * 256, 128, 512);
+              mma_bf16(tmem + (g - 2) * NT, ad, bd, idesc, first ? 0u : 1u);
+            }
+          }
+        }
+        mma_commit(bar + 16 + 8 * s);                         // stage s may be refilled
+        if ((kc & 1) == 1 || kc == nkc - 1) mma_commit(bar + 32);  // 64-chunk complete
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 own TMEM lanes 32*(warp%4) ..
+    // The 7 group sums of a 64-chunk are exact integers; with
+    //   H = a2 2^24 + a3 2^16 + a4 2^8,   L = a5 2^24 + a6 2^16 + a7 2^8 + a8
+    // (a_g the sum of group g) the chunk's value is (H 2^24 + L) 2^-48 in units of
+    // 2^(E_i + F_j - 16).  H and L stay below 2^53 for up to 64 chunks, so they are
+    // accumulated exactly in int64 and rounded once, by one FMA, at the end.
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int gi = bi * OZ_M + row;
+    const int ei = gi < d.M ? d.Ae[gi] : 0;
+    const bool unit_alpha = alpha == 1.0 || alpha == -1.0;
+    const bool neg_alpha = alpha < 0.0;
+    // alpha * 2^(E_i + F_j - 64) * (H 2^24 + L), with the scaling folded into the exponent
+    // fields: two exact integer-to-double conversions and one rounding add.
+    auto product = [&](long long H, long long Lw, int fj) -> double {
+      if (ei == 0 || fj == 0) return 0.0;
+      const int k = ei + fj - 2044 - 64;
+      double v = i64_to_double_pow2(H, k + 24, neg_alpha) + i64_to_double_pow2(Lw, k, neg_alpha);
+      return unit_alpha ? v : v * (neg_alpha ? -alpha : alpha);
+    };
+    auto finish = [&](long long H, long long Lw, int j) {
+      const int gj = bj * NT + j;
+      if (gi >= d.M || gj >= d.N) return;
+      double v = product(H, Lw, sexp[j]);
+      if ((flags & GEMM_ADD_IDENTITY) && gi == gj) v += 1.0;
+      double* cp = d.C + (size_t)gi * d.c_rs + (size_t)gj * d.c_cs;
+      if (beta == 0.0) *cp = v;
+      else if (beta == 1.0) *cp = *cp + v;
+      else *cp = fma(beta, *cp, v);
+    };
+    auto group_words = [&](const uint32_t (&v)[OZ_G][8], int j, long long& H, long long& Lw) {
+      int a[OZ_G];
+#pragma unroll
+      for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][j]));
+      H = ((long long)a[0] << 24) + ((long long)a[1] << 16) + ((long long)a[2] << 8);
+      Lw = ((long long)a[3] << 24) + ((long long)a[4] << 16) + ((long long)a[5] << 8) + a[6];
+    };
+    bool ok = true;
+    if (nchunk <= 1 || NT > 32) {
+      // single 64-chunk (K <= 64): no persistent accumulators.  The C values this thread
+      // updates are fetched before waiting for the MMAs, so their latency overlaps them.
+      double cv[NT];
+      const bool need_c = beta != 0.0 && gi < d.M;
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int gj = bj * NT + j;
+        cv[j] = (need_c && gj < d.N) ? d.C[(size_t)gi * d.c_rs + (size_t)gj * d.c_cs] : 0.0;
+      }
+      if (nchunk == 1) {
+        if (!mbar_wait_warp(bar + 32, 0)) { ok = false; *abort_flag = 1; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+      }
+      if (ok) {  // warp-uniform: every lane takes part in the tcgen05.ld below
+#pragma unroll
+        for (int cb = 0; cb < NT / 8; ++cb) {
+          uint32_t v[OZ_G][8];
+          if (nchunk == 1) {
+#pragma unroll
+            for (int g = 0; g < OZ_G; ++g) tmem_ld8(lane_base + g * NT + cb * 8, v[g]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+          } else {
+#pragma unroll
+            for (int g = 0; g < OZ_G; ++g)
+#pragma unroll
+              for (int j = 0; j < 8; ++j) v[g][j] = 0u;
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int jj = cb * 8 + j, gj = bj * NT + jj;
+            if (gi < d.M && gj < d.N) {
+              long long H, Lw;
+              group_words(v, j, H, Lw);
+              double pv = product(H, Lw, sexp[jj]);
+              if ((flags & GEMM_ADD_IDENTITY) && gi == gj) pv += 1.0;
+              d.C[(size_t)gi * d.c_rs + (size_t)gj * d.c_cs] =
+                  beta == 0.0 ? pv : (beta == 1.0 ? cv[jj] + pv : fma(beta, cv[jj], pv));
+            }
+          }
+        }
+      }
+    } else {
+      long long H[NT], Lw[NT];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) { H[j] = 0; Lw[j] = 0; }
+      for (int c = 0; c < nchunk; ++c) {
+        if (!mbar_wait_warp(bar + 32, c & 1)) { ok = false; *abort_flag = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+        for (int cb = 0; cb < NT / 8; ++cb) {
+          uint32_t v[OZ_G][8];
+#pragma unroll
+          for (int g = 0; g < OZ_G; ++g) tmem_ld8(lane_base + g * NT + cb * 8, v[g]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            long long h, l;
+            group_words(v, j, h, l);
+            H[cb * 8 + j] += h;
+            Lw[cb * 8 + j] += l;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        mbar_arrive(bar + 40);
+      }
+      if (ok) {
+#pragma unroll
+        for (int j = 0; j < NT; ++j) finish(H[j], Lw[j], j);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(L::TMEM_COLS));
+  }
+}
+
+template <int NT>
+cudaError_t launch_oz(const OzDesc* d, int count, int max_tiles, double alpha, double beta,
+                      int flags, unsigned* status, cudaStream_t st) {
+  static bool attr = false;
+  const int smem = OzSmem<NT>::TOTAL;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_ozaki<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  for (int off = 0; off < count; off += 65535) {
+    const int c = count - off < 65535 ? count - off : 65535;
+    k_ozaki<NT><<<dim3(max_tiles, c), OZ_THREADS, smem, st>>>(d + off, alpha, beta, flags, status);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int oz_tiles(int m, int n, int nt) { return ((m + OZ_M - 1) / OZ_M) * ((n + nt - 1) / nt); }
+
+size_t oz_split_elems(int R, int K, int row_tile) {
+  return (size_t)((R + row_tile - 1) / row_tile) * ((K + OZ_KC - 1) / OZ_KC) * OZ_S * row_tile * OZ_KC;
+}
+
+cudaError_t launch_split(const SplitDesc* d, int count, int max_rows, int max_split_blocks,
+                         cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  for (int off = 0; off < count; off += 65535) {
+    const int c = count - off < 65535 ? count - off : 65535;
+    k_rowexp<<<dim3((max_rows + 7) / 8, c), 256, 0, st>>>(d + off);
+    k_split<<<dim3(max_split_blocks, c), 256, 0, st>>>(d + off);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ozaki(int nt, const OzDesc* d, int count, int max_tiles, double alpha,
+                         double beta, int flags, unsigned* status, cudaStream_t st) {
+  if (count <= 0 || max_tiles <= 0) return cudaSuccess;
+  if (nt == 32) return launch_oz<32>(d, count, max_tiles, alpha, beta, flags, status, st);
+  return launch_oz<64>(d, count, max_tiles, alpha, beta, flags, status, st);
+}
+
+}  // namespace elmddm

@@ -36,7 +36,10 @@ class ElmDdmError(RuntimeError):
 class Desc(ctypes.Structure):
     _fields_ = [("n_sub", ctypes.c_int32), ("n_neurons", ctypes.c_int32),
                 ("m_max", ctypes.c_int32), ("n_gamma", ctypes.c_int32),
-                ("op", ctypes.c_int32), ("max_rhs", ctypes.c_int32)]
+                ("op", ctypes.c_int32), ("max_rhs", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+FLAG_FP64_SIMT = 1
 
 
 _lib = None
@@ -107,7 +110,7 @@ class GeometryArrays:
 class Solver:
     """One decomposition on one GPU: setup -> assemble(theta) -> schur() -> solve(rhs)."""
 
-    def __init__(self, geom, n_neurons: int, max_rhs: int = 1, stream=None):
+    def __init__(self, geom, n_neurons: int, max_rhs: int = 1, stream=None, fp64_simt: bool = False):
         import torch
         self.lib = load()
         ga = geom if isinstance(geom, GeometryArrays) else GeometryArrays.from_geometry(geom)
@@ -115,7 +118,7 @@ class Solver:
         self.N, self.n, self.m_max, self.n_gamma = N, int(n_neurons), m_max, ga.n_gamma
         self.max_rhs = max_rhs
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        desc = Desc(N, self.n, m_max, ga.n_gamma, 0, max_rhs)
+        desc = Desc(N, self.n, m_max, ga.n_gamma, 0, max_rhs, FLAG_FP64_SIMT if fp64_simt else 0)
         h = ctypes.c_void_p()
         self._keep = ga
         rc = self.lib.elm_ddm_setup(ctypes.byref(desc), ga.counts.ctypes.data, ga.xy.ctypes.data,

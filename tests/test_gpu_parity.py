@@ -53,8 +53,8 @@ def t(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a), device=DEV, dtype=dtype)
 
 
-def gpu_run(w, max_rhs=1, rhs=None):
-    s = E.Solver(w.geom, w.n_neurons, max_rhs=max_rhs)
+def gpu_run(w, max_rhs=1, rhs=None, fp64_simt=False):
+    s = E.Solver(w.geom, w.n_neurons, max_rhs=max_rhs, fp64_simt=fp64_simt)
     s.assemble(t(w.W), t(w.b))
     s.schur()
     ug, c = s.solve(t(w.rhs if rhs is None else rhs))
@@ -89,10 +89,13 @@ def test_assembly_matches_oracle(name):
     s.check()
 
 
+@pytest.mark.parametrize("fp64_simt", [False, True], ids=["tensor-core", "fp64-pipe"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_solution_matches_oracle(name):
+def test_solution_matches_oracle(name, fp64_simt):
+    """Both GEMM back ends: FP64-accurate digit-split products on the tensor cores (the
+    default) and plain FP64 on the FP64 pipe."""
     w, res, u_or, g_or = get(name)
-    s, ug, c, u, g = gpu_run(w)
+    s, ug, c, u, g = gpu_run(w, fp64_simt=fp64_simt)
     assert rel(u.cpu().numpy(), u_or) <= 1e-8
     assert rel(g.cpu().numpy(), g_or) <= 1e-7
     if w.geom.n_gamma:
@@ -101,10 +104,11 @@ def test_solution_matches_oracle(name):
         assert rel(c.cpu().numpy(), res.c) <= 1e-8
 
 
-def test_factor_pieces_match_oracle_when_well_conditioned():
+@pytest.mark.parametrize("fp64_simt", [False, True], ids=["tensor-core", "fp64-pipe"])
+def test_factor_pieces_match_oracle_when_well_conditioned(fp64_simt):
     w, res, _, _ = get("4x4_wellcond")
     assert res.rdiag_ratio.min() > 1e-6
-    s, *_ = gpu_run(w)
+    s, *_ = gpu_run(w, fp64_simt=fp64_simt)
     n = w.n_neurons
     for sd, L in enumerate(res.locs):
         F = s.export(E.BUF_K, sd).cpu().numpy()
@@ -124,13 +128,20 @@ def test_factor_pieces_match_oracle_when_well_conditioned():
     assert np.abs(S - S_or).max() <= 1e-11 * np.abs(res.S).max()
 
 
-def test_full_size_8x8_n1000_matches_oracle():
+_full = {}
+
+
+@pytest.mark.parametrize("fp64_simt", [False, True], ids=["tensor-core", "fp64-pipe"])
+def test_full_size_8x8_n1000_matches_oracle(fp64_simt):
     """The benchmark workload itself (8x8 subdomains, 1000 neurons, 2400 rows each,
     n_Gamma = 11200) in the launch configuration the benchmark times."""
-    w = wl.poisson_8x8_n1000()
-    res = O.solve(w.geom, w.W, w.b, w.rhs, keep=False)
-    u_or, g_or = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
-    s, ug, c, u, g = gpu_run(w)
+    if not _full:
+        w = wl.poisson_8x8_n1000()
+        res = O.solve(w.geom, w.W, w.b, w.rhs, keep=False)
+        u_or, g_or = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
+        _full.update(w=w, res=res, u_or=u_or)
+    w, res, u_or = _full["w"], _full["res"], _full["u_or"]
+    s, ug, c, u, g = gpu_run(w, fp64_simt=fp64_simt)
     assert rel(u.cpu().numpy(), u_or) <= 1e-8
     assert rel(ug.cpu().numpy(), res.u_gamma) <= 1e-8
     # and the method itself is accurate on this manufactured solution
