@@ -184,9 +184,10 @@ int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value);
  * bracketed by a pair of CUDA events on its stream (events are created on first use
  * and reused; no device memory is allocated).  elm_ddm_profile_report synchronises the
  * stream and writes a JSON object {"<kernel class>": {"launches": L, "ms": T,
- * "flops": F}, ..., "_dropped": D} into buf (NUL-terminated), where F is the
- * algorithmic flop count of the dense-update launches (0 for other classes), then
- * clears the records.  Returns ELM_DDM_ERR_ARG if buf is too small.
+ * "flops": F, "bytes": B}, ..., "_dropped": D} into buf (NUL-terminated), where F and B
+ * are the algorithmic flops and HBM bytes of the dense-update and operand-split launches
+ * (0 for other classes), then clears the records.  Returns ELM_DDM_ERR_ARG if buf is too
+ * small.
  */
 int elm_ddm_profile(elm_ddm_handle* h, int enable);
 int elm_ddm_profile_report(elm_ddm_handle* h, char* buf, int buflen);

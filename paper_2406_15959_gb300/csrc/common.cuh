@@ -55,6 +55,7 @@ struct OzDesc {
   double* C;
   long long c_rs, c_cs;
   int M, N, K;
+  int tile0;  // persistent launches: index of this entry's first 128 x 32 tile in the batch
 };
 
 // ---- launchers (return cudaGetLastError after the launch) ----
@@ -64,6 +65,10 @@ cudaError_t launch_split(const SplitDesc* d, int count, int max_rows, int max_sp
                          cudaStream_t st);
 cudaError_t launch_ozaki(int nt, const OzDesc* d, int count, int max_tiles, double alpha,
                          double beta, int flags, unsigned* status, cudaStream_t st);
+// Persistent variant for K <= 64 (one CTA per SM over all 128 x 32 tiles of the batch;
+// entries carry their first tile index in tile0, total_tiles = tiles of the whole batch).
+cudaError_t launch_ozaki_upd(const OzDesc* d, int count, int total_tiles, double alpha,
+                             double beta, int flags, unsigned* status, cudaStream_t st);
 cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_tiles,
                         double alpha, double beta, int flags, cudaStream_t st);
 cudaError_t launch_add_blocks(const AddDesc* d, int count, int max_elems, cudaStream_t st);

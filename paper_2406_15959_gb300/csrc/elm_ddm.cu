@@ -19,20 +19,23 @@ using namespace elmddm;
 namespace {
 
 struct LaunchRec {
-  int kind;  // 0 = FP64 gemm, 1 = add_blocks, 2 = digit split, 3 = tensor-core digit GEMM
+  int kind;  // 0 = FP64 gemm, 1 = add_blocks, 2 = digit split, 3 = tensor-core digit GEMM,
+             // 4 = persistent tensor-core digit GEMM for K <= 64 (max_tiles = total tiles)
   int off, count, max_tiles;  // split: max_tiles = blocks of k_split, nt = max rows
   bool ta, tb;
   double alpha, beta;
   int flags;
   double flops;  // algorithmic flops of the launch (2mnk per GEMM; m(m+1)k for a lower SYRK)
   int nt;        // tensor-core GEMM: tile width (32 or 64); split: largest row count
+  double bytes = 0.0;          // algorithmic HBM bytes (FP64 operands read, C read/written)
+  const char* name = nullptr;  // kernel class for profiling (nullptr: the caller's name)
 };
 
 // One profiled launch: events around it, its class and algorithmic flops.
 struct ProfRec {
   cudaEvent_t a, b;
   const char* name;
-  double flops;
+  double flops, bytes;
 };
 
 struct Edge {
@@ -183,8 +186,9 @@ struct ProfScope {
   elm_ddm_handle* h;
   cudaEvent_t a = nullptr;
   const char* name;
-  double flops;
-  ProfScope(elm_ddm_handle* h_, const char* n, double f) : h(h_), name(n), flops(f) {
+  double flops, bytes;
+  ProfScope(elm_ddm_handle* h_, const char* n, double f, double by = 0.0)
+      : h(h_), name(n), flops(f), bytes(by) {
     if (h->profiling) {
       a = next_event(h);
       if (a) cudaEventRecord(a, h->st);
@@ -195,10 +199,20 @@ struct ProfScope {
     cudaEvent_t b = a ? next_event(h) : nullptr;
     if (!b) { h->prof_dropped++; return; }
     cudaEventRecord(b, h->st);
-    h->prof.push_back({a, b, name, flops});
+    h->prof.push_back({a, b, name, flops, bytes});
   }
 };
 
+#define ELM_LAUNCH_FB(h, expr, where, flops, bytes)          \
+  do {                                                       \
+    cudaError_t e_;                                          \
+    {                                                        \
+      ProfScope ps_((h), (where), (flops), (bytes));         \
+      e_ = (expr);                                           \
+    }                                                        \
+    (h)->launches++;                                         \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, where); \
+  } while (0)
 #define ELM_LAUNCH_F(h, expr, where, flops)                  \
   do {                                                       \
     cudaError_t e_;                                          \
@@ -216,16 +230,21 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
   for (size_t r = first; r < first + cnt && r < recs.size(); ++r) {
     const LaunchRec& L = recs[r];
     if (L.count <= 0) continue;
+    const char* nm = L.name ? L.name : gemm_name;
     if (L.kind == 0)
-      ELM_LAUNCH_F(h, launch_gemm(L.ta, L.tb, h->gd + L.off, L.count, L.max_tiles, L.alpha, L.beta,
-                                  L.flags, h->st), gemm_name, L.flops);
+      ELM_LAUNCH_FB(h, launch_gemm(L.ta, L.tb, h->gd + L.off, L.count, L.max_tiles, L.alpha, L.beta,
+                                   L.flags, h->st), nm, L.flops, L.bytes);
     else if (L.kind == 1)
       ELM_LAUNCH(h, launch_add_blocks(h->ad + L.off, L.count, L.max_tiles, h->st), "add_blocks");
     else if (L.kind == 2)
-      ELM_LAUNCH(h, launch_split(h->sd + L.off, L.count, L.nt, L.max_tiles, h->st), "split");
+      ELM_LAUNCH_FB(h, launch_split(h->sd + L.off, L.count, L.nt, L.max_tiles, h->st), nm, 0.0,
+                    L.bytes);
+    else if (L.kind == 3)
+      ELM_LAUNCH_FB(h, launch_ozaki(L.nt, h->od + L.off, L.count, L.max_tiles, L.alpha, L.beta,
+                                    L.flags, h->status, h->st), nm, L.flops, L.bytes);
     else
-      ELM_LAUNCH_F(h, launch_ozaki(L.nt, h->od + L.off, L.count, L.max_tiles, L.alpha, L.beta,
-                                   L.flags, h->status, h->st), gemm_name, L.flops);
+      ELM_LAUNCH_FB(h, launch_ozaki_upd(h->od + L.off, L.count, L.max_tiles, L.alpha, L.beta,
+                                        L.flags, h->status, h->st), nm, L.flops, L.bytes);
   }
   return ELM_DDM_OK;
 }
@@ -441,10 +460,10 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const size_t s1 = al(oz_split_elems(n2max, mpmax, 128) * 2), e1 = al((size_t)n2max * 4);
   const size_t s2 = al(oz_split_elems(QR_NB, mpmax, 32) * 2), e2 = al((size_t)QR_NB * 4);
   const size_t s3 = al(oz_split_elems(mpmax, QR_NB, 128) * 2), e3 = al((size_t)mpmax * 4);
-  const size_t s4 = al(oz_split_elems(n2max, QR_NB, 64) * 2), e4 = al((size_t)n2max * 4);
+  const size_t s4 = al(oz_split_elems(n2max, QR_NB, 32) * 2), e4 = al((size_t)n2max * 4);
   const size_t per_sub = s1 + e1 + s2 + e2 + s3 + e3 + s4 + e4;
   const size_t c1 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 128) * 2);
-  const size_t c2 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 64) * 2);
+  const size_t c2 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 32) * 2);
   const size_t ce = al((size_t)std::max(restmax, 1) * 4);
   if (h->emulated) {
     char* base = nullptr;
@@ -511,26 +530,40 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   // small T^T W1 stays on the FP64 pipe.
   std::vector<SplitDesc> sds;
   std::vector<OzDesc> ods;
-  auto add_split_rec = [&](std::vector<LaunchRec>& recs, const std::vector<SplitDesc>& batch) {
+  auto add_split_rec = [&](std::vector<LaunchRec>& recs, const std::vector<SplitDesc>& batch,
+                           const char* name) {
     LaunchRec L{2, (int)sds.size(), 0, 0, false, false, 0, 0, 0, 0.0, 0};
+    L.name = name;
     for (const SplitDesc& d : batch) {
       if (d.R <= 0 || d.K <= 0) continue;
       sds.push_back(d);
       L.count++;
+      L.bytes += (8.0 + 2.0 * 7) * d.R * d.K;  // FP64 read once, 7 BF16 digit planes written
       L.nt = std::max(L.nt, d.R);
       L.max_tiles = std::max(L.max_tiles, (d.R + d.row_tile - 1) / d.row_tile * ((d.K + 31) / 32));
     }
     recs.push_back(L);
   };
   auto add_oz_rec = [&](std::vector<LaunchRec>& recs, const std::vector<OzDesc>& batch, int nt,
-                        double alpha, double beta, int flags) {
-    LaunchRec L{3, (int)ods.size(), 0, 0, false, false, alpha, beta, flags, 0.0, nt};
-    for (const OzDesc& d : batch) {
+                        double alpha, double beta, int flags, const char* name) {
+    // nt == 0: persistent K <= 64 kernel over 128 x 32 tiles (max_tiles = tiles in total)
+    LaunchRec L{nt == 0 ? 4 : 3, (int)ods.size(), 0, 0, false, false, alpha, beta, flags, 0.0, nt};
+    L.name = name;
+    for (OzDesc d : batch) {
       if (d.M <= 0 || d.N <= 0) continue;
+      if (nt == 0) {
+        d.tile0 = L.max_tiles;
+        L.max_tiles += oz_tiles(d.M, d.N, 32);
+      } else {
+        L.max_tiles = std::max(L.max_tiles, oz_tiles(d.M, d.N, nt));
+      }
       ods.push_back(d);
       L.count++;
-      L.max_tiles = std::max(L.max_tiles, oz_tiles(d.M, d.N, nt));
-      L.flops += (flags & GEMM_LOWER) ? (double)d.M * (d.M + 1) * d.K : 2.0 * d.M * d.N * d.K;
+      const bool low = (flags & GEMM_LOWER) != 0;
+      L.flops += low ? (double)d.M * (d.M + 1) * d.K : 2.0 * d.M * d.N * d.K;
+      // FP64 operands read once, C written (and read when beta != 0)
+      const double cbytes = (beta != 0.0 ? 16.0 : 8.0) * (low ? 0.5 * d.M * (d.M + 1.0) : (double)d.M * d.N);
+      L.bytes += 8.0 * ((double)d.M * d.K + (low ? 0.0 : (double)d.N * d.K)) + cbytes;
     }
     recs.push_back(L);
   };
@@ -558,19 +591,20 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
         void* t4 = sub_region(s, 6); int* x4 = (int*)sub_region(s, 7);
         sp1.push_back({A2, ld, 1, n2, mp, x1, t1, 128});     // A2^T: rows = trailing columns
         sp1.push_back({V, ld, 1, nbe, mp, x2, t2, 32});      // V^T: rows = panel columns
-        o1.push_back({t1, x1, t2, x2, w1, QR_NB, 1, n2, nbe, mp});
+        o1.push_back({t1, x1, t2, x2, w1, QR_NB, 1, n2, nbe, mp, 0});
         sp3.push_back({V, 1, ld, mp, nbe, x3, t3, 128});     // V: rows = matrix rows
-        sp3.push_back({w2, QR_NB, 1, n2, nbe, x4, t4, 64});  // W2^T: rows = trailing columns
-        o3.push_back({t3, x3, t4, x4, A2, 1, ld, mp, n2, nbe});
+        sp3.push_back({w2, QR_NB, 1, n2, nbe, x4, t4, 32});  // W2^T: rows = trailing columns
+        o3.push_back({t3, x3, t4, x4, A2, 1, ld, mp, n2, nbe, 0});
       }
     }
     h->qr_first.push_back((int)h->qr_recs.size());
     if (h->emulated) {
-      add_split_rec(h->qr_recs, sp1);
-      add_oz_rec(h->qr_recs, o1, 32, 1.0, 0.0, 0);
+      add_split_rec(h->qr_recs, sp1, "split_qr_w");
+      add_oz_rec(h->qr_recs, o1, 32, 1.0, 0.0, 0, "oz_qr_w");
       add_gemm_rec(h->qr_recs, g2, true, false, 1.0, 0.0, 0);
-      add_split_rec(h->qr_recs, sp3);
-      add_oz_rec(h->qr_recs, o3, 64, -1.0, 1.0, 0);
+      h->qr_recs.back().name = "gemm_qr_t";
+      add_split_rec(h->qr_recs, sp3, "split_qr_update");
+      add_oz_rec(h->qr_recs, o3, 0, -1.0, 1.0, 0, "oz_qr_update");
     } else {
       add_gemm_rec(h->qr_recs, g1, true, false, 1.0, 0.0, 0);
       add_gemm_rec(h->qr_recs, g2, true, false, 1.0, 0.0, 0);
@@ -667,10 +701,11 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
         int* xa = (int*)(chol_region + c1 + c2);
         int* xb = (int*)(chol_region + c1 + c2 + ce);
         std::vector<SplitDesc> sp{{L21, 1, ng, rest, nb, xa, chol_region, 128},
-                                  {L21, 1, ng, rest, nb, xb, chol_region + c1, 64}};
-        add_split_rec(h->syrk_recs, sp);
-        add_oz_rec(h->syrk_recs, {{chol_region, xa, chol_region + c1, xb, S22, 1, ng, rest, rest, nb}},
-                   64, -1.0, 1.0, GEMM_LOWER);
+                                  {L21, 1, ng, rest, nb, xb, chol_region + c1, 32}};
+        add_split_rec(h->syrk_recs, sp, "split_syrk");
+        add_oz_rec(h->syrk_recs,
+                   {{chol_region, xa, chol_region + c1, xb, S22, 1, ng, rest, rest, nb, 0}}, 0, -1.0,
+                   1.0, GEMM_LOWER, "oz_syrk");
       } else {
         add_gemm_rec(h->syrk_recs, {{L21, L21, S22, rest, rest, nb, ng, ng, ng}}, false, true, -1.0,
                      1.0, GEMM_LOWER);
@@ -871,20 +906,22 @@ int elm_ddm_profile_report(elm_ddm_handle* h, char* buf, int buflen) {
   if (!h || !buf || buflen < 2) return ELM_DDM_ERR_ARG;
   cudaError_t e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return cuda_fail(h, e, "profile_report");
-  struct Acc { long long n = 0; double ms = 0, flops = 0; };
+  struct Acc { long long n = 0; double ms = 0, flops = 0, bytes = 0; };
   std::map<std::string, Acc> acc;
   for (const ProfRec& r : h->prof) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) { cudaGetLastError(); continue; }
     Acc& a = acc[r.name];
-    a.n++; a.ms += ms; a.flops += r.flops;
+    a.n++; a.ms += ms; a.flops += r.flops; a.bytes += r.bytes;
   }
   std::string out = "{";
   bool first = true;
   for (auto& kv : acc) {
     char tmp[256];
-    snprintf(tmp, sizeof tmp, "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e}",
-             first ? "" : ", ", kv.first.c_str(), kv.second.n, kv.second.ms, kv.second.flops);
+    snprintf(tmp, sizeof tmp,
+             "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e, \"bytes\": %.6e}",
+             first ? "" : ", ", kv.first.c_str(), kv.second.n, kv.second.ms, kv.second.flops,
+             kv.second.bytes);
     out += tmp;
     first = false;
   }

@@ -463,6 +463,235 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
   }
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Persistent update kernel for short products (K <= 64: the rank-32 QR update and the
+// Cholesky SYRK).  One CTA per SM walks the 128 x 32 tiles of the whole batch; two
+// shared-memory stages and two TMEM accumulator sets (7 x 32 columns each) let the loads
+// and MMAs of the next tile run while eight epilogue warps finish the current one.
+// Warp roles: 0 producer, 1 MMA (and TMEM owner), 2..9 epilogue (warp w drains TMEM lane
+// quarter w % 4, columns 16 * ((w - 2) / 4) .. +15).
+constexpr int UPD_NT = 32;
+constexpr int UPD_THREADS = 320;
+constexpr int UPD_A = OZ_S * OZ_M * OZ_KC * 2;       // 57344 B
+constexpr int UPD_B = OZ_S * UPD_NT * OZ_KC * 2;     // 14336 B
+constexpr int UPD_STAGE = UPD_A + UPD_B;
+constexpr int UPD_BAR = 2 * UPD_STAGE;               // full0 full1 empty0 empty1 tfull0 tfull1 tempty0 tempty1
+constexpr int UPD_SLOT = UPD_BAR + 64;
+constexpr int UPD_FLAG = UPD_SLOT + 16;
+constexpr int UPD_SMEM = UPD_FLAG + 16 + 1024;
+
+struct TileRef {
+  int e, bi, bj;
+};
+
+// Entry and tile coordinates of global tile t (entries sorted by tile0).
+__device__ __forceinline__ TileRef upd_tile(const OzDesc* __restrict__ descs, int count, int t) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (descs[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+  }
+  const OzDesc& d = descs[lo];
+  const int tiles_m = (d.M + OZ_M - 1) / OZ_M;
+  const int local = t - d.tile0;
+  return {lo, local % tiles_m, local / tiles_m};
+}
+
+__device__ __forceinline__ bool upd_skip(const OzDesc& d, const TileRef& r, int flags) {
+  return (flags & GEMM_LOWER) && r.bj * UPD_NT > r.bi * OZ_M + OZ_M - 1;
+}
+
+__global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __restrict__ descs,
+                                                             int count, int total_tiles,
+                                                             double alpha, double beta, int flags,
+                                                             unsigned* status) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar = sbase + UPD_BAR;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + UPD_SLOT);
+  volatile int* abort_flag = reinterpret_cast<int*>(smem + UPD_FLAG);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t FULL = bar, EMPTY = bar + 16, TFULL = bar + 32, TEMPTY = bar + 48;
+
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(FULL + 8 * i, 1);
+      mbar_init(EMPTY + 8 * i, 1);
+      mbar_init(TFULL + 8 * i, 1);
+      mbar_init(TEMPTY + 8 * i, 256);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int sc = 0;  // stage counter
+      for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
+        const TileRef r = upd_tile(descs, count, t);
+        const OzDesc& d = descs[r.e];
+        if (upd_skip(d, r, flags)) continue;
+        const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
+        for (int kc = 0; kc < nkc; ++kc, ++sc) {
+          const int s = sc & 1, use = sc >> 1;
+          if (!mbar_wait(EMPTY + 8 * s, (use & 1) ^ 1)) { *abort_flag = 1; break; }
+          mbar_expect_tx(FULL + 8 * s, UPD_STAGE);
+          const __nv_bfloat16* srcA =
+              static_cast<const __nv_bfloat16*>(d.At) + (size_t)(r.bi * nkc + kc) * OZ_S * OZ_M * OZ_KC;
+          const __nv_bfloat16* srcB =
+              static_cast<const __nv_bfloat16*>(d.Bt) + (size_t)(r.bj * nkc + kc) * OZ_S * UPD_NT * OZ_KC;
+          const uint32_t dst = sbase + s * UPD_STAGE;
+          bulk_g2s(dst, srcA, UPD_A, FULL + 8 * s);
+          bulk_g2s(dst + UPD_A, srcB, UPD_B, FULL + 8 * s);
+        }
+      }
+      // drain: wait for the copies of the last two stages
+      for (int q = (sc > 2 ? sc - 2 : 0); q < sc; ++q) mbar_wait(FULL + 8 * (q & 1), (q >> 1) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(OZ_M, UPD_NT);
+      int sc = 0, tc = 0;  // stage and tile counters
+      for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
+        const TileRef r = upd_tile(descs, count, t);
+        const OzDesc& d = descs[r.e];
+        if (upd_skip(d, r, flags)) continue;
+        const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
+        const int buf = tc & 1;
+        if (!mbar_wait(TEMPTY + 8 * buf, ((tc >> 1) & 1) ^ 1)) { *abort_flag = 1; break; }
+        const uint32_t dbase = tmem + buf * (OZ_G * UPD_NT);
+        bool fail = false;
+        for (int kc = 0; kc < nkc; ++kc, ++sc) {
+          const int s = sc & 1, use = sc >> 1;
+          if (!mbar_wait(FULL + 8 * s, use & 1)) { fail = true; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t a0 = sbase + s * UPD_STAGE, b0 = a0 + UPD_A;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+#pragma unroll
+            for (int g = 2; g <= OZ_S + 1; ++g) {
+#pragma unroll
+              for (int p = 1; p <= OZ_S; ++p) {
+                const int q = g - p;
+                if (q < 1 || q > OZ_S) continue;
+                const uint32_t first = (kc == 0 && k == 0 && p == 1);
+                const uint64_t ad = sdesc(a0 + (p - 1) * (OZ_M * OZ_KC * 2) + k * 256, 128, 512);
+                const uint64_t bd = sdesc(b0 + (q - 1) * (UPD_NT * OZ_KC * 2) + k * 256, 128, 512);
+                mma_bf16(dbase + (g - 2) * UPD_NT, ad, bd, idesc, first ? 0u : 1u);
+              }
+            }
+          }
+          mma_commit(EMPTY + 8 * s);
+        }
+        if (fail) { *abort_flag = 1; break; }
+        mma_commit(TFULL + 8 * buf);
+        ++tc;
+      }
+    }
+  } else {
+    const int ew = warp - 2, quarter = warp & 3, half = ew >> 2;
+    const int row = quarter * 32 + lane;
+    const bool neg_alpha = alpha < 0.0, unit_alpha = alpha == 1.0 || alpha == -1.0;
+    int tc = 0;
+    // prefetch of this thread's 16 C values of its next tile
+    double cv[16];
+    auto fetch = [&](const OzDesc& d, const TileRef& r) {
+      const int gi = r.bi * OZ_M + row;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int gj = r.bj * UPD_NT + half * 16 + j;
+        cv[j] = (beta != 0.0 && gi < d.M && gj < d.N) ? d.C[(size_t)gi * d.c_rs + (size_t)gj * d.c_cs] : 0.0;
+      }
+    };
+    int t = blockIdx.x;
+    // first non-skipped tile
+    while (t < total_tiles) {
+      const TileRef r = upd_tile(descs, count, t);
+      if (!upd_skip(descs[r.e], r, flags)) break;
+      t += gridDim.x;
+    }
+    if (t < total_tiles) {
+      const TileRef r0 = upd_tile(descs, count, t);
+      fetch(descs[r0.e], r0);
+    }
+    while (t < total_tiles) {
+      const TileRef r = upd_tile(descs, count, t);
+      const OzDesc& d = descs[r.e];
+      const int buf = tc & 1;
+      if (!mbar_wait_warp(TFULL + 8 * buf, (tc >> 1) & 1)) { *abort_flag = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      uint32_t v[OZ_G][2][8];
+      const uint32_t lb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (OZ_G * UPD_NT) + half * 16;
+#pragma unroll
+      for (int g = 0; g < OZ_G; ++g) {
+        tmem_ld8(lb + g * UPD_NT, v[g][0]);
+        tmem_ld8(lb + g * UPD_NT + 8, v[g][1]);
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      mbar_arrive(TEMPTY + 8 * buf);  // accumulators copied: the MMA may reuse this buffer
+      ++tc;
+      const int gi = r.bi * OZ_M + row;
+      if (gi < d.M) {
+        const int ei = d.Ae[gi];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int gj = r.bj * UPD_NT + half * 16 + j;
+          if (gj < d.N) {
+            int a[OZ_G];
+#pragma unroll
+            for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][j >> 3][j & 7]));
+            const long long H = ((long long)a[0] << 24) + ((long long)a[1] << 16) + ((long long)a[2] << 8);
+            const long long Lw =
+                ((long long)a[3] << 24) + ((long long)a[4] << 16) + ((long long)a[5] << 8) + a[6];
+            const int fj = d.Be[gj];
+            double pv = 0.0;
+            if (ei != 0 && fj != 0) {
+              const int k = ei + fj - 2044 - 64;
+              pv = i64_to_double_pow2(H, k + 24, neg_alpha) + i64_to_double_pow2(Lw, k, neg_alpha);
+              if (!unit_alpha) pv *= (neg_alpha ? -alpha : alpha);
+            }
+            if ((flags & GEMM_ADD_IDENTITY) && gi == gj) pv += 1.0;
+            d.C[(size_t)gi * d.c_rs + (size_t)gj * d.c_cs] =
+                beta == 0.0 ? pv : (beta == 1.0 ? cv[j] + pv : fma(beta, cv[j], pv));
+          }
+        }
+      }
+      // next tile of this CTA; its C values load while its MMAs run
+      int tn = t + gridDim.x;
+      while (tn < total_tiles) {
+        const TileRef rn = upd_tile(descs, count, tn);
+        if (!upd_skip(descs[rn.e], rn, flags)) break;
+        tn += gridDim.x;
+      }
+      if (tn < total_tiles) {
+        const TileRef rn = upd_tile(descs, count, tn);
+        fetch(descs[rn.e], rn);
+      }
+      t = tn;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
 template <int NT>
 cudaError_t launch_oz(const OzDesc* d, int count, int max_tiles, double alpha, double beta,
                       int flags, unsigned* status, cudaStream_t st) {
@@ -496,6 +725,23 @@ cudaError_t launch_split(const SplitDesc* d, int count, int max_rows, int max_sp
     k_rowexp<<<dim3((max_rows + 7) / 8, c), 256, 0, st>>>(d + off);
     k_split<<<dim3(max_split_blocks, c), 256, 0, st>>>(d + off);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ozaki_upd(const OzDesc* d, int count, int total_tiles, double alpha,
+                             double beta, int flags, unsigned* status, cudaStream_t st) {
+  if (count <= 0 || total_tiles <= 0) return cudaSuccess;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaFuncSetAttribute(k_ozaki_upd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         UPD_SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = total_tiles < sms ? total_tiles : sms;
+  k_ozaki_upd<<<grid, UPD_THREADS, UPD_SMEM, st>>>(d, count, total_tiles, alpha, beta, flags, status);
   return cudaGetLastError();
 }
 
