@@ -104,7 +104,8 @@ cudaError_t launch_backsolve(const double* X, const double* K, long long kstride
                              const int* mg, const int* ifc_dof, int mgld, const double* u,
                              int n_gamma, int N, int n, int nrhs, double* c, cudaStream_t st);
 
-cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, unsigned* status,
+// inv (nullable): receives the inverse of the nb x nb factor, column-major, ld CHOL_NB.
+cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, double* inv, unsigned* status,
                               cudaStream_t st);
 cudaError_t launch_trsm_chol(double* S, int ld, int n, int k, int nb, cudaStream_t st);
 // row_end < 0 means n; j_begin 0 means all rows above the block.

@@ -109,6 +109,9 @@ struct elm_ddm_handle {
   double *K = nullptr, *Am = nullptr, *tau = nullptr, *T = nullptr, *Vp = nullptr;
   double *W1 = nullptr, *W2 = nullptr, *D = nullptr, *M = nullptr, *S = nullptr;
   double *Mdiag = nullptr, *thW = nullptr, *thb = nullptr, *xy = nullptr, *nrm = nullptr;
+  double* cinv = nullptr;             // inverse of the current Cholesky diagonal block
+  std::vector<LaunchRec> trsm_recs;   // per Cholesky step: L21 = A21 L11^{-T} as a product
+  std::vector<int> trsm_first;
   double *X = nullptr, *gq = nullptr, *hq = nullptr, *zv = nullptr;
   double *rv = nullptr, *hv = nullptr, *yv = nullptr, *uv = nullptr;
   int *cnt = nullptr, *ms = nullptr, *mg = nullptr, *dofmap = nullptr, *ifc_dof = nullptr;
@@ -443,6 +446,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->cnt, (size_t)N * 3) && dev_alloc(h, &h->ms, (size_t)N) &&
             dev_alloc(h, &h->mg, (size_t)N) && dev_alloc(h, &h->dofmap, (size_t)ng * 4) &&
             dev_alloc(h, &h->ifc_dof, (size_t)N * h->mgld) && dev_alloc(h, &h->perm, (size_t)ng) &&
+            dev_alloc(h, &h->cinv, (size_t)CHOL_NB * CHOL_NB) &&
             dev_alloc(h, &h->status, 1);
   if (!ok) {
     free_all(h);
@@ -461,7 +465,12 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const size_t s2 = al(oz_split_elems(QR_NB, mpmax, 32) * 2), e2 = al((size_t)QR_NB * 4);
   const size_t s3 = al(oz_split_elems(mpmax, QR_NB, 128) * 2), e3 = al((size_t)mpmax * 4);
   const size_t s4 = al(oz_split_elems(n2max, QR_NB, 32) * 2), e4 = al((size_t)n2max * 4);
-  const size_t per_sub = s1 + e1 + s2 + e2 + s3 + e3 + s4 + e4;
+  // D_s / M_s products: Q_G as both operands, Y as the left operand (K = n_N)
+  const int mgm = std::max(mgmax, 1);
+  const size_t s5 = al(oz_split_elems(mgm, n, 128) * 2), e5 = al((size_t)mgm * 4);
+  const size_t s6 = al(oz_split_elems(mgm, n, 32) * 2), e6 = al((size_t)mgm * 4);
+  const size_t s7 = al(oz_split_elems(mgm, n, 128) * 2), e7 = al((size_t)mgm * 4);
+  const size_t per_sub = s1 + e1 + s2 + e2 + s3 + e3 + s4 + e4 + s5 + e5 + s6 + e6 + s7 + e7;
   const size_t c1 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 128) * 2);
   const size_t c2 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 32) * 2);
   const size_t ce = al((size_t)std::max(restmax, 1) * 4);
@@ -475,9 +484,10 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     h->sp_buf = base;
   }
   auto sub_region = [&](int s, int which) -> char* {
-    const size_t off[8] = {0, s1, s1 + e1, s1 + e1 + s2, s1 + e1 + s2 + e2, s1 + e1 + s2 + e2 + s3,
-                           s1 + e1 + s2 + e2 + s3 + e3, s1 + e1 + s2 + e2 + s3 + e3 + s4};
-    return (char*)h->sp_buf + (size_t)s * per_sub + off[which];
+    const size_t sz[14] = {s1, e1, s2, e2, s3, e3, s4, e4, s5, e5, s6, e6, s7, e7};
+    size_t off = 0;
+    for (int i = 0; i < which; ++i) off += sz[i];
+    return (char*)h->sp_buf + (size_t)s * per_sub + off;
   };
   char* chol_region = (char*)h->sp_buf + per_sub * N;
 
@@ -612,19 +622,40 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
   }
   h->qr_first.push_back((int)h->qr_recs.size());
-  // D_s = I - (Q_G^T)^T Q_G^T and M_s = -Y_s Q_G^T.
+  // D_s = I - (Q_G^T)^T Q_G^T and M_s = -Y_s Q_G^T (K = n_N): tensor-core products that
+  // share the digit split of Q_G, or FP64 GEMMs.
   {
     std::vector<GemmDesc> gD, gM;
+    std::vector<SplitDesc> sp;
+    std::vector<OzDesc> oD, oM;
     for (int s = 0; s < N; ++s) {
       const int mgs = h->mg_h[s];
       if (mgs == 0) continue;
       const double* QGt = h->K + (size_t)s * h->kstride + (size_t)n * ld;
-      gD.push_back({QGt, QGt, h->D + (size_t)s * h->mstride, mgs, mgs, n, ld, ld, h->mgld});
-      gM.push_back({h->Am + (size_t)s * h->astride, QGt, h->M + (size_t)s * h->mstride, mgs, mgs, n,
-                    h->mgld, ld, h->mgld});
+      double* Ds = h->D + (size_t)s * h->mstride;
+      double* Ms = h->M + (size_t)s * h->mstride;
+      const double* Ys = h->Am + (size_t)s * h->astride;
+      gD.push_back({QGt, QGt, Ds, mgs, mgs, n, ld, ld, h->mgld});
+      gM.push_back({Ys, QGt, Ms, mgs, mgs, n, h->mgld, ld, h->mgld});
+      if (h->emulated) {
+        void* t5 = sub_region(s, 8); int* x5 = (int*)sub_region(s, 9);
+        void* t6 = sub_region(s, 10); int* x6 = (int*)sub_region(s, 11);
+        void* t7 = sub_region(s, 12); int* x7 = (int*)sub_region(s, 13);
+        sp.push_back({QGt, ld, 1, mgs, n, x5, t5, 128});   // Q_G, left operand
+        sp.push_back({QGt, ld, 1, mgs, n, x6, t6, 32});    // Q_G, right operand
+        sp.push_back({Ys, 1, h->mgld, mgs, n, x7, t7, 128});  // Y_s, left operand
+        oD.push_back({t5, x5, t6, x6, Ds, 1, h->mgld, mgs, mgs, n, 0});
+        oM.push_back({t7, x7, t6, x6, Ms, 1, h->mgld, mgs, mgs, n, 0});
+      }
     }
-    add_gemm_rec(h->dm_recs, gD, true, false, -1.0, 0.0, GEMM_ADD_IDENTITY);
-    add_gemm_rec(h->dm_recs, gM, false, false, -1.0, 0.0, 0);
+    if (h->emulated) {
+      add_split_rec(h->dm_recs, sp, "split_dm");
+      add_oz_rec(h->dm_recs, oD, 32, -1.0, 0.0, GEMM_ADD_IDENTITY, "oz_dm");
+      add_oz_rec(h->dm_recs, oM, 32, -1.0, 0.0, 0, "oz_dm");
+    } else {
+      add_gemm_rec(h->dm_recs, gD, true, false, -1.0, 0.0, GEMM_ADD_IDENTITY);
+      add_gemm_rec(h->dm_recs, gM, false, false, -1.0, 0.0, 0);
+    }
   }
   // Schur matrix (lower edge blocks, internal order): S[e1,e2] = sum of D blocks +
   // sum_e Mblk(e,e1)^T Mblk(e,e2), each output block written once per round.
@@ -694,8 +725,14 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     for (int k = 0, step = 0; k < ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, ng - k), rest = h->chol_rend[step] - k - nb;
       h->syrk_first.push_back((int)h->syrk_recs.size());
+      h->trsm_first.push_back((int)h->trsm_recs.size());
       if (rest <= 0) continue;
       double* L21 = h->S + (k + nb) + (size_t)k * ng;
+      // panel solve as an in-place product: every 64-wide tile reads all of its rows of
+      // A21 before writing them, and the tiles never share rows
+      add_gemm_rec(h->trsm_recs, {{L21, h->cinv, L21, rest, nb, nb, ng, CHOL_NB, ng}}, false, true,
+                   1.0, 0.0, 0);
+      h->trsm_recs.back().name = "trsm_chol";
       double* S22 = h->S + (k + nb) + (size_t)(k + nb) * ng;
       if (h->emulated) {
         int* xa = (int*)(chol_region + c1 + c2);
@@ -712,6 +749,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       }
     }
     h->syrk_first.push_back((int)h->syrk_recs.size());
+    h->trsm_first.push_back((int)h->trsm_recs.size());
   }
   ok = dev_alloc(h, &h->gd, gds.size()) && dev_alloc(h, &h->ad, ads.size()) &&
        dev_alloc(h, &h->sd, sds.size()) && dev_alloc(h, &h->od, ods.size());
@@ -788,9 +826,11 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     if (rc) return rc;
     for (int k = 0, step = 0; k < h->ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, h->ng - k);
-      ELM_LAUNCH(h, launch_potrf_diag(h->S, h->ng, k, nb, h->status, h->st), "potrf");
+      ELM_LAUNCH(h, launch_potrf_diag(h->S, h->ng, k, nb, h->cinv, h->status, h->st), "potrf");
       if (h->chol_rend[step] - k - nb > 0) {
-        ELM_LAUNCH(h, launch_trsm_chol(h->S, h->ng, h->chol_rend[step], k, nb, h->st), "trsm_chol");
+        rc = run_recs(h, h->trsm_recs, h->trsm_first[step],
+                      h->trsm_first[step + 1] - h->trsm_first[step], "trsm_chol");
+        if (rc) return rc;
         rc = run_recs(h, h->syrk_recs, h->syrk_first[step],
                       h->syrk_first[step + 1] - h->syrk_first[step], "gemm_syrk");
         if (rc) return rc;

@@ -9,14 +9,21 @@ namespace {
 
 constexpr int NB = CHOL_NB;
 
-// Unblocked Cholesky of the nb x nb diagonal block at (k, k), in shared memory.
+// Unblocked Cholesky of the nb x nb diagonal block at (k, k), in shared memory, and the
+// inverse of that factor (written column-major to inv, ld NB) so that the panel solve
+// L21 = A21 L11^{-T} is a matrix product.  The inverse comes from L X = I by forward
+// elimination on all columns at once: row k of X is final after division by L_kk and
+// is then eliminated from the rows below.
 __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ S, int ld, int k, int nb,
-                                                    unsigned* status) {
-  __shared__ double a[NB][NB + 1];
+                                                    double* __restrict__ inv, unsigned* status) {
+  extern __shared__ double potrf_smem[];
+  double (*a)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem);
+  double (*x)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem + NB * (NB + 1));
   const int tid = threadIdx.x;
   for (int e = tid; e < nb * nb; e += 256) {
     const int i = e % nb, j = e / nb;
     a[i][j] = (i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : 0.0;
+    x[i][j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
   bool bad = false;
@@ -42,6 +49,22 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ S, int 
     if (i >= j) S[(k + i) + (size_t)(k + j) * ld] = a[i][j];
   }
   if (bad) atomicOr(status, ST_NOT_SPD);
+  if (!inv) return;
+  for (int r = 0; r < nb; ++r) {
+    const double dr = a[r][r];
+    for (int j = tid; j <= r; j += 256) x[r][j] /= dr;
+    __syncthreads();
+    const int w = nb - r - 1;
+    for (int e = tid; e < w * (r + 1); e += 256) {
+      const int i = r + 1 + e % w, j = e / w;
+      x[i][j] = fma(-a[i][r], x[r][j], x[i][j]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < NB * NB; e += 256) {
+    const int i = e % NB, j = e / NB;
+    inv[i + j * NB] = (i < nb && j < nb && i >= j) ? x[i][j] : 0.0;
+  }
 }
 
 // L21 = A21 L11^{-T}: one thread per row below the diagonal block.
@@ -144,9 +167,16 @@ __global__ void __launch_bounds__(256) k_chol_bwd(const double* __restrict__ L, 
 
 }  // namespace
 
-cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, unsigned* status,
+cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, double* inv, unsigned* status,
                               cudaStream_t st) {
-  k_potrf_diag<<<1, 256, 0, st>>>(S, ld, k, nb, status);
+  const int smem = 2 * NB * (NB + 1) * (int)sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_potrf_diag<<<1, 256, smem, st>>>(S, ld, k, nb, inv, status);
   return cudaGetLastError();
 }
 

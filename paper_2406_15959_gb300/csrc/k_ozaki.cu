@@ -212,13 +212,16 @@ __device__ __forceinline__ double pow2i(int k) {
 
 // x * 2^k (x an integer with |x| < 2^53, sign flipped when neg) built from its bit
 // pattern with integer operations only; exact whenever the result is a normal double.
+__device__ __noinline__ double i64_to_double_pow2_slow(long long x, int k, bool neg) {
+  return (neg ? -1.0 : 1.0) * (double)x * pow2i(k);
+}
 __device__ __forceinline__ double i64_to_double_pow2(long long x, int k, bool neg) {
   if (x == 0) return 0.0;
   unsigned long long sgn = (x < 0) != neg ? (1ull << 63) : 0ull;
   const unsigned long long a = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
   const int msb = 63 - __clzll((long long)a);
   const long long e = (long long)msb + k + 1023;
-  if (e <= 0 || e >= 2047) return (neg ? -1.0 : 1.0) * (double)x * pow2i(k);
+  if (e <= 0 || e >= 2047) return i64_to_double_pow2_slow(x, k, neg);  // outside the normal range
   const unsigned long long mant = (a << (52 - msb)) & 0xFFFFFFFFFFFFFull;
   return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | mant));
 }
@@ -502,6 +505,10 @@ __device__ __forceinline__ bool upd_skip(const OzDesc& d, const TileRef& r, int 
   return (flags & GEMM_LOWER) && r.bj * UPD_NT > r.bi * OZ_M + OZ_M - 1;
 }
 
+// Epilogue modes, fixed at compile time so no FP64 compare or select runs per element:
+// EMODE 0: C = s * AB (beta = 0);  1: C = C + s * AB (beta = 1);  2: C = beta C + alpha AB.
+// s = +-1 is applied through the sign bit.  IDENT adds the identity (D = I - Q_G Q_G^T).
+template <int EMODE, bool IDENT>
 __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __restrict__ descs,
                                                              int count, int total_tiles,
                                                              double alpha, double beta, int flags,
@@ -603,7 +610,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
   } else {
     const int ew = warp - 2, quarter = warp & 3, half = ew >> 2;
     const int row = quarter * 32 + lane;
-    const bool neg_alpha = alpha < 0.0, unit_alpha = alpha == 1.0 || alpha == -1.0;
+    const bool neg_alpha = EMODE != 2 && (__double_as_longlong(alpha) < 0);
     int tc = 0;
     // prefetch of this thread's 16 C values of its next tile
     double cv[16];
@@ -612,7 +619,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int gj = r.bj * UPD_NT + half * 16 + j;
-        cv[j] = (beta != 0.0 && gi < d.M && gj < d.N) ? d.C[(size_t)gi * d.c_rs + (size_t)gj * d.c_cs] : 0.0;
+        cv[j] = (EMODE != 0 && gi < d.M && gj < d.N) ? d.C[(size_t)gi * d.c_rs + (size_t)gj * d.c_cs] : 0.0;
       }
     };
     int t = blockIdx.x;
@@ -661,11 +668,13 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
             if (ei != 0 && fj != 0) {
               const int k = ei + fj - 2044 - 64;
               pv = i64_to_double_pow2(H, k + 24, neg_alpha) + i64_to_double_pow2(Lw, k, neg_alpha);
-              if (!unit_alpha) pv *= (neg_alpha ? -alpha : alpha);
             }
-            if ((flags & GEMM_ADD_IDENTITY) && gi == gj) pv += 1.0;
-            d.C[(size_t)gi * d.c_rs + (size_t)gj * d.c_cs] =
-                beta == 0.0 ? pv : (beta == 1.0 ? cv[j] + pv : fma(beta, cv[j], pv));
+            double out;
+            if (EMODE == 0) out = pv;
+            else if (EMODE == 1) out = cv[j] + pv;
+            else out = fma(beta, cv[j], alpha * pv);
+            if (IDENT && gi == gj) out += 1.0;
+            d.C[(size_t)gi * d.c_rs + (size_t)gj * d.c_cs] = out;
           }
         }
       }
@@ -736,12 +745,26 @@ cudaError_t launch_ozaki_upd(const OzDesc* d, int count, int total_tiles, double
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaFuncSetAttribute(k_ozaki_upd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         UPD_SMEM);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, UPD_SMEM);
+    };
+    set((const void*)k_ozaki_upd<0, false>); set((const void*)k_ozaki_upd<0, true>);
+    set((const void*)k_ozaki_upd<1, false>); set((const void*)k_ozaki_upd<1, true>);
+    set((const void*)k_ozaki_upd<2, false>); set((const void*)k_ozaki_upd<2, true>);
     if (e != cudaSuccess) return e;
   }
   const int grid = total_tiles < sms ? total_tiles : sms;
-  k_ozaki_upd<<<grid, UPD_THREADS, UPD_SMEM, st>>>(d, count, total_tiles, alpha, beta, flags, status);
+  const bool unit = alpha == 1.0 || alpha == -1.0;
+  const int mode = (beta == 0.0 && unit) ? 0 : (beta == 1.0 && unit) ? 1 : 2;
+  const bool ident = (flags & GEMM_ADD_IDENTITY) != 0;
+#define ELM_UPD(M, I) \
+  k_ozaki_upd<M, I><<<grid, UPD_THREADS, UPD_SMEM, st>>>(d, count, total_tiles, alpha, beta, flags, status)
+  if (mode == 0) { if (ident) ELM_UPD(0, true); else ELM_UPD(0, false); }
+  else if (mode == 1) { if (ident) ELM_UPD(1, true); else ELM_UPD(1, false); }
+  else { if (ident) ELM_UPD(2, true); else ELM_UPD(2, false); }
+#undef ELM_UPD
   return cudaGetLastError();
 }
 

@@ -12,6 +12,8 @@
 // triangular T with H_1 ... H_nb = I - V T V^T, so Q^T = I - V T^T V^T per panel.
 #include "common.cuh"
 
+#include <cooperative_groups.h>
+
 namespace elmddm {
 
 namespace {
@@ -372,13 +374,171 @@ __global__ void __launch_bounds__(256) k_backsolve(const double* __restrict__ X,
   for (int j = tid; j < n; j += 256) co[j] = v[j];
 }
 
+
+// Cluster variant of the panel factorisation: the 4 CTAs of a cluster share one
+// subdomain's panel, each holding a contiguous quarter of its rows in shared memory.
+// The norm and the 32 dot products of every column are reduced across the cluster
+// through distributed shared memory (fixed summation order, so every CTA computes the
+// identical reflector and T), with two cluster barriers per column.  Same reflectors,
+// T and R as k_panel_qr; 4x the FP64 throughput per subdomain and no L2 round trips.
+constexpr int PCL = 4;     // CTAs per cluster
+constexpr int PLD = 33;    // shared-memory row stride of the panel chunk (doubles)
+
+__global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
+    k_panel_qr_cl(double* __restrict__ K, long long kstride, int ld, const int* __restrict__ ms_arr,
+                  int k0, int nbe, double* __restrict__ tau_out, int n, double* __restrict__ Tout,
+                  long long tstride, double* __restrict__ Vp, long long vstride, unsigned* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
+  const int s = blockIdx.y;
+  double* A = K + (size_t)s * kstride;
+  const int m = ms_arr[s];
+  const int mp = m - k0;
+  const int rows_per = (mp + PCL - 1) / PCL;
+  const int r0 = k0 + q * rows_per;                     // first global row of this chunk
+  const int nr = max(0, min(rows_per, m - r0));         // rows held here
+  extern __shared__ double P[];                         // [rows_per][PLD]
+  __shared__ double red[2][40];                         // [parity]: 0..31 dots, 32 norm, 33 alpha
+  __shared__ double bred[33];
+  __shared__ double wred[8][32];
+  __shared__ double d[32];
+  __shared__ double T[32][33];
+  __shared__ double stau[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < 32 * 33; e += 256) (&T[0][0])[e] = 0.0;
+  for (int k = 0; k < nbe; ++k)
+    for (int r = tid; r < nr; r += 256) P[r * PLD + k] = A[(r0 + r) + (size_t)(k0 + k) * ld];
+  unsigned bits = 0;
+  __syncthreads();
+
+  int par = 0;
+  for (int j = 0; j < nbe; ++j) {
+    const int c = k0 + j;
+    const int cl = c - r0;                   // local row of c (valid if 0 <= cl < nr)
+    const bool own_c = cl >= 0 && cl < nr;
+    const int rs = max(0, c + 1 - r0);       // first local row below the diagonal
+    double p = 0.0;
+    for (int r = rs + tid; r < nr; r += 256) {
+      const double v = P[r * PLD + j];
+      p = fma(v, v, p);
+    }
+    p = block_sum(p, bred);
+    if (tid == 0) {
+      red[par][32] = p;
+      red[par][33] = own_c ? P[cl * PLD + j] : 0.0;
+    }
+    cluster.sync();
+    double ss = 0.0, alpha = 0.0;
+#pragma unroll
+    for (int qq = 0; qq < PCL; ++qq) {
+      const double* rr = cluster.map_shared_rank(&red[par][0], qq);
+      ss += rr[32];
+      alpha += rr[33];
+    }
+    double beta, tau, scal;
+    if (ss == 0.0) {
+      tau = 0.0; beta = alpha; scal = 1.0;
+    } else {
+      beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
+      tau = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    if (tid == 0 && q == 0) {
+      if (beta == 0.0) bits |= ST_RANK;
+      if (!isfinite(beta)) bits |= ST_NONFINITE;
+    }
+    if (ss != 0.0)
+      for (int r = rs + tid; r < nr; r += 256) P[r * PLD + j] *= scal;
+    __syncthreads();
+    double acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+    for (int r = rs + tid; r < nr; r += 256) {
+      const double v = P[r * PLD + j];
+      const double* row = P + r * PLD;
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (k < nbe && k != j) acc[k] = fma(v, row[k], acc[k]);
+    }
+    const double ws = warp_transpose_sum32(acc);
+    wred[warp][lane] = ws;
+    __syncthreads();
+    if (tid < 32) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += wred[w][tid];
+      if (own_c && tid < nbe && tid != j) t += P[cl * PLD + tid];
+      red[par][tid] = t;
+    }
+    cluster.sync();
+    if (tid < 32) {
+      double t = 0.0;
+#pragma unroll
+      for (int qq = 0; qq < PCL; ++qq) t += cluster.map_shared_rank(&red[par][0], qq)[tid];
+      d[tid] = t;
+    }
+    __syncthreads();
+    if (tau != 0.0) {
+      const int ru = max(0, c - r0);
+      for (int r = ru + tid; r < nr; r += 256) {
+        const double tv = tau * ((r0 + r == c) ? 1.0 : P[r * PLD + j]);
+        double* row = P + r * PLD;
+        for (int k = j + 1; k < nbe; ++k) row[k] = fma(-tv, d[k], row[k]);
+      }
+    }
+    if (tid < j) {
+      double t = 0.0;
+      for (int l = tid; l < j; ++l) t = fma(T[tid][l], d[l], t);
+      T[tid][j] = -tau * t;
+    }
+    if (tid == 0) {
+      T[j][j] = tau;
+      stau[j] = tau;
+      if (own_c) P[cl * PLD + j] = beta;
+    }
+    __syncthreads();
+    par ^= 1;
+  }
+
+  for (int k = 0; k < nbe; ++k)
+    for (int r = tid; r < nr; r += 256) A[(r0 + r) + (size_t)(k0 + k) * ld] = P[r * PLD + k];
+  double* V = Vp + (size_t)s * vstride;
+  for (int e = tid; e < nr * nbe; e += 256) {
+    const int r = e % nr, k = e / nr, gr = r0 + r;
+    V[gr + (size_t)k * ld] = gr < k0 + k ? 0.0 : (gr == k0 + k ? 1.0 : P[r * PLD + k]);
+  }
+  if (q == 0) {
+    if (tid < nbe) tau_out[(size_t)s * n + k0 + tid] = stau[tid];
+    double* Ts = Tout + (size_t)s * tstride;
+    for (int e = tid; e < 32 * 32; e += 256) Ts[e] = T[e & 31][e >> 5];
+    if (tid == 0 && bits) atomicOr(status, bits);
+  }
+  cluster.sync();  // peers may still read this CTA's reduction slots
+}
+
 }  // namespace
 
 cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
                             int nbe, double* tau, int n, double* T, long long tstride,
                             double* Vp, long long vstride, unsigned* status, cudaStream_t st) {
-  k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride, Vp, vstride,
-                                status);
+  // the cluster variant keeps a quarter of the rows (up to ld - k0) in shared memory
+  const int rows_per = (ld - k0 + PCL - 1) / PCL;
+  const size_t smem = (size_t)rows_per * PLD * sizeof(double);
+  if (smem <= 180 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_panel_qr_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           180 * 1024);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_panel_qr_cl<<<dim3(PCL, N), 256, smem, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride,
+                                                   Vp, vstride, status);
+  } else {
+    k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride, Vp, vstride,
+                                  status);
+  }
   return cudaGetLastError();
 }
 

@@ -383,8 +383,16 @@ def poisson_16x16_n2000() -> Workload:
                  source="fourier", source_seed=3, modes=4, name="poisson_16x16_n2000")
 
 
+def poisson_4x4_n1000() -> Workload:
+    """4x4 subdomains with the per-subdomain shape of the 8x8 workload (1000 neurons,
+    50x40 interior points, 100 points per edge): a smaller case of the same kernels."""
+    return build(4, 4, 1000, 50, 40, 100, 100, theta="paper", theta_seed=2,
+                 source="fourier", source_seed=2, modes=4, name="poisson_4x4_n1000")
+
+
 WORKLOADS = {
     "poisson_2x2_n200": poisson_2x2_n200,
+    "poisson_4x4_n1000": poisson_4x4_n1000,
     "poisson_8x8_n1000": poisson_8x8_n1000,
     "poisson_16x16_n2000": poisson_16x16_n2000,
 }
