@@ -108,11 +108,14 @@ cudaError_t launch_backsolve(const double* X, const double* K, long long kstride
 cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, double* inv, unsigned* status,
                               cudaStream_t st);
 cudaError_t launch_trsm_chol(double* S, int ld, int n, int k, int nb, cudaStream_t st);
-// row_end < 0 means n; j_begin 0 means all rows above the block.
+// row_end < 0 means n; j_begin 0 means all rows above the block; Linv (nullable) is the
+// inverse of the diagonal block (CHOL_NB x CHOL_NB, column-major) when it is stored.
 cudaError_t launch_chol_fwd(const double* L, int ld, int n, int k, int nb, double* r,
-                            double* y, int nrhs, cudaStream_t st, int row_end = -1);
+                            double* y, int nrhs, cudaStream_t st, int row_end = -1,
+                            const double* Linv = nullptr);
 cudaError_t launch_chol_bwd(const double* L, int ld, int n, int k, int nb, double* y,
-                            double* u, int nrhs, cudaStream_t st, int j_begin = 0);
+                            double* u, int nrhs, cudaStream_t st, int j_begin = 0,
+                            const double* Linv = nullptr);
 cudaError_t launch_gather_perm(const int* idx, int n, const double* src, double* dst, int nrhs,
                                cudaStream_t st);
 

@@ -109,7 +109,7 @@ struct elm_ddm_handle {
   double *K = nullptr, *Am = nullptr, *tau = nullptr, *T = nullptr, *Vp = nullptr;
   double *W1 = nullptr, *W2 = nullptr, *D = nullptr, *M = nullptr, *S = nullptr;
   double *Mdiag = nullptr, *thW = nullptr, *thb = nullptr, *xy = nullptr, *nrm = nullptr;
-  double* cinv = nullptr;             // inverse of the current Cholesky diagonal block
+  double* cinv = nullptr;             // inverses of the Cholesky diagonal blocks, one per step
   std::vector<LaunchRec> trsm_recs;   // per Cholesky step: L21 = A21 L11^{-T} as a product
   std::vector<int> trsm_first;
   double *X = nullptr, *gq = nullptr, *hq = nullptr, *zv = nullptr;
@@ -446,7 +446,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->cnt, (size_t)N * 3) && dev_alloc(h, &h->ms, (size_t)N) &&
             dev_alloc(h, &h->mg, (size_t)N) && dev_alloc(h, &h->dofmap, (size_t)ng * 4) &&
             dev_alloc(h, &h->ifc_dof, (size_t)N * h->mgld) && dev_alloc(h, &h->perm, (size_t)ng) &&
-            dev_alloc(h, &h->cinv, (size_t)CHOL_NB * CHOL_NB) &&
+            dev_alloc(h, &h->cinv, (size_t)((ng + CHOL_NB - 1) / CHOL_NB + 1) * CHOL_NB * CHOL_NB) &&
             dev_alloc(h, &h->status, 1);
   if (!ok) {
     free_all(h);
@@ -730,8 +730,9 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       double* L21 = h->S + (k + nb) + (size_t)k * ng;
       // panel solve as an in-place product: every 64-wide tile reads all of its rows of
       // A21 before writing them, and the tiles never share rows
-      add_gemm_rec(h->trsm_recs, {{L21, h->cinv, L21, rest, nb, nb, ng, CHOL_NB, ng}}, false, true,
-                   1.0, 0.0, 0);
+      add_gemm_rec(h->trsm_recs,
+                   {{L21, h->cinv + (size_t)step * CHOL_NB * CHOL_NB, L21, rest, nb, nb, ng, CHOL_NB, ng}},
+                   false, true, 1.0, 0.0, 0);
       h->trsm_recs.back().name = "trsm_chol";
       double* S22 = h->S + (k + nb) + (size_t)(k + nb) * ng;
       if (h->emulated) {
@@ -826,7 +827,8 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     if (rc) return rc;
     for (int k = 0, step = 0; k < h->ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, h->ng - k);
-      ELM_LAUNCH(h, launch_potrf_diag(h->S, h->ng, k, nb, h->cinv, h->status, h->st), "potrf");
+      ELM_LAUNCH(h, launch_potrf_diag(h->S, h->ng, k, nb, h->cinv + (size_t)step * CHOL_NB * CHOL_NB,
+                                      h->status, h->st), "potrf");
       if (h->chol_rend[step] - k - nb > 0) {
         rc = run_recs(h, h->trsm_recs, h->trsm_first[step],
                       h->trsm_first[step + 1] - h->trsm_first[step], "trsm_chol");
@@ -862,12 +864,15 @@ int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
     for (int k = 0, step = 0; k < ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, ng - k);
       ELM_LAUNCH(h, launch_chol_fwd(h->S, ng, ng, k, nb, h->rv, h->yv, nrhs, h->st,
-                                    h->chol_rend[step]), "chol_fwd");
+                                    h->chol_rend[step], h->cinv + (size_t)step * CHOL_NB * CHOL_NB),
+                 "chol_fwd");
     }
     for (int k = ((ng - 1) / CHOL_NB) * CHOL_NB; k >= 0; k -= CHOL_NB) {
       const int nb = std::min(CHOL_NB, ng - k);
       ELM_LAUNCH(h, launch_chol_bwd(h->S, ng, ng, k, nb, h->yv, h->uv, nrhs, h->st,
-                                    h->chol_jbeg[k / CHOL_NB]), "chol_bwd");
+                                    h->chol_jbeg[k / CHOL_NB],
+                                    h->cinv + (size_t)(k / CHOL_NB) * CHOL_NB * CHOL_NB),
+                 "chol_bwd");
     }
   }
   ELM_LAUNCH(h, launch_backsolve(h->X, h->K, h->kstride, h->ld, h->mg, h->ifc_dof, h->mgld,

@@ -19,7 +19,8 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ S, int 
   extern __shared__ double potrf_smem[];
   double (*a)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem);
   double (*x)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem + NB * (NB + 1));
-  const int tid = threadIdx.x;
+  __shared__ double rdiag[NB];  // reciprocal pivots
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int e = tid; e < nb * nb; e += 256) {
     const int i = e % nb, j = e / nb;
     a[i][j] = (i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : 0.0;
@@ -31,16 +32,18 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ S, int 
     if (tid == 0) {
       double dj = a[j][j];
       if (!(dj > 0.0) || !isfinite(dj)) { bad = true; dj = 1.0; }
-      a[j][j] = sqrt(dj);
+      const double pv = sqrt(dj);
+      a[j][j] = pv;
+      rdiag[j] = 1.0 / pv;
     }
     __syncthreads();
-    const double piv = a[j][j];
-    for (int i = j + 1 + tid; i < nb; i += 256) a[i][j] /= piv;
+    const double rp = rdiag[j];
+    for (int i = j + 1 + tid; i < nb; i += 256) a[i][j] *= rp;
     __syncthreads();
-    const int w = nb - j - 1;
-    for (int e = tid; e < w * w; e += 256) {
-      const int ii = j + 1 + e % w, kk = j + 1 + e / w;
-      if (kk <= ii) a[ii][kk] = fma(-a[ii][j], a[kk][j], a[ii][kk]);
+    // trailing update of the lower triangle, 16 x 16 thread grid, no index division
+    for (int ii = j + 1 + ty; ii < nb; ii += 16) {
+      const double lij = a[ii][j];
+      for (int kk = j + 1 + tx; kk <= ii; kk += 16) a[ii][kk] = fma(-lij, a[kk][j], a[ii][kk]);
     }
     __syncthreads();
   }
@@ -50,14 +53,14 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ S, int 
   }
   if (bad) atomicOr(status, ST_NOT_SPD);
   if (!inv) return;
+  // L X = I: row r of X is final after scaling by 1/L_rr, then eliminated from rows below
   for (int r = 0; r < nb; ++r) {
-    const double dr = a[r][r];
-    for (int j = tid; j <= r; j += 256) x[r][j] /= dr;
+    const double dr = rdiag[r];
+    for (int j = tid; j <= r; j += 256) x[r][j] *= dr;
     __syncthreads();
-    const int w = nb - r - 1;
-    for (int e = tid; e < w * (r + 1); e += 256) {
-      const int i = r + 1 + e % w, j = e / w;
-      x[i][j] = fma(-a[i][r], x[r][j], x[i][j]);
+    for (int i = r + 1 + ty; i < nb; i += 16) {
+      const double lir = a[i][r];
+      for (int j = tx; j <= r; j += 16) x[i][j] = fma(-lir, x[r][j], x[i][j]);
     }
     __syncthreads();
   }
@@ -90,29 +93,41 @@ __global__ void __launch_bounds__(64) k_trsm_chol(double* __restrict__ S, int ld
     for (int j = 0; j < nb; ++j) S[i + (size_t)(k + j) * ld] = X[tid][j];
 }
 
-// Forward substitution step for block k: y_k = L_kk^{-1} r_k, r_i -= L_ik y_k for the
-// rows k+nb <= i < row_end that can hold nonzeros of the block column (the envelope).
-// Every block solves the small triangle itself, so one launch covers the step.
+// Forward substitution step for block k: y_k = L_kk^{-1} r_k with the stored inverse of
+// the diagonal block (a 64 x 64 matrix-vector product, no division chain), then
+// r_i -= L_ik y_k for the rows k+nb <= i < row_end that can hold nonzeros of the block
+// column (the envelope).  Every block forms y_k itself, so one launch covers the step;
+// when Linv is NULL the small triangle is solved by substitution instead.
 __global__ void __launch_bounds__(256) k_chol_fwd(const double* __restrict__ L, int ld, int n, int k,
-                                                  int nb, int row_end, double* __restrict__ r,
-                                                  double* __restrict__ y) {
+                                                  int nb, int row_end, const double* __restrict__ Linv,
+                                                  double* __restrict__ r, double* __restrict__ y) {
   __shared__ double Ls[NB][NB + 1];
-  __shared__ double ys[NB];
+  __shared__ double rs[NB], ys[NB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* rr = r + (size_t)blockIdx.y * n;
   double* yy = y + (size_t)blockIdx.y * n;
+  const double* src = Linv ? Linv : L;
+  const int lds = Linv ? NB : ld;
+  const int off = Linv ? 0 : k;
   for (int e = tid; e < nb * nb; e += 256) {
     const int i = e % nb, j = e / nb;
-    Ls[i][j] = (i >= j) ? L[(k + i) + (size_t)(k + j) * ld] : 0.0;
+    Ls[i][j] = (i >= j) ? src[(off + i) + (size_t)(off + j) * lds] : 0.0;
   }
-  if (tid < nb) ys[tid] = rr[k + tid];
+  if (tid < nb) rs[tid] = rr[k + tid];
   __syncthreads();
-  if (warp == 0) {
+  if (Linv) {
+    for (int i = warp; i < nb; i += 8) {
+      double p = 0.0;
+      for (int l = lane; l <= i; l += 32) p = fma(Ls[i][l], rs[l], p);
+      p = warp_sum(p);
+      if (lane == 0) ys[i] = p;
+    }
+  } else if (warp == 0) {
     for (int i = 0; i < nb; ++i) {
       double p = 0.0;
       for (int l = lane; l < i; l += 32) p = fma(Ls[i][l], ys[l], p);
       p = warp_sum(p);
-      const double yi = (ys[i] - p) / Ls[i][i];
+      const double yi = (rs[i] - p) / Ls[i][i];
       __syncwarp();
       if (lane == 0) ys[i] = yi;
       __syncwarp();
@@ -128,28 +143,40 @@ __global__ void __launch_bounds__(256) k_chol_fwd(const double* __restrict__ L, 
   }
 }
 
-// Backward substitution step for block k: u_k = L_kk^{-T} y_k, y_j -= L_k,j^T u_k for
-// j_begin <= j < k (L_k,j is zero left of the envelope's first column j_begin).
+// Backward substitution step for block k: u_k = L_kk^{-T} y_k (with the stored inverse
+// when given), y_j -= L_k,j^T u_k for j_begin <= j < k (L_k,j is zero left of the
+// envelope's first column j_begin).
 __global__ void __launch_bounds__(256) k_chol_bwd(const double* __restrict__ L, int ld, int n, int k,
-                                                  int nb, int j_begin, double* __restrict__ y,
-                                                  double* __restrict__ u) {
+                                                  int nb, int j_begin, const double* __restrict__ Linv,
+                                                  double* __restrict__ y, double* __restrict__ u) {
   __shared__ double Ls[NB][NB + 1];
-  __shared__ double us[NB];
+  __shared__ double ysh[NB], us[NB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* yy = y + (size_t)blockIdx.y * n;
   double* uu = u + (size_t)blockIdx.y * n;
+  const double* src = Linv ? Linv : L;
+  const int lds = Linv ? NB : ld;
+  const int off = Linv ? 0 : k;
   for (int e = tid; e < nb * nb; e += 256) {
     const int i = e % nb, j = e / nb;
-    Ls[i][j] = (i >= j) ? L[(k + i) + (size_t)(k + j) * ld] : 0.0;
+    Ls[i][j] = (i >= j) ? src[(off + i) + (size_t)(off + j) * lds] : 0.0;
   }
-  if (tid < nb) us[tid] = yy[k + tid];
+  if (tid < nb) ysh[tid] = yy[k + tid];
   __syncthreads();
-  if (warp == 0) {
+  if (Linv) {
+    // u = Linv^T y: u_i = sum_{l >= i} Linv[l][i] y_l
+    for (int i = warp; i < nb; i += 8) {
+      double p = 0.0;
+      for (int l = i + lane; l < nb; l += 32) p = fma(Ls[l][i], ysh[l], p);
+      p = warp_sum(p);
+      if (lane == 0) us[i] = p;
+    }
+  } else if (warp == 0) {
     for (int i = nb - 1; i >= 0; --i) {
       double p = 0.0;
       for (int l = i + 1 + lane; l < nb; l += 32) p = fma(Ls[l][i], us[l], p);
       p = warp_sum(p);
-      const double ui = (us[i] - p) / Ls[i][i];
+      const double ui = (ysh[i] - p) / Ls[i][i];
       __syncwarp();
       if (lane == 0) us[i] = ui;
       __syncwarp();
@@ -195,21 +222,21 @@ cudaError_t launch_trsm_chol(double* S, int ld, int n, int k, int nb, cudaStream
 }
 
 cudaError_t launch_chol_fwd(const double* L, int ld, int n, int k, int nb, double* r,
-                            double* y, int nrhs, cudaStream_t st, int row_end) {
+                            double* y, int nrhs, cudaStream_t st, int row_end, const double* Linv) {
   if (row_end < 0 || row_end > n) row_end = n;
   const int rows = row_end - k - nb;
   const int gx = rows > 0 ? (rows + 255) / 256 : 1;
-  k_chol_fwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, row_end, r, y);
+  k_chol_fwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, row_end, Linv, r, y);
   return cudaGetLastError();
 }
 
 cudaError_t launch_chol_bwd(const double* L, int ld, int n, int k, int nb, double* y,
-                            double* u, int nrhs, cudaStream_t st, int j_begin) {
+                            double* u, int nrhs, cudaStream_t st, int j_begin, const double* Linv) {
   if (j_begin < 0 || j_begin > k) j_begin = 0;
   int gx = (k - j_begin + 7) / 8;
   if (gx < 1) gx = 1;
   if (gx > 1024) gx = 1024;
-  k_chol_bwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, j_begin, y, u);
+  k_chol_bwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, j_begin, Linv, y, u);
   return cudaGetLastError();
 }
 

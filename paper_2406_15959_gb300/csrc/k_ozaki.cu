@@ -472,10 +472,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
 // Cholesky SYRK).  One CTA per SM walks the 128 x 32 tiles of the whole batch; two
 // shared-memory stages and two TMEM accumulator sets (7 x 32 columns each) let the loads
 // and MMAs of the next tile run while eight epilogue warps finish the current one.
-// Warp roles: 0 producer, 1 MMA (and TMEM owner), 2..9 epilogue (warp w drains TMEM lane
-// quarter w % 4, columns 16 * ((w - 2) / 4) .. +15).
+// Warp roles: 0 producer, 1 MMA (and TMEM owner), 2..17 epilogue (warp w drains TMEM lane
+// quarter w % 4, columns 8 * ((w - 2) / 4) .. +7); four epilogue warps per SM sub-partition
+// hide the latency of the per-element integer work and of the C traffic.
 constexpr int UPD_NT = 32;
-constexpr int UPD_THREADS = 320;
+constexpr int UPD_EPI_WARPS = 16;
+constexpr int UPD_COLS = UPD_NT / (UPD_EPI_WARPS / 4);   // columns per epilogue thread
+constexpr int UPD_THREADS = 32 * (2 + UPD_EPI_WARPS);
 constexpr int UPD_A = OZ_S * OZ_M * OZ_KC * 2;       // 57344 B
 constexpr int UPD_B = OZ_S * UPD_NT * OZ_KC * 2;     // 14336 B
 constexpr int UPD_STAGE = UPD_A + UPD_B;
@@ -527,7 +530,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
       mbar_init(FULL + 8 * i, 1);
       mbar_init(EMPTY + 8 * i, 1);
       mbar_init(TFULL + 8 * i, 1);
-      mbar_init(TEMPTY + 8 * i, 256);
+      mbar_init(TEMPTY + 8 * i, 32 * UPD_EPI_WARPS);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -608,23 +611,21 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
       }
     }
   } else {
-    const int ew = warp - 2, quarter = warp & 3, half = ew >> 2;
+    const int ew = warp - 2, quarter = warp & 3, part = ew >> 2;
     const int row = quarter * 32 + lane;
+    const int col0 = part * UPD_COLS;
     const bool neg_alpha = EMODE != 2 && (__double_as_longlong(alpha) < 0);
     int tc = 0;
-    // prefetch of this thread's 16 C values of its next tile
-    double cv[16];
+    double cv[UPD_COLS];  // this thread's C values of its next tile, loaded ahead
     auto fetch = [&](const OzDesc& d, const TileRef& r) {
-      const int gi = r.bi * OZ_M + row;
+      const int gi = r.bi * OZ_M + row, gj0 = r.bj * UPD_NT + col0;
+      const double* cp = d.C + (size_t)gi * d.c_rs + (size_t)gj0 * d.c_cs;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int gj = r.bj * UPD_NT + half * 16 + j;
-        cv[j] = (EMODE != 0 && gi < d.M && gj < d.N) ? d.C[(size_t)gi * d.c_rs + (size_t)gj * d.c_cs] : 0.0;
-      }
+      for (int j = 0; j < UPD_COLS; ++j)
+        cv[j] = (EMODE != 0 && gi < d.M && gj0 + j < d.N) ? cp[(size_t)j * d.c_cs] : 0.0;
     };
     int t = blockIdx.x;
-    // first non-skipped tile
-    while (t < total_tiles) {
+    while (t < total_tiles) {  // first tile of this CTA that is not skipped
       const TileRef r = upd_tile(descs, count, t);
       if (!upd_skip(descs[r.e], r, flags)) break;
       t += gridDim.x;
@@ -639,31 +640,29 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
       const int buf = tc & 1;
       if (!mbar_wait_warp(TFULL + 8 * buf, (tc >> 1) & 1)) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      uint32_t v[OZ_G][2][8];
-      const uint32_t lb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (OZ_G * UPD_NT) + half * 16;
+      uint32_t v[OZ_G][8];
+      const uint32_t lb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (OZ_G * UPD_NT) + col0;
 #pragma unroll
-      for (int g = 0; g < OZ_G; ++g) {
-        tmem_ld8(lb + g * UPD_NT, v[g][0]);
-        tmem_ld8(lb + g * UPD_NT + 8, v[g][1]);
-      }
+      for (int g = 0; g < OZ_G; ++g) tmem_ld8(lb + g * UPD_NT, v[g]);
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       asm volatile("tcgen05.fence::before_thread_sync;");
       mbar_arrive(TEMPTY + 8 * buf);  // accumulators copied: the MMA may reuse this buffer
       ++tc;
-      const int gi = r.bi * OZ_M + row;
+      const int gi = r.bi * OZ_M + row, gj0 = r.bj * UPD_NT + col0;
       if (gi < d.M) {
         const int ei = d.Ae[gi];
+        double* cp = d.C + (size_t)gi * d.c_rs + (size_t)gj0 * d.c_cs;
+        const int* be = d.Be + gj0;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int gj = r.bj * UPD_NT + half * 16 + j;
-          if (gj < d.N) {
+        for (int j = 0; j < UPD_COLS; ++j) {
+          if (gj0 + j < d.N) {
             int a[OZ_G];
 #pragma unroll
-            for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][j >> 3][j & 7]));
+            for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][j]));
             const long long H = ((long long)a[0] << 24) + ((long long)a[1] << 16) + ((long long)a[2] << 8);
             const long long Lw =
                 ((long long)a[3] << 24) + ((long long)a[4] << 16) + ((long long)a[5] << 8) + a[6];
-            const int fj = d.Be[gj];
+            const int fj = be[j];
             double pv = 0.0;
             if (ei != 0 && fj != 0) {
               const int k = ei + fj - 2044 - 64;
@@ -673,13 +672,12 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
             if (EMODE == 0) out = pv;
             else if (EMODE == 1) out = cv[j] + pv;
             else out = fma(beta, cv[j], alpha * pv);
-            if (IDENT && gi == gj) out += 1.0;
-            d.C[(size_t)gi * d.c_rs + (size_t)gj * d.c_cs] = out;
+            if (IDENT && gi == gj0 + j) out += 1.0;
+            cp[(size_t)j * d.c_cs] = out;
           }
         }
       }
-      // next tile of this CTA; its C values load while its MMAs run
-      int tn = t + gridDim.x;
+      int tn = t + gridDim.x;  // next tile of this CTA; its C values load while its MMAs run
       while (tn < total_tiles) {
         const TileRef rn = upd_tile(descs, count, tn);
         if (!upd_skip(descs[rn.e], rn, flags)) break;
