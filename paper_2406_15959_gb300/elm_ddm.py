@@ -255,3 +255,42 @@ def run_workload(w, device="cuda", max_rhs=1):
     s.check()
     out = {"u_gamma": ug, "c": c, "u": u, "grad": g, "solver": s}
     return out
+
+
+def _main(argv=None):
+    """python -m paper_2406_15959_gb300.elm_ddm WORKLOAD [SOLVES] [--fp64-simt]
+
+    Runs SOLVES full solves (setup once, then assemble + schur + solve + eval) of a named
+    workload from workload.WORKLOADS on cuda:0 and prints the time of the last one."""
+    import sys
+    import time
+    import torch
+    from . import workload as wl
+    args = list(sys.argv[1:] if argv is None else argv)
+    simt = "--fp64-simt" in args
+    args = [a for a in args if a != "--fp64-simt"]
+    name = args[0] if args else "poisson_2x2_n200"
+    count = int(args[1]) if len(args) > 1 else 1
+    w = wl.WORKLOADS[name]()
+    dev = torch.device("cuda:0")
+    s = Solver(w.geom, w.n_neurons, fp64_simt=simt)
+    W = torch.as_tensor(w.W, device=dev)
+    b = torch.as_tensor(w.b, device=dev)
+    rhs = torch.as_tensor(w.rhs, device=dev)
+    txy = torch.as_tensor(w.test_xy, device=dev)
+    own = torch.as_tensor(w.test_owner, device=dev, dtype=torch.int32)
+    for _ in range(count):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s.assemble(W, b)
+        s.schur()
+        _, c = s.solve(rhs)
+        u, _ = s.eval(txy, own, c)
+        s.check()
+        dt = time.perf_counter() - t0
+    print(f"{name}: {count} solve(s), last {1e3 * dt:.2f} ms, u[0] = {float(u[0]):.12e}")
+    s.close()
+
+
+if __name__ == "__main__":
+    _main()
