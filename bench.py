@@ -36,7 +36,7 @@ WORKLOAD = "poisson_8x8_n1000"
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 KERNEL_OF_CLASS = {
     "oz_qr_update": "k_ozaki_upd (persistent tensor-core FP64 product: A2 -= V W2 of every QR panel)",
-    "oz_qr_w": "k_ozaki<32> (tensor-core FP64 product: W1^T = A2^T V of every QR panel)",
+    "oz_qr_w": "k_ozaki_fa (tensor-core FP64 product with fused digit split: W1^T = A2^T V of every QR panel)",
     "oz_syrk": "k_ozaki_upd (persistent tensor-core FP64 product: Schur Cholesky SYRK)",
     "split_qr_w": "k_rowexp + k_split (digit split of A2^T and V^T)",
     "split_qr_update": "k_rowexp + k_split (digit split of V and W2^T)",

@@ -38,6 +38,7 @@ struct AddDesc {
 // Digit split of one FP64 operand (k_ozaki.cu): the logical R x K matrix with element
 // (r, k) at X[r * rs + k * ks] becomes 7 BF16 digit planes in row tiles of row_tile rows
 // (128 for the A side, the GEMM's NT for the B side); E receives per-row exponent bounds.
+// tiles == nullptr: row exponents only (the operand is split inside the product kernel).
 struct SplitDesc {
   const double* X;
   long long rs, ks;
@@ -56,6 +57,7 @@ struct OzDesc {
   long long c_rs, c_cs;
   int M, N, K;
   int tile0;  // persistent launches: index of this entry's first 128 x 32 tile in the batch
+  long long a_rs;  // fused-split launches: At is the FP64 A, element (i, k) at At[i * a_rs + k]
 };
 
 // ---- launchers (return cudaGetLastError after the launch) ----
@@ -69,6 +71,10 @@ cudaError_t launch_ozaki(int nt, const OzDesc* d, int count, int max_tiles, doub
 // entries carry their first tile index in tile0, total_tiles = tiles of the whole batch).
 cudaError_t launch_ozaki_upd(const OzDesc* d, int count, int total_tiles, double alpha,
                              double beta, int flags, unsigned* status, cudaStream_t st);
+// C = A B^T with the FP64 A split inside the kernel (At = FP64 A, a_rs its row stride, K
+// contiguous; Ae its row exponents), B split as usual with row_tile 32, N <= 32, beta = 0.
+cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned* status,
+                            cudaStream_t st);
 cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_tiles,
                         double alpha, double beta, int flags, cudaStream_t st);
 cudaError_t launch_add_blocks(const AddDesc* d, int count, int max_elems, cudaStream_t st);

@@ -20,7 +20,8 @@ namespace {
 
 struct LaunchRec {
   int kind;  // 0 = FP64 gemm, 1 = add_blocks, 2 = digit split, 3 = tensor-core digit GEMM,
-             // 4 = persistent tensor-core digit GEMM for K <= 64 (max_tiles = total tiles)
+             // 4 = persistent tensor-core digit GEMM for K <= 64 (max_tiles = total tiles),
+             // 5 = tensor-core digit GEMM with the FP64 A operand split in the kernel
   int off, count, max_tiles;  // split: max_tiles = blocks of k_split, nt = max rows
   bool ta, tb;
   double alpha, beta;
@@ -245,9 +246,12 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
     else if (L.kind == 3)
       ELM_LAUNCH_FB(h, launch_ozaki(L.nt, h->od + L.off, L.count, L.max_tiles, L.alpha, L.beta,
                                     L.flags, h->status, h->st), nm, L.flops, L.bytes);
-    else
+    else if (L.kind == 4)
       ELM_LAUNCH_FB(h, launch_ozaki_upd(h->od + L.off, L.count, L.max_tiles, L.alpha, L.beta,
                                         L.flags, h->status, h->st), nm, L.flops, L.bytes);
+    else
+      ELM_LAUNCH_FB(h, launch_ozaki_fa(h->od + L.off, L.count, L.max_tiles, h->status, h->st), nm,
+                    L.flops, L.bytes);
   }
   return ELM_DDM_OK;
 }
@@ -461,7 +465,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   for (int k = 0, st = 0; k < ng; k += CHOL_NB, ++st)
     restmax = std::max(restmax, h->chol_rend[st] - k - std::min(CHOL_NB, ng - k));
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t s1 = al(oz_split_elems(n2max, mpmax, 128) * 2), e1 = al((size_t)n2max * 4);
+  // (A2^T is split inside the fused product kernel: only its row exponents are stored)
+  const size_t s1 = 0, e1 = al((size_t)n2max * 4);
   const size_t s2 = al(oz_split_elems(QR_NB, mpmax, 32) * 2), e2 = al((size_t)QR_NB * 4);
   const size_t s3 = al(oz_split_elems(mpmax, QR_NB, 128) * 2), e3 = al((size_t)mpmax * 4);
   const size_t s4 = al(oz_split_elems(n2max, QR_NB, 32) * 2), e4 = al((size_t)n2max * 4);
@@ -548,8 +553,12 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       if (d.R <= 0 || d.K <= 0) continue;
       sds.push_back(d);
       L.count++;
-      L.bytes += (8.0 + 2.0 * 7) * d.R * d.K;  // FP64 read once, 7 BF16 digit planes written
       L.nt = std::max(L.nt, d.R);
+      if (!d.tiles) {  // row exponents only
+        L.bytes += 8.0 * d.R * d.K;
+        continue;
+      }
+      L.bytes += (8.0 + 2.0 * 7) * d.R * d.K;  // FP64 read once, 7 BF16 digit planes written
       L.max_tiles = std::max(L.max_tiles, (d.R + d.row_tile - 1) / d.row_tile * ((d.K + 31) / 32));
     }
     recs.push_back(L);
@@ -577,6 +586,20 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
     recs.push_back(L);
   };
+  // C = A B^T with A = FP64 operand split inside the kernel (N <= 32, beta = 0)
+  auto add_fa_rec = [&](std::vector<LaunchRec>& recs, const std::vector<OzDesc>& batch, const char* name) {
+    LaunchRec L{5, (int)ods.size(), 0, 0, false, false, 1.0, 0.0, 0, 0.0, 0};
+    L.name = name;
+    for (const OzDesc& d : batch) {
+      if (d.M <= 0 || d.N <= 0) continue;
+      ods.push_back(d);
+      L.count++;
+      L.max_tiles = std::max(L.max_tiles, (d.M + 127) / 128);
+      L.flops += 2.0 * d.M * d.N * d.K;
+      L.bytes += 8.0 * ((double)d.M * d.K + (double)d.N * d.K + (double)d.M * d.N);
+    }
+    recs.push_back(L);
+  };
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, n - k0);
     std::vector<GemmDesc> g1, g2, g3;
@@ -599,9 +622,10 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
         void* t2 = sub_region(s, 2); int* x2 = (int*)sub_region(s, 3);
         void* t3 = sub_region(s, 4); int* x3 = (int*)sub_region(s, 5);
         void* t4 = sub_region(s, 6); int* x4 = (int*)sub_region(s, 7);
-        sp1.push_back({A2, ld, 1, n2, mp, x1, t1, 128});     // A2^T: rows = trailing columns
-        sp1.push_back({V, ld, 1, nbe, mp, x2, t2, 32});      // V^T: rows = panel columns
-        o1.push_back({t1, x1, t2, x2, w1, QR_NB, 1, n2, nbe, mp, 0});
+        (void)t1;
+        sp1.push_back({A2, ld, 1, n2, mp, x1, nullptr, 128});  // A2^T: row exponents only
+        sp1.push_back({V, ld, 1, nbe, mp, x2, t2, 32});        // V^T: rows = panel columns
+        o1.push_back({A2, x1, t2, x2, w1, QR_NB, 1, n2, nbe, mp, 0, ld});
         sp3.push_back({V, 1, ld, mp, nbe, x3, t3, 128});     // V: rows = matrix rows
         sp3.push_back({w2, QR_NB, 1, n2, nbe, x4, t4, 32});  // W2^T: rows = trailing columns
         o3.push_back({t3, x3, t4, x4, A2, 1, ld, mp, n2, nbe, 0});
@@ -610,7 +634,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     h->qr_first.push_back((int)h->qr_recs.size());
     if (h->emulated) {
       add_split_rec(h->qr_recs, sp1, "split_qr_w");
-      add_oz_rec(h->qr_recs, o1, 32, 1.0, 0.0, 0, "oz_qr_w");
+      add_fa_rec(h->qr_recs, o1, "oz_qr_w");
       add_gemm_rec(h->qr_recs, g2, true, false, 1.0, 0.0, 0);
       h->qr_recs.back().name = "gemm_qr_t";
       add_split_rec(h->qr_recs, sp3, "split_qr_update");

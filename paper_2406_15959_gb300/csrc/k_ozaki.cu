@@ -113,6 +113,12 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr));
+}
+
 // Element offset of (r, k) inside an R x 32 tile in the canonical K-major layout
 // [r/8][k/8][r%8][k%8].
 __device__ __forceinline__ int tile_off32(int r, int k) {
@@ -123,31 +129,49 @@ __device__ __forceinline__ unsigned biased_exp(double x) {
   return (unsigned)((__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-// Balanced base-256 digits of x relative to the row bound 2^(emax-1022).
-__device__ __forceinline__ void digits7(double x, unsigned emax, int (&d)[OZ_S]) {
+// Fixed-point image of x relative to the row bound 2^(emax-1022): the signed integer
+// F = round_toward_zero(x * 2^(1078 - emax)), |F| < 2^56 (zero for x = 0, for subnormal
+// x and for an all-zero row).
+__device__ __forceinline__ long long fixed56(double x, unsigned emax) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((bits >> 52) & 0x7FF);
-#pragma unroll
-  for (int p = 0; p < OZ_S; ++p) d[p] = 0;
-  if (e == 0 || emax == 0) return;  // zero (subnormals are below the digits' reach)
+  if (e == 0 || emax == 0) return 0;
   const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
   const int shift = (int)emax - e - 3;  // >= -3 because e <= emax
-  unsigned long long F;
-  if (shift >= 64) F = 0;
-  else if (shift >= 0) F = M >> shift;
-  else F = M << (-shift);
-  int carry = 0;
+  const unsigned long long F = shift >= 64 ? 0ull : shift >= 0 ? M >> shift : M << (-shift);
+  return (bits >> 63) ? -(long long)F : (long long)F;
+}
+
+// Balanced base-256 digits of F = sum_p d_p 256^(7-p), p = 1..7, d_p in [-128, 127] for
+// p >= 2, without a carry chain: adding 128 to each of the six low byte positions makes
+// every low byte of F + C equal d_p + 128, and the bits above them equal d_1.  Each digit
+// becomes a BF16 through a float magic-number add (1.5 * 2^23 + b has the integer b in its
+// low mantissa bits; subtracting the constant back is exact), and two BF16 values are
+// packed by a byte permute of the floats' upper halves.  Returns the 7 planes' words for
+// 8 consecutive k (w[p][j] holds k = 2j, 2j+1).
+__device__ __forceinline__ void split8(const double (&x)[8], unsigned emax, uint32_t (&w)[OZ_S][4]) {
+  constexpr unsigned long long kBias = 0x0000808080808080ull;
+  float f[OZ_S][8];
 #pragma unroll
-  for (int p = OZ_S - 1; p >= 1; --p) {
-    int t = (int)((F >> (56 - 8 * (p + 1))) & 0xFF) + carry;
-    carry = t >= 128;
-    d[p] = t - (carry << 8);
-  }
-  d[0] = (int)((F >> 48) & 0xFF) + carry;
-  if (bits >> 63) {
+  for (int j = 0; j < 8; ++j) {
+    const unsigned long long Fp = (unsigned long long)fixed56(x[j], emax) + kBias;
+    const uint32_t lo = (uint32_t)Fp, hi = (uint32_t)(Fp >> 32);
+    const int d1 = (int)((long long)Fp >> 48);
+    f[0][j] = __int_as_float(0x4B400000 + d1) - 12582912.0f;
+    // low bytes of Fp: digit p (p = 2..7) sits in byte 7 - p
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p) d[p] = -d[p];
+    for (int p = 2; p <= OZ_S; ++p) {
+      const int byte = 7 - p;
+      const uint32_t src = byte >= 4 ? hi : lo;
+      const uint32_t b = __byte_perm(src, 0x4B400000u, 0x7650 | (byte & 3));
+      f[p - 1][j] = __uint_as_float(b) - 12583040.0f;  // (1.5 * 2^23 + b) - (1.5 * 2^23 + 128)
+    }
   }
+#pragma unroll
+  for (int p = 0; p < OZ_S; ++p)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      w[p][j] = __byte_perm(__float_as_uint(f[p][2 * j]), __float_as_uint(f[p][2 * j + 1]), 0x7632);
 }
 
 // Warp per row: E[r] = largest biased exponent in row r (0 for an all-zero row).
@@ -164,9 +188,11 @@ __global__ void __launch_bounds__(256) k_rowexp(const SplitDesc* __restrict__ de
   if (lane == 0) d.E[r] = (int)mx;
 }
 
-// One block per (row tile, 32-wide K chunk): the 7 digit planes of that tile.
+// One block per (row tile, 32-wide K chunk): the 7 digit planes of that tile.  A
+// descriptor without tiles asks for the row exponents only (k_rowexp).
 __global__ void __launch_bounds__(256) k_split(const SplitDesc* __restrict__ descs) {
   const SplitDesc d = descs[blockIdx.y];
+  if (!d.tiles) return;
   const int TR = d.row_tile;
   const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
   const int ntr = (d.R + TR - 1) / TR;
@@ -179,21 +205,14 @@ __global__ void __launch_bounds__(256) k_split(const SplitDesc* __restrict__ des
     if (d.ks == 1) { r = it >> 2; kg = it & 3; } else { r = it % TR; kg = it / TR; }
     const int gr = rt * TR + r;
     const unsigned emax = gr < d.R ? (unsigned)d.E[gr] : 0u;
-    uint32_t w[OZ_S][4];
+    double x[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int k = kc * OZ_KC + kg * 8 + j;
-      double x = 0.0;
-      if (gr < d.R && k < d.K) x = d.X[(long long)gr * d.rs + (long long)k * d.ks];
-      int dg[OZ_S];
-      digits7(x, emax, dg);
-#pragma unroll
-      for (int p = 0; p < OZ_S; ++p) {
-        const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn((float)dg[p]));
-        if (j & 1) w[p][j >> 1] |= b << 16;
-        else w[p][j >> 1] = b;
-      }
+      x[j] = (gr < d.R && k < d.K) ? d.X[(long long)gr * d.rs + (long long)k * d.ks] : 0.0;
     }
+    uint32_t w[OZ_S][4];
+    split8(x, emax, w);
     const int off = tile_off32(r, kg * 8);
 #pragma unroll
     for (int p = 0; p < OZ_S; ++p)
@@ -466,6 +485,233 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
   }
 }
 
+
+
+// ---------------------------------------------------------------------------------------
+// Wide-K product with the digit split of the FP64 A operand fused in: C = A B^T with A
+// (M x K, element (i, k) at A[i * a_rs + k], K contiguous) read from HBM once, and B
+// (N <= 32) already split.  One CTA per 128-row tile of A.  Sixteen worker warps load the
+// FP64 tile of each 32-wide K step (one 64-byte row segment per thread, the next step's
+// segment prefetched), write its 7 BF16 digit planes into a 3-stage shared-memory ring in
+// the MMA's canonical layout, and drain the TMEM group sums of each 64-wide chunk into
+// exact int64 words; warp 0 streams the B planes with cp.async.bulk, one thread of warp 1
+// issues the 28 digit-pair MMAs per 16-wide k-step into one of two TMEM accumulator sets,
+// so the MMAs of chunk c+1 run while chunk c is drained.  Digit planes never touch HBM:
+// 8 bytes per element of A instead of 8 (split read) + 14 (planes written) + 14 (planes
+// read).
+constexpr int FA_WORKERS = 16;
+constexpr int FA_THREADS = 32 * (2 + FA_WORKERS);
+constexpr int FA_NS = 3;
+constexpr int FA_A = OZ_S * OZ_M * OZ_KC * 2;     // 57344 B of A planes per stage
+constexpr int FA_B = OZ_S * 32 * OZ_KC * 2;       // 14336 B of B planes per stage
+constexpr int FA_STAGE = FA_A + FA_B;
+constexpr int FA_BAR = FA_NS * FA_STAGE;          // FULL[3] EMPTY[3] TFULL[2] TEMPTY[2] DONE
+constexpr int FA_SLOT = FA_BAR + 128;
+constexpr int FA_FLAG = FA_SLOT + 16;
+constexpr int FA_SMEM = FA_FLAG + 16 + 1024;
+static_assert(FA_SMEM <= 227 * 1024, "fused product exceeds the shared memory of one CTA");
+static_assert(FA_WORKERS * 32 == 4 * OZ_M, "one worker thread per (row, 8-wide k group)");
+
+__global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __restrict__ descs,
+                                                           unsigned* status) {
+  const OzDesc d = descs[blockIdx.y];
+  const int tiles_m = (d.M + OZ_M - 1) / OZ_M;
+  if ((int)blockIdx.x >= tiles_m) return;
+  if (d.N > 32) {
+    if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
+    return;
+  }
+  const int bi = blockIdx.x;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar = sbase + FA_BAR;
+  // FULL: the workers' A planes are in; BFULL: the B planes landed (tracked on their own so
+  // the producer can always wait for its copies); EMPTY: the MMAs of a stage completed.
+  const uint32_t FULL = bar, BFULL = bar + 24, EMPTY = bar + 48, TFULL = bar + 72, TEMPTY = bar + 88,
+                 DONE = bar + 104;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + FA_SLOT);
+  volatile int* abort_flag = reinterpret_cast<int*>(smem + FA_FLAG);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
+  const int nch = (nkc + 1) / 2;
+
+  if (tid == 0) {
+    for (int i = 0; i < FA_NS; ++i) {
+      mbar_init(FULL + 8 * i, 32 * FA_WORKERS);
+      mbar_init(BFULL + 8 * i, 1);
+      mbar_init(EMPTY + 8 * i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(TFULL + 8 * i, 1);
+      mbar_init(TEMPTY + 8 * i, 32 * FA_WORKERS);
+    }
+    mbar_init(DONE, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *slot;
+
+  if (warp == 0) {
+    // ---------------- B planes (N <= 32 rows: a single column tile)
+    if (lane == 0) {
+      int issued = 0;
+      for (int kc = 0; kc < nkc && !*abort_flag; ++kc) {
+        const int s = kc % FA_NS, use = kc / FA_NS;
+        if (!mbar_wait(EMPTY + 8 * s, (use & 1) ^ 1)) { *abort_flag = 1; break; }
+        mbar_expect_tx(BFULL + 8 * s, FA_B);
+        const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(d.Bt) + (size_t)kc * OZ_S * 32 * OZ_KC;
+        bulk_g2s(sbase + s * FA_STAGE + FA_A, src, FA_B, BFULL + 8 * s);
+        issued = kc + 1;
+      }
+      for (int kc = (issued > FA_NS ? issued - FA_NS : 0); kc < issued; ++kc)
+        mbar_wait(BFULL + 8 * (kc % FA_NS), (kc / FA_NS) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(OZ_M, 32);
+      for (int kc = 0; kc < nkc && !*abort_flag; ++kc) {
+        const int s = kc % FA_NS, use = kc / FA_NS, c = kc >> 1, buf = c & 1;
+        const bool chunk_start = (kc & 1) == 0;
+        if (chunk_start && !mbar_wait(TEMPTY + 8 * buf, ((c >> 1) & 1) ^ 1)) { *abort_flag = 1; break; }
+        if (!mbar_wait(BFULL + 8 * s, use & 1) || !mbar_wait(FULL + 8 * s, use & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = sbase + s * FA_STAGE, b0 = a0 + FA_A;
+        const uint32_t dbase = tmem + buf * (OZ_G * 32);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+#pragma unroll
+          for (int g = 2; g <= OZ_S + 1; ++g) {
+#pragma unroll
+            for (int p = 1; p <= OZ_S; ++p) {
+              const int q = g - p;
+              if (q < 1 || q > OZ_S) continue;
+              const uint32_t first = (chunk_start && t == 0 && p == (g - 1 < OZ_S ? 1 : g - OZ_S));
+              const uint64_t ad = sdesc(a0 + (p - 1) * (OZ_M * OZ_KC * 2) + t * 256, 128, 512);
+              const uint64_t bd = sdesc(b0 + (q - 1) * (32 * OZ_KC * 2) + t * 256, 128, 512);
+              mma_bf16(dbase + (g - 2) * 32, ad, bd, idesc, first ? 0u : 1u);
+            }
+          }
+        }
+        mma_commit(EMPTY + 8 * s);
+        if ((kc & 1) == 1 || kc == nkc - 1) mma_commit(TFULL + 8 * buf);
+      }
+      // every MMA issued so far completes before the accumulators are released
+      mma_commit(DONE);
+      mbar_wait(DONE, 0);
+    }
+  } else {
+    // ---------------- workers: split A, drain TMEM
+    const int ew = warp - 2, wt = ew * 32 + lane;
+    const int r = wt >> 2, kg = wt & 3;             // split item: tile row, 8-wide k group
+    const int gi = bi * OZ_M + r;
+    const bool row_ok = gi < d.M;
+    const unsigned emax = row_ok ? (unsigned)d.Ae[gi] : 0u;
+    const double* rowp = static_cast<const double*>(d.At) + (row_ok ? (size_t)gi * d.a_rs : 0);
+    const bool vec = ((reinterpret_cast<uintptr_t>(rowp) | (uintptr_t)d.a_rs * 8) & 15) == 0;
+    const int quarter = warp & 3, col0 = (ew >> 2) * 8;  // drain: TMEM lane quarter, 8 columns
+    const int drow = bi * OZ_M + quarter * 32 + lane;
+    auto load = [&](int kc, double (&x)[8]) {
+      const int k0 = kc * OZ_KC + kg * 8;
+      if (row_ok && vec && k0 + 8 <= d.K) {
+        const double2* p2 = reinterpret_cast<const double2*>(rowp + k0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const double2 v = p2[j];
+          x[2 * j] = v.x;
+          x[2 * j + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = (row_ok && k0 + j < d.K) ? rowp[k0 + j] : 0.0;
+      }
+    };
+    long long H[8], Lw[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { H[j] = 0; Lw[j] = 0; }
+    bool alive = true;
+    auto drain = [&](int c) {
+      const int buf = c & 1;
+      if (!mbar_wait_warp(TFULL + 8 * buf, (c >> 1) & 1)) { alive = false; *abort_flag = 1; return; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t lb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (OZ_G * 32) + col0;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        uint32_t v[OZ_G][4];
+#pragma unroll
+        for (int g = 0; g < OZ_G; ++g) tmem_ld4(lb + g * 32 + half * 4, v[g]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (half == 1) {
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(TEMPTY + 8 * buf);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          int a[OZ_G];
+#pragma unroll
+          for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][j]));
+          H[half * 4 + j] += ((long long)a[0] << 24) + ((long long)a[1] << 16) + ((long long)a[2] << 8);
+          Lw[half * 4 + j] +=
+              ((long long)a[3] << 24) + ((long long)a[4] << 16) + ((long long)a[5] << 8) + a[6];
+        }
+      }
+    };
+    double xn[8];
+    load(0, xn);
+    for (int kc = 0; kc < nkc && alive; ++kc) {
+      const int s = kc % FA_NS, use = kc / FA_NS;
+      uint32_t w[OZ_S][4];
+      split8(xn, emax, w);
+      if (kc + 1 < nkc) load(kc + 1, xn);  // in flight while this step is stored
+      if (!mbar_wait_warp(EMPTY + 8 * s, (use & 1) ^ 1)) { alive = false; *abort_flag = 1; break; }
+      unsigned char* stA = smem + s * FA_STAGE;
+      const int off = tile_off32(r, kg * 8);
+#pragma unroll
+      for (int p = 0; p < OZ_S; ++p)
+        *reinterpret_cast<uint4*>(stA + 2 * ((size_t)p * OZ_M * OZ_KC + off)) =
+            make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(FULL + 8 * s);
+      if (((kc & 1) == 1 || kc == nkc - 1) && (kc >> 1) >= 1) drain((kc >> 1) - 1);
+    }
+    if (alive && nch >= 1) drain(nch - 1);
+    if (alive && drow < d.M) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int gj = col0 + j;
+        if (gj < d.N) {
+          const int fj = d.Be[gj];
+          double v = 0.0;
+          if (d.Ae[drow] != 0 && fj != 0) {
+            const int k = d.Ae[drow] + fj - 2044 - 64;
+            v = i64_to_double_pow2(H[j], k + 24, false) + i64_to_double_pow2(Lw[j], k, false);
+          }
+          d.C[(size_t)drow * d.c_rs + (size_t)gj * d.c_cs] = v;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
 
 // ---------------------------------------------------------------------------------------
 // Persistent update kernel for short products (K <= 64: the rank-32 QR update and the
@@ -763,6 +1009,22 @@ cudaError_t launch_ozaki_upd(const OzDesc* d, int count, int total_tiles, double
   else if (mode == 1) { if (ident) ELM_UPD(1, true); else ELM_UPD(1, false); }
   else { if (ident) ELM_UPD(2, true); else ELM_UPD(2, false); }
 #undef ELM_UPD
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned* status,
+                            cudaStream_t st) {
+  if (count <= 0 || max_tiles <= 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_ozaki_fa, cudaFuncAttributeMaxDynamicSharedMemorySize, FA_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  for (int off = 0; off < count; off += 65535) {
+    const int c = count - off < 65535 ? count - off : 65535;
+    k_ozaki_fa<<<dim3(max_tiles, c), FA_THREADS, FA_SMEM, st>>>(d + off, status);
+  }
   return cudaGetLastError();
 }
 
