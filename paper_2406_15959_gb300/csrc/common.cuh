@@ -56,7 +56,7 @@ struct OzDesc {
   double* C;
   long long c_rs, c_cs;
   int M, N, K;
-  int tile0;  // persistent launches: index of this entry's first 128 x 32 tile in the batch
+  int tile0;  // unused (kept zero)
   long long a_rs;  // fused-split launches: At is the FP64 A, element (i, k) at At[i * a_rs + k]
 };
 
@@ -67,10 +67,14 @@ cudaError_t launch_split(const SplitDesc* d, int count, int max_rows, int max_sp
                          cudaStream_t st);
 cudaError_t launch_ozaki(int nt, const OzDesc* d, int count, int max_tiles, double alpha,
                          double beta, int flags, unsigned* status, cudaStream_t st);
-// Persistent variant for K <= 64 (one CTA per SM over all 128 x 32 tiles of the batch;
-// entries carry their first tile index in tile0, total_tiles = tiles of the whole batch).
-cudaError_t launch_ozaki_upd(const OzDesc* d, int count, int total_tiles, double alpha,
-                             double beta, int flags, unsigned* status, cudaStream_t st);
+// Persistent variant for K <= 64: one CTA per SM walks a tile table of (entry, row tile,
+// column tile) over all 128 x 32 output tiles of the batch.  oz_upd_tile_table (host)
+// writes that table (out may be null to count) and skips the tiles above the diagonal of
+// a GEMM_LOWER product; it returns the number of tiles.
+int oz_upd_tile_table(const OzDesc* descs, int count, int flags, int4* out);
+cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int total_tiles,
+                             double alpha, double beta, int flags, unsigned* status,
+                             cudaStream_t st);
 // C = A B^T with the FP64 A split inside the kernel (At = FP64 A, a_rs its row stride, K
 // contiguous; Ae its row exponents), B split as usual with row_tile 32, N <= 32, beta = 0.
 cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned* status,
@@ -93,6 +97,11 @@ cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms,
 cudaError_t launch_trsm_y(double* Y, long long ystride, int mgld, const double* K,
                           long long kstride, int ld, const int* mg, int mgmax, int N, int n,
                           cudaStream_t st);
+// Diagonal step c0 of the blocked solve Y R = A (64 columns; the blocks to the left are
+// already applied): Y[:, c0:c0+64] <- Y[:, c0:c0+64] R[c0:c0+64, c0:c0+64]^{-1}.
+cudaError_t launch_trsm_y_diag(double* Y, long long ystride, int mgld, const double* K,
+                               long long kstride, int ld, const int* mg, int mgmax, int N, int n,
+                               int c0, cudaStream_t st);
 cudaError_t launch_load_rhs(double* X, const double* rhs, int N, int m_max, int ld,
                             const int* cnt, int nrhs, unsigned* status, cudaStream_t st);
 cudaError_t launch_apply_qt(double* X, const double* K, long long kstride, int ld,

@@ -21,7 +21,8 @@ namespace {
 struct LaunchRec {
   int kind;  // 0 = FP64 gemm, 1 = add_blocks, 2 = digit split, 3 = tensor-core digit GEMM,
              // 4 = persistent tensor-core digit GEMM for K <= 64 (max_tiles = total tiles),
-             // 5 = tensor-core digit GEMM with the FP64 A operand split in the kernel
+             // 5 = tensor-core digit GEMM with the FP64 A operand split in the kernel,
+             // 6 = diagonal step of the blocked Y = A R^{-1} (off = first column, nt = width)
   int off, count, max_tiles;  // split: max_tiles = blocks of k_split, nt = max rows
   bool ta, tb;
   double alpha, beta;
@@ -30,6 +31,7 @@ struct LaunchRec {
   int nt;        // tensor-core GEMM: tile width (32 or 64); split: largest row count
   double bytes = 0.0;          // algorithmic HBM bytes (FP64 operands read, C read/written)
   const char* name = nullptr;  // kernel class for profiling (nullptr: the caller's name)
+  int toff = 0;                // persistent launches: offset of the tile table
 };
 
 // One profiled launch: events around it, its class and algorithmic flops.
@@ -112,6 +114,7 @@ struct elm_ddm_handle {
   double *Mdiag = nullptr, *thW = nullptr, *thb = nullptr, *xy = nullptr, *nrm = nullptr;
   double* cinv = nullptr;             // inverses of the Cholesky diagonal blocks, one per step
   std::vector<LaunchRec> trsm_recs;   // per Cholesky step: L21 = A21 L11^{-T} as a product
+  std::vector<LaunchRec> ty_recs;     // blocked Y = A R^{-1} (tensor-core path)
   std::vector<int> trsm_first;
   double *X = nullptr, *gq = nullptr, *hq = nullptr, *zv = nullptr;
   double *rv = nullptr, *hv = nullptr, *yv = nullptr, *uv = nullptr;
@@ -122,6 +125,7 @@ struct elm_ddm_handle {
   AddDesc* ad = nullptr;
   SplitDesc* sd = nullptr;
   OzDesc* od = nullptr;
+  int4* ut = nullptr;  // tile tables of the persistent launches
   bool emulated = true;          // FP64 products on the tensor cores (digit split)
   void* sp_buf = nullptr;        // digit tiles and row exponents of the split operands
   std::vector<int> qr_first;     // first record of each panel in qr_recs
@@ -246,9 +250,12 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
     else if (L.kind == 3)
       ELM_LAUNCH_FB(h, launch_ozaki(L.nt, h->od + L.off, L.count, L.max_tiles, L.alpha, L.beta,
                                     L.flags, h->status, h->st), nm, L.flops, L.bytes);
+    else if (L.kind == 6)
+      ELM_LAUNCH_F(h, launch_trsm_y_diag(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg,
+                                         h->mgmax, h->N, h->n, L.off, h->st), nm, L.flops);
     else if (L.kind == 4)
-      ELM_LAUNCH_FB(h, launch_ozaki_upd(h->od + L.off, L.count, L.max_tiles, L.alpha, L.beta,
-                                        L.flags, h->status, h->st), nm, L.flops, L.bytes);
+      ELM_LAUNCH_FB(h, launch_ozaki_upd(h->od + L.off, L.count, h->ut + L.toff, L.max_tiles, L.alpha,
+                                        L.beta, L.flags, h->status, h->st), nm, L.flops, L.bytes);
     else
       ELM_LAUNCH_FB(h, launch_ozaki_fa(h->od + L.off, L.count, L.max_tiles, h->status, h->st), nm,
                     L.flops, L.bytes);
@@ -475,13 +482,17 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const size_t s5 = al(oz_split_elems(mgm, n, 128) * 2), e5 = al((size_t)mgm * 4);
   const size_t s6 = al(oz_split_elems(mgm, n, 32) * 2), e6 = al((size_t)mgm * 4);
   const size_t s7 = al(oz_split_elems(mgm, n, 128) * 2), e7 = al((size_t)mgm * 4);
-  const size_t per_sub = s1 + e1 + s2 + e2 + s3 + e3 + s4 + e4 + s5 + e5 + s6 + e6 + s7 + e7;
+  // Y = A R^{-1} updates: the 64-row block of R to the right of the diagonal (Y_b reuses s7)
+  const size_t s8 = al(oz_split_elems(n, 64, 32) * 2), e8 = al((size_t)n * 4);
+  const size_t per_sub = s1 + e1 + s2 + e2 + s3 + e3 + s4 + e4 + s5 + e5 + s6 + e6 + s7 + e7 + s8 + e8;
   const size_t c1 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 128) * 2);
   const size_t c2 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 32) * 2);
   const size_t ce = al((size_t)std::max(restmax, 1) * 4);
+  // digit planes and row exponents of the diagonal-block inverse (panel solve operand)
+  const size_t c3 = al(oz_split_elems(CHOL_NB, CHOL_NB, 32) * 2), ec3 = al((size_t)CHOL_NB * 4);
   if (h->emulated) {
     char* base = nullptr;
-    if (!dev_alloc(h, &base, per_sub * N + c1 + c2 + 2 * ce)) {
+    if (!dev_alloc(h, &base, per_sub * N + c1 + c2 + 2 * ce + c3 + ec3)) {
       free_all(h);
       delete h;
       return fail(nullptr, ELM_DDM_ERR_OOM, "device allocation failed (split workspace)");
@@ -489,7 +500,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     h->sp_buf = base;
   }
   auto sub_region = [&](int s, int which) -> char* {
-    const size_t sz[14] = {s1, e1, s2, e2, s3, e3, s4, e4, s5, e5, s6, e6, s7, e7};
+    const size_t sz[16] = {s1, e1, s2, e2, s3, e3, s4, e4, s5, e5, s6, e6, s7, e7, s8, e8};
     size_t off = 0;
     for (int i = 0; i < which; ++i) off += sz[i];
     return (char*)h->sp_buf + (size_t)s * per_sub + off;
@@ -545,6 +556,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   // small T^T W1 stays on the FP64 pipe.
   std::vector<SplitDesc> sds;
   std::vector<OzDesc> ods;
+  std::vector<int4> uts;
   auto add_split_rec = [&](std::vector<LaunchRec>& recs, const std::vector<SplitDesc>& batch,
                            const char* name) {
     LaunchRec L{2, (int)sds.size(), 0, 0, false, false, 0, 0, 0, 0.0, 0};
@@ -565,17 +577,12 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   };
   auto add_oz_rec = [&](std::vector<LaunchRec>& recs, const std::vector<OzDesc>& batch, int nt,
                         double alpha, double beta, int flags, const char* name) {
-    // nt == 0: persistent K <= 64 kernel over 128 x 32 tiles (max_tiles = tiles in total)
+    // nt == 0: persistent K <= 64 kernel over a table of 128 x 32 tiles (max_tiles = its size)
     LaunchRec L{nt == 0 ? 4 : 3, (int)ods.size(), 0, 0, false, false, alpha, beta, flags, 0.0, nt};
     L.name = name;
-    for (OzDesc d : batch) {
+    for (const OzDesc& d : batch) {
       if (d.M <= 0 || d.N <= 0) continue;
-      if (nt == 0) {
-        d.tile0 = L.max_tiles;
-        L.max_tiles += oz_tiles(d.M, d.N, 32);
-      } else {
-        L.max_tiles = std::max(L.max_tiles, oz_tiles(d.M, d.N, nt));
-      }
+      if (nt != 0) L.max_tiles = std::max(L.max_tiles, oz_tiles(d.M, d.N, nt));
       ods.push_back(d);
       L.count++;
       const bool low = (flags & GEMM_LOWER) != 0;
@@ -583,6 +590,12 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       // FP64 operands read once, C written (and read when beta != 0)
       const double cbytes = (beta != 0.0 ? 16.0 : 8.0) * (low ? 0.5 * d.M * (d.M + 1.0) : (double)d.M * d.N);
       L.bytes += 8.0 * ((double)d.M * d.K + (low ? 0.0 : (double)d.N * d.K)) + cbytes;
+    }
+    if (nt == 0 && L.count > 0) {
+      L.toff = (int)uts.size();
+      L.max_tiles = oz_upd_tile_table(ods.data() + L.off, L.count, flags, nullptr);
+      uts.resize(uts.size() + L.max_tiles);
+      oz_upd_tile_table(ods.data() + L.off, L.count, flags, uts.data() + L.toff);
     }
     recs.push_back(L);
   };
@@ -646,6 +659,33 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
   }
   h->qr_first.push_back((int)h->qr_recs.size());
+  // Y = A R^{-1}, blocked by 64 columns: substitution on the diagonal block of R, then the
+  // columns to its right take Y_b R[b, >b] off as a digit-split product (K = 64).
+  if (h->emulated && mgmax > 0) {
+    for (int c0 = 0; c0 < n; c0 += 64) {
+      const int nbe = std::min(64, n - c0), nrest = n - c0 - nbe;
+      LaunchRec D{6, c0, 1, 0, false, false, 0.0, 0.0, 0, 0.0, nbe};
+      for (int s = 0; s < N; ++s) D.flops += (double)h->mg_h[s] * nbe * nbe;
+      D.name = "trsm_y";
+      h->ty_recs.push_back(D);
+      if (nrest <= 0) continue;
+      std::vector<SplitDesc> sp;
+      std::vector<OzDesc> od;
+      for (int s = 0; s < N; ++s) {
+        const int mgs = h->mg_h[s];
+        if (mgs == 0) continue;
+        double* Ys = h->Am + (size_t)s * h->astride;
+        const double* Rb = h->K + (size_t)s * h->kstride + c0 + (size_t)(c0 + nbe) * ld;
+        void* ty = sub_region(s, 12); int* xy = (int*)sub_region(s, 13);
+        void* tr = sub_region(s, 14); int* xr = (int*)sub_region(s, 15);
+        sp.push_back({Ys + (size_t)c0 * h->mgld, 1, h->mgld, mgs, nbe, xy, ty, 128});
+        sp.push_back({Rb, ld, 1, nrest, nbe, xr, tr, 32});
+        od.push_back({ty, xy, tr, xr, Ys + (size_t)(c0 + nbe) * h->mgld, 1, h->mgld, mgs, nrest, nbe, 0});
+      }
+      add_split_rec(h->ty_recs, sp, "split_trsm_y");
+      add_oz_rec(h->ty_recs, od, 0, -1.0, 1.0, 0, "oz_trsm_y");
+    }
+  }
   // D_s = I - (Q_G^T)^T Q_G^T and M_s = -Y_s Q_G^T (K = n_N): tensor-core products that
   // share the digit split of Q_G, or FP64 GEMMs.
   {
@@ -752,16 +792,20 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       h->trsm_first.push_back((int)h->trsm_recs.size());
       if (rest <= 0) continue;
       double* L21 = h->S + (k + nb) + (size_t)k * ng;
-      // panel solve as an in-place product: every 64-wide tile reads all of its rows of
-      // A21 before writing them, and the tiles never share rows
-      add_gemm_rec(h->trsm_recs,
-                   {{L21, h->cinv + (size_t)step * CHOL_NB * CHOL_NB, L21, rest, nb, nb, ng, CHOL_NB, ng}},
-                   false, true, 1.0, 0.0, 0);
-      h->trsm_recs.back().name = "trsm_chol";
+      const double* cinv = h->cinv + (size_t)step * CHOL_NB * CHOL_NB;
       double* S22 = h->S + (k + nb) + (size_t)(k + nb) * ng;
       if (h->emulated) {
         int* xa = (int*)(chol_region + c1 + c2);
         int* xb = (int*)(chol_region + c1 + c2 + ce);
+        // panel solve L21 = A21 L11^{-T} as a digit-split product with the stored inverse:
+        // A21 is split before the product overwrites it in place
+        char* t3 = chol_region + c1 + c2 + 2 * ce;
+        int* x3 = (int*)(t3 + c3);
+        std::vector<SplitDesc> spt{{L21, 1, ng, rest, nb, xa, chol_region, 128},
+                                   {cinv, 1, CHOL_NB, nb, nb, x3, t3, 32}};
+        add_split_rec(h->trsm_recs, spt, "split_trsm");
+        add_oz_rec(h->trsm_recs, {{chol_region, xa, t3, x3, L21, 1, ng, rest, nb, nb, 0}}, 0, 1.0, 0.0,
+                   0, "trsm_chol");
         std::vector<SplitDesc> sp{{L21, 1, ng, rest, nb, xa, chol_region, 128},
                                   {L21, 1, ng, rest, nb, xb, chol_region + c1, 32}};
         add_split_rec(h->syrk_recs, sp, "split_syrk");
@@ -769,6 +813,11 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
                    {{chol_region, xa, chol_region + c1, xb, S22, 1, ng, rest, rest, nb, 0}}, 0, -1.0,
                    1.0, GEMM_LOWER, "oz_syrk");
       } else {
+        // panel solve as an in-place product: every 64-wide tile reads all of its rows of
+        // A21 before writing them, and the tiles never share rows
+        add_gemm_rec(h->trsm_recs, {{L21, cinv, L21, rest, nb, nb, ng, CHOL_NB, ng}}, false, true, 1.0,
+                     0.0, 0);
+        h->trsm_recs.back().name = "trsm_chol";
         add_gemm_rec(h->syrk_recs, {{L21, L21, S22, rest, rest, nb, ng, ng, ng}}, false, true, -1.0,
                      1.0, GEMM_LOWER);
       }
@@ -777,7 +826,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     h->trsm_first.push_back((int)h->trsm_recs.size());
   }
   ok = dev_alloc(h, &h->gd, gds.size()) && dev_alloc(h, &h->ad, ads.size()) &&
-       dev_alloc(h, &h->sd, sds.size()) && dev_alloc(h, &h->od, ods.size());
+       dev_alloc(h, &h->sd, sds.size()) && dev_alloc(h, &h->od, ods.size()) &&
+       dev_alloc(h, &h->ut, uts.size());
   if (!ok) {
     free_all(h);
     delete h;
@@ -791,6 +841,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   cp(h->ad, ads.data(), ads.size() * sizeof(AddDesc));
   cp(h->sd, sds.data(), sds.size() * sizeof(SplitDesc));
   cp(h->od, ods.data(), ods.size() * sizeof(OzDesc));
+  cp(h->ut, uts.data(), uts.size() * sizeof(int4));
   cp(h->xy, xy, (size_t)N * m_max * 2 * sizeof(double));
   cp(h->nrm, nrm, (size_t)N * m_max * 2 * sizeof(double));
   cp(h->cnt, counts, (size_t)N * 3 * sizeof(int));
@@ -840,9 +891,15 @@ int elm_ddm_schur(elm_ddm_handle* h) {
   }
   h->state = 0;  // K is factored in place: assemble again before another schur
   if (h->ng > 0) {
-    ELM_LAUNCH(h, launch_trsm_y(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg, h->mgmax,
-                                h->N, h->n, h->st), "trsm_y");
-    int rc = run_recs(h, h->dm_recs, 0, h->dm_recs.size(), "gemm_dm");
+    int rc;
+    if (h->emulated) {
+      rc = run_recs(h, h->ty_recs, 0, h->ty_recs.size(), "trsm_y");
+      if (rc) return rc;
+    } else {
+      ELM_LAUNCH(h, launch_trsm_y(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg, h->mgmax,
+                                  h->N, h->n, h->st), "trsm_y");
+    }
+    rc = run_recs(h, h->dm_recs, 0, h->dm_recs.size(), "gemm_dm");
     if (rc) return rc;
     cudaError_t e = cudaMemsetAsync(h->S, 0, (size_t)h->ng * h->ng * sizeof(double), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->Mdiag, 0, h->mdiag_elems * sizeof(double), h->st);

@@ -11,62 +11,78 @@ constexpr int NB = CHOL_NB;
 
 // Unblocked Cholesky of the nb x nb diagonal block at (k, k), in shared memory, and the
 // inverse of that factor (written column-major to inv, ld NB) so that the panel solve
-// L21 = A21 L11^{-T} is a matrix product.  The inverse comes from L X = I by forward
-// elimination on all columns at once: row k of X is final after division by L_kk and
-// is then eliminated from the rows below.
-__global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ S, int ld, int k, int nb,
-                                                    double* __restrict__ inv, unsigned* status) {
+// L21 = A21 L11^{-T} is a matrix product.  Both run in one loop over the pivots with one
+// barrier per column.  Step j works with the unscaled column j (a_ij, i > j, final at this
+// point) and the multipliers t_i = a_ij / d_j, d_j = a_jj:
+//   Cholesky:  a_ik -= t_i a_kj              for j < k <= i  (= l_ij l_kj)
+//   inverse:   y_ic -= t_i y_jc              for i > j, c <= j
+// where Y = unscaled rows of L^{-1} (forward elimination of L X = I, row r of X being
+// y_r / l_rr).  The two updates touch disjoint entries and read only column j of a and
+// row j of y, so they share the barrier.  At the end l_jj = sqrt(d_j), l_ij = a_ij / l_jj
+// and x_rc = y_rc / l_rr.
+//
+// FP64 arithmetic is the scarce resource (2 FMA per clock per SM), so nothing is computed
+// redundantly: the thread that updates the next diagonal entry forms its reciprocal
+// before the barrier, each row's multiplier is formed by one lane and shuffled to the 15
+// lanes that share the row, and sqrt / reciprocal of the pivots are taken once per column.
+constexpr int POTRF_THREADS = 512;
+__global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict__ S, int ld, int k, int nb,
+                                                              double* __restrict__ inv, unsigned* status) {
   extern __shared__ double potrf_smem[];
   double (*a)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem);
-  double (*x)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem + NB * (NB + 1));
-  __shared__ double rdiag[NB];  // reciprocal pivots
+  double (*y)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem + NB * (NB + 1));
+  __shared__ double piv[NB], rdv[NB], rl[NB];  // d_j, 1 / d_j, 1 / sqrt(d_j)
+  __shared__ int bad;
+  // 32 row groups x 16 column groups; the 16 lanes of a row group sit in one half-warp
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int e = tid; e < nb * nb; e += 256) {
-    const int i = e % nb, j = e / nb;
-    a[i][j] = (i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : 0.0;
-    x[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
+    const int i = e % NB, j = e / NB;
+    a[i][j] = (i < nb && j < nb && i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : 0.0;
+    y[i][j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  bool bad = false;
+  // a pivot that is not positive (not SPD) is flagged and replaced by 1 so the loop ends
+  auto set_pivot = [&](int j) {
+    double d = a[j][j];
+    if (!(d > 0.0) || !isfinite(d)) {
+      bad = 1;
+      d = 1.0;
+    }
+    piv[j] = d;
+    rdv[j] = 1.0 / d;
+  };
+  if (tid == 0) {
+    bad = 0;
+    if (nb > 0) set_pivot(0);
+  }
+  __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {
-      double dj = a[j][j];
-      if (!(dj > 0.0) || !isfinite(dj)) { bad = true; dj = 1.0; }
-      const double pv = sqrt(dj);
-      a[j][j] = pv;
-      rdiag[j] = 1.0 / pv;
+    const double rd = rdv[j];
+    for (int i0 = j + 1; i0 < nb; i0 += 32) {  // uniform trip count inside each half-warp
+      const int i = i0 + ty;
+      double t = (tx == 0 && i < nb) ? a[i][j] * rd : 0.0;
+      t = __shfl_sync(0xffffffffu, t, threadIdx.x & 16);  // lane 0 or 16 of the warp
+      if (i < nb) {
+        for (int kk = j + 1 + tx; kk <= i; kk += 16) a[i][kk] = fma(-t, a[kk][j], a[i][kk]);
+        for (int c = tx; c <= j; c += 16) y[i][c] = fma(-t, y[j][c], y[i][c]);
+      }
     }
-    __syncthreads();
-    const double rp = rdiag[j];
-    for (int i = j + 1 + tid; i < nb; i += 256) a[i][j] *= rp;
-    __syncthreads();
-    // trailing update of the lower triangle, 16 x 16 thread grid, no index division
-    for (int ii = j + 1 + ty; ii < nb; ii += 16) {
-      const double lij = a[ii][j];
-      for (int kk = j + 1 + tx; kk <= ii; kk += 16) a[ii][kk] = fma(-lij, a[kk][j], a[ii][kk]);
-    }
+    // thread 0 updated a[j+1][j+1] above (row group 0, column group 0)
+    if (tid == 0 && j + 1 < nb) set_pivot(j + 1);
     __syncthreads();
   }
-  for (int e = tid; e < nb * nb; e += 256) {
-    const int i = e % nb, j = e / nb;
-    if (i >= j) S[(k + i) + (size_t)(k + j) * ld] = a[i][j];
-  }
-  if (bad) atomicOr(status, ST_NOT_SPD);
-  if (!inv) return;
-  // L X = I: row r of X is final after scaling by 1/L_rr, then eliminated from rows below
-  for (int r = 0; r < nb; ++r) {
-    const double dr = rdiag[r];
-    for (int j = tid; j <= r; j += 256) x[r][j] *= dr;
-    __syncthreads();
-    for (int i = r + 1 + ty; i < nb; i += 16) {
-      const double lir = a[i][r];
-      for (int j = tx; j <= r; j += 16) x[i][j] = fma(-lir, x[r][j], x[i][j]);
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < NB * NB; e += 256) {
+  if (tid < nb) rl[tid] = 1.0 / sqrt(piv[tid]);
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
     const int i = e % NB, j = e / NB;
-    inv[i + j * NB] = (i < nb && j < nb && i >= j) ? x[i][j] : 0.0;
+    if (i >= nb || j >= nb || i < j) continue;
+    S[(k + i) + (size_t)(k + j) * ld] = i == j ? sqrt(piv[j]) : a[i][j] * rl[j];
+  }
+  if (tid == 0 && bad) atomicOr(status, ST_NOT_SPD);
+  if (!inv) return;
+  for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
+    const int i = e % NB, j = e / NB;
+    inv[i + j * NB] = (i < nb && j < nb && i >= j) ? y[i][j] * rl[i] : 0.0;
   }
 }
 
@@ -203,7 +219,7 @@ cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, double* inv, uns
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_potrf_diag<<<1, 256, smem, st>>>(S, ld, k, nb, inv, status);
+  k_potrf_diag<<<1, POTRF_THREADS, smem, st>>>(S, ld, k, nb, inv, status);
   return cudaGetLastError();
 }
 

@@ -1,26 +1,29 @@
 // FP64-accurate GEMM on the BF16 tensor cores (tcgen05), by exact digit splitting.
 //
 // GB300 runs FP64 at ~1/60 of FP32 and has no fast FP64 tensor path, while every large
-// dense update of the solver (QR trailing updates, the Schur Cholesky's SYRK) needs
-// FP64 accuracy.  Each FP64 operand row r is written as x = 2^E_r * sum_p d_p 2^(-8p),
-// p = 1..7, with integer digits |d_1| <= 256, |d_p| <= 128 (p >= 2), exactly
-// representable in BF16 (E_r: exponent bound of the row, truncation error < 2^(E_r-56)).
-// Then
-//     (A B^T)_ij = 2^(E_i + F_j) * sum_g 2^(-8g) * sum_{p+q=g} sum_k dA_p(i,k) dB_q(j,k),
-// and for g = 2..8 the inner integer sums over 64 consecutive k are exact in the
-// FP32 accumulators of the tensor core (|sum| < 2.25 * 2^22 < 2^24).  Each K chunk of 64
-// is drained from TMEM into float-float registers (error-free TwoSum); the result meets
-// the FP64 rounding level and is combined into the FP64 output with two FP64 ops per
-// element instead of 2K.
+// dense update of the solver (QR trailing updates, the Schur Cholesky's SYRK, the D_s and
+// M_s products) needs FP64 accuracy.  Each FP64 operand row r is written as
+// x = 2^(E_r - 1022) * sum_p d_p 2^(1 - 8p), p = 1..7, with balanced integer digits
+// |d_p| <= 128, exactly representable in BF16 (E_r: largest biased exponent of the row;
+// truncation error < 2^(E_r - 1077), i.e. 2^-55 relative to the row's bound).  Then
+//     (A B^T)_ij = 2^(E_i + F_j - 2044) * sum_g 2^(-8g + 2) * sum_{p+q=g} sum_k dA_p dB_q,
+// and for g = 2..8 (28 digit pairs) the inner integer sums over 128 consecutive k are
+// exact in the FP32 accumulators of the tensor core (|sum| <= 7 * 2^14 * 128 < 2^24);
+// the groups g > 8 lie below the truncation level and are not formed.  Each 128-wide
+// chunk is drained from TMEM into two exact int64 words, and the FP64 result is built
+// from them with integer exponent arithmetic and one rounding add, so C gets the
+// accuracy of an FP64 GEMM with two FP64 operations per element instead of 2K.
 //
-// Splitting uses only integer operations on the FP64 bit pattern (no FP64 arithmetic).
+// Splitting uses only integer and FP32 operations on the FP64 bit pattern.
 // Kernels:
-//   k_rowexp  exponent bound (max biased exponent) of each operand row
-//   k_split   7 BF16 digit planes per (row tile, 32-wide K chunk), written directly in
-//             the tcgen05 K-major no-swizzle canonical layout (8x8 core matrices)
-//   k_ozaki   one CTA per 128 x NT output tile: warp 0 streams the digit tiles with
-//             cp.async.bulk, warp 1 issues the 28 digit-pair MMAs per 16-wide k-step
-//             into 7 TMEM accumulators (one per g), warps 2..5 drain TMEM and write C.
+//   k_rowexp    exponent bound (max biased exponent) of each operand row
+//   k_split     7 BF16 digit planes per (row tile, 32-wide K step), written directly in
+//               the tcgen05 K-major no-swizzle canonical layout (8x8 core matrices)
+//   k_ozaki     one CTA per 128 x NT output tile: warp 0 streams the digit tiles with
+//               cp.async.bulk, warp 1 issues the 28 digit-pair MMAs per 16-wide k-step
+//               into 7 TMEM accumulators (one per g), warps 2..5 drain TMEM and write C
+//   k_ozaki_fa  wide-K product whose FP64 A operand is split inside the kernel
+//   k_ozaki_upd persistent product for K <= 128 over a table of output tiles
 #include "common.cuh"
 
 #include <cuda_bf16.h>
@@ -130,41 +133,47 @@ __device__ __forceinline__ unsigned biased_exp(double x) {
 }
 
 // Fixed-point image of x relative to the row bound 2^(emax-1022): the signed integer
-// F = round_toward_zero(x * 2^(1078 - emax)), |F| < 2^56 (zero for x = 0, for subnormal
-// x and for an all-zero row).
-__device__ __forceinline__ long long fixed56(double x, unsigned emax) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((bits >> 52) & 0x7FF);
-  if (e == 0 || emax == 0) return 0;
-  const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int shift = (int)emax - e - 3;  // >= -3 because e <= emax
-  const unsigned long long F = shift >= 64 ? 0ull : shift >= 0 ? M >> shift : M << (-shift);
-  return (bits >> 63) ? -(long long)F : (long long)F;
+// F = trunc(x * 2^(1077 - emax)), |F| < 2^55 (zero for x = 0, for subnormal x and for an
+// all-zero row).  Branch-free: the 55-bit mantissa M << 2 is shifted right by
+// emax - e in two 32-bit halves, and the sign is applied as (F ^ s) - s.
+__device__ __forceinline__ long long fixed55(double x, unsigned emax) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  const uint32_t mh = e ? ((((hi & 0xFFFFFu) | 0x100000u) << 2) | (lo >> 30)) : 0u;
+  const uint32_t ml = e ? (lo << 2) : 0u;
+  const uint32_t s = min(emax - e, 63u);  // a shift of 55 or more leaves 0
+  const uint32_t fl = s < 32 ? __funnelshift_r(ml, mh, s) : (mh >> (s & 31));
+  const uint32_t fh = s < 32 ? (mh >> s) : 0u;
+  const unsigned long long F = ((unsigned long long)fh << 32) | fl;
+  const unsigned long long sg = (unsigned long long)((long long)(int)hi >> 31);
+  return (long long)((F ^ sg) - sg);
 }
 
-// Balanced base-256 digits of F = sum_p d_p 256^(7-p), p = 1..7, d_p in [-128, 127] for
-// p >= 2, without a carry chain: adding 128 to each of the six low byte positions makes
-// every low byte of F + C equal d_p + 128, and the bits above them equal d_1.  Each digit
-// becomes a BF16 through a float magic-number add (1.5 * 2^23 + b has the integer b in its
-// low mantissa bits; subtracting the constant back is exact), and two BF16 values are
-// packed by a byte permute of the floats' upper halves.  Returns the 7 planes' words for
-// 8 consecutive k (w[p][j] holds k = 2j, 2j+1).
+// Balanced base-256 digits of F = sum_p d_p 256^(7-p), p = 1..7, all |d_p| <= 128,
+// without a carry chain: adding 128 to each of the seven byte positions makes every low
+// byte of F + C equal to d_p + 128 (p >= 2) and the bits from 48 up equal to d_1 + 128.
+// Each digit becomes a BF16 through a float magic-number add (1.5 * 2^23 + b holds the
+// integer b in its low mantissa bits; subtracting 1.5 * 2^23 + 128 is exact), and two
+// BF16 values are packed by a byte permute of the floats' upper halves.  Returns the 7
+// planes' words for 8 consecutive k (w[p][j] holds k = 2j, 2j+1).
+//
+// With |d| <= 128 on both operands a digit product is at most 2^14 and a group
+// g = p + q has at most 7 pairs, so any 128 consecutive k sum to less than
+// 7 * 2^14 * 128 < 2^24: exact in the FP32 accumulators of the tensor core.
 __device__ __forceinline__ void split8(const double (&x)[8], unsigned emax, uint32_t (&w)[OZ_S][4]) {
-  constexpr unsigned long long kBias = 0x0000808080808080ull;
+  constexpr unsigned long long kBias = 0x0080808080808080ull;
   float f[OZ_S][8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const unsigned long long Fp = (unsigned long long)fixed56(x[j], emax) + kBias;
+    const unsigned long long Fp = (unsigned long long)fixed55(x[j], emax) + kBias;
     const uint32_t lo = (uint32_t)Fp, hi = (uint32_t)(Fp >> 32);
-    const int d1 = (int)((long long)Fp >> 48);
-    f[0][j] = __int_as_float(0x4B400000 + d1) - 12582912.0f;
-    // low bytes of Fp: digit p (p = 2..7) sits in byte 7 - p
+    f[0][j] = __uint_as_float(0x4B400000u + (hi >> 16)) - 12583040.0f;  // bits 48.. (0..256)
 #pragma unroll
-    for (int p = 2; p <= OZ_S; ++p) {
+    for (int p = 2; p <= OZ_S; ++p) {  // digit p sits in byte 7 - p
       const int byte = 7 - p;
       const uint32_t src = byte >= 4 ? hi : lo;
       const uint32_t b = __byte_perm(src, 0x4B400000u, 0x7650 | (byte & 3));
-      f[p - 1][j] = __uint_as_float(b) - 12583040.0f;  // (1.5 * 2^23 + b) - (1.5 * 2^23 + 128)
+      f[p - 1][j] = __uint_as_float(b) - 12583040.0f;
     }
   }
 #pragma unroll
@@ -279,8 +288,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
-  const int nchunk = (nkc + 1) / 2;  // exact-accumulation chunks of 64
-  if (NT > 32 && nchunk > 1) {       // the wide tile keeps no accumulators across chunks
+  const int nchunk = (nkc + 3) / 4;  // exact-accumulation chunks of 128
+  // the wide tile keeps no accumulators across chunks; H and L stay exact up to 62 chunks
+  if ((NT > 32 && nchunk > 1) || nchunk > 62) {
     if (tid == 0) atomicOr(status, ST_INTERNAL);
     return;
   }
@@ -338,8 +348,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(OZ_M, NT);
       for (int kc = 0; kc < nkc && !*abort_flag; ++kc) {
-        const int s = kc & 1, use = kc >> 1, chunk = kc >> 1;
-        const bool chunk_start = (kc & 1) == 0;
+        const int s = kc & 1, use = kc >> 1, chunk = kc >> 2;
+        const bool chunk_start = (kc & 3) == 0;
         if (chunk_start && !mbar_wait(bar + 40, (chunk & 1) ^ 1)) { *abort_flag = 1; break; }
         if (!mbar_wait(bar + 8 * s, use & 1)) { *abort_flag = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -360,15 +370,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
           }
         }
         mma_commit(bar + 16 + 8 * s);                         // stage s may be refilled
-        if ((kc & 1) == 1 || kc == nkc - 1) mma_commit(bar + 32);  // 64-chunk complete
+        if ((kc & 3) == 3 || kc == nkc - 1) mma_commit(bar + 32);  // 128-chunk complete
       }
     }
   } else {
     // ---------------- epilogue: warps 2..5 own TMEM lanes 32*(warp%4) ..
-    // The 7 group sums of a 64-chunk are exact integers; with
+    // The 7 group sums of a 128-chunk are exact integers (|a_g| < 7 * 2^21); with
     //   H = a2 2^24 + a3 2^16 + a4 2^8,   L = a5 2^24 + a6 2^16 + a7 2^8 + a8
     // (a_g the sum of group g) the chunk's value is (H 2^24 + L) 2^-48 in units of
-    // 2^(E_i + F_j - 16).  H and L stay below 2^53 for up to 64 chunks, so they are
+    // 2^(E_i + F_j - 14).  |H| < 2^45.1 and |L| < 2^47.1 per chunk, so their sums stay
+    // below 2^53 for up to 62 chunks and are
     // accumulated exactly in int64 and rounded once, by one FMA, at the end.
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
@@ -377,11 +388,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
     const int ei = gi < d.M ? d.Ae[gi] : 0;
     const bool unit_alpha = alpha == 1.0 || alpha == -1.0;
     const bool neg_alpha = alpha < 0.0;
-    // alpha * 2^(E_i + F_j - 64) * (H 2^24 + L), with the scaling folded into the exponent
+    // alpha * 2^(E_i + F_j - 62) * (H 2^24 + L), with the scaling folded into the exponent
     // fields: two exact integer-to-double conversions and one rounding add.
     auto product = [&](long long H, long long Lw, int fj) -> double {
       if (ei == 0 || fj == 0) return 0.0;
-      const int k = ei + fj - 2044 - 64;
+      const int k = ei + fj - 2044 - 62;
       double v = i64_to_double_pow2(H, k + 24, neg_alpha) + i64_to_double_pow2(Lw, k, neg_alpha);
       return unit_alpha ? v : v * (neg_alpha ? -alpha : alpha);
     };
@@ -404,7 +415,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
     };
     bool ok = true;
     if (nchunk <= 1 || NT > 32) {
-      // single 64-chunk (K <= 64): no persistent accumulators.  The C values this thread
+      // single 128-chunk (K <= 128): no persistent accumulators.  The C values this thread
       // updates are fetched before waiting for the MMAs, so their latency overlaps them.
       double cv[NT];
       const bool need_c = beta != 0.0 && gi < d.M;
@@ -493,7 +504,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
 // (N <= 32) already split.  One CTA per 128-row tile of A.  Sixteen worker warps load the
 // FP64 tile of each 32-wide K step (one 64-byte row segment per thread, the next step's
 // segment prefetched), write its 7 BF16 digit planes into a 3-stage shared-memory ring in
-// the MMA's canonical layout, and drain the TMEM group sums of each 64-wide chunk into
+// the MMA's canonical layout, and drain the TMEM group sums of each 128-wide chunk into
 // exact int64 words; warp 0 streams the B planes with cp.async.bulk, one thread of warp 1
 // issues the 28 digit-pair MMAs per 16-wide k-step into one of two TMEM accumulator sets,
 // so the MMAs of chunk c+1 run while chunk c is drained.  Digit planes never touch HBM:
@@ -534,7 +545,11 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
   volatile int* abort_flag = reinterpret_cast<int*>(smem + FA_FLAG);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
-  const int nch = (nkc + 1) / 2;
+  const int nch = (nkc + 3) / 4;  // exact 128-wide chunks; H, L stay exact up to 62 of them
+  if (nch > 62) {
+    if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
+    return;
+  }
 
   if (tid == 0) {
     for (int i = 0; i < FA_NS; ++i) {
@@ -581,8 +596,8 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(OZ_M, 32);
       for (int kc = 0; kc < nkc && !*abort_flag; ++kc) {
-        const int s = kc % FA_NS, use = kc / FA_NS, c = kc >> 1, buf = c & 1;
-        const bool chunk_start = (kc & 1) == 0;
+        const int s = kc % FA_NS, use = kc / FA_NS, c = kc >> 2, buf = c & 1;
+        const bool chunk_start = (kc & 3) == 0;
         if (chunk_start && !mbar_wait(TEMPTY + 8 * buf, ((c >> 1) & 1) ^ 1)) { *abort_flag = 1; break; }
         if (!mbar_wait(BFULL + 8 * s, use & 1) || !mbar_wait(FULL + 8 * s, use & 1)) {
           *abort_flag = 1;
@@ -607,7 +622,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
           }
         }
         mma_commit(EMPTY + 8 * s);
-        if ((kc & 1) == 1 || kc == nkc - 1) mma_commit(TFULL + 8 * buf);
+        if ((kc & 3) == 3 || kc == nkc - 1) mma_commit(TFULL + 8 * buf);
       }
       // every MMA issued so far completes before the accumulators are released
       mma_commit(DONE);
@@ -615,8 +630,11 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
     }
   } else {
     // ---------------- workers: split A, drain TMEM
-    const int ew = warp - 2, wt = ew * 32 + lane;
-    const int r = wt >> 2, kg = wt & 3;             // split item: tile row, 8-wide k group
+    // split item: tile row r, 8-wide k group kg.  A warp covers 8 rows x 4 groups with the
+    // 8 lanes of each quarter-warp on 8 rows of one group, so their 16-byte digit stores
+    // fill 128 contiguous bytes (no bank conflict).
+    const int ew = warp - 2;
+    const int r = ew * 8 + (lane & 7), kg = lane >> 3;
     const int gi = bi * OZ_M + r;
     const bool row_ok = gi < d.M;
     const unsigned emax = row_ok ? (unsigned)d.Ae[gi] : 0u;
@@ -685,7 +703,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
             make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(FULL + 8 * s);
-      if (((kc & 1) == 1 || kc == nkc - 1) && (kc >> 1) >= 1) drain((kc >> 1) - 1);
+      if (((kc & 3) == 3 || kc == nkc - 1) && (kc >> 2) >= 1) drain((kc >> 2) - 1);
     }
     if (alive && nch >= 1) drain(nch - 1);
     if (alive && drow < d.M) {
@@ -696,7 +714,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
           const int fj = d.Be[gj];
           double v = 0.0;
           if (d.Ae[drow] != 0 && fj != 0) {
-            const int k = d.Ae[drow] + fj - 2044 - 64;
+            const int k = d.Ae[drow] + fj - 2044 - 62;
             v = i64_to_double_pow2(H[j], k + 24, false) + i64_to_double_pow2(Lw[j], k, false);
           }
           d.C[(size_t)drow * d.c_rs + (size_t)gj * d.c_cs] = v;
@@ -714,7 +732,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
 }
 
 // ---------------------------------------------------------------------------------------
-// Persistent update kernel for short products (K <= 64: the rank-32 QR update and the
+// Persistent update kernel for short products (K <= 128: the rank-32 QR update and the
 // Cholesky SYRK).  One CTA per SM walks the 128 x 32 tiles of the whole batch; two
 // shared-memory stages and two TMEM accumulator sets (7 x 32 columns each) let the loads
 // and MMAs of the next tile run while eight epilogue warps finish the current one.
@@ -733,35 +751,14 @@ constexpr int UPD_SLOT = UPD_BAR + 64;
 constexpr int UPD_FLAG = UPD_SLOT + 16;
 constexpr int UPD_SMEM = UPD_FLAG + 16 + 1024;
 
-struct TileRef {
-  int e, bi, bj;
-};
-
-// Entry and tile coordinates of global tile t (entries sorted by tile0).
-__device__ __forceinline__ TileRef upd_tile(const OzDesc* __restrict__ descs, int count, int t) {
-  int lo = 0, hi = count - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (descs[mid].tile0 <= t) lo = mid; else hi = mid - 1;
-  }
-  const OzDesc& d = descs[lo];
-  const int tiles_m = (d.M + OZ_M - 1) / OZ_M;
-  const int local = t - d.tile0;
-  return {lo, local % tiles_m, local / tiles_m};
-}
-
-__device__ __forceinline__ bool upd_skip(const OzDesc& d, const TileRef& r, int flags) {
-  return (flags & GEMM_LOWER) && r.bj * UPD_NT > r.bi * OZ_M + OZ_M - 1;
-}
-
 // Epilogue modes, fixed at compile time so no FP64 compare or select runs per element:
 // EMODE 0: C = s * AB (beta = 0);  1: C = C + s * AB (beta = 1);  2: C = beta C + alpha AB.
 // s = +-1 is applied through the sign bit.  IDENT adds the identity (D = I - Q_G Q_G^T).
 template <int EMODE, bool IDENT>
 __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __restrict__ descs,
-                                                             int count, int total_tiles,
-                                                             double alpha, double beta, int flags,
-                                                             unsigned* status) {
+                                                             const int4* __restrict__ tiles,
+                                                             int total_tiles, double alpha,
+                                                             double beta, unsigned* status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sbase = smem_u32(smem);
@@ -796,18 +793,17 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
     if (lane == 0) {
       int sc = 0;  // stage counter
       for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
-        const TileRef r = upd_tile(descs, count, t);
-        const OzDesc& d = descs[r.e];
-        if (upd_skip(d, r, flags)) continue;
+        const int4 r = tiles[t];  // (entry, row tile, column tile)
+        const OzDesc& d = descs[r.x];
         const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
         for (int kc = 0; kc < nkc; ++kc, ++sc) {
           const int s = sc & 1, use = sc >> 1;
           if (!mbar_wait(EMPTY + 8 * s, (use & 1) ^ 1)) { *abort_flag = 1; break; }
           mbar_expect_tx(FULL + 8 * s, UPD_STAGE);
           const __nv_bfloat16* srcA =
-              static_cast<const __nv_bfloat16*>(d.At) + (size_t)(r.bi * nkc + kc) * OZ_S * OZ_M * OZ_KC;
+              static_cast<const __nv_bfloat16*>(d.At) + (size_t)(r.y * nkc + kc) * OZ_S * OZ_M * OZ_KC;
           const __nv_bfloat16* srcB =
-              static_cast<const __nv_bfloat16*>(d.Bt) + (size_t)(r.bj * nkc + kc) * OZ_S * UPD_NT * OZ_KC;
+              static_cast<const __nv_bfloat16*>(d.Bt) + (size_t)(r.z * nkc + kc) * OZ_S * UPD_NT * OZ_KC;
           const uint32_t dst = sbase + s * UPD_STAGE;
           bulk_g2s(dst, srcA, UPD_A, FULL + 8 * s);
           bulk_g2s(dst + UPD_A, srcB, UPD_B, FULL + 8 * s);
@@ -821,9 +817,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
       const uint32_t idesc = idesc_bf16(OZ_M, UPD_NT);
       int sc = 0, tc = 0;  // stage and tile counters
       for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
-        const TileRef r = upd_tile(descs, count, t);
-        const OzDesc& d = descs[r.e];
-        if (upd_skip(d, r, flags)) continue;
+        const OzDesc& d = descs[tiles[t].x];
         const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
         const int buf = tc & 1;
         if (!mbar_wait(TEMPTY + 8 * buf, ((tc >> 1) & 1) ^ 1)) { *abort_flag = 1; break; }
@@ -863,26 +857,20 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
     const bool neg_alpha = EMODE != 2 && (__double_as_longlong(alpha) < 0);
     int tc = 0;
     double cv[UPD_COLS];  // this thread's C values of its next tile, loaded ahead
-    auto fetch = [&](const OzDesc& d, const TileRef& r) {
-      const int gi = r.bi * OZ_M + row, gj0 = r.bj * UPD_NT + col0;
+    auto fetch = [&](const OzDesc& d, int bi, int bj) {
+      const int gi = bi * OZ_M + row, gj0 = bj * UPD_NT + col0;
       const double* cp = d.C + (size_t)gi * d.c_rs + (size_t)gj0 * d.c_cs;
 #pragma unroll
       for (int j = 0; j < UPD_COLS; ++j)
         cv[j] = (EMODE != 0 && gi < d.M && gj0 + j < d.N) ? cp[(size_t)j * d.c_cs] : 0.0;
     };
     int t = blockIdx.x;
-    while (t < total_tiles) {  // first tile of this CTA that is not skipped
-      const TileRef r = upd_tile(descs, count, t);
-      if (!upd_skip(descs[r.e], r, flags)) break;
-      t += gridDim.x;
-    }
-    if (t < total_tiles) {
-      const TileRef r0 = upd_tile(descs, count, t);
-      fetch(descs[r0.e], r0);
-    }
+    int4 r = t < total_tiles ? tiles[t] : make_int4(0, 0, 0, 0);
+    if (t < total_tiles) fetch(descs[r.x], r.y, r.z);
     while (t < total_tiles) {
-      const TileRef r = upd_tile(descs, count, t);
-      const OzDesc& d = descs[r.e];
+      const OzDesc& d = descs[r.x];
+      const int tn = t + gridDim.x;  // next tile of this CTA: its entry is read ahead
+      const int4 rn = tn < total_tiles ? tiles[tn] : make_int4(0, 0, 0, 0);
       const int buf = tc & 1;
       if (!mbar_wait_warp(TFULL + 8 * buf, (tc >> 1) & 1)) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
@@ -894,7 +882,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
       asm volatile("tcgen05.fence::before_thread_sync;");
       mbar_arrive(TEMPTY + 8 * buf);  // accumulators copied: the MMA may reuse this buffer
       ++tc;
-      const int gi = r.bi * OZ_M + row, gj0 = r.bj * UPD_NT + col0;
+      const int gi = r.y * OZ_M + row, gj0 = r.z * UPD_NT + col0;
       if (gi < d.M) {
         const int ei = d.Ae[gi];
         double* cp = d.C + (size_t)gi * d.c_rs + (size_t)gj0 * d.c_cs;
@@ -911,7 +899,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
             const int fj = be[j];
             double pv = 0.0;
             if (ei != 0 && fj != 0) {
-              const int k = ei + fj - 2044 - 64;
+              const int k = ei + fj - 2044 - 62;
               pv = i64_to_double_pow2(H, k + 24, neg_alpha) + i64_to_double_pow2(Lw, k, neg_alpha);
             }
             double out;
@@ -923,17 +911,9 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
           }
         }
       }
-      int tn = t + gridDim.x;  // next tile of this CTA; its C values load while its MMAs run
-      while (tn < total_tiles) {
-        const TileRef rn = upd_tile(descs, count, tn);
-        if (!upd_skip(descs[rn.e], rn, flags)) break;
-        tn += gridDim.x;
-      }
-      if (tn < total_tiles) {
-        const TileRef rn = upd_tile(descs, count, tn);
-        fetch(descs[rn.e], rn);
-      }
+      if (tn < total_tiles) fetch(descs[rn.x], rn.y, rn.z);  // loads while the next MMAs run
       t = tn;
+      r = rn;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -981,8 +961,23 @@ cudaError_t launch_split(const SplitDesc* d, int count, int max_rows, int max_sp
   return cudaGetLastError();
 }
 
-cudaError_t launch_ozaki_upd(const OzDesc* d, int count, int total_tiles, double alpha,
-                             double beta, int flags, unsigned* status, cudaStream_t st) {
+int oz_upd_tile_table(const OzDesc* descs, int count, int flags, int4* out) {
+  int n = 0;
+  for (int e = 0; e < count; ++e) {
+    const OzDesc& d = descs[e];
+    const int tm = (d.M + OZ_M - 1) / OZ_M, tn = (d.N + UPD_NT - 1) / UPD_NT;
+    for (int bj = 0; bj < tn; ++bj)
+      for (int bi = 0; bi < tm; ++bi) {
+        if ((flags & GEMM_LOWER) && bj * UPD_NT > bi * OZ_M + OZ_M - 1) continue;  // above the diagonal
+        if (out) out[n] = make_int4(e, bi, bj, 0);
+        ++n;
+      }
+  }
+  return n;
+}
+
+cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int total_tiles,
+                             double alpha, double beta, int flags, unsigned* status, cudaStream_t st) {
   if (count <= 0 || total_tiles <= 0) return cudaSuccess;
   static int sms = 0;
   if (!sms) {
@@ -1004,7 +999,7 @@ cudaError_t launch_ozaki_upd(const OzDesc* d, int count, int total_tiles, double
   const int mode = (beta == 0.0 && unit) ? 0 : (beta == 1.0 && unit) ? 1 : 2;
   const bool ident = (flags & GEMM_ADD_IDENTITY) != 0;
 #define ELM_UPD(M, I) \
-  k_ozaki_upd<M, I><<<grid, UPD_THREADS, UPD_SMEM, st>>>(d, count, total_tiles, alpha, beta, flags, status)
+  k_ozaki_upd<M, I><<<grid, UPD_THREADS, UPD_SMEM, st>>>(d, tiles, total_tiles, alpha, beta, status)
   if (mode == 0) { if (ident) ELM_UPD(0, true); else ELM_UPD(0, false); }
   else if (mode == 1) { if (ident) ELM_UPD(1, true); else ELM_UPD(1, false); }
   else { if (ident) ELM_UPD(2, true); else ELM_UPD(2, false); }

@@ -187,6 +187,49 @@ __global__ void __launch_bounds__(256) k_trsm_y(double* __restrict__ Y, long lon
   }
 }
 
+// Diagonal step of the blocked Y R = A solve: for the 64 columns c0.. of Y (already
+// updated with the blocks to their left), Y_b <- Y_b R_bb^{-1} by substitution, one row of
+// Y per thread.  The thread's row and R_bb live in shared memory (row stride 65: the
+// threads' own-row reads are conflict-free, R reads are broadcasts); columns past n are
+// padded with an identity block.
+constexpr int TRSMY_NB = 64;
+__global__ void __launch_bounds__(64) k_trsm_y_diag(double* __restrict__ Y, long long ystride, int mgld,
+                                                    const double* __restrict__ K, long long kstride,
+                                                    int ld, const int* __restrict__ mg_arr, int n,
+                                                    int c0) {
+  extern __shared__ double trsmy_smem[];
+  double (*sR)[TRSMY_NB + 1] = reinterpret_cast<double (*)[TRSMY_NB + 1]>(trsmy_smem);
+  double (*sy)[TRSMY_NB + 1] = reinterpret_cast<double (*)[TRSMY_NB + 1]>(trsmy_smem + TRSMY_NB * (TRSMY_NB + 1));
+  __shared__ double rdg[TRSMY_NB];
+  const int s = blockIdx.y, i0 = blockIdx.x * 64, t = threadIdx.x;
+  const int mg = mg_arr[s];
+  if (i0 >= mg) return;
+  const int nbe = min(TRSMY_NB, n - c0);
+  const double* R = K + (size_t)s * kstride;
+  double* Ys = Y + (size_t)s * ystride;
+  for (int e = t; e < TRSMY_NB * TRSMY_NB; e += 64) {
+    const int r = e % TRSMY_NB, c = e / TRSMY_NB;
+    double v = (r == c) ? 1.0 : 0.0;
+    if (r <= c && c < nbe) v = R[(c0 + r) + (size_t)(c0 + c) * ld];
+    sR[r][c] = v;
+    sy[r][c] = (i0 + r < mg && c < nbe) ? Ys[(i0 + r) + (size_t)(c0 + c) * mgld] : 0.0;
+  }
+  __syncthreads();
+  rdg[t] = 1.0 / sR[t][t];
+  __syncthreads();
+  for (int c = 0; c < nbe; ++c) {
+    double x = sy[t][c];
+#pragma unroll 8
+    for (int k = 0; k < c; ++k) x = fma(-sy[t][k], sR[k][c], x);
+    sy[t][c] = x * rdg[c];
+  }
+  __syncthreads();
+  for (int e = t; e < TRSMY_NB * TRSMY_NB; e += 64) {
+    const int r = e % TRSMY_NB, c = e / TRSMY_NB;
+    if (i0 + r < mg && c < nbe) Ys[(i0 + r) + (size_t)(c0 + c) * mgld] = sy[r][c];
+  }
+}
+
 // X[r][s][row] = F^s: f/g on interior and boundary rows, zero elsewhere.
 __global__ void k_load_rhs(double* __restrict__ X, const double* __restrict__ rhs, int N,
                            int m_max, int ld, const int* __restrict__ cnt, unsigned* status) {
@@ -547,6 +590,21 @@ cudaError_t launch_trsm_y(double* Y, long long ystride, int mgld, const double* 
                           cudaStream_t st) {
   if (mgmax <= 0) return cudaSuccess;
   k_trsm_y<<<dim3((mgmax + 31) / 32, N), 256, 0, st>>>(Y, ystride, mgld, K, kstride, ld, mg, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_y_diag(double* Y, long long ystride, int mgld, const double* K,
+                               long long kstride, int ld, const int* mg, int mgmax, int N, int n,
+                               int c0, cudaStream_t st) {
+  if (mgmax <= 0 || c0 >= n) return cudaSuccess;
+  const int smem = 2 * TRSMY_NB * (TRSMY_NB + 1) * (int)sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_trsm_y_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_trsm_y_diag<<<dim3((mgmax + 63) / 64, N), 64, smem, st>>>(Y, ystride, mgld, K, kstride, ld, mg, n, c0);
   return cudaGetLastError();
 }
 
