@@ -784,7 +784,54 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       }
     }
     for (auto& b : drounds) add_add_rec(h->s_recs, b);
-    for (auto& b : mrounds) add_gemm_rec(h->s_recs, b, true, false, 1.0, 1.0, 0);
+    // M^T M blocks: with the tensor-core path every distinct M block is split once (as a
+    // 128-row A operand and a 32-row B operand; rows = the block's columns, K = its rows)
+    // and each round is one persistent product launch (K = edge length <= 128).
+    int maxlen = 0;
+    for (const Edge& E : h->edges) maxlen = std::max(maxlen, E.len);
+    if (h->emulated && maxlen <= 128) {
+      struct MB { const double* p; int ld, rows, K; size_t ta, tb, ea, eb; };
+      std::vector<MB> blocks;
+      std::map<const double*, int> idx;
+      size_t bytes = 0;
+      for (auto& b : mrounds)
+        for (const GemmDesc& g : b)
+          for (int side = 0; side < 2; ++side) {
+            const double* ptr = side ? g.B : g.A;
+            if (idx.count(ptr)) continue;
+            MB m{ptr, side ? g.ldb : g.lda, side ? g.n : g.m, g.k, 0, 0, 0, 0};
+            m.ta = bytes; bytes += al(oz_split_elems(m.rows, m.K, 128) * 2);
+            m.tb = bytes; bytes += al(oz_split_elems(m.rows, m.K, 32) * 2);
+            m.ea = bytes; bytes += al((size_t)m.rows * 4);
+            m.eb = bytes; bytes += al((size_t)m.rows * 4);
+            idx[ptr] = (int)blocks.size();
+            blocks.push_back(m);
+          }
+      char* mbase = nullptr;
+      if (!blocks.empty() && !dev_alloc(h, &mbase, bytes)) {
+        free_all(h);
+        delete h;
+        return fail(nullptr, ELM_DDM_ERR_OOM, "device allocation failed (Schur split workspace)");
+      }
+      std::vector<SplitDesc> sp;
+      for (const MB& m : blocks) {
+        sp.push_back({m.p, m.ld, 1, m.rows, m.K, (int*)(mbase + m.ea), mbase + m.ta, 128});
+        sp.push_back({m.p, m.ld, 1, m.rows, m.K, (int*)(mbase + m.eb), mbase + m.tb, 32});
+      }
+      add_split_rec(h->s_recs, sp, "split_schur");
+      for (auto& b : mrounds) {
+        std::vector<OzDesc> od;
+        for (const GemmDesc& g : b) {
+          const MB& A = blocks[idx[g.A]];
+          const MB& B = blocks[idx[g.B]];
+          od.push_back({mbase + A.ta, (int*)(mbase + A.ea), mbase + B.tb, (int*)(mbase + B.eb), g.C, 1,
+                        g.ldc, g.m, g.n, g.k, 0});
+        }
+        add_oz_rec(h->s_recs, od, 0, 1.0, 1.0, 0, "oz_schur");
+      }
+    } else {
+      for (auto& b : mrounds) add_gemm_rec(h->s_recs, b, true, false, 1.0, 1.0, 0);
+    }
     // Cholesky trailing updates, restricted to the envelope rows [k+nb, rend)
     for (int k = 0, step = 0; k < ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, ng - k), rest = h->chol_rend[step] - k - nb;

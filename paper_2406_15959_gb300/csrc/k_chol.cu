@@ -21,20 +21,22 @@ constexpr int NB = CHOL_NB;
 // row j of y, so they share the barrier.  At the end l_jj = sqrt(d_j), l_ij = a_ij / l_jj
 // and x_rc = y_rc / l_rr.
 //
-// FP64 arithmetic is the scarce resource (2 FMA per clock per SM), so nothing is computed
-// redundantly: the thread that updates the next diagonal entry forms its reciprocal
-// before the barrier, each row's multiplier is formed by one lane and shuffled to the 15
-// lanes that share the row, and sqrt / reciprocal of the pivots are taken once per column.
+// FP64 arithmetic is the scarce resource (2 FMA per clock per SM, and a warp-wide FMA
+// occupies the pipe whatever its active lanes), so nothing is computed redundantly and the
+// updates of a step are flattened: the m(m+1)/2 entries of the trailing triangle
+// (m = nb - j - 1) and the m (j+1) entries of the inverse's rectangle form one index range
+// dealt out to consecutive threads, so every warp-wide FMA has 32 active lanes.  The row
+// multipliers t_i are formed once per row (first barrier); the thread that updates the
+// next diagonal entry forms its reciprocal before the second barrier.
 constexpr int POTRF_THREADS = 512;
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict__ S, int ld, int k, int nb,
                                                               double* __restrict__ inv, unsigned* status) {
   extern __shared__ double potrf_smem[];
   double (*a)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem);
   double (*y)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem + NB * (NB + 1));
-  __shared__ double piv[NB], rdv[NB], rl[NB];  // d_j, 1 / d_j, 1 / sqrt(d_j)
+  __shared__ double piv[NB], rdv[NB], rl[NB], tcol[NB];  // d_j, 1/d_j, 1/sqrt(d_j), t_i
   __shared__ int bad;
-  // 32 row groups x 16 column groups; the 16 lanes of a row group sit in one half-warp
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x;
   for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
     const int i = e % NB, j = e / NB;
     a[i][j] = (i < nb && j < nb && i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : 0.0;
@@ -57,17 +59,24 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict
   }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    const double rd = rdv[j];
-    for (int i0 = j + 1; i0 < nb; i0 += 32) {  // uniform trip count inside each half-warp
-      const int i = i0 + ty;
-      double t = (tx == 0 && i < nb) ? a[i][j] * rd : 0.0;
-      t = __shfl_sync(0xffffffffu, t, threadIdx.x & 16);  // lane 0 or 16 of the warp
-      if (i < nb) {
-        for (int kk = j + 1 + tx; kk <= i; kk += 16) a[i][kk] = fma(-t, a[kk][j], a[i][kk]);
-        for (int c = tx; c <= j; c += 16) y[i][c] = fma(-t, y[j][c], y[i][c]);
+    const int m = nb - j - 1;
+    if (tid < m) tcol[j + 1 + tid] = a[j + 1 + tid][j] * rdv[j];
+    __syncthreads();
+    const int ntri = m * (m + 1) / 2, total = ntri + m * (j + 1);
+    for (int e = tid; e < total; e += POTRF_THREADS) {
+      if (e < ntri) {  // trailing triangle: row r, column c <= r (from the row's start index)
+        int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        if ((r + 1) * (r + 2) / 2 <= e) ++r;
+        if (r * (r + 1) / 2 > e) --r;
+        const int c = e - r * (r + 1) / 2;
+        const int i = j + 1 + r, kk = j + 1 + c;
+        a[i][kk] = fma(-tcol[i], a[kk][j], a[i][kk]);
+      } else {  // inverse rectangle: rows j+1.., columns 0..j
+        const int f = e - ntri, i = j + 1 + f / (j + 1), c = f % (j + 1);
+        y[i][c] = fma(-tcol[i], y[j][c], y[i][c]);
       }
     }
-    // thread 0 updated a[j+1][j+1] above (row group 0, column group 0)
+    // index 0 of the triangle is the next diagonal entry, updated above by thread 0
     if (tid == 0 && j + 1 < nb) set_pivot(j + 1);
     __syncthreads();
   }

@@ -122,6 +122,16 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
                : "r"(taddr));
 }
 
+// Asynchronous 8-byte global -> shared copies (completion tracked per thread by groups).
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Element offset of (r, k) inside an R x 32 tile in the canonical K-major layout
 // [r/8][k/8][r%8][k%8].
 __device__ __forceinline__ int tile_off32(int r, int k) {
@@ -749,7 +759,11 @@ constexpr int UPD_STAGE = UPD_A + UPD_B;
 constexpr int UPD_BAR = 2 * UPD_STAGE;               // full0 full1 empty0 empty1 tfull0 tfull1 tempty0 tempty1
 constexpr int UPD_SLOT = UPD_BAR + 64;
 constexpr int UPD_FLAG = UPD_SLOT + 16;
-constexpr int UPD_SMEM = UPD_FLAG + 16 + 1024;
+// C staging: per epilogue thread two tiles' worth (UPD_COLS values each), slot-major so
+// every thread's cp.async writes and reads hit consecutive 8-byte words
+constexpr int UPD_CBUF = UPD_FLAG + 16;
+constexpr int UPD_SMEM = UPD_CBUF + 2 * UPD_COLS * 32 * UPD_EPI_WARPS * 8 + 1024;
+static_assert(UPD_SMEM <= 227 * 1024, "persistent product exceeds the shared memory of one CTA");
 
 // Epilogue modes, fixed at compile time so no FP64 compare or select runs per element:
 // EMODE 0: C = s * AB (beta = 0);  1: C = C + s * AB (beta = 1);  2: C = beta C + alpha AB.
@@ -854,67 +868,96 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
     const int ew = warp - 2, quarter = warp & 3, part = ew >> 2;
     const int row = quarter * 32 + lane;
     const int col0 = part * UPD_COLS;
+    const int wt = ew * 32 + lane;  // epilogue thread 0..511
     const bool neg_alpha = EMODE != 2 && (__double_as_longlong(alpha) < 0);
-    int tc = 0;
-    double cv[UPD_COLS];  // this thread's C values of its next tile, loaded ahead
-    auto fetch = [&](const OzDesc& d, int bi, int bj) {
-      const int gi = bi * OZ_M + row, gj0 = bj * UPD_NT + col0;
-      const double* cp = d.C + (size_t)gi * d.c_rs + (size_t)gj0 * d.c_cs;
+    double* cbuf = reinterpret_cast<double*>(smem + UPD_CBUF);
+    constexpr int ET = 32 * UPD_EPI_WARPS;
+    // Everything a tile's epilogue reads from memory is requested one tile ahead: the
+    // row / column exponents into registers, the C values by cp.async into shared memory
+    // (one commit group per tile), and the tile-table entry two tiles ahead.  The MMAs run
+    // ahead of the epilogue, so without this the C latency would be exposed on every tile.
+    auto stage = [&](const int4& r, int buf, int& ei, int (&fj)[UPD_COLS]) {
+      const OzDesc& d = descs[r.x];
+      const int gi = r.y * OZ_M + row, gj0 = r.z * UPD_NT + col0;
+      ei = gi < d.M ? d.Ae[gi] : 0;
 #pragma unroll
-      for (int j = 0; j < UPD_COLS; ++j)
-        cv[j] = (EMODE != 0 && gi < d.M && gj0 + j < d.N) ? cp[(size_t)j * d.c_cs] : 0.0;
+      for (int j = 0; j < UPD_COLS; ++j) fj[j] = gj0 + j < d.N ? d.Be[gj0 + j] : 0;
+      if (EMODE != 0 && gi < d.M) {
+        const double* cp = d.C + (size_t)gi * d.c_rs + (size_t)gj0 * d.c_cs;
+#pragma unroll
+        for (int j = 0; j < UPD_COLS; ++j)
+          if (gj0 + j < d.N) cp_async8(smem_u32(cbuf + (buf * UPD_COLS + j) * ET + wt), cp + (size_t)j * d.c_cs);
+      }
+      cp_async_commit();
     };
+    int tc = 0;
     int t = blockIdx.x;
     int4 r = t < total_tiles ? tiles[t] : make_int4(0, 0, 0, 0);
-    if (t < total_tiles) fetch(descs[r.x], r.y, r.z);
+    int4 rn = t + (int)gridDim.x < total_tiles ? tiles[t + gridDim.x] : make_int4(0, 0, 0, 0);
+    int ei = 0, ein = 0, fj[UPD_COLS], fjn[UPD_COLS];
+#pragma unroll
+    for (int j = 0; j < UPD_COLS; ++j) { fj[j] = 0; fjn[j] = 0; }
+    if (t < total_tiles) stage(r, 0, ei, fj);
     while (t < total_tiles) {
       const OzDesc& d = descs[r.x];
-      const int tn = t + gridDim.x;  // next tile of this CTA: its entry is read ahead
-      const int4 rn = tn < total_tiles ? tiles[tn] : make_int4(0, 0, 0, 0);
+      const int tn = t + gridDim.x, tnn = tn + gridDim.x;
+      const int4 rnn = tnn < total_tiles ? tiles[tnn] : make_int4(0, 0, 0, 0);
+      if (tn < total_tiles) stage(rn, (tc + 1) & 1, ein, fjn);
       const int buf = tc & 1;
       if (!mbar_wait_warp(TFULL + 8 * buf, (tc >> 1) & 1)) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      uint32_t v[OZ_G][8];
       const uint32_t lb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (OZ_G * UPD_NT) + col0;
-#pragma unroll
-      for (int g = 0; g < OZ_G; ++g) tmem_ld8(lb + g * UPD_NT, v[g]);
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      mbar_arrive(TEMPTY + 8 * buf);  // accumulators copied: the MMA may reuse this buffer
-      ++tc;
+      if (tn < total_tiles) cp_async_wait<1>();  // this tile's C group is complete
+      else cp_async_wait<0>();
       const int gi = r.y * OZ_M + row, gj0 = r.z * UPD_NT + col0;
-      if (gi < d.M) {
-        const int ei = d.Ae[gi];
-        double* cp = d.C + (size_t)gi * d.c_rs + (size_t)gj0 * d.c_cs;
-        const int* be = d.Be + gj0;
+      double* cp = d.C + (size_t)gi * d.c_rs + (size_t)gj0 * d.c_cs;
+      // two halves of 4 columns keep the TMEM copies at 28 registers
 #pragma unroll
-        for (int j = 0; j < UPD_COLS; ++j) {
-          if (gj0 + j < d.N) {
-            int a[OZ_G];
+      for (int half = 0; half < 2; ++half) {
+        uint32_t v[OZ_G][4];
 #pragma unroll
-            for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][j]));
-            const long long H = ((long long)a[0] << 24) + ((long long)a[1] << 16) + ((long long)a[2] << 8);
-            const long long Lw =
-                ((long long)a[3] << 24) + ((long long)a[4] << 16) + ((long long)a[5] << 8) + a[6];
-            const int fj = be[j];
-            double pv = 0.0;
-            if (ei != 0 && fj != 0) {
-              const int k = ei + fj - 2044 - 62;
-              pv = i64_to_double_pow2(H, k + 24, neg_alpha) + i64_to_double_pow2(Lw, k, neg_alpha);
+        for (int g = 0; g < OZ_G; ++g) tmem_ld4(lb + g * UPD_NT + half * 4, v[g]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (half == 1) {
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(TEMPTY + 8 * buf);  // accumulators copied: the MMA may reuse this buffer
+        }
+        if (gi < d.M) {
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = half * 4 + jj;
+            if (gj0 + j < d.N) {
+              int a[OZ_G];
+#pragma unroll
+              for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][jj]));
+              const long long H = ((long long)a[0] << 24) + ((long long)a[1] << 16) + ((long long)a[2] << 8);
+              const long long Lw =
+                  ((long long)a[3] << 24) + ((long long)a[4] << 16) + ((long long)a[5] << 8) + a[6];
+              double pv = 0.0;
+              if (ei != 0 && fj[j] != 0) {
+                const int k = ei + fj[j] - 2044 - 62;
+                pv = i64_to_double_pow2(H, k + 24, neg_alpha) + i64_to_double_pow2(Lw, k, neg_alpha);
+              }
+              const double cv = EMODE != 0 ? cbuf[(buf * UPD_COLS + j) * ET + wt] : 0.0;
+              double out;
+              if (EMODE == 0) out = pv;
+              else if (EMODE == 1) out = cv + pv;
+              else out = fma(beta, cv, alpha * pv);
+              if (IDENT && gi == gj0 + j) out += 1.0;
+              cp[(size_t)j * d.c_cs] = out;
             }
-            double out;
-            if (EMODE == 0) out = pv;
-            else if (EMODE == 1) out = cv[j] + pv;
-            else out = fma(beta, cv[j], alpha * pv);
-            if (IDENT && gi == gj0 + j) out += 1.0;
-            cp[(size_t)j * d.c_cs] = out;
           }
         }
       }
-      if (tn < total_tiles) fetch(descs[rn.x], rn.y, rn.z);  // loads while the next MMAs run
+      ++tc;
       t = tn;
       r = rn;
+      rn = rnn;
+      ei = ein;
+#pragma unroll
+      for (int j = 0; j < UPD_COLS; ++j) fj[j] = fjn[j];
     }
+    cp_async_wait<0>();  // no copy may land after this thread has left
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
