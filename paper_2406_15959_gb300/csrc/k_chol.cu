@@ -22,62 +22,75 @@ constexpr int NB = CHOL_NB;
 // and x_rc = y_rc / l_rr.
 //
 // FP64 arithmetic is the scarce resource (2 FMA per clock per SM, and a warp-wide FMA
-// occupies the pipe whatever its active lanes), so nothing is computed redundantly and the
-// updates of a step are flattened: the m(m+1)/2 entries of the trailing triangle
-// (m = nb - j - 1) and the m (j+1) entries of the inverse's rectangle form one index range
-// dealt out to consecutive threads, so every warp-wide FMA has 32 active lanes.  The row
-// multipliers t_i are formed once per row (first barrier); the thread that updates the
-// next diagonal entry forms its reciprocal before the second barrier.
+// occupies the pipe whatever its active lanes), and the pivot reciprocal is a long
+// dependent chain.  So step j is split between a look-ahead warp and the rest:
+//   warp 0:      updates column j+1 (the next pivot column), forms d_{j+1}, its
+//                reciprocal and the next multipliers t^(j+1) (double-buffered);
+//   warps 1..15: the rest of the trailing triangle (columns > j+1) and the inverse's
+//                rectangle, flattened into one index range so every warp-wide FMA has 32
+//                active lanes.
+// One barrier per column; the reciprocal's latency hides behind the bulk update.
 constexpr int POTRF_THREADS = 512;
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict__ S, int ld, int k, int nb,
                                                               double* __restrict__ inv, unsigned* status) {
   extern __shared__ double potrf_smem[];
   double (*a)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem);
   double (*y)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem + NB * (NB + 1));
-  __shared__ double piv[NB], rdv[NB], rl[NB], tcol[NB];  // d_j, 1/d_j, 1/sqrt(d_j), t_i
+  __shared__ double piv[NB], rl[NB], tcol[2][NB];  // d_j, 1/sqrt(d_j), t^(j) (by parity of j)
   __shared__ int bad;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int BULK = POTRF_THREADS - 32;
   for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
     const int i = e % NB, j = e / NB;
     a[i][j] = (i < nb && j < nb && i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : 0.0;
     y[i][j] = (i == j) ? 1.0 : 0.0;
   }
+  if (tid == 0) bad = 0;
   __syncthreads();
-  // a pivot that is not positive (not SPD) is flagged and replaced by 1 so the loop ends
-  auto set_pivot = [&](int j) {
-    double d = a[j][j];
-    if (!(d > 0.0) || !isfinite(d)) {
-      bad = 1;
-      d = 1.0;
+  // warp 0: pivot d_c (column c already final), its multipliers into tcol[c & 1].  A pivot
+  // that is not positive (not SPD) is flagged and replaced by 1 so the loop ends.
+  auto pivot_column = [&](int c) {
+    double rd = 0.0;
+    if (lane == 0) {
+      double d = a[c][c];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+        d = 1.0;
+      }
+      piv[c] = d;
+      rd = 1.0 / d;
     }
-    piv[j] = d;
-    rdv[j] = 1.0 / d;
+    rd = __shfl_sync(0xffffffffu, rd, 0);
+    for (int i = c + 1 + lane; i < nb; i += 32) tcol[c & 1][i] = a[i][c] * rd;
   };
-  if (tid == 0) {
-    bad = 0;
-    if (nb > 0) set_pivot(0);
-  }
+  if (warp == 0 && nb > 0) pivot_column(0);
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
+    const double* t = tcol[j & 1];
     const int m = nb - j - 1;
-    if (tid < m) tcol[j + 1 + tid] = a[j + 1 + tid][j] * rdv[j];
-    __syncthreads();
-    const int ntri = m * (m + 1) / 2, total = ntri + m * (j + 1);
-    for (int e = tid; e < total; e += POTRF_THREADS) {
-      if (e < ntri) {  // trailing triangle: row r, column c <= r (from the row's start index)
-        int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-        if ((r + 1) * (r + 2) / 2 <= e) ++r;
-        if (r * (r + 1) / 2 > e) --r;
-        const int c = e - r * (r + 1) / 2;
-        const int i = j + 1 + r, kk = j + 1 + c;
-        a[i][kk] = fma(-tcol[i], a[kk][j], a[i][kk]);
-      } else {  // inverse rectangle: rows j+1.., columns 0..j
-        const int f = e - ntri, i = j + 1 + f / (j + 1), c = f % (j + 1);
-        y[i][c] = fma(-tcol[i], y[j][c], y[i][c]);
+    if (warp == 0) {
+      if (m > 0) {
+        for (int i = j + 1 + lane; i < nb; i += 32) a[i][j + 1] = fma(-t[i], a[j + 1][j], a[i][j + 1]);
+        __syncwarp();
+        pivot_column(j + 1);
+      }
+    } else {
+      // triangle of columns j+2.. (size m-1), then rectangle rows j+1.., columns 0..j
+      const int tri = m > 0 ? (m - 1) * m / 2 : 0, total = tri + m * (j + 1);
+      for (int e = tid - 32; e < total; e += BULK) {
+        if (e < tri) {
+          int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+          if ((r + 1) * (r + 2) / 2 <= e) ++r;
+          if (r * (r + 1) / 2 > e) --r;
+          const int c = e - r * (r + 1) / 2;
+          const int i = j + 2 + r, kk = j + 2 + c;
+          a[i][kk] = fma(-t[i], a[kk][j], a[i][kk]);
+        } else {
+          const int f = e - tri, i = j + 1 + f / (j + 1), c = f % (j + 1);
+          y[i][c] = fma(-t[i], y[j][c], y[i][c]);
+        }
       }
     }
-    // index 0 of the triangle is the next diagonal entry, updated above by thread 0
-    if (tid == 0 && j + 1 < nb) set_pivot(j + 1);
     __syncthreads();
   }
   if (tid < nb) rl[tid] = 1.0 / sqrt(piv[tid]);
