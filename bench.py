@@ -34,7 +34,11 @@ METRIC = "ELM-DDM solves/sec & ms/solve at stated rel-L2 vs FP64 oracle; % of ro
 WORKLOAD = "poisson_8x8_n1000"
 # FP64 FMA pipe of GB300: 152 SMs x 2 FP64 FMA/clk (4 flop/clk) x 2.07 GHz.
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07
+# classes whose kernel runs as one CTA (their roofline is one SM's FP64 pipe)
+SINGLE_CTA_CLASSES = ("potrf",)
 KERNEL_OF_CLASS = {
+    "panel_qr": "k_panel_qr_cl (Householder panel of 32 columns, 4-CTA cluster per subdomain, FP64 pipe)",
+    "potrf": "k_potrf_diag (64x64 diagonal Cholesky + inverse, one CTA, FP64 pipe)",
     "oz_qr_update": "k_ozaki_upd (persistent tensor-core FP64 product: A2 -= V W2 of every QR panel)",
     "oz_qr_w": "k_ozaki_fa (tensor-core FP64 product with fused digit split: W1^T = A2^T V of every QR panel)",
     "oz_syrk": "k_ozaki_upd (persistent tensor-core FP64 product: Schur Cholesky SYRK)",
@@ -253,8 +257,33 @@ def run_ours(args):
         step(d["W"], d["b"], d["rhs"])
     s.check()
 
-    # ---- device-resident timed region (with per-launch events for the roofline)
+    # ---- one profiled step (not timed): per-class device times and the dominant class
+    hbm_peak, hbm_src = measured_hbm_peak()
     s.profile(True)
+    s.profile_report()
+    step(d["W"], d["b"], d["rhs"])
+    prof1 = s.profile_report()
+    s.profile(False)
+    classes = {k: v for k, v in prof1.items() if not k.startswith("_")}
+
+    def roof(k, v, ms):
+        if k.startswith("oz_") or k.startswith("split"):
+            ach = v["bytes"] / (ms * 1e-3) / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ach / hbm_peak}
+        if v["flops"] > 0:
+            ach = v["flops"] / (ms * 1e-3) / 1e9
+            peak = FP64_PEAK_GFLOPS / 152 if k in SINGLE_CTA_CLASSES else FP64_PEAK_GFLOPS
+            return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "GFLOP/s",
+                    "frac": ach / peak}
+        return None
+
+    roof_all = {k: r for k, v in classes.items() if v["ms"] > 0 for r in [roof(k, v, v["ms"])] if r}
+    dom = max(roof_all, key=lambda k: classes[k]["ms"]) if roof_all else None
+
+    # ---- device-resident timed region: CUDA events around the whole steps, and around
+    # the dominant class's launches only (its live average launch time gives `achieved`)
+    s.profile(True, only=dom)
     s.profile_report()
     clocks = ClockSampler(torch.cuda.current_device() if ws == 1 else local)
     clocks.start()
@@ -307,26 +336,12 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel class (by device time in the timed region)
-    hbm_peak, hbm_src = measured_hbm_peak()
-    classes = {k: v for k, v in prof.items() if not k.startswith("_")}
-    roof_all = {}
-    for k, v in classes.items():
-        if v["ms"] <= 0:
-            continue
-        if k.startswith("oz_") or k.startswith("split"):
-            ach = v["bytes"] / (v["ms"] * 1e-3) / 1e9
-            roof_all[k] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                           "frac": ach / hbm_peak}
-        elif v["flops"] > 0:
-            ach = v["flops"] / (v["ms"] * 1e-3) / 1e9
-            roof_all[k] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS,
-                           "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS}
-    dom = max(roof_all, key=lambda k: classes[k]["ms"]) if roof_all else None
+    # ---- roofline of the dominant kernel class (by device time), measured live in the
+    # timed region; every class from the profiled step in roofline_by_class
     roofline = None
-    if dom:
-        v = classes[dom]
-        roofline = dict(roof_all[dom])
+    if dom and dom in prof:
+        v = prof[dom]
+        roofline = roof(dom, v, v["ms"])
         roofline.update({
             "traffic": None, "kernel_class": dom,
             "kernel": KERNEL_OF_CLASS.get(dom, dom),
@@ -336,8 +351,7 @@ def run_ours(args):
                            "bytes": v["bytes"] / max(v["launches"], 1)},
             "peak_source": (hbm_src if roofline["bound"] == "hbm" else
                             "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz (recipe units/clock)")})
-    step_ms_breakdown = {k: round(v["ms"] / args.steps, 3) for k, v in sorted(prof.items())
-                         if not k.startswith("_")}
+    step_ms_breakdown = {k: round(v["ms"], 3) for k, v in sorted(classes.items())}
 
     # ---- CPU oracle: parity of this result and the timed baseline
     cpu = None
@@ -369,6 +383,8 @@ def run_ours(args):
         "roofline": roofline,
         "roofline_by_class": roof_all,
         "step_ms_by_kernel_class": step_ms_breakdown,
+        "breakdown_note": ("step_ms_by_kernel_class and roofline_by_class come from one extra "
+                           "profiled step (every launch bracketed by events), not the timed region"),
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

@@ -193,6 +193,14 @@ int elm_ddm_profile(elm_ddm_handle* h, int enable);
 int elm_ddm_profile_report(elm_ddm_handle* h, char* buf, int buflen);
 
 /*
+ * Restrict per-launch profiling to one kernel class (the names elm_ddm_profile_report
+ * prints; NULL or "" restores all classes), so that a timed region can measure one class's
+ * launches without bracketing every other launch with events.  Host-only; the paper has
+ * no counterpart (measurement support).  Returns ELM_DDM_ERR_ARG for a NULL handle.
+ */
+int elm_ddm_profile_only(elm_ddm_handle* h, const char* kernel_class);
+
+/*
  * No-allocation Cholesky solve.  The paper has no counterpart: this entry point exists
  * for callers that cannot call cudaMalloc -- code running while a CUDA graph is being
  * captured in global mode, hosts that route all device memory through their own pool

@@ -129,6 +129,9 @@ struct elm_ddm_handle {
   bool emulated = true;          // FP64 products on the tensor cores (digit split)
   void* sp_buf = nullptr;        // digit tiles and row exponents of the split operands
   std::vector<int> qr_first;     // first record of each panel in qr_recs
+  // algorithmic flops of each Householder panel launch: per subdomain a m' x nb panel
+  // (2 m' nb^2 - 2 nb^3 / 3) and its compact-WY factor T (m' nb^2)
+  std::vector<double> panel_flops;
   std::vector<int> syrk_first;   // first record of each Cholesky step in syrk_recs
   size_t mdiag_elems = 0;
   // plans
@@ -138,6 +141,7 @@ struct elm_ddm_handle {
   std::vector<LaunchRec> syrk_recs;  // one per Cholesky block step
   int state = 0;
   bool profiling = false;
+  std::string prof_only;  // non-empty: profile launches of this class only
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<ProfRec> prof;
@@ -197,14 +201,15 @@ struct ProfScope {
   double flops, bytes;
   ProfScope(elm_ddm_handle* h_, const char* n, double f, double by = 0.0)
       : h(h_), name(n), flops(f), bytes(by) {
-    if (h->profiling) {
+    if (h->profiling && (h->prof_only.empty() || h->prof_only == name)) {
       a = next_event(h);
       if (a) cudaEventRecord(a, h->st);
+      else h->prof_dropped++;
     }
   }
   ~ProfScope() {
-    if (!h->profiling) return;
-    cudaEvent_t b = a ? next_event(h) : nullptr;
+    if (!a) return;
+    cudaEvent_t b = next_event(h);
     if (!b) { h->prof_dropped++; return; }
     cudaEventRecord(b, h->st);
     h->prof.push_back({a, b, name, flops, bytes});
@@ -615,6 +620,12 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   };
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, n - k0);
+    double pf = 0.0;
+    for (int s = 0; s < N; ++s) {
+      const double mp = std::max(0, h->ms_h[s] - k0);
+      pf += 3.0 * mp * nbe * nbe - 2.0 * nbe * (double)nbe * nbe / 3.0;
+    }
+    h->panel_flops.push_back(pf);
     std::vector<GemmDesc> g1, g2, g3;
     std::vector<SplitDesc> sp1, sp3;
     std::vector<OzDesc> o1, o3;
@@ -929,9 +940,9 @@ int elm_ddm_schur(elm_ddm_handle* h) {
   // (b) blocked Householder QR of [K^s | J]
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, h->n - k0);
-    ELM_LAUNCH(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->T +
-                                  (size_t)b * QR_NB * QR_NB, h->tstride, h->Vp, h->vstride, h->status,
-                                  h->st), "panel_qr");
+    ELM_LAUNCH_F(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->T +
+                                    (size_t)b * QR_NB * QR_NB, h->tstride, h->Vp, h->vstride, h->status,
+                                    h->st), "panel_qr", h->panel_flops[b]);
     int rc = run_recs(h, h->qr_recs, h->qr_first[b], h->qr_first[b + 1] - h->qr_first[b],
                       "gemm_qr");
     if (rc) return rc;
@@ -955,8 +966,9 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     if (rc) return rc;
     for (int k = 0, step = 0; k < h->ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, h->ng - k);
-      ELM_LAUNCH(h, launch_potrf_diag(h->S, h->ng, k, nb, h->cinv + (size_t)step * CHOL_NB * CHOL_NB,
-                                      h->status, h->st), "potrf");
+      // nb^3/3 for the factor and as much again for its inverse
+      ELM_LAUNCH_F(h, launch_potrf_diag(h->S, h->ng, k, nb, h->cinv + (size_t)step * CHOL_NB * CHOL_NB,
+                                        h->status, h->st), "potrf", 2.0 * nb * nb * (double)nb / 3.0);
       if (h->chol_rend[step] - k - nb > 0) {
         rc = run_recs(h, h->trsm_recs, h->trsm_first[step],
                       h->trsm_first[step + 1] - h->trsm_first[step], "trsm_chol");
@@ -1072,6 +1084,12 @@ int elm_ddm_interface_order(const elm_ddm_handle* h, int32_t* order) {
 int elm_ddm_profile(elm_ddm_handle* h, int enable) {
   if (!h) return ELM_DDM_ERR_ARG;
   h->profiling = enable != 0;
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_profile_only(elm_ddm_handle* h, const char* kernel_class) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  h->prof_only = kernel_class ? kernel_class : "";
   return ELM_DDM_OK;
 }
 

@@ -23,7 +23,8 @@ ERROR_NAMES = {ERR_ARG: "ERR_ARG", ERR_STATE: "ERR_STATE", ERR_CUDA: "ERR_CUDA",
 SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve",
            "elm_ddm_eval", "elm_ddm_export", "elm_ddm_check", "elm_ddm_get_info",
            "elm_ddm_profile", "elm_ddm_profile_report", "elm_ddm_destroy",
-           "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order")
+           "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order",
+           "elm_ddm_profile_only")
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
 
 
@@ -68,6 +69,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_check.argtypes = [P]
     lib.elm_ddm_interface_order.argtypes = [P, P]
     lib.elm_ddm_profile.argtypes = [P, I]
+    lib.elm_ddm_profile_only.argtypes = [P, ctypes.c_char_p]
     lib.elm_ddm_profile_report.argtypes = [P, ctypes.c_char_p, I]
     lib.elm_ddm_get_info.argtypes = [P, I, D]
     lib.elm_ddm_destroy.argtypes = [P]
@@ -207,7 +209,9 @@ class Solver:
         self._check_rc(self.lib.elm_ddm_interface_order(self.h, order.ctypes.data))
         return order[:self.n_gamma]
 
-    def profile(self, enable: bool = True):
+    def profile(self, enable: bool = True, only: str | None = None):
+        """Per-launch event timing on (optionally of one kernel class only) or off."""
+        self._check_rc(self.lib.elm_ddm_profile_only(self.h, only.encode() if only else None))
         self._check_rc(self.lib.elm_ddm_profile(self.h, int(enable)))
 
     def profile_report(self) -> dict:
