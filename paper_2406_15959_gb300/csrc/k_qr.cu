@@ -427,6 +427,16 @@ __global__ void __launch_bounds__(256) k_backsolve(const double* __restrict__ X,
 constexpr int PCL = 4;     // CTAs per cluster
 constexpr int PLD = 33;    // shared-memory row stride of the panel chunk (doubles)
 
+// Householder panel of nbe <= 32 columns [k0, k0+nbe) of subdomain s, rows split over a
+// cluster of PCL CTAs (rows k0 + q*rows_per .. in CTA q, held in shared memory).  Column j
+// takes one fused reduction: every thread sums x_r a_k(r) over its rows strictly below the
+// diagonal row c = k0 + j for all 32 columns k (the k = j slot is sigma = |x_below|^2), and
+// the owner of row c contributes a_k(c).  After one cluster barrier every quantity is local:
+//   beta = -sign(alpha) sqrt(alpha^2 + sigma),  tau = (beta - alpha) / beta,
+//   v = (x - beta e_c) / (alpha - beta),  v^T a_k = a_k(c) + y_k / (alpha - beta),
+// which gives the trailing update a_k -= tau v (v^T a_k) and, for l < j, the products
+// v_l^T v_j that build T (compact WY, I - V T V^T).  Rows stay with their threads, so the
+// update needs no barrier before the next column's sums: three barriers per column.
 __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
     k_panel_qr_cl(double* __restrict__ K, long long kstride, int ld, const int* __restrict__ ms_arr,
                   int k0, int nbe, double* __restrict__ tau_out, int n, double* __restrict__ Tout,
@@ -442,10 +452,10 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
   const int r0 = k0 + q * rows_per;                     // first global row of this chunk
   const int nr = max(0, min(rows_per, m - r0));         // rows held here
   extern __shared__ double P[];                         // [rows_per][PLD]
-  __shared__ double red[2][40];                         // [parity]: 0..31 dots, 32 norm, 33 alpha
-  __shared__ double bred[33];
-  __shared__ double wred[8][32];
-  __shared__ double d[32];
+  __shared__ double red[2][64];                         // [parity]: y_k (sigma at j), a_k(c)
+  __shared__ double wred[8][33];
+  __shared__ double dsh[32];                            // v^T a_k (k > j), v_l^T v_j (l < j)
+  __shared__ double coef[2];                            // tau, 1 / (alpha - beta)
   __shared__ double T[32][33];
   __shared__ double stau[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -460,89 +470,82 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
     const int c = k0 + j;
     const int cl = c - r0;                   // local row of c (valid if 0 <= cl < nr)
     const bool own_c = cl >= 0 && cl < nr;
-    const int rs = max(0, c + 1 - r0);       // first local row below the diagonal
-    double p = 0.0;
-    for (int r = rs + tid; r < nr; r += 256) {
-      const double v = P[r * PLD + j];
-      p = fma(v, v, p);
-    }
-    p = block_sum(p, bred);
-    if (tid == 0) {
-      red[par][32] = p;
-      red[par][33] = own_c ? P[cl * PLD + j] : 0.0;
-    }
-    cluster.sync();
-    double ss = 0.0, alpha = 0.0;
-#pragma unroll
-    for (int qq = 0; qq < PCL; ++qq) {
-      const double* rr = cluster.map_shared_rank(&red[par][0], qq);
-      ss += rr[32];
-      alpha += rr[33];
-    }
-    double beta, tau, scal;
-    if (ss == 0.0) {
-      tau = 0.0; beta = alpha; scal = 1.0;
-    } else {
-      beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
-      tau = (beta - alpha) / beta;
-      scal = 1.0 / (alpha - beta);
-    }
-    if (tid == 0 && q == 0) {
-      if (beta == 0.0) bits |= ST_RANK;
-      if (!isfinite(beta)) bits |= ST_NONFINITE;
-    }
-    if (ss != 0.0)
-      for (int r = rs + tid; r < nr; r += 256) P[r * PLD + j] *= scal;
-    __syncthreads();
     double acc[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc[k] = 0.0;
-    for (int r = rs + tid; r < nr; r += 256) {
-      const double v = P[r * PLD + j];
+    for (int r = tid; r < nr; r += 256) {
+      if (r0 + r <= c) continue;
       const double* row = P + r * PLD;
+      const double x = row[j];
 #pragma unroll
       for (int k = 0; k < 32; ++k)
-        if (k < nbe && k != j) acc[k] = fma(v, row[k], acc[k]);
+        if (k < nbe) acc[k] = fma(x, row[k], acc[k]);
     }
     const double ws = warp_transpose_sum32(acc);
     wred[warp][lane] = ws;
     __syncthreads();
-    if (tid < 32) {
+    if (warp == 0) {
       double t = 0.0;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) t += wred[w][tid];
-      if (own_c && tid < nbe && tid != j) t += P[cl * PLD + tid];
-      red[par][tid] = t;
+      for (int w = 0; w < 8; ++w) t += wred[w][lane];
+      red[par][lane] = t;
+      red[par][32 + lane] = (own_c && lane < nbe) ? P[cl * PLD + lane] : 0.0;
     }
     cluster.sync();
-    if (tid < 32) {
-      double t = 0.0;
+    if (warp == 0) {
+      double y = 0.0, rc = 0.0;
 #pragma unroll
-      for (int qq = 0; qq < PCL; ++qq) t += cluster.map_shared_rank(&red[par][0], qq)[tid];
-      d[tid] = t;
+      for (int qq = 0; qq < PCL; ++qq) {
+        const double* rr = cluster.map_shared_rank(&red[par][0], qq);
+        y += rr[lane];
+        rc += rr[32 + lane];
+      }
+      const double alpha = __shfl_sync(0xffffffffu, rc, j);
+      const double ss = __shfl_sync(0xffffffffu, y, j);
+      double beta, tau, scal;
+      if (ss == 0.0) {
+        tau = 0.0; beta = alpha; scal = 1.0;
+      } else {
+        beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      dsh[lane] = fma(scal, y, rc);
+      __syncwarp();
+      if (lane < j) {
+        double t = 0.0;
+        for (int l = lane; l < j; ++l) t = fma(T[lane][l], dsh[l], t);
+        T[lane][j] = -tau * t;
+      }
+      if (lane == 0) {
+        coef[0] = tau;
+        coef[1] = scal;
+        T[j][j] = tau;
+        stau[j] = tau;
+        if (q == 0) {
+          if (beta == 0.0) bits |= ST_RANK;
+          if (!isfinite(beta)) bits |= ST_NONFINITE;
+        }
+      }
+      if (own_c && lane == 0) P[cl * PLD + j] = beta;  // row c: R_jj (read as alpha above)
+      // keep beta for the owner thread's update below through the stored value
     }
     __syncthreads();
-    if (tau != 0.0) {
-      const int ru = max(0, c - r0);
-      for (int r = ru + tid; r < nr; r += 256) {
-        const double tv = tau * ((r0 + r == c) ? 1.0 : P[r * PLD + j]);
-        double* row = P + r * PLD;
-        for (int k = j + 1; k < nbe; ++k) row[k] = fma(-tv, d[k], row[k]);
+    const double tau = coef[0], scal = coef[1];
+    for (int r = tid; r < nr; r += 256) {
+      const int gr = r0 + r;
+      if (gr < c) continue;
+      double* row = P + r * PLD;
+      const double v = gr == c ? 1.0 : row[j] * scal;
+      if (gr > c) row[j] = v;
+      if (tau != 0.0) {
+        const double tv = tau * v;
+        for (int k = j + 1; k < nbe; ++k) row[k] = fma(-tv, dsh[k], row[k]);
       }
     }
-    if (tid < j) {
-      double t = 0.0;
-      for (int l = tid; l < j; ++l) t = fma(T[tid][l], d[l], t);
-      T[tid][j] = -tau * t;
-    }
-    if (tid == 0) {
-      T[j][j] = tau;
-      stau[j] = tau;
-      if (own_c) P[cl * PLD + j] = beta;
-    }
-    __syncthreads();
     par ^= 1;
   }
+  __syncthreads();
 
   for (int k = 0; k < nbe; ++k)
     for (int r = tid; r < nr; r += 256) A[(r0 + r) + (size_t)(k0 + k) * ld] = P[r * PLD + k];
