@@ -863,7 +863,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
                                    {cinv, 1, CHOL_NB, nb, nb, x3, t3, 32}};
         add_split_rec(h->trsm_recs, spt, "split_trsm");
         add_oz_rec(h->trsm_recs, {{chol_region, xa, t3, x3, L21, 1, ng, rest, nb, nb, 0}}, 0, 1.0, 0.0,
-                   0, "trsm_chol");
+                   0, "oz_trsm_chol");
         std::vector<SplitDesc> sp{{L21, 1, ng, rest, nb, xa, chol_region, 128},
                                   {L21, 1, ng, rest, nb, xb, chol_region + c1, 32}};
         add_split_rec(h->syrk_recs, sp, "split_syrk");
@@ -971,7 +971,7 @@ int elm_ddm_schur(elm_ddm_handle* h) {
                                         h->status, h->st), "potrf", 2.0 * nb * nb * (double)nb / 3.0);
       if (h->chol_rend[step] - k - nb > 0) {
         rc = run_recs(h, h->trsm_recs, h->trsm_first[step],
-                      h->trsm_first[step + 1] - h->trsm_first[step], "trsm_chol");
+                      h->trsm_first[step + 1] - h->trsm_first[step], "oz_trsm_chol");
         if (rc) return rc;
         rc = run_recs(h, h->syrk_recs, h->syrk_first[step],
                       h->syrk_first[step + 1] - h->syrk_first[step], "gemm_syrk");
