@@ -56,11 +56,16 @@ extern "C" {
 #define ELM_DDM_ERR_RANK      6  /* some R^s has an exactly zero diagonal entry */
 #define ELM_DDM_ERR_NOT_SPD   7  /* a Cholesky pivot of the Schur matrix was <= 0 */
 #define ELM_DDM_ERR_CAPACITY  8  /* request larger than a no-allocation entry point's fixed scratch */
+#define ELM_DDM_ERR_NOCONV    9  /* elm_ddm_solve_cg: tolerance not reached (outputs hold the last iterate) */
 
 /* elm_ddm_desc.flags */
 #define ELM_DDM_FLAG_FP64_SIMT 1  /* run every dense update on the FP64 pipe (default: the
                                      large ones as FP64-accurate digit-split products on the
                                      BF16 tensor cores) */
+#define ELM_DDM_FLAG_SCHUR_CG  2  /* the paper's interface solve only: elm_ddm_schur stops
+                                     after D_s and M_s, the Schur matrix is neither formed
+                                     nor factored (no n_gamma^2 workspace); solve with
+                                     elm_ddm_solve_cg (elm_ddm_solve returns ERR_STATE) */
 
 /* Differential operators. */
 #define ELM_DDM_OP_POISSON 0  /* L = -Laplacian (Eq. (4.4)) */
@@ -126,6 +131,23 @@ int elm_ddm_schur(elm_ddm_handle* h);
  * Requires elm_ddm_schur.  1 <= nrhs <= desc->max_rhs.
  */
 int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c);
+
+/*
+ * The paper's interface solve (Section 4: the Schur system of Eq. (3.5) by conjugate
+ * gradients to a relative residual): as elm_ddm_solve, but u_Gamma comes from
+ * unpreconditioned CG started at zero, with S applied from the stored local pieces,
+ * S p = sum_s E_s^T D_s E_s p + M^T (M p), M p = sum_s E_s^T M_s E_s p (never formed).
+ * Every right-hand side stops once |r| <= tol |rhs|.
+ *   tol    relative residual, finite and > 0 (the paper uses 1e-9)
+ *   maxit  iteration limit, >= 1
+ *   iters  host int (may be NULL): the largest number of CG steps any right-hand side took
+ * Synchronises with the host every 16 steps to test convergence.  Returns ELM_DDM_OK, or
+ * ELM_DDM_ERR_NOCONV when some right-hand side did not reach tol within maxit steps (or
+ * CG broke down: p^T S p <= 0); its outputs then hold the last iterate.  Works after
+ * elm_ddm_schur with or without ELM_DDM_FLAG_SCHUR_CG.
+ */
+int elm_ddm_solve_cg(elm_ddm_handle* h, const double* rhs, int nrhs, double tol, int maxit,
+                     double* u_gamma, double* c, int* iters);
 
 /*
  * u(x) = sum_j c^s_j tanh(w^s_j . x + b^s_j) and grad u at npts points, s = owner[i].

@@ -191,6 +191,32 @@ def solve(geom, W, b, rhs_rows, keep=True):
     return Result(u, c, S, r, ratio, locs if keep else [])
 
 
+def cg_solve(S, rhs, tol, maxit):
+    """Conjugate gradients (Hestenes and Stiefel) for the SPD interface system S u = rhs,
+    the solver the paper uses for Eq. (3.5) (Section 4: stopped at a relative residual
+    of 1e-9).  Unpreconditioned, started at u = 0, stopped at the first step with
+    |r| <= tol |rhs|.  Returns (u, steps, converged)."""
+    b = np.asarray(rhs, dtype=np.float64)
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    target = tol * tol * rr
+    if rr == 0.0:
+        return x, 0, True
+    for k in range(1, maxit + 1):
+        q = S @ p
+        alpha = rr / float(p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = float(r @ r)
+        if rr_new <= target:
+            return x, k, True
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x, maxit, False
+
+
 def evaluate(W, b, c, xy, owner):
     """u(x) = sum_j c^s_j tanh(w^s_j . x + b^s_j) and grad u, s = owner of x."""
     u = np.zeros(len(xy))

@@ -60,6 +60,13 @@ struct OzDesc {
   long long a_rs;  // fused-split launches: At is the FP64 A, element (i, k) at At[i * a_rs + k]
 };
 
+// Per right-hand side state of the CG solve of the Schur system (k_cg.cu).
+struct CgState {
+  double rr, bb;  // r^T r of the current residual, b^T b
+  int iters;      // CG steps taken
+  int done;       // 0 running, 1 converged, 2 breakdown (p^T S p <= 0 or not finite)
+};
+
 // ---- launchers (return cudaGetLastError after the launch) ----
 int oz_tiles(int m, int n, int nt);
 size_t oz_split_elems(int R, int K, int row_tile);
@@ -133,6 +140,15 @@ cudaError_t launch_chol_bwd(const double* L, int ld, int n, int k, int nb, doubl
                             const double* Linv = nullptr);
 cudaError_t launch_gather_perm(const int* idx, int n, const double* src, double* dst, int nrhs,
                                cudaStream_t st);
+// q = S p without forming S (zl, wl: [nrhs][N][mgld] scratch, wg: [nrhs][ng] scratch).
+cudaError_t launch_schur_apply(const double* D, const double* M, long long mstride, int mgld,
+                               const int* mg, int mgmax, const int* ifc_dof, const int* dofmap,
+                               const double* p, double* q, double* zl, double* wl, double* wg,
+                               int ng, int N, int nrhs, cudaStream_t st);
+cudaError_t launch_cg_init(const double* b, double* x, double* r, double* p, CgState* state, int ng,
+                           int nrhs, cudaStream_t st);
+cudaError_t launch_cg_update(double* x, double* r, double* p, const double* q, CgState* state, int ng,
+                             int nrhs, double tol2, cudaStream_t st);
 
 // ---- device helpers ----
 #ifdef __CUDACC__

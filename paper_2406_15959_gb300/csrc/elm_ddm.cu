@@ -127,6 +127,9 @@ struct elm_ddm_handle {
   OzDesc* od = nullptr;
   int4* ut = nullptr;  // tile tables of the persistent launches
   bool emulated = true;          // FP64 products on the tensor cores (digit split)
+  bool cg_only = false;          // S is neither formed nor factored (elm_ddm_solve_cg only)
+  double *cg_p = nullptr, *cg_q = nullptr;  // CG search direction and S p, [max_rhs][ng]
+  CgState* cg_st = nullptr;                 // [max_rhs]
   void* sp_buf = nullptr;        // digit tiles and row exponents of the split operands
   std::vector<int> qr_first;     // first record of each panel in qr_recs
   // algorithmic flops of each Householder panel launch: per subdomain a m' x nb panel
@@ -285,7 +288,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const int max_rhs = desc->max_rhs == 0 ? 1 : desc->max_rhs;
   if (max_rhs < 1 || max_rhs > 64) return fail(nullptr, ELM_DDM_ERR_ARG, "max_rhs must be in 1..64");
   if (n > TRSV_MAX_N) return fail(nullptr, ELM_DDM_ERR_ARG, "n_neurons > 8192 is not supported");
-  if (desc->flags & ~ELM_DDM_FLAG_FP64_SIMT) return fail(nullptr, ELM_DDM_ERR_ARG, "unknown flags");
+  if (desc->flags & ~(ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG))
+    return fail(nullptr, ELM_DDM_ERR_ARG, "unknown flags");
   if ((long long)N * m_max > (1ll << 31)) return fail(nullptr, ELM_DDM_ERR_ARG, "geometry too large");
 
   auto h = new elm_ddm_handle();
@@ -293,6 +297,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->st = static_cast<cudaStream_t>(stream);
   h->N = N; h->n = n; h->m_max = m_max; h->ng = ng; h->max_rhs = max_rhs;
   h->emulated = !(desc->flags & ELM_DDM_FLAG_FP64_SIMT);
+  h->cg_only = (desc->flags & ELM_DDM_FLAG_SCHUR_CG) != 0;
   h->cnt_h.assign(counts, counts + 3 * N);
   h->ms_h.resize(N); h->mg_h.resize(N);
   int msmax = 0, mgmax = 0;
@@ -449,7 +454,11 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->W2, (size_t)N * h->wstride) &&
             dev_alloc(h, &h->D, (size_t)N * h->mstride) &&
             dev_alloc(h, &h->M, (size_t)N * h->mstride) &&
-            dev_alloc(h, &h->S, (size_t)ng * ng) && dev_alloc(h, &h->Mdiag, h->mdiag_elems) &&
+            dev_alloc(h, &h->S, h->cg_only ? (size_t)1 : (size_t)ng * ng) &&
+            dev_alloc(h, &h->Mdiag, h->mdiag_elems) &&
+            dev_alloc(h, &h->cg_p, (size_t)max_rhs * std::max(ng, 1)) &&
+            dev_alloc(h, &h->cg_q, (size_t)max_rhs * std::max(ng, 1)) &&
+            dev_alloc(h, &h->cg_st, (size_t)max_rhs) &&
             dev_alloc(h, &h->thW, (size_t)N * n * 2) && dev_alloc(h, &h->thb, (size_t)N * n) &&
             dev_alloc(h, &h->xy, (size_t)N * m_max * 2) &&
             dev_alloc(h, &h->nrm, (size_t)N * m_max * 2) &&
@@ -733,8 +742,9 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
   }
   // Schur matrix (lower edge blocks, internal order): S[e1,e2] = sum of D blocks +
-  // sum_e Mblk(e,e1)^T Mblk(e,e2), each output block written once per round.
-  if (ng > 0) {
+  // sum_e Mblk(e,e1)^T Mblk(e,e2), each output block written once per round.  Not
+  // formed at all when the interface problem is solved by CG.
+  if (ng > 0 && !h->cg_only) {
     std::vector<size_t> mdoff(ne);
     size_t acc = 0;
     for (int e = 0; e < ne; ++e) { mdoff[e] = acc; acc += (size_t)h->edges[e].len * h->edges[e].len; }
@@ -959,6 +969,10 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     }
     rc = run_recs(h, h->dm_recs, 0, h->dm_recs.size(), "gemm_dm");
     if (rc) return rc;
+    if (h->cg_only) {  // D_s and M_s are all that elm_ddm_solve_cg needs
+      h->state = 2;
+      return ELM_DDM_OK;
+    }
     cudaError_t e = cudaMemsetAsync(h->S, 0, (size_t)h->ng * h->ng * sizeof(double), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->Mdiag, 0, h->mdiag_elems * sizeof(double), h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "schur: memset");
@@ -986,6 +1000,8 @@ int elm_ddm_schur(elm_ddm_handle* h) {
 int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c) {
   if (!h) return ELM_DDM_ERR_ARG;
   if (h->state != 2) return fail(h, ELM_DDM_ERR_STATE, "solve: call elm_ddm_schur first");
+  if (h->cg_only)
+    return fail(h, ELM_DDM_ERR_STATE, "solve: S is not factored (ELM_DDM_FLAG_SCHUR_CG); use elm_ddm_solve_cg");
   if (!rhs || !c) return fail(h, ELM_DDM_ERR_ARG, "solve: NULL rhs or c");
   if (nrhs < 1 || nrhs > h->max_rhs) return fail(h, ELM_DDM_ERR_ARG, "solve: nrhs out of range");
   const int N = h->N, n = h->n, ng = h->ng;
@@ -1022,6 +1038,67 @@ int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
   return ELM_DDM_OK;
 }
 
+int elm_ddm_solve_cg(elm_ddm_handle* h, const double* rhs, int nrhs, double tol, int maxit,
+                     double* u_gamma, double* c, int* iters) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  if (iters) *iters = 0;
+  if (h->state != 2) return fail(h, ELM_DDM_ERR_STATE, "solve_cg: call elm_ddm_schur first");
+  if (!rhs || !c) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: NULL rhs or c");
+  if (nrhs < 1 || nrhs > h->max_rhs) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: nrhs out of range");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: tol must be > 0");
+  if (maxit < 1) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: maxit must be >= 1");
+  const int N = h->N, n = h->n, ng = h->ng;
+  ELM_LAUNCH(h, launch_load_rhs(h->X, rhs, N, h->m_max, h->ld, h->cnt, nrhs, h->status, h->st),
+             "load_rhs");
+  ELM_LAUNCH(h, launch_apply_qt(h->X, h->K, h->kstride, h->ld, h->ms, N, n, h->T, h->tstride, nrhs,
+                                h->st), "apply_qt");
+  bool converged = true;
+  int taken = 0;
+  if (ng > 0) {
+    // right-hand side of Eq. (3.5), as in elm_ddm_solve
+    ELM_LAUNCH(h, launch_iface_vecs(h->X, h->K, h->kstride, h->ld, h->Am, h->astride, h->mgld, h->mg,
+                                    N, n, nrhs, h->gq, h->hq, h->st), "iface_vecs");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->gq, h->rv, 0, nrhs, h->st), "gather_r");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->hq, h->hv, 0, nrhs, h->st), "gather_h");
+    ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, h->mgld, h->mg, h->ifc_dof, h->hv, ng, N, nrhs, h->zv,
+                              h->st), "mt_h");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
+    // CG: x in uv, r in yv; gq / hq / hv are free now and serve as the operator's scratch
+    ELM_LAUNCH(h, launch_cg_init(h->rv, h->uv, h->yv, h->cg_p, h->cg_st, ng, nrhs, h->st), "cg_init");
+    std::vector<CgState> hs(nrhs);
+    const double tol2 = tol * tol;
+    for (int it = 0; it < maxit;) {
+      const int chunk = std::min(16, maxit - it);
+      for (int k = 0; k < chunk; ++k) {
+        ELM_LAUNCH(h, launch_schur_apply(h->D, h->M, h->mstride, h->mgld, h->mg, h->mgmax, h->ifc_dof,
+                                         h->dofmap, h->cg_p, h->cg_q, h->gq, h->hq, h->hv, ng, N, nrhs,
+                                         h->st), "cg_apply");
+        ELM_LAUNCH(h, launch_cg_update(h->uv, h->yv, h->cg_p, h->cg_q, h->cg_st, ng, nrhs, tol2, h->st),
+                   "cg_update");
+      }
+      it += chunk;
+      cudaError_t e = cudaMemcpyAsync(hs.data(), h->cg_st, nrhs * sizeof(CgState), cudaMemcpyDeviceToHost,
+                                      h->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "solve_cg: state");
+      bool all = true;
+      for (const CgState& q : hs) all = all && q.done != 0;
+      if (all) break;
+    }
+    for (const CgState& q : hs) {
+      taken = std::max(taken, q.iters);
+      converged = converged && q.done == 1;
+    }
+  }
+  ELM_LAUNCH(h, launch_backsolve(h->X, h->K, h->kstride, h->ld, h->mg, h->ifc_dof, h->mgld,
+                                 ng > 0 ? h->uv : h->rv, ng, N, n, nrhs, c, h->st), "backsolve");
+  if (u_gamma && ng > 0)
+    ELM_LAUNCH(h, launch_gather_perm(h->perm, ng, h->uv, u_gamma, nrhs, h->st), "gather_u");
+  if (iters) *iters = taken;
+  if (!converged) return fail(h, ELM_DDM_ERR_NOCONV, "solve_cg: relative residual above tol");
+  return ELM_DDM_OK;
+}
+
 int elm_ddm_eval(elm_ddm_handle* h, int npts, const double* xy, const int32_t* owner,
                  const double* c, double* u, double* grad) {
   if (!h) return ELM_DDM_ERR_ARG;
@@ -1048,6 +1125,7 @@ int elm_ddm_export(elm_ddm_handle* h, int what, int s, double* dst, int ld_dst) 
     case ELM_DDM_BUF_M:
       src = h->M + (size_t)s * h->mstride; rows = cols = h->mg_h[s]; lds = h->mgld; break;
     case ELM_DDM_BUF_L:
+      if (h->cg_only) return fail(h, ELM_DDM_ERR_STATE, "export: S is not formed (ELM_DDM_FLAG_SCHUR_CG)");
       src = h->S; rows = cols = h->ng; lds = h->ng; break;
     default: return fail(h, ELM_DDM_ERR_ARG, "export: unknown buffer");
   }

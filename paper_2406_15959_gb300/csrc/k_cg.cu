@@ -1,0 +1,171 @@
+// Conjugate gradients on the Schur system of Eq. (3.5), the solver the paper uses for
+// the interface problem (Section 4: CG to a relative residual of 1e-9).  S is applied
+// without being formed, from the stored local pieces:
+//     S p = sum_s E_s^T D_s E_s p + M^T (M p),   M p = sum_s E_s^T M_s E_s p,
+// i.e. per subdomain two dense products with D_s and M_s, one with M_s^T, and two
+// local -> global sums (launch_gather2, every interface unknown has two owners).
+#include "common.cuh"
+
+namespace elmddm {
+
+namespace {
+
+// z_s = D_s E_s p and w_s = M_s E_s p.  Block (row chunk of 64, s, rhs), 256 threads:
+// 64 rows x 4 column phases; a warp reads 32 consecutive rows of a column (coalesced).
+__global__ void __launch_bounds__(256) k_schur_apply1(const double* __restrict__ D,
+                                                      const double* __restrict__ M, long long mstride,
+                                                      int mgld, const int* __restrict__ mg_arr,
+                                                      const int* __restrict__ ifc_dof,
+                                                      const double* __restrict__ p, int ng, int N,
+                                                      double* __restrict__ zl, double* __restrict__ wl) {
+  extern __shared__ double cg_smem[];
+  double* ps = cg_smem;                          // [mgld]
+  __shared__ double red[2][4][64];
+  const int s = blockIdx.y, rh = blockIdx.z, i0 = blockIdx.x * 64;
+  const int mg = mg_arr[s];
+  if (i0 >= mg) return;
+  const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
+  const int* dofs = ifc_dof + (size_t)s * mgld;
+  const double* pp = p + (size_t)rh * ng;
+  for (int k = tid; k < mg; k += 256) ps[k] = pp[dofs[k]];
+  __syncthreads();
+  const double* Ds = D + (size_t)s * mstride;
+  const double* Ms = M + (size_t)s * mstride;
+  const int i = i0 + tx;
+  double a = 0.0, b = 0.0;
+  if (i < mg)
+    for (int j = ty; j < mg; j += 4) {
+      const double pj = ps[j];
+      a = fma(Ds[i + (size_t)j * mgld], pj, a);
+      b = fma(Ms[i + (size_t)j * mgld], pj, b);
+    }
+  red[0][ty][tx] = a;
+  red[1][ty][tx] = b;
+  __syncthreads();
+  if (ty == 0 && i < mg) {
+    const size_t o = ((size_t)rh * N + s) * mgld + i;
+    zl[o] = red[0][0][tx] + red[0][1][tx] + red[0][2][tx] + red[0][3][tx];
+    wl[o] = red[1][0][tx] + red[1][1][tx] + red[1][2][tx] + red[1][3][tx];
+  }
+}
+
+// z_s += M_s^T E_s w.  Block (16 columns, s, rhs), 8 warps, warp per column of M_s
+// (contiguous in memory), lanes over its rows.
+__global__ void __launch_bounds__(256) k_schur_apply2(const double* __restrict__ M, long long mstride,
+                                                      int mgld, const int* __restrict__ mg_arr,
+                                                      const int* __restrict__ ifc_dof,
+                                                      const double* __restrict__ w, int ng, int N,
+                                                      double* __restrict__ zl) {
+  extern __shared__ double cg_smem[];
+  double* ws = cg_smem;                          // [mgld]
+  const int s = blockIdx.y, rh = blockIdx.z, c0 = blockIdx.x * 16;
+  const int mg = mg_arr[s];
+  if (c0 >= mg) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int* dofs = ifc_dof + (size_t)s * mgld;
+  const double* ww = w + (size_t)rh * ng;
+  for (int k = tid; k < mg; k += 256) ws[k] = ww[dofs[k]];
+  __syncthreads();
+  const double* Ms = M + (size_t)s * mstride;
+  for (int i = c0 + warp; i < min(c0 + 16, mg); i += 8) {
+    double a = 0.0;
+    for (int k = lane; k < mg; k += 32) a = fma(Ms[k + (size_t)i * mgld], ws[k], a);
+    a = warp_sum(a);
+    if (lane == 0) zl[((size_t)rh * N + s) * mgld + i] += a;
+  }
+}
+
+// x = 0, r = p = b, rr = bb = b^T b.  One block per right-hand side.
+__global__ void __launch_bounds__(1024) k_cg_init(const double* __restrict__ b, double* __restrict__ x,
+                                                  double* __restrict__ r, double* __restrict__ p,
+                                                  CgState* __restrict__ st, int ng) {
+  __shared__ double red[33];
+  const int rh = blockIdx.x, tid = threadIdx.x;
+  const size_t o = (size_t)rh * ng;
+  double bb = 0.0;
+  for (int g = tid; g < ng; g += blockDim.x) {
+    const double v = b[o + g];
+    x[o + g] = 0.0;
+    r[o + g] = v;
+    p[o + g] = v;
+    bb = fma(v, v, bb);
+  }
+  bb = block_sum(bb, red);
+  if (tid == 0) {
+    st[rh].rr = bb;
+    st[rh].bb = bb;
+    st[rh].iters = 0;
+    st[rh].done = (bb == 0.0 || !isfinite(bb)) ? (isfinite(bb) ? 1 : 2) : 0;
+  }
+}
+
+// One CG step for every right-hand side not yet converged: alpha = rr / p^T q,
+// x += alpha p, r -= alpha q, beta = r^T r / rr, p = r + beta p.  done = 1 once
+// r^T r <= tol^2 b^T b; done = 2 if p^T q <= 0 (S not positive definite in floating
+// point) or a quantity is not finite.
+__global__ void __launch_bounds__(1024) k_cg_update(double* __restrict__ x, double* __restrict__ r,
+                                                    double* __restrict__ p, const double* __restrict__ q,
+                                                    CgState* __restrict__ st, int ng, double tol2) {
+  __shared__ double red[33];
+  const int rh = blockIdx.x, tid = threadIdx.x;
+  if (st[rh].done) return;
+  const double rr_old = st[rh].rr, bb = st[rh].bb;
+  const size_t o = (size_t)rh * ng;
+  double pq = 0.0;
+  for (int g = tid; g < ng; g += blockDim.x) pq = fma(p[o + g], q[o + g], pq);
+  pq = block_sum(pq, red);
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    if (tid == 0) st[rh].done = 2;
+    return;
+  }
+  const double alpha = rr_old / pq;
+  double rr = 0.0;
+  for (int g = tid; g < ng; g += blockDim.x) {
+    x[o + g] = fma(alpha, p[o + g], x[o + g]);
+    const double rg = fma(-alpha, q[o + g], r[o + g]);
+    r[o + g] = rg;
+    rr = fma(rg, rg, rr);
+  }
+  rr = block_sum(rr, red);
+  const double beta = rr / rr_old;
+  for (int g = tid; g < ng; g += blockDim.x) p[o + g] = fma(beta, p[o + g], r[o + g]);
+  if (tid == 0) {
+    st[rh].rr = rr;
+    st[rh].iters += 1;
+    if (!isfinite(rr)) st[rh].done = 2;
+    else if (rr <= tol2 * bb) st[rh].done = 1;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_schur_apply(const double* D, const double* M, long long mstride, int mgld,
+                               const int* mg, int mgmax, const int* ifc_dof, const int* dofmap,
+                               const double* p, double* q, double* zl, double* wl, double* wg,
+                               int ng, int N, int nrhs, cudaStream_t st) {
+  if (ng <= 0 || mgmax <= 0) return cudaSuccess;
+  const size_t smem = (size_t)mgld * sizeof(double);
+  k_schur_apply1<<<dim3((mgmax + 63) / 64, N, nrhs), 256, smem, st>>>(D, M, mstride, mgld, mg, ifc_dof,
+                                                                     p, ng, N, zl, wl);
+  cudaError_t e = launch_gather2(dofmap, ng, mgld, N, wl, wg, 0, nrhs, st);
+  if (e != cudaSuccess) return e;
+  k_schur_apply2<<<dim3((mgmax + 15) / 16, N, nrhs), 256, smem, st>>>(M, mstride, mgld, mg, ifc_dof, wg,
+                                                                     ng, N, zl);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_gather2(dofmap, ng, mgld, N, zl, q, 0, nrhs, st);
+}
+
+cudaError_t launch_cg_init(const double* b, double* x, double* r, double* p, CgState* state, int ng,
+                           int nrhs, cudaStream_t st) {
+  k_cg_init<<<nrhs, 1024, 0, st>>>(b, x, r, p, state, ng);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(double* x, double* r, double* p, const double* q, CgState* state, int ng,
+                             int nrhs, double tol2, cudaStream_t st) {
+  k_cg_update<<<nrhs, 1024, 0, st>>>(x, r, p, q, state, ng, tol2);
+  return cudaGetLastError();
+}
+
+}  // namespace elmddm

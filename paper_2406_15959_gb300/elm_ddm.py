@@ -14,17 +14,18 @@ import numpy as np
 
 from . import build as _build
 
-OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_RANK, ERR_NOT_SPD, ERR_CAPACITY = range(9)
+(OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_RANK, ERR_NOT_SPD, ERR_CAPACITY,
+ ERR_NOCONV) = range(10)
 ERROR_NAMES = {ERR_ARG: "ERR_ARG", ERR_STATE: "ERR_STATE", ERR_CUDA: "ERR_CUDA",
                ERR_OOM: "ERR_OOM", ERR_NONFINITE: "ERR_NONFINITE", ERR_RANK: "ERR_RANK",
-               ERR_NOT_SPD: "ERR_NOT_SPD"}
+               ERR_NOT_SPD: "ERR_NOT_SPD", ERR_CAPACITY: "ERR_CAPACITY", ERR_NOCONV: "ERR_NOCONV"}
 
 # Every symbol the header declares.
 SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve",
            "elm_ddm_eval", "elm_ddm_export", "elm_ddm_check", "elm_ddm_get_info",
            "elm_ddm_profile", "elm_ddm_profile_report", "elm_ddm_destroy",
            "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order",
-           "elm_ddm_profile_only")
+           "elm_ddm_profile_only", "elm_ddm_solve_cg")
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
 
 
@@ -41,6 +42,7 @@ class Desc(ctypes.Structure):
 
 
 FLAG_FP64_SIMT = 1
+FLAG_SCHUR_CG = 2
 
 
 _lib = None
@@ -69,6 +71,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_check.argtypes = [P]
     lib.elm_ddm_interface_order.argtypes = [P, P]
     lib.elm_ddm_profile.argtypes = [P, I]
+    lib.elm_ddm_solve_cg.argtypes = [P, P, I, ctypes.c_double, I, P, P, ctypes.POINTER(I)]
     lib.elm_ddm_profile_only.argtypes = [P, ctypes.c_char_p]
     lib.elm_ddm_profile_report.argtypes = [P, ctypes.c_char_p, I]
     lib.elm_ddm_get_info.argtypes = [P, I, D]
@@ -112,7 +115,8 @@ class GeometryArrays:
 class Solver:
     """One decomposition on one GPU: setup -> assemble(theta) -> schur() -> solve(rhs)."""
 
-    def __init__(self, geom, n_neurons: int, max_rhs: int = 1, stream=None, fp64_simt: bool = False):
+    def __init__(self, geom, n_neurons: int, max_rhs: int = 1, stream=None, fp64_simt: bool = False,
+                 schur_cg: bool = False):
         import torch
         self.lib = load()
         ga = geom if isinstance(geom, GeometryArrays) else GeometryArrays.from_geometry(geom)
@@ -120,7 +124,8 @@ class Solver:
         self.N, self.n, self.m_max, self.n_gamma = N, int(n_neurons), m_max, ga.n_gamma
         self.max_rhs = max_rhs
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        desc = Desc(N, self.n, m_max, ga.n_gamma, 0, max_rhs, FLAG_FP64_SIMT if fp64_simt else 0)
+        flags = (FLAG_FP64_SIMT if fp64_simt else 0) | (FLAG_SCHUR_CG if schur_cg else 0)
+        desc = Desc(N, self.n, m_max, ga.n_gamma, 0, max_rhs, flags)
         h = ctypes.c_void_p()
         self._keep = ga
         rc = self.lib.elm_ddm_setup(ctypes.byref(desc), ga.counts.ctypes.data, ga.xy.ctypes.data,
@@ -170,6 +175,28 @@ class Solver:
         if squeeze:
             return (u_gamma[0] if u_gamma is not None else None), c[0]
         return u_gamma, c
+
+    def solve_cg(self, rhs, tol: float = 1e-9, maxit: int = 10000, u_gamma=None, c=None,
+                 require_convergence: bool = True):
+        """As solve(), with the interface system solved by CG to relative residual tol.
+        Returns (u_gamma, c, iterations)."""
+        import torch
+        squeeze = rhs.dim() == 2
+        r = rhs.unsqueeze(0) if squeeze else rhs
+        nrhs = r.shape[0]
+        if c is None:
+            c = torch.empty((nrhs, self.N, self.n), dtype=torch.float64, device=rhs.device)
+        if u_gamma is None and self.n_gamma > 0:
+            u_gamma = torch.empty((nrhs, self.n_gamma), dtype=torch.float64, device=rhs.device)
+        it = ctypes.c_int(0)
+        rc = self.lib.elm_ddm_solve_cg(self.h, _ptr(r.contiguous()), nrhs, float(tol), int(maxit),
+                                       _ptr(u_gamma) if self.n_gamma > 0 else None, _ptr(c),
+                                       ctypes.byref(it))
+        if rc != ERR_NOCONV or require_convergence:
+            self._check_rc(rc)
+        if squeeze:
+            return (u_gamma[0] if u_gamma is not None else None), c[0], it.value
+        return u_gamma, c, it.value
 
     def eval(self, xy, owner, c, u=None, grad=None):
         import torch

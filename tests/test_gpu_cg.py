@@ -1,0 +1,147 @@
+"""GPU conjugate-gradient interface solve (the paper's solver for Eq. (3.5), Section 4)
+against the oracle.
+
+CG stops at a relative residual tol of its own Schur system.  The GPU's and the
+oracle's Schur matrices are two roundings of the same least-squares pieces: they give the
+same interface solution to 1e-8 (the direct-solve parity tests), but with kappa(S) ~ 3e5 and
+|S||u|/|rhs| ~ 3e3 on the paper-initialised cases, a residual taken in the *other* system
+is not pinned at tol.  So the pins are: the true residual of the CG iterate in the GPU's
+own system (S = L L^T from the exported Cholesky factor, rhs = S u_direct from the direct
+solve of the same handle) <= tol, up to rounding; the distance to the oracle's exact
+(Cholesky) interface solution that the residual bound allows, 2 kappa(S) tol + 1e-8; and,
+as a sanity check where S is determined by the data, the number of CG steps against the
+oracle's own CG.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import elm_oracle as O
+from paper_2406_15959_gb300 import elm_ddm as E
+from paper_2406_15959_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+DEV = torch.device("cuda:0")
+TOL = 1e-9  # the paper's stopping rule
+
+CASES = {
+    "2x2_n200": wl.poisson_2x2_n200,
+    "3x3_ragged": lambda: wl.build(3, 3, 150, 17, 13, 23, 21, theta="paper", theta_seed=5,
+                                   source="fourier", source_seed=5, n_test_side=60),
+    "5x3_edges70": lambda: wl.build(5, 3, 97, 14, 12, 30, 70, theta="paper", theta_seed=9,
+                                    source="fourier", source_seed=9, n_test_side=50),
+    "4x4_n1000": wl.poisson_4x4_n1000,
+}
+
+_cache = {}
+
+
+def get(name):
+    if name not in _cache:
+        w = CASES[name]()
+        res = O.solve(w.geom, w.W, w.b, w.rhs, keep=False)
+        _cache[name] = (w, res)
+    return _cache[name]
+
+
+def t(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV, dtype=dtype)
+
+
+def cg_run(w, schur_cg=False, tol=TOL, maxit=20000, require=True):
+    s = E.Solver(w.geom, w.n_neurons, schur_cg=schur_cg)
+    s.assemble(t(w.W), t(w.b))
+    s.schur()
+    ug, c, it = s.solve_cg(t(w.rhs), tol=tol, maxit=maxit, require_convergence=require)
+    u, g = s.eval(t(w.test_xy), t(w.test_owner, torch.int32), c)
+    s.check()
+    return s, ug, c, u, it
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_cg_residual_steps_and_distance_to_direct_solution(name):
+    w, res = get(name)
+    s, ug, _, u, it = cg_run(w)
+    ud, _ = s.solve(t(w.rhs))                      # direct solve, same handle and operator
+    ug, ud = ug.cpu().numpy(), ud.cpu().numpy()
+    Lg = np.tril(s.export(E.BUF_L).cpu().numpy())  # S = L L^T in the internal order
+    inv = np.argsort(s.interface_order())          # internal index -> caller unknown
+    r = Lg @ (Lg.T @ (ug - ud)[inv])               # S u_cg - rhs
+    b = Lg @ (Lg.T @ ud[inv])                      # rhs
+    assert np.linalg.norm(r) <= 1.5 * TOL * np.linalg.norm(b), np.linalg.norm(r) / np.linalg.norm(b)
+    ev = np.linalg.eigvalsh(res.S)
+    kappa = ev[-1] / ev[0]
+    err = np.linalg.norm(ug - res.u_gamma) / np.linalg.norm(res.u_gamma)
+    assert err <= 2 * kappa * TOL + 1e-8, (err, kappa)
+    _, k_or, ok = O.cg_solve(res.S, res.rhs, TOL, 100000)
+    assert ok
+    # Step counts depend on S's spectrum.  Where some K^s is numerically rank-deficient
+    # (the paper's initialisation), S itself is not determined by the data: two backward-
+    # stable factorizations give Schur matrices several percent apart (6% on the 4x4 case)
+    # with the same u_Gamma.  Compare step counts only where the two S agree; finite-
+    # precision CG still follows a rounding-dependent path, so this is a sanity check.
+    S_gpu = Lg @ Lg.T
+    if np.abs(S_gpu - res.S[np.ix_(inv, inv)]).max() <= 1e-10 * np.abs(res.S).max():
+        assert abs(it - k_or) <= max(5, 0.1 * k_or), (it, k_or)
+
+
+def test_cg_only_mode_skips_the_schur_matrix_and_matches():
+    """ELM_DDM_FLAG_SCHUR_CG: no S, no Cholesky; the CG result is bitwise the one of the
+    full mode (same D_s, M_s, same operator), elm_ddm_solve and the L export refuse."""
+    w, _ = get("3x3_ragged")
+    s1, ug1, c1, _, it1 = cg_run(w)
+    s2, ug2, c2, _, it2 = cg_run(w, schur_cg=True)
+    assert it1 == it2
+    assert torch.equal(ug1, ug2) and torch.equal(c1, c2)
+    with pytest.raises(E.ElmDdmError) as ei:
+        s2.solve(t(w.rhs))
+    assert ei.value.code == E.ERR_STATE
+    with pytest.raises(E.ElmDdmError) as ei:
+        s2.export(E.BUF_L)
+    assert ei.value.code == E.ERR_STATE
+    assert s2.workspace_bytes < s1.workspace_bytes
+
+
+def test_cg_iteration_limit_reports_nonconvergence():
+    w, _ = get("2x2_n200")
+    _, _, _, _, it = cg_run(w, maxit=3, require=False)
+    assert it == 3
+    with pytest.raises(E.ElmDdmError) as ei:
+        cg_run(w, maxit=3)
+    assert ei.value.code == E.ERR_NOCONV
+
+
+def test_cg_rejects_bad_arguments():
+    w, _ = get("2x2_n200")
+    s = E.Solver(w.geom, w.n_neurons)
+    s.assemble(t(w.W), t(w.b))
+    with pytest.raises(E.ElmDdmError) as ei:  # before schur
+        s.solve_cg(t(w.rhs))
+    assert ei.value.code == E.ERR_STATE
+    s.schur()
+    for kw in (dict(tol=0.0), dict(tol=float("nan")), dict(maxit=0)):
+        with pytest.raises(E.ElmDdmError) as ei:
+            s.solve_cg(t(w.rhs), **kw)
+        assert ei.value.code == E.ERR_ARG
+
+
+def test_cg_full_size_8x8_n1000():
+    """The benchmark workload solved the paper's way (no Schur matrix formed): distance to
+    the oracle's exact interface solution within 2 kappa(S) tol, and the manufactured-
+    solution error of the resulting network."""
+    w = wl.poisson_8x8_n1000()
+    res = O.solve(w.geom, w.W, w.b, w.rhs, keep=False)
+    _, ug, _, u, it = cg_run(w, schur_cg=True)
+    ug = ug.cpu().numpy()
+    ev = np.linalg.eigvalsh(res.S)
+    kappa = ev[-1] / ev[0]
+    err = np.linalg.norm(ug - res.u_gamma) / np.linalg.norm(res.u_gamma)
+    assert err <= 2 * kappa * TOL + 1e-8, (err, kappa)
+    l2, _ = O.rel_errors(u.cpu().numpy(), np.zeros((len(w.test_xy), 2)), w.src.u(w.test_xy),
+                         w.src.grad_u(w.test_xy))
+    assert l2 < 1e-6, l2

@@ -234,3 +234,54 @@ def test_fourier_source_has_the_stated_exact_solution():
     ex, ey = np.array([h, 0.0]), np.array([0.0, h])
     lap = (src.u(p + ex) + src.u(p - ex) + src.u(p + ey) + src.u(p - ey) - 4 * src.u(p)) / h ** 2
     np.testing.assert_allclose(-lap, src.f(p), rtol=1e-5, atol=1e-6)
+
+
+# --- CG for the interface system (Section 4), pinned to properties of the algorithm ---
+
+def test_cg_terminates_in_distinct_eigenvalue_count():
+    """In exact arithmetic CG ends after as many steps as S has distinct eigenvalues;
+    with 4 well-separated ones it must meet a tight tolerance within 4 (+1) steps."""
+    rng = np.random.default_rng(7)
+    Qm, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    lam = np.repeat([1.0, 3.0, 7.0, 20.0], 10)
+    S = (Qm * lam) @ Qm.T
+    b = rng.standard_normal(40)
+    x, k, ok = O.cg_solve(S, b, 1e-12, 200)
+    assert ok and k <= 5
+    assert np.linalg.norm(x - np.linalg.solve(S, b)) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_cg_matches_direct_solve_within_condition_bound():
+    rng = np.random.default_rng(8)
+    B = rng.standard_normal((60, 60))
+    S = B @ B.T + 60 * np.eye(60)
+    b = rng.standard_normal(60)
+    tol = 1e-10
+    x, k, ok = O.cg_solve(S, b, tol, 1000)
+    xd = np.linalg.solve(S, b)
+    assert ok
+    assert np.linalg.norm(S @ x - b) <= tol * np.linalg.norm(b) * (1 + 1e-6)
+    assert np.linalg.norm(x - xd) <= np.linalg.cond(S) * tol * np.linalg.norm(xd) * 2
+
+
+def test_cg_reports_non_convergence_at_maxit():
+    rng = np.random.default_rng(9)
+    B = rng.standard_normal((50, 50))
+    S = B @ B.T + 1e-3 * np.eye(50)
+    x, k, ok = O.cg_solve(S, rng.standard_normal(50), 1e-14, 5)
+    assert not ok and k == 5
+
+
+def test_cg_on_schur_system_reaches_cholesky_solution():
+    """On the 2x2 tiny problem the CG interface solution agrees with the Cholesky one
+    to the accuracy the residual bound allows."""
+    g = wl.make_geometry(2, 2, 6, 6, 6, 6)
+    n = 12
+    W, b = wl.draw_theta(g, n, mode="paper", c=0.5, seed=3)
+    rows = wl.rhs_rows(g, wl.make_source("sinsin"))
+    res = O.solve(g, W, b, rows)
+    tol = 1e-11
+    u, k, ok = O.cg_solve(res.S, res.rhs, tol, 10 * len(res.rhs))
+    assert ok
+    kappa = np.linalg.cond(res.S)
+    assert np.linalg.norm(u - res.u_gamma) <= 2 * kappa * tol * np.linalg.norm(res.u_gamma)
