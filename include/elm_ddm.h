@@ -69,6 +69,8 @@ extern "C" {
 
 /* Differential operators. */
 #define ELM_DDM_OP_POISSON 0  /* L = -Laplacian (Eq. (4.4)) */
+#define ELM_DDM_OP_VARCOEF 1  /* L = -div(rho grad) (Section 4, the variable-coefficient
+                                 problem); rho given by elm_ddm_set_coefficient */
 
 typedef struct elm_ddm_handle elm_ddm_handle;
 
@@ -109,6 +111,19 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
  * theta is copied into the handle (elm_ddm_eval uses it).
  */
 int elm_ddm_assemble(elm_ddm_handle* h, const double* W, const double* b);
+
+/*
+ * Coefficient of ELM_DDM_OP_VARCOEF (Section 4: -div(rho grad u) = f).  Interior rows
+ * of K^s become L phi = 2 rho |w|^2 t (1 - t^2) - (grad rho . w)(1 - t^2); rho is taken
+ * continuous across the interfaces, so the flux condition rho du/dn reduces to the
+ * normal-derivative rows A^s, which are unchanged.
+ *   coef  device double [N][m_max][3]: (rho, d rho/dx, d rho/dy) at every row of every
+ *         subdomain (only the interior rows are read); copied into the handle.
+ * Required before elm_ddm_assemble for ELM_DDM_OP_VARCOEF (assemble returns ERR_STATE
+ * without it); returns ERR_ARG for ELM_DDM_OP_POISSON.  Non-finite values make
+ * elm_ddm_assemble flag ELM_DDM_ERR_NONFINITE (reported by elm_ddm_check).
+ */
+int elm_ddm_set_coefficient(elm_ddm_handle* h, const double* coef);
 
 /*
  * Step (b) and the RHS-independent part of step (c): Householder QR K^s = Q_s R_s

@@ -59,7 +59,7 @@ def hidden(W, b, xy):
     return np.tanh(z)
 
 
-def assemble_local(xy, nrm, counts, W, b):
+def assemble_local(xy, nrm, counts, W, b, coef=None):
     """K^s [m, n] and A^s [m_G, n] of subdomain s (Section 3).
 
     Rows of K^s: L phi_j at interior points, phi_j at boundary points, phi_j at
@@ -67,6 +67,12 @@ def assemble_local(xy, nrm, counts, W, b):
       d phi / dx_d = w_d (1 - t^2),  d^2 phi / dx_d^2 = -2 w_d^2 t (1 - t^2),
       L phi = -Laplacian phi = 2 |w|^2 t (1 - t^2),
       d phi / d n  = (w . n)(1 - t^2)   (rows of A^s, outward normal n).
+    With a variable coefficient (Section 4, -div(rho grad u) = f; coef = rows of
+    (rho, d rho/dx, d rho/dy) at the points):
+      L phi = -rho Laplacian phi - grad rho . grad phi
+            = 2 rho |w|^2 t (1 - t^2) - (grad rho . w)(1 - t^2).
+    The transmission rows are unchanged: with rho continuous across Gamma the flux
+    condition rho du/dn is the normal-derivative condition.
     """
     mi, mb, mg = (int(v) for v in counts)
     m = mi + mb + mg
@@ -74,6 +80,9 @@ def assemble_local(xy, nrm, counts, W, b):
     wsq = (W * W).sum(axis=1)
     K = t.copy()
     K[:mi] = 2.0 * wsq[None, :] * t[:mi] * (1.0 - t[:mi] ** 2)
+    if coef is not None:
+        rho, grho = coef[:mi, 0:1], coef[:mi, 1:3]
+        K[:mi] = rho * K[:mi] - (grho @ W.T) * (1.0 - t[:mi] ** 2)
     tg = t[mi + mb:m]
     wn = nrm[mi + mb:m] @ W.T                     # [m_G, n]: w_j . n_i
     A = wn * (1.0 - tg ** 2)
@@ -166,13 +175,15 @@ class Result:
     locs: list
 
 
-def solve(geom, W, b, rhs_rows, keep=True):
-    """Algorithm 1: assemble, factor, solve Eq. (3.5) by Cholesky, back-solve."""
+def solve(geom, W, b, rhs_rows, keep=True, coef=None):
+    """Algorithm 1: assemble, factor, solve Eq. (3.5) by Cholesky, back-solve.
+    coef: None (-Laplacian) or [N, m_max, 3] rows of (rho, grad rho)."""
     N = geom.n_sub
     locs, qs = [], []
     for s in range(N):
         mi, mb, mg = (int(v) for v in geom.counts[s])
-        K, A = assemble_local(geom.xy[s], geom.nrm[s], geom.counts[s], W[s], b[s])
+        K, A = assemble_local(geom.xy[s], geom.nrm[s], geom.counts[s], W[s], b[s],
+                              None if coef is None else coef[s])
         dof = geom.dof[s, mi + mb:mi + mb + mg].astype(np.int64)
         L = factor_local(K, A, dof, mi + mb)
         F = rhs_local(rhs_rows[s], geom.counts[s])
@@ -242,7 +253,7 @@ def rel_errors(u, g, u_ex, g_ex):
 # Global dense operators of Eqs. (3.1)-(3.4), for brute-force checks (tiny inputs)
 # --------------------------------------------------------------------------
 
-def global_blocks(geom, W, b, rhs_rows):
+def global_blocks(geom, W, b, rhs_rows, coef=None):
     """Dense K = diag(K^s), B = [B^s], A = [A^s] (one row per interface unknown),
     F = [F^s] of Eq. (3.2)."""
     Ks, As, Fs, Bs = [], [], [], []
@@ -250,7 +261,8 @@ def global_blocks(geom, W, b, rhs_rows):
     N = geom.n_sub
     for s in range(N):
         mi, mb, mg = (int(v) for v in geom.counts[s])
-        K, A = assemble_local(geom.xy[s], geom.nrm[s], geom.counts[s], W[s], b[s])
+        K, A = assemble_local(geom.xy[s], geom.nrm[s], geom.counts[s], W[s], b[s],
+                              None if coef is None else coef[s])
         Ks.append(K)
         Fs.append(rhs_local(rhs_rows[s], geom.counts[s]))
         Bs_ = np.zeros((mi + mb + mg, geom.n_gamma))
@@ -268,10 +280,10 @@ def global_blocks(geom, W, b, rhs_rows):
     return K, A, B, F
 
 
-def monolithic_ls(geom, W, b, rhs_rows):
+def monolithic_ls(geom, W, b, rhs_rows, coef=None):
     """LS solution of Eq. (3.3): [[K, B], [0, -A K^+ B]] [c; u] = [F; -A K^+ F],
     K^+ = (K^T K)^{-1} K^T.  Returns (c [N, n], u_gamma)."""
-    K, A, B, F = global_blocks(geom, W, b, rhs_rows)
+    K, A, B, F = global_blocks(geom, W, b, rhs_rows, coef)
     Kp = np.linalg.solve(K.T @ K, K.T)
     top = np.hstack([K, B])
     bot = np.hstack([np.zeros((A.shape[0], K.shape[1])), -A @ Kp @ B])
@@ -282,9 +294,9 @@ def monolithic_ls(geom, W, b, rhs_rows):
     return x[:nc].reshape(geom.n_sub, -1), x[nc:]
 
 
-def normal_equations(geom, W, b, rhs_rows):
+def normal_equations(geom, W, b, rhs_rows, coef=None):
     """Dense Eq. (3.4) solved by LU.  Returns (c [N, n], u_gamma)."""
-    K, A, B, F = global_blocks(geom, W, b, rhs_rows)
+    K, A, B, F = global_blocks(geom, W, b, rhs_rows, coef)
     Kp = np.linalg.solve(K.T @ K, K.T)
     T = np.eye(K.shape[0]) + Kp.T @ A.T @ A @ Kp
     top = np.hstack([K.T @ K, K.T @ B])

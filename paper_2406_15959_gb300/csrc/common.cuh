@@ -90,10 +90,11 @@ cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_
                         double alpha, double beta, int flags, cudaStream_t st);
 cudaError_t launch_add_blocks(const AddDesc* d, int count, int max_elems, cudaStream_t st);
 
+// coef: NULL for -Laplacian, else [N][m_max][3] (rho, grad rho) for -div(rho grad).
 cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, double* Amat,
                             long long astride, int mgld, const double* xy, const double* nrm,
                             int m_max, const int* cnt, const double* W, const double* b, int N,
-                            int n, unsigned* status, cudaStream_t st);
+                            int n, const double* coef, unsigned* status, cudaStream_t st);
 cudaError_t launch_eval(const double* W, const double* b, int N, int n, int npts,
                         const double* xy, const int* owner, const double* c, double* u,
                         double* grad, cudaStream_t st);

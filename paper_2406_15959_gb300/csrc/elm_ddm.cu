@@ -128,6 +128,9 @@ struct elm_ddm_handle {
   int4* ut = nullptr;  // tile tables of the persistent launches
   bool emulated = true;          // FP64 products on the tensor cores (digit split)
   bool cg_only = false;          // S is neither formed nor factored (elm_ddm_solve_cg only)
+  int op = ELM_DDM_OP_POISSON;
+  double* coef = nullptr;        // [N][m_max][3] rho, grad rho (ELM_DDM_OP_VARCOEF)
+  bool coef_set = false;
   double *cg_p = nullptr, *cg_q = nullptr;  // CG search direction and S p, [max_rhs][ng]
   CgState* cg_st = nullptr;                 // [max_rhs]
   void* sp_buf = nullptr;        // digit tiles and row exponents of the split operands
@@ -284,7 +287,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const int N = desc->n_sub, n = desc->n_neurons, m_max = desc->m_max, ng = desc->n_gamma;
   if (N < 1 || n < 1 || m_max < 1 || ng < 0)
     return fail(nullptr, ELM_DDM_ERR_ARG, "n_sub, n_neurons, m_max must be >= 1 and n_gamma >= 0");
-  if (desc->op != ELM_DDM_OP_POISSON) return fail(nullptr, ELM_DDM_ERR_ARG, "unsupported operator");
+  if (desc->op != ELM_DDM_OP_POISSON && desc->op != ELM_DDM_OP_VARCOEF)
+    return fail(nullptr, ELM_DDM_ERR_ARG, "unsupported operator");
   const int max_rhs = desc->max_rhs == 0 ? 1 : desc->max_rhs;
   if (max_rhs < 1 || max_rhs > 64) return fail(nullptr, ELM_DDM_ERR_ARG, "max_rhs must be in 1..64");
   if (n > TRSV_MAX_N) return fail(nullptr, ELM_DDM_ERR_ARG, "n_neurons > 8192 is not supported");
@@ -298,6 +302,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->N = N; h->n = n; h->m_max = m_max; h->ng = ng; h->max_rhs = max_rhs;
   h->emulated = !(desc->flags & ELM_DDM_FLAG_FP64_SIMT);
   h->cg_only = (desc->flags & ELM_DDM_FLAG_SCHUR_CG) != 0;
+  h->op = desc->op;
   h->cnt_h.assign(counts, counts + 3 * N);
   h->ms_h.resize(N); h->mg_h.resize(N);
   int msmax = 0, mgmax = 0;
@@ -459,6 +464,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->cg_p, (size_t)max_rhs * std::max(ng, 1)) &&
             dev_alloc(h, &h->cg_q, (size_t)max_rhs * std::max(ng, 1)) &&
             dev_alloc(h, &h->cg_st, (size_t)max_rhs) &&
+            dev_alloc(h, &h->coef, h->op == ELM_DDM_OP_VARCOEF ? (size_t)N * m_max * 3 : (size_t)1) &&
             dev_alloc(h, &h->thW, (size_t)N * n * 2) && dev_alloc(h, &h->thb, (size_t)N * n) &&
             dev_alloc(h, &h->xy, (size_t)N * m_max * 2) &&
             dev_alloc(h, &h->nrm, (size_t)N * m_max * 2) &&
@@ -929,16 +935,30 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   return ELM_DDM_OK;
 }
 
+int elm_ddm_set_coefficient(elm_ddm_handle* h, const double* coef) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  if (h->op != ELM_DDM_OP_VARCOEF) return fail(h, ELM_DDM_ERR_ARG, "set_coefficient: operator has none");
+  if (!coef) return fail(h, ELM_DDM_ERR_ARG, "set_coefficient: NULL coef");
+  cudaError_t e = cudaMemcpyAsync(h->coef, coef, (size_t)h->N * h->m_max * 3 * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, h->st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_coefficient");
+  h->coef_set = true;
+  return ELM_DDM_OK;
+}
+
 int elm_ddm_assemble(elm_ddm_handle* h, const double* W, const double* b) {
   if (!h) return ELM_DDM_ERR_ARG;
   if (!W || !b) return fail(h, ELM_DDM_ERR_ARG, "assemble: NULL theta");
+  if (h->op == ELM_DDM_OP_VARCOEF && !h->coef_set)
+    return fail(h, ELM_DDM_ERR_STATE, "assemble: call elm_ddm_set_coefficient first");
   const size_t nw = (size_t)h->N * h->n;
   cudaError_t e = cudaMemcpyAsync(h->thW, W, nw * 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->thb, b, nw * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Am, 0, (size_t)h->N * h->astride * sizeof(double), h->st);
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble: copy theta");
   ELM_LAUNCH(h, launch_assemble(h->K, h->kstride, h->ld, h->ncap, h->Am, h->astride, h->mgld, h->xy,
-                                h->nrm, h->m_max, h->cnt, h->thW, h->thb, h->N, h->n, h->status, h->st),
+                                h->nrm, h->m_max, h->cnt, h->thW, h->thb, h->N, h->n,
+                                h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr, h->status, h->st),
              "assemble");
   h->state = 1;
   return ELM_DDM_OK;

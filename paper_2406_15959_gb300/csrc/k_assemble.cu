@@ -2,7 +2,9 @@
 // evaluation of the trained local networks at arbitrary points.
 //
 // For subdomain s and hidden neuron j, with t = tanh(w_j . x + b_j):
-//   interior rows          L phi_j = -Laplacian phi_j = 2 |w_j|^2 t (1 - t^2)
+//   interior rows          L phi_j = -Laplacian phi_j = 2 |w_j|^2 t (1 - t^2), or for
+//                          L = -div(rho grad) (Section 4, variable coefficient)
+//                          2 rho |w_j|^2 t (1 - t^2) - (grad rho . w_j)(1 - t^2)
 //   boundary/interface     phi_j = t
 //   A^s (interface rows)   d phi_j / d n = (w_j . n)(1 - t^2)
 // The kernel also writes the m_Gamma "interface identity" columns J = E^T next to
@@ -25,6 +27,7 @@ __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long l
                                                   const int* __restrict__ cnt,
                                                   const double* __restrict__ W,
                                                   const double* __restrict__ bias, int n,
+                                                  const double* __restrict__ coef,
                                                   unsigned* status) {
   const int s = blockIdx.z;
   const int r = blockIdx.x * AR + threadIdx.x;
@@ -48,9 +51,15 @@ __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long l
   if (r >= ld) return;
 
   double px = 0, py = 0, nx = 0, ny = 0;
+  double rho = 1.0, rx = 0.0, ry = 0.0;  // coefficient and its gradient (interior rows)
   if (r < ms) {
     px = xy[((size_t)s * m_max + r) * 2];
     py = xy[((size_t)s * m_max + r) * 2 + 1];
+    if (coef && r < mi) {
+      const double* cr = coef + ((size_t)s * m_max + r) * 3;
+      rho = cr[0]; rx = cr[1]; ry = cr[2];
+      if (!isfinite(rho) || !isfinite(rx) || !isfinite(ry)) atomicOr(status, ST_NONFINITE);
+    }
     if (r >= row0g) {
       nx = nrm[((size_t)s * m_max + r) * 2];
       ny = nrm[((size_t)s * m_max + r) * 2 + 1];
@@ -72,8 +81,12 @@ __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long l
         const double t = tanh(z);
         const double d1 = 1.0 - t * t;
         bad |= !isfinite(z);
-        if (r < mi) v = 2.0 * fma(wx, wx, wy * wy) * t * d1;
-        else v = t;
+        if (r < mi) {
+          v = 2.0 * fma(wx, wx, wy * wy) * t * d1;
+          if (coef) v = fma(rho, v, -fma(rx, wx, ry * wy) * d1);
+        } else {
+          v = t;
+        }
         if (r >= row0g) As[(r - row0g) + (size_t)c * mgld] = fma(wx, nx, wy * ny) * d1;
       }
     } else if (c - n < mg) {
@@ -130,10 +143,10 @@ __global__ void __launch_bounds__(256) k_eval(const double* __restrict__ W,
 cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, double* Amat,
                             long long astride, int mgld, const double* xy, const double* nrm,
                             int m_max, const int* cnt, const double* W, const double* b, int N,
-                            int n, unsigned* status, cudaStream_t st) {
+                            int n, const double* coef, unsigned* status, cudaStream_t st) {
   dim3 grid((ld + AR - 1) / AR, (ncap + AC - 1) / AC, N);
   k_assemble<<<grid, dim3(AR, 4), 0, st>>>(K, kstride, ld, ncap, Amat, astride, mgld, xy, nrm,
-                                           m_max, cnt, W, b, n, status);
+                                           m_max, cnt, W, b, n, coef, status);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve"
            "elm_ddm_eval", "elm_ddm_export", "elm_ddm_check", "elm_ddm_get_info",
            "elm_ddm_profile", "elm_ddm_profile_report", "elm_ddm_destroy",
            "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order",
-           "elm_ddm_profile_only", "elm_ddm_solve_cg")
+           "elm_ddm_profile_only", "elm_ddm_solve_cg", "elm_ddm_set_coefficient")
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
 
 
@@ -43,6 +43,7 @@ class Desc(ctypes.Structure):
 
 FLAG_FP64_SIMT = 1
 FLAG_SCHUR_CG = 2
+OP_POISSON, OP_VARCOEF = 0, 1
 
 
 _lib = None
@@ -71,6 +72,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_check.argtypes = [P]
     lib.elm_ddm_interface_order.argtypes = [P, P]
     lib.elm_ddm_profile.argtypes = [P, I]
+    lib.elm_ddm_set_coefficient.argtypes = [P, P]
     lib.elm_ddm_solve_cg.argtypes = [P, P, I, ctypes.c_double, I, P, P, ctypes.POINTER(I)]
     lib.elm_ddm_profile_only.argtypes = [P, ctypes.c_char_p]
     lib.elm_ddm_profile_report.argtypes = [P, ctypes.c_char_p, I]
@@ -116,7 +118,7 @@ class Solver:
     """One decomposition on one GPU: setup -> assemble(theta) -> schur() -> solve(rhs)."""
 
     def __init__(self, geom, n_neurons: int, max_rhs: int = 1, stream=None, fp64_simt: bool = False,
-                 schur_cg: bool = False):
+                 schur_cg: bool = False, op: int = OP_POISSON):
         import torch
         self.lib = load()
         ga = geom if isinstance(geom, GeometryArrays) else GeometryArrays.from_geometry(geom)
@@ -125,7 +127,7 @@ class Solver:
         self.max_rhs = max_rhs
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         flags = (FLAG_FP64_SIMT if fp64_simt else 0) | (FLAG_SCHUR_CG if schur_cg else 0)
-        desc = Desc(N, self.n, m_max, ga.n_gamma, 0, max_rhs, flags)
+        desc = Desc(N, self.n, m_max, ga.n_gamma, op, max_rhs, flags)
         h = ctypes.c_void_p()
         self._keep = ga
         rc = self.lib.elm_ddm_setup(ctypes.byref(desc), ga.counts.ctypes.data, ga.xy.ctypes.data,
@@ -156,6 +158,10 @@ class Solver:
     # -- Algorithm 1
     def assemble(self, W, b):
         self._check_rc(self.lib.elm_ddm_assemble(self.h, _ptr(W), _ptr(b)))
+
+    def set_coefficient(self, coef_rows):
+        """ELM_DDM_OP_VARCOEF: (rho, d rho/dx, d rho/dy) per row, CUDA float64 [N, m_max, 3]."""
+        self._check_rc(self.lib.elm_ddm_set_coefficient(self.h, _ptr(coef_rows.contiguous())))
 
     def schur(self):
         self._check_rc(self.lib.elm_ddm_schur(self.h))
@@ -273,7 +279,10 @@ def run_workload(w, device="cuda", max_rhs=1):
     Returns dict with u_gamma, c, u and grad at the test points (torch CUDA tensors)."""
     import torch
     dev = torch.device(device)
-    s = Solver(w.geom, w.n_neurons, max_rhs=max_rhs)
+    coef = getattr(w, "coef_rows", None)
+    s = Solver(w.geom, w.n_neurons, max_rhs=max_rhs, op=OP_VARCOEF if coef is not None else OP_POISSON)
+    if coef is not None:
+        s.set_coefficient(torch.as_tensor(coef, device=dev))
     W = torch.as_tensor(w.W, device=dev).contiguous()
     b = torch.as_tensor(w.b, device=dev).contiguous()
     rhs = torch.as_tensor(w.rhs, device=dev).contiguous()
@@ -304,7 +313,10 @@ def _main(argv=None):
     count = int(args[1]) if len(args) > 1 else 1
     w = wl.WORKLOADS[name]()
     dev = torch.device("cuda:0")
-    s = Solver(w.geom, w.n_neurons, fp64_simt=simt)
+    coef = getattr(w, "coef_rows", None)
+    s = Solver(w.geom, w.n_neurons, fp64_simt=simt, op=OP_VARCOEF if coef is not None else OP_POISSON)
+    if coef is not None:
+        s.set_coefficient(torch.as_tensor(coef, device=dev))
     W = torch.as_tensor(w.W, device=dev)
     b = torch.as_tensor(w.b, device=dev)
     rhs = torch.as_tensor(w.rhs, device=dev)

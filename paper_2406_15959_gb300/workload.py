@@ -230,7 +230,14 @@ class Source:
     params: dict
 
     def f(self, xy):
+        coef = self.params.get("coef")
+        if coef is not None and self.kind != "const":
+            # -div(rho grad u) = -rho Lap u - grad rho . grad u for the closed-form u
+            return (-coef.rho(xy) * self.lap_u(xy)
+                    - (coef.grad(xy) * self.grad_u(xy)).sum(-1))
         x, y = xy[..., 0], xy[..., 1]
+        if self.kind == "const":
+            return np.full(x.shape, float(self.params.get("value", 1.0)))
         if self.kind == "sinsin":
             return 2.0 * math.pi ** 2 * np.sin(math.pi * x) * np.sin(math.pi * y)
         if self.kind == "sin2pi_exp":
@@ -286,14 +293,102 @@ class Source:
             return np.stack([gx_, gy_], axis=-1)
         raise ValueError(f"no closed-form solution for {self.kind}")
 
+    def lap_u(self, xy):
+        """Laplacian of the closed-form solution."""
+        x, y = xy[..., 0], xy[..., 1]
+        pi = math.pi
+        if self.kind == "sinsin":
+            return -2.0 * pi ** 2 * np.sin(pi * x) * np.sin(pi * y)
+        if self.kind == "sin2pi_exp":
+            return (1.0 - 4.0 * pi ** 2) * np.sin(2.0 * pi * x) * np.exp(y)
+        if self.kind == "fourier":
+            a = self.params["a"]
+            out = np.zeros_like(x)
+            for k in range(a.shape[0]):
+                for l in range(a.shape[1]):
+                    out -= a[k, l] * np.sin((k + 1) * pi * x) * np.sin((l + 1) * pi * y)
+            return out
+        raise ValueError(f"no closed-form solution for {self.kind}")
+
     def g(self, xy):
-        if self.kind in ("fourier", "grf"):
+        if self.kind in ("fourier", "grf", "const"):
             return np.zeros(xy.shape[:-1])
         return self.u(xy)
 
     @property
     def has_exact(self) -> bool:
         return self.kind in ("sinsin", "sin2pi_exp", "fourier")
+
+
+# --------------------------------------------------------------------------
+# Variable coefficient of -div(rho grad u) = f (Section 4, variable-coefficient
+# Poisson): rho and grad rho at points; these are problem data, not the method
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Coefficient:
+    """``sine``: rho = 1 + amp sin(2 pi k . x) with an integer wave vector k.
+    ``grf``: rho = tanh(grf(x)) + 1.1 with grf the approximate Gaussian random field of
+    Eq. (4.5) (the paper's coefficient, between 0.1 and 2.1).
+    ``const``: rho = value (reduces the operator to value * (-Laplacian))."""
+    kind: str
+    params: dict
+
+    def _grf(self, xy):
+        a, w, b = self.params["a"], self.params["w"], self.params["b"]
+        z = xy[..., 0, None] * w[:, 0] + xy[..., 1, None] * w[:, 1] + b
+        return (a * np.sin(z)).sum(-1), np.stack([(a * np.cos(z) * w[:, 0]).sum(-1),
+                                                  (a * np.cos(z) * w[:, 1]).sum(-1)], axis=-1)
+
+    def rho(self, xy):
+        if self.kind == "sine":
+            k, amp = self.params["k"], self.params["amp"]
+            return 1.0 + amp * np.sin(2.0 * math.pi * (xy[..., 0] * k[0] + xy[..., 1] * k[1]))
+        if self.kind == "grf":
+            return np.tanh(self._grf(xy)[0]) + 1.1
+        if self.kind == "const":
+            return np.full(xy.shape[:-1], float(self.params["value"]))
+        raise ValueError(self.kind)
+
+    def grad(self, xy):
+        if self.kind == "sine":
+            k, amp = self.params["k"], self.params["amp"]
+            c = amp * 2.0 * math.pi * np.cos(2.0 * math.pi * (xy[..., 0] * k[0] + xy[..., 1] * k[1]))
+            return np.stack([c * k[0], c * k[1]], axis=-1)
+        if self.kind == "grf":
+            g, dg = self._grf(xy)
+            return (1.0 - np.tanh(g) ** 2)[..., None] * dg
+        if self.kind == "const":
+            return np.zeros(xy.shape[:-1] + (2,))
+        raise ValueError(self.kind)
+
+
+def make_coefficient(kind: str, seed: int = 0, amp: float = 0.5, alpha: float = 16.0,
+                     value: float = 1.0) -> Coefficient:
+    """``sine``: k = (k1, k2) with k_i uniform in {1..4} (seeded); ``grf``: Eq. (4.5) with
+    256 terms as make_source('grf'); ``const``: rho = value."""
+    rng = np.random.default_rng(seed)
+    if kind == "sine":
+        return Coefficient(kind, {"k": rng.integers(1, 5, size=2).astype(np.float64), "amp": amp})
+    if kind == "grf":
+        a = rng.normal(0.0, alpha ** 2 / 16.0, size=256)
+        w = rng.normal(0.0, alpha, size=(256, 2))
+        b = rng.uniform(0.0, 2.0 * math.pi, size=256)
+        return Coefficient(kind, {"a": a, "w": w, "b": b})
+    if kind == "const":
+        return Coefficient(kind, {"value": value})
+    raise ValueError(kind)
+
+
+def coef_rows(geom: Geometry, coef: Coefficient) -> np.ndarray:
+    """Per-row coefficient data [N, m_max, 3] = (rho, d rho/dx, d rho/dy) at every
+    collocation point (only interior rows enter the operator); zero on padding."""
+    out = np.zeros((geom.n_sub, geom.m_max, 3))
+    for s in range(geom.n_sub):
+        m = int(geom.counts[s].sum())
+        out[s, :m, 0] = coef.rho(geom.xy[s, :m])
+        out[s, :m, 1:] = coef.grad(geom.xy[s, :m])
+    return out
 
 
 def make_source(kind: str, seed: int = 0, modes: int = 4, alpha: float = 16.0) -> Source:
@@ -309,6 +404,8 @@ def make_source(kind: str, seed: int = 0, modes: int = 4, alpha: float = 16.0) -
         w = rng.normal(0.0, alpha, size=(256, 2))
         b = rng.uniform(0.0, 2.0 * math.pi, size=256)
         return Source(kind, {"a": a, "w": w, "b": b})
+    if kind == "const":
+        return Source(kind, {"value": 1.0})
     return Source(kind, {})
 
 
@@ -349,16 +446,25 @@ class Workload:
     rhs: np.ndarray          # [N, m_max]
     test_xy: np.ndarray      # [T, 2]
     test_owner: np.ndarray   # [T]
+    coef: Coefficient | None = None      # variable coefficient (None: -Laplacian)
+    coef_rows: np.ndarray | None = None  # [N, m_max, 3]: rho, grad rho at every row
 
 
 def build(gx, gy, n_neurons, mi_x, mi_y, p_bnd, p_ifc, theta="paper", theta_seed=0,
           source="sinsin", source_seed=0, modes=4, c=1.0 / 8.0, name="custom",
-          n_test_side=100, m_max=None) -> Workload:
+          n_test_side=100, m_max=None, coef=None, coef_seed=0, coef_alpha=16.0) -> Workload:
+    """coef: None (-Laplacian) or a make_coefficient kind; with a coefficient the
+    source's f becomes -div(rho grad u) of its closed-form u (or stays f = 1 for 'const')."""
     geom = make_geometry(gx, gy, mi_x, mi_y, p_bnd, p_ifc, m_max=m_max)
     W, b = draw_theta(geom, n_neurons, theta, theta_seed, c=c)
     src = make_source(source, source_seed, modes=modes)
+    cf = None
+    if coef is not None:
+        cf = make_coefficient(coef, coef_seed, alpha=coef_alpha)
+        src.params["coef"] = cf
     txy, own = test_points(geom, n_test_side)
-    return Workload(name, geom, n_neurons, W, b, src, rhs_rows(geom, src), txy, own)
+    return Workload(name, geom, n_neurons, W, b, src, rhs_rows(geom, src), txy, own, cf,
+                    coef_rows(geom, cf) if cf is not None else None)
 
 
 def poisson_2x2_n200() -> Workload:
@@ -390,7 +496,24 @@ def poisson_4x4_n1000() -> Workload:
                  source="fourier", source_seed=2, modes=4, name="poisson_4x4_n1000")
 
 
+def varcoef_4x4_n800() -> Workload:
+    """-div(rho grad u) = f with rho = 1 + 0.5 sin(2 pi k . x), k_i uniform in {1..4}
+    (seed 4); 4x4 subdomains, 800 neurons, 2 n_N interior points (40x40), 64 points per
+    edge, manufactured u = sin(pi x) sin(pi y), paper initialisation (seed 4)."""
+    return build(4, 4, 800, 40, 40, 64, 64, theta="paper", theta_seed=4, source="sinsin",
+                 coef="sine", coef_seed=4, name="varcoef_4x4_n800")
+
+
+def varcoef_grf_4x4_n800() -> Workload:
+    """The paper's variable-coefficient problem: rho = tanh(grf) + 1.1 (alpha = 16,
+    seed 6), f = 1, g = 0 (no closed form; its FEM reference is out of scope)."""
+    return build(4, 4, 800, 40, 40, 64, 64, theta="paper", theta_seed=6, source="const",
+                 coef="grf", coef_seed=6, name="varcoef_grf_4x4_n800")
+
+
 WORKLOADS = {
+    "varcoef_4x4_n800": varcoef_4x4_n800,
+    "varcoef_grf_4x4_n800": varcoef_grf_4x4_n800,
     "poisson_2x2_n200": poisson_2x2_n200,
     "poisson_4x4_n1000": poisson_4x4_n1000,
     "poisson_8x8_n1000": poisson_8x8_n1000,

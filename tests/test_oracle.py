@@ -285,3 +285,67 @@ def test_cg_on_schur_system_reaches_cholesky_solution():
     assert ok
     kappa = np.linalg.cond(res.S)
     assert np.linalg.norm(u - res.u_gamma) <= 2 * kappa * tol * np.linalg.norm(res.u_gamma)
+
+
+# --- variable coefficient -div(rho grad u) = f (Section 4) ---
+
+def test_varcoef_rows_match_conservative_finite_differences():
+    """Interior rows against a flux-form difference of -div(rho grad phi) with the
+    coefficient evaluated at half points (independent of the closed form)."""
+    w = tiny(gx=2, gy=2, n=7, mi=4, p=3, seed=5)
+    g = w.geom
+    cf = wl.make_coefficient("sine", seed=3)
+    crow = wl.coef_rows(g, cf)
+    h = 1e-4
+    for s in range(g.n_sub):
+        K, _ = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s], crow[s])
+        ri, _, _ = g.rows(s)
+        W, b = w.W[s], w.b[s]
+
+        def phi(p):
+            return np.tanh(p @ W.T + b)
+        for r in range(ri.start, ri.stop):
+            p0 = g.xy[s, r]
+            div = 0.0
+            for e in (np.array([h, 0.0]), np.array([0.0, h])):
+                rp, rm = cf.rho(p0 + e / 2), cf.rho(p0 - e / 2)
+                div = div + (rp * (phi(p0 + e) - phi(p0)) - rm * (phi(p0) - phi(p0 - e))) / h ** 2
+            np.testing.assert_allclose(K[r], -div, rtol=1e-5, atol=1e-3)
+
+
+def test_unit_coefficient_reduces_to_poisson_rows():
+    w = tiny(gx=2, gy=2, n=9, mi=5, p=4, seed=6)
+    g = w.geom
+    crow = wl.coef_rows(g, wl.make_coefficient("const", value=1.0))
+    for s in range(g.n_sub):
+        K0, A0 = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s])
+        K1, A1 = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s], crow[s])
+        assert np.array_equal(K0, K1) and np.array_equal(A0, A1)
+
+
+def test_varcoef_manufactured_source_and_routes():
+    """f of the manufactured problem is -div(rho grad u) (checked by differences of u),
+    and the DDM route equals the monolithic LS of Eq. (3.3) with the coefficient."""
+    w = wl.build(2, 2, 12, 6, 6, 6, 6, theta="paper", theta_seed=3, c=0.5, source="sinsin",
+                 coef="sine", coef_seed=2, n_test_side=8)
+    cf, src, h = w.coef, w.src, 1e-4
+    p0 = np.array([[0.31, 0.67], [0.52, 0.18]])
+    div = 0.0
+    for e in (np.array([h, 0.0]), np.array([0.0, h])):
+        div = div + (cf.rho(p0 + e / 2) * (src.u(p0 + e) - src.u(p0))
+                     - cf.rho(p0 - e / 2) * (src.u(p0) - src.u(p0 - e))) / h ** 2
+    np.testing.assert_allclose(src.f(p0), -div, rtol=1e-6)
+    res = O.solve(w.geom, w.W, w.b, w.rhs, coef=w.coef_rows)
+    c_m, u_m = O.monolithic_ls(w.geom, w.W, w.b, w.rhs, coef=w.coef_rows)
+    assert np.linalg.norm(res.u_gamma - u_m) <= 1e-10 * np.linalg.norm(u_m)
+
+
+def test_varcoef_error_falls_with_neurons():
+    errs = []
+    for n, m in ((30, 8), (120, 16)):
+        w = wl.build(2, 2, n, m, m, m, m, theta="local_unit", theta_seed=1, source="sinsin",
+                     coef="sine", coef_seed=2, n_test_side=20)
+        res = O.solve(w.geom, w.W, w.b, w.rhs, coef=w.coef_rows)
+        u, g = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
+        errs.append(np.linalg.norm(u - w.src.u(w.test_xy)) / np.linalg.norm(w.src.u(w.test_xy)))
+    assert errs[1] < 0.1 * errs[0] and errs[1] < 1e-4, errs
