@@ -296,7 +296,7 @@ def run_ours(args):
     clocks = ClockSampler(torch.cuda.current_device() if ws == 1 else local)
     clocks.start()
     time.sleep(0.3)
-    l0 = s.launches
+    l0 = s.kernels_launched
     barrier()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -306,7 +306,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
-    launches = (s.launches - l0) // args.steps
+    launches = (s.kernels_launched - l0) // args.steps
     clk = clocks.stop()
     prof = s.profile_report()
     s.profile(False)

@@ -210,9 +210,10 @@ int elm_ddm_interface_order(const elm_ddm_handle* h, int32_t* order);
 int elm_ddm_export(elm_ddm_handle* h, int what, int s, double* dst, int ld_dst);
 
 /*
- * Queries.  key: 0 = n_gamma, 1 = device workspace bytes, 2 = number of kernel
- * launches enqueued since setup, 3 = number of Schur-matrix edges (interface blocks),
- * 4 = m_max, 5 = n_neurons, 6 = n_sub.
+ * Queries.  key: 0 = n_gamma, 1 = device workspace bytes, 2 = number of launch calls
+ * (one per kernel class invocation, some launch several kernels) enqueued since setup,
+ * 3 = number of Schur-matrix edges (interface blocks), 4 = m_max, 5 = n_neurons,
+ * 6 = n_sub, 7 = CUDA kernels launched by the library in this process (all handles).
  */
 int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value);
 

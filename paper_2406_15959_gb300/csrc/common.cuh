@@ -3,7 +3,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace elmddm {
+
+// Kernels launched by the library in this process (every launcher counts its own).
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launch(int k = 1) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
 
 constexpr int QR_NB = 32;     // panel width of the blocked Householder QR
 constexpr int CHOL_NB = 64;   // block size of the Schur-matrix Cholesky

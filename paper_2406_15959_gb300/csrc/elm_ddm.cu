@@ -14,6 +14,10 @@
 #include <string>
 #include <vector>
 
+namespace elmddm {
+std::atomic<long long> g_kernel_launches{0};
+}  // namespace elmddm
+
 using namespace elmddm;
 
 namespace {
@@ -1233,6 +1237,7 @@ int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value) {
     case 2: *value = (double)h->launches; break;
     case 3: *value = (double)h->edges.size(); break;
     case 4: *value = h->m_max; break;
+    case 7: *value = (double)elmddm::g_kernel_launches.load(); break;
     case 5: *value = h->n; break;
     case 6: *value = h->N; break;
     default: return ELM_DDM_ERR_ARG;

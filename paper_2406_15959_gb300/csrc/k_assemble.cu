@@ -146,7 +146,7 @@ cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, doub
                             int n, const double* coef, unsigned* status, cudaStream_t st) {
   dim3 grid((ld + AR - 1) / AR, (ncap + AC - 1) / AC, N);
   k_assemble<<<grid, dim3(AR, 4), 0, st>>>(K, kstride, ld, ncap, Amat, astride, mgld, xy, nrm,
-                                           m_max, cnt, W, b, n, coef, status);
+                                           m_max, cnt, W, b, n, coef, status); count_launch();
   return cudaGetLastError();
 }
 
@@ -154,7 +154,7 @@ cudaError_t launch_eval(const double* W, const double* b, int N, int n, int npts
                         const double* xy, const int* owner, const double* c, double* u,
                         double* grad, cudaStream_t st) {
   if (npts <= 0) return cudaSuccess;
-  k_eval<<<(npts + 7) / 8, 256, 0, st>>>(W, b, N, n, npts, xy, owner, c, u, grad);
+  k_eval<<<(npts + 7) / 8, 256, 0, st>>>(W, b, N, n, npts, xy, owner, c, u, grad); count_launch();
   return cudaGetLastError();
 }
 

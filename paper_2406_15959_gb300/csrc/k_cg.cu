@@ -146,11 +146,11 @@ cudaError_t launch_schur_apply(const double* D, const double* M, long long mstri
   if (ng <= 0 || mgmax <= 0) return cudaSuccess;
   const size_t smem = (size_t)mgld * sizeof(double);
   k_schur_apply1<<<dim3((mgmax + 63) / 64, N, nrhs), 256, smem, st>>>(D, M, mstride, mgld, mg, ifc_dof,
-                                                                     p, ng, N, zl, wl);
+                                                                     p, ng, N, zl, wl); count_launch();
   cudaError_t e = launch_gather2(dofmap, ng, mgld, N, wl, wg, 0, nrhs, st);
   if (e != cudaSuccess) return e;
   k_schur_apply2<<<dim3((mgmax + 15) / 16, N, nrhs), 256, smem, st>>>(M, mstride, mgld, mg, ifc_dof, wg,
-                                                                     ng, N, zl);
+                                                                     ng, N, zl); count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_gather2(dofmap, ng, mgld, N, zl, q, 0, nrhs, st);
@@ -158,13 +158,13 @@ cudaError_t launch_schur_apply(const double* D, const double* M, long long mstri
 
 cudaError_t launch_cg_init(const double* b, double* x, double* r, double* p, CgState* state, int ng,
                            int nrhs, cudaStream_t st) {
-  k_cg_init<<<nrhs, 1024, 0, st>>>(b, x, r, p, state, ng);
+  k_cg_init<<<nrhs, 1024, 0, st>>>(b, x, r, p, state, ng); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update(double* x, double* r, double* p, const double* q, CgState* state, int ng,
                              int nrhs, double tol2, cudaStream_t st) {
-  k_cg_update<<<nrhs, 1024, 0, st>>>(x, r, p, q, state, ng, tol2);
+  k_cg_update<<<nrhs, 1024, 0, st>>>(x, r, p, q, state, ng, tol2); count_launch();
   return cudaGetLastError();
 }
 

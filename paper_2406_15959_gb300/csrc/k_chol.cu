@@ -241,7 +241,7 @@ cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, double* inv, uns
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_potrf_diag<<<1, POTRF_THREADS, smem, st>>>(S, ld, k, nb, inv, status);
+  k_potrf_diag<<<1, POTRF_THREADS, smem, st>>>(S, ld, k, nb, inv, status); count_launch();
   return cudaGetLastError();
 }
 
@@ -255,7 +255,7 @@ cudaError_t launch_trsm_chol(double* S, int ld, int n, int k, int nb, cudaStream
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_trsm_chol<<<(rows + 63) / 64, 64, smem, st>>>(S, ld, n, k, nb);
+  k_trsm_chol<<<(rows + 63) / 64, 64, smem, st>>>(S, ld, n, k, nb); count_launch();
   return cudaGetLastError();
 }
 
@@ -264,7 +264,7 @@ cudaError_t launch_chol_fwd(const double* L, int ld, int n, int k, int nb, doubl
   if (row_end < 0 || row_end > n) row_end = n;
   const int rows = row_end - k - nb;
   const int gx = rows > 0 ? (rows + 255) / 256 : 1;
-  k_chol_fwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, row_end, Linv, r, y);
+  k_chol_fwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, row_end, Linv, r, y); count_launch();
   return cudaGetLastError();
 }
 
@@ -274,7 +274,7 @@ cudaError_t launch_chol_bwd(const double* L, int ld, int n, int k, int nb, doubl
   int gx = (k - j_begin + 7) / 8;
   if (gx < 1) gx = 1;
   if (gx > 1024) gx = 1024;
-  k_chol_bwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, j_begin, Linv, y, u);
+  k_chol_bwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, j_begin, Linv, y, u); count_launch();
   return cudaGetLastError();
 }
 

@@ -113,6 +113,7 @@ void gemm_dispatch(bool ta, bool tb, dim3 grid, cudaStream_t st, const GemmDesc*
   else if (ta) k_gemm<true, false, TM, TN><<<grid, 256, 0, st>>>(d, alpha, beta, flags);
   else if (tb) k_gemm<false, true, TM, TN><<<grid, 256, 0, st>>>(d, alpha, beta, flags);
   else k_gemm<false, false, TM, TN><<<grid, 256, 0, st>>>(d, alpha, beta, flags);
+  count_launch();
 }
 
 cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_tiles,
@@ -134,7 +135,7 @@ cudaError_t launch_add_blocks(const AddDesc* d, int count, int max_elems, cudaSt
   if (bx > 64) bx = 64;
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
-    k_add_blocks<<<dim3(bx, c), 256, 0, st>>>(d + off);
+    k_add_blocks<<<dim3(bx, c), 256, 0, st>>>(d + off); count_launch();
   }
   return cudaGetLastError();
 }

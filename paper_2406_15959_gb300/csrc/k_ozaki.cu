@@ -980,7 +980,7 @@ cudaError_t launch_oz(const OzDesc* d, int count, int max_tiles, double alpha, d
   }
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
-    k_ozaki<NT><<<dim3(max_tiles, c), OZ_THREADS, smem, st>>>(d + off, alpha, beta, flags, status);
+    k_ozaki<NT><<<dim3(max_tiles, c), OZ_THREADS, smem, st>>>(d + off, alpha, beta, flags, status); count_launch();
   }
   return cudaGetLastError();
 }
@@ -998,8 +998,8 @@ cudaError_t launch_split(const SplitDesc* d, int count, int max_rows, int max_sp
   if (count <= 0) return cudaSuccess;
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
-    k_rowexp<<<dim3((max_rows + 7) / 8, c), 256, 0, st>>>(d + off);
-    k_split<<<dim3(max_split_blocks, c), 256, 0, st>>>(d + off);
+    k_rowexp<<<dim3((max_rows + 7) / 8, c), 256, 0, st>>>(d + off); count_launch();
+    k_split<<<dim3(max_split_blocks, c), 256, 0, st>>>(d + off); count_launch();
   }
   return cudaGetLastError();
 }
@@ -1047,6 +1047,7 @@ cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int 
   else if (mode == 1) { if (ident) ELM_UPD(1, true); else ELM_UPD(1, false); }
   else { if (ident) ELM_UPD(2, true); else ELM_UPD(2, false); }
 #undef ELM_UPD
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -1061,7 +1062,7 @@ cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned*
   }
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
-    k_ozaki_fa<<<dim3(max_tiles, c), FA_THREADS, FA_SMEM, st>>>(d + off, status);
+    k_ozaki_fa<<<dim3(max_tiles, c), FA_THREADS, FA_SMEM, st>>>(d + off, status); count_launch();
   }
   return cudaGetLastError();
 }

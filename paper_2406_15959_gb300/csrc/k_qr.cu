@@ -580,10 +580,10 @@ cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms,
       attr = true;
     }
     k_panel_qr_cl<<<dim3(PCL, N), 256, smem, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride,
-                                                   Vp, vstride, status);
+                                                   Vp, vstride, status); count_launch();
   } else {
     k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride, Vp, vstride,
-                                  status);
+                                  status); count_launch();
   }
   return cudaGetLastError();
 }
@@ -592,7 +592,7 @@ cudaError_t launch_trsm_y(double* Y, long long ystride, int mgld, const double* 
                           long long kstride, int ld, const int* mg, int mgmax, int N, int n,
                           cudaStream_t st) {
   if (mgmax <= 0) return cudaSuccess;
-  k_trsm_y<<<dim3((mgmax + 31) / 32, N), 256, 0, st>>>(Y, ystride, mgld, K, kstride, ld, mg, n);
+  k_trsm_y<<<dim3((mgmax + 31) / 32, N), 256, 0, st>>>(Y, ystride, mgld, K, kstride, ld, mg, n); count_launch();
   return cudaGetLastError();
 }
 
@@ -607,20 +607,20 @@ cudaError_t launch_trsm_y_diag(double* Y, long long ystride, int mgld, const dou
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_trsm_y_diag<<<dim3((mgmax + 63) / 64, N), 64, smem, st>>>(Y, ystride, mgld, K, kstride, ld, mg, n, c0);
+  k_trsm_y_diag<<<dim3((mgmax + 63) / 64, N), 64, smem, st>>>(Y, ystride, mgld, K, kstride, ld, mg, n, c0); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_load_rhs(double* X, const double* rhs, int N, int m_max, int ld,
                             const int* cnt, int nrhs, unsigned* status, cudaStream_t st) {
-  k_load_rhs<<<dim3((ld + 255) / 256, N, nrhs), 256, 0, st>>>(X, rhs, N, m_max, ld, cnt, status);
+  k_load_rhs<<<dim3((ld + 255) / 256, N, nrhs), 256, 0, st>>>(X, rhs, N, m_max, ld, cnt, status); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply_qt(double* X, const double* K, long long kstride, int ld,
                             const int* ms, int N, int n, const double* T, long long tstride,
                             int nrhs, cudaStream_t st) {
-  k_apply_qt<<<dim3(N, nrhs), 256, 0, st>>>(X, K, kstride, ld, ms, N, n, T, tstride);
+  k_apply_qt<<<dim3(N, nrhs), 256, 0, st>>>(X, K, kstride, ld, ms, N, n, T, tstride); count_launch();
   return cudaGetLastError();
 }
 
@@ -628,7 +628,7 @@ cudaError_t launch_iface_vecs(const double* X, const double* K, long long kstrid
                               const double* Y, long long ystride, int mgld, const int* mg,
                               int N, int n, int nrhs, double* gq, double* hq, cudaStream_t st) {
   k_iface_vecs<<<dim3(N, nrhs), 256, 0, st>>>(X, K, kstride, ld, Y, ystride, mgld, mg, N, n, gq,
-                                              hq);
+                                              hq); count_launch();
   return cudaGetLastError();
 }
 
@@ -636,21 +636,21 @@ cudaError_t launch_gather2(const int* dofmap, int n_gamma, int mgld, int N, cons
                            double* out, int accumulate, int nrhs, cudaStream_t st) {
   if (n_gamma <= 0) return cudaSuccess;
   k_gather2<<<dim3((n_gamma + 255) / 256, nrhs), 256, 0, st>>>(dofmap, n_gamma, mgld, N, a, out,
-                                                               accumulate);
+                                                               accumulate); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_perm(const int* idx, int n, const double* src, double* dst, int nrhs,
                                cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_gather_perm<<<dim3((n + 255) / 256, nrhs), 256, 0, st>>>(idx, n, src, dst);
+  k_gather_perm<<<dim3((n + 255) / 256, nrhs), 256, 0, st>>>(idx, n, src, dst); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_mt_h(const double* M, long long mstride, int mgld, const int* mg,
                         const int* ifc_dof, const double* h, int n_gamma, int N, int nrhs,
                         double* z, cudaStream_t st) {
-  k_mt_h<<<dim3(N, nrhs), 256, 0, st>>>(M, mstride, mgld, mg, ifc_dof, h, n_gamma, N, z);
+  k_mt_h<<<dim3(N, nrhs), 256, 0, st>>>(M, mstride, mgld, mg, ifc_dof, h, n_gamma, N, z); count_launch();
   return cudaGetLastError();
 }
 
@@ -664,7 +664,7 @@ cudaError_t launch_backsolve(const double* X, const double* K, long long kstride
     if (e != cudaSuccess) return e;
   }
   k_backsolve<<<dim3(N, nrhs), 256, smem, st>>>(X, K, kstride, ld, mg, ifc_dof, mgld, u, n_gamma,
-                                                N, n, c);
+                                                N, n, c); count_launch();
   return cudaGetLastError();
 }
 

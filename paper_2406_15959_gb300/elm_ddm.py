@@ -152,6 +152,11 @@ class Solver:
         return int(self.info(2))
 
     @property
+    def kernels_launched(self) -> int:
+        """CUDA kernels the library has launched in this process."""
+        return int(self.info(7))
+
+    @property
     def workspace_bytes(self) -> int:
         return int(self.info(1))
 
