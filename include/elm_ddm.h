@@ -165,6 +165,19 @@ int elm_ddm_solve_cg(elm_ddm_handle* h, const double* rhs, int nrhs, double tol,
                      double* u_gamma, double* c, int* iters);
 
 /*
+ * As elm_ddm_solve_cg, started from an initial guess and optionally preconditioned (the
+ * paper names no preconditioner; a learned initial guess is the warm start of the
+ * learned-interface extension):
+ *   x0      device double [nrhs][n_gamma] initial u_Gamma in the caller's order, or NULL (zero)
+ *   jacobi  1: preconditioner diag(S)^{-1} (needs the assembled S, i.e. not
+ *           ELM_DDM_FLAG_SCHUR_CG; ERR_STATE otherwise), 0: none
+ * The stopping rule is on the true residual of the recurrence, |r| <= tol |rhs|, checked
+ * also at the start (a guess that already meets it takes 0 steps).
+ */
+int elm_ddm_solve_pcg(elm_ddm_handle* h, const double* rhs, int nrhs, const double* x0, int jacobi,
+                      double tol, int maxit, double* u_gamma, double* c, int* iters);
+
+/*
  * u(x) = sum_j c^s_j tanh(w^s_j . x + b^s_j) and grad u at npts points, s = owner[i].
  *   xy     device double [npts][2]
  *   owner  device int32  [npts]   subdomain index of each point, in [0, N)

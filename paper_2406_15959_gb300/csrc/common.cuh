@@ -68,9 +68,9 @@ struct OzDesc {
 
 // Per right-hand side state of the CG solve of the Schur system (k_cg.cu).
 struct CgState {
-  double rr, bb;  // r^T r of the current residual, b^T b
-  int iters;      // CG steps taken
-  int done;       // 0 running, 1 converged, 2 breakdown (p^T S p <= 0 or not finite)
+  double rr, rz, bb;  // r^T r of the current residual, r^T M^{-1} r, b^T b
+  int iters;          // CG steps taken
+  int done;           // 0 running, 1 converged, 2 breakdown (p^T S p <= 0 or not finite)
 };
 
 // ---- launchers (return cudaGetLastError after the launch) ----
@@ -152,10 +152,14 @@ cudaError_t launch_schur_apply(const double* D, const double* M, long long mstri
                                const int* mg, int mgmax, const int* ifc_dof, const int* dofmap,
                                const double* p, double* q, double* zl, double* wl, double* wg,
                                int ng, int N, int nrhs, cudaStream_t st);
-cudaError_t launch_cg_init(const double* b, double* x, double* r, double* p, CgState* state, int ng,
-                           int nrhs, cudaStream_t st);
-cudaError_t launch_cg_update(double* x, double* r, double* p, const double* q, CgState* state, int ng,
-                             int nrhs, double tol2, cudaStream_t st);
+// (Preconditioned) CG on the Schur system: dinv = 1 / diag(S) (Jacobi) or NULL.
+cudaError_t launch_pcg_init(const double* b, const double* q, double* r, double* p, const double* dinv,
+                            CgState* state, int ng, int nrhs, int has_x0, double tol2, cudaStream_t st);
+cudaError_t launch_pcg_update(double* x, double* r, double* p, const double* q, const double* dinv,
+                              CgState* state, int ng, int nrhs, double tol2, cudaStream_t st);
+cudaError_t launch_scatter_perm(const int* idx, int n, const double* src, double* dst, int nrhs,
+                                cudaStream_t st);
+cudaError_t launch_diag_inv(const double* S, int n, double* dinv, cudaStream_t st);
 
 // ---- device helpers ----
 #ifdef __CUDACC__

@@ -137,6 +137,8 @@ struct elm_ddm_handle {
   bool coef_set = false;
   double *cg_p = nullptr, *cg_q = nullptr;  // CG search direction and S p, [max_rhs][ng]
   CgState* cg_st = nullptr;                 // [max_rhs]
+  double* sdinv = nullptr;                  // 1 / diag(S), internal order (Jacobi), set by schur
+  bool has_sdinv = false;
   void* sp_buf = nullptr;        // digit tiles and row exponents of the split operands
   std::vector<int> qr_first;     // first record of each panel in qr_recs
   // algorithmic flops of each Householder panel launch: per subdomain a m' x nb panel
@@ -468,6 +470,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->cg_p, (size_t)max_rhs * std::max(ng, 1)) &&
             dev_alloc(h, &h->cg_q, (size_t)max_rhs * std::max(ng, 1)) &&
             dev_alloc(h, &h->cg_st, (size_t)max_rhs) &&
+            dev_alloc(h, &h->sdinv, (size_t)std::max(ng, 1)) &&
             dev_alloc(h, &h->coef, h->op == ELM_DDM_OP_VARCOEF ? (size_t)N * m_max * 3 : (size_t)1) &&
             dev_alloc(h, &h->thW, (size_t)N * n * 2) && dev_alloc(h, &h->thb, (size_t)N * n) &&
             dev_alloc(h, &h->xy, (size_t)N * m_max * 2) &&
@@ -1002,6 +1005,9 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     if (e != cudaSuccess) return cuda_fail(h, e, "schur: memset");
     rc = run_recs(h, h->s_recs, 0, h->s_recs.size(), "gemm_schur");
     if (rc) return rc;
+    // Jacobi preconditioner of the CG solves, taken before the factorisation overwrites S
+    ELM_LAUNCH(h, launch_diag_inv(h->S, h->ng, h->sdinv, h->st), "diag_inv");
+    h->has_sdinv = true;
     for (int k = 0, step = 0; k < h->ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, h->ng - k);
       // nb^3/3 for the factor and as much again for its inverse
@@ -1062,8 +1068,10 @@ int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
   return ELM_DDM_OK;
 }
 
-int elm_ddm_solve_cg(elm_ddm_handle* h, const double* rhs, int nrhs, double tol, int maxit,
-                     double* u_gamma, double* c, int* iters) {
+}  // extern "C"
+
+static int solve_cg_impl(elm_ddm_handle* h, const double* rhs, int nrhs, const double* x0, int jacobi,
+                         double tol, int maxit, double* u_gamma, double* c, int* iters) {
   if (!h) return ELM_DDM_ERR_ARG;
   if (iters) *iters = 0;
   if (h->state != 2) return fail(h, ELM_DDM_ERR_STATE, "solve_cg: call elm_ddm_schur first");
@@ -1071,6 +1079,8 @@ int elm_ddm_solve_cg(elm_ddm_handle* h, const double* rhs, int nrhs, double tol,
   if (nrhs < 1 || nrhs > h->max_rhs) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: nrhs out of range");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: tol must be > 0");
   if (maxit < 1) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: maxit must be >= 1");
+  if (jacobi && !h->has_sdinv)
+    return fail(h, ELM_DDM_ERR_STATE, "solve_cg: Jacobi needs the assembled S (not ELM_DDM_FLAG_SCHUR_CG)");
   const int N = h->N, n = h->n, ng = h->ng;
   ELM_LAUNCH(h, launch_load_rhs(h->X, rhs, N, h->m_max, h->ld, h->cnt, nrhs, h->status, h->st),
              "load_rhs");
@@ -1088,17 +1098,36 @@ int elm_ddm_solve_cg(elm_ddm_handle* h, const double* rhs, int nrhs, double tol,
                               h->st), "mt_h");
     ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
     // CG: x in uv, r in yv; gq / hq / hv are free now and serve as the operator's scratch
-    ELM_LAUNCH(h, launch_cg_init(h->rv, h->uv, h->yv, h->cg_p, h->cg_st, ng, nrhs, h->st), "cg_init");
-    std::vector<CgState> hs(nrhs);
     const double tol2 = tol * tol;
-    for (int it = 0; it < maxit;) {
+    const double* dinv = jacobi ? h->sdinv : nullptr;
+    if (x0) {  // start from the caller's guess: x = x0 (internal order), q = S x
+      ELM_LAUNCH(h, launch_scatter_perm(h->perm, ng, x0, h->uv, nrhs, h->st), "cg_x0");
+      ELM_LAUNCH(h, launch_schur_apply(h->D, h->M, h->mstride, h->mgld, h->mg, h->mgmax, h->ifc_dof,
+                                       h->dofmap, h->uv, h->cg_q, h->gq, h->hq, h->hv, ng, N, nrhs,
+                                       h->st), "cg_apply");
+    } else {
+      cudaError_t e = cudaMemsetAsync(h->uv, 0, (size_t)nrhs * ng * sizeof(double), h->st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "solve_cg: x0");
+    }
+    ELM_LAUNCH(h, launch_pcg_init(h->rv, h->cg_q, h->yv, h->cg_p, dinv, h->cg_st, ng, nrhs, x0 ? 1 : 0,
+                                  tol2, h->st), "cg_init");
+    std::vector<CgState> hs(nrhs);
+    {
+      cudaError_t e = cudaMemcpyAsync(hs.data(), h->cg_st, nrhs * sizeof(CgState), cudaMemcpyDeviceToHost,
+                                      h->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "solve_cg: state");
+    }
+    bool start_done = true;
+    for (const CgState& q : hs) start_done = start_done && q.done != 0;
+    for (int it = 0; it < maxit && !start_done;) {
       const int chunk = std::min(16, maxit - it);
       for (int k = 0; k < chunk; ++k) {
         ELM_LAUNCH(h, launch_schur_apply(h->D, h->M, h->mstride, h->mgld, h->mg, h->mgmax, h->ifc_dof,
                                          h->dofmap, h->cg_p, h->cg_q, h->gq, h->hq, h->hv, ng, N, nrhs,
                                          h->st), "cg_apply");
-        ELM_LAUNCH(h, launch_cg_update(h->uv, h->yv, h->cg_p, h->cg_q, h->cg_st, ng, nrhs, tol2, h->st),
-                   "cg_update");
+        ELM_LAUNCH(h, launch_pcg_update(h->uv, h->yv, h->cg_p, h->cg_q, dinv, h->cg_st, ng, nrhs, tol2,
+                                        h->st), "cg_update");
       }
       it += chunk;
       cudaError_t e = cudaMemcpyAsync(hs.data(), h->cg_st, nrhs * sizeof(CgState), cudaMemcpyDeviceToHost,
@@ -1121,6 +1150,18 @@ int elm_ddm_solve_cg(elm_ddm_handle* h, const double* rhs, int nrhs, double tol,
   if (iters) *iters = taken;
   if (!converged) return fail(h, ELM_DDM_ERR_NOCONV, "solve_cg: relative residual above tol");
   return ELM_DDM_OK;
+}
+
+extern "C" {
+
+int elm_ddm_solve_cg(elm_ddm_handle* h, const double* rhs, int nrhs, double tol, int maxit,
+                     double* u_gamma, double* c, int* iters) {
+  return solve_cg_impl(h, rhs, nrhs, nullptr, 0, tol, maxit, u_gamma, c, iters);
+}
+
+int elm_ddm_solve_pcg(elm_ddm_handle* h, const double* rhs, int nrhs, const double* x0, int jacobi,
+                      double tol, int maxit, double* u_gamma, double* c, int* iters) {
+  return solve_cg_impl(h, rhs, nrhs, x0, jacobi, tol, maxit, u_gamma, c, iters);
 }
 
 int elm_ddm_eval(elm_ddm_handle* h, int npts, const double* xy, const int32_t* owner,

@@ -75,41 +75,53 @@ __global__ void __launch_bounds__(256) k_schur_apply2(const double* __restrict__
   }
 }
 
-// x = 0, r = p = b, rr = bb = b^T b.  One block per right-hand side.
-__global__ void __launch_bounds__(1024) k_cg_init(const double* __restrict__ b, double* __restrict__ x,
-                                                  double* __restrict__ r, double* __restrict__ p,
-                                                  CgState* __restrict__ st, int ng) {
+// Start of (preconditioned) CG from x (zero or the caller's guess, with q = S x already
+// formed): r = b - q, z = M^{-1} r, p = z; rr = r^T r, rz = r^T z, bb = b^T b.  M is the
+// Jacobi preconditioner diag(S) (dinv = its inverse) or the identity (dinv = NULL).
+// One block per right-hand side.
+__global__ void __launch_bounds__(1024) k_pcg_init(const double* __restrict__ b, const double* __restrict__ q,
+                                                   double* __restrict__ r, double* __restrict__ p,
+                                                   const double* __restrict__ dinv, CgState* __restrict__ st,
+                                                   int ng, int has_x0, double tol2) {
   __shared__ double red[33];
   const int rh = blockIdx.x, tid = threadIdx.x;
   const size_t o = (size_t)rh * ng;
-  double bb = 0.0;
+  double bb = 0.0, rr = 0.0, rz = 0.0;
   for (int g = tid; g < ng; g += blockDim.x) {
-    const double v = b[o + g];
-    x[o + g] = 0.0;
-    r[o + g] = v;
-    p[o + g] = v;
-    bb = fma(v, v, bb);
+    const double bv = b[o + g];
+    const double rg = has_x0 ? bv - q[o + g] : bv;
+    const double zg = dinv ? rg * dinv[g] : rg;
+    r[o + g] = rg;
+    p[o + g] = zg;
+    bb = fma(bv, bv, bb);
+    rr = fma(rg, rg, rr);
+    rz = fma(rg, zg, rz);
   }
   bb = block_sum(bb, red);
+  rr = block_sum(rr, red);
+  rz = block_sum(rz, red);
   if (tid == 0) {
-    st[rh].rr = bb;
+    st[rh].rr = rr;
+    st[rh].rz = rz;
     st[rh].bb = bb;
     st[rh].iters = 0;
-    st[rh].done = (bb == 0.0 || !isfinite(bb)) ? (isfinite(bb) ? 1 : 2) : 0;
+    st[rh].done = !isfinite(rr) || !isfinite(rz) ? 2 : (rr <= tol2 * bb ? 1 : 0);
   }
 }
 
-// One CG step for every right-hand side not yet converged: alpha = rr / p^T q,
-// x += alpha p, r -= alpha q, beta = r^T r / rr, p = r + beta p.  done = 1 once
-// r^T r <= tol^2 b^T b; done = 2 if p^T q <= 0 (S not positive definite in floating
-// point) or a quantity is not finite.
-__global__ void __launch_bounds__(1024) k_cg_update(double* __restrict__ x, double* __restrict__ r,
-                                                    double* __restrict__ p, const double* __restrict__ q,
-                                                    CgState* __restrict__ st, int ng, double tol2) {
+// One (preconditioned) CG step for every right-hand side not yet converged:
+// alpha = rz / p^T q, x += alpha p, r -= alpha q, z = M^{-1} r, beta = r^T z / rz,
+// p = z + beta p.  done = 1 once r^T r <= tol^2 b^T b (the true residual of the
+// recurrence, not the preconditioned one); done = 2 if p^T q <= 0 (S not positive
+// definite in floating point) or a quantity is not finite.
+__global__ void __launch_bounds__(1024) k_pcg_update(double* __restrict__ x, double* __restrict__ r,
+                                                     double* __restrict__ p, const double* __restrict__ q,
+                                                     const double* __restrict__ dinv,
+                                                     CgState* __restrict__ st, int ng, double tol2) {
   __shared__ double red[33];
   const int rh = blockIdx.x, tid = threadIdx.x;
   if (st[rh].done) return;
-  const double rr_old = st[rh].rr, bb = st[rh].bb;
+  const double rz_old = st[rh].rz, bb = st[rh].bb;
   const size_t o = (size_t)rh * ng;
   double pq = 0.0;
   for (int g = tid; g < ng; g += blockDim.x) pq = fma(p[o + g], q[o + g], pq);
@@ -118,23 +130,42 @@ __global__ void __launch_bounds__(1024) k_cg_update(double* __restrict__ x, doub
     if (tid == 0) st[rh].done = 2;
     return;
   }
-  const double alpha = rr_old / pq;
-  double rr = 0.0;
+  const double alpha = rz_old / pq;
+  double rr = 0.0, rz = 0.0;
   for (int g = tid; g < ng; g += blockDim.x) {
     x[o + g] = fma(alpha, p[o + g], x[o + g]);
     const double rg = fma(-alpha, q[o + g], r[o + g]);
     r[o + g] = rg;
     rr = fma(rg, rg, rr);
+    rz = fma(rg, dinv ? rg * dinv[g] : rg, rz);
   }
   rr = block_sum(rr, red);
-  const double beta = rr / rr_old;
-  for (int g = tid; g < ng; g += blockDim.x) p[o + g] = fma(beta, p[o + g], r[o + g]);
+  rz = block_sum(rz, red);
+  const double beta = rz / rz_old;
+  for (int g = tid; g < ng; g += blockDim.x) {
+    const double zg = dinv ? r[o + g] * dinv[g] : r[o + g];
+    p[o + g] = fma(beta, p[o + g], zg);
+  }
   if (tid == 0) {
     st[rh].rr = rr;
+    st[rh].rz = rz;
     st[rh].iters += 1;
-    if (!isfinite(rr)) st[rh].done = 2;
+    if (!isfinite(rr) || !isfinite(rz)) st[rh].done = 2;
     else if (rr <= tol2 * bb) st[rh].done = 1;
   }
+}
+
+// dst[idx[g]] = src[g] for every right-hand side (caller order -> internal order).
+__global__ void k_scatter_perm(const int* __restrict__ idx, int n, const double* __restrict__ src,
+                               double* __restrict__ dst) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, rh = blockIdx.y;
+  if (g < n) dst[(size_t)rh * n + idx[g]] = src[(size_t)rh * n + g];
+}
+
+// dinv[i] = 1 / S[i, i] (the Jacobi preconditioner; S column-major, ld n).
+__global__ void k_diag_inv(const double* __restrict__ S, int n, double* __restrict__ dinv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dinv[i] = 1.0 / S[i + (size_t)i * n];
 }
 
 }  // namespace
@@ -156,15 +187,28 @@ cudaError_t launch_schur_apply(const double* D, const double* M, long long mstri
   return launch_gather2(dofmap, ng, mgld, N, zl, q, 0, nrhs, st);
 }
 
-cudaError_t launch_cg_init(const double* b, double* x, double* r, double* p, CgState* state, int ng,
-                           int nrhs, cudaStream_t st) {
-  k_cg_init<<<nrhs, 1024, 0, st>>>(b, x, r, p, state, ng); count_launch();
+cudaError_t launch_pcg_init(const double* b, const double* q, double* r, double* p, const double* dinv,
+                            CgState* state, int ng, int nrhs, int has_x0, double tol2, cudaStream_t st) {
+  k_pcg_init<<<nrhs, 1024, 0, st>>>(b, q, r, p, dinv, state, ng, has_x0, tol2); count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_update(double* x, double* r, double* p, const double* q, CgState* state, int ng,
-                             int nrhs, double tol2, cudaStream_t st) {
-  k_cg_update<<<nrhs, 1024, 0, st>>>(x, r, p, q, state, ng, tol2); count_launch();
+cudaError_t launch_pcg_update(double* x, double* r, double* p, const double* q, const double* dinv,
+                              CgState* state, int ng, int nrhs, double tol2, cudaStream_t st) {
+  k_pcg_update<<<nrhs, 1024, 0, st>>>(x, r, p, q, dinv, state, ng, tol2); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_perm(const int* idx, int n, const double* src, double* dst, int nrhs,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_scatter_perm<<<dim3((n + 255) / 256, nrhs), 256, 0, st>>>(idx, n, src, dst); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_inv(const double* S, int n, double* dinv, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_diag_inv<<<(n + 255) / 256, 256, 0, st>>>(S, n, dinv); count_launch();
   return cudaGetLastError();
 }
 

@@ -25,7 +25,8 @@ SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve"
            "elm_ddm_eval", "elm_ddm_export", "elm_ddm_check", "elm_ddm_get_info",
            "elm_ddm_profile", "elm_ddm_profile_report", "elm_ddm_destroy",
            "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order",
-           "elm_ddm_profile_only", "elm_ddm_solve_cg", "elm_ddm_set_coefficient")
+           "elm_ddm_profile_only", "elm_ddm_solve_cg", "elm_ddm_set_coefficient",
+           "elm_ddm_solve_pcg")
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
 
 
@@ -74,6 +75,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_profile.argtypes = [P, I]
     lib.elm_ddm_set_coefficient.argtypes = [P, P]
     lib.elm_ddm_solve_cg.argtypes = [P, P, I, ctypes.c_double, I, P, P, ctypes.POINTER(I)]
+    lib.elm_ddm_solve_pcg.argtypes = [P, P, I, P, I, ctypes.c_double, I, P, P, ctypes.POINTER(I)]
     lib.elm_ddm_profile_only.argtypes = [P, ctypes.c_char_p]
     lib.elm_ddm_profile_report.argtypes = [P, ctypes.c_char_p, I]
     lib.elm_ddm_get_info.argtypes = [P, I, D]
@@ -188,8 +190,9 @@ class Solver:
         return u_gamma, c
 
     def solve_cg(self, rhs, tol: float = 1e-9, maxit: int = 10000, u_gamma=None, c=None,
-                 require_convergence: bool = True):
-        """As solve(), with the interface system solved by CG to relative residual tol.
+                 require_convergence: bool = True, x0=None, jacobi: bool = False):
+        """As solve(), with the interface system solved by CG to relative residual tol
+        (from x0 [nrhs, n_gamma] if given, Jacobi-preconditioned if asked).
         Returns (u_gamma, c, iterations)."""
         import torch
         squeeze = rhs.dim() == 2
@@ -200,9 +203,17 @@ class Solver:
         if u_gamma is None and self.n_gamma > 0:
             u_gamma = torch.empty((nrhs, self.n_gamma), dtype=torch.float64, device=rhs.device)
         it = ctypes.c_int(0)
-        rc = self.lib.elm_ddm_solve_cg(self.h, _ptr(r.contiguous()), nrhs, float(tol), int(maxit),
-                                       _ptr(u_gamma) if self.n_gamma > 0 else None, _ptr(c),
-                                       ctypes.byref(it))
+        x0p = None
+        if x0 is not None:
+            x0 = (x0.unsqueeze(0) if x0.dim() == 1 else x0).contiguous()
+            x0p = _ptr(x0)
+        ugp = _ptr(u_gamma) if self.n_gamma > 0 else None
+        if x0p is None and not jacobi:  # the paper's plain CG from zero
+            rc = self.lib.elm_ddm_solve_cg(self.h, _ptr(r.contiguous()), nrhs, float(tol), int(maxit), ugp,
+                                           _ptr(c), ctypes.byref(it))
+        else:
+            rc = self.lib.elm_ddm_solve_pcg(self.h, _ptr(r.contiguous()), nrhs, x0p, int(bool(jacobi)),
+                                            float(tol), int(maxit), ugp, _ptr(c), ctypes.byref(it))
         if rc != ERR_NOCONV or require_convergence:
             self._check_rc(rc)
         if squeeze:

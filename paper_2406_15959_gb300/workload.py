@@ -420,6 +420,21 @@ def rhs_rows(geom: Geometry, src: Source) -> np.ndarray:
     return out
 
 
+def fourier_basis_rows(geom: Geometry, modes: int) -> np.ndarray:
+    """Per-row data [modes*modes, N, m_max] of the sources f = sin(k pi x) sin(l pi y),
+    k, l = 1..modes (row-major in (k, l)), g = 0: the right-hand side of a source with
+    coefficients a is a @ basis (the learned warm start's inputs are these a)."""
+    out = np.zeros((modes * modes, geom.n_sub, geom.m_max))
+    for s in range(geom.n_sub):
+        ri, _, _ = geom.rows(s)
+        x, y = geom.xy[s, ri, 0], geom.xy[s, ri, 1]
+        for k in range(modes):
+            sx = np.sin((k + 1) * math.pi * x)
+            for l in range(modes):
+                out[k * modes + l, s, ri] = sx * np.sin((l + 1) * math.pi * y)
+    return out
+
+
 def test_points(geom: Geometry, n_side: int = 100):
     """n_side^2 cell-centred test points and the subdomain that owns each one
     (owner index min(floor(x*gx), gx-1) per axis)."""

@@ -19,7 +19,7 @@ def declared_symbols():
     for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(hdr).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names |= set(re.findall(r"\b(elm_ddm_\w+)\s*\(", text))
+        names |= set(re.findall(r"\b(elm_(?:ddm|mlp)_\w+)\s*\(", text))
     return names
 
 
@@ -29,7 +29,8 @@ def test_library_exports_every_declared_symbol():
     assert {"elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve"} <= names
     for name in names:
         assert hasattr(lib, name), name
-    assert set(E.SYMBOLS) >= names
+    from paper_2406_15959_gb300 import mlp as M
+    assert set(E.SYMBOLS) | set(M.SYMBOLS) >= names
 
 
 def _setup(desc, counts, xy, nrm, dof):

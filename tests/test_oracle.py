@@ -349,3 +349,43 @@ def test_varcoef_error_falls_with_neurons():
         u, g = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
         errs.append(np.linalg.norm(u - w.src.u(w.test_xy)) / np.linalg.norm(w.src.u(w.test_xy)))
     assert errs[1] < 0.1 * errs[0] and errs[1] < 1e-4, errs
+
+
+# --- the learned warm start's network (oracle/mlp_oracle.py) ---
+
+def test_mlp_gradient_matches_central_differences():
+    from oracle import mlp_oracle as MO
+    rng = np.random.default_rng(21)
+    d_in, d_h, d_out, B = 5, 7, 4, 6
+    n = d_in * d_h + d_h + d_h * d_h + d_h + d_h * d_out + d_out
+    p = rng.standard_normal(n) * 0.5
+    X, T = rng.standard_normal((B, d_in)), rng.standard_normal((B, d_out))
+    _, g = MO.loss_and_grad(p, X, T, d_in, d_h, d_out)
+    h = 1e-6
+    for i in rng.choice(n, size=40, replace=False):
+        e = np.zeros(n)
+        e[i] = h
+        lp, _ = MO.loss_and_grad(p + e, X, T, d_in, d_h, d_out)
+        lm, _ = MO.loss_and_grad(p - e, X, T, d_in, d_h, d_out)
+        assert abs((lp - lm) / (2 * h) - g[i]) <= 1e-7 * max(1.0, abs(g[i]))
+
+
+def test_gelu_matches_its_definition_and_derivative():
+    from oracle import mlp_oracle as MO
+    import math
+    for z in (-3.0, -0.7, 0.0, 0.4, 2.5):
+        phi = 0.5 * (1 + math.erf(z / math.sqrt(2)))
+        assert abs(MO.gelu(np.array(z)) - z * phi) <= 1e-15
+        h = 1e-6
+        fd = (MO.gelu(np.array(z + h)) - MO.gelu(np.array(z - h))) / (2 * h)
+        assert abs(MO.gelu_grad(np.array(z)) - fd) <= 1e-8
+
+
+def test_adam_first_step_is_signed_learning_rate():
+    """With zero moments the bias-corrected first step (Kingma and Ba, Section 2 form
+    with the step size folded: alpha_t = alpha sqrt(1 - b2^t) / (1 - b1^t)) is
+    -lr g / (|g| + eps / sqrt(1 - b2)): the signed learning rate for |g| >> eps."""
+    from oracle import mlp_oracle as MO
+    g = np.array([0.3, -2.0, 1e-3])
+    p1, _, _ = MO.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, 0.01)
+    np.testing.assert_allclose(p1, -0.01 * g / (np.abs(g) + 1e-8 / np.sqrt(1 - 0.999)), rtol=1e-12)
