@@ -82,9 +82,10 @@ class WarmStart:
 
 
 def evaluate(solver, ws: WarmStart, basis: np.ndarray, A: np.ndarray, tol: float = 1e-9,
-             maxit: int = 100000):
-    """Per held-out sample: CG steps from zero and from the prediction (both Jacobi),
-    the prediction's relative error, and each CG result's distance to the direct solve."""
+             maxit: int = 100000, jacobi: bool = True):
+    """Per held-out sample: CG steps from zero and from the prediction (both with or both
+    without the Jacobi preconditioner), the prediction's relative error, and the warm
+    result's distance to the direct solve."""
     import torch
     flat = basis.reshape(basis.shape[0], -1)
     pred = ws.predict(A)
@@ -92,8 +93,8 @@ def evaluate(solver, ws: WarmStart, basis: np.ndarray, A: np.ndarray, tol: float
     for i in range(A.shape[0]):
         rhs = torch.as_tensor((A[i] @ flat).reshape(1, solver.N, solver.m_max), device="cuda")
         ud, _ = solver.solve(rhs)
-        _, _, it0 = solver.solve_cg(rhs, tol=tol, maxit=maxit, jacobi=True)
-        ug1, _, it1 = solver.solve_cg(rhs, tol=tol, maxit=maxit, jacobi=True, x0=pred[i:i + 1])
+        _, _, it0 = solver.solve_cg(rhs, tol=tol, maxit=maxit, jacobi=jacobi)
+        ug1, _, it1 = solver.solve_cg(rhs, tol=tol, maxit=maxit, jacobi=jacobi, x0=pred[i:i + 1])
         nd = float(torch.linalg.norm(ud))
         rows.append({"cold_steps": it0, "warm_steps": it1,
                      "prediction_rel_err": float(torch.linalg.norm(pred[i] - ud[0])) / nd,
@@ -125,16 +126,20 @@ def main(argv=None):
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
     At = np.random.default_rng(99).standard_normal((args.test, args.modes * args.modes))
-    rows = evaluate(s, ws, basis, At)
-    cold = [r["cold_steps"] for r in rows]
-    warm = [r["warm_steps"] for r in rows]
+    out = {}
+    for jac in (False, True):
+        rows = evaluate(s, ws, basis, At, jacobi=jac)
+        key = "jacobi" if jac else "plain"
+        out[key] = {"cold_steps_mean": float(np.mean([r["cold_steps"] for r in rows])),
+                    "warm_steps_mean": float(np.mean([r["warm_steps"] for r in rows])),
+                    "warm_rel_err_vs_direct_max": float(np.max([r["warm_rel_err_vs_direct"]
+                                                                for r in rows]))}
     print(json.dumps({
         "workload": args.workload, "n_gamma": w.geom.n_gamma, "samples": args.samples,
         "generate_s": t_gen, "train_s": t_fit, "epochs": args.epochs,
         "final_train_loss": losses[-1], "test_samples": args.test,
-        "cold_steps_mean": float(np.mean(cold)), "warm_steps_mean": float(np.mean(warm)),
         "prediction_rel_err_mean": float(np.mean([r["prediction_rel_err"] for r in rows])),
-        "warm_rel_err_vs_direct_max": float(np.max([r["warm_rel_err_vs_direct"] for r in rows])),
+        "cg": out,
     }))
 
 
