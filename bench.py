@@ -250,16 +250,13 @@ def run_ours(args):
             s.solve(rt.unsqueeze(0), ug_dev, c_dev)
         s.eval(txy, own, c_dev[0], u_dev, g_dev)
 
+    from paper_2406_15959_gb300 import replicas as R
+
     def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
+        R.barrier(ws)
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return R.max_over_ranks(x, ws, device=dev)
 
     for _ in range(args.warmup):
         step(d["W"], d["b"], d["rhs"])
@@ -375,7 +372,7 @@ def run_ours(args):
                "seconds": t_full}
 
     line = {
-        "metric": METRIC, "value": ws * 1e3 / ms, "unit": "solves/s", "n_gpus": ws,
+        "metric": METRIC, "value": R.job_throughput(ms, ws), "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
@@ -386,7 +383,7 @@ def run_ours(args):
                    "schur_solver": ("cg (unpreconditioned, relative residual 1e-9, matrix-free S)"
                                     if cg else "direct (envelope Cholesky)")},
         "rel_l2_vs_oracle": l2_oracle, "rel_l2_vs_exact": l2_exact,
-        "e2e": {"value": ws * 1e3 / ms_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": R.job_throughput(ms_e2e, ws), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
