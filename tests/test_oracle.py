@@ -389,3 +389,52 @@ def test_adam_first_step_is_signed_learning_rate():
     g = np.array([0.3, -2.0, 1e-3])
     p1, _, _ = MO.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, 0.01)
     np.testing.assert_allclose(p1, -0.01 * g / (np.abs(g) + 1e-8 / np.sqrt(1 - 0.999)), rtol=1e-12)
+
+
+def test_radial_weights_have_density_proportional_to_norm():
+    """Remark 4.2's radial initialisation: w on [-l, l]^2 with density proportional to |w|.
+    Under that density E|w| = E_u|w|^2 / E_u|w| with E_u the uniform square:
+    l (2/3) / ((sqrt 2 + asinh 1) / 3) = 0.8712 l."""
+    import math
+    g = wl.make_geometry(1, 1, 4, 4, 3, 3)
+    W, _ = wl.draw_theta(g, 40000, "radial", seed=3, c=0.125)
+    lim = 0.125 * math.sqrt(40000)
+    r = np.hypot(W[0, :, 0], W[0, :, 1]) / lim
+    expect = (2.0 / 3.0) / ((math.sqrt(2.0) + math.asinh(1.0)) / 3.0)
+    assert abs(r.mean() - expect) < 0.01
+    assert np.abs(W).max() <= lim
+
+
+def _fp32_qr_refinement(w, s=0, iters=12):
+    """Least squares K c = F from an FP32 Householder QR refined in FP64 by the corrected
+    seminormal equations (Bjorck): c <- c + R^{-1} R^{-T} K^T (F - K c) with the FP32 R.
+    Returns (kappa(K), relative error of K c against the FP64 least-squares fit)."""
+    import scipy.linalg as sla
+    g = w.geom
+    K, _ = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s])
+    F = O.rhs_local(w.rhs[s], g.counts[s])
+    ref = K @ np.linalg.lstsq(K, F, rcond=None)[0]
+    Q32, R32 = np.linalg.qr(K.astype(np.float32))
+    R = R32.astype(np.float64)
+    c = sla.solve_triangular(R, Q32.T.astype(np.float64) @ F)
+    for _ in range(iters):
+        c = c + sla.solve_triangular(R, sla.solve_triangular(R.T, K.T @ (F - K @ c), lower=True))
+    sv = np.linalg.svd(K, compute_uv=False)
+    with np.errstate(all="ignore"):
+        err = np.linalg.norm(K @ c - ref) / np.linalg.norm(ref)
+    return sv[0] / sv[-1], err
+
+
+def test_mixed_precision_refinement_needs_kappa_below_inverse_unit_roundoff():
+    """The precision axis: refinement from an FP32-level factorisation converges only when
+    kappa(K) u_32 < 1 (u_32 = 2^-24).  It does on a well-conditioned local matrix and fails
+    on the paper's initialisation, whose K^s have kappa ~ 1e14: why every product of the
+    path keeps FP64 accuracy (digit-split on the BF16 tensor cores) instead."""
+    good = wl.build(2, 2, 40, 10, 10, 10, 10, theta="local_unit", theta_seed=1, source="sinsin",
+                    n_test_side=10)
+    paper = wl.build(2, 2, 200, 20, 20, 40, 40, theta="paper", theta_seed=2, source="sinsin",
+                     n_test_side=10)
+    k1, e1 = _fp32_qr_refinement(good)
+    k2, e2 = _fp32_qr_refinement(paper)
+    assert k1 * 2.0 ** -24 < 1 and e1 < 1e-12
+    assert k2 * 2.0 ** -24 > 1e6 and not (e2 < 1e-6)
