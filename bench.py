@@ -39,7 +39,8 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 SINGLE_CTA_CLASSES = ("potrf",)
 KERNEL_OF_CLASS = {
     "panel_qr": "k_panel_qr_cl (Householder panel of 32 columns, 4-CTA cluster per subdomain, FP64 pipe)",
-    "potrf": "k_potrf_diag (64x64 diagonal Cholesky + inverse, one CTA, FP64 pipe)",
+    "potrf": "k_potrf_diag (64x64 diagonal Cholesky, one CTA, FP64 pipe)",
+    "trsm_rows": "k_trsm_chol_rows (Cholesky panel solve by substitution in 4-column blocks, 16 rows per CTA, FP64 pipe)",
     "oz_qr_update": "k_ozaki_upd (persistent tensor-core FP64 product: A2 -= V W2 of every QR panel)",
     "oz_qr_w": "k_ozaki_fa (tensor-core FP64 product with fused digit split: W1^T = A2^T V of every QR panel)",
     "oz_syrk": "k_ozaki_upd (persistent tensor-core FP64 product: Schur Cholesky SYRK)",

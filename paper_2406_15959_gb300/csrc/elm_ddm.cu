@@ -515,11 +515,9 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const size_t c1 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 128) * 2);
   const size_t c2 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 32) * 2);
   const size_t ce = al((size_t)std::max(restmax, 1) * 4);
-  // digit planes and row exponents of the diagonal-block inverse (panel solve operand)
-  const size_t c3 = al(oz_split_elems(CHOL_NB, CHOL_NB, 32) * 2), ec3 = al((size_t)CHOL_NB * 4);
   if (h->emulated) {
     char* base = nullptr;
-    if (!dev_alloc(h, &base, per_sub * N + c1 + c2 + 2 * ce + c3 + ec3)) {
+    if (!dev_alloc(h, &base, per_sub * N + c1 + c2 + 2 * ce)) {
       free_all(h);
       delete h;
       return fail(nullptr, ELM_DDM_ERR_OOM, "device allocation failed (split workspace)");
@@ -878,15 +876,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       if (h->emulated) {
         int* xa = (int*)(chol_region + c1 + c2);
         int* xb = (int*)(chol_region + c1 + c2 + ce);
-        // panel solve L21 = A21 L11^{-T} as a digit-split product with the stored inverse:
-        // A21 is split before the product overwrites it in place
-        char* t3 = chol_region + c1 + c2 + 2 * ce;
-        int* x3 = (int*)(t3 + c3);
-        std::vector<SplitDesc> spt{{L21, 1, ng, rest, nb, xa, chol_region, 128},
-                                   {cinv, 1, CHOL_NB, nb, nb, x3, t3, 32}};
-        add_split_rec(h->trsm_recs, spt, "split_trsm");
-        add_oz_rec(h->trsm_recs, {{chol_region, xa, t3, x3, L21, 1, ng, rest, nb, nb, 0}}, 0, 1.0, 0.0,
-                   0, "oz_trsm_chol");
+        // the panel solve L21 = A21 L11^{-T} runs by substitution (launch_trsm_chol_rows)
         std::vector<SplitDesc> sp{{L21, 1, ng, rest, nb, xa, chol_region, 128},
                                   {L21, 1, ng, rest, nb, xb, chol_region + c1, 32}};
         add_split_rec(h->syrk_recs, sp, "split_syrk");
@@ -1010,18 +1000,30 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     h->has_sdinv = true;
     for (int k = 0, step = 0; k < h->ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, h->ng - k);
-      // nb^3/3 for the factor and as much again for its inverse
-      ELM_LAUNCH_F(h, launch_potrf_diag(h->S, h->ng, k, nb, h->cinv + (size_t)step * CHOL_NB * CHOL_NB,
-                                        h->status, h->st), "potrf", 2.0 * nb * nb * (double)nb / 3.0);
-      if (h->chol_rend[step] - k - nb > 0) {
+      // emulated path: the factor only (nb^3/3), the panel solve by substitution and the
+      // inverses for the solve phase afterwards; otherwise the factor and its inverse
+      // (as much again), the panel solve being a product with the inverse
+      const int rend = h->chol_rend[step];
+      if (h->emulated) {
+        ELM_LAUNCH_F(h, launch_potrf_diag(h->S, h->ng, k, nb, nullptr, h->status, h->st), "potrf",
+                     nb * nb * (double)nb / 3.0);
+        if (rend - k - nb > 0)
+          ELM_LAUNCH_F(h, launch_trsm_chol_rows(h->S, h->ng, k, nb, rend, h->st), "trsm_rows",
+                       (double)(rend - k - nb) * nb * nb);
+      } else {
+        ELM_LAUNCH_F(h, launch_potrf_diag(h->S, h->ng, k, nb, h->cinv + (size_t)step * CHOL_NB * CHOL_NB,
+                                          h->status, h->st), "potrf", 2.0 * nb * nb * (double)nb / 3.0);
+      }
+      if (rend - k - nb > 0) {
         rc = run_recs(h, h->trsm_recs, h->trsm_first[step],
-                      h->trsm_first[step + 1] - h->trsm_first[step], "oz_trsm_chol");
+                      h->trsm_first[step + 1] - h->trsm_first[step], "trsm_chol");
         if (rc) return rc;
         rc = run_recs(h, h->syrk_recs, h->syrk_first[step],
                       h->syrk_first[step + 1] - h->syrk_first[step], "gemm_syrk");
         if (rc) return rc;
       }
     }
+    if (h->emulated) ELM_LAUNCH(h, launch_tri_inv(h->S, h->ng, h->ng, h->cinv, h->st), "tri_inv");
   }
   h->state = 2;
   return ELM_DDM_OK;

@@ -9,10 +9,10 @@ namespace {
 
 constexpr int NB = CHOL_NB;
 
-// Unblocked Cholesky of the nb x nb diagonal block at (k, k), in shared memory, and the
-// inverse of that factor (written column-major to inv, ld NB) so that the panel solve
-// L21 = A21 L11^{-T} is a matrix product.  Both run in one loop over the pivots with one
-// barrier per column.  Step j works with the unscaled column j (a_ij, i > j, final at this
+// Unblocked Cholesky of the nb x nb diagonal block at (k, k), in shared memory, and, when
+// inv is not NULL, the inverse of that factor (written column-major to inv, ld NB) so that
+// the panel solve L21 = A21 L11^{-T} is a matrix product.  Both run in one loop over the
+// pivots with one barrier per column.  Step j works with the unscaled column j (a_ij, i > j, final at this
 // point) and the multipliers t_i = a_ij / d_j, d_j = a_jj:
 //   Cholesky:  a_ik -= t_i a_kj              for j < k <= i  (= l_ij l_kj)
 //   inverse:   y_ic -= t_i y_jc              for i > j, c <= j
@@ -27,7 +27,7 @@ constexpr int NB = CHOL_NB;
 //   warp 0:      updates column j+1 (the next pivot column), forms d_{j+1}, its
 //                reciprocal and the next multipliers t^(j+1) (double-buffered);
 //   warps 1..15: the rest of the trailing triangle (columns > j+1) and the inverse's
-//                rectangle, flattened into one index range so every warp-wide FMA has 32
+//                rectangle (when requested), flattened into one index range so every warp-wide FMA has 32
 //                active lanes.
 // One barrier per column; the reciprocal's latency hides behind the bulk update.
 constexpr int POTRF_THREADS = 512;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict
       }
     } else {
       // triangle of columns j+2.. (size m-1), then rectangle rows j+1.., columns 0..j
-      const int tri = m > 0 ? (m - 1) * m / 2 : 0, total = tri + m * (j + 1);
+      const int tri = m > 0 ? (m - 1) * m / 2 : 0, total = tri + (inv ? m * (j + 1) : 0);
       for (int e = tid - 32; e < total; e += BULK) {
         if (e < tri) {
           int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
@@ -108,27 +108,90 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict
   }
 }
 
-// L21 = A21 L11^{-T}: one thread per row below the diagonal block.
-__global__ void __launch_bounds__(64) k_trsm_chol(double* __restrict__ S, int ld, int n, int k,
-                                                  int nb) {
-  extern __shared__ double smem_trsm[];
-  double (*L)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(smem_trsm);
-  double (*X)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(smem_trsm + NB * (NB + 1));
-  const int tid = threadIdx.x;
-  for (int e = tid; e < nb * nb; e += 64) {
-    const int i = e % nb, j = e / nb;
-    L[i][j] = (i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : 0.0;
+// Inverses of all diagonal blocks of the finished factor, one block per CTA: column c of
+// X = L_kk^{-1} by forward substitution, x_rc = (delta_rc - sum_{c<=l<r} l_rl x_lc) / l_rr,
+// one thread per column.  Used by the triangular solves of the solve phase; runs once
+// after the factorisation, off its critical path.
+__global__ void __launch_bounds__(NB) k_tri_inv(const double* __restrict__ S, int ld, int n,
+                                               double* __restrict__ inv) {
+  extern __shared__ double tinv_smem[];
+  double (*L)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(tinv_smem);
+  double (*X)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(tinv_smem + NB * (NB + 1));
+  __shared__ double rd[NB];
+  const int t = threadIdx.x, k = blockIdx.x * NB, nb = min(NB, n - k);
+  for (int e = t; e < NB * NB; e += NB) {
+    const int i = e % NB, j = e / NB;
+    L[i][j] = (i < nb && j < nb && i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : (i == j ? 1.0 : 0.0);
   }
-  const int i = k + nb + blockIdx.x * 64 + tid;
-  for (int j = 0; j < nb; ++j) X[tid][j] = (i < n) ? S[i + (size_t)(k + j) * ld] : 0.0;
   __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    double x = X[tid][j];
-    for (int l = 0; l < j; ++l) x = fma(-X[tid][l], L[j][l], x);
-    X[tid][j] = x / L[j][j];
+  rd[t] = 1.0 / L[t][t];
+  __syncthreads();
+  for (int r = 0; r < NB; ++r) {
+    double v = r == t ? 1.0 : 0.0;
+    for (int l = t; l < r; ++l) v = fma(-L[r][l], X[l][t], v);
+    X[r][t] = r >= t ? v * rd[r] : 0.0;
   }
-  if (i < n)
-    for (int j = 0; j < nb; ++j) S[i + (size_t)(k + j) * ld] = X[tid][j];
+  __syncthreads();
+  double* out = inv + (size_t)blockIdx.x * NB * NB;
+  for (int e = t; e < NB * NB; e += NB) {
+    const int i = e % NB, j = e / NB;
+    out[i + j * NB] = (i < nb && j < nb) ? X[i][j] : 0.0;
+  }
+}
+
+// L21 = A21 L11^{-T} by substitution, for the rows k+nb .. row_end-1 of the block column
+// (the envelope): each row solves x L11^T = a.  Columns go in blocks of TRC_BW: the
+// block's small triangle by plain substitution (one thread per row), then a rank-TRC_BW
+// update of the row's remaining columns spread over all threads, so the FP64 pipe sees
+// independent FMAs instead of one long dependent chain.  Same operations as the
+// unblocked solve up to summation order, hence its backward stability.  TRC_ROWS rows per
+// block keep about one block per SM on the envelopes of interest.
+constexpr int TRC_ROWS = 16, TRC_THREADS = 128, TRC_BW = 4;
+__global__ void __launch_bounds__(TRC_THREADS) k_trsm_chol_rows(double* __restrict__ S, int ld, int k, int nb,
+                                                                int row_end) {
+  __shared__ double L[NB][NB + 1];
+  __shared__ double X[TRC_ROWS][NB + 1];
+  __shared__ double rd[NB];
+  const int t = threadIdx.x;
+  const int r0 = k + nb + blockIdx.x * TRC_ROWS;
+  for (int e = t; e < NB * NB; e += TRC_THREADS) {
+    const int i = e % NB, j = e / NB;
+    L[i][j] = (i < nb && j < nb && i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : (i == j ? 1.0 : 0.0);
+  }
+  for (int e = t; e < TRC_ROWS * NB; e += TRC_THREADS) {
+    const int r = e % TRC_ROWS, j = e / TRC_ROWS;
+    X[r][j] = (r0 + r < row_end && j < nb) ? S[(r0 + r) + (size_t)(k + j) * ld] : 0.0;
+  }
+  __syncthreads();
+  if (t < NB) rd[t] = 1.0 / L[t][t];
+  __syncthreads();
+  for (int b = 0; b < nb; b += TRC_BW) {
+    if (t < TRC_ROWS) {
+      double x[TRC_BW];
+#pragma unroll
+      for (int q = 0; q < TRC_BW; ++q) {
+        double v = X[t][b + q];
+#pragma unroll
+        for (int l = 0; l < q; ++l) v = fma(-x[l], L[b + q][b + l], v);
+        x[q] = v * rd[b + q];
+        X[t][b + q] = x[q];
+      }
+    }
+    __syncthreads();
+    const int c0 = b + TRC_BW, pairs = TRC_ROWS * (nb - c0);
+    for (int e = t; e < pairs; e += TRC_THREADS) {
+      const int r = e % TRC_ROWS, c = c0 + e / TRC_ROWS;
+      double v = X[r][c];
+#pragma unroll
+      for (int l = 0; l < TRC_BW; ++l) v = fma(-X[r][b + l], L[c][b + l], v);
+      X[r][c] = v;
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < TRC_ROWS * NB; e += TRC_THREADS) {
+    const int r = e % TRC_ROWS, j = e / TRC_ROWS;
+    if (r0 + r < row_end && j < nb) S[(r0 + r) + (size_t)(k + j) * ld] = X[r][j];
+  }
 }
 
 // Forward substitution step for block k: y_k = L_kk^{-1} r_k with the stored inverse of
@@ -245,17 +308,23 @@ cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, double* inv, uns
   return cudaGetLastError();
 }
 
-cudaError_t launch_trsm_chol(double* S, int ld, int n, int k, int nb, cudaStream_t st) {
-  const int rows = n - k - nb;
-  if (rows <= 0) return cudaSuccess;
+cudaError_t launch_tri_inv(const double* S, int ld, int n, double* inv, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
   const int smem = 2 * NB * (NB + 1) * (int)sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_trsm_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tri_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr = true;
   }
-  k_trsm_chol<<<(rows + 63) / 64, 64, smem, st>>>(S, ld, n, k, nb); count_launch();
+  k_tri_inv<<<(n + NB - 1) / NB, NB, smem, st>>>(S, ld, n, inv); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_chol_rows(double* S, int ld, int k, int nb, int row_end, cudaStream_t st) {
+  const int rows = row_end - k - nb;
+  if (rows <= 0) return cudaSuccess;
+  k_trsm_chol_rows<<<(rows + TRC_ROWS - 1) / TRC_ROWS, TRC_THREADS, 0, st>>>(S, ld, k, nb, row_end); count_launch();
   return cudaGetLastError();
 }
 

@@ -264,6 +264,36 @@ __device__ __forceinline__ double i64_to_double_pow2(long long x, int k, bool ne
   return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | mant));
 }
 
+// One output element of a single-chunk product (K <= 128) from its seven group sums:
+// V = sum_g a_g 2^(8 (6 - g)), integers with |a_g| < 2^24, times 2^k, negated when neg,
+// rounded once to the nearest double (ties to even) without an FP64 addition.
+// V = P 2^32 + Q with |P| < 2^40 and |Q| < 2^48 spans up to 73 bits, so it is shifted
+// right by t in {0, 7, 13} (chosen from |P|) into one 63-bit integer X: for t = 0 exactly;
+// otherwise X keeps at least 55 significant bits and the dropped bits are folded in by
+// rounding to odd (a sticky least significant bit).  Rounding X to 53 bits then gives the
+// correctly rounded V (round-to-odd at two extra bits, then round-to-nearest, is a single
+// correct rounding: Boldo and Melquiond, IEEE Trans. Computers 57(4), 2008), the same
+// result as two exact conversions of P 2^32 and Q and one FP64 addition.  The FP64 pipe
+// (2 operations per clock per SM) is the scarce unit of this epilogue, and the remaining
+// FP64 addition is the one with C.  Outside the normal range the slow path rounds twice.
+__device__ __forceinline__ double groups_to_double(const int (&a)[OZ_G], int k, bool neg) {
+  const long long P = (long long)a[0] * 65536 + (long long)a[1] * 256 + a[2];
+  const long long Q = (long long)a[3] * 16777216 + (long long)a[4] * 65536 + (long long)a[5] * 256 + a[6];
+  const unsigned long long ap = P < 0 ? 0ull - (unsigned long long)P : (unsigned long long)P;
+  const int t = ap < (1ull << 30) ? 0 : (ap < (1ull << 36) ? 7 : 13);
+  long long X = (long long)((unsigned long long)P << (32 - t)) + (Q >> t);
+  if (Q & ((1ll << t) - 1)) X |= 1;
+  if (X == 0) return 0.0;
+  // X -> double rounds to nearest (the second rounding); 2^(k + t) and the sign go into
+  // the bit pattern
+  long long b = __double_as_longlong(__ll2double_rn(X));
+  const int e = (int)((b >> 52) & 0x7FF) + k + t;
+  if (e <= 0 || e >= 2047) return i64_to_double_pow2_slow(X, k + t, neg);
+  b += (long long)(k + t) * (1ll << 52);
+  if (neg) b ^= (long long)(1ull << 63);
+  return __longlong_as_double(b);
+}
+
 template <int NT>
 struct OzSmem {
   static constexpr int A_BYTES = OZ_S * OZ_M * OZ_KC * 2;  // one stage of A digit tiles
@@ -930,14 +960,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
               int a[OZ_G];
 #pragma unroll
               for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][jj]));
-              const long long H = ((long long)a[0] << 24) + ((long long)a[1] << 16) + ((long long)a[2] << 8);
-              const long long Lw =
-                  ((long long)a[3] << 24) + ((long long)a[4] << 16) + ((long long)a[5] << 8) + a[6];
-              double pv = 0.0;
-              if (ei != 0 && fj[j] != 0) {
-                const int k = ei + fj[j] - 2044 - 62;
-                pv = i64_to_double_pow2(H, k + 24, neg_alpha) + i64_to_double_pow2(Lw, k, neg_alpha);
-              }
+              const double pv =
+                  (ei != 0 && fj[j] != 0) ? groups_to_double(a, ei + fj[j] - 2044 - 62, neg_alpha) : 0.0;
               const double cv = EMODE != 0 ? cbuf[(buf * UPD_COLS + j) * ET + wt] : 0.0;
               double out;
               if (EMODE == 0) out = pv;
