@@ -66,6 +66,11 @@ extern "C" {
                                      after D_s and M_s, the Schur matrix is neither formed
                                      nor factored (no n_gamma^2 workspace); solve with
                                      elm_ddm_solve_cg (elm_ddm_solve returns ERR_STATE) */
+#define ELM_DDM_FLAG_DIRECT_ASSEMBLY 4  /* evaluate tanh for every entry of K^s and A^s.
+                                     Default: where the collocation points of the
+                                     subdomains share few x and y coordinates (the paper's
+                                     grids), exp(2 z) is factored into per-neuron tables over
+                                     those coordinates (same values to a few ulp) */
 
 /* Differential operators. */
 #define ELM_DDM_OP_POISSON 0  /* L = -Laplacian (Eq. (4.4)) */
@@ -226,7 +231,8 @@ int elm_ddm_export(elm_ddm_handle* h, int what, int s, double* dst, int ld_dst);
  * Queries.  key: 0 = n_gamma, 1 = device workspace bytes, 2 = number of launch calls
  * (one per kernel class invocation, some launch several kernels) enqueued since setup,
  * 3 = number of Schur-matrix edges (interface blocks), 4 = m_max, 5 = n_neurons,
- * 6 = n_sub, 7 = CUDA kernels launched by the library in this process (all handles).
+ * 6 = n_sub, 7 = CUDA kernels launched by the library in this process (all handles),
+ * 8 = 1 if elm_ddm_assemble uses the factored activation tables, else 0.
  */
 int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value);
 

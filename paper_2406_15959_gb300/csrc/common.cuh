@@ -96,11 +96,27 @@ cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_
                         double alpha, double beta, int flags, cudaStream_t st);
 cudaError_t launch_add_blocks(const AddDesc* d, int count, int max_elems, cudaStream_t st);
 
+// Per-subdomain coordinate tables of the factored activation (k_assemble.cu): distinct
+// x (xs [N][nxmax]) and y (ys [N][nymax]) values, their counts (nxy [N][2]), a centre
+// (ctr [N][2]), each row's coordinate indices (rix [N][m_max], ix | iy << 16), and the
+// factor tables Tx [N][n][nxmax], Ty [N][n][nymax] filled by the assembly launch.
+struct AsmTables {
+  const double* xs = nullptr;
+  const double* ys = nullptr;
+  const int* nxy = nullptr;
+  const double* ctr = nullptr;
+  const int* rix = nullptr;
+  double* Tx = nullptr;
+  double* Ty = nullptr;
+  int nxmax = 0, nymax = 0;
+};
 // coef: NULL for -Laplacian, else [N][m_max][3] (rho, grad rho) for -div(rho grad).
+// tb: NULL (tanh per entry) or the coordinate tables (factored activation).
 cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, double* Amat,
                             long long astride, int mgld, const double* xy, const double* nrm,
                             int m_max, const int* cnt, const double* W, const double* b, int N,
-                            int n, const double* coef, unsigned* status, cudaStream_t st);
+                            int n, const double* coef, const AsmTables* tb, unsigned* status,
+                            cudaStream_t st);
 cudaError_t launch_eval(const double* W, const double* b, int N, int n, int npts,
                         const double* xy, const int* owner, const double* c, double* u,
                         double* grad, cudaStream_t st);

@@ -117,6 +117,11 @@ struct elm_ddm_handle {
   double *W1 = nullptr, *W2 = nullptr, *D = nullptr, *M = nullptr, *S = nullptr;
   double *Mdiag = nullptr, *thW = nullptr, *thb = nullptr, *xy = nullptr, *nrm = nullptr;
   double* cinv = nullptr;             // inverses of the Cholesky diagonal blocks, one per step
+  // factored activation (k_assemble.cu): distinct coordinates per subdomain and tables
+  AsmTables tabs;
+  bool use_tabs = false;
+  double *tab_xs = nullptr, *tab_ys = nullptr, *tab_ctr = nullptr, *tab_Tx = nullptr, *tab_Ty = nullptr;
+  int *tab_nxy = nullptr, *tab_rix = nullptr;
   std::vector<LaunchRec> trsm_recs;   // per Cholesky step: L21 = A21 L11^{-T} as a product
   std::vector<LaunchRec> ty_recs;     // blocked Y = A R^{-1} (tensor-core path)
   std::vector<int> trsm_first;
@@ -298,7 +303,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const int max_rhs = desc->max_rhs == 0 ? 1 : desc->max_rhs;
   if (max_rhs < 1 || max_rhs > 64) return fail(nullptr, ELM_DDM_ERR_ARG, "max_rhs must be in 1..64");
   if (n > TRSV_MAX_N) return fail(nullptr, ELM_DDM_ERR_ARG, "n_neurons > 8192 is not supported");
-  if (desc->flags & ~(ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG))
+  if (desc->flags & ~(ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG | ELM_DDM_FLAG_DIRECT_ASSEMBLY))
     return fail(nullptr, ELM_DDM_ERR_ARG, "unknown flags");
   if ((long long)N * m_max > (1ll << 31)) return fail(nullptr, ELM_DDM_ERR_ARG, "geometry too large");
 
@@ -456,6 +461,54 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->wstride = (long long)QR_NB * h->ncap;
   for (const Edge& e : h->edges) h->mdiag_elems += (size_t)e.len * e.len;
 
+  // ---- distinct coordinates of each subdomain's rows (factored activation) ----
+  std::vector<double> txs, tys, tctr(2 * (size_t)N);
+  std::vector<int> tnxy(2 * (size_t)N), trix;
+  {
+    std::vector<std::vector<double>> ux(N), uy(N);
+    size_t total = 0, rows = 0;
+    int nxmax = 0, nymax = 0;
+    for (int s = 0; s < N; ++s) {
+      for (int r = 0; r < h->ms_h[s]; ++r) {
+        ux[s].push_back(xy[((size_t)s * m_max + r) * 2]);
+        uy[s].push_back(xy[((size_t)s * m_max + r) * 2 + 1]);
+      }
+      for (auto* u : {&ux[s], &uy[s]}) {
+        std::sort(u->begin(), u->end());
+        u->erase(std::unique(u->begin(), u->end()), u->end());
+      }
+      nxmax = std::max(nxmax, (int)ux[s].size());
+      nymax = std::max(nymax, (int)uy[s].size());
+      total += ux[s].size() + uy[s].size();
+      rows += h->ms_h[s];
+    }
+    // a table entry costs one exp, about what an entry's tanh costs, so the tables pay
+    // when they hold fewer activations than K^s (the grids: about a tenth)
+    h->use_tabs = !(desc->flags & ELM_DDM_FLAG_DIRECT_ASSEMBLY) && rows > 0 && total <= rows &&
+                  nxmax < 65536 && nymax < 65536;
+    if (h->use_tabs) {
+      h->tabs.nxmax = nxmax;
+      h->tabs.nymax = nymax;
+      txs.assign((size_t)N * nxmax, 0.0);
+      tys.assign((size_t)N * nymax, 0.0);
+      trix.assign((size_t)N * m_max, 0);
+      for (int s = 0; s < N; ++s) {
+        tnxy[2 * s] = (int)ux[s].size();
+        tnxy[2 * s + 1] = (int)uy[s].size();
+        std::copy(ux[s].begin(), ux[s].end(), txs.begin() + (size_t)s * nxmax);
+        std::copy(uy[s].begin(), uy[s].end(), tys.begin() + (size_t)s * nymax);
+        tctr[2 * s] = ux[s].empty() ? 0.0 : 0.5 * (ux[s].front() + ux[s].back());
+        tctr[2 * s + 1] = uy[s].empty() ? 0.0 : 0.5 * (uy[s].front() + uy[s].back());
+        for (int r = 0; r < h->ms_h[s]; ++r) {
+          const double x = xy[((size_t)s * m_max + r) * 2], y = xy[((size_t)s * m_max + r) * 2 + 1];
+          const int ix = (int)(std::lower_bound(ux[s].begin(), ux[s].end(), x) - ux[s].begin());
+          const int iy = (int)(std::lower_bound(uy[s].begin(), uy[s].end(), y) - uy[s].begin());
+          trix[(size_t)s * m_max + r] = ix | (iy << 16);
+        }
+      }
+    }
+  }
+
   // ---- allocation ----
   bool ok = dev_alloc(h, &h->K, (size_t)N * h->kstride) &&
             dev_alloc(h, &h->Am, (size_t)N * h->astride) &&
@@ -486,6 +539,15 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->ifc_dof, (size_t)N * h->mgld) && dev_alloc(h, &h->perm, (size_t)ng) &&
             dev_alloc(h, &h->cinv, (size_t)((ng + CHOL_NB - 1) / CHOL_NB + 1) * CHOL_NB * CHOL_NB) &&
             dev_alloc(h, &h->status, 1);
+  if (ok && h->use_tabs) {
+    const AsmTables& t = h->tabs;
+    ok = dev_alloc(h, &h->tab_xs, (size_t)N * t.nxmax) && dev_alloc(h, &h->tab_ys, (size_t)N * t.nymax) &&
+         dev_alloc(h, &h->tab_ctr, (size_t)N * 2) && dev_alloc(h, &h->tab_nxy, (size_t)N * 2) &&
+         dev_alloc(h, &h->tab_rix, (size_t)N * m_max) &&
+         dev_alloc(h, &h->tab_Tx, (size_t)N * n * t.nxmax) && dev_alloc(h, &h->tab_Ty, (size_t)N * n * t.nymax);
+    h->tabs.xs = h->tab_xs; h->tabs.ys = h->tab_ys; h->tabs.ctr = h->tab_ctr; h->tabs.nxy = h->tab_nxy;
+    h->tabs.rix = h->tab_rix; h->tabs.Tx = h->tab_Tx; h->tabs.Ty = h->tab_Ty;
+  }
   if (!ok) {
     free_all(h);
     delete h;
@@ -921,6 +983,13 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   cp(h->dofmap, dofmap.data(), dofmap.size() * sizeof(int));
   cp(h->ifc_dof, ifc.data(), ifc.size() * sizeof(int));
   cp(h->perm, h->perm_h.data(), h->perm_h.size() * sizeof(int));
+  if (h->use_tabs) {
+    cp(h->tab_xs, txs.data(), txs.size() * sizeof(double));
+    cp(h->tab_ys, tys.data(), tys.size() * sizeof(double));
+    cp(h->tab_ctr, tctr.data(), tctr.size() * sizeof(double));
+    cp(h->tab_nxy, tnxy.data(), tnxy.size() * sizeof(int));
+    cp(h->tab_rix, trix.data(), trix.size() * sizeof(int));
+  }
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
     std::string msg = std::string("setup copy: ") + cudaGetErrorString(e);
@@ -955,7 +1024,8 @@ int elm_ddm_assemble(elm_ddm_handle* h, const double* W, const double* b) {
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble: copy theta");
   ELM_LAUNCH(h, launch_assemble(h->K, h->kstride, h->ld, h->ncap, h->Am, h->astride, h->mgld, h->xy,
                                 h->nrm, h->m_max, h->cnt, h->thW, h->thb, h->N, h->n,
-                                h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr, h->status, h->st),
+                                h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr,
+                                h->use_tabs ? &h->tabs : nullptr, h->status, h->st),
              "assemble");
   h->state = 1;
   return ELM_DDM_OK;
@@ -1281,6 +1351,7 @@ int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value) {
     case 3: *value = (double)h->edges.size(); break;
     case 4: *value = h->m_max; break;
     case 7: *value = (double)elmddm::g_kernel_launches.load(); break;
+    case 8: *value = h->use_tabs ? 1.0 : 0.0; break;
     case 5: *value = h->n; break;
     case 6: *value = h->N; break;
     default: return ELM_DDM_ERR_ARG;

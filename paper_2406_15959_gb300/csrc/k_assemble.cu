@@ -10,6 +10,23 @@
 // The kernel also writes the m_Gamma "interface identity" columns J = E^T next to
 // K^s (row mi+mb+k of column n+k is 1), so that the Householder QR applies Q^T to
 // them and leaves Q_G^T in rows 0..n-1 of those columns.
+//
+// tanh costs some 30 FP64 operations, and the FP64 pipe (2 per clock per SM) bounds
+// this step.  The paper's collocation points are tensor grids and edge lines, so a
+// subdomain has few distinct x and y coordinates, and
+//   E = exp(2 z) = exp(2 (w_x (x - c_x) + z_c)) * exp(2 w_y (y - c_y)),
+//   z_c = w . c + b (c the centre of the subdomain's coordinates),
+// factors into per-neuron tables over those coordinates (k_exp_tables).  Then with
+// r = 1 / (E + 1)
+//   t = (E - 1) r,   1 - t^2 = 4 E r^2,
+// one product and one reciprocal per entry instead of a tanh.  Accuracy: E carries the
+// relative error of the two factors (a few ulp plus the rounding of their centred
+// arguments), E - 1 is exact near E = 1, so t has an absolute error of a few ulp times
+// the argument's magnitude -- no more than tanh(w . x + b) itself, whose argument rounds
+// at the scale of |w| |x| with x uncentred.  The y factor is kept within exp(+-600)
+// (larger arguments store NaN), so an overflowing product means z > 50 and saturates
+// (t = 1, 1 - t^2 = 0), an underflowing one means t = -1, and a product that is not a
+// number (such a y factor, or non-finite parameters) falls back to tanh(z).
 #include "common.cuh"
 
 namespace elmddm {
@@ -19,6 +36,36 @@ namespace {
 constexpr int AR = 64;  // rows per block
 constexpr int AC = 32;  // columns per block
 
+// Factor tables of subdomain s = blockIdx.y: Tx[s][j][ix] = exp(2 (w_x (x_ix - c_x) + z_c))
+// and Ty[s][j][iy] = exp(2 w_y (y_iy - c_y)), over its distinct coordinates.
+__global__ void __launch_bounds__(256) k_exp_tables(const double* __restrict__ W,
+                                                    const double* __restrict__ bias, int n,
+                                                    const AsmTables tb) {
+  const int s = blockIdx.y;
+  const int per = tb.nxmax + tb.nymax;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * per) return;
+  const int j = (int)(idx / per), i = (int)(idx % per);
+  const double wx = W[((size_t)s * n + j) * 2], wy = W[((size_t)s * n + j) * 2 + 1];
+  const double cx = tb.ctr[2 * s], cy = tb.ctr[2 * s + 1];
+  if (i < tb.nxmax) {
+    if (i >= tb.nxy[2 * s]) return;
+    const double zc = fma(wx, cx, fma(wy, cy, bias[(size_t)s * n + j]));
+    const double x = tb.xs[(size_t)s * tb.nxmax + i];
+    tb.Tx[((size_t)s * n + j) * tb.nxmax + i] = exp(2.0 * fma(wx, x - cx, zc));
+  } else {
+    const int iy = i - tb.nxmax;
+    if (iy >= tb.nxy[2 * s + 1]) return;
+    const double y = tb.ys[(size_t)s * tb.nymax + iy];
+    // beyond |arg| = 600 the product could pair an overflow with a compensating
+    // underflow: a NaN entry sends that neuron's entries to tanh(z)
+    const double arg = 2.0 * wy * (y - cy);
+    tb.Ty[((size_t)s * n + j) * tb.nymax + iy] =
+        fabs(arg) <= 600.0 ? exp(arg) : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+template <bool TAB>
 __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long long kstride, int ld,
                                                   int ncap, double* __restrict__ Amat,
                                                   long long astride, int mgld,
@@ -28,14 +75,14 @@ __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long l
                                                   const double* __restrict__ W,
                                                   const double* __restrict__ bias, int n,
                                                   const double* __restrict__ coef,
-                                                  unsigned* status) {
+                                                  const AsmTables tb, unsigned* status) {
   const int s = blockIdx.z;
   const int r = blockIdx.x * AR + threadIdx.x;
   const int c0 = blockIdx.y * AC;
   const int mi = cnt[3 * s], mb = cnt[3 * s + 1], mg = cnt[3 * s + 2];
   const int row0g = mi + mb, ms = row0g + mg;
 
-  __shared__ double sw[AC][3];
+  __shared__ double sw[AC][4];  // w_x, w_y, b, 2 |w|^2
   const int tl = threadIdx.y * AR + threadIdx.x;
   if (tl < AC) {
     const int c = c0 + tl;
@@ -45,7 +92,7 @@ __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long l
       wy = W[((size_t)s * n + c) * 2 + 1];
       bb = bias[(size_t)s * n + c];
     }
-    sw[tl][0] = wx; sw[tl][1] = wy; sw[tl][2] = bb;
+    sw[tl][0] = wx; sw[tl][1] = wy; sw[tl][2] = bb; sw[tl][3] = 2.0 * fma(wx, wx, wy * wy);
   }
   __syncthreads();
   if (r >= ld) return;
@@ -65,6 +112,12 @@ __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long l
       ny = nrm[((size_t)s * m_max + r) * 2 + 1];
     }
   }
+  int ix = 0, iy = 0;
+  if (TAB && r < ms) {
+    const int pk = tb.rix[(size_t)s * m_max + r];
+    ix = pk & 0xFFFF;
+    iy = pk >> 16;
+  }
   double* Ks = K + (size_t)s * kstride;
   double* As = Amat + (size_t)s * astride;
   bool bad = false;
@@ -77,12 +130,31 @@ __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long l
     if (c < n) {
       if (r < ms) {
         const double wx = sw[cl][0], wy = sw[cl][1];
-        const double z = fma(wx, px, fma(wy, py, sw[cl][2]));
-        const double t = tanh(z);
-        const double d1 = 1.0 - t * t;
-        bad |= !isfinite(z);
+        double t, d1;
+        bool direct = !TAB;
+        if (TAB) {
+          const double a = tb.Tx[((size_t)s * n + c) * tb.nxmax + ix];
+          const double b = tb.Ty[((size_t)s * n + c) * tb.nymax + iy];
+          const double E = a * b;
+          if (E < 1e300) {
+            const double rr = __drcp_rn(E + 1.0);
+            t = (E - 1.0) * rr;
+            d1 = 4.0 * rr * (E * rr);
+          } else if (E >= 1e300) {
+            t = 1.0;
+            d1 = 0.0;
+          } else {
+            direct = true;
+          }
+        }
+        if (direct) {
+          const double z = fma(wx, px, fma(wy, py, sw[cl][2]));
+          t = tanh(z);
+          d1 = 1.0 - t * t;
+          bad |= !isfinite(z);
+        }
         if (r < mi) {
-          v = 2.0 * fma(wx, wx, wy * wy) * t * d1;
+          v = sw[cl][3] * t * d1;
           if (coef) v = fma(rho, v, -fma(rx, wx, ry * wy) * d1);
         } else {
           v = t;
@@ -143,10 +215,21 @@ __global__ void __launch_bounds__(256) k_eval(const double* __restrict__ W,
 cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, double* Amat,
                             long long astride, int mgld, const double* xy, const double* nrm,
                             int m_max, const int* cnt, const double* W, const double* b, int N,
-                            int n, const double* coef, unsigned* status, cudaStream_t st) {
+                            int n, const double* coef, const AsmTables* tb, unsigned* status,
+                            cudaStream_t st) {
   dim3 grid((ld + AR - 1) / AR, (ncap + AC - 1) / AC, N);
-  k_assemble<<<grid, dim3(AR, 4), 0, st>>>(K, kstride, ld, ncap, Amat, astride, mgld, xy, nrm,
-                                           m_max, cnt, W, b, n, coef, status); count_launch();
+  if (tb && tb->rix) {
+    const long long per = (long long)n * (tb->nxmax + tb->nymax);
+    if (per > 0) {
+      k_exp_tables<<<dim3((unsigned)((per + 255) / 256), N), 256, 0, st>>>(W, b, n, *tb); count_launch();
+    }
+    k_assemble<true><<<grid, dim3(AR, 4), 0, st>>>(K, kstride, ld, ncap, Amat, astride, mgld, xy, nrm,
+                                                   m_max, cnt, W, b, n, coef, *tb, status); count_launch();
+  } else {
+    k_assemble<false><<<grid, dim3(AR, 4), 0, st>>>(K, kstride, ld, ncap, Amat, astride, mgld, xy, nrm,
+                                                    m_max, cnt, W, b, n, coef, AsmTables{}, status);
+    count_launch();
+  }
   return cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ class Desc(ctypes.Structure):
 
 FLAG_FP64_SIMT = 1
 FLAG_SCHUR_CG = 2
+FLAG_DIRECT_ASSEMBLY = 4
 OP_POISSON, OP_VARCOEF = 0, 1
 
 
@@ -120,7 +121,7 @@ class Solver:
     """One decomposition on one GPU: setup -> assemble(theta) -> schur() -> solve(rhs)."""
 
     def __init__(self, geom, n_neurons: int, max_rhs: int = 1, stream=None, fp64_simt: bool = False,
-                 schur_cg: bool = False, op: int = OP_POISSON):
+                 schur_cg: bool = False, op: int = OP_POISSON, direct_assembly: bool = False):
         import torch
         self.lib = load()
         ga = geom if isinstance(geom, GeometryArrays) else GeometryArrays.from_geometry(geom)
@@ -128,7 +129,8 @@ class Solver:
         self.N, self.n, self.m_max, self.n_gamma = N, int(n_neurons), m_max, ga.n_gamma
         self.max_rhs = max_rhs
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        flags = (FLAG_FP64_SIMT if fp64_simt else 0) | (FLAG_SCHUR_CG if schur_cg else 0)
+        flags = ((FLAG_FP64_SIMT if fp64_simt else 0) | (FLAG_SCHUR_CG if schur_cg else 0) |
+                 (FLAG_DIRECT_ASSEMBLY if direct_assembly else 0))
         desc = Desc(N, self.n, m_max, ga.n_gamma, op, max_rhs, flags)
         h = ctypes.c_void_p()
         self._keep = ga
