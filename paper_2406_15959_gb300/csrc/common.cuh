@@ -149,9 +149,8 @@ cudaError_t launch_backsolve(const double* X, const double* K, long long kstride
                              const int* mg, const int* ifc_dof, int mgld, const double* u,
                              int n_gamma, int N, int n, int nrhs, double* c, cudaStream_t st);
 
-// inv (nullable): receives the inverse of the nb x nb factor, column-major, ld CHOL_NB.
-cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, double* inv, unsigned* status,
-                              cudaStream_t st);
+// Cholesky factor of the nb x nb diagonal block at (k, k) of S, in place (lower).
+cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, unsigned* status, cudaStream_t st);
 // Inverses of every CHOL_NB diagonal block of the factor L (in S), column-major, ld CHOL_NB.
 cudaError_t launch_tri_inv(const double* S, int ld, int n, double* inv, cudaStream_t st);
 // L21 = A21 L11^{-T} by substitution for rows k+nb .. row_end-1 (16 rows per block).

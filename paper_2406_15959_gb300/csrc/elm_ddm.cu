@@ -122,9 +122,7 @@ struct elm_ddm_handle {
   bool use_tabs = false;
   double *tab_xs = nullptr, *tab_ys = nullptr, *tab_ctr = nullptr, *tab_Tx = nullptr, *tab_Ty = nullptr;
   int *tab_nxy = nullptr, *tab_rix = nullptr;
-  std::vector<LaunchRec> trsm_recs;   // per Cholesky step: L21 = A21 L11^{-T} as a product
   std::vector<LaunchRec> ty_recs;     // blocked Y = A R^{-1} (tensor-core path)
-  std::vector<int> trsm_first;
   double *X = nullptr, *gq = nullptr, *hq = nullptr, *zv = nullptr;
   double *rv = nullptr, *hv = nullptr, *yv = nullptr, *uv = nullptr;
   int *cnt = nullptr, *ms = nullptr, *mg = nullptr, *dofmap = nullptr, *ifc_dof = nullptr;
@@ -930,10 +928,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     for (int k = 0, step = 0; k < ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, ng - k), rest = h->chol_rend[step] - k - nb;
       h->syrk_first.push_back((int)h->syrk_recs.size());
-      h->trsm_first.push_back((int)h->trsm_recs.size());
       if (rest <= 0) continue;
       double* L21 = h->S + (k + nb) + (size_t)k * ng;
-      const double* cinv = h->cinv + (size_t)step * CHOL_NB * CHOL_NB;
       double* S22 = h->S + (k + nb) + (size_t)(k + nb) * ng;
       if (h->emulated) {
         int* xa = (int*)(chol_region + c1 + c2);
@@ -946,17 +942,11 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
                    {{chol_region, xa, chol_region + c1, xb, S22, 1, ng, rest, rest, nb, 0}}, 0, -1.0,
                    1.0, GEMM_LOWER, "oz_syrk");
       } else {
-        // panel solve as an in-place product: every 64-wide tile reads all of its rows of
-        // A21 before writing them, and the tiles never share rows
-        add_gemm_rec(h->trsm_recs, {{L21, cinv, L21, rest, nb, nb, ng, CHOL_NB, ng}}, false, true, 1.0,
-                     0.0, 0);
-        h->trsm_recs.back().name = "trsm_chol";
         add_gemm_rec(h->syrk_recs, {{L21, L21, S22, rest, rest, nb, ng, ng, ng}}, false, true, -1.0,
                      1.0, GEMM_LOWER);
       }
     }
     h->syrk_first.push_back((int)h->syrk_recs.size());
-    h->trsm_first.push_back((int)h->trsm_recs.size());
   }
   ok = dev_alloc(h, &h->gd, gds.size()) && dev_alloc(h, &h->ad, ads.size()) &&
        dev_alloc(h, &h->sd, sds.size()) && dev_alloc(h, &h->od, ods.size()) &&
@@ -1070,30 +1060,21 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     h->has_sdinv = true;
     for (int k = 0, step = 0; k < h->ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, h->ng - k);
-      // emulated path: the factor only (nb^3/3), the panel solve by substitution and the
-      // inverses for the solve phase afterwards; otherwise the factor and its inverse
-      // (as much again), the panel solve being a product with the inverse
+      // the factor (nb^3/3), then the panel solve L21 = A21 L11^{-T} by substitution
       const int rend = h->chol_rend[step];
-      if (h->emulated) {
-        ELM_LAUNCH_F(h, launch_potrf_diag(h->S, h->ng, k, nb, nullptr, h->status, h->st), "potrf",
-                     nb * nb * (double)nb / 3.0);
-        if (rend - k - nb > 0)
-          ELM_LAUNCH_F(h, launch_trsm_chol_rows(h->S, h->ng, k, nb, rend, h->st), "trsm_rows",
-                       (double)(rend - k - nb) * nb * nb);
-      } else {
-        ELM_LAUNCH_F(h, launch_potrf_diag(h->S, h->ng, k, nb, h->cinv + (size_t)step * CHOL_NB * CHOL_NB,
-                                          h->status, h->st), "potrf", 2.0 * nb * nb * (double)nb / 3.0);
-      }
+      ELM_LAUNCH_F(h, launch_potrf_diag(h->S, h->ng, k, nb, h->status, h->st), "potrf",
+                   nb * nb * (double)nb / 3.0);
+      if (rend - k - nb > 0)
+        ELM_LAUNCH_F(h, launch_trsm_chol_rows(h->S, h->ng, k, nb, rend, h->st), "trsm_rows",
+                     (double)(rend - k - nb) * nb * nb);
       if (rend - k - nb > 0) {
-        rc = run_recs(h, h->trsm_recs, h->trsm_first[step],
-                      h->trsm_first[step + 1] - h->trsm_first[step], "trsm_chol");
-        if (rc) return rc;
         rc = run_recs(h, h->syrk_recs, h->syrk_first[step],
                       h->syrk_first[step + 1] - h->syrk_first[step], "gemm_syrk");
         if (rc) return rc;
       }
     }
-    if (h->emulated) ELM_LAUNCH(h, launch_tri_inv(h->S, h->ng, h->ng, h->cinv, h->st), "tri_inv");
+    // inverses of the diagonal blocks for the triangular solves of the solve phase
+    ELM_LAUNCH(h, launch_tri_inv(h->S, h->ng, h->ng, h->cinv, h->st), "tri_inv");
   }
   h->state = 2;
   return ELM_DDM_OK;

@@ -9,33 +9,27 @@ namespace {
 
 constexpr int NB = CHOL_NB;
 
-// Unblocked Cholesky of the nb x nb diagonal block at (k, k), in shared memory, and, when
-// inv is not NULL, the inverse of that factor (written column-major to inv, ld NB) so that
-// the panel solve L21 = A21 L11^{-T} is a matrix product.  Both run in one loop over the
-// pivots with one barrier per column.  Step j works with the unscaled column j (a_ij, i > j, final at this
+// Unblocked Cholesky of the nb x nb diagonal block at (k, k), in shared memory, one
+// barrier per pivot.  Step j works with the unscaled column j (a_ij, i > j, final at this
 // point) and the multipliers t_i = a_ij / d_j, d_j = a_jj:
-//   Cholesky:  a_ik -= t_i a_kj              for j < k <= i  (= l_ij l_kj)
-//   inverse:   y_ic -= t_i y_jc              for i > j, c <= j
-// where Y = unscaled rows of L^{-1} (forward elimination of L X = I, row r of X being
-// y_r / l_rr).  The two updates touch disjoint entries and read only column j of a and
-// row j of y, so they share the barrier.  At the end l_jj = sqrt(d_j), l_ij = a_ij / l_jj
-// and x_rc = y_rc / l_rr.
+//   a_ik -= t_i a_kj   for j < k <= i   (= l_ij l_kj);
+// at the end l_jj = sqrt(d_j) and l_ij = a_ij / l_jj.
 //
-// FP64 arithmetic is the scarce resource (2 FMA per clock per SM, and a warp-wide FMA
-// occupies the pipe whatever its active lanes), and the pivot reciprocal is a long
-// dependent chain.  So step j is split between a look-ahead warp and the rest:
+// FP64 arithmetic is the scarce resource (2 FMA per clock per SM, a quarter of that for
+// the warps of one SM sub-partition, and a warp-wide FMA occupies the pipe whatever its
+// active lanes), and the pivot reciprocal is a long dependent chain.  So step j is split
+// between a look-ahead warp and the rest:
 //   warp 0:      updates column j+1 (the next pivot column), forms d_{j+1}, its
 //                reciprocal and the next multipliers t^(j+1) (double-buffered);
-//   warps 1..15: the rest of the trailing triangle (columns > j+1) and the inverse's
-//                rectangle (when requested), flattened into one index range so every warp-wide FMA has 32
-//                active lanes.
-// One barrier per column; the reciprocal's latency hides behind the bulk update.
+//   warps 1..15: the rest of the trailing triangle (columns > j+1), flattened into one
+//                index range so every warp-wide FMA has 32 active lanes.
+// The reciprocal's latency hides behind the bulk update.  (Panels of 8 columns factored
+// by one warp in registers measured slower: the whole chain then runs on one
+// sub-partition's quarter of the FP64 pipe.)
 constexpr int POTRF_THREADS = 512;
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict__ S, int ld, int k, int nb,
-                                                              double* __restrict__ inv, unsigned* status) {
-  extern __shared__ double potrf_smem[];
-  double (*a)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem);
-  double (*y)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(potrf_smem + NB * (NB + 1));
+                                                              unsigned* status) {
+  __shared__ double a[NB][NB + 1];
   __shared__ double piv[NB], rl[NB], tcol[2][NB];  // d_j, 1/sqrt(d_j), t^(j) (by parity of j)
   __shared__ int bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -43,7 +37,6 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict
   for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
     const int i = e % NB, j = e / NB;
     a[i][j] = (i < nb && j < nb && i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : 0.0;
-    y[i][j] = (i == j) ? 1.0 : 0.0;
   }
   if (tid == 0) bad = 0;
   __syncthreads();
@@ -75,20 +68,15 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict
         pivot_column(j + 1);
       }
     } else {
-      // triangle of columns j+2.. (size m-1), then rectangle rows j+1.., columns 0..j
-      const int tri = m > 0 ? (m - 1) * m / 2 : 0, total = tri + (inv ? m * (j + 1) : 0);
-      for (int e = tid - 32; e < total; e += BULK) {
-        if (e < tri) {
-          int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-          if ((r + 1) * (r + 2) / 2 <= e) ++r;
-          if (r * (r + 1) / 2 > e) --r;
-          const int c = e - r * (r + 1) / 2;
-          const int i = j + 2 + r, kk = j + 2 + c;
-          a[i][kk] = fma(-t[i], a[kk][j], a[i][kk]);
-        } else {
-          const int f = e - tri, i = j + 1 + f / (j + 1), c = f % (j + 1);
-          y[i][c] = fma(-t[i], y[j][c], y[i][c]);
-        }
+      // triangle of columns j+2.. (size m-1)
+      const int tri = m > 0 ? (m - 1) * m / 2 : 0;
+      for (int e = tid - 32; e < tri; e += BULK) {
+        int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        if ((r + 1) * (r + 2) / 2 <= e) ++r;
+        if (r * (r + 1) / 2 > e) --r;
+        const int c = e - r * (r + 1) / 2;
+        const int i = j + 2 + r, kk = j + 2 + c;
+        a[i][kk] = fma(-t[i], a[kk][j], a[i][kk]);
       }
     }
     __syncthreads();
@@ -101,11 +89,6 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict
     S[(k + i) + (size_t)(k + j) * ld] = i == j ? sqrt(piv[j]) : a[i][j] * rl[j];
   }
   if (tid == 0 && bad) atomicOr(status, ST_NOT_SPD);
-  if (!inv) return;
-  for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
-    const int i = e % NB, j = e / NB;
-    inv[i + j * NB] = (i < nb && j < nb && i >= j) ? y[i][j] * rl[i] : 0.0;
-  }
 }
 
 // Inverses of all diagonal blocks of the finished factor, one block per CTA: column c of
@@ -295,16 +278,8 @@ __global__ void __launch_bounds__(256) k_chol_bwd(const double* __restrict__ L, 
 
 }  // namespace
 
-cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, double* inv, unsigned* status,
-                              cudaStream_t st) {
-  const int smem = 2 * NB * (NB + 1) * (int)sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  k_potrf_diag<<<1, POTRF_THREADS, smem, st>>>(S, ld, k, nb, inv, status); count_launch();
+cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, unsigned* status, cudaStream_t st) {
+  k_potrf_diag<<<1, POTRF_THREADS, 0, st>>>(S, ld, k, nb, status); count_launch();
   return cudaGetLastError();
 }
 
