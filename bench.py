@@ -52,6 +52,22 @@ KERNEL_OF_CLASS = {
 }
 
 
+# DRAM traffic per algorithmic byte of the top kernels, from one ncu capture each on the
+# 4x4 workload (poisson_4x4_n1000, 16 subdomains; the bench's 8x8 workload is too large
+# to capture under the size rule), dram__bytes_read.sum + dram__bytes_write.sum over the
+# launch's algorithmic bytes; traffic scales with the units a launch processes, so the
+# bench's per-launch traffic is this ratio times its per-launch algorithmic bytes.
+TRAFFIC_PER_ALGO_BYTE = {
+    # first QR panel: 9.876 MB read + 256 B written (the panel stays in L2) for
+    # 16 x 2400 x 32 x 8 B read and written once (19.66 MB)
+    "panel_qr": (9.875712e6 / 19.6608e6, "profiles/k_panel_qr_cl_poisson_4x4_n1000.md"),
+    # first QR update A2 -= V W2: 745.95 MB for 855.9 MB (C read + written, V and W2 once)
+    "oz_qr_update": (745.953536e6 / 855.90e6, "profiles/k_ozaki_upd_poisson_4x4_n1000.md"),
+    # first W1^T = A2^T V: 410.99 MB for 435.7 MB (A2, V, W1 once)
+    "oz_qr_w": (410.991872e6 / 435.69e6, "profiles/k_ozaki_fa_poisson_4x4_n1000.md"),
+}
+
+
 def measured_hbm_peak():
     """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else the fallback."""
     try:
@@ -348,8 +364,13 @@ def run_ours(args):
     if dom and dom in prof:
         v = prof[dom]
         roofline = roof(dom, v, v["ms"])
+        per_launch_bytes = v["bytes"] / max(v["launches"], 1)
+        ratio = TRAFFIC_PER_ALGO_BYTE.get(dom)
         roofline.update({
-            "traffic": None, "kernel_class": dom,
+            "traffic": (ratio[0] * per_launch_bytes if ratio and per_launch_bytes > 0 else None),
+            "traffic_source": (f"ncu DRAM bytes of the 4x4 workload ({ratio[1]}) scaled by this "
+                               f"launch's algorithmic bytes" if ratio else None),
+            "kernel_class": dom,
             "kernel": KERNEL_OF_CLASS.get(dom, dom),
             "launches_per_step": v["launches"] // args.steps,
             "avg_launch_us": 1e3 * v["ms"] / max(v["launches"], 1),

@@ -146,7 +146,7 @@ struct elm_ddm_handle {
   std::vector<int> qr_first;     // first record of each panel in qr_recs
   // algorithmic flops of each Householder panel launch: per subdomain a m' x nb panel
   // (2 m' nb^2 - 2 nb^3 / 3) and its compact-WY factor T (m' nb^2)
-  std::vector<double> panel_flops;
+  std::vector<double> panel_flops, panel_bytes;  // per QR panel, summed over subdomains
   std::vector<int> syrk_first;   // first record of each Cholesky step in syrk_recs
   size_t mdiag_elems = 0;
   // plans
@@ -700,12 +700,14 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   };
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, n - k0);
-    double pf = 0.0;
+    double pf = 0.0, pb = 0.0;
     for (int s = 0; s < N; ++s) {
       const double mp = std::max(0, h->ms_h[s] - k0);
       pf += 3.0 * mp * nbe * nbe - 2.0 * nbe * (double)nbe * nbe / 3.0;
+      pb += 2.0 * 8.0 * mp * nbe;  // the panel read and written once
     }
     h->panel_flops.push_back(pf);
+    h->panel_bytes.push_back(pb);
     std::vector<GemmDesc> g1, g2, g3;
     std::vector<SplitDesc> sp1, sp3;
     std::vector<OzDesc> o1, o3;
@@ -1027,9 +1029,9 @@ int elm_ddm_schur(elm_ddm_handle* h) {
   // (b) blocked Householder QR of [K^s | J]
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, h->n - k0);
-    ELM_LAUNCH_F(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->T +
+    ELM_LAUNCH_FB(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->T +
                                     (size_t)b * QR_NB * QR_NB, h->tstride, h->Vp, h->vstride, h->status,
-                                    h->st), "panel_qr", h->panel_flops[b]);
+                                    h->st), "panel_qr", h->panel_flops[b], h->panel_bytes[b]);
     int rc = run_recs(h, h->qr_recs, h->qr_first[b], h->qr_first[b + 1] - h->qr_first[b],
                       "gemm_qr");
     if (rc) return rc;
