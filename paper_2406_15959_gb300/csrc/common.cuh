@@ -151,6 +151,17 @@ cudaError_t launch_backsolve(const double* X, const double* K, long long kstride
 
 // Cholesky factor of the nb x nb diagonal block at (k, k) of S, in place (lower).
 cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, unsigned* status, cudaStream_t st);
+// Whole triangular solves with the factor in S (envelope per 64-row step: rend / jbeg,
+// device arrays of nsteps; Linv the stored diagonal-block inverses), one cooperative
+// launch each on `grid` blocks (chol_solve_grid: 0 when no co-resident grid fits).
+// bar: 2 device words of barrier state.
+int chol_solve_grid(bool forward, int work_max);
+cudaError_t launch_chol_fwd_all(const double* L, int ld, int n, const double* Linv, const int* rend,
+                                int nsteps, double* r, double* y, int nrhs, int grid, unsigned* bar,
+                                unsigned* status, cudaStream_t st);
+cudaError_t launch_chol_bwd_all(const double* L, int ld, int n, const double* Linv, const int* jbeg,
+                                int nsteps, double* y, double* u, int nrhs, int grid, unsigned* bar,
+                                unsigned* status, cudaStream_t st);
 // Inverses of every CHOL_NB diagonal block of the factor L (in S), column-major, ld CHOL_NB.
 cudaError_t launch_tri_inv(const double* S, int ld, int n, double* inv, cudaStream_t st);
 // L21 = A21 L11^{-T} by substitution for rows k+nb .. row_end-1 (16 rows per block).

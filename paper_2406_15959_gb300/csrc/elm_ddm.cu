@@ -112,6 +112,10 @@ struct elm_ddm_handle {
   std::vector<int> perm_h;      // caller interface unknown -> internal index
   std::vector<int> chol_rend;   // per Cholesky block step: end of the envelope rows
   std::vector<int> chol_jbeg;   // per Cholesky block step: first column the block rows touch
+  int* d_rend = nullptr;        // device copies of chol_rend / chol_jbeg
+  int* d_jbeg = nullptr;
+  unsigned* cbar = nullptr;     // grid-barrier state of the persistent triangular solves
+  int fwd_grid = 0, bwd_grid = 0;  // their grids (0: one launch per block step instead)
   // device buffers
   double *K = nullptr, *Am = nullptr, *tau = nullptr, *T = nullptr, *Vp = nullptr;
   double *W1 = nullptr, *W2 = nullptr, *D = nullptr, *M = nullptr, *S = nullptr;
@@ -536,6 +540,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->mg, (size_t)N) && dev_alloc(h, &h->dofmap, (size_t)ng * 4) &&
             dev_alloc(h, &h->ifc_dof, (size_t)N * h->mgld) && dev_alloc(h, &h->perm, (size_t)ng) &&
             dev_alloc(h, &h->cinv, (size_t)((ng + CHOL_NB - 1) / CHOL_NB + 1) * CHOL_NB * CHOL_NB) &&
+            dev_alloc(h, &h->d_rend, h->chol_rend.size()) && dev_alloc(h, &h->d_jbeg, h->chol_jbeg.size()) &&
+            dev_alloc(h, &h->cbar, (size_t)2) &&
             dev_alloc(h, &h->status, 1);
   if (ok && h->use_tabs) {
     const AsmTables& t = h->tabs;
@@ -975,6 +981,18 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   cp(h->dofmap, dofmap.data(), dofmap.size() * sizeof(int));
   cp(h->ifc_dof, ifc.data(), ifc.size() * sizeof(int));
   cp(h->perm, h->perm_h.data(), h->perm_h.size() * sizeof(int));
+  cp(h->d_rend, h->chol_rend.data(), h->chol_rend.size() * sizeof(int));
+  cp(h->d_jbeg, h->chol_jbeg.data(), h->chol_jbeg.size() * sizeof(int));
+  {
+    int rows = 0, cols = 0;
+    for (size_t st = 0; st < h->chol_rend.size(); ++st) {
+      const int k = (int)st * CHOL_NB, nb = std::min(CHOL_NB, ng - k);
+      rows = std::max(rows, h->chol_rend[st] - k - nb);
+      cols = std::max(cols, k - h->chol_jbeg[st]);
+    }
+    h->fwd_grid = ng > 0 ? chol_solve_grid(true, rows) : 0;
+    h->bwd_grid = ng > 0 ? chol_solve_grid(false, cols) : 0;
+  }
   if (h->use_tabs) {
     cp(h->tab_xs, txs.data(), txs.size() * sizeof(double));
     cp(h->tab_ys, tys.data(), tys.size() * sizeof(double));
@@ -1102,18 +1120,26 @@ int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
     ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, h->mgld, h->mg, h->ifc_dof, h->hv, ng, N, nrhs, h->zv,
                               h->st), "mt_h");
     ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
-    for (int k = 0, step = 0; k < ng; k += CHOL_NB, ++step) {
-      const int nb = std::min(CHOL_NB, ng - k);
-      ELM_LAUNCH(h, launch_chol_fwd(h->S, ng, ng, k, nb, h->rv, h->yv, nrhs, h->st,
-                                    h->chol_rend[step], h->cinv + (size_t)step * CHOL_NB * CHOL_NB),
-                 "chol_fwd");
-    }
-    for (int k = ((ng - 1) / CHOL_NB) * CHOL_NB; k >= 0; k -= CHOL_NB) {
-      const int nb = std::min(CHOL_NB, ng - k);
-      ELM_LAUNCH(h, launch_chol_bwd(h->S, ng, ng, k, nb, h->yv, h->uv, nrhs, h->st,
-                                    h->chol_jbeg[k / CHOL_NB],
-                                    h->cinv + (size_t)(k / CHOL_NB) * CHOL_NB * CHOL_NB),
-                 "chol_bwd");
+    const int nsteps = (int)h->chol_rend.size();
+    if (h->fwd_grid > 0 && h->bwd_grid > 0) {
+      ELM_LAUNCH(h, launch_chol_fwd_all(h->S, ng, ng, h->cinv, h->d_rend, nsteps, h->rv, h->yv, nrhs,
+                                        h->fwd_grid, h->cbar, h->status, h->st), "chol_fwd");
+      ELM_LAUNCH(h, launch_chol_bwd_all(h->S, ng, ng, h->cinv, h->d_jbeg, nsteps, h->yv, h->uv, nrhs,
+                                        h->bwd_grid, h->cbar, h->status, h->st), "chol_bwd");
+    } else {
+      for (int k = 0, step = 0; k < ng; k += CHOL_NB, ++step) {
+        const int nb = std::min(CHOL_NB, ng - k);
+        ELM_LAUNCH(h, launch_chol_fwd(h->S, ng, ng, k, nb, h->rv, h->yv, nrhs, h->st,
+                                      h->chol_rend[step], h->cinv + (size_t)step * CHOL_NB * CHOL_NB),
+                   "chol_fwd");
+      }
+      for (int k = ((ng - 1) / CHOL_NB) * CHOL_NB; k >= 0; k -= CHOL_NB) {
+        const int nb = std::min(CHOL_NB, ng - k);
+        ELM_LAUNCH(h, launch_chol_bwd(h->S, ng, ng, k, nb, h->yv, h->uv, nrhs, h->st,
+                                      h->chol_jbeg[k / CHOL_NB],
+                                      h->cinv + (size_t)(k / CHOL_NB) * CHOL_NB * CHOL_NB),
+                   "chol_bwd");
+      }
     }
   }
   ELM_LAUNCH(h, launch_backsolve(h->X, h->K, h->kstride, h->ld, h->mg, h->ifc_dof, h->mgld,

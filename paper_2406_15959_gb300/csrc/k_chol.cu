@@ -276,6 +276,159 @@ __global__ void __launch_bounds__(256) k_chol_bwd(const double* __restrict__ L, 
   }
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Whole triangular solves in one cooperative launch each: the 64-row block steps of
+// k_chol_fwd / k_chol_bwd separated by a grid barrier instead of a kernel boundary (a
+// launch and its tail cost more than a step's work).  Every block forms the step's
+// 64-entry diagonal solve itself from the stored inverse, so one barrier per step
+// suffices; the vectors that other blocks update are read through L2 (ld.global.cg),
+// since L1 is not coherent between SMs.  The barrier's wait is bounded (2 s of
+// %globaltimer): on timeout the kernel flags ST_TIMEOUT and every block returns.
+__device__ __forceinline__ unsigned long long chol_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bar[0]: arrivals, bar[1]: generation.  Returns false (for the whole block) on timeout.
+__device__ bool grid_barrier(unsigned* bar, unsigned* status) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    const unsigned g = *(volatile unsigned*)(bar + 1);
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = chol_ns();
+      while (*(volatile unsigned*)(bar + 1) == g) {
+        if (chol_ns() - t0 > 2000000000ull) {
+          atomicOr(status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// Four threads share each row (forward) or column (backward) of a step, a quarter of
+// the 64 terms each: a single warp's FP64 instructions go through one SM sub-partition's
+// quarter of the FP64 pipe, so neither a 64-term chain per thread nor a warp-wide
+// shuffle reduction per row (five FP64 additions) is cheap here.
+constexpr int CS_ROWS = 64;  // rows / columns per block and pass
+
+// L y = b over all block steps; r holds b on entry and is consumed.
+__global__ void __launch_bounds__(256) k_chol_fwd_all(const double* __restrict__ L, int ld, int n,
+                                                      const double* __restrict__ Linv,
+                                                      const int* __restrict__ rend, int nsteps,
+                                                      double* r, double* y, int nrhs,
+                                                      unsigned* bar, unsigned* status) {
+  __shared__ double Ls[NB][NB + 1];
+  __shared__ double rs[NB], ys[NB], part[4][CS_ROWS];
+  const int tid = threadIdx.x, il = tid % CS_ROWS, q = tid / CS_ROWS;
+  for (int st = 0; st < nsteps; ++st) {
+    const int k = st * NB, nb = min(NB, n - k), row_end = rend[st];
+    const double* Li = Linv + (size_t)st * NB * NB;
+    for (int e = tid; e < NB * NB; e += 256) {
+      const int i = e % NB, j = e / NB;
+      Ls[i][j] = (i < nb && j < nb && i >= j) ? Li[i + (size_t)j * NB] : 0.0;
+    }
+    for (int c = 0; c < nrhs; ++c) {
+      double* rr = r + (size_t)c * n;
+      __syncthreads();
+      if (tid < NB) rs[tid] = tid < nb ? __ldcg(rr + k + tid) : 0.0;
+      __syncthreads();
+      {  // y_k = Linv r_k, row il, terms 16 q .. 16 q + 15
+        double p = 0.0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) p = fma(Ls[il][16 * q + t], rs[16 * q + t], p);
+        part[q][il] = p;
+      }
+      __syncthreads();
+      if (tid < NB) ys[tid] = (part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid]);
+      __syncthreads();
+      if (blockIdx.x == 0 && tid < nb) y[(size_t)c * n + k + tid] = ys[tid];
+      for (int base = k + nb + blockIdx.x * CS_ROWS; base < row_end; base += gridDim.x * CS_ROWS) {
+        const int i = base + il;
+        double p = 0.0;
+        if (i < row_end) {
+          const double* Lr = L + i + (size_t)(k + 16 * q) * ld;
+#pragma unroll
+          for (int t = 0; t < 16; ++t)
+            if (16 * q + t < nb) p = fma(Lr[(size_t)t * ld], ys[16 * q + t], p);
+        }
+        __syncthreads();
+        part[q][il] = p;
+        __syncthreads();
+        if (q == 0 && i < row_end)
+          __stcg(rr + i, __ldcg(rr + i) - ((part[0][il] + part[1][il]) + (part[2][il] + part[3][il])));
+      }
+    }
+    if (!grid_barrier(bar, status)) return;
+  }
+}
+
+// L^T u = y over all block steps (last to first); y is consumed.
+__global__ void __launch_bounds__(256) k_chol_bwd_all(const double* __restrict__ L, int ld, int n,
+                                                      const double* __restrict__ Linv,
+                                                      const int* __restrict__ jbeg, int nsteps,
+                                                      double* y, double* u, int nrhs,
+                                                      unsigned* bar, unsigned* status) {
+  __shared__ double Ls[NB][NB + 1];
+  __shared__ double ysh[NB], us[NB], part[4][CS_ROWS];
+  const int tid = threadIdx.x, il = tid % CS_ROWS, q = tid / CS_ROWS;
+  const int jl = tid >> 2, qq = tid & 3;  // column pass: 4 lanes per column
+  for (int st = nsteps - 1; st >= 0; --st) {
+    const int k = st * NB, nb = min(NB, n - k), j_begin = jbeg[st];
+    const double* Li = Linv + (size_t)st * NB * NB;
+    for (int e = tid; e < NB * NB; e += 256) {
+      const int i = e % NB, j = e / NB;
+      Ls[i][j] = (i < nb && j < nb && i >= j) ? Li[i + (size_t)j * NB] : 0.0;
+    }
+    for (int c = 0; c < nrhs; ++c) {
+      double* yy = y + (size_t)c * n;
+      __syncthreads();
+      if (tid < NB) ysh[tid] = tid < nb ? __ldcg(yy + k + tid) : 0.0;
+      __syncthreads();
+      {  // u_k = Linv^T y_k: u_i = sum_l Linv[l][i] y_l, terms 16 q .. 16 q + 15
+        double p = 0.0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) p = fma(Ls[16 * q + t][il], ysh[16 * q + t], p);
+        part[q][il] = p;
+      }
+      __syncthreads();
+      if (tid < NB) us[tid] = (part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid]);
+      __syncthreads();
+      if (blockIdx.x == 0 && tid < nb) u[(size_t)c * n + k + tid] = us[tid];
+      // y_j -= L_{k,j}^T u_k for j_begin <= j < k: column j's 64 rows are contiguous
+      for (int base = j_begin + blockIdx.x * CS_ROWS; base < k; base += gridDim.x * CS_ROWS) {
+        const int j = base + jl;
+        double p = 0.0;
+        if (j < k) {
+          const double* Lc = L + (k + 16 * qq) + (size_t)j * ld;
+#pragma unroll
+          for (int t = 0; t < 16; ++t)
+            if (16 * qq + t < nb) p = fma(Lc[t], us[16 * qq + t], p);
+        }
+        p += __shfl_xor_sync(0xffffffffu, p, 1);
+        p += __shfl_xor_sync(0xffffffffu, p, 2);
+        if (qq == 0 && j < k) __stcg(yy + j, __ldcg(yy + j) - p);
+      }
+    }
+    if (!grid_barrier(bar, status)) return;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, unsigned* status, cudaStream_t st) {
@@ -310,6 +463,43 @@ cudaError_t launch_chol_fwd(const double* L, int ld, int n, int k, int nb, doubl
   const int gx = rows > 0 ? (rows + 255) / 256 : 1;
   k_chol_fwd<<<dim3(gx, nrhs), 256, 0, st>>>(L, ld, n, k, nb, row_end, Linv, r, y); count_launch();
   return cudaGetLastError();
+}
+
+int chol_solve_grid(bool forward, int work_max) {
+  int g = (work_max + CS_ROWS - 1) / CS_ROWS;  // rows (forward) or columns (backward) per block
+  if (g < 1) g = 1;
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, forward ? (const void*)k_chol_fwd_all
+                                                              : (const void*)k_chol_bwd_all, 256, 0);
+  const int cap = sms * (occ > 0 ? occ : 0);
+  if (g > sms) g = sms;
+  return g <= cap ? g : 0;  // 0: no co-resident grid (use the step kernels)
+}
+
+cudaError_t launch_chol_fwd_all(const double* L, int ld, int n, const double* Linv, const int* rend,
+                                int nsteps, double* r, double* y, int nrhs, int grid, unsigned* bar,
+                                unsigned* status, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&L, (void*)&ld, (void*)&n, (void*)&Linv, (void*)&rend, (void*)&nsteps,
+                  (void*)&r, (void*)&y, (void*)&nrhs, (void*)&bar, (void*)&status};
+  e = cudaLaunchCooperativeKernel((const void*)k_chol_fwd_all, dim3(grid), dim3(256), args, 0, st);
+  count_launch();
+  return e;
+}
+
+cudaError_t launch_chol_bwd_all(const double* L, int ld, int n, const double* Linv, const int* jbeg,
+                                int nsteps, double* y, double* u, int nrhs, int grid, unsigned* bar,
+                                unsigned* status, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&L, (void*)&ld, (void*)&n, (void*)&Linv, (void*)&jbeg, (void*)&nsteps,
+                  (void*)&y, (void*)&u, (void*)&nrhs, (void*)&bar, (void*)&status};
+  e = cudaLaunchCooperativeKernel((const void*)k_chol_bwd_all, dim3(grid), dim3(256), args, 0, st);
+  count_launch();
+  return e;
 }
 
 cudaError_t launch_chol_bwd(const double* L, int ld, int n, int k, int nb, double* y,
