@@ -304,6 +304,116 @@ __global__ void __launch_bounds__(256) k_apply_qt(double* __restrict__ X, const 
   }
 }
 
+// x <- Q^T x as k_apply_qt, with a cluster of AQ_CL CTAs per (subdomain, right-hand side)
+// so that every SM's FP64 pipe takes part (one CTA per subdomain left most SMs idle).
+// The 32-row groups of x are dealt round-robin to the CTAs (group g to CTA g % AQ_CL),
+// which keeps the shrinking active rows (r >= k0) balanced; each row stays with one
+// thread for both phases of a panel, so x needs no synchronisation.  Per panel: the
+// CTA's 32 partial dot products V^T x (warp transpose-sums, then the warps' sums), one
+// cluster barrier, every CTA adds the AQ_CL partials through distributed shared memory
+// (double-buffered by panel parity, so one barrier per panel suffices), w2 = T^T w with
+// all threads, and x -= V w2 on the CTA's rows.
+constexpr int AQ_CL = 4;
+__global__ void __cluster_dims__(AQ_CL, 1, 1) __launch_bounds__(256)
+    k_apply_qt_cl(double* __restrict__ X, const double* __restrict__ K, long long kstride, int ld,
+                  const int* __restrict__ ms_arr, int N, int n, const double* __restrict__ Tb,
+                  long long tstride) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int c = (int)cluster.block_rank();
+  const int s = blockIdx.y, rh = blockIdx.z;
+  const int m = ms_arr[s];
+  double* x = X + ((size_t)rh * N + s) * ld;
+  const double* A = K + (size_t)s * kstride;
+  const double* Ts = Tb + (size_t)s * tstride;
+  __shared__ double wred[8][32];
+  __shared__ double part[2][32];  // this CTA's partial V^T x, by panel parity
+  __shared__ double w[32], w2p[8][32], w2[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ngroups = (m + 31) / 32;
+  for (int k0 = 0, pan = 0; k0 < n; k0 += 32, ++pan) {
+    const int nbe = min(32, n - k0), par = pan & 1;
+    // owned groups g >= k0 / 32 with g % AQ_CL == c; warp w takes every 8th of them
+    int g0 = k0 / 32;
+    g0 += (c - g0 % AQ_CL + AQ_CL) % AQ_CL;
+    double acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+    for (int g = g0 + warp * AQ_CL; g < ngroups; g += 8 * AQ_CL) {
+      const int r = g * 32 + lane;
+      if (r >= m) continue;
+      const double xr = x[r];
+      const double* row = A + r + (size_t)k0 * ld;
+      if (r >= k0 + 32) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if (k < nbe) acc[k] = fma(row[(size_t)k * ld], xr, acc[k]);
+      } else {  // the panel's own 32 rows: unit diagonal, zeros above
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          if (k < nbe) {
+            if (r > k0 + k) acc[k] = fma(row[(size_t)k * ld], xr, acc[k]);
+            else if (r == k0 + k) acc[k] += xr;
+          }
+        }
+      }
+    }
+    const double ws = warp_transpose_sum32(acc);
+    wred[warp][lane] = ws;
+    __syncthreads();
+    if (tid < 32) {
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t += wred[q][tid];
+      part[par][tid] = t;
+    }
+    cluster.sync();
+    if (tid < 32) {
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < AQ_CL; ++q) t += cluster.map_shared_rank(&part[par][0], q)[tid];
+      w[tid] = tid < nbe ? t : 0.0;
+    }
+    __syncthreads();
+    {  // w2 = T^T w, T upper triangular: w2_i = sum_{j <= i} T[j][i] w_j, 4 terms per thread
+      const int i = lane, j0 = warp * 4;
+      const double* Tk = Ts + (size_t)pan * 1024;
+      double t = 0.0;
+#pragma unroll
+      for (int j = j0; j < j0 + 4; ++j)
+        if (j <= i) t = fma(Tk[j + 32 * i], w[j], t);
+      w2p[warp][i] = t;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t += w2p[q][tid];
+      w2[tid] = t;
+    }
+    __syncthreads();
+    for (int g = g0 + warp * AQ_CL; g < ngroups; g += 8 * AQ_CL) {
+      const int r = g * 32 + lane;
+      if (r >= m) continue;
+      double xr = x[r];
+      const double* row = A + r + (size_t)k0 * ld;
+      if (r >= k0 + 32) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if (k < nbe) xr = fma(-row[(size_t)k * ld], w2[k], xr);
+      } else {
+        for (int k = 0; k < nbe; ++k) {
+          const double v = r > k0 + k ? row[(size_t)k * ld] : (r == k0 + k ? 1.0 : 0.0);
+          xr = fma(-v, w2[k], xr);
+        }
+      }
+      x[r] = xr;
+    }
+    __syncthreads();
+  }
+  cluster.sync();  // no CTA leaves while another may still read its partials
+}
+
 // gq = Q_G q and hq = Y q for one subdomain / right-hand side (warp per interface row).
 __global__ void __launch_bounds__(256) k_iface_vecs(const double* __restrict__ X,
                                                     const double* __restrict__ K, long long kstride,
@@ -620,7 +730,7 @@ cudaError_t launch_load_rhs(double* X, const double* rhs, int N, int m_max, int 
 cudaError_t launch_apply_qt(double* X, const double* K, long long kstride, int ld,
                             const int* ms, int N, int n, const double* T, long long tstride,
                             int nrhs, cudaStream_t st) {
-  k_apply_qt<<<dim3(N, nrhs), 256, 0, st>>>(X, K, kstride, ld, ms, N, n, T, tstride); count_launch();
+  k_apply_qt_cl<<<dim3(AQ_CL, N, nrhs), 256, 0, st>>>(X, K, kstride, ld, ms, N, n, T, tstride); count_launch();
   return cudaGetLastError();
 }
 
