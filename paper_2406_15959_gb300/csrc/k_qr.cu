@@ -528,6 +528,82 @@ __global__ void __launch_bounds__(256) k_backsolve(const double* __restrict__ X,
 }
 
 
+// k_backsolve with a cluster of AQ_CL CTAs per (subdomain, right-hand side).  Entry j of
+// v and the rows of R it heads belong to CTA (j / 32) % AQ_CL.  Each CTA forms its own
+// entries of v = q + Q_G^T E u_Gamma, then for each 32-column block of R from the last:
+// the owning CTA solves the block's triangle (one warp, multiplying by the stored
+// reciprocals of R's diagonal), one cluster barrier, every CTA reads the block's 32
+// results from the owner's shared memory and updates its own entries above the block.
+// The owner of the next block has applied every earlier block before it starts, since
+// it reads them after the barriers in order.
+__global__ void __cluster_dims__(AQ_CL, 1, 1) __launch_bounds__(256)
+    k_backsolve_cl(const double* __restrict__ X, const double* __restrict__ K, long long kstride,
+                   int ld, const int* __restrict__ mg_arr, const int* __restrict__ ifc_dof, int mgld,
+                   const double* __restrict__ u, int n_gamma, int N, int n, double* __restrict__ cout) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int c = (int)cluster.block_rank();
+  extern __shared__ double bs_smem[];
+  double* v = bs_smem;            // [n]: this CTA's entries (others unused)
+  double* rinv = bs_smem + n;     // [n]: 1 / R_jj for this CTA's entries
+  double* ug = bs_smem + 2 * n;   // [mg]: u_Gamma at this subdomain's interface rows
+  __shared__ double cb[32];
+  const int s = blockIdx.y, rh = blockIdx.z;
+  const int mg = mg_arr[s];
+  const double* q = X + ((size_t)rh * N + s) * ld;
+  const double* A = K + (size_t)s * kstride;
+  const double* QGt = A + (size_t)n * ld;
+  const int* dofs = ifc_dof + (size_t)s * mgld;
+  const double* uu = u + (size_t)rh * n_gamma;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ng32 = (n + 31) / 32;
+  for (int i = tid; i < mg; i += 256) ug[i] = uu[dofs[i]];
+  __syncthreads();
+  // owned entry number e -> j = ((e / 32) * AQ_CL + c) * 32 + e % 32
+  const int owned = ((ng32 - c + AQ_CL - 1) / AQ_CL) * 32;
+  for (int e = tid; e < owned; e += 256) {
+    const int j = ((e / 32) * AQ_CL + c) * 32 + (e % 32);
+    if (j >= n) continue;
+    double a = q[j];
+    for (int i = 0; i < mg; ++i) a = fma(QGt[j + (size_t)i * ld], ug[i], a);
+    v[j] = a;
+    rinv[j] = 1.0 / A[j + (size_t)j * ld];
+  }
+  __syncthreads();
+  for (int jb = (ng32 - 1) * 32; jb >= 0; jb -= 32) {
+    const int nbj = min(32, n - jb), own = (jb / 32) % AQ_CL;
+    if (c == own && warp == 0) {
+      for (int j = jb + nbj - 1; j >= jb; --j) {
+        const double cj = v[j] * rinv[j];
+        __syncwarp();
+        if (lane == 0) v[j] = cj;
+        if (lane < j - jb) v[jb + lane] = fma(-A[(jb + lane) + (size_t)j * ld], cj, v[jb + lane]);
+        __syncwarp();
+      }
+    }
+    cluster.sync();
+    if (tid < 32) cb[tid] = tid < nbj ? cluster.map_shared_rank(v, own)[jb + tid] : 0.0;
+    __syncthreads();
+    // this CTA's entries above the block
+    const int owned_above = ((jb / 32 - c + AQ_CL - 1) / AQ_CL) * 32;
+    for (int e = tid; e < owned_above; e += 256) {
+      const int i = ((e / 32) * AQ_CL + c) * 32 + (e % 32);
+      double t = v[i];
+      const double* Ar = A + i + (size_t)jb * ld;
+#pragma unroll 8
+      for (int l = 0; l < nbj; ++l) t = fma(-Ar[(size_t)l * ld], cb[l], t);
+      v[i] = t;
+    }
+    __syncthreads();
+  }
+  double* co = cout + ((size_t)rh * N + s) * n;
+  for (int e = tid; e < owned; e += 256) {
+    const int j = ((e / 32) * AQ_CL + c) * 32 + (e % 32);
+    if (j < n) co[j] = v[j];
+  }
+  cluster.sync();  // no CTA leaves while another may still read its results
+}
+
 // Cluster variant of the panel factorisation: the 4 CTAs of a cluster share one
 // subdomain's panel, each holding a contiguous quarter of its rows in shared memory.
 // The norm and the 32 dot products of every column are reduced across the cluster
@@ -767,14 +843,26 @@ cudaError_t launch_mt_h(const double* M, long long mstride, int mgld, const int*
 cudaError_t launch_backsolve(const double* X, const double* K, long long kstride, int ld,
                              const int* mg, const int* ifc_dof, int mgld, const double* u,
                              int n_gamma, int N, int n, int nrhs, double* c, cudaStream_t st) {
-  const size_t smem = (size_t)n * sizeof(double);
+  // v, 1 / R_jj and u_Gamma at the interface rows (mgld >= every subdomain's m_Gamma)
+  const size_t smem = (2 * (size_t)n + (size_t)mgld) * sizeof(double);
+  if (smem > 227 * 1024) {
+    const size_t sm1 = (size_t)n * sizeof(double);
+    if (sm1 > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sm1);
+      if (e != cudaSuccess) return e;
+    }
+    k_backsolve<<<dim3(N, nrhs), 256, sm1, st>>>(X, K, kstride, ld, mg, ifc_dof, mgld, u, n_gamma,
+                                                 N, n, c); count_launch();
+    return cudaGetLastError();
+  }
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_backsolve_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_backsolve<<<dim3(N, nrhs), 256, smem, st>>>(X, K, kstride, ld, mg, ifc_dof, mgld, u, n_gamma,
-                                                N, n, c); count_launch();
+  k_backsolve_cl<<<dim3(AQ_CL, N, nrhs), 256, smem, st>>>(X, K, kstride, ld, mg, ifc_dof, mgld, u,
+                                                          n_gamma, N, n, c); count_launch();
   return cudaGetLastError();
 }
 
