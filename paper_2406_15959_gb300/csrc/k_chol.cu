@@ -336,12 +336,25 @@ __global__ void __launch_bounds__(256) k_chol_fwd_all(const double* __restrict__
   __shared__ double Ls[NB][NB + 1];
   __shared__ double rs[NB], ys[NB], part[4][CS_ROWS];
   const int tid = threadIdx.x, il = tid % CS_ROWS, q = tid / CS_ROWS;
+  // this thread's 16 entries of a step's diagonal-block inverse: fetched before the
+  // previous step's barrier, stored after it
+  double pre[NB * NB / 256];
+  auto fetch = [&](int st) {
+    const int nb = min(NB, n - st * NB);
+    const double* Li = Linv + (size_t)st * NB * NB;
+#pragma unroll
+    for (int m = 0; m < NB * NB / 256; ++m) {
+      const int e = tid + 256 * m, i = e % NB, j = e / NB;
+      pre[m] = (i < nb && j < nb && i >= j) ? Li[i + (size_t)j * NB] : 0.0;
+    }
+  };
+  if (nsteps > 0) fetch(0);
   for (int st = 0; st < nsteps; ++st) {
     const int k = st * NB, nb = min(NB, n - k), row_end = rend[st];
-    const double* Li = Linv + (size_t)st * NB * NB;
-    for (int e = tid; e < NB * NB; e += 256) {
-      const int i = e % NB, j = e / NB;
-      Ls[i][j] = (i < nb && j < nb && i >= j) ? Li[i + (size_t)j * NB] : 0.0;
+#pragma unroll
+    for (int m = 0; m < NB * NB / 256; ++m) {
+      const int e = tid + 256 * m;
+      Ls[e % NB][e / NB] = pre[m];
     }
     for (int c = 0; c < nrhs; ++c) {
       double* rr = r + (size_t)c * n;
@@ -374,6 +387,7 @@ __global__ void __launch_bounds__(256) k_chol_fwd_all(const double* __restrict__
           __stcg(rr + i, __ldcg(rr + i) - ((part[0][il] + part[1][il]) + (part[2][il] + part[3][il])));
       }
     }
+    if (st + 1 < nsteps) fetch(st + 1);
     if (!grid_barrier(bar, status)) return;
   }
 }
@@ -388,12 +402,23 @@ __global__ void __launch_bounds__(256) k_chol_bwd_all(const double* __restrict__
   __shared__ double ysh[NB], us[NB], part[4][CS_ROWS];
   const int tid = threadIdx.x, il = tid % CS_ROWS, q = tid / CS_ROWS;
   const int jl = tid >> 2, qq = tid & 3;  // column pass: 4 lanes per column
+  double pre[NB * NB / 256];
+  auto fetch = [&](int st) {
+    const int nb = min(NB, n - st * NB);
+    const double* Li = Linv + (size_t)st * NB * NB;
+#pragma unroll
+    for (int m = 0; m < NB * NB / 256; ++m) {
+      const int e = tid + 256 * m, i = e % NB, j = e / NB;
+      pre[m] = (i < nb && j < nb && i >= j) ? Li[i + (size_t)j * NB] : 0.0;
+    }
+  };
+  if (nsteps > 0) fetch(nsteps - 1);
   for (int st = nsteps - 1; st >= 0; --st) {
     const int k = st * NB, nb = min(NB, n - k), j_begin = jbeg[st];
-    const double* Li = Linv + (size_t)st * NB * NB;
-    for (int e = tid; e < NB * NB; e += 256) {
-      const int i = e % NB, j = e / NB;
-      Ls[i][j] = (i < nb && j < nb && i >= j) ? Li[i + (size_t)j * NB] : 0.0;
+#pragma unroll
+    for (int m = 0; m < NB * NB / 256; ++m) {
+      const int e = tid + 256 * m;
+      Ls[e % NB][e / NB] = pre[m];
     }
     for (int c = 0; c < nrhs; ++c) {
       double* yy = y + (size_t)c * n;
@@ -425,6 +450,7 @@ __global__ void __launch_bounds__(256) k_chol_bwd_all(const double* __restrict__
         if (qq == 0 && j < k) __stcg(yy + j, __ldcg(yy + j) - p);
       }
     }
+    if (st > 0) fetch(st - 1);
     if (!grid_barrier(bar, status)) return;
   }
 }
