@@ -64,6 +64,9 @@ struct OzDesc {
   int M, N, K;
   int tile0;  // unused (kept zero)
   long long a_rs;  // fused-split launches: At is the FP64 A, element (i, k) at At[i * a_rs + k]
+  // persistent product with GEMM_LOWER: column j of this C is column j + lower_off of the
+  // symmetric matrix, so a tile is kept when its first column is on or below the diagonal
+  int lower_off = 0;
 };
 
 // Per right-hand side state of the CG solve of the Schur system (k_cg.cu).
@@ -85,9 +88,10 @@ cudaError_t launch_ozaki(int nt, const OzDesc* d, int count, int max_tiles, doub
 // writes that table (out may be null to count) and skips the tiles above the diagonal of
 // a GEMM_LOWER product; it returns the number of tiles.
 int oz_upd_tile_table(const OzDesc* descs, int count, int flags, int4* out);
+// max_grid > 0 caps the persistent grid (SMs left to work on another stream).
 cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int total_tiles,
                              double alpha, double beta, int flags, unsigned* status,
-                             cudaStream_t st);
+                             cudaStream_t st, int max_grid = 0);
 // C = A B^T with the FP64 A split inside the kernel (At = FP64 A, a_rs its row stride, K
 // contiguous; Ae its row exponents), B split as usual with row_tile 32, N <= 32, beta = 0.
 cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned* status,

@@ -36,6 +36,7 @@ struct LaunchRec {
   double bytes = 0.0;          // algorithmic HBM bytes (FP64 operands read, C read/written)
   const char* name = nullptr;  // kernel class for profiling (nullptr: the caller's name)
   int toff = 0;                // persistent launches: offset of the tile table
+  int side = 0;                // 1: runs on the handle's second stream, one SM left free
 };
 
 // One profiled launch: events around it, its class and algorithmic flops.
@@ -103,6 +104,11 @@ std::vector<int> rcm_order(const std::vector<std::vector<int>>& adj) {
 struct elm_ddm_handle {
   elm_ddm_desc desc{};
   cudaStream_t st = nullptr;
+  // Cholesky look-ahead (tensor-core back end): the SYRK of block step k beyond the next
+  // block column runs on st2 while st factors that column; evS / evB order the two
+  int sms = 0;
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t evS = nullptr, evB = nullptr;
   int N = 0, n = 0, m_max = 0, ld = 0, ncap = 0, mgmax = 0, mgld = 0, ng = 0, nblk = 0;
   int max_rhs = 1;
   long long kstride = 0, astride = 0, mstride = 0, tstride = 0, vstride = 0, wstride = 0;
@@ -200,6 +206,9 @@ bool dev_alloc(elm_ddm_handle* h, T** p, size_t count) {
 void free_all(elm_ddm_handle* h) {
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
+  if (h->st2) { cudaStreamSynchronize(h->st2); cudaStreamDestroy(h->st2); h->st2 = nullptr; }
+  if (h->evS) { cudaEventDestroy(h->evS); h->evS = nullptr; }
+  if (h->evB) { cudaEventDestroy(h->evB); h->evB = nullptr; }
 }
 
 cudaEvent_t next_event(elm_ddm_handle* h) {
@@ -218,11 +227,12 @@ struct ProfScope {
   cudaEvent_t a = nullptr;
   const char* name;
   double flops, bytes;
-  ProfScope(elm_ddm_handle* h_, const char* n, double f, double by = 0.0)
-      : h(h_), name(n), flops(f), bytes(by) {
+  cudaStream_t st;
+  ProfScope(elm_ddm_handle* h_, const char* n, double f, double by = 0.0, cudaStream_t s = nullptr)
+      : h(h_), name(n), flops(f), bytes(by), st(s ? s : h_->st) {
     if (h->profiling && (h->prof_only.empty() || h->prof_only == name)) {
       a = next_event(h);
-      if (a) cudaEventRecord(a, h->st);
+      if (a) cudaEventRecord(a, st);
       else h->prof_dropped++;
     }
   }
@@ -230,7 +240,7 @@ struct ProfScope {
     if (!a) return;
     cudaEvent_t b = next_event(h);
     if (!b) { h->prof_dropped++; return; }
-    cudaEventRecord(b, h->st);
+    cudaEventRecord(b, st);
     h->prof.push_back({a, b, name, flops, bytes});
   }
 };
@@ -277,7 +287,16 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
     else if (L.kind == 6)
       ELM_LAUNCH_F(h, launch_trsm_y_diag(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg,
                                          h->mgmax, h->N, h->n, L.off, h->st), nm, L.flops);
-    else if (L.kind == 4)
+    else if (L.kind == 4 && L.side) {
+      cudaError_t e_;
+      {
+        ProfScope ps_(h, nm, L.flops, L.bytes, h->st2);
+        e_ = launch_ozaki_upd(h->od + L.off, L.count, h->ut + L.toff, L.max_tiles, L.alpha, L.beta,
+                              L.flags, h->status, h->st2, h->sms - 1);
+      }
+      h->launches++;
+      if (e_ != cudaSuccess) return cuda_fail(h, e_, nm);
+    } else if (L.kind == 4)
       ELM_LAUNCH_FB(h, launch_ozaki_upd(h->od + L.off, L.count, h->ut + L.toff, L.max_tiles, L.alpha,
                                         L.beta, L.flags, h->status, h->st), nm, L.flops, L.bytes);
     else
@@ -511,6 +530,22 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
   }
 
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->evS, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->evB, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (h->st2) cudaStreamDestroy(h->st2);
+      if (h->evS) cudaEventDestroy(h->evS);
+      if (h->evB) cudaEventDestroy(h->evB);
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_CUDA, "setup: second stream");
+    }
+  }
+
   // ---- allocation ----
   bool ok = dev_alloc(h, &h->K, (size_t)N * h->kstride) &&
             dev_alloc(h, &h->Am, (size_t)N * h->astride) &&
@@ -583,7 +618,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const size_t ce = al((size_t)std::max(restmax, 1) * 4);
   if (h->emulated) {
     char* base = nullptr;
-    if (!dev_alloc(h, &base, per_sub * N + c1 + c2 + 2 * ce)) {
+    if (!dev_alloc(h, &base, per_sub * N + 2 * (c1 + c2 + 2 * ce))) {
       free_all(h);
       delete h;
       return fail(nullptr, ELM_DDM_ERR_OOM, "device allocation failed (split workspace)");
@@ -940,15 +975,29 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       double* L21 = h->S + (k + nb) + (size_t)k * ng;
       double* S22 = h->S + (k + nb) + (size_t)(k + nb) * ng;
       if (h->emulated) {
-        int* xa = (int*)(chol_region + c1 + c2);
-        int* xb = (int*)(chol_region + c1 + c2 + ce);
+        // digit planes of L21 in one of two buffers (by step parity: the split of step
+        // k + 1 runs while part B of step k still reads those of step k)
+        char* reg = chol_region + (size_t)(step & 1) * (c1 + c2 + 2 * ce);
+        int* xa = (int*)(reg + c1 + c2);
+        int* xb = (int*)(reg + c1 + c2 + ce);
         // the panel solve L21 = A21 L11^{-T} runs by substitution (launch_trsm_chol_rows)
-        std::vector<SplitDesc> sp{{L21, 1, ng, rest, nb, xa, chol_region, 128},
-                                  {L21, 1, ng, rest, nb, xb, chol_region + c1, 32}};
+        std::vector<SplitDesc> sp{{L21, 1, ng, rest, nb, xa, reg, 128},
+                                  {L21, 1, ng, rest, nb, xb, reg + c1, 32}};
         add_split_rec(h->syrk_recs, sp, "split_syrk");
-        add_oz_rec(h->syrk_recs,
-                   {{chol_region, xa, chol_region + c1, xb, S22, 1, ng, rest, rest, nb, 0}}, 0, -1.0,
-                   1.0, GEMM_LOWER, "oz_syrk");
+        // SYRK A22 -= L21 L21^T in two parts: A, the next block column (what the next
+        // step's factor and panel solve need), on the main stream; B, the columns beyond,
+        // on the second stream (B operand rows and C columns offset by nb2)
+        const int nb2 = std::min(CHOL_NB, rest);
+        add_oz_rec(h->syrk_recs, {{reg, xa, reg + c1, xb, S22, 1, ng, rest, nb2, nb, 0}}, 0, -1.0, 1.0,
+                   GEMM_LOWER, "oz_syrk");
+        if (rest > nb2) {
+          const size_t btile = oz_split_elems(32, nb, 32) * 2;  // bytes of one 32-row B tile
+          OzDesc b{reg, xa, reg + c1 + (size_t)(nb2 / 32) * btile, xb + nb2, S22 + (size_t)nb2 * ng,
+                   1, ng, rest, rest - nb2, nb, 0};
+          b.lower_off = nb2;
+          add_oz_rec(h->syrk_recs, {b}, 0, -1.0, 1.0, GEMM_LOWER, "oz_syrk_b");
+          h->syrk_recs.back().side = 1;
+        }
       } else {
         add_gemm_rec(h->syrk_recs, {{L21, L21, S22, rest, rest, nb, ng, ng, ng}}, false, true, -1.0,
                      1.0, GEMM_LOWER);
@@ -1078,6 +1127,11 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     // Jacobi preconditioner of the CG solves, taken before the factorisation overwrites S
     ELM_LAUNCH(h, launch_diag_inv(h->S, h->ng, h->sdinv, h->st), "diag_inv");
     h->has_sdinv = true;
+    // Look-ahead (tensor-core back end): part B of step k's SYRK (columns beyond the next
+    // block column) runs on st2 while st factors and solves that column.  st2 starts B
+    // after st's split of step k (evS); st waits for B(k - 1) (evB) before its part A(k),
+    // the first launch that touches B(k - 1)'s columns.
+    bool b_pending = false;
     for (int k = 0, step = 0; k < h->ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, h->ng - k);
       // the factor (nb^3/3), then the panel solve L21 = A21 L11^{-T} by substitution
@@ -1088,10 +1142,38 @@ int elm_ddm_schur(elm_ddm_handle* h) {
         ELM_LAUNCH_F(h, launch_trsm_chol_rows(h->S, h->ng, k, nb, rend, h->st), "trsm_rows",
                      (double)(rend - k - nb) * nb * nb);
       if (rend - k - nb > 0) {
-        rc = run_recs(h, h->syrk_recs, h->syrk_first[step],
-                      h->syrk_first[step + 1] - h->syrk_first[step], "gemm_syrk");
-        if (rc) return rc;
+        const int r0 = h->syrk_first[step], nr = h->syrk_first[step + 1] - r0;
+        if (!h->emulated) {
+          rc = run_recs(h, h->syrk_recs, r0, nr, "gemm_syrk");
+          if (rc) return rc;
+        } else {
+          // records: split, part A, part B (when there are columns beyond the next block)
+          const bool has_b = nr == 3 && h->syrk_recs[r0 + 2].side;
+          rc = run_recs(h, h->syrk_recs, r0, 1, "split_syrk");
+          if (rc) return rc;
+          cudaError_t e2 = cudaSuccess;
+          if (has_b) {
+            e2 = cudaEventRecord(h->evS, h->st);
+            if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(h->st2, h->evS, 0);
+          }
+          if (e2 == cudaSuccess && b_pending) e2 = cudaStreamWaitEvent(h->st, h->evB, 0);
+          if (e2 != cudaSuccess) return cuda_fail(h, e2, "schur: look-ahead events");
+          b_pending = false;
+          rc = run_recs(h, h->syrk_recs, r0 + 1, 1, "oz_syrk");
+          if (rc) return rc;
+          if (has_b) {
+            rc = run_recs(h, h->syrk_recs, r0 + 2, 1, "oz_syrk_b");
+            if (rc) return rc;
+            e2 = cudaEventRecord(h->evB, h->st2);
+            if (e2 != cudaSuccess) return cuda_fail(h, e2, "schur: look-ahead events");
+            b_pending = true;
+          }
+        }
       }
+    }
+    if (b_pending) {
+      const cudaError_t e2 = cudaStreamWaitEvent(h->st, h->evB, 0);
+      if (e2 != cudaSuccess) return cuda_fail(h, e2, "schur: look-ahead join");
     }
     // inverses of the diagonal blocks for the triangular solves of the solve phase
     ELM_LAUNCH(h, launch_tri_inv(h->S, h->ng, h->ng, h->cinv, h->st), "tri_inv");

@@ -1035,7 +1035,7 @@ int oz_upd_tile_table(const OzDesc* descs, int count, int flags, int4* out) {
     const int tm = (d.M + OZ_M - 1) / OZ_M, tn = (d.N + UPD_NT - 1) / UPD_NT;
     for (int bj = 0; bj < tn; ++bj)
       for (int bi = 0; bi < tm; ++bi) {
-        if ((flags & GEMM_LOWER) && bj * UPD_NT > bi * OZ_M + OZ_M - 1) continue;  // above the diagonal
+        if ((flags & GEMM_LOWER) && bj * UPD_NT + d.lower_off > bi * OZ_M + OZ_M - 1) continue;  // above the diagonal
         if (out) out[n] = make_int4(e, bi, bj, 0);
         ++n;
       }
@@ -1044,7 +1044,8 @@ int oz_upd_tile_table(const OzDesc* descs, int count, int flags, int4* out) {
 }
 
 cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int total_tiles,
-                             double alpha, double beta, int flags, unsigned* status, cudaStream_t st) {
+                             double alpha, double beta, int flags, unsigned* status, cudaStream_t st,
+                             int max_grid) {
   if (count <= 0 || total_tiles <= 0) return cudaSuccess;
   static int sms = 0;
   if (!sms) {
@@ -1061,7 +1062,8 @@ cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int 
     set((const void*)k_ozaki_upd<2, false>); set((const void*)k_ozaki_upd<2, true>);
     if (e != cudaSuccess) return e;
   }
-  const int grid = total_tiles < sms ? total_tiles : sms;
+  int grid = total_tiles < sms ? total_tiles : sms;
+  if (max_grid > 0 && grid > max_grid) grid = max_grid;  // SMs left to a concurrent stream
   const bool unit = alpha == 1.0 || alpha == -1.0;
   const int mode = (beta == 0.0 && unit) ? 0 : (beta == 1.0 && unit) ? 1 : 2;
   const bool ident = (flags & GEMM_ADD_IDENTITY) != 0;
