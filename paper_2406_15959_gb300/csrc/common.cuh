@@ -168,8 +168,12 @@ cudaError_t launch_chol_bwd_all(const double* L, int ld, int n, const double* Li
                                 unsigned* status, cudaStream_t st);
 // Inverses of every CHOL_NB diagonal block of the factor L (in S), column-major, ld CHOL_NB.
 cudaError_t launch_tri_inv(const double* S, int ld, int n, double* inv, cudaStream_t st);
-// L21 = A21 L11^{-T} by substitution for rows k+nb .. row_end-1 (16 rows per block).
-cudaError_t launch_trsm_chol_rows(double* S, int ld, int k, int nb, int row_end, cudaStream_t st);
+// L21 = A21 L11^{-T} by substitution for rows k+nb .. row_end-1 (16 rows per block).  With
+// tA non-NULL it also writes L21's digit split for the SYRK: planes tA (128-row tiles) and
+// tB (32-row tiles), row exponents eA and eB (K = nb).
+cudaError_t launch_trsm_chol_rows(double* S, int ld, int k, int nb, int row_end, cudaStream_t st,
+                                  void* tA = nullptr, void* tB = nullptr, int* eA = nullptr,
+                                  int* eB = nullptr);
 // row_end < 0 means n; j_begin 0 means all rows above the block; Linv (nullable) is the
 // inverse of the diagonal block (CHOL_NB x CHOL_NB, column-major) when it is stored.
 cudaError_t launch_chol_fwd(const double* L, int ld, int n, int k, int nb, double* r,

@@ -107,6 +107,8 @@ struct elm_ddm_handle {
   // Cholesky look-ahead (tensor-core back end): the SYRK of block step k beyond the next
   // block column runs on st2 while st factors that column; evS / evB order the two
   int sms = 0;
+  char* creg = nullptr;       // the two parity buffers of L21's digit planes and exponents
+  size_t creg_c1 = 0, creg_c2 = 0, creg_ce = 0;
   cudaStream_t st2 = nullptr;
   cudaEvent_t evS = nullptr, evB = nullptr;
   int N = 0, n = 0, m_max = 0, ld = 0, ncap = 0, mgmax = 0, mgld = 0, ng = 0, nblk = 0;
@@ -632,6 +634,10 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     return (char*)h->sp_buf + (size_t)s * per_sub + off;
   };
   char* chol_region = (char*)h->sp_buf + per_sub * N;
+  h->creg = chol_region;
+  h->creg_c1 = c1;
+  h->creg_c2 = c2;
+  h->creg_ce = ce;
 
   // ---- geometry tables ----
   std::vector<int> dofmap((size_t)ng * 4), ifc((size_t)N * h->mgld, -1);
@@ -980,10 +986,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
         char* reg = chol_region + (size_t)(step & 1) * (c1 + c2 + 2 * ce);
         int* xa = (int*)(reg + c1 + c2);
         int* xb = (int*)(reg + c1 + c2 + ce);
-        // the panel solve L21 = A21 L11^{-T} runs by substitution (launch_trsm_chol_rows)
-        std::vector<SplitDesc> sp{{L21, 1, ng, rest, nb, xa, reg, 128},
-                                  {L21, 1, ng, rest, nb, xb, reg + c1, 32}};
-        add_split_rec(h->syrk_recs, sp, "split_syrk");
+        // the panel solve L21 = A21 L11^{-T} (launch_trsm_chol_rows) writes L21's split:
+        // planes reg (128-row tiles), reg + c1 (32-row tiles), exponents xa, xb
         // SYRK A22 -= L21 L21^T in two parts: A, the next block column (what the next
         // step's factor and panel solve need), on the main stream; B, the columns beyond,
         // on the second stream (B operand rows and C columns offset by nb2)
@@ -1129,8 +1133,9 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     h->has_sdinv = true;
     // Look-ahead (tensor-core back end): part B of step k's SYRK (columns beyond the next
     // block column) runs on st2 while st factors and solves that column.  st2 starts B
-    // after st's split of step k (evS); st waits for B(k - 1) (evB) before its part A(k),
-    // the first launch that touches B(k - 1)'s columns.
+    // after st's panel solve of step k, which writes the split operands (evS); st waits
+    // for B(k - 1) (evB) before its part A(k), the first launch that touches B(k - 1)'s
+    // columns.
     bool b_pending = false;
     for (int k = 0, step = 0; k < h->ng; k += CHOL_NB, ++step) {
       const int nb = std::min(CHOL_NB, h->ng - k);
@@ -1138,19 +1143,28 @@ int elm_ddm_schur(elm_ddm_handle* h) {
       const int rend = h->chol_rend[step];
       ELM_LAUNCH_F(h, launch_potrf_diag(h->S, h->ng, k, nb, h->status, h->st), "potrf",
                    nb * nb * (double)nb / 3.0);
-      if (rend - k - nb > 0)
-        ELM_LAUNCH_F(h, launch_trsm_chol_rows(h->S, h->ng, k, nb, rend, h->st), "trsm_rows",
-                     (double)(rend - k - nb) * nb * nb);
+      if (rend - k - nb > 0) {
+        void *tA = nullptr, *tB = nullptr;
+        int *eA = nullptr, *eB = nullptr;
+        if (h->emulated) {  // this step's parity buffer (see the look-ahead below)
+          char* reg = h->creg + (size_t)(step & 1) * (h->creg_c1 + h->creg_c2 + 2 * h->creg_ce);
+          tA = reg;
+          tB = reg + h->creg_c1;
+          eA = (int*)(reg + h->creg_c1 + h->creg_c2);
+          eB = (int*)(reg + h->creg_c1 + h->creg_c2 + h->creg_ce);
+        }
+        ELM_LAUNCH_F(h, launch_trsm_chol_rows(h->S, h->ng, k, nb, rend, h->st, tA, tB, eA, eB),
+                     "trsm_rows", (double)(rend - k - nb) * nb * nb);
+      }
       if (rend - k - nb > 0) {
         const int r0 = h->syrk_first[step], nr = h->syrk_first[step + 1] - r0;
         if (!h->emulated) {
           rc = run_recs(h, h->syrk_recs, r0, nr, "gemm_syrk");
           if (rc) return rc;
         } else {
-          // records: split, part A, part B (when there are columns beyond the next block)
-          const bool has_b = nr == 3 && h->syrk_recs[r0 + 2].side;
-          rc = run_recs(h, h->syrk_recs, r0, 1, "split_syrk");
-          if (rc) return rc;
+          // records: part A, part B (when there are columns beyond the next block); the
+          // panel solve above wrote their split operands
+          const bool has_b = nr == 2 && h->syrk_recs[r0 + 1].side;
           cudaError_t e2 = cudaSuccess;
           if (has_b) {
             e2 = cudaEventRecord(h->evS, h->st);
@@ -1159,10 +1173,10 @@ int elm_ddm_schur(elm_ddm_handle* h) {
           if (e2 == cudaSuccess && b_pending) e2 = cudaStreamWaitEvent(h->st, h->evB, 0);
           if (e2 != cudaSuccess) return cuda_fail(h, e2, "schur: look-ahead events");
           b_pending = false;
-          rc = run_recs(h, h->syrk_recs, r0 + 1, 1, "oz_syrk");
+          rc = run_recs(h, h->syrk_recs, r0, 1, "oz_syrk");
           if (rc) return rc;
           if (has_b) {
-            rc = run_recs(h, h->syrk_recs, r0 + 2, 1, "oz_syrk_b");
+            rc = run_recs(h, h->syrk_recs, r0 + 1, 1, "oz_syrk_b");
             if (rc) return rc;
             e2 = cudaEventRecord(h->evB, h->st2);
             if (e2 != cudaSuccess) return cuda_fail(h, e2, "schur: look-ahead events");

@@ -2,6 +2,9 @@
 // (the paper states the system is SPD), and the blocked triangular solves that give
 // u_Gamma.  The trailing SYRK update of the factorisation goes through launch_gemm.
 #include "common.cuh"
+#include "digits.cuh"
+
+#include <cuda_bf16.h>
 
 namespace elmddm {
 
@@ -129,9 +132,15 @@ __global__ void __launch_bounds__(NB) k_tri_inv(const double* __restrict__ S, in
 // independent FMAs instead of one long dependent chain.  Same operations as the
 // unblocked solve up to summation order, hence its backward stability.  TRC_ROWS rows per
 // block keep about one block per SM on the envelopes of interest.
+//
+// With split outputs (tensor-core back end) the block also writes the finished rows as
+// the SYRK's operands, so no separate split launch follows: each row's largest biased
+// exponent (the 8 threads of a row reduce it) into eA and eB, and its 7 digit planes into
+// tA (128-row tiles) and tB (32-row tiles), the layout k_split writes for K = nb.
 constexpr int TRC_ROWS = 16, TRC_THREADS = 128, TRC_BW = 4;
 __global__ void __launch_bounds__(TRC_THREADS) k_trsm_chol_rows(double* __restrict__ S, int ld, int k, int nb,
-                                                                int row_end) {
+                                                                int row_end, void* tA, void* tB, int* eA,
+                                                                int* eB) {
   __shared__ double L[NB][NB + 1];
   __shared__ double X[TRC_ROWS][NB + 1];
   __shared__ double rd[NB];
@@ -174,6 +183,40 @@ __global__ void __launch_bounds__(TRC_THREADS) k_trsm_chol_rows(double* __restri
   for (int e = t; e < TRC_ROWS * NB; e += TRC_THREADS) {
     const int r = e % TRC_ROWS, j = e / TRC_ROWS;
     if (r0 + r < row_end && j < nb) S[(r0 + r) + (size_t)(k + j) * ld] = X[r][j];
+  }
+  if (tA) {  // 128 threads = 16 rows x 8 groups of 8 k
+    static_assert(TRC_THREADS == TRC_ROWS * NB / 8, "one thread per 8 entries of the block's rows");
+    const int r = t >> 3, g8 = t & 7, kc = g8 >> 2, kg = g8 & 3;
+    const int gr = blockIdx.x * TRC_ROWS + r;  // row of L21
+    const bool valid = r0 + r < row_end;
+    double x[8];
+    unsigned em = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      x[j] = X[r][8 * g8 + j];  // zero beyond nb and on rows past the envelope
+      em = max(em, biased_exp(x[j]));
+    }
+    em = max(em, __shfl_xor_sync(0xffffffffu, em, 1));
+    em = max(em, __shfl_xor_sync(0xffffffffu, em, 2));
+    em = max(em, __shfl_xor_sync(0xffffffffu, em, 4));
+    const int nkc = (nb + OZ_KC - 1) / OZ_KC;
+    if (valid && kc < nkc) {
+      uint32_t w[OZ_S][4];
+      split8(x, em, w);
+      __nv_bfloat16* oa = static_cast<__nv_bfloat16*>(tA) + (size_t)((gr >> 7) * nkc + kc) * OZ_S * 128 * OZ_KC;
+      __nv_bfloat16* ob = static_cast<__nv_bfloat16*>(tB) + (size_t)((gr >> 5) * nkc + kc) * OZ_S * 32 * OZ_KC;
+      const int offa = tile_off32(gr & 127, kg * 8), offb = tile_off32(gr & 31, kg * 8);
+#pragma unroll
+      for (int p = 0; p < OZ_S; ++p) {
+        const uint4 v = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+        *reinterpret_cast<uint4*>(oa + (size_t)p * 128 * OZ_KC + offa) = v;
+        *reinterpret_cast<uint4*>(ob + (size_t)p * 32 * OZ_KC + offb) = v;
+      }
+      if (g8 == 0) {
+        eA[gr] = (int)em;
+        eB[gr] = (int)em;
+      }
+    }
   }
 }
 
@@ -475,10 +518,12 @@ cudaError_t launch_tri_inv(const double* S, int ld, int n, double* inv, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_trsm_chol_rows(double* S, int ld, int k, int nb, int row_end, cudaStream_t st) {
+cudaError_t launch_trsm_chol_rows(double* S, int ld, int k, int nb, int row_end, cudaStream_t st,
+                                  void* tA, void* tB, int* eA, int* eB) {
   const int rows = row_end - k - nb;
   if (rows <= 0) return cudaSuccess;
-  k_trsm_chol_rows<<<(rows + TRC_ROWS - 1) / TRC_ROWS, TRC_THREADS, 0, st>>>(S, ld, k, nb, row_end); count_launch();
+  k_trsm_chol_rows<<<(rows + TRC_ROWS - 1) / TRC_ROWS, TRC_THREADS, 0, st>>>(S, ld, k, nb, row_end, tA, tB,
+                                                                            eA, eB); count_launch();
   return cudaGetLastError();
 }
 
