@@ -610,7 +610,6 @@ __global__ void __cluster_dims__(AQ_CL, 1, 1) __launch_bounds__(256)
 // through distributed shared memory (fixed summation order, so every CTA computes the
 // identical reflector and T), with two cluster barriers per column.  Same reflectors,
 // T and R as k_panel_qr; 4x the FP64 throughput per subdomain and no L2 round trips.
-constexpr int PCL = 4;     // CTAs per cluster
 constexpr int PLD = 33;    // shared-memory row stride of the panel chunk (doubles)
 
 // Householder panel of nbe <= 32 columns [k0, k0+nbe) of subdomain s, rows split over a
@@ -623,6 +622,7 @@ constexpr int PLD = 33;    // shared-memory row stride of the panel chunk (doubl
 // which gives the trailing update a_k -= tau v (v^T a_k) and, for l < j, the products
 // v_l^T v_j that build T (compact WY, I - V T V^T).  Rows stay with their threads, so the
 // update needs no barrier before the next column's sums: three barriers per column.
+template <int PCL>
 __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
     k_panel_qr_cl(double* __restrict__ K, long long kstride, int ld, const int* __restrict__ ms_arr,
                   int k0, int nbe, double* __restrict__ tau_out, int n, double* __restrict__ Tout,
@@ -754,19 +754,25 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
 cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
                             int nbe, double* tau, int n, double* T, long long tstride,
                             double* Vp, long long vstride, unsigned* status, cudaStream_t st) {
-  // the cluster variant keeps a quarter of the rows (up to ld - k0) in shared memory
-  const int rows_per = (ld - k0 + PCL - 1) / PCL;
-  const size_t smem = (size_t)rows_per * PLD * sizeof(double);
-  if (smem <= 180 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_panel_qr_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           180 * 1024);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
-    k_panel_qr_cl<<<dim3(PCL, N), 256, smem, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride,
-                                                   Vp, vstride, status); count_launch();
+  // the cluster variant keeps 1/PCL of the rows (up to ld - k0) in shared memory: 4 CTAs
+  // per subdomain, or 8 when a quarter of the rows does not fit
+  const size_t smem4 = (size_t)((ld - k0 + 3) / 4) * PLD * sizeof(double);
+  const size_t smem8 = (size_t)((ld - k0 + 7) / 8) * PLD * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_panel_qr_cl<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         180 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_panel_qr_cl<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (smem4 <= 180 * 1024) {
+    k_panel_qr_cl<4><<<dim3(4, N), 256, smem4, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride,
+                                                     Vp, vstride, status); count_launch();
+  } else if (smem8 <= 180 * 1024) {
+    k_panel_qr_cl<8><<<dim3(8, N), 256, smem8, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride,
+                                                     Vp, vstride, status); count_launch();
   } else {
     k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride, Vp, vstride,
                                   status); count_launch();

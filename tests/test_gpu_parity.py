@@ -35,6 +35,9 @@ CASES = {
                                      source="fourier", source_seed=8, c=0.5, n_test_side=40),
     "5x3_edges70": lambda: wl.build(5, 3, 97, 14, 12, 30, 70, theta="paper", theta_seed=9,
                                     source="fourier", source_seed=9, n_test_side=50),
+    # tall subdomains (3120 rows): the panel factorisation runs on 8-CTA clusters
+    "2x2_tall": lambda: wl.build(2, 2, 100, 60, 50, 40, 40, theta="paper", theta_seed=14,
+                                 source="fourier", source_seed=14, n_test_side=40),
     # Remark 4.2's radial weight density
     "3x3_radial": lambda: wl.build(3, 3, 110, 13, 12, 18, 16, theta="radial", theta_seed=13,
                                    source="sin2pi_exp", n_test_side=50),
