@@ -1,0 +1,239 @@
+"""Batched serving of independent problem instances as one decomposition.
+
+Instances that share the number of neurons per subdomain are solved together: their
+subdomains are stacked into one batch and their interface unknowns numbered one
+instance after another.  No interface unknown couples two instances, so the Schur
+matrix of Eq. (3.5) is block diagonal (one block per instance) and the library's
+reverse Cuthill-McKee envelope keeps every Cholesky step inside its instance's block:
+the batch costs what its instances cost together, but every launch of assemble / schur /
+solve / eval covers all instances at once (one launch sequence instead of one per
+instance).  Instances may mix subdomain grids; the operator is the variable-coefficient
+one whenever any instance has a coefficient (the others get rho = 1, grad rho = 0).
+
+Instances with different neuron counts form separate batches (the kernels take one n_N
+per batch), and so does a batch whose interface would outgrow `max_gamma` unknowns: the
+library stores the Schur matrix densely (n_Gamma^2 doubles, though only each block's
+envelope is computed), so `plan` packs instances into batches under that cap.  This
+module is host-side marshalling only: every step of the solve runs in the library's
+kernels through elm_ddm.Solver.
+"""
+from __future__ import annotations
+
+import dataclasses
+import json
+import time
+
+import numpy as np
+
+from . import elm_ddm as E
+from . import workload as wl
+
+
+@dataclasses.dataclass
+class BatchGeometry:
+    """The stacked decomposition (the attributes elm_ddm.Solver and the oracle read)."""
+    counts: np.ndarray    # int32 [N, 3]
+    xy: np.ndarray        # float64 [N, m_max, 2]
+    nrm: np.ndarray       # float64 [N, m_max, 2]
+    dof: np.ndarray       # int32 [N, m_max], interface unknown of the batch or -1
+    n_gamma: int
+
+    @property
+    def n_sub(self) -> int:
+        return int(self.counts.shape[0])
+
+    @property
+    def m_max(self) -> int:
+        return int(self.xy.shape[1])
+
+
+@dataclasses.dataclass
+class Batch:
+    geom: BatchGeometry
+    n_neurons: int
+    W: np.ndarray                 # [N, n, 2]
+    b: np.ndarray                 # [N, n]
+    rhs: np.ndarray               # [N, m_max]
+    coef_rows: np.ndarray | None  # [N, m_max, 3] or None
+    test_xy: np.ndarray           # [T, 2]
+    test_owner: np.ndarray        # [T], subdomain of the batch
+    sub_off: np.ndarray           # [I + 1]: subdomains of instance i are sub_off[i]:sub_off[i+1]
+    gamma_off: np.ndarray         # [I + 1]: its interface unknowns
+    test_off: np.ndarray          # [I + 1]: its test points
+
+    @property
+    def n_instances(self) -> int:
+        return len(self.sub_off) - 1
+
+
+def combine(workloads) -> Batch:
+    """Stack workload.Workload instances (equal n_neurons) into one Batch."""
+    ws = list(workloads)
+    if not ws:
+        raise ValueError("no instances")
+    n = ws[0].n_neurons
+    if any(w.n_neurons != n for w in ws):
+        raise ValueError("instances of one batch need the same number of neurons per subdomain")
+    m_max = max(w.geom.m_max for w in ws)
+    N = sum(w.geom.n_sub for w in ws)
+    counts = np.zeros((N, 3), np.int32)
+    xy = np.zeros((N, m_max, 2))
+    nrm = np.zeros((N, m_max, 2))
+    dof = np.full((N, m_max), -1, np.int32)
+    rhs = np.zeros((N, m_max))
+    W = np.zeros((N, n, 2))
+    b = np.zeros((N, n))
+    any_coef = any(w.coef_rows is not None for w in ws)
+    coef = np.zeros((N, m_max, 3)) if any_coef else None
+    sub_off, gamma_off, test_off = [0], [0], [0]
+    txy, town = [], []
+    for w in ws:
+        g = w.geom
+        s0, s1 = sub_off[-1], sub_off[-1] + g.n_sub
+        mm = g.m_max
+        counts[s0:s1] = g.counts
+        xy[s0:s1, :mm] = g.xy
+        nrm[s0:s1, :mm] = g.nrm
+        d = np.asarray(g.dof, np.int64)
+        dof[s0:s1, :mm] = np.where(d >= 0, d + gamma_off[-1], -1)
+        rhs[s0:s1, :mm] = w.rhs
+        W[s0:s1] = w.W
+        b[s0:s1] = w.b
+        if any_coef:
+            if w.coef_rows is not None:
+                coef[s0:s1, :mm] = w.coef_rows
+            else:
+                coef[s0:s1, :, 0] = 1.0
+        txy.append(w.test_xy)
+        town.append(np.asarray(w.test_owner, np.int64) + s0)
+        sub_off.append(s1)
+        gamma_off.append(gamma_off[-1] + g.n_gamma)
+        test_off.append(test_off[-1] + len(w.test_xy))
+    geom = BatchGeometry(counts, xy, nrm, dof, int(gamma_off[-1]))
+    return Batch(geom, n, W, b, rhs, coef, np.concatenate(txy), np.concatenate(town).astype(np.int32),
+                 np.array(sub_off), np.array(gamma_off), np.array(test_off))
+
+
+def plan(workloads, max_gamma: int = 32768):
+    """Indices of the instances, grouped into batches: equal n_neurons, and at most
+    max_gamma interface unknowns per batch (an instance larger than that alone)."""
+    by_n = {}
+    for i, w in enumerate(workloads):
+        by_n.setdefault(w.n_neurons, []).append(i)
+    batches = []
+    for n in sorted(by_n):
+        cur, ng = [], 0
+        for i in by_n[n]:
+            g = workloads[i].geom.n_gamma
+            if cur and ng + g > max_gamma:
+                batches.append(cur)
+                cur, ng = [], 0
+            cur.append(i)
+            ng += g
+        if cur:
+            batches.append(cur)
+    return batches
+
+
+def split(batch: Batch, u_gamma=None, c=None, u=None):
+    """Per-instance pieces of batch results: lists of (u_gamma, c, u at its test points)."""
+    out = []
+    for i in range(batch.n_instances):
+        s0, s1 = batch.sub_off[i], batch.sub_off[i + 1]
+        g0, g1 = batch.gamma_off[i], batch.gamma_off[i + 1]
+        t0, t1 = batch.test_off[i], batch.test_off[i + 1]
+        out.append((None if u_gamma is None else u_gamma[g0:g1],
+                    None if c is None else c[s0:s1],
+                    None if u is None else u[t0:t1]))
+    return out
+
+
+class BatchSolver:
+    """One elm_ddm.Solver over a Batch: assemble + schur + solve + eval for all instances."""
+
+    def __init__(self, batch: Batch, stream=None):
+        import torch
+        self.batch = batch
+        op = E.OP_VARCOEF if batch.coef_rows is not None else E.OP_POISSON
+        self.solver = E.Solver(E.GeometryArrays.from_geometry(batch.geom), batch.n_neurons,
+                               stream=stream, op=op)
+        dev = torch.device("cuda")
+        t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), device=dev, dtype=dt)
+        # inputs resident on the device from here on
+        self.W, self.b, self.rhs = t(batch.W), t(batch.b), t(batch.rhs)
+        self.coef = t(batch.coef_rows) if batch.coef_rows is not None else None
+        self.test_xy, self.test_owner = t(batch.test_xy), t(batch.test_owner, torch.int32)
+
+    def run(self):
+        """One full solve of every instance; returns device (u_gamma, c, u at test points)."""
+        s = self.solver
+        if self.coef is not None:
+            s.set_coefficient(self.coef)
+        s.assemble(self.W, self.b)
+        s.schur()
+        ug, c = s.solve(self.rhs)
+        u, _ = s.eval(self.test_xy, self.test_owner, c)
+        return ug, c, u
+
+
+def serving_instances(count: int, neurons=(200,), seed: int = 0):
+    """Seeded instances of the serving workload: -div(a grad u) = f with
+    a = 1 + 0.5 sin(2 pi k . x), k in {1..4}^2, sine-mode f, subdomain grids drawn from
+    {2x2, 4x4, 8x8}, neurons per subdomain drawn from `neurons`, 2 n_N interior points per
+    subdomain and 64 points per edge."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        G = int(rng.choice([2, 4, 8]))
+        n = int(rng.choice(list(neurons)))
+        mi_x = int(np.ceil(np.sqrt(2 * n)))
+        mi_y = int(np.ceil(2 * n / mi_x))
+        s = int(rng.integers(0, 2 ** 31 - 1))
+        out.append(wl.build(G, G, n, mi_x, mi_y, 64, 64, theta="paper", theta_seed=s,
+                            source="fourier", source_seed=s, coef="sine", coef_seed=s,
+                            n_test_side=20, name=f"instance{i}"))
+    return out
+
+
+def _main(argv=None):
+    """Serving measurement: instances per second (device time, CUDA events, inputs
+    resident) of full solves of `--instances` seeded instances, packed into batches."""
+    import argparse
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--neurons", type=int, nargs="+", default=[200])
+    ap.add_argument("--max-gamma", type=int, default=32768)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=4)
+    a = ap.parse_args(argv)
+    t0 = time.perf_counter()
+    inst = serving_instances(a.instances, a.neurons, a.seed)
+    groups = plan(inst, a.max_gamma)
+    solvers = [BatchSolver(combine([inst[i] for i in g])) for g in groups]
+    host_s = time.perf_counter() - t0
+    for _ in range(a.warmup):
+        for bs in solvers:
+            bs.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        for bs in solvers:
+            bs.run()
+    e1.record()
+    torch.cuda.synchronize()
+    for bs in solvers:
+        bs.solver.check()
+    ms = e0.elapsed_time(e1) / a.steps
+    print(json.dumps({"metric": "batched serving (full solves, inputs resident)",
+                      "instances": a.instances, "neurons": a.neurons, "batches": len(solvers),
+                      "subdomains": int(sum(bs.batch.geom.n_sub for bs in solvers)),
+                      "n_gamma": int(sum(bs.batch.geom.n_gamma for bs in solvers)),
+                      "ms_per_round": ms, "instances_per_s": a.instances / (ms * 1e-3),
+                      "host_setup_s": host_s}))
+
+
+if __name__ == "__main__":
+    _main()

@@ -1,0 +1,73 @@
+"""Batched serving (paper_2406_15959_gb300/batch.py): independent instances stacked
+into one decomposition.
+
+CPU pins of the stacking itself: the oracle's solution of the stacked decomposition
+equals the oracle's per-instance solutions (the Schur matrix of Eq. (3.5) is block
+diagonal across instances, so the interface values and the fitted functions must agree
+to rounding), every interface unknown of the batch keeps exactly two owning
+subdomains, and the batch plan respects the neuron-count grouping and the interface cap.
+"""
+import numpy as np
+import pytest
+
+from oracle import elm_oracle as O
+from paper_2406_15959_gb300 import batch as B
+from paper_2406_15959_gb300 import workload as wl
+
+
+def instances():
+    return [
+        wl.build(2, 2, 30, 7, 6, 8, 8, theta="paper", theta_seed=31, source="fourier",
+                 source_seed=31, n_test_side=12),
+        wl.build(3, 2, 30, 6, 6, 7, 6, theta="paper", theta_seed=32, source="sinsin", coef="sine",
+                 coef_seed=32, n_test_side=12),
+        wl.build(2, 2, 30, 6, 7, 9, 7, theta="paper", theta_seed=33, source="sin2pi_exp",
+                 n_test_side=12),
+    ]
+
+
+def solve_oracle(geom, W, b, rhs, coef, txy, town):
+    res = O.solve(geom, W, b, rhs, coef=coef)
+    u, _ = O.evaluate(W, b, res.c, txy, town)
+    return res, u
+
+
+def test_stacked_oracle_equals_per_instance_oracle():
+    ws = instances()
+    bt = B.combine(ws)
+    assert bt.coef_rows is not None  # one instance has a coefficient: the batch uses the flux form
+    res, u = solve_oracle(bt.geom, bt.W, bt.b, bt.rhs, bt.coef_rows, bt.test_xy, bt.test_owner)
+    for w, (ug_b, c_b, u_b) in zip(ws, B.split(bt, res.u_gamma, res.c, u)):
+        r1, u1 = solve_oracle(w.geom, w.W, w.b, w.rhs, w.coef_rows, w.test_xy, w.test_owner)
+        assert np.linalg.norm(ug_b - r1.u_gamma) <= 1e-10 * np.linalg.norm(r1.u_gamma)
+        assert np.linalg.norm(u_b - u1) <= 1e-10 * np.linalg.norm(u1)
+
+
+def test_stacked_interface_map_has_two_owners_per_unknown():
+    bt = B.combine(instances())
+    g = bt.geom
+    owners = [set() for _ in range(g.n_gamma)]
+    for s in range(g.n_sub):
+        mi, mb, mg = (int(v) for v in g.counts[s])
+        for d in g.dof[s, mi + mb:mi + mb + mg]:
+            owners[int(d)].add(s)
+        assert np.all(g.dof[s, :mi + mb] == -1)
+    assert all(len(o) == 2 for o in owners)
+    # the unknowns of instance i are owned by instance i's subdomains only
+    for i in range(bt.n_instances):
+        s0, s1 = bt.sub_off[i], bt.sub_off[i + 1]
+        for d in range(bt.gamma_off[i], bt.gamma_off[i + 1]):
+            assert all(s0 <= s < s1 for s in owners[d])
+
+
+def test_plan_groups_by_neurons_and_caps_the_interface():
+    ws = B.serving_instances(12, (20, 30), seed=7)
+    groups = B.plan(ws, max_gamma=700)
+    assert sorted(i for g in groups for i in g) == list(range(12))
+    for g in groups:
+        assert len({ws[i].n_neurons for i in g}) == 1
+        ng = sum(ws[i].geom.n_gamma for i in g)
+        assert ng <= 700 or len(g) == 1
+    with pytest.raises(ValueError):
+        B.combine([ws[i] for i in range(12) if ws[i].n_neurons == 20][:1] +
+                  [ws[i] for i in range(12) if ws[i].n_neurons == 30][:1])

@@ -1,0 +1,42 @@
+"""Batched serving on the GPU: the stacked instances solved in one launch sequence agree
+with the oracle's per-instance solutions (relative L2 <= 1e-8 at each instance's test
+points, the parity bound of the single-instance path)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import elm_oracle as O
+from paper_2406_15959_gb300 import batch as B
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from tests.test_batch import instances  # noqa: E402
+
+
+def test_batched_solve_matches_per_instance_oracle():
+    ws = instances()
+    bt = B.combine(ws)
+    bs = B.BatchSolver(bt)
+    ug, c, u = bs.run()
+    bs.solver.check()
+    ug, c, u = ug.cpu().numpy(), c.cpu().numpy(), u.cpu().numpy()
+    for w, (ug_b, _, u_b) in zip(ws, B.split(bt, ug, c, u)):
+        res = O.solve(w.geom, w.W, w.b, w.rhs, coef=w.coef_rows)
+        u1, _ = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
+        assert np.linalg.norm(u_b - u1) <= 1e-8 * np.linalg.norm(u1)
+        assert np.linalg.norm(ug_b - res.u_gamma) <= 1e-8 * np.linalg.norm(res.u_gamma)
+
+
+def test_serving_plan_runs_every_batch():
+    ws = B.serving_instances(6, (40,), seed=3)
+    groups = B.plan(ws, max_gamma=1200)
+    for g in groups:
+        bt = B.combine([ws[i] for i in g])
+        bs = B.BatchSolver(bt)
+        _, _, u = bs.run()
+        bs.solver.check()
+        assert torch.isfinite(u).all()
