@@ -149,14 +149,17 @@ def split(batch: Batch, u_gamma=None, c=None, u=None):
 
 
 class BatchSolver:
-    """One elm_ddm.Solver over a Batch: assemble + schur + solve + eval for all instances."""
+    """One elm_ddm.Solver over a Batch: assemble + schur + solve + eval for all instances,
+    on its own CUDA stream (a new one unless given), so that several batches submitted one
+    after another run concurrently on the GPU."""
 
     def __init__(self, batch: Batch, stream=None):
         import torch
         self.batch = batch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
         op = E.OP_VARCOEF if batch.coef_rows is not None else E.OP_POISSON
         self.solver = E.Solver(E.GeometryArrays.from_geometry(batch.geom), batch.n_neurons,
-                               stream=stream, op=op)
+                               stream=self.stream, op=op)
         dev = torch.device("cuda")
         t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), device=dev, dtype=dt)
         # inputs resident on the device from here on
@@ -165,15 +168,34 @@ class BatchSolver:
         self.test_xy, self.test_owner = t(batch.test_xy), t(batch.test_owner, torch.int32)
 
     def run(self):
-        """One full solve of every instance; returns device (u_gamma, c, u at test points)."""
+        """One full solve of every instance, enqueued on this batch's stream; returns
+        device (u_gamma, c, u at test points), valid once that stream has run."""
+        import torch
         s = self.solver
-        if self.coef is not None:
-            s.set_coefficient(self.coef)
-        s.assemble(self.W, self.b)
-        s.schur()
-        ug, c = s.solve(self.rhs)
-        u, _ = s.eval(self.test_xy, self.test_owner, c)
+        with torch.cuda.stream(self.stream):  # outputs are allocated for this stream
+            if self.coef is not None:
+                s.set_coefficient(self.coef)
+            s.assemble(self.W, self.b)
+            s.schur()
+            ug, c = s.solve(self.rhs)
+            u, _ = s.eval(self.test_xy, self.test_owner, c)
         return ug, c, u
+
+    def capture(self):
+        """Record run() once as a CUDA graph (every entry point is stream-ordered, with no
+        allocation and no host synchronisation after setup); replay() then submits the
+        whole solve as one graph launch.  Returns the graph's output tensors."""
+        import torch
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            self.graph_out = self.run()
+        return self.graph_out
+
+    def replay(self):
+        import torch
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
+        return self.graph_out
 
 
 def serving_instances(count: int, neurons=(200,), seed: int = 0):
@@ -196,8 +218,9 @@ def serving_instances(count: int, neurons=(200,), seed: int = 0):
 
 
 def _main(argv=None):
-    """Serving measurement: instances per second (device time, CUDA events, inputs
-    resident) of full solves of `--instances` seeded instances, packed into batches."""
+    """Serving measurement: instances per second of full solves of `--instances` seeded
+    instances packed into batches, every batch on its own stream (wall clock around
+    synchronised rounds, inputs resident)."""
     import argparse
     import torch
     ap = argparse.ArgumentParser()
@@ -207,6 +230,7 @@ def _main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--graphs", action="store_true", help="replay one CUDA graph per batch")
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
     inst = serving_instances(a.instances, a.neurons, a.seed)
@@ -217,21 +241,31 @@ def _main(argv=None):
         for bs in solvers:
             bs.run()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    same = None
+    if a.graphs:
+        eager = [bs.run()[2].clone() for bs in solvers]
+        torch.cuda.synchronize()
+        for bs in solvers:
+            bs.capture()
+        for bs in solvers:
+            bs.replay()
+        torch.cuda.synchronize()
+        same = all(torch.equal(e, bs.graph_out[2]) for e, bs in zip(eager, solvers))
+    step = (lambda bs: bs.replay()) if a.graphs else (lambda bs: bs.run())
+    t1 = time.perf_counter()
     for _ in range(a.steps):
         for bs in solvers:
-            bs.run()
-    e1.record()
-    torch.cuda.synchronize()
+            step(bs)
+        torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t1) / a.steps
     for bs in solvers:
         bs.solver.check()
-    ms = e0.elapsed_time(e1) / a.steps
-    print(json.dumps({"metric": "batched serving (full solves, inputs resident)",
+    print(json.dumps({"metric": "batched serving (full solves, inputs resident, wall clock)",
                       "instances": a.instances, "neurons": a.neurons, "batches": len(solvers),
                       "subdomains": int(sum(bs.batch.geom.n_sub for bs in solvers)),
                       "n_gamma": int(sum(bs.batch.geom.n_gamma for bs in solvers)),
                       "ms_per_round": ms, "instances_per_s": a.instances / (ms * 1e-3),
+                      "cuda_graphs": a.graphs, "graph_equals_eager": same,
                       "host_setup_s": host_s}))
 
 
