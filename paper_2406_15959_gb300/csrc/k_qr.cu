@@ -626,11 +626,12 @@ template <int PCL>
 __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
     k_panel_qr_cl(double* __restrict__ K, long long kstride, int ld, const int* __restrict__ ms_arr,
                   int k0, int nbe, double* __restrict__ tau_out, int n, double* __restrict__ Tout,
-                  long long tstride, double* __restrict__ Vp, long long vstride, unsigned* status) {
+                  long long tstride, double* __restrict__ Vp, long long vstride, unsigned* status,
+                  int s_off) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int q = (int)cluster.block_rank();
-  const int s = blockIdx.y;
+  const int s = s_off + blockIdx.y;
   double* A = K + (size_t)s * kstride;
   const int m = ms_arr[s];
   const int mp = m - k0;
@@ -755,7 +756,9 @@ cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms,
                             int nbe, double* tau, int n, double* T, long long tstride,
                             double* Vp, long long vstride, unsigned* status, cudaStream_t st) {
   // the cluster variant keeps 1/PCL of the rows (up to ld - k0) in shared memory: 4 CTAs
-  // per subdomain, or 8 when a quarter of the rows does not fit
+  // per subdomain, or 8 when a quarter of the rows does not fit.  (Splitting the launch
+  // into a full wave of 4-CTA clusters and a remainder of 5-CTA clusters measured slower:
+  // a cluster has to fit in one GPC, so fewer clusters run at once than SMs / size.)
   const size_t smem4 = (size_t)((ld - k0 + 3) / 4) * PLD * sizeof(double);
   const size_t smem8 = (size_t)((ld - k0 + 7) / 8) * PLD * sizeof(double);
   static bool attr = false;
@@ -769,10 +772,10 @@ cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms,
   }
   if (smem4 <= 180 * 1024) {
     k_panel_qr_cl<4><<<dim3(4, N), 256, smem4, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride,
-                                                     Vp, vstride, status); count_launch();
+                                                     Vp, vstride, status, 0); count_launch();
   } else if (smem8 <= 180 * 1024) {
     k_panel_qr_cl<8><<<dim3(8, N), 256, smem8, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride,
-                                                     Vp, vstride, status); count_launch();
+                                                     Vp, vstride, status, 0); count_launch();
   } else {
     k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride, Vp, vstride,
                                   status); count_launch();
