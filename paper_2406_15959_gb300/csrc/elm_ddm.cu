@@ -614,7 +614,11 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const size_t s7 = al(oz_split_elems(mgm, n, 128) * 2), e7 = al((size_t)mgm * 4);
   // Y = A R^{-1} updates: the 64-row block of R to the right of the diagonal (Y_b reuses s7)
   const size_t s8 = al(oz_split_elems(n, 64, 32) * 2), e8 = al((size_t)n * 4);
-  const size_t per_sub = s1 + e1 + s2 + e2 + s3 + e3 + s4 + e4 + s5 + e5 + s6 + e6 + s7 + e7 + s8 + e8;
+  // W2^T = W1^T T per QR panel: W1^T (rows = trailing columns) and T^T
+  const size_t s9 = al(oz_split_elems(n2max, QR_NB, 128) * 2), e9 = al((size_t)n2max * 4);
+  const size_t s10 = al(oz_split_elems(QR_NB, QR_NB, 32) * 2), e10 = al((size_t)QR_NB * 4);
+  const size_t per_sub = s1 + e1 + s2 + e2 + s3 + e3 + s4 + e4 + s5 + e5 + s6 + e6 + s7 + e7 + s8 + e8 +
+                         s9 + e9 + s10 + e10;
   const size_t c1 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 128) * 2);
   const size_t c2 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 32) * 2);
   const size_t ce = al((size_t)std::max(restmax, 1) * 4);
@@ -628,7 +632,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     h->sp_buf = base;
   }
   auto sub_region = [&](int s, int which) -> char* {
-    const size_t sz[16] = {s1, e1, s2, e2, s3, e3, s4, e4, s5, e5, s6, e6, s7, e7, s8, e8};
+    const size_t sz[20] = {s1, e1, s2, e2, s3, e3, s4, e4, s5, e5, s6, e6, s7, e7, s8, e8, s9, e9, s10, e10};
     size_t off = 0;
     for (int i = 0; i < which; ++i) off += sz[i];
     return (char*)h->sp_buf + (size_t)s * per_sub + off;
@@ -756,8 +760,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     h->panel_flops.push_back(pf);
     h->panel_bytes.push_back(pb);
     std::vector<GemmDesc> g1, g2, g3;
-    std::vector<SplitDesc> sp1, sp3;
-    std::vector<OzDesc> o1, o3;
+    std::vector<SplitDesc> sp1, sp3, spt;
+    std::vector<OzDesc> o1, o3, ot;
     for (int s = 0; s < N; ++s) {
       const int n2 = n + h->mg_h[s] - (k0 + nbe), mp = h->ms_h[s] - k0;
       if (n2 <= 0 || mp <= 0) continue;
@@ -779,7 +783,14 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
         sp1.push_back({A2, ld, 1, n2, mp, x1, nullptr, 128});  // A2^T: row exponents only
         sp1.push_back({V, ld, 1, nbe, mp, x2, t2, 32});        // V^T: rows = panel columns
         o1.push_back({A2, x1, t2, x2, w1, QR_NB, 1, n2, nbe, mp, 0, ld});
-        sp3.push_back({V, 1, ld, mp, nbe, x3, t3, 128});     // V: rows = matrix rows
+        void* t9 = sub_region(s, 16); int* x9 = (int*)sub_region(s, 17);
+        void* t10 = sub_region(s, 18); int* x10 = (int*)sub_region(s, 19);
+        // W2^T = W1^T T as a tensor-core product: A = W1^T (row j = trailing column j,
+        // 32 contiguous values), B = T^T (row i = column i of the column-major T)
+        spt.push_back({w1, QR_NB, 1, n2, nbe, x9, t9, 128});
+        spt.push_back({Tb, QR_NB, 1, nbe, nbe, x10, t10, 32});
+        spt.push_back({V, 1, ld, mp, nbe, x3, t3, 128});     // V: rows = matrix rows
+        ot.push_back({t9, x9, t10, x10, w2, QR_NB, 1, n2, nbe, nbe, 0});
         sp3.push_back({w2, QR_NB, 1, n2, nbe, x4, t4, 32});  // W2^T: rows = trailing columns
         o3.push_back({t3, x3, t4, x4, A2, 1, ld, mp, n2, nbe, 0});
       }
@@ -788,8 +799,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     if (h->emulated) {
       add_split_rec(h->qr_recs, sp1, "split_qr_w");
       add_fa_rec(h->qr_recs, o1, "oz_qr_w");
-      add_gemm_rec(h->qr_recs, g2, true, false, 1.0, 0.0, 0);
-      h->qr_recs.back().name = "gemm_qr_t";
+      add_split_rec(h->qr_recs, spt, "split_qr_t");
+      add_oz_rec(h->qr_recs, ot, 0, 1.0, 0.0, 0, "oz_qr_t");
       add_split_rec(h->qr_recs, sp3, "split_qr_update");
       add_oz_rec(h->qr_recs, o3, 0, -1.0, 1.0, 0, "oz_qr_update");
     } else {
