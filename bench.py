@@ -58,9 +58,9 @@ KERNEL_OF_CLASS = {
 # launch's algorithmic bytes; traffic scales with the units a launch processes, so the
 # bench's per-launch traffic is this ratio times its per-launch algorithmic bytes.
 TRAFFIC_PER_ALGO_BYTE = {
-    # first QR panel: 9.876 MB read + 256 B written (the panel stays in L2) for
+    # first QR panel: 9.880 MB read + 0 B written (the panel stays in L2) for
     # 16 x 2400 x 32 x 8 B read and written once (19.66 MB)
-    "panel_qr": (9.875712e6 / 19.6608e6, "profiles/k_panel_qr_cl_poisson_4x4_n1000.md"),
+    "panel_qr": (9.880320e6 / 19.6608e6, "profiles/k_panel_qr_cl_poisson_4x4_n1000.md"),
     # first QR update A2 -= V W2: 745.95 MB for 855.9 MB (C read + written, V and W2 once)
     "oz_qr_update": (745.953536e6 / 855.90e6, "profiles/k_ozaki_upd_poisson_4x4_n1000.md"),
     # first W1^T = A2^T V: 410.99 MB for 435.7 MB (A2, V, W1 once)
