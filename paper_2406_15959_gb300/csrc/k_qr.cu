@@ -245,67 +245,9 @@ __global__ void k_load_rhs(double* __restrict__ X, const double* __restrict__ rh
   X[((size_t)rh * N + s) * ld + row] = v;
 }
 
-// x <- Q^T x for one subdomain and one right-hand side, panel by panel.
-__global__ void __launch_bounds__(256) k_apply_qt(double* __restrict__ X, const double* __restrict__ K,
-                                                  long long kstride, int ld,
-                                                  const int* __restrict__ ms_arr, int N, int n,
-                                                  const double* __restrict__ Tb, long long tstride) {
-  const int s = blockIdx.x, rh = blockIdx.y;
-  const int m = ms_arr[s];
-  double* x = X + ((size_t)rh * N + s) * ld;
-  const double* A = K + (size_t)s * kstride;
-  const double* Ts = Tb + (size_t)s * tstride;
-  __shared__ double wred[8][32];
-  __shared__ double w[32], w2[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int k0 = 0; k0 < n; k0 += 32) {
-    const int nbe = min(32, n - k0);
-    double acc[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
-    for (int r = k0 + tid; r < m; r += 256) {
-      const double xr = x[r];
-      const double* row = A + r + (size_t)k0 * ld;
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        if (k < nbe) {
-          if (r > k0 + k) acc[k] = fma(row[(size_t)k * ld], xr, acc[k]);
-          else if (r == k0 + k) acc[k] += xr;
-        }
-      }
-    }
-    const double ws = warp_transpose_sum32(acc);
-    wred[warp][lane] = ws;
-    __syncthreads();
-    if (tid < 32) {
-      double t = 0.0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) t += wred[q][tid];
-      w[tid] = tid < nbe ? t : 0.0;
-    }
-    __syncthreads();
-    if (tid < 32) {
-      const double* Tk = Ts + (size_t)(k0 / 32) * 1024;
-      double t = 0.0;
-      for (int i = 0; i <= tid; ++i) t = fma(Tk[i + 32 * tid], w[i], t);
-      w2[tid] = t;
-    }
-    __syncthreads();
-    for (int r = k0 + tid; r < m; r += 256) {
-      double xr = x[r];
-      const double* row = A + r + (size_t)k0 * ld;
-      for (int k = 0; k < nbe; ++k) {
-        const double v = r > k0 + k ? row[(size_t)k * ld] : (r == k0 + k ? 1.0 : 0.0);
-        xr = fma(-v, w2[k], xr);
-      }
-      x[r] = xr;
-    }
-    __syncthreads();
-  }
-}
-
-// x <- Q^T x as k_apply_qt, with a cluster of AQ_CL CTAs per (subdomain, right-hand side)
-// so that every SM's FP64 pipe takes part (one CTA per subdomain left most SMs idle).
+// x <- Q^T x for each subdomain and right-hand side, panel by panel (x -= V T^T V^T x),
+// with a cluster of AQ_CL CTAs per (subdomain, right-hand side) so that every SM's FP64
+// pipe takes part (one CTA per subdomain left most SMs idle).
 // The 32-row groups of x are dealt round-robin to the CTAs (group g to CTA g % AQ_CL),
 // which keeps the shrinking active rows (r >= k0) balanced; each row stays with one
 // thread for both phases of a panel, so x needs no synchronisation.  Per panel: the
