@@ -1,7 +1,7 @@
 """Learned interface warm start: an MLP maps the coefficients a of a source
 f = sum a_kl sin(k pi x) sin(l pi y) to the interface variable u_Gamma of Eq. (3.5), and
 its prediction starts the (Jacobi-preconditioned) CG interface solve; the direct solve
-of the same handle is the fallback and the judge of the error.
+of the same handle is the fallback and the reference for the error.
 
 The training set is generated by the method itself: one factorisation, then batches of
 right-hand sides through the direct solve.  Network, loss and Adam run in the library's

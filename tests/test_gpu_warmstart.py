@@ -1,7 +1,7 @@
 """The learned interface warm start on the GPU: the network's forward pass, loss gradient
 and Adam step against the FP64 oracle (oracle/mlp_oracle.py, itself pinned by finite
 differences), and the gain of the trained network as the initial guess of the CG
-interface solve, with the direct solve as the judge of the error.
+interface solve, with the direct solve as the reference for the error.
 
 Tolerances: the library computes in FP32.  A forward value or gradient entry is a sum of
 at most a few hundred FP32 products (relative rounding <= K * 2^-24 ~ 3e-5 for K = 512),
