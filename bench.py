@@ -193,6 +193,19 @@ def cpu_cores():
     return os.cpu_count()
 
 
+def workload_config(args, w, ws):
+    """The `config` object of both arms' JSON lines for workload w."""
+    n = w.n_neurons
+    mg = int(w.geom.counts[:, 2].max())
+    k_gb = w.geom.n_sub * int(w.geom.counts[0].sum()) * (n + mg) * 8 / 1e9
+    return {"workload": args.workload, "subdomains": f"{w.geom.gx}x{w.geom.gy}",
+            "neurons_per_subdomain": n, "rows_per_subdomain": int(w.geom.counts[0].sum()),
+            "n_gamma": w.geom.n_gamma, "test_points": len(w.test_xy), "parallelism": f"replicas{ws}",
+            "l2_flush": f"inputs larger than L2 (K alone is {k_gb:.1f} GB per step)",
+            "schur_solver": ("cg (unpreconditioned, relative residual 1e-9, matrix-free S)"
+                             if args.schur_solver == "cg" else "direct (envelope Cholesky)")}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -213,7 +226,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "l2_flush": "inputs larger than L2"},
+            "config": workload_config(args, w, ws),
             "cpu_baseline": {"value": 1.0 / sec, "unit": "solves/s", "cores": cpu_cores(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": 1.0 / sec, "unit": "solves/s", "h2d_bytes_per_step": 0,
@@ -398,12 +411,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "subdomains": f"{w.geom.gx}x{w.geom.gy}", "neurons_per_subdomain": n,
-                   "rows_per_subdomain": int(w.geom.counts[0].sum()), "n_gamma": w.geom.n_gamma,
-                   "test_points": len(w.test_xy), "parallelism": f"replicas{ws}",
-                   "l2_flush": "inputs larger than L2 (K alone is 1.7 GB per step)",
-                   "schur_solver": ("cg (unpreconditioned, relative residual 1e-9, matrix-free S)"
-                                    if cg else "direct (envelope Cholesky)")},
+        "config": workload_config(args, w, ws),
         "rel_l2_vs_oracle": l2_oracle, "rel_l2_vs_exact": l2_exact,
         "e2e": {"value": R.job_throughput(ms_e2e, ws), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
