@@ -58,13 +58,14 @@ KERNEL_OF_CLASS = {
 # launch's algorithmic bytes; traffic scales with the units a launch processes, so the
 # bench's per-launch traffic is this ratio times its per-launch algorithmic bytes.
 TRAFFIC_PER_ALGO_BYTE = {
+    # class: (DRAM bytes of the captured launch, its algorithmic bytes, summary)
     # first QR panel: 9.880 MB read + 0 B written (the panel stays in L2) for
-    # 16 x 2400 x 32 x 8 B read and written once (19.66 MB)
-    "panel_qr": (9.880320e6 / 19.6608e6, "profiles/k_panel_qr_cl_poisson_4x4_n1000.md"),
-    # first QR update A2 -= V W2: 745.95 MB for 855.9 MB (C read + written, V and W2 once)
-    "oz_qr_update": (745.953536e6 / 855.90e6, "profiles/k_ozaki_upd_poisson_4x4_n1000.md"),
-    # first W1^T = A2^T V: 410.99 MB for 435.7 MB (A2, V, W1 once)
-    "oz_qr_w": (410.991872e6 / 435.69e6, "profiles/k_ozaki_fa_poisson_4x4_n1000.md"),
+    # 16 x 2400 x 32 x 8 B read and written once
+    "panel_qr": (9.880320e6, 19.6608e6, "profiles/k_panel_qr_cl_poisson_4x4_n1000.md"),
+    # first QR update A2 -= V W2: C read + written, V and W2 once
+    "oz_qr_update": (745.953536e6, 855.90e6, "profiles/k_ozaki_upd_poisson_4x4_n1000.md"),
+    # first W1^T = A2^T V: A2, V, W1 once
+    "oz_qr_w": (410.991872e6, 435.69e6, "profiles/k_ozaki_fa_poisson_4x4_n1000.md"),
 }
 
 
@@ -378,11 +379,11 @@ def run_ours(args):
         v = prof[dom]
         roofline = roof(dom, v, v["ms"])
         per_launch_bytes = v["bytes"] / max(v["launches"], 1)
-        ratio = TRAFFIC_PER_ALGO_BYTE.get(dom)
+        cap = TRAFFIC_PER_ALGO_BYTE.get(dom)
         roofline.update({
-            "traffic": (ratio[0] * per_launch_bytes if ratio and per_launch_bytes > 0 else None),
-            "traffic_source": (f"ncu DRAM bytes of the 4x4 workload ({ratio[1]}) scaled by this "
-                               f"launch's algorithmic bytes" if ratio else None),
+            "traffic": (cap[0] / cap[1] * per_launch_bytes if cap and per_launch_bytes > 0 else None),
+            "traffic_source": (f"ncu DRAM bytes of the 4x4 workload ({cap[2]}) scaled by this "
+                               f"launch's algorithmic bytes" if cap else None),
             "kernel_class": dom,
             "kernel": KERNEL_OF_CLASS.get(dom, dom),
             "launches_per_step": v["launches"] // args.steps,
