@@ -211,6 +211,69 @@ def test_evaluation_matches_collocation_rows():
         np.testing.assert_allclose(u, K[rb.start:rg.stop] @ res.c[s], rtol=1e-12, atol=1e-12)
 
 
+def test_evaluated_gradient_matches_central_differences_of_u():
+    """grad u of the oracle's evaluation against central differences of its own u (the
+    u half is pinned by the collocation rows above), at random points of every
+    subdomain, each point kept with its owner.  A wrong sign, a missing (1 - t^2) or the
+    weights applied per component in the wrong order fails this."""
+    w = tiny(gx=2, gy=2, n=9, mi=5, p=4, seed=21)
+    res = O.solve(w.geom, w.W, w.b, w.rhs)
+    g = w.geom
+    rng = np.random.default_rng(4)
+    h = 1e-5
+    for s in range(g.n_sub):
+        x0, x1, y0, y1 = g.box(s)
+        pts = np.stack([rng.uniform(x0, x1, 12), rng.uniform(y0, y1, 12)], axis=1)
+        own = np.full(len(pts), s)
+        _, gr = O.evaluate(w.W, w.b, res.c, pts, own)
+        for d in range(2):
+            e = np.zeros(2)
+            e[d] = h
+            up, _ = O.evaluate(w.W, w.b, res.c, pts + e, own)
+            um, _ = O.evaluate(w.W, w.b, res.c, pts - e, own)
+            fd = (up - um) / (2 * h)
+            np.testing.assert_allclose(gr[:, d], fd, rtol=1e-6, atol=1e-6 * np.abs(fd).max())
+
+
+def test_evaluated_gradient_of_one_neuron_is_the_sech_squared_closed_form():
+    """u = c tanh(w.x + b) has grad u = c w sech^2(w.x + b): one neuron per subdomain,
+    values written out by hand (sech through cosh, not through 1 - tanh^2)."""
+    import math
+    W = np.array([[[1.5, -0.5]], [[-2.0, 0.25]]])
+    b = np.array([[0.3], [-0.1]])
+    c = np.array([[2.0], [-0.75]])
+    pts = np.array([[0.2, 0.7], [0.9, 0.1], [0.5, 0.5]])
+    for s in range(2):
+        u, gr = O.evaluate(W, b, c, pts, np.full(3, s))
+        for i, (x, y) in enumerate(pts):
+            z = W[s, 0, 0] * x + W[s, 0, 1] * y + b[s, 0]
+            sech2 = 1.0 / math.cosh(z) ** 2
+            assert u[i] == pytest.approx(c[s, 0] * math.tanh(z), rel=1e-14)
+            assert gr[i, 0] == pytest.approx(c[s, 0] * W[s, 0, 0] * sech2, rel=1e-13)
+            assert gr[i, 1] == pytest.approx(c[s, 0] * W[s, 0, 1] * sech2, rel=1e-13)
+
+
+def test_relative_h1_error_has_its_closed_form_on_the_test_grid():
+    """Discrete relative L2 / H1 errors (the metric of Table 2) on the cell-centred test
+    grid, where sum_i sin^2(pi x_i) = sum_i cos^2(pi x_i) = n/2 exactly: for
+    u_ex = sin(pi x) sin(pi y), sum u_ex^2 = n^2/4 and sum |grad u_ex|^2 = 2 pi^2 n^2/4.
+    A shift u = u_ex + eps and a gradient error (delta, 0) at every point then give
+    L2 = 2 eps and H1 = 2 sqrt(eps^2 + delta^2) / sqrt(1 + 2 pi^2)."""
+    import math
+    g = wl.make_geometry(2, 2, 3, 3, 3, 3)
+    n = 40
+    xy, _ = wl.test_points(g, n)
+    src = wl.make_source("sinsin")
+    u_ex, g_ex = src.u(xy), src.grad_u(xy)
+    eps, delta = 1e-3, 3e-3
+    l2, h1 = O.rel_errors(u_ex + eps, g_ex + np.array([delta, 0.0]), u_ex, g_ex)
+    assert l2 == pytest.approx(2 * eps, rel=1e-10)
+    assert h1 == pytest.approx(2 * math.sqrt(eps ** 2 + delta ** 2) / math.sqrt(1 + 2 * math.pi ** 2),
+                               rel=1e-10)
+    # exact values and gradients: both errors vanish
+    assert O.rel_errors(u_ex, g_ex, u_ex, g_ex) == (0.0, 0.0)
+
+
 def test_error_falls_with_neurons_and_points():
     """Manufactured solution sin(pi x) sin(pi y): the relative L2 error at the test
     points falls as the networks and the point sets grow (Theorem 2.1, Table 2)."""
@@ -389,6 +452,26 @@ def test_adam_first_step_is_signed_learning_rate():
     g = np.array([0.3, -2.0, 1e-3])
     p1, _, _ = MO.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, 0.01)
     np.testing.assert_allclose(p1, -0.01 * g / (np.abs(g) + 1e-8 / np.sqrt(1 - 0.999)), rtol=1e-12)
+
+
+def test_adam_steps_with_constant_gradient_follow_the_bias_corrected_closed_form():
+    """With a constant gradient g and zero initial moments, m_t = (1 - b1^t) g and
+    v_t = (1 - b2^t) g^2 after t steps, so step t moves a parameter by exactly
+    -lr g / (|g| + eps / sqrt(1 - b2^t)).  The sum over t = 1..5 pins the powers t of
+    the bias correction (a factor b1 * t instead of b1^t flips the second step)."""
+    from oracle import mlp_oracle as MO
+    g = np.array([0.3, -2.0, 1e-3, 5.0])
+    lr, b1, b2, eps = 0.01, 0.9, 0.999, 1e-8
+    p = np.zeros(4)
+    m = np.zeros(4)
+    v = np.zeros(4)
+    expect = np.zeros(4)
+    for t in range(1, 6):
+        p, m, v = MO.adam_step(p, g, m, v, t, lr, b1, b2, eps)
+        expect -= lr * g / (np.abs(g) + eps / np.sqrt(1.0 - b2 ** t))
+        np.testing.assert_allclose(m, (1 - b1 ** t) * g, rtol=1e-13)
+        np.testing.assert_allclose(v, (1 - b2 ** t) * g * g, rtol=1e-12)
+        np.testing.assert_allclose(p, expect, rtol=1e-12)
 
 
 def test_radial_weights_have_density_proportional_to_norm():
