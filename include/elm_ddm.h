@@ -57,6 +57,9 @@ extern "C" {
 #define ELM_DDM_ERR_NOT_SPD   7  /* a Cholesky pivot of the Schur matrix was <= 0 */
 #define ELM_DDM_ERR_CAPACITY  8  /* request larger than a no-allocation entry point's fixed scratch */
 #define ELM_DDM_ERR_NOCONV    9  /* elm_ddm_solve_cg: tolerance not reached (outputs hold the last iterate) */
+#define ELM_DDM_ERR_TIMEOUT  10  /* a bounded device-side wait gave up (see elm_ddm_set_wait_limit);
+                                    the outputs of the affected call are invalid, the handle
+                                    and the CUDA context stay usable */
 
 /* elm_ddm_desc.flags */
 #define ELM_DDM_FLAG_FP64_SIMT 1  /* run every dense update on the FP64 pipe (default: the
@@ -196,8 +199,9 @@ int elm_ddm_eval(elm_ddm_handle* h, int npts, const double* xy, const int32_t* o
 
 /*
  * Synchronises the handle's stream and returns the first failure the kernels
- * recorded since the previous check (ELM_DDM_ERR_NOT_SPD, _RANK, _NONFINITE), a
- * pending CUDA error (ELM_DDM_ERR_CUDA), or ELM_DDM_OK.  Clears the status word.
+ * recorded since the previous check (ELM_DDM_ERR_NONFINITE, _RANK, _NOT_SPD, _TIMEOUT in
+ * that order of precedence), a pending CUDA error (ELM_DDM_ERR_CUDA), or ELM_DDM_OK.
+ * Clears the status word.
  */
 int elm_ddm_check(elm_ddm_handle* h);
 
@@ -211,6 +215,44 @@ int elm_ddm_check(elm_ddm_handle* h);
 #define ELM_DDM_BUF_L 4  /* n_gamma x n_gamma: lower Cholesky factor of S in the internal
                             interface order (elm_ddm_interface_order), after schur; s ignored;
                             the strict upper triangle is unspecified */
+
+/*
+ * Collocation points of the decomposition as the handle holds them (Section 3: the
+ * point sets x^s_i, x^s_b, x^s_Gamma, and the outward normals n_s on Gamma).  The
+ * geometry enters through elm_ddm_setup as explicit point arrays, so any point layout
+ * (the paper's global grid, per-subdomain grids, random points) and any batch of
+ * independent problems can be described; this call returns it in per-kind form.
+ *   kind    ELM_DDM_PTS_INTERIOR, _BOUNDARY, _INTERFACE (points) or _NORMALS (the outward
+ *           normal of every interface point)
+ *   xy      device double [N][kmax][2], kmax = the largest count of that kind over the
+ *           subdomains; row i of subdomain s is its i-th point of the kind (in the order
+ *           of elm_ddm_setup's rows), rows past counts[s] are zero.  May be NULL: only
+ *           the counts are returned.  Written on the handle's stream.
+ *   counts  host int32 [N] (may be NULL): number of points of the kind per subdomain.
+ * Returns ELM_DDM_ERR_ARG for an unknown kind.
+ */
+#define ELM_DDM_PTS_INTERIOR  0
+#define ELM_DDM_PTS_BOUNDARY  1
+#define ELM_DDM_PTS_INTERFACE 2
+#define ELM_DDM_PTS_NORMALS   3
+int elm_ddm_get_points(elm_ddm_handle* h, int kind, double* xy, int32_t* counts);
+
+/*
+ * Limit of the bounded device-side waits of elm_ddm_solve's triangular solves (the grid
+ * barriers between the block steps of the cooperative forward and backward substitution
+ * kernels; the paper has no counterpart: failure detection).  A barrier that has not been
+ * released within `seconds` of wall time makes every block of the kernel record the
+ * timeout and return; elm_ddm_check then reports ELM_DDM_ERR_TIMEOUT and the solve's
+ * outputs are invalid, while the handle stays usable.
+ *   seconds       0 .. 60 (default 2)
+ *   hold_release  0 normally; 1 makes every barrier wait for one arrival more than the
+ *                 kernel's grid supplies, so the wait runs out for certain (a test hook
+ *                 for the timeout path; no asynchronous copy is in flight at these waits)
+ * Applies to later calls; host-only.  elm_ddm_get_info key 9 says whether this handle's
+ * solves use the cooperative kernels (when no co-resident grid fits, one launch per block
+ * step is used instead and there is no device-side wait).
+ */
+int elm_ddm_set_wait_limit(elm_ddm_handle* h, double seconds, int hold_release);
 
 /*
  * The Schur matrix is assembled and factored with its interface unknowns renumbered
@@ -232,7 +274,8 @@ int elm_ddm_export(elm_ddm_handle* h, int what, int s, double* dst, int ld_dst);
  * (one per kernel class invocation, some launch several kernels) enqueued since setup,
  * 3 = number of Schur-matrix edges (interface blocks), 4 = m_max, 5 = n_neurons,
  * 6 = n_sub, 7 = CUDA kernels launched by the library in this process (all handles),
- * 8 = 1 if elm_ddm_assemble uses the factored activation tables, else 0.
+ * 8 = 1 if elm_ddm_assemble uses the factored activation tables, else 0,
+ * 9 = 1 if elm_ddm_solve's triangular solves run as one cooperative launch each, else 0.
  */
 int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value);
 
@@ -260,24 +303,31 @@ int elm_ddm_profile_only(elm_ddm_handle* h, const char* kernel_class);
 /*
  * No-allocation Cholesky solve.  The paper has no counterpart: this entry point exists
  * for callers that cannot call cudaMalloc -- code running while a CUDA graph is being
- * captured in global mode, hosts that route all device memory through their own pool
- * and forbid hidden allocations, real-time loops.  It solves L L^T u = b for nrhs
- * right-hand sides with the same blocked substitution kernels as elm_ddm_solve's
- * interface solve, needs no handle, and calls no cudaMalloc, cudaFree or allocating
- * library routine: its working vectors live in one fixed device array of
- * 2 * ELM_DDM_NOALLOC_MAX_ELEMS doubles (2 MiB) that every GPU loading the library holds
- * until the process exits.
+ * captured in global mode (an allocation there invalidates the capture), hosts that route
+ * all device memory through their own pool and forbid hidden allocations, real-time
+ * loops.  It solves L L^T u = b for nrhs right-hand sides with the same blocked
+ * substitution kernels as elm_ddm_solve's interface solve, needs no handle, and calls no
+ * cudaMalloc, cudaFree or allocating library routine: its working vectors live in one
+ * fixed device array of 2 * ELM_DDM_NOALLOC_MAX_ELEMS doubles (2 MiB) that every GPU
+ * loading the library holds until the process exits.
  *   L     device double, lower Cholesky factor (n x n, column-major, leading dimension
  *         ld >= n; the strict upper triangle is not read) -- e.g. elm_ddm_export's
  *         ELM_DDM_BUF_L
  *   b     device double [nrhs][n] right-hand sides (read only; may alias u)
  *   u     device double [nrhs][n] solutions
  *   stream cudaStream_t to enqueue on (NULL = legacy default stream)
- * Returns ELM_DDM_ERR_ARG for NULL pointers, n < 1, nrhs < 1 or ld < n;
- * ELM_DDM_ERR_CAPACITY if n * nrhs > ELM_DDM_NOALLOC_MAX_ELEMS (nothing is enqueued);
- * ELM_DDM_ERR_CUDA if a launch or copy fails.  Asynchronous otherwise.
+ * b and u are in the order of L's rows.  With the factor that ELM_DDM_BUF_L exports, that
+ * is the handle's internal interface order: unknown g of the caller's numbering is entry
+ * order[g] of b and u, with order from elm_ddm_interface_order; a vector in the caller's
+ * order (as elm_ddm_solve takes and returns them) must be permuted first.
+ * Returns ELM_DDM_ERR_ARG for NULL pointers, n < 1, nrhs < 1, nrhs > 65535 or ld < n;
+ * ELM_DDM_ERR_CAPACITY if n * nrhs > ELM_DDM_NOALLOC_MAX_ELEMS (nothing is enqueued
+ * in either case); ELM_DDM_ERR_CUDA if a launch or copy fails.  Asynchronous otherwise.
  * The first call on each device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture begins.
+ * with that device current) and keeps it for the life of the process; make that first
+ * call before any stream capture begins.  The kept address does not survive
+ * cudaDeviceReset (or anything else that unloads the library's module from the device):
+ * do not call this entry point on a device after resetting it.
  * All calls share the array and it keeps the previous call's contents (nothing in it
  * needs to start at zero: each call overwrites what it reads).  Calls whose work
  * overlaps on the GPU -- on different streams, or from different host threads without

@@ -16,8 +16,8 @@ constexpr int CHOL_NB = 64;   // block size of the Schur-matrix Cholesky
 constexpr int TRSV_MAX_N = 8192;  // largest n_neurons the back-solve keeps in shared memory
 
 // Bits of the device status word.
-// ST_TIMEOUT: a bounded wait inside a kernel gave up; ST_INTERNAL: a launch violated a
-// kernel's documented limits.  Both are reported as ELM_DDM_ERR_CUDA.
+// ST_TIMEOUT: a bounded wait inside a kernel gave up (ELM_DDM_ERR_TIMEOUT); ST_INTERNAL: a
+// launch violated a kernel's documented limits (ELM_DDM_ERR_CUDA).
 enum : unsigned { ST_RANK = 1u, ST_NOT_SPD = 2u, ST_NONFINITE = 4u, ST_TIMEOUT = 8u, ST_INTERNAL = 16u };
 
 // C(m x n) = alpha * op(A) op(B) + beta * C, column-major; op = transpose or not.
@@ -121,6 +121,10 @@ cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, doub
                             int m_max, const int* cnt, const double* W, const double* b, int N,
                             int n, const double* coef, const AsmTables* tb, unsigned* status,
                             cudaStream_t st);
+// Rows of one kind (0 interior, 1 boundary, 2 interface, 3 interface normals) of every
+// subdomain into out [N][kmax][2] (zero past each subdomain's count).
+cudaError_t launch_get_points(const double* xy, const double* nrm, int m_max, const int* cnt, int N,
+                              int kind, int kmax, double* out, cudaStream_t st);
 cudaError_t launch_eval(const double* W, const double* b, int N, int n, int npts,
                         const double* xy, const int* owner, const double* c, double* u,
                         double* grad, cudaStream_t st);
@@ -158,14 +162,18 @@ cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, unsigned* status
 // Whole triangular solves with the factor in S (envelope per 64-row step: rend / jbeg,
 // device arrays of nsteps; Linv the stored diagonal-block inverses), one cooperative
 // launch each on `grid` blocks (chol_solve_grid: 0 when no co-resident grid fits).
-// bar: 2 device words of barrier state.
+// bar: 2 device words of barrier state.  Each grid barrier gives up after limit_ns of
+// %globaltimer (flagging ST_TIMEOUT); hold = 1 withholds its release (test hook).
 int chol_solve_grid(bool forward, int work_max);
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;
 cudaError_t launch_chol_fwd_all(const double* L, int ld, int n, const double* Linv, const int* rend,
                                 int nsteps, double* r, double* y, int nrhs, int grid, unsigned* bar,
-                                unsigned* status, cudaStream_t st);
+                                unsigned* status, cudaStream_t st,
+                                unsigned long long limit_ns = kDefaultWaitNs, int hold = 0);
 cudaError_t launch_chol_bwd_all(const double* L, int ld, int n, const double* Linv, const int* jbeg,
                                 int nsteps, double* y, double* u, int nrhs, int grid, unsigned* bar,
-                                unsigned* status, cudaStream_t st);
+                                unsigned* status, cudaStream_t st,
+                                unsigned long long limit_ns = kDefaultWaitNs, int hold = 0);
 // Inverses of every CHOL_NB diagonal block of the factor L (in S), column-major, ld CHOL_NB.
 cudaError_t launch_tri_inv(const double* S, int ld, int n, double* inv, cudaStream_t st);
 // L21 = A21 L11^{-T} by substitution for rows k+nb .. row_end-1 (16 rows per block).  With

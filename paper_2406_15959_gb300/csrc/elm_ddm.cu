@@ -123,6 +123,8 @@ struct elm_ddm_handle {
   int* d_rend = nullptr;        // device copies of chol_rend / chol_jbeg
   int* d_jbeg = nullptr;
   unsigned* cbar = nullptr;     // grid-barrier state of the persistent triangular solves
+  unsigned long long wait_ns = kDefaultWaitNs;  // limit of their bounded grid-barrier waits
+  int wait_hold = 0;            // 1: withhold every barrier's release (failure-detection test)
   int fwd_grid = 0, bwd_grid = 0;  // their grids (0: one launch per block step instead)
   // device buffers
   double *K = nullptr, *Am = nullptr, *tau = nullptr, *T = nullptr, *Vp = nullptr;
@@ -156,9 +158,11 @@ struct elm_ddm_handle {
   bool has_sdinv = false;
   void* sp_buf = nullptr;        // digit tiles and row exponents of the split operands
   std::vector<int> qr_first;     // first record of each panel in qr_recs
-  // algorithmic flops of each Householder panel launch: per subdomain a m' x nb panel
-  // (2 m' nb^2 - 2 nb^3 / 3) and its compact-WY factor T (m' nb^2)
+  // algorithmic flops of each Householder panel launch: per subdomain the m' x nb panel's
+  // Householder work, 2 m' nb^2 - 2 nb^3 / 3 (the compact-WY factor T, m' nb^2 more, is
+  // blocking overhead and not counted)
   std::vector<double> panel_flops, panel_bytes;  // per QR panel, summed over subdomains
+  double asm_bytes = 0.0;        // algorithmic HBM bytes of one assembly: [K^s | J] and A^s written
   std::vector<int> syrk_first;   // first record of each Cholesky step in syrk_recs
   size_t mdiag_elems = 0;
   // plans
@@ -483,6 +487,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->vstride = (long long)h->ld * QR_NB;
   h->wstride = (long long)QR_NB * h->ncap;
   for (const Edge& e : h->edges) h->mdiag_elems += (size_t)e.len * e.len;
+  for (int s = 0; s < N; ++s)
+    h->asm_bytes += 8.0 * ((double)h->ms_h[s] * (n + h->mg_h[s]) + (double)h->mg_h[s] * n);
 
   // ---- distinct coordinates of each subdomain's rows (factored activation) ----
   std::vector<double> txs, tys, tctr(2 * (size_t)N);
@@ -754,7 +760,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     double pf = 0.0, pb = 0.0;
     for (int s = 0; s < N; ++s) {
       const double mp = std::max(0, h->ms_h[s] - k0);
-      pf += 3.0 * mp * nbe * nbe - 2.0 * nbe * (double)nbe * nbe / 3.0;
+      pf += 2.0 * mp * nbe * nbe - 2.0 * nbe * (double)nbe * nbe / 3.0;
       pb += 2.0 * 8.0 * mp * nbe;  // the panel read and written once
     }
     h->panel_flops.push_back(pf);
@@ -1096,11 +1102,11 @@ int elm_ddm_assemble(elm_ddm_handle* h, const double* W, const double* b) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->thb, b, nw * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Am, 0, (size_t)h->N * h->astride * sizeof(double), h->st);
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble: copy theta");
-  ELM_LAUNCH(h, launch_assemble(h->K, h->kstride, h->ld, h->ncap, h->Am, h->astride, h->mgld, h->xy,
-                                h->nrm, h->m_max, h->cnt, h->thW, h->thb, h->N, h->n,
-                                h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr,
-                                h->use_tabs ? &h->tabs : nullptr, h->status, h->st),
-             "assemble");
+  ELM_LAUNCH_FB(h, launch_assemble(h->K, h->kstride, h->ld, h->ncap, h->Am, h->astride, h->mgld, h->xy,
+                                   h->nrm, h->m_max, h->cnt, h->thW, h->thb, h->N, h->n,
+                                   h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr,
+                                   h->use_tabs ? &h->tabs : nullptr, h->status, h->st),
+                "assemble", 0.0, h->asm_bytes);
   h->state = 1;
   return ELM_DDM_OK;
 }
@@ -1230,9 +1236,11 @@ int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
     const int nsteps = (int)h->chol_rend.size();
     if (h->fwd_grid > 0 && h->bwd_grid > 0) {
       ELM_LAUNCH(h, launch_chol_fwd_all(h->S, ng, ng, h->cinv, h->d_rend, nsteps, h->rv, h->yv, nrhs,
-                                        h->fwd_grid, h->cbar, h->status, h->st), "chol_fwd");
+                                        h->fwd_grid, h->cbar, h->status, h->st, h->wait_ns, h->wait_hold),
+                 "chol_fwd");
       ELM_LAUNCH(h, launch_chol_bwd_all(h->S, ng, ng, h->cinv, h->d_jbeg, nsteps, h->yv, h->uv, nrhs,
-                                        h->bwd_grid, h->cbar, h->status, h->st), "chol_bwd");
+                                        h->bwd_grid, h->cbar, h->status, h->st, h->wait_ns, h->wait_hold),
+                 "chol_bwd");
     } else {
       for (int k = 0, step = 0; k < ng; k += CHOL_NB, ++step) {
         const int nb = std::min(CHOL_NB, ng - k);
@@ -1401,8 +1409,36 @@ int elm_ddm_check(elm_ddm_handle* h) {
   if (bits & ST_NONFINITE) return fail(h, ELM_DDM_ERR_NONFINITE, "non-finite value in theta, f/g or R");
   if (bits & ST_RANK) return fail(h, ELM_DDM_ERR_RANK, "a local R has an exactly zero diagonal entry");
   if (bits & ST_NOT_SPD) return fail(h, ELM_DDM_ERR_NOT_SPD, "Schur matrix is not positive definite");
-  if (bits & ST_TIMEOUT) return fail(h, ELM_DDM_ERR_CUDA, "a device-side wait timed out");
+  if (bits & ST_TIMEOUT) return fail(h, ELM_DDM_ERR_TIMEOUT, "a device-side wait timed out");
   if (bits & ST_INTERNAL) return fail(h, ELM_DDM_ERR_CUDA, "a kernel was launched outside its limits");
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_get_points(elm_ddm_handle* h, int kind, double* xy, int32_t* counts) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  if (kind < ELM_DDM_PTS_INTERIOR || kind > ELM_DDM_PTS_NORMALS)
+    return fail(h, ELM_DDM_ERR_ARG, "get_points: unknown kind");
+  const int col = kind == ELM_DDM_PTS_NORMALS ? 2 : kind;
+  int kmax = 0;
+  for (int s = 0; s < h->N; ++s) {
+    const int c = h->cnt_h[3 * s + col];
+    if (counts) counts[s] = c;
+    kmax = std::max(kmax, c);
+  }
+  if (!xy) return ELM_DDM_OK;
+  ELM_LAUNCH(h, launch_get_points(h->xy, h->nrm, h->m_max, h->cnt, h->N, kind, kmax, xy, h->st),
+             "get_points");
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_set_wait_limit(elm_ddm_handle* h, double seconds, int hold_release) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  if (!(seconds >= 0.0) || !(seconds <= 60.0))
+    return fail(h, ELM_DDM_ERR_ARG, "set_wait_limit: seconds must be in [0, 60]");
+  if (hold_release != 0 && hold_release != 1)
+    return fail(h, ELM_DDM_ERR_ARG, "set_wait_limit: hold_release must be 0 or 1");
+  h->wait_ns = (unsigned long long)(seconds * 1e9);
+  h->wait_hold = hold_release;
   return ELM_DDM_OK;
 }
 
@@ -1468,6 +1504,7 @@ int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value) {
     case 4: *value = h->m_max; break;
     case 7: *value = (double)elmddm::g_kernel_launches.load(); break;
     case 8: *value = h->use_tabs ? 1.0 : 0.0; break;
+    case 9: *value = (h->fwd_grid > 0 && h->bwd_grid > 0) ? 1.0 : 0.0; break;
     case 5: *value = h->n; break;
     case 6: *value = h->N; break;
     default: return ELM_DDM_ERR_ARG;

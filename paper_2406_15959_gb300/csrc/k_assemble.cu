@@ -210,7 +210,34 @@ __global__ void __launch_bounds__(256) k_eval(const double* __restrict__ W,
   }
 }
 
+// Copy of one kind of row (0 interior, 1 boundary, 2 interface points, 3 interface
+// normals) of every subdomain into out [N][kmax][2], zero-padded past each count.
+__global__ void k_get_points(const double* __restrict__ xy, const double* __restrict__ nrm, int m_max,
+                             const int* __restrict__ cnt, int kind, int kmax, double* __restrict__ out) {
+  const int s = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kmax) return;
+  const int mi = cnt[3 * s], mb = cnt[3 * s + 1], mg = cnt[3 * s + 2];
+  const int k = kind > 2 ? 2 : kind;
+  const int off = k == 0 ? 0 : (k == 1 ? mi : mi + mb), count = k == 0 ? mi : (k == 1 ? mb : mg);
+  const double* src = kind == 3 ? nrm : xy;
+  double a = 0.0, b = 0.0;
+  if (i < count) {
+    a = src[((size_t)s * m_max + off + i) * 2];
+    b = src[((size_t)s * m_max + off + i) * 2 + 1];
+  }
+  out[((size_t)s * kmax + i) * 2] = a;
+  out[((size_t)s * kmax + i) * 2 + 1] = b;
+}
+
 }  // namespace
+
+cudaError_t launch_get_points(const double* xy, const double* nrm, int m_max, const int* cnt, int N,
+                              int kind, int kmax, double* out, cudaStream_t st) {
+  if (kmax <= 0 || N <= 0) return cudaSuccess;
+  k_get_points<<<dim3((kmax + 127) / 128, N), 128, 0, st>>>(xy, nrm, m_max, cnt, kind, kmax, out);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, double* Amat,
                             long long astride, int mgld, const double* xy, const double* nrm,

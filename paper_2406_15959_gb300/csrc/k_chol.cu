@@ -327,7 +327,11 @@ __global__ void __launch_bounds__(256) k_chol_bwd(const double* __restrict__ L, 
 // 64-entry diagonal solve itself from the stored inverse, so one barrier per step
 // suffices; the vectors that other blocks update are read through L2 (ld.global.cg),
 // since L1 is not coherent between SMs.  The barrier's wait is bounded (2 s of
-// %globaltimer): on timeout the kernel flags ST_TIMEOUT and every block returns.
+// %globaltimer by default, set per handle): on timeout the kernel flags ST_TIMEOUT and
+// every block returns.  `hold` makes every barrier wait for one arrival more than the
+// grid has, i.e. for a release that never comes: the failure-detection tests use it to
+// make the wait run out on purpose (no asynchronous copy is in flight in these kernels,
+// so giving up and returning leaves nothing behind).
 __device__ __forceinline__ unsigned long long chol_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -335,21 +339,21 @@ __device__ __forceinline__ unsigned long long chol_ns() {
 }
 
 // bar[0]: arrivals, bar[1]: generation.  Returns false (for the whole block) on timeout.
-__device__ bool grid_barrier(unsigned* bar, unsigned* status) {
+__device__ bool grid_barrier(unsigned* bar, unsigned* status, unsigned long long limit_ns, int hold) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
     __threadfence();
     const unsigned g = *(volatile unsigned*)(bar + 1);
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    if (atomicAdd(bar, 1u) == gridDim.x - 1 + (unsigned)hold) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
       const unsigned long long t0 = chol_ns();
       while (*(volatile unsigned*)(bar + 1) == g) {
-        if (chol_ns() - t0 > 2000000000ull) {
+        if (chol_ns() - t0 >= limit_ns) {
           atomicOr(status, ST_TIMEOUT);
           ok = 0;
           break;
@@ -375,7 +379,8 @@ __global__ void __launch_bounds__(256) k_chol_fwd_all(const double* __restrict__
                                                       const double* __restrict__ Linv,
                                                       const int* __restrict__ rend, int nsteps,
                                                       double* r, double* y, int nrhs,
-                                                      unsigned* bar, unsigned* status) {
+                                                      unsigned* bar, unsigned* status,
+                                                      unsigned long long limit_ns, int hold) {
   __shared__ double Ls[NB][NB + 1];
   __shared__ double rs[NB], ys[NB], part[4][CS_ROWS];
   const int tid = threadIdx.x, il = tid % CS_ROWS, q = tid / CS_ROWS;
@@ -431,7 +436,7 @@ __global__ void __launch_bounds__(256) k_chol_fwd_all(const double* __restrict__
       }
     }
     if (st + 1 < nsteps) fetch(st + 1);
-    if (!grid_barrier(bar, status)) return;
+    if (!grid_barrier(bar, status, limit_ns, hold)) return;
   }
 }
 
@@ -440,7 +445,8 @@ __global__ void __launch_bounds__(256) k_chol_bwd_all(const double* __restrict__
                                                       const double* __restrict__ Linv,
                                                       const int* __restrict__ jbeg, int nsteps,
                                                       double* y, double* u, int nrhs,
-                                                      unsigned* bar, unsigned* status) {
+                                                      unsigned* bar, unsigned* status,
+                                                      unsigned long long limit_ns, int hold) {
   __shared__ double Ls[NB][NB + 1];
   __shared__ double ysh[NB], us[NB], part[4][CS_ROWS];
   const int tid = threadIdx.x, il = tid % CS_ROWS, q = tid / CS_ROWS;
@@ -494,7 +500,7 @@ __global__ void __launch_bounds__(256) k_chol_bwd_all(const double* __restrict__
       }
     }
     if (st > 0) fetch(st - 1);
-    if (!grid_barrier(bar, status)) return;
+    if (!grid_barrier(bar, status, limit_ns, hold)) return;
   }
 }
 
@@ -551,11 +557,12 @@ int chol_solve_grid(bool forward, int work_max) {
 
 cudaError_t launch_chol_fwd_all(const double* L, int ld, int n, const double* Linv, const int* rend,
                                 int nsteps, double* r, double* y, int nrhs, int grid, unsigned* bar,
-                                unsigned* status, cudaStream_t st) {
+                                unsigned* status, cudaStream_t st, unsigned long long limit_ns, int hold) {
   cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&L, (void*)&ld, (void*)&n, (void*)&Linv, (void*)&rend, (void*)&nsteps,
-                  (void*)&r, (void*)&y, (void*)&nrhs, (void*)&bar, (void*)&status};
+                  (void*)&r, (void*)&y, (void*)&nrhs, (void*)&bar, (void*)&status, (void*)&limit_ns,
+                  (void*)&hold};
   e = cudaLaunchCooperativeKernel((const void*)k_chol_fwd_all, dim3(grid), dim3(256), args, 0, st);
   count_launch();
   return e;
@@ -563,11 +570,12 @@ cudaError_t launch_chol_fwd_all(const double* L, int ld, int n, const double* Li
 
 cudaError_t launch_chol_bwd_all(const double* L, int ld, int n, const double* Linv, const int* jbeg,
                                 int nsteps, double* y, double* u, int nrhs, int grid, unsigned* bar,
-                                unsigned* status, cudaStream_t st) {
+                                unsigned* status, cudaStream_t st, unsigned long long limit_ns, int hold) {
   cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&L, (void*)&ld, (void*)&n, (void*)&Linv, (void*)&jbeg, (void*)&nsteps,
-                  (void*)&y, (void*)&u, (void*)&nrhs, (void*)&bar, (void*)&status};
+                  (void*)&y, (void*)&u, (void*)&nrhs, (void*)&bar, (void*)&status, (void*)&limit_ns,
+                  (void*)&hold};
   e = cudaLaunchCooperativeKernel((const void*)k_chol_bwd_all, dim3(grid), dim3(256), args, 0, st);
   count_launch();
   return e;

@@ -26,8 +26,10 @@ static __device__ __align__(256) double g_noalloc_scratch[2 * ELM_DDM_NOALLOC_MA
 std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once per device.
-// In host code g_noalloc_scratch names a host-side stand-in, not device memory.
+// Device address of the scratch array on the current device, looked up once per device
+// and kept for the life of the process (a device reset would invalidate it; the header
+// says not to call the entry point after one).  In host code g_noalloc_scratch names a
+// host-side stand-in, not device memory.
 cudaError_t scratch_on_current_device(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -48,7 +50,8 @@ cudaError_t scratch_on_current_device(double** out) {
 
 extern "C" int elm_ddm_chol_solve_noalloc(const double* L, int n, int ld, const double* b,
                                           int nrhs, double* u, void* stream) {
-  if (!L || !b || !u || n < 1 || nrhs < 1 || ld < n) return ELM_DDM_ERR_ARG;
+  // nrhs is the y dimension of the substitution kernels' grids (at most 65535)
+  if (!L || !b || !u || n < 1 || nrhs < 1 || nrhs > 65535 || ld < n) return ELM_DDM_ERR_ARG;
   if ((long long)n * nrhs > ELM_DDM_NOALLOC_MAX_ELEMS) return ELM_DDM_ERR_CAPACITY;
   double* scratch = nullptr;
   if (scratch_on_current_device(&scratch) != cudaSuccess) {

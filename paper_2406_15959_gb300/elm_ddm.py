@@ -15,10 +15,11 @@ import numpy as np
 from . import build as _build
 
 (OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_RANK, ERR_NOT_SPD, ERR_CAPACITY,
- ERR_NOCONV) = range(10)
+ ERR_NOCONV, ERR_TIMEOUT) = range(11)
 ERROR_NAMES = {ERR_ARG: "ERR_ARG", ERR_STATE: "ERR_STATE", ERR_CUDA: "ERR_CUDA",
                ERR_OOM: "ERR_OOM", ERR_NONFINITE: "ERR_NONFINITE", ERR_RANK: "ERR_RANK",
-               ERR_NOT_SPD: "ERR_NOT_SPD", ERR_CAPACITY: "ERR_CAPACITY", ERR_NOCONV: "ERR_NOCONV"}
+               ERR_NOT_SPD: "ERR_NOT_SPD", ERR_CAPACITY: "ERR_CAPACITY", ERR_NOCONV: "ERR_NOCONV",
+               ERR_TIMEOUT: "ERR_TIMEOUT"}
 
 # Every symbol the header declares.
 SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve",
@@ -26,8 +27,9 @@ SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve"
            "elm_ddm_profile", "elm_ddm_profile_report", "elm_ddm_destroy",
            "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order",
            "elm_ddm_profile_only", "elm_ddm_solve_cg", "elm_ddm_set_coefficient",
-           "elm_ddm_solve_pcg")
+           "elm_ddm_solve_pcg", "elm_ddm_get_points", "elm_ddm_set_wait_limit")
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
+PTS_INTERIOR, PTS_BOUNDARY, PTS_INTERFACE, PTS_NORMALS = range(4)
 
 
 class ElmDdmError(RuntimeError):
@@ -80,6 +82,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_profile_only.argtypes = [P, ctypes.c_char_p]
     lib.elm_ddm_profile_report.argtypes = [P, ctypes.c_char_p, I]
     lib.elm_ddm_get_info.argtypes = [P, I, D]
+    lib.elm_ddm_get_points.argtypes = [P, I, P, P]
+    lib.elm_ddm_set_wait_limit.argtypes = [P, ctypes.c_double, I]
     lib.elm_ddm_destroy.argtypes = [P]
     lib.elm_ddm_last_error.argtypes = [P]
     lib.elm_ddm_last_error.restype = ctypes.c_char_p
@@ -253,6 +257,26 @@ class Solver:
         if what == BUF_L:
             return self.n_gamma, self.n_gamma
         raise ValueError(what)
+
+    def get_points(self, kind: int):
+        """Points of one kind (PTS_*) as held by the handle: (CUDA float64 [N, kmax, 2],
+        int32 counts [N])."""
+        import torch
+        counts = np.zeros(self.N, np.int32)
+        self._check_rc(self.lib.elm_ddm_get_points(self.h, kind, None, counts.ctypes.data))
+        kmax = int(counts.max()) if self.N else 0
+        out = torch.empty((self.N, max(kmax, 1), 2), dtype=torch.float64, device="cuda")
+        self._check_rc(self.lib.elm_ddm_get_points(self.h, kind, _ptr(out), None))
+        return out[:, :kmax], counts
+
+    def set_wait_limit(self, seconds: float = 2.0, hold_release: bool = False):
+        """Limit of the device-side waits of the triangular solves (hold_release: test hook
+        that makes them run out)."""
+        self._check_rc(self.lib.elm_ddm_set_wait_limit(self.h, float(seconds), int(bool(hold_release))))
+
+    @property
+    def cooperative_solves(self) -> bool:
+        return self.info(9) == 1.0
 
     def interface_order(self) -> np.ndarray:
         """Internal index of every interface unknown (the order of BUF_L's rows)."""

@@ -111,3 +111,9 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.elm_ddm_solve(None, None, 1, None, None) == E.ERR_ARG
     assert lib.elm_ddm_check(None) == E.ERR_ARG
     assert lib.elm_ddm_destroy(None) == E.ERR_ARG
+
+
+def test_new_entry_points_reject_null_handles():
+    lib = E.load()
+    assert lib.elm_ddm_get_points(None, 0, None, None) == E.ERR_ARG
+    assert lib.elm_ddm_set_wait_limit(None, 1.0, 0) == E.ERR_ARG

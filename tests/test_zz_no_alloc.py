@@ -4,8 +4,9 @@ It serves callers that cannot call cudaMalloc (a CUDA graph being captured in gl
 mode, a host that owns all device memory through its own pool, a real-time loop).
 The test checks its output against the interface solution u_Gamma that elm_ddm_solve
 computes with the same Cholesky factor, on two calls in a row (the fixed scratch array
-keeps the first call's contents when the second one runs), and that the second call
-changes the device's free memory by nothing.  This file is collected last on purpose.
+keeps the first call's contents when the second one runs), that the second call
+changes the device's free memory by nothing, and that three right-hand sides in one
+call give what the three give one at a time.  This file is collected last on purpose.
 """
 import ctypes
 
@@ -68,6 +69,19 @@ def test_noalloc_solve_matches_elm_ddm_solve_on_two_calls():
         assert err <= 1e-8, (k, err)
     free.append(torch.cuda.mem_get_info(dev)[0])
     assert free[1] == free[2]                    # the second call allocated nothing
+    # three right-hand sides in one call ([nrhs][n] layout, each its own grid row) against
+    # the same three solved one at a time
+    us = [ref[0][inv], ref[1][inv], (ref[0] - 2.0 * ref[1])[inv]]
+    B = torch.stack([(Ltri @ (Ltri.t() @ v)) for v in us]).contiguous()
+    U = torch.full((3, n), float("nan"), dtype=torch.float64, device=dev)
+    assert f(Lcm.data_ptr(), n, n, B.data_ptr(), 3, U.data_ptr(), stream.cuda_stream) == E.OK
+    one = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    for k in range(3):
+        bk = B[k].contiguous()
+        assert f(Lcm.data_ptr(), n, n, bk.data_ptr(), 1, one.data_ptr(), stream.cuda_stream) == E.OK
+        torch.cuda.synchronize(dev)
+        assert (torch.linalg.norm(U[k] - one) / torch.linalg.norm(one)).item() <= 1e-12, k
+        assert (torch.linalg.norm(U[k] - us[k]) / torch.linalg.norm(us[k])).item() <= 1e-8, k
     s.close()
 
 
@@ -79,4 +93,6 @@ def test_noalloc_solve_rejects_sizes_beyond_its_scratch():
     assert f(x.data_ptr(), MAX_ELEMS // 2 + 1, MAX_ELEMS // 2 + 1, x.data_ptr(), 2,
              x.data_ptr(), None) == E.ERR_CAPACITY
     assert f(x.data_ptr(), 4, 3, x.data_ptr(), 1, x.data_ptr(), None) == E.ERR_ARG
+    # within the capacity but more right-hand sides than a grid's y dimension holds
+    assert f(x.data_ptr(), 1, 1, x.data_ptr(), 65536, x.data_ptr(), None) == E.ERR_ARG
     assert f(None, 4, 4, x.data_ptr(), 1, x.data_ptr(), None) == E.ERR_ARG
