@@ -40,6 +40,7 @@
 #ifndef ELM_DDM_H
 #define ELM_DDM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -336,6 +337,45 @@ int elm_ddm_profile_only(elm_ddm_handle* h, const char* kernel_class);
 #define ELM_DDM_NOALLOC_MAX_ELEMS 131072
 int elm_ddm_chol_solve_noalloc(const double* L, int n, int ld, const double* b, int nrhs,
                                double* u, void* stream);
+
+/*
+ * FP64-accurate matrix product on the BF16 tensor cores: the digit-split scheme the
+ * solver runs its dense updates with (QR trailing updates, D_s and M_s of Eq. (3.5), the
+ * Schur matrix's M^T M blocks and Cholesky SYRK), as a stand-alone call.  The paper has
+ * no counterpart (it states these products in FP64; this is how they are computed here):
+ *   C[i*c_rs + j*c_cs] = alpha * sum_k A(i,k) B(j,k) + beta * C[i*c_rs + j*c_cs],
+ *   A(i,k) = A[i*a_rs + k*a_ks],  B(j,k) = B[j*b_rs + k*b_ks],  0 <= i < M, 0 <= j < N.
+ * Each row of A and of B is written as 2^(E-1022) sum_{p=1..7} d_p 2^(1-8p) with integer
+ * digits |d_p| <= 128 (E its largest biased exponent; truncation below 2^-54 of the
+ * row's largest magnitude), the 28 digit pairs of weight >= 2^-62 are multiplied exactly
+ * on the tensor cores, and each element is rounded once.  The error bound is therefore
+ * normwise per row and column, not componentwise like an FP64 GEMM's:
+ *   |C_ij - (A B^T)_ij| <= 2^-53 |(A B^T)_ij|
+ *                          + 2^-54 (max_k |A(i,k)| sum_k |B(j,k)| + max_k |B(j,k)| sum_k |A(i,k)|)
+ * (with beta != 0 or |alpha| != 1 one more rounding of the update).
+ *   kernel  ELM_DDM_GEMM_TILE32      one CTA per 128 x 32 output tile, K <= 7936
+ *           ELM_DDM_GEMM_TILE64      one CTA per 128 x 64 output tile, K <= 128
+ *           ELM_DDM_GEMM_PERSISTENT  one CTA per SM over a table of 128 x 32 tiles, K <= 128
+ *           ELM_DDM_GEMM_FUSED_SPLIT A split inside the product kernel: a_ks = 1, N <= 32,
+ *                                    K <= 7936, alpha = 1, beta = 0
+ *   A, B, C  device double (C must not overlap A or B)
+ *   workspace  device memory, 256-byte aligned, of at least
+ *              elm_ddm_fp64_gemm_workspace(kernel, M, N, K) bytes (0 for an unsupported
+ *              shape); owned by the caller, free again when the call returns
+ *   stream  cudaStream_t (NULL = legacy default stream)
+ * Synchronises the stream before returning.  Returns ELM_DDM_ERR_ARG for an unsupported
+ * kernel or shape, NULL pointers, a short or misaligned workspace;
+ * ELM_DDM_ERR_TIMEOUT if a bounded wait of the product kernel gave up; ELM_DDM_ERR_CUDA.
+ */
+#define ELM_DDM_GEMM_TILE32      0
+#define ELM_DDM_GEMM_TILE64      1
+#define ELM_DDM_GEMM_PERSISTENT  2
+#define ELM_DDM_GEMM_FUSED_SPLIT 3
+size_t elm_ddm_fp64_gemm_workspace(int kernel, int M, int N, int K);
+int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, const double* A,
+                      long long a_rs, long long a_ks, const double* B, long long b_rs,
+                      long long b_ks, double beta, double* C, long long c_rs, long long c_cs,
+                      void* workspace, size_t workspace_bytes, void* stream);
 
 /* Frees all device workspace and the handle.  Synchronises the stream first. */
 int elm_ddm_destroy(elm_ddm_handle* h);

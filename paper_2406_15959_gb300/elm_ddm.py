@@ -27,7 +27,9 @@ SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve"
            "elm_ddm_profile", "elm_ddm_profile_report", "elm_ddm_destroy",
            "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order",
            "elm_ddm_profile_only", "elm_ddm_solve_cg", "elm_ddm_set_coefficient",
-           "elm_ddm_solve_pcg", "elm_ddm_get_points", "elm_ddm_set_wait_limit")
+           "elm_ddm_solve_pcg", "elm_ddm_get_points", "elm_ddm_set_wait_limit",
+           "elm_ddm_fp64_gemm", "elm_ddm_fp64_gemm_workspace")
+GEMM_TILE32, GEMM_TILE64, GEMM_PERSISTENT, GEMM_FUSED_SPLIT = range(4)
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
 PTS_INTERIOR, PTS_BOUNDARY, PTS_INTERFACE, PTS_NORMALS = range(4)
 
@@ -84,11 +86,16 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_get_info.argtypes = [P, I, D]
     lib.elm_ddm_get_points.argtypes = [P, I, P, P]
     lib.elm_ddm_set_wait_limit.argtypes = [P, ctypes.c_double, I]
+    LL = ctypes.c_longlong
+    lib.elm_ddm_fp64_gemm_workspace.argtypes = [I, I, I, I]
+    lib.elm_ddm_fp64_gemm_workspace.restype = ctypes.c_size_t
+    lib.elm_ddm_fp64_gemm.argtypes = [I, I, I, I, ctypes.c_double, P, LL, LL, P, LL, LL, ctypes.c_double,
+                                      P, LL, LL, P, ctypes.c_size_t, P]
     lib.elm_ddm_destroy.argtypes = [P]
     lib.elm_ddm_last_error.argtypes = [P]
     lib.elm_ddm_last_error.restype = ctypes.c_char_p
     for name in SYMBOLS:
-        if name != "elm_ddm_last_error":
+        if name not in ("elm_ddm_last_error", "elm_ddm_fp64_gemm_workspace"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -314,6 +321,28 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def fp64_gemm(A, B, C, alpha: float = 1.0, beta: float = 0.0, kernel: int = GEMM_TILE32, stream=None):
+    """C = alpha A B^T + beta C with the library's FP64-accurate tensor-core product
+    (elm_ddm_fp64_gemm); A [M, K], B [N, K], C [M, N] CUDA float64 tensors of any strides.
+    Returns C."""
+    import torch
+    lib = load()
+    M, K = A.shape
+    N = B.shape[0]
+    ws_bytes = lib.elm_ddm_fp64_gemm_workspace(kernel, M, N, K)
+    if ws_bytes == 0:
+        raise ElmDdmError(ERR_ARG, f"unsupported shape {M}x{N}x{K} for kernel {kernel}")
+    ws = torch.empty(ws_bytes // 8 + 32, dtype=torch.float64, device=A.device)
+    base = (ws.data_ptr() + 255) // 256 * 256
+    st = (stream or torch.cuda.current_stream(A.device)).cuda_stream
+    rc = lib.elm_ddm_fp64_gemm(kernel, M, N, K, float(alpha), A.data_ptr(), A.stride(0), A.stride(1),
+                               B.data_ptr(), B.stride(0), B.stride(1), float(beta), C.data_ptr(),
+                               C.stride(0), C.stride(1), base, ws_bytes, st)
+    if rc != OK:
+        raise ElmDdmError(rc, "elm_ddm_fp64_gemm")
+    return C
 
 
 def run_workload(w, device="cuda", max_rhs=1):

@@ -40,3 +40,28 @@ def test_serving_plan_runs_every_batch():
         _, _, u = bs.run()
         bs.solver.check()
         assert torch.isfinite(u).all()
+
+
+def test_graph_replay_equals_eager_and_oracle():
+    """Serving captures a batch's whole solve (assembly, factorisation, Schur solve,
+    back-solves, evaluation) as one CUDA graph and replays it: the replay must give the
+    eager run's bits, and both must match the per-instance oracle."""
+    ws = instances()
+    bt = B.combine(ws)
+    eager = B.BatchSolver(bt)
+    out = eager.run()
+    eager.solver.check()                  # synchronises the batch's stream
+    ug_e, c_e, u_e = (x.clone() for x in out)
+    torch.cuda.synchronize()
+    bs = B.BatchSolver(bt)
+    bs.capture()
+    for _ in range(2):
+        ug_g, c_g, u_g = bs.replay()
+        torch.cuda.synchronize()
+        bs.solver.check()
+        assert torch.equal(ug_g, ug_e) and torch.equal(c_g, c_e) and torch.equal(u_g, u_e)
+    ug, c, u = ug_g.cpu().numpy(), c_g.cpu().numpy(), u_g.cpu().numpy()
+    for w, (ug_b, _, u_b) in zip(ws, B.split(bt, ug, c, u)):
+        res = O.solve(w.geom, w.W, w.b, w.rhs, coef=w.coef_rows)
+        u1, _ = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
+        assert np.linalg.norm(u_b - u1) <= 1e-8 * np.linalg.norm(u1)

@@ -232,3 +232,31 @@ def test_call_order_and_numerical_failures_are_reported():
     with pytest.raises(E.ElmDdmError) as ei:
         s.check()
     assert ei.value.code == E.ERR_RANK
+
+
+def test_16x16_grid_matches_oracle():
+    """A 16 x 16 decomposition (the mixed-precision configuration's grid): 256 subdomains
+    of 4464 rows, so the panels run on 8-CTA clusters, n_Gamma = 7680 interface unknowns,
+    and the envelope Cholesky of a G = 16 edge graph; small networks keep the oracle fast."""
+    w = wl.build(16, 16, 96, 80, 55, 16, 16, theta="paper", theta_seed=16, source="fourier",
+                 source_seed=16, n_test_side=100)
+    assert int(w.geom.counts[:, :].sum(1).max()) > 4 * 698     # a quarter exceeds one CTA's panel
+    res = O.solve(w.geom, w.W, w.b, w.rhs, keep=False)
+    u_or, g_or = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
+    for fp64_simt in (False, True):
+        s, ug, c, u, g = gpu_run(w, fp64_simt=fp64_simt)
+        assert rel(u.cpu().numpy(), u_or) <= 1e-8, fp64_simt
+        assert rel(g.cpu().numpy(), g_or) <= 1e-7, fp64_simt
+        assert rel(ug.cpu().numpy(), res.u_gamma) <= 1e-8, fp64_simt
+        s.close()
+
+
+def test_full_size_16x16_n2000_is_accurate():
+    """The 16 x 16 workload at full size (256 subdomains, 2000 neurons, 4512 rows each,
+    n_Gamma = 61,440; too large for the oracle): the solution against the closed-form u
+    of its sine-mode source (the paper's 16 x 16 Poisson row of Table 2 reports 1e-7)."""
+    w = wl.poisson_16x16_n2000()
+    s, ug, c, u, g = gpu_run(w)
+    l2, h1 = O.rel_errors(u.cpu().numpy(), g.cpu().numpy(), w.src.u(w.test_xy), w.src.grad_u(w.test_xy))
+    assert l2 < 1e-8 and h1 < 1e-6, (l2, h1)
+    s.close()
