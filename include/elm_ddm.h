@@ -347,12 +347,15 @@ int elm_ddm_chol_solve_noalloc(const double* L, int n, int ld, const double* b, 
  *   A(i,k) = A[i*a_rs + k*a_ks],  B(j,k) = B[j*b_rs + k*b_ks],  0 <= i < M, 0 <= j < N.
  * Each row of A and of B is written as 2^(E-1022) sum_{p=1..7} d_p 2^(1-8p) with integer
  * digits |d_p| <= 128 (E its largest biased exponent; truncation below 2^-54 of the
- * row's largest magnitude), the 28 digit pairs of weight >= 2^-62 are multiplied exactly
- * on the tensor cores, and each element is rounded once.  The error bound is therefore
+ * row's largest magnitude), the 28 digit pairs with p + q <= 8 are multiplied exactly on
+ * the tensor cores (the pairs not formed weigh at most 6 * 2^-54 of the row maxima's
+ * product per term), and each element is rounded once.  The error bound is therefore
  * normwise per row and column, not componentwise like an FP64 GEMM's:
  *   |C_ij - (A B^T)_ij| <= 2^-53 |(A B^T)_ij|
  *                          + 2^-54 (max_k |A(i,k)| sum_k |B(j,k)| + max_k |B(j,k)| sum_k |A(i,k)|)
- * (with beta != 0 or |alpha| != 1 one more rounding of the update).
+ *                          + 6 K 2^-54 max_k |A(i,k)| max_k |B(j,k)|
+ * (with beta != 0 or |alpha| != 1 one more rounding of the update): entries far below
+ * the largest of their row and column carry no relative accuracy of their own.
  *   kernel  ELM_DDM_GEMM_TILE32      one CTA per 128 x 32 output tile, K <= 7936
  *           ELM_DDM_GEMM_TILE64      one CTA per 128 x 64 output tile, K <= 128
  *           ELM_DDM_GEMM_PERSISTENT  one CTA per SM over a table of 128 x 32 tiles, K <= 128

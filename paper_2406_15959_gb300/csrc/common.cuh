@@ -67,6 +67,10 @@ struct OzDesc {
   // persistent product with GEMM_LOWER: column j of this C is column j + lower_off of the
   // symmetric matrix, so a tile is kept when its first column is on or below the diagonal
   int lower_off = 0;
+  // fused-split launches: rows i < lead of A are read from At2 (same row stride a_rs)
+  // instead of At, so one product can stack two FP64 operands with equal leading dimension
+  const void* At2 = nullptr;
+  int lead = 0;
 };
 
 // Per right-hand side state of the CG solve of the Schur system (k_cg.cu).
@@ -129,9 +133,15 @@ cudaError_t launch_eval(const double* W, const double* b, int N, int n, int npts
                         const double* xy, const int* owner, const double* c, double* u,
                         double* grad, cudaStream_t st);
 
+// Householder panel [k0, k0+nbe) of every subdomain: R and the reflectors in place, tau,
+// the explicit reflectors in Vp.  T is formed afterwards by launch_form_t.
 cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
-                            int nbe, double* tau, int n, double* T, long long tstride,
-                            double* Vp, long long vstride, unsigned* status, cudaStream_t st);
+                            int nbe, double* tau, int n, double* Vp, long long vstride, unsigned* status,
+                            cudaStream_t st);
+// Compact-WY T of panel [k0, k0+nbe) of every subdomain from G (v_l^T v_j at G[l*32 + j],
+// l < j, per subdomain at stride gstride) and tau; T [32 x 32] column-major at T + s*tstride.
+cudaError_t launch_form_t(const double* G, long long gstride, const double* tau, int n, int k0, int nbe,
+                          int N, double* T, long long tstride, cudaStream_t st);
 cudaError_t launch_trsm_y(double* Y, long long ystride, int mgld, const double* K,
                           long long kstride, int ld, const int* mg, int mgmax, int N, int n,
                           cudaStream_t st);

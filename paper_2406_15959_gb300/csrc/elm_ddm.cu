@@ -26,7 +26,8 @@ struct LaunchRec {
   int kind;  // 0 = FP64 gemm, 1 = add_blocks, 2 = digit split, 3 = tensor-core digit GEMM,
              // 4 = persistent tensor-core digit GEMM for K <= 64 (max_tiles = total tiles),
              // 5 = tensor-core digit GEMM with the FP64 A operand split in the kernel,
-             // 6 = diagonal step of the blocked Y = A R^{-1} (off = first column, nt = width)
+             // 6 = diagonal step of the blocked Y = A R^{-1} (off = first column, nt = width),
+             // 7 = compact-WY T of QR panel `off` from the Gram rows of its W1 product
   int off, count, max_tiles;  // split: max_tiles = blocks of k_split, nt = max rows
   bool ta, tb;
   double alpha, beta;
@@ -290,6 +291,9 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
     else if (L.kind == 3)
       ELM_LAUNCH_FB(h, launch_ozaki(L.nt, h->od + L.off, L.count, L.max_tiles, L.alpha, L.beta,
                                     L.flags, h->status, h->st), nm, L.flops, L.bytes);
+    else if (L.kind == 7)
+      ELM_LAUNCH(h, launch_form_t(h->W1, h->wstride, h->tau, h->n, L.off * QR_NB, L.nt, h->N,
+                                  h->T + (size_t)L.off * QR_NB * QR_NB, h->tstride, h->st), "form_t");
     else if (L.kind == 6)
       ELM_LAUNCH_F(h, launch_trsm_y_diag(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg,
                                          h->mgmax, h->N, h->n, L.off, h->st), nm, L.flops);
@@ -609,7 +613,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     restmax = std::max(restmax, h->chol_rend[st] - k - std::min(CHOL_NB, ng - k));
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   // (A2^T is split inside the fused product kernel: only its row exponents are stored)
-  const size_t s1 = 0, e1 = al((size_t)n2max * 4);
+  const size_t s1 = 0, e1 = al((size_t)(n2max + QR_NB) * 4);
   const size_t s2 = al(oz_split_elems(QR_NB, mpmax, 32) * 2), e2 = al((size_t)QR_NB * 4);
   const size_t s3 = al(oz_split_elems(mpmax, QR_NB, 128) * 2), e3 = al((size_t)mpmax * 4);
   const size_t s4 = al(oz_split_elems(n2max, QR_NB, 32) * 2), e4 = al((size_t)n2max * 4);
@@ -765,35 +769,53 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
     h->panel_flops.push_back(pf);
     h->panel_bytes.push_back(pb);
+    // W1 = V^T [V | A2]: its first nbe rows of W1^T are v_l^T v_j (what T needs,
+    // launch_form_t), the rest V^T A2 (the FP64 back end takes V^T [P | A2], P the panel's
+    // stored columns, whose rows give the same v_l^T v_j for l < j exactly).  Then
+    // W2 = T^T W1 and A2 -= V W2 on the trailing columns only.  With the tensor-core back
+    // end W1^T = [P | A2]^T V and A2 -= V W2 are digit-split products (W2 too, K = 32).
     std::vector<GemmDesc> g1, g2, g3;
     std::vector<SplitDesc> sp1, sp3, spt;
     std::vector<OzDesc> o1, o3, ot;
     for (int s = 0; s < N; ++s) {
+      // the W1 product runs for every panel (T needs its Gram rows even when no trailing
+      // column is left); W2 and the update only when there are trailing columns
       const int n2 = n + h->mg_h[s] - (k0 + nbe), mp = h->ms_h[s] - k0;
-      if (n2 <= 0 || mp <= 0) continue;
+      if (mp <= 0) continue;
       double* Ks = h->K + (size_t)s * h->kstride;
       const double* V = h->Vp + (size_t)s * h->vstride + k0;
-      double* A2 = Ks + k0 + (size_t)(k0 + nbe) * ld;
+      double* PA2 = Ks + k0 + (size_t)k0 * ld;           // [P | A2], n2 + nbe columns
+      double* A2 = PA2 + (size_t)nbe * ld;
       double* w1 = h->W1 + (size_t)s * h->wstride;
+      double* w1t = w1 + (size_t)nbe * QR_NB;             // rows of W1^T for the trailing columns
       double* w2 = h->W2 + (size_t)s * h->wstride;
       const double* Tb = h->T + (size_t)s * h->tstride + (size_t)b * QR_NB * QR_NB;
-      g1.push_back({V, A2, w1, nbe, n2, mp, ld, ld, QR_NB});
-      g2.push_back({Tb, w1, w2, nbe, n2, nbe, QR_NB, QR_NB, QR_NB});
-      g3.push_back({V, w2, A2, mp, n2, nbe, ld, QR_NB, ld});
+      g1.push_back({V, PA2, w1, nbe, n2 + nbe, mp, ld, ld, QR_NB});
+      if (n2 > 0) {
+        g2.push_back({Tb, w1t, w2, nbe, n2, nbe, QR_NB, QR_NB, QR_NB});
+        g3.push_back({V, w2, A2, mp, n2, nbe, ld, QR_NB, ld});
+      }
       if (h->emulated) {
-        void* t1 = sub_region(s, 0); int* x1 = (int*)sub_region(s, 1);
+        int* x1 = (int*)sub_region(s, 1);
         void* t2 = sub_region(s, 2); int* x2 = (int*)sub_region(s, 3);
         void* t3 = sub_region(s, 4); int* x3 = (int*)sub_region(s, 5);
         void* t4 = sub_region(s, 6); int* x4 = (int*)sub_region(s, 7);
-        (void)t1;
-        sp1.push_back({A2, ld, 1, n2, mp, x1, nullptr, 128});  // A2^T: row exponents only
-        sp1.push_back({V, ld, 1, nbe, mp, x2, t2, 32});        // V^T: rows = panel columns
-        o1.push_back({A2, x1, t2, x2, w1, QR_NB, 1, n2, nbe, mp, 0, ld});
+        // A = [V | A2]^T (the Gram rows from the explicit reflectors: |v| <= 1 with a unit
+        // diagonal, so the digit split keeps them to FP64 accuracy, where the stored panel
+        // columns would be truncated relative to R's entries): row exponents only
+        sp1.push_back({V, ld, 1, nbe, mp, x1, nullptr, 128});
+        sp1.push_back({A2, ld, 1, n2, mp, x1 + nbe, nullptr, 128});
+        sp1.push_back({V, ld, 1, nbe, mp, x2, t2, 32});              // V^T: rows = panel columns
+        OzDesc ow{PA2, x1, t2, x2, w1, QR_NB, 1, n2 + nbe, nbe, mp, 0, ld};
+        ow.At2 = V;   // rows i < nbe at V + i * ld, rows i >= nbe at PA2 + i * ld = A2
+        ow.lead = nbe;
+        o1.push_back(ow);
+        if (n2 <= 0) continue;
         void* t9 = sub_region(s, 16); int* x9 = (int*)sub_region(s, 17);
         void* t10 = sub_region(s, 18); int* x10 = (int*)sub_region(s, 19);
         // W2^T = W1^T T as a tensor-core product: A = W1^T (row j = trailing column j,
         // 32 contiguous values), B = T^T (row i = column i of the column-major T)
-        spt.push_back({w1, QR_NB, 1, n2, nbe, x9, t9, 128});
+        spt.push_back({w1t, QR_NB, 1, n2, nbe, x9, t9, 128});
         spt.push_back({Tb, QR_NB, 1, nbe, nbe, x10, t10, 32});
         spt.push_back({V, 1, ld, mp, nbe, x3, t3, 128});     // V: rows = matrix rows
         ot.push_back({t9, x9, t10, x10, w2, QR_NB, 1, n2, nbe, nbe, 0});
@@ -802,15 +824,19 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       }
     }
     h->qr_first.push_back((int)h->qr_recs.size());
+    LaunchRec FT{7, b, 1, 0, false, false, 0.0, 0.0, 0, 0.0, nbe};
+    FT.name = "form_t";
     if (h->emulated) {
       add_split_rec(h->qr_recs, sp1, "split_qr_w");
       add_fa_rec(h->qr_recs, o1, "oz_qr_w");
+      h->qr_recs.push_back(FT);
       add_split_rec(h->qr_recs, spt, "split_qr_t");
       add_oz_rec(h->qr_recs, ot, 0, 1.0, 0.0, 0, "oz_qr_t");
       add_split_rec(h->qr_recs, sp3, "split_qr_update");
       add_oz_rec(h->qr_recs, o3, 0, -1.0, 1.0, 0, "oz_qr_update");
     } else {
       add_gemm_rec(h->qr_recs, g1, true, false, 1.0, 0.0, 0);
+      h->qr_recs.push_back(FT);
       add_gemm_rec(h->qr_recs, g2, true, false, 1.0, 0.0, 0);
       add_gemm_rec(h->qr_recs, g3, false, false, -1.0, 1.0, 0);
     }
@@ -1117,9 +1143,9 @@ int elm_ddm_schur(elm_ddm_handle* h) {
   // (b) blocked Householder QR of [K^s | J]
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, h->n - k0);
-    ELM_LAUNCH_FB(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->T +
-                                    (size_t)b * QR_NB * QR_NB, h->tstride, h->Vp, h->vstride, h->status,
-                                    h->st), "panel_qr", h->panel_flops[b], h->panel_bytes[b]);
+    ELM_LAUNCH_FB(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->Vp,
+                                     h->vstride, h->status, h->st), "panel_qr", h->panel_flops[b],
+                  h->panel_bytes[b]);
     int rc = run_recs(h, h->qr_recs, h->qr_first[b], h->qr_first[b + 1] - h->qr_first[b],
                       "gemm_qr");
     if (rc) return rc;

@@ -9,10 +9,13 @@
 //     (A B^T)_ij = 2^(E_i + F_j - 2044) * sum_g 2^(-8g + 2) * sum_{p+q=g} sum_k dA_p dB_q,
 // and for g = 2..8 (28 digit pairs) the inner integer sums over 128 consecutive k are
 // exact in the FP32 accumulators of the tensor core (|sum| <= 7 * 2^14 * 128 < 2^24);
-// the groups g > 8 lie below the truncation level and are not formed.  Each 128-wide
-// chunk is drained from TMEM into two exact int64 words, and the FP64 result is built
-// from them with integer exponent arithmetic and one rounding add, so C gets the
-// accuracy of an FP64 GEMM with two FP64 operations per element instead of 2K.
+// the groups g > 8 are not formed (each term loses at most 6 * 2^-54 of the product of
+// its row and column maxima to them).  Each 128-wide chunk is drained from TMEM into two
+// exact int64 words, and the FP64 result is built from them with integer exponent
+// arithmetic and one rounding add: two FP64 operations per element instead of 2K, with
+// an error bound normwise per row and column (|C_ij - exact| <= 2^-53 |C_ij| +
+// 2^-54 (max|a_i| sum|b_j| + max|b_j| sum|a_i|) + 6 K 2^-54 max|a_i| max|b_j|) where an
+// FP64 GEMM's is componentwise.
 //
 // Splitting uses only integer and FP32 operations on the FP64 bit pattern.
 // Kernels:
@@ -616,7 +619,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
     const int gi = bi * OZ_M + r;
     const bool row_ok = gi < d.M;
     const unsigned emax = row_ok ? (unsigned)d.Ae[gi] : 0u;
-    const double* rowp = static_cast<const double*>(d.At) + (row_ok ? (size_t)gi * d.a_rs : 0);
+    const double* rowp = static_cast<const double*>(gi < d.lead ? d.At2 : d.At) + (row_ok ? (size_t)gi * d.a_rs : 0);
     const bool vec = ((reinterpret_cast<uintptr_t>(rowp) | (uintptr_t)d.a_rs * 8) & 15) == 0;
     const int quarter = warp & 3, col0 = (ew >> 2) * 8;  // drain: TMEM lane quarter, 8 columns
     const int drow = bi * OZ_M + quarter * 32 + lane;

@@ -18,11 +18,11 @@ namespace elmddm {
 
 namespace {
 
-// One block per subdomain: factor the panel of columns [k0, k0+nbe) over rows [k0, m_s).
+// One block per subdomain: factor the panel of columns [k0, k0+nbe) over rows [k0, m_s)
+// (the fallback for panels whose rows do not fit in the shared memory of an 8-CTA cluster).
 __global__ void __launch_bounds__(256) k_panel_qr(double* __restrict__ K, long long kstride, int ld,
                                                   const int* __restrict__ ms_arr, int k0, int nbe,
                                                   double* __restrict__ tau_out, int n,
-                                                  double* __restrict__ Tout, long long tstride,
                                                   double* __restrict__ Vp, long long vstride,
                                                   unsigned* status) {
   const int s = blockIdx.x;
@@ -31,10 +31,8 @@ __global__ void __launch_bounds__(256) k_panel_qr(double* __restrict__ K, long l
   __shared__ double red[33];
   __shared__ double wred[8][32];
   __shared__ double d[32];
-  __shared__ double T[32][33];
   __shared__ double stau[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < 32 * 33; e += 256) (&T[0][0])[e] = 0.0;
   unsigned bits = 0;
   __syncthreads();
 
@@ -65,9 +63,7 @@ __global__ void __launch_bounds__(256) k_panel_qr(double* __restrict__ K, long l
       for (int r = c + 1 + tid; r < m; r += 256) ac[r] *= scal;
     __syncthreads();
 
-    // d_k = v_j . (column k0+k) over rows >= c, for every other panel column:
-    // for k > j it is the w of H_j applied to column k; for k < j it is v_k . v_j,
-    // the entry the T recurrence needs.
+    // d_k = v_j . (column k0+k) over rows >= c: for k > j the w of H_j applied to column k
     double acc[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc[k] = 0.0;
@@ -97,13 +93,7 @@ __global__ void __launch_bounds__(256) k_panel_qr(double* __restrict__ K, long l
         for (int k = j + 1; k < nbe; ++k) row[(size_t)k * ld] = fma(-tv, d[k], row[(size_t)k * ld]);
       }
     }
-    if (tid < j) {
-      double t = 0.0;
-      for (int l = tid; l < j; ++l) t = fma(T[tid][l], d[l], t);
-      T[tid][j] = -tau * t;
-    }
     if (tid == 0) {
-      T[j][j] = tau;
       stau[j] = tau;
       if (c < m) ac[c] = beta;
     }
@@ -111,8 +101,6 @@ __global__ void __launch_bounds__(256) k_panel_qr(double* __restrict__ K, long l
   }
 
   if (tid < nbe) tau_out[(size_t)s * n + k0 + tid] = stau[tid];
-  double* Ts = Tout + (size_t)s * tstride;
-  for (int e = tid; e < 32 * 32; e += 256) Ts[e] = T[e & 31][e >> 5];
   double* V = Vp + (size_t)s * vstride;
   const int rows = m - k0;
   if (rows > 0) {
@@ -546,30 +534,31 @@ __global__ void __cluster_dims__(AQ_CL, 1, 1) __launch_bounds__(256)
   cluster.sync();  // no CTA leaves while another may still read its results
 }
 
-// Cluster variant of the panel factorisation: the 4 CTAs of a cluster share one
-// subdomain's panel, each holding a contiguous quarter of its rows in shared memory.
-// The norm and the 32 dot products of every column are reduced across the cluster
-// through distributed shared memory (fixed summation order, so every CTA computes the
-// identical reflector and T), with two cluster barriers per column.  Same reflectors,
-// T and R as k_panel_qr; 4x the FP64 throughput per subdomain and no L2 round trips.
 constexpr int PLD = 33;    // shared-memory row stride of the panel chunk (doubles)
 
-// Householder panel of nbe <= 32 columns [k0, k0+nbe) of subdomain s, rows split over a
-// cluster of PCL CTAs (rows k0 + q*rows_per .. in CTA q, held in shared memory).  Column j
-// takes one fused reduction: every thread sums x_r a_k(r) over its rows strictly below the
-// diagonal row c = k0 + j for all 32 columns k (the k = j slot is sigma = |x_below|^2), and
-// the owner of row c contributes a_k(c).  After one cluster barrier every quantity is local:
-//   beta = -sign(alpha) sqrt(alpha^2 + sigma),  tau = (beta - alpha) / beta,
-//   v = (x - beta e_c) / (alpha - beta),  v^T a_k = a_k(c) + y_k / (alpha - beta),
-// which gives the trailing update a_k -= tau v (v^T a_k) and, for l < j, the products
-// v_l^T v_j that build T (compact WY, I - V T V^T).  Rows stay with their threads, so the
-// update needs no barrier before the next column's sums: three barriers per column.
+// Cluster variant of the panel factorisation: the PCL CTAs of a cluster share one
+// subdomain's panel, each holding a contiguous slice of its rows in shared memory.
+// Column j of the panel takes two phases over the CTA's rows, with the threads mapped to
+// (column, row subset) pairs of the columns still active, so that no FP64 work goes to
+// columns already factored and the cross-thread reduction is one add per partial:
+//   phase 1: for the active columns k = j .. nbe-1, y_k = sum of x_r a_k(r) over the rows
+//            strictly below the diagonal row c = k0 + j (k = j gives sigma = |x_below|^2);
+//            partials are summed within each warp (lanes 32 apart modulo the column
+//            count hold the same column), across the 8 warps, then across the cluster
+//            through distributed shared memory in a fixed order, so every CTA computes the
+//            identical reflector;
+//   then     beta = -sign(alpha) sqrt(alpha^2 + sigma),  tau = (beta - alpha) / beta,
+//            v = (x - beta e_c) / (alpha - beta),  v^T a_k = a_k(c) + y_k / (alpha - beta);
+//   phase 2: a_k -= tau v (v^T a_k) for k > j on the rows from c down, written as
+//            a_k(c) -= tau (v^T a_k) and a_k(r) -= [tau (v^T a_k) / (alpha - beta)] x_r,
+//            so column j itself is scaled into v only once, when the panel is written back.
+// The compact-WY factor T is not formed here: the products v_l^T v_j (l < j) it needs come
+// out of the next W1 = V^T A2 product as its first rows (k_form_t).
 template <int PCL>
 __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
     k_panel_qr_cl(double* __restrict__ K, long long kstride, int ld, const int* __restrict__ ms_arr,
-                  int k0, int nbe, double* __restrict__ tau_out, int n, double* __restrict__ Tout,
-                  long long tstride, double* __restrict__ Vp, long long vstride, unsigned* status,
-                  int s_off) {
+                  int k0, int nbe, double* __restrict__ tau_out, int n, double* __restrict__ Vp,
+                  long long vstride, unsigned* status, int s_off) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int q = (int)cluster.block_rank();
@@ -581,14 +570,11 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
   const int r0 = k0 + q * rows_per;                     // first global row of this chunk
   const int nr = max(0, min(rows_per, m - r0));         // rows held here
   extern __shared__ double P[];                         // [rows_per][PLD]
-  __shared__ double red[2][64];                         // [parity]: y_k (sigma at j), a_k(c)
-  __shared__ double wred[8][33];
-  __shared__ double dsh[32];                            // v^T a_k (k > j), v_l^T v_j (l < j)
-  __shared__ double coef[2];                            // tau, 1 / (alpha - beta)
-  __shared__ double T[32][33];
-  __shared__ double stau[32];
+  __shared__ double red[2][64];                         // [parity]: y_k, a_k(c) by column slot
+  __shared__ double wred[8][32];                        // per warp, by column slot
+  __shared__ double cf[32], cfs[32];                    // tau v^T a_k, and divided by (alpha - beta)
+  __shared__ double stau[32], sscal[32];                // tau_j, 1 / (alpha_j - beta_j)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < 32 * 33; e += 256) (&T[0][0])[e] = 0.0;
   for (int k = 0; k < nbe; ++k)
     for (int r = tid; r < nr; r += 256) P[r * PLD + k] = A[(r0 + r) + (size_t)(k0 + k) * ld];
   unsigned bits = 0;
@@ -599,26 +585,30 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
     const int c = k0 + j;
     const int cl = c - r0;                   // local row of c (valid if 0 <= cl < nr)
     const bool own_c = cl >= 0 && cl < nr;
-    double acc[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
-    for (int r = tid; r < nr; r += 256) {
-      if (r0 + r <= c) continue;
-      const double* row = P + r * PLD;
-      const double x = row[j];
-#pragma unroll
-      for (int k = 0; k < 32; ++k)
-        if (k < nbe) acc[k] = fma(x, row[k], acc[k]);
+    const int na = nbe - j;                  // active columns j .. nbe-1, slot = k - j
+    {
+      const int P1 = 256 / na;
+      double acc = 0.0;
+      if (tid < P1 * na) {
+        const int col = j + tid % na, p = tid / na;
+        for (int r = max(0, cl + 1) + p; r < nr; r += P1) acc = fma(P[r * PLD + j], P[r * PLD + col], acc);
+      }
+      // lanes l and l + na hold the same column (thread index modulo na)
+      for (int o = na; o < 32; o <<= 1) {
+        const double v = __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane + o < 32) acc += v;
+      }
+      if (lane < na) wred[warp][(32 * warp + lane) % na] = acc;
     }
-    const double ws = warp_transpose_sum32(acc);
-    wred[warp][lane] = ws;
     __syncthreads();
     if (warp == 0) {
       double t = 0.0;
+      if (lane < na) {
 #pragma unroll
-      for (int w = 0; w < 8; ++w) t += wred[w][lane];
+        for (int w = 0; w < 8; ++w) t += wred[w][lane];
+      }
       red[par][lane] = t;
-      red[par][32 + lane] = (own_c && lane < nbe) ? P[cl * PLD + lane] : 0.0;
+      red[par][32 + lane] = (own_c && lane < na) ? P[cl * PLD + j + lane] : 0.0;
     }
     cluster.sync();
     if (warp == 0) {
@@ -629,8 +619,8 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
         y += rr[lane];
         rc += rr[32 + lane];
       }
-      const double alpha = __shfl_sync(0xffffffffu, rc, j);
-      const double ss = __shfl_sync(0xffffffffu, y, j);
+      const double alpha = __shfl_sync(0xffffffffu, rc, 0);
+      const double ss = __shfl_sync(0xffffffffu, y, 0);
       double beta, tau, scal;
       if (ss == 0.0) {
         tau = 0.0; beta = alpha; scal = 1.0;
@@ -639,64 +629,96 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
         tau = (beta - alpha) / beta;
         scal = 1.0 / (alpha - beta);
       }
-      dsh[lane] = fma(scal, y, rc);
-      __syncwarp();
-      if (lane < j) {
-        double t = 0.0;
-        for (int l = lane; l < j; ++l) t = fma(T[lane][l], dsh[l], t);
-        T[lane][j] = -tau * t;
-      }
+      const double td = tau * fma(scal, y, rc);  // tau v^T a_k for slot `lane`
+      cf[lane] = td;
+      cfs[lane] = td * scal;
       if (lane == 0) {
-        coef[0] = tau;
-        coef[1] = scal;
-        T[j][j] = tau;
         stau[j] = tau;
+        sscal[j] = scal;
         if (q == 0) {
           if (beta == 0.0) bits |= ST_RANK;
           if (!isfinite(beta)) bits |= ST_NONFINITE;
         }
+        if (own_c) P[cl * PLD + j] = beta;  // row c: R_jj (read as alpha above)
       }
-      if (own_c && lane == 0) P[cl * PLD + j] = beta;  // row c: R_jj (read as alpha above)
-      // keep beta for the owner thread's update below through the stored value
     }
     __syncthreads();
-    const double tau = coef[0], scal = coef[1];
-    for (int r = tid; r < nr; r += 256) {
-      const int gr = r0 + r;
-      if (gr < c) continue;
-      double* row = P + r * PLD;
-      const double v = gr == c ? 1.0 : row[j] * scal;
-      if (gr > c) row[j] = v;
-      if (tau != 0.0) {
-        const double tv = tau * v;
-        for (int k = j + 1; k < nbe; ++k) row[k] = fma(-tv, dsh[k], row[k]);
+    const int nu = na - 1;                   // columns j+1 .. nbe-1
+    if (nu > 0 && stau[j] != 0.0) {
+      const int P2 = 256 / nu;
+      if (tid < P2 * nu) {
+        const int sl = 1 + tid % nu, col = j + sl, p = tid / nu;
+        const double b = cfs[sl];
+        if (own_c && p == 0) P[cl * PLD + col] -= cf[sl];
+        for (int r = max(0, cl + 1) + p; r < nr; r += P2)
+          P[r * PLD + col] = fma(-b, P[r * PLD + j], P[r * PLD + col]);
       }
     }
+    __syncthreads();
     par ^= 1;
   }
-  __syncthreads();
 
-  for (int k = 0; k < nbe; ++k)
-    for (int r = tid; r < nr; r += 256) A[(r0 + r) + (size_t)(k0 + k) * ld] = P[r * PLD + k];
+  // R on and above the diagonal, the reflectors (x scaled into v) below it; V explicit
   double* V = Vp + (size_t)s * vstride;
-  for (int e = tid; e < nr * nbe; e += 256) {
-    const int r = e % nr, k = e / nr, gr = r0 + r;
-    V[gr + (size_t)k * ld] = gr < k0 + k ? 0.0 : (gr == k0 + k ? 1.0 : P[r * PLD + k]);
+  for (int k = 0; k < nbe; ++k) {
+    const double sc = sscal[k];
+    for (int r = tid; r < nr; r += 256) {
+      const int gr = r0 + r;
+      double v = P[r * PLD + k];
+      if (gr > k0 + k) v *= sc;
+      A[gr + (size_t)(k0 + k) * ld] = v;
+      V[gr + (size_t)k * ld] = gr < k0 + k ? 0.0 : (gr == k0 + k ? 1.0 : v);
+    }
   }
   if (q == 0) {
     if (tid < nbe) tau_out[(size_t)s * n + k0 + tid] = stau[tid];
-    double* Ts = Tout + (size_t)s * tstride;
-    for (int e = tid; e < 32 * 32; e += 256) Ts[e] = T[e & 31][e >> 5];
     if (tid == 0 && bits) atomicOr(status, bits);
   }
   cluster.sync();  // peers may still read this CTA's reduction slots
 }
 
+// Compact-WY factor of one panel, H_0 ... H_{nb-1} = I - V T V^T (T upper triangular), by
+// the forward column recurrence T_jj = tau_j, T(0:j, j) = -tau_j T(0:j, 0:j) g_j with
+// g_j(l) = v_l^T v_j, l < j: the first nb rows of the panel's W1 product (G[l * 32 + j]).
+// One CTA of 128 threads per subdomain: G and tau are staged in shared memory, and each
+// row i of T is shared by 4 threads (every fourth term of the sum, added by shuffles), so
+// a column of the recurrence costs a few dependent FMAs.
+__global__ void __launch_bounds__(128) k_form_t(const double* __restrict__ G, long long gstride,
+                                               const double* __restrict__ tau, int n, int k0, int nbe,
+                                               double* __restrict__ Tout, long long tstride) {
+  const int s = blockIdx.x, t = threadIdx.x, i = t >> 2, qd = t & 3;
+  __shared__ double T[32][33];
+  __shared__ double Gs[32][33];
+  __shared__ double ts[32];
+  const double* Gp = G + (size_t)s * gstride;
+  for (int e = t; e < 32 * 32; e += 128) {
+    const int l = e >> 5, j = e & 31;
+    Gs[l][j] = (l < nbe && j < nbe) ? Gp[e] : 0.0;
+    T[l][j] = 0.0;
+  }
+  if (t < 32) ts[t] = t < nbe ? tau[(size_t)s * n + k0 + t] : 0.0;
+  __syncthreads();
+  for (int j = 0; j < nbe; ++j) {
+    double p = 0.0;
+    if (i < j)
+      for (int l = i + qd; l < j; l += 4) p = fma(T[i][l], Gs[l][j], p);
+    p += __shfl_xor_sync(0xffffffffu, p, 1);
+    p += __shfl_xor_sync(0xffffffffu, p, 2);
+    if (qd == 0) {
+      if (i < j) T[i][j] = -ts[j] * p;
+      else if (i == j) T[j][j] = ts[j];
+    }
+    __syncthreads();
+  }
+  double* Tp = Tout + (size_t)s * tstride;
+  for (int e = t; e < 32 * 32; e += 128) Tp[e] = T[e & 31][e >> 5];
+}
+
 }  // namespace
 
 cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
-                            int nbe, double* tau, int n, double* T, long long tstride,
-                            double* Vp, long long vstride, unsigned* status, cudaStream_t st) {
+                            int nbe, double* tau, int n, double* Vp, long long vstride, unsigned* status,
+                            cudaStream_t st) {
   // the cluster variant keeps 1/PCL of the rows (up to ld - k0) in shared memory: 4 CTAs
   // per subdomain, or 8 when a quarter of the rows does not fit.  (Splitting the launch
   // into a full wave of 4-CTA clusters and a remainder of 5-CTA clusters measured slower:
@@ -713,15 +735,20 @@ cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms,
     attr = true;
   }
   if (smem4 <= 180 * 1024) {
-    k_panel_qr_cl<4><<<dim3(4, N), 256, smem4, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride,
-                                                     Vp, vstride, status, 0); count_launch();
+    k_panel_qr_cl<4><<<dim3(4, N), 256, smem4, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, Vp, vstride,
+                                                     status, 0); count_launch();
   } else if (smem8 <= 180 * 1024) {
-    k_panel_qr_cl<8><<<dim3(8, N), 256, smem8, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride,
-                                                     Vp, vstride, status, 0); count_launch();
+    k_panel_qr_cl<8><<<dim3(8, N), 256, smem8, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, Vp, vstride,
+                                                     status, 0); count_launch();
   } else {
-    k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, T, tstride, Vp, vstride,
-                                  status); count_launch();
+    k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, Vp, vstride, status); count_launch();
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_form_t(const double* G, long long gstride, const double* tau, int n, int k0, int nbe,
+                          int N, double* T, long long tstride, cudaStream_t st) {
+  k_form_t<<<N, 128, 0, st>>>(G, gstride, tau, n, k0, nbe, T, tstride); count_launch();
   return cudaGetLastError();
 }
 

@@ -279,7 +279,7 @@ class Solver:
     def set_wait_limit(self, seconds: float = 2.0, hold_release: bool = False):
         """Limit of the device-side waits of the triangular solves (hold_release: test hook
         that makes them run out)."""
-        self._check_rc(self.lib.elm_ddm_set_wait_limit(self.h, float(seconds), int(bool(hold_release))))
+        self._check_rc(self.lib.elm_ddm_set_wait_limit(self.h, float(seconds), int(hold_release)))
 
     @property
     def cooperative_solves(self) -> bool:

@@ -3,9 +3,12 @@ tensor-core products the solver's dense updates run on) against an extended-prec
 reference, kernel by kernel.
 
 Bound under test (include/elm_ddm.h): each row of A and B loses less than 2^-54 of its
-largest magnitude to the digit truncation, and each element is rounded once, so
+largest magnitude to the digit truncation, the digit pairs of weight below 2^-62 that
+are not formed add at most 6 * 2^-54 max_k|A_ik| max_k|B_jk| per term, and each element
+is rounded once, so
     |C_ij - (A B^T)_ij| <= 2^-53 |(A B^T)_ij|
-                           + 2^-54 (max_k|A_ik| sum_k|B_jk| + max_k|B_jk| sum_k|A_ik|).
+                           + 2^-54 (max_k|A_ik| sum_k|B_jk| + max_k|B_jk| sum_k|A_ik|)
+                           + 6 K 2^-54 max_k|A_ik| max_k|B_jk|.
 This is normwise per row and column: entries far below their row's largest one get no
 componentwise guarantee, which the test shows on rows spanning more than 40 binades and
 on an upper-triangular factor with kappa ~ 1e14 (the shape of the local R factors).
@@ -38,7 +41,8 @@ def _bound(A, B, exact):
     amax, asum = np.abs(A).max(1), np.abs(A).sum(1)
     bmax, bsum = np.abs(B).max(1), np.abs(B).sum(1)
     trunc = 2.0 ** -54 * (amax[:, None] * bsum[None, :] + bmax[None, :] * asum[:, None])
-    return 2.0 ** -53 * np.abs(exact.astype(np.float64)) + 1.0001 * trunc + 1e-300
+    dropped = 6.0 * A.shape[1] * 2.0 ** -54 * amax[:, None] * bmax[None, :]
+    return 2.0 ** -53 * np.abs(exact.astype(np.float64)) + 1.0001 * (trunc + dropped) + 1e-300
 
 
 def _check(kernel, A, B, alpha=1.0, beta=0.0, C0=None, a_layout="row", b_layout="row"):
