@@ -67,9 +67,11 @@ struct OzDesc {
   // persistent product with GEMM_LOWER: column j of this C is column j + lower_off of the
   // symmetric matrix, so a tile is kept when its first column is on or below the diagonal
   int lower_off = 0;
-  // fused-split launches: rows i < lead of A are read from At2 (same row stride a_rs)
-  // instead of At, so one product can stack two FP64 operands with equal leading dimension
+  // fused-split launches: rows i < lead of A are read from At2 (same row stride a_rs) and
+  // take their exponent bounds from Ae2, instead of At and Ae, so one product can stack
+  // two FP64 operands with equal leading dimension
   const void* At2 = nullptr;
+  const int* Ae2 = nullptr;
   int lead = 0;
 };
 
@@ -129,6 +131,11 @@ cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, doub
 // subdomain into out [N][kmax][2] (zero past each subdomain's count).
 cudaError_t launch_get_points(const double* xy, const double* nrm, int m_max, const int* cnt, int N,
                               int kind, int kmax, double* out, cudaStream_t st);
+// Exponent bound of every column of the assembled [K^s | J] (colexp [N][ncap]): the
+// biased exponent of 1.0001 |column|_2, so that 2^(E - 1022) exceeds every entry the
+// column can hold under orthogonal updates of its rows (0 for a zero column).
+cudaError_t launch_colexp(const double* K, long long kstride, int ld, int ncap, const int* ms, int N,
+                          int* colexp, cudaStream_t st);
 cudaError_t launch_eval(const double* W, const double* b, int N, int n, int npts,
                         const double* xy, const int* owner, const double* c, double* u,
                         double* grad, cudaStream_t st);

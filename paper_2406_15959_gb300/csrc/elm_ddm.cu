@@ -142,6 +142,7 @@ struct elm_ddm_handle {
   double *rv = nullptr, *hv = nullptr, *yv = nullptr, *uv = nullptr;
   int *cnt = nullptr, *ms = nullptr, *mg = nullptr, *dofmap = nullptr, *ifc_dof = nullptr;
   int* perm = nullptr;
+  int* colexp = nullptr;        // [N][ncap] exponent bounds of the columns of [K^s | J] (tensor-core QR)
   unsigned* status = nullptr;
   GemmDesc* gd = nullptr;
   AddDesc* ad = nullptr;
@@ -589,6 +590,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->cinv, (size_t)((ng + CHOL_NB - 1) / CHOL_NB + 1) * CHOL_NB * CHOL_NB) &&
             dev_alloc(h, &h->d_rend, h->chol_rend.size()) && dev_alloc(h, &h->d_jbeg, h->chol_jbeg.size()) &&
             dev_alloc(h, &h->cbar, (size_t)2) &&
+            dev_alloc(h, &h->colexp, h->emulated ? (size_t)N * h->ncap : (size_t)1) &&
             dev_alloc(h, &h->status, 1);
   if (ok && h->use_tabs) {
     const AsmTables& t = h->tabs;
@@ -613,7 +615,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     restmax = std::max(restmax, h->chol_rend[st] - k - std::min(CHOL_NB, ng - k));
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   // (A2^T is split inside the fused product kernel: only its row exponents are stored)
-  const size_t s1 = 0, e1 = al((size_t)(n2max + QR_NB) * 4);
+  const size_t s1 = 0, e1 = 0;  // (unused region)
   const size_t s2 = al(oz_split_elems(QR_NB, mpmax, 32) * 2), e2 = al((size_t)QR_NB * 4);
   const size_t s3 = al(oz_split_elems(mpmax, QR_NB, 128) * 2), e3 = al((size_t)mpmax * 4);
   const size_t s4 = al(oz_split_elems(n2max, QR_NB, 32) * 2), e4 = al((size_t)n2max * 4);
@@ -796,18 +798,19 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
         g3.push_back({V, w2, A2, mp, n2, nbe, ld, QR_NB, ld});
       }
       if (h->emulated) {
-        int* x1 = (int*)sub_region(s, 1);
         void* t2 = sub_region(s, 2); int* x2 = (int*)sub_region(s, 3);
         void* t3 = sub_region(s, 4); int* x3 = (int*)sub_region(s, 5);
         void* t4 = sub_region(s, 6); int* x4 = (int*)sub_region(s, 7);
-        // A = [V | A2]^T (the Gram rows from the explicit reflectors: |v| <= 1 with a unit
-        // diagonal, so the digit split keeps them to FP64 accuracy, where the stored panel
-        // columns would be truncated relative to R's entries): row exponents only
-        sp1.push_back({V, ld, 1, nbe, mp, x1, nullptr, 128});
-        sp1.push_back({A2, ld, 1, n2, mp, x1 + nbe, nullptr, 128});
+        // A = [V | A2]^T, split inside the product: the Gram rows from the explicit
+        // reflectors (|v| <= 1 with a unit diagonal, so the digit split keeps them to FP64
+        // accuracy, where the stored panel columns would be truncated relative to R's
+        // entries), with V's row exponents from its split as the B operand; the rows of
+        // A2^T take the exponent bounds of their columns' original norms, which no
+        // orthogonal update of the column can exceed (no pass over A2 per panel)
         sp1.push_back({V, ld, 1, nbe, mp, x2, t2, 32});              // V^T: rows = panel columns
-        OzDesc ow{PA2, x1, t2, x2, w1, QR_NB, 1, n2 + nbe, nbe, mp, 0, ld};
+        OzDesc ow{PA2, h->colexp + (size_t)s * h->ncap + k0, t2, x2, w1, QR_NB, 1, n2 + nbe, nbe, mp, 0, ld};
         ow.At2 = V;   // rows i < nbe at V + i * ld, rows i >= nbe at PA2 + i * ld = A2
+        ow.Ae2 = x2;
         ow.lead = nbe;
         o1.push_back(ow);
         if (n2 <= 0) continue;
@@ -1133,6 +1136,8 @@ int elm_ddm_assemble(elm_ddm_handle* h, const double* W, const double* b) {
                                    h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr,
                                    h->use_tabs ? &h->tabs : nullptr, h->status, h->st),
                 "assemble", 0.0, h->asm_bytes);
+  if (h->emulated)
+    ELM_LAUNCH(h, launch_colexp(h->K, h->kstride, h->ld, h->ncap, h->ms, h->N, h->colexp, h->st), "colexp");
   h->state = 1;
   return ELM_DDM_OK;
 }

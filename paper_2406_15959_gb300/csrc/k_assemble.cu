@@ -229,7 +229,30 @@ __global__ void k_get_points(const double* __restrict__ xy, const double* __rest
   out[((size_t)s * kmax + i) * 2 + 1] = b;
 }
 
+// Warp per column: E = biased exponent of 1.0001 sqrt(sum of squares) over the rows.
+__global__ void __launch_bounds__(256) k_colexp(const double* __restrict__ K, long long kstride, int ld,
+                                               int ncap, const int* __restrict__ ms, int* __restrict__ colexp) {
+  const int s = blockIdx.y, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= ncap) return;
+  const int m = ms[s];
+  const double* col = K + (size_t)s * kstride + (size_t)j * ld;
+  double acc = 0.0;
+  for (int r = lane; r < m; r += 32) acc = fma(col[r], col[r], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    const double b = sqrt(acc) * 1.0001;
+    colexp[(size_t)s * ncap + j] = acc > 0.0 ? (int)((__double_as_longlong(b) >> 52) & 0x7FF) : 0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_colexp(const double* K, long long kstride, int ld, int ncap, const int* ms, int N,
+                          int* colexp, cudaStream_t st) {
+  k_colexp<<<dim3((ncap + 7) / 8, N), 256, 0, st>>>(K, kstride, ld, ncap, ms, colexp); count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_get_points(const double* xy, const double* nrm, int m_max, const int* cnt, int N,
                               int kind, int kmax, double* out, cudaStream_t st) {

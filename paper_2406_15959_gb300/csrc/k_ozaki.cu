@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
     const int r = ew * 8 + (lane & 7), kg = lane >> 3;
     const int gi = bi * OZ_M + r;
     const bool row_ok = gi < d.M;
-    const unsigned emax = row_ok ? (unsigned)d.Ae[gi] : 0u;
+    const unsigned emax = row_ok ? (unsigned)(gi < d.lead ? d.Ae2 : d.Ae)[gi] : 0u;
     const double* rowp = static_cast<const double*>(gi < d.lead ? d.At2 : d.At) + (row_ok ? (size_t)gi * d.a_rs : 0);
     const bool vec = ((reinterpret_cast<uintptr_t>(rowp) | (uintptr_t)d.a_rs * 8) & 15) == 0;
     const int quarter = warp & 3, col0 = (ew >> 2) * 8;  // drain: TMEM lane quarter, 8 columns
@@ -694,8 +694,9 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
         if (gj < d.N) {
           const int fj = d.Be[gj];
           double v = 0.0;
-          if (d.Ae[drow] != 0 && fj != 0) {
-            const int k = d.Ae[drow] + fj - 2044 - 62;
+          const int ed = (drow < d.lead ? d.Ae2 : d.Ae)[drow];
+          if (ed != 0 && fj != 0) {
+            const int k = ed + fj - 2044 - 62;
             v = i64_to_double_pow2(H[j], k + 24, false) + i64_to_double_pow2(Lw[j], k, false);
           }
           d.C[(size_t)drow * d.c_rs + (size_t)gj * d.c_cs] = v;
