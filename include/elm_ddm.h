@@ -76,6 +76,22 @@ extern "C" {
                                      grids), exp(2 z) is factored into per-neuron tables over
                                      those coordinates (same values to a few ulp) */
 
+#define ELM_DDM_FLAG_MIXED 8  /* mixed precision: elm_ddm_schur factors the local matrices in
+                                     low precision (FP32 Householder panels; BF16 digit-split
+                                     products with FP32 accumulation keeping the 10 leading
+                                     digit pairs, about 28 bits), assembles the Schur matrix and
+                                     factors it in FP64; elm_ddm_solve refines the solution on
+                                     FP64 residuals of the method's system (products with the
+                                     FP64 K^s and A^s, kept from elm_ddm_assemble) until the
+                                     relative u_Gamma correction is <= 1e-12, and falls back to
+                                     the FP64 path (re-assembly, FP64 factorisation, direct
+                                     solve) when refinement stalls.  elm_ddm_get_info keys
+                                     10-13 report the steps, the fallback and the last
+                                     correction.  Not with ELM_DDM_FLAG_FP64_SIMT or
+                                     ELM_DDM_FLAG_SCHUR_CG; the CG entry points return
+                                     ERR_STATE while the factorisation is the low-precision one.
+                                     Needs about one more copy of K^s in device memory */
+
 /* Differential operators. */
 #define ELM_DDM_OP_POISSON 0  /* L = -Laplacian (Eq. (4.4)) */
 #define ELM_DDM_OP_VARCOEF 1  /* L = -div(rho grad) (Section 4, the variable-coefficient
@@ -276,7 +292,11 @@ int elm_ddm_export(elm_ddm_handle* h, int what, int s, double* dst, int ld_dst);
  * 3 = number of Schur-matrix edges (interface blocks), 4 = m_max, 5 = n_neurons,
  * 6 = n_sub, 7 = CUDA kernels launched by the library in this process (all handles),
  * 8 = 1 if elm_ddm_assemble uses the factored activation tables, else 0,
- * 9 = 1 if elm_ddm_solve's triangular solves run as one cooperative launch each, else 0.
+ * 9 = 1 if elm_ddm_solve's triangular solves run as one cooperative launch each, else 0,
+ * 10 = refinement steps of the last mixed-precision solve, 11 = 1 if that solve stalled and
+ * fell back to the FP64 path, 12 = its last relative u_Gamma correction (the c correction
+ * without interface unknowns), the solve's error estimate, 13 = 1 while the current
+ * factorisation is the low-precision one.
  */
 int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value);
 

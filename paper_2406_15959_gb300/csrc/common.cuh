@@ -87,8 +87,11 @@ int oz_tiles(int m, int n, int nt);
 size_t oz_split_elems(int R, int K, int row_tile);
 cudaError_t launch_split(const SplitDesc* d, int count, int max_rows, int max_split_blocks,
                          cudaStream_t st);
+// gmax (2..8): the digit pairs formed are those with p + q <= gmax; 8 (all 28 pairs of
+// weight >= 2^-62) is the FP64-accurate product, smaller values a lower-precision one
+// (5: the 10 leading pairs, an error below about 2^-28 of the row and column maxima).
 cudaError_t launch_ozaki(int nt, const OzDesc* d, int count, int max_tiles, double alpha,
-                         double beta, int flags, unsigned* status, cudaStream_t st);
+                         double beta, int flags, unsigned* status, cudaStream_t st, int gmax = 8);
 // Persistent variant for K <= 64: one CTA per SM walks a tile table of (entry, row tile,
 // column tile) over all 128 x 32 output tiles of the batch.  oz_upd_tile_table (host)
 // writes that table (out may be null to count) and skips the tiles above the diagonal of
@@ -97,11 +100,11 @@ int oz_upd_tile_table(const OzDesc* descs, int count, int flags, int4* out);
 // max_grid > 0 caps the persistent grid (SMs left to work on another stream).
 cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int total_tiles,
                              double alpha, double beta, int flags, unsigned* status,
-                             cudaStream_t st, int max_grid = 0);
+                             cudaStream_t st, int max_grid = 0, int gmax = 8);
 // C = A B^T with the FP64 A split inside the kernel (At = FP64 A, a_rs its row stride, K
 // contiguous; Ae its row exponents), B split as usual with row_tile 32, N <= 32, beta = 0.
 cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned* status,
-                            cudaStream_t st);
+                            cudaStream_t st, int gmax = 8);
 cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_tiles,
                         double alpha, double beta, int flags, cudaStream_t st);
 cudaError_t launch_add_blocks(const AddDesc* d, int count, int max_elems, cudaStream_t st);
@@ -144,7 +147,7 @@ cudaError_t launch_eval(const double* W, const double* b, int N, int n, int npts
 // the explicit reflectors in Vp.  T is formed afterwards by launch_form_t.
 cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
                             int nbe, double* tau, int n, double* Vp, long long vstride, unsigned* status,
-                            cudaStream_t st);
+                            cudaStream_t st, bool fp32 = false);
 // Compact-WY T of panel [k0, k0+nbe) of every subdomain from G (v_l^T v_j at G[l*32 + j],
 // l < j, per subdomain at stride gstride) and tau; T [32 x 32] column-major at T + s*tstride.
 cudaError_t launch_form_t(const double* G, long long gstride, const double* tau, int n, int k0, int nbe,
@@ -222,6 +225,27 @@ cudaError_t launch_pcg_update(double* x, double* r, double* p, const double* q, 
 cudaError_t launch_scatter_perm(const int* idx, int n, const double* src, double* dst, int nrhs,
                                 cudaStream_t st);
 cudaError_t launch_diag_inv(const double* S, int n, double* dinv, cudaStream_t st);
+
+// Mixed-precision refinement (k_refine.cu): FP64 residuals of the (c, w, u) system and
+// the pieces of its correction.  Layouts: e, kw, F [nrhs][N][ld]; c, w, r1, t [nrhs][N][n];
+// z, interface products [nrhs][N][mgld]; u, g [nrhs][ng] (internal interface order).
+cudaError_t launch_resid_rows(const double* K, long long kstride, int ld, int n, const int* ms, const int* cnt,
+                              const int* ifc_dof, int mgld, const double* F, const double* c, const double* w,
+                              const double* u, int ng, int N, int mmax, int nrhs, double* e, double* kw,
+                              double* z, cudaStream_t st);
+cudaError_t launch_resid_cols(const double* K, long long kstride, int ld, int n, const int* ms, const double* e,
+                              const double* kw, int N, int nrhs, double* r1, double* t, cudaStream_t st);
+cudaError_t launch_amul(const double* A, long long astride, int mgld, const int* mg, int mgmax, int n,
+                        const double* x, int N, int nrhs, double* out, cudaStream_t st);
+// out = A^T (E g) + sg * t; with r1 non-NULL also d = r1 - out
+cudaError_t launch_atmul(const double* A, long long astride, int mgld, const int* mg, const int* ifc_dof, int n,
+                         const double* g, int ng, const double* t, double sg, const double* r1, int N, int nrhs,
+                         double* out, double* d, cudaStream_t st);
+// p = R^{-T} v for nvec vectors per subdomain (v at v + (vec N + s) vs, p at p + (vec N + s) ps)
+cudaError_t launch_rt_solve(const double* K, long long kstride, int ld, int n, const double* v, long long vs,
+                            double* p, long long ps, int N, int nvec, cudaStream_t st);
+cudaError_t launch_refine_update(double* c, const double* dc, double* w, const double* dw, long long nc, double* u,
+                                 const double* du, int ng, int nrhs, unsigned long long* nrm, cudaStream_t st);
 
 // ---- device helpers ----
 #ifdef __CUDACC__

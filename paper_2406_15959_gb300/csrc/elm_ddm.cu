@@ -54,6 +54,10 @@ struct Edge {
 
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+// Digit groups g = p + q of the low-precision local products (the 10 leading digit pairs:
+// an error below about 2^-28 of the row and column maxima, against the FP32 panels' 2^-24).
+constexpr int LO_GMAX = 5;
+
 std::string g_setup_error;
 
 // Reverse Cuthill-McKee ordering of a graph given by adjacency lists (self loops
@@ -150,6 +154,21 @@ struct elm_ddm_handle {
   OzDesc* od = nullptr;
   int4* ut = nullptr;  // tile tables of the persistent launches
   bool emulated = true;          // FP64 products on the tensor cores (digit split)
+  // mixed-precision mode (ELM_DDM_FLAG_MIXED): the local factorisation in low precision
+  // (FP32 Householder panels, digit-split products with LO_GMAX groups), the Schur matrix
+  // assembled and factored in FP64, and the solve refined on FP64 residuals
+  bool mixed = false;
+  bool lowfac = false;           // the current factorisation is the low-precision one
+  int refine_maxit = 16;
+  double refine_tol = 1e-12;     // relative size of the last u_Gamma correction
+  int last_iters = 0, last_fallback = 0;
+  double last_eta = 0.0;
+  double *K64 = nullptr, *A64 = nullptr, *F64 = nullptr;  // FP64 K^s (n columns), A^s, F^s
+  double *cit = nullptr, *wit = nullptr, *uit = nullptr;  // iterates c, w, u (internal order)
+  double *dcv = nullptr, *dwv = nullptr, *ebuf = nullptr, *kwbuf = nullptr, *zb = nullptr;
+  double *r1b = nullptr, *r3b = nullptr, *r13b = nullptr, *tb = nullptr, *Pb = nullptr;
+  double *Acl = nullptr, *Acg = nullptr, *zero_ng = nullptr, *gq2 = nullptr, *hq2 = nullptr;
+  unsigned long long* nrmb = nullptr;
   bool cg_only = false;          // S is neither formed nor factored (elm_ddm_solve_cg only)
   int op = ELM_DDM_OP_POISSON;
   double* coef = nullptr;        // [N][m_max][3] rho, grad rho (ELM_DDM_OP_VARCOEF)
@@ -276,7 +295,7 @@ struct ProfScope {
 #define ELM_LAUNCH(h, expr, where) ELM_LAUNCH_F(h, expr, where, 0.0)
 
 int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first, size_t cnt,
-             const char* gemm_name) {
+             const char* gemm_name, int gmax = 8) {
   for (size_t r = first; r < first + cnt && r < recs.size(); ++r) {
     const LaunchRec& L = recs[r];
     if (L.count <= 0) continue;
@@ -291,7 +310,7 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
                     L.bytes);
     else if (L.kind == 3)
       ELM_LAUNCH_FB(h, launch_ozaki(L.nt, h->od + L.off, L.count, L.max_tiles, L.alpha, L.beta,
-                                    L.flags, h->status, h->st), nm, L.flops, L.bytes);
+                                    L.flags, h->status, h->st, gmax), nm, L.flops, L.bytes);
     else if (L.kind == 7)
       ELM_LAUNCH(h, launch_form_t(h->W1, h->wstride, h->tau, h->n, L.off * QR_NB, L.nt, h->N,
                                   h->T + (size_t)L.off * QR_NB * QR_NB, h->tstride, h->st), "form_t");
@@ -303,19 +322,47 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
       {
         ProfScope ps_(h, nm, L.flops, L.bytes, h->st2);
         e_ = launch_ozaki_upd(h->od + L.off, L.count, h->ut + L.toff, L.max_tiles, L.alpha, L.beta,
-                              L.flags, h->status, h->st2, h->sms - 1);
+                              L.flags, h->status, h->st2, h->sms - 1, gmax);
       }
       h->launches++;
       if (e_ != cudaSuccess) return cuda_fail(h, e_, nm);
     } else if (L.kind == 4)
       ELM_LAUNCH_FB(h, launch_ozaki_upd(h->od + L.off, L.count, h->ut + L.toff, L.max_tiles, L.alpha,
-                                        L.beta, L.flags, h->status, h->st), nm, L.flops, L.bytes);
+                                        L.beta, L.flags, h->status, h->st, 0, gmax), nm, L.flops, L.bytes);
     else
-      ELM_LAUNCH_FB(h, launch_ozaki_fa(h->od + L.off, L.count, L.max_tiles, h->status, h->st), nm,
+      ELM_LAUNCH_FB(h, launch_ozaki_fa(h->od + L.off, L.count, L.max_tiles, h->status, h->st, gmax), nm,
                     L.flops, L.bytes);
   }
   return ELM_DDM_OK;
 }
+
+// Step (a) from the handle's theta: K^s, J, A^s (and, in mixed-precision mode, the FP64
+// copies of K^s and A^s that the refinement's residuals use).
+int assemble_launch(elm_ddm_handle* h) {
+  cudaError_t e = cudaMemsetAsync(h->Am, 0, (size_t)h->N * h->astride * sizeof(double), h->st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "assemble: clear A");
+  ELM_LAUNCH_FB(h, launch_assemble(h->K, h->kstride, h->ld, h->ncap, h->Am, h->astride, h->mgld, h->xy,
+                                   h->nrm, h->m_max, h->cnt, h->thW, h->thb, h->N, h->n,
+                                   h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr,
+                                   h->use_tabs ? &h->tabs : nullptr, h->status, h->st),
+                "assemble", 0.0, h->asm_bytes);
+  if (h->emulated)
+    ELM_LAUNCH(h, launch_colexp(h->K, h->kstride, h->ld, h->ncap, h->ms, h->N, h->colexp, h->st), "colexp");
+  if (h->mixed) {
+    const size_t col = (size_t)h->ld * h->n * sizeof(double);
+    e = cudaMemcpy2DAsync(h->K64, col, h->K, (size_t)h->kstride * sizeof(double), col, h->N,
+                          cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->A64, h->Am, (size_t)h->N * h->astride * sizeof(double), cudaMemcpyDeviceToDevice,
+                          h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "assemble: FP64 copies");
+  }
+  h->state = 1;
+  return ELM_DDM_OK;
+}
+
+int solve_refined(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c);
+int chol_solves(elm_ddm_handle* h, int nrhs);
 
 }  // namespace
 
@@ -335,8 +382,12 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const int max_rhs = desc->max_rhs == 0 ? 1 : desc->max_rhs;
   if (max_rhs < 1 || max_rhs > 64) return fail(nullptr, ELM_DDM_ERR_ARG, "max_rhs must be in 1..64");
   if (n > TRSV_MAX_N) return fail(nullptr, ELM_DDM_ERR_ARG, "n_neurons > 8192 is not supported");
-  if (desc->flags & ~(ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG | ELM_DDM_FLAG_DIRECT_ASSEMBLY))
+  if (desc->flags & ~(ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG | ELM_DDM_FLAG_DIRECT_ASSEMBLY |
+                      ELM_DDM_FLAG_MIXED))
     return fail(nullptr, ELM_DDM_ERR_ARG, "unknown flags");
+  if ((desc->flags & ELM_DDM_FLAG_MIXED) && (desc->flags & (ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG)))
+    return fail(nullptr, ELM_DDM_ERR_ARG,
+                "ELM_DDM_FLAG_MIXED needs the tensor-core back end and the direct Schur solve");
   if ((long long)N * m_max > (1ll << 31)) return fail(nullptr, ELM_DDM_ERR_ARG, "geometry too large");
 
   auto h = new elm_ddm_handle();
@@ -345,6 +396,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->N = N; h->n = n; h->m_max = m_max; h->ng = ng; h->max_rhs = max_rhs;
   h->emulated = !(desc->flags & ELM_DDM_FLAG_FP64_SIMT);
   h->cg_only = (desc->flags & ELM_DDM_FLAG_SCHUR_CG) != 0;
+  h->mixed = (desc->flags & ELM_DDM_FLAG_MIXED) != 0;
   h->op = desc->op;
   h->cnt_h.assign(counts, counts + 3 * N);
   h->ms_h.resize(N); h->mg_h.resize(N);
@@ -481,6 +533,10 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
 
   // ---- sizes ----
   h->ld = round_up(std::max(msmax, 1), 32);
+  if (h->mixed && (size_t)((h->ld + 7) / 8) * 33 * sizeof(float) > 180 * 1024) {
+    delete h;
+    return fail(nullptr, ELM_DDM_ERR_ARG, "ELM_DDM_FLAG_MIXED: too many rows per subdomain for the FP32 panels");
+  }
   h->mgmax = mgmax;
   h->mgld = round_up(std::max(mgmax, 1), 32);
   h->ncap = n + mgmax;
@@ -592,6 +648,19 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->cbar, (size_t)2) &&
             dev_alloc(h, &h->colexp, h->emulated ? (size_t)N * h->ncap : (size_t)1) &&
             dev_alloc(h, &h->status, 1);
+  if (ok && h->mixed) {
+    const size_t R = (size_t)max_rhs, ngs = (size_t)std::max(ng, 1);
+    const size_t xn = R * N * h->ld, cn = R * N * n, gn = R * N * h->mgld;
+    ok = dev_alloc(h, &h->K64, (size_t)N * h->ld * n) && dev_alloc(h, &h->A64, (size_t)N * h->astride) &&
+         dev_alloc(h, &h->F64, xn) && dev_alloc(h, &h->cit, cn) && dev_alloc(h, &h->wit, cn) &&
+         dev_alloc(h, &h->uit, R * ngs) && dev_alloc(h, &h->dcv, cn) && dev_alloc(h, &h->dwv, cn) &&
+         dev_alloc(h, &h->ebuf, xn) && dev_alloc(h, &h->kwbuf, xn) && dev_alloc(h, &h->zb, gn) &&
+         dev_alloc(h, &h->r1b, cn) && dev_alloc(h, &h->r3b, cn) && dev_alloc(h, &h->r13b, cn) &&
+         dev_alloc(h, &h->tb, cn) && dev_alloc(h, &h->Pb, 2 * xn) && dev_alloc(h, &h->Acl, gn) &&
+         dev_alloc(h, &h->Acg, R * ngs) && dev_alloc(h, &h->zero_ng, R * ngs) &&
+         dev_alloc(h, &h->gq2, 2 * gn) && dev_alloc(h, &h->hq2, 2 * gn) && dev_alloc(h, &h->nrmb, 4 * R);
+    if (ok) ok = cudaMemset(h->zero_ng, 0, R * ngs * sizeof(double)) == cudaSuccess;
+  }
   if (ok && h->use_tabs) {
     const AsmTables& t = h->tabs;
     ok = dev_alloc(h, &h->tab_xs, (size_t)N * t.nxmax) && dev_alloc(h, &h->tab_ys, (size_t)N * t.nymax) &&
@@ -1129,43 +1198,38 @@ int elm_ddm_assemble(elm_ddm_handle* h, const double* W, const double* b) {
   const size_t nw = (size_t)h->N * h->n;
   cudaError_t e = cudaMemcpyAsync(h->thW, W, nw * 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->thb, b, nw * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->Am, 0, (size_t)h->N * h->astride * sizeof(double), h->st);
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble: copy theta");
-  ELM_LAUNCH_FB(h, launch_assemble(h->K, h->kstride, h->ld, h->ncap, h->Am, h->astride, h->mgld, h->xy,
-                                   h->nrm, h->m_max, h->cnt, h->thW, h->thb, h->N, h->n,
-                                   h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr,
-                                   h->use_tabs ? &h->tabs : nullptr, h->status, h->st),
-                "assemble", 0.0, h->asm_bytes);
-  if (h->emulated)
-    ELM_LAUNCH(h, launch_colexp(h->K, h->kstride, h->ld, h->ncap, h->ms, h->N, h->colexp, h->st), "colexp");
-  h->state = 1;
-  return ELM_DDM_OK;
+  h->lowfac = h->mixed;  // the next factorisation is the low-precision one
+  return assemble_launch(h);
 }
 
 int elm_ddm_schur(elm_ddm_handle* h) {
   if (!h) return ELM_DDM_ERR_ARG;
   if (h->state != 1) return fail(h, ELM_DDM_ERR_STATE, "schur: call elm_ddm_assemble first");
+  // digit groups of the local products (QR, Y, D_s, M_s): all of them, or the leading ones of
+  // the low-precision factorisation; the Schur matrix's M^T M and Cholesky stay FP64
+  const int lo_gmax = h->lowfac ? LO_GMAX : 8;
   // (b) blocked Householder QR of [K^s | J]
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, h->n - k0);
     ELM_LAUNCH_FB(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->Vp,
-                                     h->vstride, h->status, h->st), "panel_qr", h->panel_flops[b],
+                                     h->vstride, h->status, h->st, h->lowfac), "panel_qr", h->panel_flops[b],
                   h->panel_bytes[b]);
     int rc = run_recs(h, h->qr_recs, h->qr_first[b], h->qr_first[b + 1] - h->qr_first[b],
-                      "gemm_qr");
+                      "gemm_qr", lo_gmax);
     if (rc) return rc;
   }
   h->state = 0;  // K is factored in place: assemble again before another schur
   if (h->ng > 0) {
     int rc;
     if (h->emulated) {
-      rc = run_recs(h, h->ty_recs, 0, h->ty_recs.size(), "trsm_y");
+      rc = run_recs(h, h->ty_recs, 0, h->ty_recs.size(), "trsm_y", lo_gmax);
       if (rc) return rc;
     } else {
       ELM_LAUNCH(h, launch_trsm_y(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg, h->mgmax,
                                   h->N, h->n, h->st), "trsm_y");
     }
-    rc = run_recs(h, h->dm_recs, 0, h->dm_recs.size(), "gemm_dm");
+    rc = run_recs(h, h->dm_recs, 0, h->dm_recs.size(), "gemm_dm", lo_gmax);
     if (rc) return rc;
     if (h->cg_only) {  // D_s and M_s are all that elm_ddm_solve_cg needs
       h->state = 2;
@@ -1247,6 +1311,11 @@ int elm_ddm_schur(elm_ddm_handle* h) {
 int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c) {
   if (!h) return ELM_DDM_ERR_ARG;
   if (h->state != 2) return fail(h, ELM_DDM_ERR_STATE, "solve: call elm_ddm_schur first");
+  if (h->lowfac) {
+    if (!rhs || !c) return fail(h, ELM_DDM_ERR_ARG, "solve: NULL rhs or c");
+    if (nrhs < 1 || nrhs > h->max_rhs) return fail(h, ELM_DDM_ERR_ARG, "solve: nrhs out of range");
+    return solve_refined(h, rhs, nrhs, u_gamma, c);
+  }
   if (h->cg_only)
     return fail(h, ELM_DDM_ERR_STATE, "solve: S is not factored (ELM_DDM_FLAG_SCHUR_CG); use elm_ddm_solve_cg");
   if (!rhs || !c) return fail(h, ELM_DDM_ERR_ARG, "solve: NULL rhs or c");
@@ -1264,6 +1333,24 @@ int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
     ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, h->mgld, h->mg, h->ifc_dof, h->hv, ng, N, nrhs, h->zv,
                               h->st), "mt_h");
     ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
+    const int rc = chol_solves(h, nrhs);
+    if (rc) return rc;
+  }
+  ELM_LAUNCH(h, launch_backsolve(h->X, h->K, h->kstride, h->ld, h->mg, h->ifc_dof, h->mgld,
+                                 ng > 0 ? h->uv : h->rv, ng, N, n, nrhs, c, h->st), "backsolve");
+  if (u_gamma && ng > 0)
+    ELM_LAUNCH(h, launch_gather_perm(h->perm, ng, h->uv, u_gamma, nrhs, h->st), "gather_u");
+  return ELM_DDM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// u = S^{-1} r for nrhs vectors (rv -> yv -> uv) with the Cholesky factor in S.
+int chol_solves(elm_ddm_handle* h, int nrhs) {
+  const int ng = h->ng;
+  {
     const int nsteps = (int)h->chol_rend.size();
     if (h->fwd_grid > 0 && h->bwd_grid > 0) {
       ELM_LAUNCH(h, launch_chol_fwd_all(h->S, ng, ng, h->cinv, h->d_rend, nsteps, h->rv, h->yv, nrhs,
@@ -1288,20 +1375,131 @@ int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
       }
     }
   }
-  ELM_LAUNCH(h, launch_backsolve(h->X, h->K, h->kstride, h->ld, h->mg, h->ifc_dof, h->mgld,
-                                 ng > 0 ? h->uv : h->rv, ng, N, n, nrhs, c, h->st), "backsolve");
-  if (u_gamma && ng > 0)
-    ELM_LAUNCH(h, launch_gather_perm(h->perm, ng, h->uv, u_gamma, nrhs, h->st), "gather_u");
   return ELM_DDM_OK;
 }
 
-}  // extern "C"
+// Solve of the mixed-precision mode.  Iterates (c, w, u) of the block system in k_refine.cu
+// start at zero; every step takes the FP64 residual (products with the FP64 K^s, A^s) and
+// adds the correction the low-precision factors give by the elimination of Eq. (3.5):
+//   p1 = R^{-T} r1,  p13 = R^{-T} (r1 - r3),
+//   S du = r2 + sum_s E_s^T Q_G p13 + M^T h,  h = sum_s E_s^T Y p1,
+//   dc = R^{-1} (p1 + Q_G^T E du),  dw = R^{-1} R^{-T} (r3 + A^T A dc).
+// It stops when the relative u_Gamma correction eta (the c correction when there is no
+// interface) is at most refine_tol, or below 1e-10 and no longer contracting (the rounding
+// floor).  Otherwise -- a step from the third on that does not halve eta, a correction that
+// is not finite, refine_maxit steps -- refinement has stalled: the handle falls back to the
+// FP64 path (re-assembly from theta, FP64 factorisation, direct solve), which also serves
+// the later solves until the next elm_ddm_assemble.
+int solve_refined(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c) {
+  const int N = h->N, n = h->n, ng = h->ng, ld = h->ld, mgld = h->mgld;
+  const size_t cn = (size_t)nrhs * N * n, xn = (size_t)nrhs * N * ld;
+  const long long k64 = (long long)ld * n;
+  int mmax = 0;
+  for (int s = 0; s < N; ++s) mmax = std::max(mmax, h->ms_h[s]);
+  ELM_LAUNCH(h, launch_load_rhs(h->F64, rhs, N, h->m_max, ld, h->cnt, nrhs, h->status, h->st), "load_rhs");
+  cudaError_t e = cudaMemsetAsync(h->cit, 0, cn * sizeof(double), h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->wit, 0, cn * sizeof(double), h->st);
+  if (e == cudaSuccess && ng > 0) e = cudaMemsetAsync(h->uit, 0, (size_t)nrhs * ng * sizeof(double), h->st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "solve: refinement start");
+  const double* ug = ng > 0 ? h->uv : h->zero_ng;  // the u_Gamma correction (zero without interface)
+  std::vector<unsigned long long> nb(4 * (size_t)nrhs);
+  double eta = INFINITY, eta_prev = INFINITY;
+  bool converged = false;
+  int steps = 0;
+  for (int it = 0; it < h->refine_maxit; ++it) {
+    // FP64 residual: e = F - K c + [0; 0; E u], z = -(e + K w) (interface rows), r1 = K^T e,
+    // r3 = A^T (A c) - K^T K w, r13 = r1 - r3
+    ELM_LAUNCH(h, launch_resid_rows(h->K64, k64, ld, n, h->ms, h->cnt, h->ifc_dof, mgld, h->F64, h->cit, h->wit,
+                                    h->uit, ng, N, mmax, nrhs, h->ebuf, h->kwbuf, h->zb, h->st), "refine_resid");
+    ELM_LAUNCH(h, launch_resid_cols(h->K64, k64, ld, n, h->ms, h->ebuf, h->kwbuf, N, nrhs, h->r1b, h->tb, h->st),
+               "refine_resid");
+    if (ng > 0) {
+      ELM_LAUNCH(h, launch_amul(h->A64, h->astride, mgld, h->mg, h->mgmax, n, h->cit, N, nrhs, h->Acl, h->st),
+                 "refine_resid");
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->Acl, h->Acg, 0, nrhs, h->st), "refine_resid");
+    }
+    ELM_LAUNCH(h, launch_atmul(h->A64, h->astride, mgld, h->mg, h->ifc_dof, n, ng > 0 ? h->Acg : h->zero_ng, ng,
+                               h->tb, -1.0, h->r1b, N, nrhs, h->r3b, h->r13b, h->st), "refine_resid");
+    // correction through the low-precision factors
+    ELM_LAUNCH(h, launch_rt_solve(h->K, h->kstride, ld, n, h->r1b, n, h->Pb, ld, N, nrhs, h->st), "refine_rt");
+    ELM_LAUNCH(h, launch_rt_solve(h->K, h->kstride, ld, n, h->r13b, n, h->Pb + xn, ld, N, nrhs, h->st),
+               "refine_rt");
+    if (ng > 0) {
+      const size_t gslot = (size_t)nrhs * N * mgld;
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->zb, h->rv, 0, nrhs, h->st), "gather_r");
+      ELM_LAUNCH(h, launch_iface_vecs(h->Pb, h->K, h->kstride, ld, h->Am, h->astride, mgld, h->mg, N, n, 2 * nrhs,
+                                      h->gq2, h->hq2, h->st), "iface_vecs");
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->gq2 + gslot, h->rv, 1, nrhs, h->st), "gather_r");
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->hq2, h->hv, 0, nrhs, h->st), "gather_h");
+      ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, mgld, h->mg, h->ifc_dof, h->hv, ng, N, nrhs, h->zv, h->st),
+                 "mt_h");
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
+      const int rc = chol_solves(h, nrhs);
+      if (rc) return rc;
+    }
+    ELM_LAUNCH(h, launch_backsolve(h->Pb, h->K, h->kstride, ld, h->mg, h->ifc_dof, mgld, ug, ng, N, n, nrhs,
+                                   h->dcv, h->st), "backsolve");
+    if (ng > 0) {
+      ELM_LAUNCH(h, launch_amul(h->A64, h->astride, mgld, h->mg, h->mgmax, n, h->dcv, N, nrhs, h->Acl, h->st),
+                 "refine_resid");
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->Acl, h->Acg, 0, nrhs, h->st), "refine_resid");
+    }
+    ELM_LAUNCH(h, launch_atmul(h->A64, h->astride, mgld, h->mg, h->ifc_dof, n, ng > 0 ? h->Acg : h->zero_ng, ng,
+                               h->r3b, 1.0, nullptr, N, nrhs, h->r13b, nullptr, h->st), "refine_resid");
+    ELM_LAUNCH(h, launch_rt_solve(h->K, h->kstride, ld, n, h->r13b, n, h->Pb, ld, N, nrhs, h->st), "refine_rt");
+    ELM_LAUNCH(h, launch_backsolve(h->Pb, h->K, h->kstride, ld, h->mg, h->ifc_dof, mgld, h->zero_ng, ng, N, n,
+                                   nrhs, h->dwv, h->st), "backsolve");
+    e = cudaMemsetAsync(h->nrmb, 0, 4 * (size_t)nrhs * sizeof(unsigned long long), h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "solve: refinement norms");
+    ELM_LAUNCH(h, launch_refine_update(h->cit, h->dcv, h->wit, h->dwv, (long long)N * n, h->uit, ug, ng, nrhs,
+                                       h->nrmb, h->st), "refine_update");
+    e = cudaMemcpyAsync(nb.data(), h->nrmb, nb.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "solve: refinement norms");
+    steps = it + 1;
+    eta = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+      double v[4];
+      for (int q = 0; q < 4; ++q) memcpy(&v[q], &nb[4 * (size_t)r + q], sizeof(double));
+      const double er = ng > 0 ? (v[1] > 0.0 ? v[0] / v[1] : (v[0] > 0.0 ? INFINITY : 0.0))
+                               : (v[3] > 0.0 ? v[2] / v[3] : (v[2] > 0.0 ? INFINITY : 0.0));
+      eta = std::isnan(er) || std::isnan(eta) ? NAN : std::max(eta, er);
+    }
+    if (!std::isfinite(eta)) break;
+    if (eta <= h->refine_tol) { converged = true; break; }
+    if (it >= 2 && eta > 0.5 * eta_prev) {
+      converged = eta <= 1e-10;  // the rounding floor above refine_tol
+      break;
+    }
+    eta_prev = eta;
+  }
+  h->last_iters = steps;
+  h->last_eta = eta;
+  if (!converged) {
+    h->last_fallback = 1;
+    h->lowfac = false;
+    int rc = assemble_launch(h);
+    if (rc == ELM_DDM_OK) rc = elm_ddm_schur(h);
+    if (rc == ELM_DDM_OK) rc = elm_ddm_solve(h, rhs, nrhs, u_gamma, c);
+    return rc;
+  }
+  h->last_fallback = 0;
+  e = cudaMemcpyAsync(c, h->cit, cn * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "solve: refined c");
+  if (u_gamma && ng > 0)
+    ELM_LAUNCH(h, launch_gather_perm(h->perm, ng, h->uit, u_gamma, nrhs, h->st), "gather_u");
+  return ELM_DDM_OK;
+}
+
+}  // namespace
 
 static int solve_cg_impl(elm_ddm_handle* h, const double* rhs, int nrhs, const double* x0, int jacobi,
                          double tol, int maxit, double* u_gamma, double* c, int* iters) {
   if (!h) return ELM_DDM_ERR_ARG;
   if (iters) *iters = 0;
   if (h->state != 2) return fail(h, ELM_DDM_ERR_STATE, "solve_cg: call elm_ddm_schur first");
+  if (h->lowfac)
+    return fail(h, ELM_DDM_ERR_STATE, "solve_cg: the factorisation is the low-precision one (ELM_DDM_FLAG_MIXED)");
   if (!rhs || !c) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: NULL rhs or c");
   if (nrhs < 1 || nrhs > h->max_rhs) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: nrhs out of range");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: tol must be > 0");
@@ -1536,6 +1734,10 @@ int elm_ddm_get_info(const elm_ddm_handle* h, int key, double* value) {
     case 7: *value = (double)elmddm::g_kernel_launches.load(); break;
     case 8: *value = h->use_tabs ? 1.0 : 0.0; break;
     case 9: *value = (h->fwd_grid > 0 && h->bwd_grid > 0) ? 1.0 : 0.0; break;
+    case 10: *value = h->last_iters; break;
+    case 11: *value = h->last_fallback; break;
+    case 12: *value = h->last_eta; break;
+    case 13: *value = h->lowfac ? 1.0 : 0.0; break;
     case 5: *value = h->n; break;
     case 6: *value = h->N; break;
     default: return ELM_DDM_ERR_ARG;

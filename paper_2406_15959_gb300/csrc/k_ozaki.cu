@@ -251,7 +251,7 @@ struct OzSmem {
 
 template <int NT>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restrict__ descs, double alpha,
-                                                        double beta, int flags, unsigned* status) {
+                                                        double beta, int flags, unsigned* status, int gmax) {
   using L = OzSmem<NT>;
   const OzDesc d = descs[blockIdx.y];
   const int tiles_m = (d.M + OZ_M - 1) / OZ_M, tiles_n = (d.N + NT - 1) / NT;
@@ -339,6 +339,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
         for (int t = 0; t < 2; ++t) {
 #pragma unroll
           for (int g = 2; g <= OZ_S + 1; ++g) {
+            if (g > gmax) continue;  // digit groups beyond gmax are not formed
 #pragma unroll
             for (int p = 1; p <= OZ_S; ++p) {
               const int q = g - p;
@@ -415,7 +416,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
           uint32_t v[OZ_G][8];
           if (nchunk == 1) {
 #pragma unroll
-            for (int g = 0; g < OZ_G; ++g) tmem_ld8(lane_base + g * NT + cb * 8, v[g]);
+            for (int g = 0; g < OZ_G; ++g) {
+              if (g + 2 <= gmax) tmem_ld8(lane_base + g * NT + cb * 8, v[g]);
+              else for (int j = 0; j < 8; ++j) v[g][j] = 0u;
+            }
             asm volatile("tcgen05.wait::ld.sync.aligned;");
           } else {
 #pragma unroll
@@ -448,7 +452,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
         for (int cb = 0; cb < NT / 8; ++cb) {
           uint32_t v[OZ_G][8];
 #pragma unroll
-          for (int g = 0; g < OZ_G; ++g) tmem_ld8(lane_base + g * NT + cb * 8, v[g]);
+          for (int g = 0; g < OZ_G; ++g) {
+              if (g + 2 <= gmax) tmem_ld8(lane_base + g * NT + cb * 8, v[g]);
+              else for (int j = 0; j < 8; ++j) v[g][j] = 0u;
+            }
           asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
@@ -505,7 +512,7 @@ static_assert(FA_SMEM <= 227 * 1024, "fused product exceeds the shared memory of
 static_assert(FA_WORKERS * 32 == 4 * OZ_M, "one worker thread per (row, 8-wide k group)");
 
 __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __restrict__ descs,
-                                                           unsigned* status) {
+                                                           unsigned* status, int gmax) {
   const OzDesc d = descs[blockIdx.y];
   const int tiles_m = (d.M + OZ_M - 1) / OZ_M;
   if ((int)blockIdx.x >= tiles_m) return;
@@ -591,6 +598,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
         for (int t = 0; t < 2; ++t) {
 #pragma unroll
           for (int g = 2; g <= OZ_S + 1; ++g) {
+            if (g > gmax) continue;  // digit groups beyond gmax are not formed
 #pragma unroll
             for (int p = 1; p <= OZ_S; ++p) {
               const int q = g - p;
@@ -651,7 +659,10 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
       for (int half = 0; half < 2; ++half) {
         uint32_t v[OZ_G][4];
 #pragma unroll
-        for (int g = 0; g < OZ_G; ++g) tmem_ld4(lb + g * 32 + half * 4, v[g]);
+        for (int g = 0; g < OZ_G; ++g) {
+          if (g + 2 <= gmax) tmem_ld4(lb + g * 32 + half * 4, v[g]);
+          else for (int j = 0; j < 4; ++j) v[g][j] = 0u;
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         if (half == 1) {
           asm volatile("tcgen05.fence::before_thread_sync;");
@@ -744,7 +755,7 @@ template <int EMODE, bool IDENT>
 __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __restrict__ descs,
                                                              const int4* __restrict__ tiles,
                                                              int total_tiles, double alpha,
-                                                             double beta, unsigned* status) {
+                                                             double beta, unsigned* status, int gmax) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sbase = smem_u32(smem);
@@ -818,6 +829,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
           for (int k = 0; k < 2; ++k) {
 #pragma unroll
             for (int g = 2; g <= OZ_S + 1; ++g) {
+            if (g > gmax) continue;  // digit groups beyond gmax are not formed
 #pragma unroll
               for (int p = 1; p <= OZ_S; ++p) {
                 const int q = g - p;
@@ -888,7 +900,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
       for (int half = 0; half < 2; ++half) {
         uint32_t v[OZ_G][4];
 #pragma unroll
-        for (int g = 0; g < OZ_G; ++g) tmem_ld4(lb + g * UPD_NT + half * 4, v[g]);
+        for (int g = 0; g < OZ_G; ++g) {
+          if (g + 2 <= gmax) tmem_ld4(lb + g * UPD_NT + half * 4, v[g]);
+          else for (int j = 0; j < 4; ++j) v[g][j] = 0u;
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         if (half == 1) {
           asm volatile("tcgen05.fence::before_thread_sync;");
@@ -936,7 +951,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
 
 template <int NT>
 cudaError_t launch_oz(const OzDesc* d, int count, int max_tiles, double alpha, double beta,
-                      int flags, unsigned* status, cudaStream_t st) {
+                      int flags, unsigned* status, cudaStream_t st, int gmax) {
   static bool attr = false;
   const int smem = OzSmem<NT>::TOTAL;
   if (!attr) {
@@ -946,7 +961,8 @@ cudaError_t launch_oz(const OzDesc* d, int count, int max_tiles, double alpha, d
   }
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
-    k_ozaki<NT><<<dim3(max_tiles, c), OZ_THREADS, smem, st>>>(d + off, alpha, beta, flags, status); count_launch();
+    k_ozaki<NT><<<dim3(max_tiles, c), OZ_THREADS, smem, st>>>(d + off, alpha, beta, flags, status, gmax);
+    count_launch();
   }
   return cudaGetLastError();
 }
@@ -987,8 +1003,9 @@ int oz_upd_tile_table(const OzDesc* descs, int count, int flags, int4* out) {
 
 cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int total_tiles,
                              double alpha, double beta, int flags, unsigned* status, cudaStream_t st,
-                             int max_grid) {
+                             int max_grid, int gmax) {
   if (count <= 0 || total_tiles <= 0) return cudaSuccess;
+  if (gmax < 2 || gmax > OZ_S + 1) return cudaErrorInvalidValue;
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -1010,7 +1027,7 @@ cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int 
   const int mode = (beta == 0.0 && unit) ? 0 : (beta == 1.0 && unit) ? 1 : 2;
   const bool ident = (flags & GEMM_ADD_IDENTITY) != 0;
 #define ELM_UPD(M, I) \
-  k_ozaki_upd<M, I><<<grid, UPD_THREADS, UPD_SMEM, st>>>(d, tiles, total_tiles, alpha, beta, status)
+  k_ozaki_upd<M, I><<<grid, UPD_THREADS, UPD_SMEM, st>>>(d, tiles, total_tiles, alpha, beta, status, gmax)
   if (mode == 0) { if (ident) ELM_UPD(0, true); else ELM_UPD(0, false); }
   else if (mode == 1) { if (ident) ELM_UPD(1, true); else ELM_UPD(1, false); }
   else { if (ident) ELM_UPD(2, true); else ELM_UPD(2, false); }
@@ -1020,8 +1037,9 @@ cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int 
 }
 
 cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned* status,
-                            cudaStream_t st) {
+                            cudaStream_t st, int gmax) {
   if (count <= 0 || max_tiles <= 0) return cudaSuccess;
+  if (gmax < 2 || gmax > OZ_S + 1) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_ozaki_fa, cudaFuncAttributeMaxDynamicSharedMemorySize, FA_SMEM);
@@ -1030,16 +1048,17 @@ cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned*
   }
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
-    k_ozaki_fa<<<dim3(max_tiles, c), FA_THREADS, FA_SMEM, st>>>(d + off, status); count_launch();
+    k_ozaki_fa<<<dim3(max_tiles, c), FA_THREADS, FA_SMEM, st>>>(d + off, status, gmax); count_launch();
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_ozaki(int nt, const OzDesc* d, int count, int max_tiles, double alpha,
-                         double beta, int flags, unsigned* status, cudaStream_t st) {
+                         double beta, int flags, unsigned* status, cudaStream_t st, int gmax) {
   if (count <= 0 || max_tiles <= 0) return cudaSuccess;
-  if (nt == 32) return launch_oz<32>(d, count, max_tiles, alpha, beta, flags, status, st);
-  return launch_oz<64>(d, count, max_tiles, alpha, beta, flags, status, st);
+  if (gmax < 2 || gmax > OZ_S + 1) return cudaErrorInvalidValue;
+  if (nt == 32) return launch_oz<32>(d, count, max_tiles, alpha, beta, flags, status, st, gmax);
+  return launch_oz<64>(d, count, max_tiles, alpha, beta, flags, status, st, gmax);
 }
 
 }  // namespace elmddm

@@ -553,8 +553,11 @@ constexpr int PLD = 33;    // shared-memory row stride of the panel chunk (doubl
 //            a_k(c) -= tau (v^T a_k) and a_k(r) -= [tau (v^T a_k) / (alpha - beta)] x_r,
 //            so column j itself is scaled into v only once, when the panel is written back.
 // The compact-WY factor T is not formed here: the products v_l^T v_j (l < j) it needs come
-// out of the next W1 = V^T A2 product as its first rows (k_form_t).
-template <int PCL>
+// out of the next W1 = V^T A2 product as its first rows (k_form_t).  T = double is the
+// FP64 path; T = float gives the low-precision factorisation of the mixed-precision mode
+// (the FP32 pipe is some 60 times the FP64 pipe; every value stays FP32 until the panel
+// is written back as FP64).
+template <int PCL, typename T>
 __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
     k_panel_qr_cl(double* __restrict__ K, long long kstride, int ld, const int* __restrict__ ms_arr,
                   int k0, int nbe, double* __restrict__ tau_out, int n, double* __restrict__ Vp,
@@ -569,14 +572,15 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
   const int rows_per = (mp + PCL - 1) / PCL;
   const int r0 = k0 + q * rows_per;                     // first global row of this chunk
   const int nr = max(0, min(rows_per, m - r0));         // rows held here
-  extern __shared__ double P[];                         // [rows_per][PLD]
-  __shared__ double red[2][64];                         // [parity]: y_k, a_k(c) by column slot
-  __shared__ double wred[8][32];                        // per warp, by column slot
-  __shared__ double cf[32], cfs[32];                    // tau v^T a_k, and divided by (alpha - beta)
-  __shared__ double stau[32], sscal[32];                // tau_j, 1 / (alpha_j - beta_j)
+  extern __shared__ __align__(16) unsigned char panel_smem[];
+  T* P = reinterpret_cast<T*>(panel_smem);              // [rows_per][PLD]
+  __shared__ T red[2][64];                         // [parity]: y_k, a_k(c) by column slot
+  __shared__ T wred[8][32];                        // per warp, by column slot
+  __shared__ T cf[32], cfs[32];                    // tau v^T a_k, and divided by (alpha - beta)
+  __shared__ T stau[32], sscal[32];                // tau_j, 1 / (alpha_j - beta_j)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int k = 0; k < nbe; ++k)
-    for (int r = tid; r < nr; r += 256) P[r * PLD + k] = A[(r0 + r) + (size_t)(k0 + k) * ld];
+    for (int r = tid; r < nr; r += 256) P[r * PLD + k] = (T)A[(r0 + r) + (size_t)(k0 + k) * ld];
   unsigned bits = 0;
   __syncthreads();
 
@@ -588,55 +592,55 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
     const int na = nbe - j;                  // active columns j .. nbe-1, slot = k - j
     {
       const int P1 = 256 / na;
-      double acc = 0.0;
+      T acc = 0;
       if (tid < P1 * na) {
         const int col = j + tid % na, p = tid / na;
         for (int r = max(0, cl + 1) + p; r < nr; r += P1) acc = fma(P[r * PLD + j], P[r * PLD + col], acc);
       }
       // lanes l and l + na hold the same column (thread index modulo na)
       for (int o = na; o < 32; o <<= 1) {
-        const double v = __shfl_down_sync(0xffffffffu, acc, o);
+        const T v = __shfl_down_sync(0xffffffffu, acc, o);
         if (lane + o < 32) acc += v;
       }
       if (lane < na) wred[warp][(32 * warp + lane) % na] = acc;
     }
     __syncthreads();
     if (warp == 0) {
-      double t = 0.0;
+      T t = 0;
       if (lane < na) {
 #pragma unroll
         for (int w = 0; w < 8; ++w) t += wred[w][lane];
       }
       red[par][lane] = t;
-      red[par][32 + lane] = (own_c && lane < na) ? P[cl * PLD + j + lane] : 0.0;
+      red[par][32 + lane] = (own_c && lane < na) ? P[cl * PLD + j + lane] : (T)0;
     }
     cluster.sync();
     if (warp == 0) {
-      double y = 0.0, rc = 0.0;
+      T y = 0, rc = 0;
 #pragma unroll
       for (int qq = 0; qq < PCL; ++qq) {
-        const double* rr = cluster.map_shared_rank(&red[par][0], qq);
+        const T* rr = cluster.map_shared_rank(&red[par][0], qq);
         y += rr[lane];
         rc += rr[32 + lane];
       }
-      const double alpha = __shfl_sync(0xffffffffu, rc, 0);
-      const double ss = __shfl_sync(0xffffffffu, y, 0);
-      double beta, tau, scal;
-      if (ss == 0.0) {
-        tau = 0.0; beta = alpha; scal = 1.0;
+      const T alpha = __shfl_sync(0xffffffffu, rc, 0);
+      const T ss = __shfl_sync(0xffffffffu, y, 0);
+      T beta, tau, scal;
+      if (ss == (T)0) {
+        tau = 0; beta = alpha; scal = 1;
       } else {
         beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
         tau = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
+        scal = (T)1 / (alpha - beta);
       }
-      const double td = tau * fma(scal, y, rc);  // tau v^T a_k for slot `lane`
+      const T td = tau * fma(scal, y, rc);  // tau v^T a_k for slot `lane`
       cf[lane] = td;
       cfs[lane] = td * scal;
       if (lane == 0) {
         stau[j] = tau;
         sscal[j] = scal;
         if (q == 0) {
-          if (beta == 0.0) bits |= ST_RANK;
+          if (beta == (T)0) bits |= ST_RANK;
           if (!isfinite(beta)) bits |= ST_NONFINITE;
         }
         if (own_c) P[cl * PLD + j] = beta;  // row c: R_jj (read as alpha above)
@@ -644,11 +648,11 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
     }
     __syncthreads();
     const int nu = na - 1;                   // columns j+1 .. nbe-1
-    if (nu > 0 && stau[j] != 0.0) {
+    if (nu > 0 && stau[j] != (T)0) {
       const int P2 = 256 / nu;
       if (tid < P2 * nu) {
         const int sl = 1 + tid % nu, col = j + sl, p = tid / nu;
-        const double b = cfs[sl];
+        const T b = cfs[sl];
         if (own_c && p == 0) P[cl * PLD + col] -= cf[sl];
         for (int r = max(0, cl + 1) + p; r < nr; r += P2)
           P[r * PLD + col] = fma(-b, P[r * PLD + j], P[r * PLD + col]);
@@ -661,17 +665,18 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
   // R on and above the diagonal, the reflectors (x scaled into v) below it; V explicit
   double* V = Vp + (size_t)s * vstride;
   for (int k = 0; k < nbe; ++k) {
-    const double sc = sscal[k];
+    const T sc = sscal[k];
     for (int r = tid; r < nr; r += 256) {
       const int gr = r0 + r;
-      double v = P[r * PLD + k];
-      if (gr > k0 + k) v *= sc;
+      T tv = P[r * PLD + k];
+      if (gr > k0 + k) tv *= sc;
+      const double v = (double)tv;
       A[gr + (size_t)(k0 + k) * ld] = v;
       V[gr + (size_t)k * ld] = gr < k0 + k ? 0.0 : (gr == k0 + k ? 1.0 : v);
     }
   }
   if (q == 0) {
-    if (tid < nbe) tau_out[(size_t)s * n + k0 + tid] = stau[tid];
+    if (tid < nbe) tau_out[(size_t)s * n + k0 + tid] = (double)stau[tid];
     if (tid == 0 && bits) atomicOr(status, bits);
   }
   cluster.sync();  // peers may still read this CTA's reduction slots
@@ -718,31 +723,43 @@ __global__ void __launch_bounds__(128) k_form_t(const double* __restrict__ G, lo
 
 cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
                             int nbe, double* tau, int n, double* Vp, long long vstride, unsigned* status,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool fp32) {
   // the cluster variant keeps 1/PCL of the rows (up to ld - k0) in shared memory: 4 CTAs
   // per subdomain, or 8 when a quarter of the rows does not fit.  (Splitting the launch
   // into a full wave of 4-CTA clusters and a remainder of 5-CTA clusters measured slower:
-  // a cluster has to fit in one GPC, so fewer clusters run at once than SMs / size.)
-  const size_t smem4 = (size_t)((ld - k0 + 3) / 4) * PLD * sizeof(double);
-  const size_t smem8 = (size_t)((ld - k0 + 7) / 8) * PLD * sizeof(double);
+  // a cluster has to fit in one GPC, so fewer clusters run at once than SMs / size.)  The
+  // FP32 panel needs half the space per row and takes 2 CTAs where they suffice.
+  constexpr int kMax = 180 * 1024;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_panel_qr_cl<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         180 * 1024);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_panel_qr_cl<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
+    };
+    set((const void*)k_panel_qr_cl<4, double>); set((const void*)k_panel_qr_cl<8, double>);
+    set((const void*)k_panel_qr_cl<2, float>); set((const void*)k_panel_qr_cl<4, float>);
+    set((const void*)k_panel_qr_cl<8, float>);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (smem4 <= 180 * 1024) {
-    k_panel_qr_cl<4><<<dim3(4, N), 256, smem4, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, Vp, vstride,
-                                                     status, 0); count_launch();
-  } else if (smem8 <= 180 * 1024) {
-    k_panel_qr_cl<8><<<dim3(8, N), 256, smem8, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, Vp, vstride,
-                                                     status, 0); count_launch();
+  auto smem = [&](int pcl, size_t bytes) { return (size_t)((ld - k0 + pcl - 1) / pcl) * PLD * bytes; };
+#define ELM_PANEL(PCL_, T_)                                                                          \
+  k_panel_qr_cl<PCL_, T_><<<dim3(PCL_, N), 256, smem(PCL_, sizeof(T_)), st>>>(K, kstride, ld, ms, k0, nbe, \
+                                                                          tau, n, Vp, vstride, status, 0)
+  if (fp32) {
+    if (smem(2, 4) <= kMax) ELM_PANEL(2, float);
+    else if (smem(4, 4) <= kMax) ELM_PANEL(4, float);
+    else if (smem(8, 4) <= kMax) ELM_PANEL(8, float);
+    else return cudaErrorInvalidValue;  // rows beyond the low-precision panel's shared memory
+  } else if (smem(4, 8) <= kMax) {
+    ELM_PANEL(4, double);
+  } else if (smem(8, 8) <= kMax) {
+    ELM_PANEL(8, double);
   } else {
-    k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, Vp, vstride, status); count_launch();
+    k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, Vp, vstride, status);
   }
+#undef ELM_PANEL
+  count_launch();
   return cudaGetLastError();
 }
 

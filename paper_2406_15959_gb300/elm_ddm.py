@@ -49,6 +49,7 @@ class Desc(ctypes.Structure):
 FLAG_FP64_SIMT = 1
 FLAG_SCHUR_CG = 2
 FLAG_DIRECT_ASSEMBLY = 4
+FLAG_MIXED = 8
 OP_POISSON, OP_VARCOEF = 0, 1
 
 
@@ -132,7 +133,8 @@ class Solver:
     """One decomposition on one GPU: setup -> assemble(theta) -> schur() -> solve(rhs)."""
 
     def __init__(self, geom, n_neurons: int, max_rhs: int = 1, stream=None, fp64_simt: bool = False,
-                 schur_cg: bool = False, op: int = OP_POISSON, direct_assembly: bool = False):
+                 schur_cg: bool = False, op: int = OP_POISSON, direct_assembly: bool = False,
+                 mixed: bool = False):
         import torch
         self.lib = load()
         ga = geom if isinstance(geom, GeometryArrays) else GeometryArrays.from_geometry(geom)
@@ -141,7 +143,7 @@ class Solver:
         self.max_rhs = max_rhs
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         flags = ((FLAG_FP64_SIMT if fp64_simt else 0) | (FLAG_SCHUR_CG if schur_cg else 0) |
-                 (FLAG_DIRECT_ASSEMBLY if direct_assembly else 0))
+                 (FLAG_DIRECT_ASSEMBLY if direct_assembly else 0) | (FLAG_MIXED if mixed else 0))
         desc = Desc(N, self.n, m_max, ga.n_gamma, op, max_rhs, flags)
         h = ctypes.c_void_p()
         self._keep = ga
@@ -280,6 +282,12 @@ class Solver:
         """Limit of the device-side waits of the triangular solves (hold_release: test hook
         that makes them run out)."""
         self._check_rc(self.lib.elm_ddm_set_wait_limit(self.h, float(seconds), int(hold_release)))
+
+    @property
+    def refinement(self) -> dict:
+        """Mixed-precision mode: steps, fallback and last relative correction of the last solve."""
+        return {"steps": int(self.info(10)), "fell_back": bool(self.info(11)), "eta": self.info(12),
+                "low_precision_factor": bool(self.info(13))}
 
     @property
     def cooperative_solves(self) -> bool:

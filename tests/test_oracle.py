@@ -521,3 +521,82 @@ def test_mixed_precision_refinement_needs_kappa_below_inverse_unit_roundoff():
     k2, e2 = _fp32_qr_refinement(paper)
     assert k1 * 2.0 ** -24 < 1 and e1 < 1e-12
     assert k2 * 2.0 ** -24 > 1e6 and not (e2 < 1e-6)
+
+
+def _refined_solve(w, iters=12):
+    """The mixed-precision path's algorithm on the CPU: low-precision (float32) local QR,
+    FP64 Schur Cholesky of the low-precision Schur matrix, and refinement of (c, w, u) on
+    FP64 residuals of K^T K c + K^T B u = K^T F, K^T K w - A^T A c = 0,
+    B^T K c - B^T K w + B^T B u = B^T F (Eq. (3.4) with K^{+T} A^T A c written as K w),
+    corrected by the elimination of Eq. (3.5) with the low-precision factors.  Returns the
+    relative u corrections per step and the final (c, u)."""
+    g = w.geom
+    N, ng = g.n_sub, g.n_gamma
+    Ks, As, Fs, dofs, L = [], [], [], [], []
+    for s in range(N):
+        mi, mb, mg = (int(v) for v in g.counts[s])
+        K, A = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s])
+        Q, R = np.linalg.qr(K.astype(np.float32))
+        Q, R = Q.astype(np.float64), R.astype(np.float64)
+        QG = Q[mi + mb:]
+        Y = sla.solve_triangular(R, A.T, trans="T").T
+        Ks.append(K); As.append(A); Fs.append(O.rhs_local(w.rhs[s], g.counts[s]))
+        dofs.append(g.dof[s, mi + mb:mi + mb + mg].astype(int))
+        L.append((R, QG, Y, mi + mb))
+    S = np.zeros((ng, ng)); Mg = np.zeros((ng, ng))
+    for s in range(N):
+        R, QG, Y, _ = L[s]
+        S[np.ix_(dofs[s], dofs[s])] += np.eye(len(dofs[s])) - QG @ QG.T
+        Mg[np.ix_(dofs[s], dofs[s])] += -(Y @ QG.T)
+    Lc = np.linalg.cholesky(S + Mg.T @ Mg)
+
+    def gsum(v):
+        out = np.zeros(ng)
+        for s in range(N):
+            np.add.at(out, dofs[s], v[s])
+        return out
+    n = w.n_neurons
+    c, wv, u = np.zeros((N, n)), np.zeros((N, n)), np.zeros(ng)
+    etas = []
+    for _ in range(iters):
+        Ac = gsum([As[s] @ c[s] for s in range(N)])
+        r1, r3, z = [], [], []
+        for s in range(N):
+            ifc = L[s][3]
+            e = Fs[s] - Ks[s] @ c[s]
+            e[ifc:] += u[dofs[s]]
+            kw = Ks[s] @ wv[s]
+            r1.append(Ks[s].T @ e)
+            r3.append(As[s].T @ Ac[dofs[s]] - Ks[s].T @ kw)
+            z.append(-(e[ifc:] + kw[ifc:]))
+        p1 = [sla.solve_triangular(L[s][0], r1[s], trans="T") for s in range(N)]
+        p13 = [sla.solve_triangular(L[s][0], r1[s] - r3[s], trans="T") for s in range(N)]
+        rhs = gsum(z) + gsum([L[s][1] @ p13[s] for s in range(N)]) + Mg.T @ gsum([L[s][2] @ p1[s] for s in range(N)])
+        du = sla.solve_triangular(Lc.T, sla.solve_triangular(Lc, rhs, lower=True), lower=False)
+        dc = np.array([sla.solve_triangular(L[s][0], p1[s] + L[s][1].T @ du[dofs[s]]) for s in range(N)])
+        Adc = gsum([As[s] @ dc[s] for s in range(N)])
+        dw = np.array([sla.solve_triangular(L[s][0], sla.solve_triangular(
+            L[s][0], r3[s] + As[s].T @ Adc[dofs[s]], trans="T")) for s in range(N)])
+        c, wv, u = c + dc, wv + dw, u + du
+        with np.errstate(all="ignore"):
+            etas.append(np.abs(du).max() / np.abs(u).max())
+    return etas, c, u
+
+
+def test_mixed_precision_refinement_system_converges_to_the_method_result():
+    """The (c, w, u) system the mixed-precision path refines has the method's result as its
+    solution: refinement from a float32 factorisation reaches the oracle (Eq. (3.5) solved
+    in FP64) to rounding level on a well-conditioned case, with the relative correction
+    contracting by orders of magnitude per step, and does not converge at the paper's
+    initialisation (kappa(K^s) ~ 1e14 > 1 / u_32), where the path falls back to FP64."""
+    good = wl.build(3, 3, 60, 12, 12, 12, 12, theta="local_unit", theta_seed=3, source="fourier",
+                    source_seed=3, n_test_side=10)
+    etas, c, u = _refined_solve(good)
+    res = O.solve(good.geom, good.W, good.b, good.rhs)
+    assert np.linalg.norm(u - res.u_gamma) <= 1e-12 * np.linalg.norm(res.u_gamma)
+    assert np.abs(c - res.c).max() <= 1e-9 * np.abs(res.c).max()
+    assert etas[3] < 1e-4 and min(etas) < 1e-12
+    paper = wl.build(2, 2, 200, 20, 20, 40, 40, theta="paper", theta_seed=2, source="sinsin",
+                     n_test_side=10)
+    etas_p, _, _ = _refined_solve(paper, iters=6)
+    assert not (min(etas_p[2:]) < 0.5)                       # no contraction: a stall
