@@ -200,7 +200,8 @@ def workload_config(args, w, ws):
             "n_gamma": w.geom.n_gamma, "test_points": len(w.test_xy), "parallelism": f"replicas{ws}",
             "l2_flush": f"inputs larger than L2 (K alone is {k_gb:.1f} GB per step)",
             "schur_solver": ("cg (unpreconditioned, relative residual 1e-9, matrix-free S)"
-                             if args.schur_solver == "cg" else "direct (envelope Cholesky)")}
+                             if args.schur_solver == "cg" else "direct (envelope Cholesky)"),
+            "precision": getattr(args, "precision", "fp64")}
 
 
 def run_reference(args):
@@ -246,7 +247,8 @@ def run_ours(args):
     w = wl.WORKLOADS[args.workload]()
     stream = torch.cuda.current_stream(dev)
     cg = args.schur_solver == "cg"
-    s = E.Solver(w.geom, w.n_neurons, stream=stream, schur_cg=cg)
+    mixed = args.precision == "mixed"
+    s = E.Solver(w.geom, w.n_neurons, stream=stream, schur_cg=cg, mixed=mixed)
     host = {
         "W": torch.as_tensor(w.W).pin_memory(), "b": torch.as_tensor(w.b).pin_memory(),
         "rhs": torch.as_tensor(w.rhs).pin_memory(),
@@ -400,7 +402,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": R.job_throughput(ms, ws), "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if not mixed else "f32/bf16 factors + f64 refinement",
         "data": "synthetic",
         "config": workload_config(args, w, ws),
         "rel_l2_vs_oracle": l2_oracle, "rel_l2_vs_exact": l2_exact,
@@ -417,6 +420,9 @@ def run_ours(args):
     }
     if cg:
         line["cg_steps"] = max(cg_steps) if cg_steps else None
+    if mixed:
+        line["precision"] = "mixed"
+        line["refinement"] = s.refinement
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -433,6 +439,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schur-solver", choices=["direct", "cg"], default="direct",
                     help="interface solve: direct Cholesky (default) or the paper's CG")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="fp64 (default) or the mixed-precision path (low-precision local factors, "
+                         "FP64 Schur factorisation, FP64-residual refinement, FP64 fallback)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -526,7 +526,17 @@ def varcoef_grf_4x4_n800() -> Workload:
                  coef="grf", coef_seed=6, name="varcoef_grf_4x4_n800")
 
 
+def mixed_16x16_n60_local() -> Workload:
+    """16 x 16 subdomains with few neurons (60, 40 x 40 interior points, 40 points per edge) and
+    local U(-1, 1) weights: kappa(K^s) ~ 1e6, well-conditioned enough for the mixed-precision
+    path to refine instead of falling back (the 16 x 16 decomposition of the mixed-precision
+    configuration with a network small enough to be well conditioned)."""
+    return build(16, 16, 60, 40, 40, 40, 40, theta="local_unit", theta_seed=16, source="fourier",
+                 source_seed=16, modes=4, name="mixed_16x16_n60_local")
+
+
 WORKLOADS = {
+    "mixed_16x16_n60_local": mixed_16x16_n60_local,
     "varcoef_4x4_n800": varcoef_4x4_n800,
     "varcoef_grf_4x4_n800": varcoef_grf_4x4_n800,
     "poisson_2x2_n200": poisson_2x2_n200,
