@@ -92,6 +92,17 @@ extern "C" {
                                      ERR_STATE while the factorisation is the low-precision one.
                                      Needs about one more copy of K^s in device memory */
 
+#define ELM_DDM_FLAG_NEURONS_PER_SUB 16  /* counts passed to elm_ddm_setup are [N][4] =
+                                     {m_i, m_b, m_Gamma, n_s}: subdomain s has n_s <= n_neurons
+                                     neurons (independent problems with different network sizes
+                                     share one decomposition and one launch sequence).  Its
+                                     columns n_s .. n_neurons-1 are identity columns on as many
+                                     extra rows after the interface rows (no collocation point;
+                                     m_max need not cover them): the least-squares solution of
+                                     the other columns is unchanged, their weights come out 0,
+                                     and their theta is ignored (set to 0 in the handle).
+                                     Requires m_i + m_b + m_Gamma >= n_s */
+
 /* Differential operators. */
 #define ELM_DDM_OP_POISSON 0  /* L = -Laplacian (Eq. (4.4)) */
 #define ELM_DDM_OP_VARCOEF 1  /* L = -div(rho grad) (Section 4, the variable-coefficient
@@ -115,7 +126,9 @@ typedef struct elm_ddm_desc {
  * onto u_Gamma).
  *   counts  host int32  [N][3]        {m_i, m_b, m_Gamma}; each subdomain needs
  *                                     m_i + m_b + m_Gamma >= n_neurons (the premise of
- *                                     the full-rank proposition in Section 3)
+ *                                     the full-rank proposition in Section 3); [N][4]
+ *                                     {m_i, m_b, m_Gamma, n_s} with
+ *                                     ELM_DDM_FLAG_NEURONS_PER_SUB
  *   xy      host double [N][m_max][2] collocation points
  *   nrm     host double [N][m_max][2] outward unit normal of interface rows (other rows ignored)
  *   dof     host int32  [N][m_max]    global interface unknown of interface rows, in

@@ -1,8 +1,7 @@
 """Batched serving of independent problem instances as one decomposition.
 
-Instances that share the number of neurons per subdomain are solved together: their
-subdomains are stacked into one batch and their interface unknowns numbered one
-instance after another.  No interface unknown couples two instances, so the Schur
+Instances are solved together by stacking their subdomains into one batch and numbering
+their interface unknowns one instance after another.  No interface unknown couples two instances, so the Schur
 matrix of Eq. (3.5) is block diagonal (one block per instance) and the library's
 reverse Cuthill-McKee envelope keeps every Cholesky step inside its instance's block:
 the batch costs what its instances cost together, but every launch of assemble / schur /
@@ -10,10 +9,13 @@ solve / eval covers all instances at once (one launch sequence instead of one pe
 instance).  Instances may mix subdomain grids; the operator is the variable-coefficient
 one whenever any instance has a coefficient (the others get rho = 1, grad rho = 0).
 
-Instances with different neuron counts form separate batches (the kernels take one n_N
-per batch), and so does a batch whose interface would outgrow `max_gamma` unknowns: the
-library stores the Schur matrix densely (n_Gamma^2 doubles, though only each block's
-envelope is computed), so `plan` packs instances into batches under that cap.  This
+Instances with different neuron counts share a batch through the library's per-subdomain
+neuron counts (ELM_DDM_FLAG_NEURONS_PER_SUB: a smaller network's missing columns are
+identity columns on pad rows, which leave its least-squares solution unchanged and
+cost their share of the batch's work), so `plan` groups instances whose neuron counts are
+within `max_pad` of each other (the padded work stays below that fraction); a batch whose
+interface would outgrow `max_gamma` unknowns is split too: the library stores the Schur
+matrix densely (n_Gamma^2 doubles, though only each block's envelope is computed).  This
 module is host-side marshalling only: every step of the solve runs in the library's
 kernels through elm_ddm.Solver.
 """
@@ -50,7 +52,7 @@ class BatchGeometry:
 @dataclasses.dataclass
 class Batch:
     geom: BatchGeometry
-    n_neurons: int
+    n_neurons: int                # the largest neuron count of the batch
     W: np.ndarray                 # [N, n, 2]
     b: np.ndarray                 # [N, n]
     rhs: np.ndarray               # [N, m_max]
@@ -60,6 +62,7 @@ class Batch:
     sub_off: np.ndarray           # [I + 1]: subdomains of instance i are sub_off[i]:sub_off[i+1]
     gamma_off: np.ndarray         # [I + 1]: its interface unknowns
     test_off: np.ndarray          # [I + 1]: its test points
+    neurons: np.ndarray = None    # [N] neurons of every subdomain (<= n_neurons)
 
     @property
     def n_instances(self) -> int:
@@ -67,16 +70,17 @@ class Batch:
 
 
 def combine(workloads) -> Batch:
-    """Stack workload.Workload instances (equal n_neurons) into one Batch."""
+    """Stack workload.Workload instances into one Batch (neuron counts may differ: the
+    smaller networks are padded to the largest with zero parameters, which the library's
+    per-subdomain neuron counts turn into identity columns)."""
     ws = list(workloads)
     if not ws:
         raise ValueError("no instances")
-    n = ws[0].n_neurons
-    if any(w.n_neurons != n for w in ws):
-        raise ValueError("instances of one batch need the same number of neurons per subdomain")
+    n = max(w.n_neurons for w in ws)
     m_max = max(w.geom.m_max for w in ws)
     N = sum(w.geom.n_sub for w in ws)
     counts = np.zeros((N, 3), np.int32)
+    neurons = np.zeros(N, np.int32)
     xy = np.zeros((N, m_max, 2))
     nrm = np.zeros((N, m_max, 2))
     dof = np.full((N, m_max), -1, np.int32)
@@ -92,13 +96,14 @@ def combine(workloads) -> Batch:
         s0, s1 = sub_off[-1], sub_off[-1] + g.n_sub
         mm = g.m_max
         counts[s0:s1] = g.counts
+        neurons[s0:s1] = w.n_neurons
         xy[s0:s1, :mm] = g.xy
         nrm[s0:s1, :mm] = g.nrm
         d = np.asarray(g.dof, np.int64)
         dof[s0:s1, :mm] = np.where(d >= 0, d + gamma_off[-1], -1)
         rhs[s0:s1, :mm] = w.rhs
-        W[s0:s1] = w.W
-        b[s0:s1] = w.b
+        W[s0:s1, :w.n_neurons] = w.W
+        b[s0:s1, :w.n_neurons] = w.b
         if any_coef:
             if w.coef_rows is not None:
                 coef[s0:s1, :mm] = w.coef_rows
@@ -111,27 +116,28 @@ def combine(workloads) -> Batch:
         test_off.append(test_off[-1] + len(w.test_xy))
     geom = BatchGeometry(counts, xy, nrm, dof, int(gamma_off[-1]))
     return Batch(geom, n, W, b, rhs, coef, np.concatenate(txy), np.concatenate(town).astype(np.int32),
-                 np.array(sub_off), np.array(gamma_off), np.array(test_off))
+                 np.array(sub_off), np.array(gamma_off), np.array(test_off), neurons)
 
 
-def plan(workloads, max_gamma: int = 32768):
-    """Indices of the instances, grouped into batches: equal n_neurons, and at most
-    max_gamma interface unknowns per batch (an instance larger than that alone)."""
-    by_n = {}
-    for i, w in enumerate(workloads):
-        by_n.setdefault(w.n_neurons, []).append(i)
-    batches = []
-    for n in sorted(by_n):
-        cur, ng = [], 0
-        for i in by_n[n]:
-            g = workloads[i].geom.n_gamma
-            if cur and ng + g > max_gamma:
-                batches.append(cur)
-                cur, ng = [], 0
-            cur.append(i)
-            ng += g
-        if cur:
+def plan(workloads, max_gamma: int = 32768, max_pad: float = 0.25):
+    """Indices of the instances, grouped into batches: neuron counts within a factor
+    1 + max_pad of the batch's smallest (so padding adds at most that fraction of columns),
+    and at most max_gamma interface unknowns per batch (an instance larger than that
+    alone).  max_pad = 0 groups equal neuron counts only."""
+    order = sorted(range(len(workloads)), key=lambda i: (workloads[i].n_neurons, i))
+    batches, cur, ng, n0 = [], [], 0, None
+    for i in order:
+        w = workloads[i]
+        g = w.geom.n_gamma
+        if cur and (ng + g > max_gamma or w.n_neurons > (1.0 + max_pad) * n0):
             batches.append(cur)
+            cur, ng = [], 0
+        if not cur:
+            n0 = w.n_neurons
+        cur.append(i)
+        ng += g
+    if cur:
+        batches.append(cur)
     return batches
 
 
@@ -142,8 +148,9 @@ def split(batch: Batch, u_gamma=None, c=None, u=None):
         s0, s1 = batch.sub_off[i], batch.sub_off[i + 1]
         g0, g1 = batch.gamma_off[i], batch.gamma_off[i + 1]
         t0, t1 = batch.test_off[i], batch.test_off[i + 1]
+        nn = batch.n_neurons if batch.neurons is None else int(batch.neurons[s0])
         out.append((None if u_gamma is None else u_gamma[g0:g1],
-                    None if c is None else c[s0:s1],
+                    None if c is None else c[s0:s1, :nn],
                     None if u is None else u[t0:t1]))
     return out
 
@@ -158,8 +165,9 @@ class BatchSolver:
         self.batch = batch
         self.stream = stream if stream is not None else torch.cuda.Stream()
         op = E.OP_VARCOEF if batch.coef_rows is not None else E.OP_POISSON
+        uneven = batch.neurons is not None and int(batch.neurons.min()) < batch.n_neurons
         self.solver = E.Solver(E.GeometryArrays.from_geometry(batch.geom), batch.n_neurons,
-                               stream=self.stream, op=op)
+                               stream=self.stream, op=op, neurons=batch.neurons if uneven else None)
         dev = torch.device("cuda")
         t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), device=dev, dtype=dt)
         # inputs resident on the device from here on

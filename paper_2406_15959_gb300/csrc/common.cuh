@@ -125,11 +125,15 @@ struct AsmTables {
 };
 // coef: NULL for -Laplacian, else [N][m_max][3] (rho, grad rho) for -div(rho grad).
 // tb: NULL (tanh per entry) or the coordinate tables (factored activation).
+// nsub: NULL (n neurons everywhere) or [N] neurons per subdomain; columns n_s .. n-1 of
+// K^s are then identity columns on the pad rows after the interface rows.
 cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, double* Amat,
                             long long astride, int mgld, const double* xy, const double* nrm,
                             int m_max, const int* cnt, const double* W, const double* b, int N,
                             int n, const double* coef, const AsmTables* tb, unsigned* status,
-                            cudaStream_t st);
+                            cudaStream_t st, const int* nsub = nullptr);
+// theta of the pad neurons (j >= nsub[s]) set to zero, so that they evaluate to zero
+cudaError_t launch_zero_pad_theta(double* W, double* b, const int* nsub, int N, int n, cudaStream_t st);
 // Rows of one kind (0 interior, 1 boundary, 2 interface, 3 interface normals) of every
 // subdomain into out [N][kmax][2] (zero past each subdomain's count).
 cudaError_t launch_get_points(const double* xy, const double* nrm, int m_max, const int* cnt, int N,

@@ -120,6 +120,11 @@ struct elm_ddm_handle {
   int max_rhs = 1;
   long long kstride = 0, astride = 0, mstride = 0, tstride = 0, vstride = 0, wstride = 0;
   std::vector<int> cnt_h, ms_h, mg_h;
+  // ELM_DDM_FLAG_NEURONS_PER_SUB: neurons of each subdomain (n_s <= n); the n - n_s pad
+  // columns of K^s are identity columns on as many pad rows after the interface rows, so
+  // ms_h = m_i + m_b + m_Gamma + (n - n_s) and mr_h = m_i + m_b + m_Gamma (rows with points)
+  std::vector<int> ns_h, mr_h;
+  int* nsub = nullptr;          // device copy of ns_h (NULL when every subdomain has n)
   std::vector<Edge> edges;
   std::vector<int> newoff;      // internal offset of each edge's first unknown
   std::vector<int> perm_h;      // caller interface unknown -> internal index
@@ -341,10 +346,12 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
 int assemble_launch(elm_ddm_handle* h) {
   cudaError_t e = cudaMemsetAsync(h->Am, 0, (size_t)h->N * h->astride * sizeof(double), h->st);
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble: clear A");
+  if (h->nsub)
+    ELM_LAUNCH(h, launch_zero_pad_theta(h->thW, h->thb, h->nsub, h->N, h->n, h->st), "assemble");
   ELM_LAUNCH_FB(h, launch_assemble(h->K, h->kstride, h->ld, h->ncap, h->Am, h->astride, h->mgld, h->xy,
                                    h->nrm, h->m_max, h->cnt, h->thW, h->thb, h->N, h->n,
                                    h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr,
-                                   h->use_tabs ? &h->tabs : nullptr, h->status, h->st),
+                                   h->use_tabs ? &h->tabs : nullptr, h->status, h->st, h->nsub),
                 "assemble", 0.0, h->asm_bytes);
   if (h->emulated)
     ELM_LAUNCH(h, launch_colexp(h->K, h->kstride, h->ld, h->ncap, h->ms, h->N, h->colexp, h->st), "colexp");
@@ -383,7 +390,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   if (max_rhs < 1 || max_rhs > 64) return fail(nullptr, ELM_DDM_ERR_ARG, "max_rhs must be in 1..64");
   if (n > TRSV_MAX_N) return fail(nullptr, ELM_DDM_ERR_ARG, "n_neurons > 8192 is not supported");
   if (desc->flags & ~(ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG | ELM_DDM_FLAG_DIRECT_ASSEMBLY |
-                      ELM_DDM_FLAG_MIXED))
+                      ELM_DDM_FLAG_MIXED | ELM_DDM_FLAG_NEURONS_PER_SUB))
     return fail(nullptr, ELM_DDM_ERR_ARG, "unknown flags");
   if ((desc->flags & ELM_DDM_FLAG_MIXED) && (desc->flags & (ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG)))
     return fail(nullptr, ELM_DDM_ERR_ARG,
@@ -398,20 +405,30 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->cg_only = (desc->flags & ELM_DDM_FLAG_SCHUR_CG) != 0;
   h->mixed = (desc->flags & ELM_DDM_FLAG_MIXED) != 0;
   h->op = desc->op;
-  h->cnt_h.assign(counts, counts + 3 * N);
-  h->ms_h.resize(N); h->mg_h.resize(N);
+  const int cst = (desc->flags & ELM_DDM_FLAG_NEURONS_PER_SUB) ? 4 : 3;  // counts row stride
+  h->cnt_h.resize(3 * (size_t)N);
+  h->ms_h.resize(N); h->mg_h.resize(N); h->ns_h.resize(N); h->mr_h.resize(N);
   int msmax = 0, mgmax = 0;
   for (int s = 0; s < N; ++s) {
-    const int mi = counts[3 * s], mb = counts[3 * s + 1], mgs = counts[3 * s + 2];
+    const int mi = counts[cst * s], mb = counts[cst * s + 1], mgs = counts[cst * s + 2];
+    const int ns = cst == 4 ? counts[cst * s + 3] : n;
     if (mi < 0 || mb < 0 || mgs < 0 || mi + mb + mgs > m_max) {
       delete h;
       return fail(nullptr, ELM_DDM_ERR_ARG, "counts of subdomain " + std::to_string(s) + " invalid");
     }
-    if (mi + mb + mgs < n) {
+    if (ns < 1 || ns > n) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_ARG,
+                  "neurons of subdomain " + std::to_string(s) + " not in 1..n_neurons");
+    }
+    if (mi + mb + mgs < ns) {
       delete h;
       return fail(nullptr, ELM_DDM_ERR_ARG,
                   "subdomain " + std::to_string(s) + " has fewer rows than neurons");
     }
+    h->cnt_h[3 * s] = mi; h->cnt_h[3 * s + 1] = mb; h->cnt_h[3 * s + 2] = mgs;
+    h->ns_h[s] = ns;
+    h->mr_h[s] = mi + mb + mgs;
     if ((ng == 0) != (mgs == 0) && N > 1) {
       delete h;
       return fail(nullptr, ELM_DDM_ERR_ARG, "interface rows inconsistent with n_gamma");
@@ -420,9 +437,9 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       delete h;
       return fail(nullptr, ELM_DDM_ERR_ARG, "a single subdomain cannot have interface rows");
     }
-    h->ms_h[s] = mi + mb + mgs;
+    h->ms_h[s] = mi + mb + mgs + (n - ns);
     h->mg_h[s] = mgs;
-    msmax = std::max(msmax, mi + mb + mgs);
+    msmax = std::max(msmax, h->ms_h[s]);
     mgmax = std::max(mgmax, mgs);
   }
   for (size_t i = 0; i < (size_t)N * m_max * 2; ++i) {
@@ -435,7 +452,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   // ---- interface unknowns: owners, edges ----
   std::vector<std::vector<std::pair<int, int>>> owners(ng);
   for (int s = 0; s < N; ++s) {
-    const int r0 = counts[3 * s] + counts[3 * s + 1];
+    const int r0 = h->cnt_h[3 * s] + h->cnt_h[3 * s + 1];
     for (int i = 0; i < h->mg_h[s]; ++i) {
       const int g = dof[(size_t)s * m_max + r0 + i];
       if (g < 0 || g >= ng) {
@@ -458,7 +475,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   // segments: maximal runs with consecutive unknowns and the same neighbour
   std::map<int, std::vector<std::array<int, 3>>> segs;  // g0 -> list of {s, i0, len}
   for (int s = 0; s < N; ++s) {
-    const int r0 = counts[3 * s] + counts[3 * s + 1];
+    const int r0 = h->cnt_h[3 * s] + h->cnt_h[3 * s + 1];
     const int* d = dof + (size_t)s * m_max + r0;
     int i = 0;
     while (i < h->mg_h[s]) {
@@ -559,7 +576,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     size_t total = 0, rows = 0;
     int nxmax = 0, nymax = 0;
     for (int s = 0; s < N; ++s) {
-      for (int r = 0; r < h->ms_h[s]; ++r) {
+      for (int r = 0; r < h->mr_h[s]; ++r) {
         ux[s].push_back(xy[((size_t)s * m_max + r) * 2]);
         uy[s].push_back(xy[((size_t)s * m_max + r) * 2 + 1]);
       }
@@ -570,7 +587,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       nxmax = std::max(nxmax, (int)ux[s].size());
       nymax = std::max(nymax, (int)uy[s].size());
       total += ux[s].size() + uy[s].size();
-      rows += h->ms_h[s];
+      rows += h->mr_h[s];
     }
     // a table entry costs one exp, about what an entry's tanh costs, so the tables pay
     // when they hold fewer activations than K^s (the grids: about a tenth)
@@ -589,7 +606,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
         std::copy(uy[s].begin(), uy[s].end(), tys.begin() + (size_t)s * nymax);
         tctr[2 * s] = ux[s].empty() ? 0.0 : 0.5 * (ux[s].front() + ux[s].back());
         tctr[2 * s + 1] = uy[s].empty() ? 0.0 : 0.5 * (uy[s].front() + uy[s].back());
-        for (int r = 0; r < h->ms_h[s]; ++r) {
+        for (int r = 0; r < h->mr_h[s]; ++r) {
           const double x = xy[((size_t)s * m_max + r) * 2], y = xy[((size_t)s * m_max + r) * 2 + 1];
           const int ix = (int)(std::lower_bound(ux[s].begin(), ux[s].end(), x) - ux[s].begin());
           const int iy = (int)(std::lower_bound(uy[s].begin(), uy[s].end(), y) - uy[s].begin());
@@ -646,6 +663,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->cinv, (size_t)((ng + CHOL_NB - 1) / CHOL_NB + 1) * CHOL_NB * CHOL_NB) &&
             dev_alloc(h, &h->d_rend, h->chol_rend.size()) && dev_alloc(h, &h->d_jbeg, h->chol_jbeg.size()) &&
             dev_alloc(h, &h->cbar, (size_t)2) &&
+            (cst == 3 || dev_alloc(h, &h->nsub, (size_t)N)) &&
             dev_alloc(h, &h->colexp, h->emulated ? (size_t)N * h->ncap : (size_t)1) &&
             dev_alloc(h, &h->status, 1);
   if (ok && h->mixed) {
@@ -734,7 +752,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     dofmap[4 * gi + 2] = b.first; dofmap[4 * gi + 3] = b.second;
   }
   for (int s = 0; s < N; ++s) {
-    const int r0 = counts[3 * s] + counts[3 * s + 1];
+    const int r0 = h->cnt_h[3 * s] + h->cnt_h[3 * s + 1];
     for (int i = 0; i < h->mg_h[s]; ++i)
       ifc[(size_t)s * h->mgld + i] = h->perm_h[dof[(size_t)s * m_max + r0 + i]];
   }
@@ -1143,7 +1161,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   cp(h->ut, uts.data(), uts.size() * sizeof(int4));
   cp(h->xy, xy, (size_t)N * m_max * 2 * sizeof(double));
   cp(h->nrm, nrm, (size_t)N * m_max * 2 * sizeof(double));
-  cp(h->cnt, counts, (size_t)N * 3 * sizeof(int));
+  cp(h->cnt, h->cnt_h.data(), (size_t)N * 3 * sizeof(int));
+  if (h->nsub) cp(h->nsub, h->ns_h.data(), (size_t)N * sizeof(int));
   cp(h->ms, h->ms_h.data(), (size_t)N * sizeof(int));
   cp(h->mg, h->mg_h.data(), (size_t)N * sizeof(int));
   cp(h->dofmap, dofmap.data(), dofmap.size() * sizeof(int));

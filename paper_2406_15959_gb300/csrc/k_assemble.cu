@@ -75,12 +75,14 @@ __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long l
                                                   const double* __restrict__ W,
                                                   const double* __restrict__ bias, int n,
                                                   const double* __restrict__ coef,
-                                                  const AsmTables tb, unsigned* status) {
+                                                  const AsmTables tb, unsigned* status,
+                                                  const int* __restrict__ nsub) {
   const int s = blockIdx.z;
   const int r = blockIdx.x * AR + threadIdx.x;
   const int c0 = blockIdx.y * AC;
   const int mi = cnt[3 * s], mb = cnt[3 * s + 1], mg = cnt[3 * s + 2];
-  const int row0g = mi + mb, ms = row0g + mg;
+  const int row0g = mi + mb, ms = row0g + mg;   // rows with collocation points
+  const int ns = nsub ? nsub[s] : n;            // columns ns .. n-1: pad neurons
 
   __shared__ double sw[AC][4];  // w_x, w_y, b, 2 |w|^2
   const int tl = threadIdx.y * AR + threadIdx.x;
@@ -127,7 +129,9 @@ __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long l
     const int c = c0 + cl;
     if (c >= ncap) break;
     double v = 0.0;
-    if (c < n) {
+    if (c >= ns && c < n) {
+      v = (r == ms + (c - ns)) ? 1.0 : 0.0;  // identity column on pad row ms + (c - ns)
+    } else if (c < n) {
       if (r < ms) {
         const double wx = sw[cl][0], wy = sw[cl][1];
         double t, d1;
@@ -262,11 +266,25 @@ cudaError_t launch_get_points(const double* xy, const double* nrm, int m_max, co
   return cudaGetLastError();
 }
 
+__global__ void k_zero_pad_theta(double* __restrict__ W, double* __restrict__ b, const int* __restrict__ nsub,
+                                 int n) {
+  const int s = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || j < nsub[s]) return;
+  W[((size_t)s * n + j) * 2] = 0.0;
+  W[((size_t)s * n + j) * 2 + 1] = 0.0;
+  b[(size_t)s * n + j] = 0.0;
+}
+
+cudaError_t launch_zero_pad_theta(double* W, double* b, const int* nsub, int N, int n, cudaStream_t st) {
+  k_zero_pad_theta<<<dim3((n + 127) / 128, N), 128, 0, st>>>(W, b, nsub, n); count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, double* Amat,
                             long long astride, int mgld, const double* xy, const double* nrm,
                             int m_max, const int* cnt, const double* W, const double* b, int N,
                             int n, const double* coef, const AsmTables* tb, unsigned* status,
-                            cudaStream_t st) {
+                            cudaStream_t st, const int* nsub) {
   dim3 grid((ld + AR - 1) / AR, (ncap + AC - 1) / AC, N);
   if (tb && tb->rix) {
     const long long per = (long long)n * (tb->nxmax + tb->nymax);
@@ -274,10 +292,11 @@ cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, doub
       k_exp_tables<<<dim3((unsigned)((per + 255) / 256), N), 256, 0, st>>>(W, b, n, *tb); count_launch();
     }
     k_assemble<true><<<grid, dim3(AR, 4), 0, st>>>(K, kstride, ld, ncap, Amat, astride, mgld, xy, nrm,
-                                                   m_max, cnt, W, b, n, coef, *tb, status); count_launch();
+                                                   m_max, cnt, W, b, n, coef, *tb, status, nsub);
+    count_launch();
   } else {
     k_assemble<false><<<grid, dim3(AR, 4), 0, st>>>(K, kstride, ld, ncap, Amat, astride, mgld, xy, nrm,
-                                                    m_max, cnt, W, b, n, coef, AsmTables{}, status);
+                                                    m_max, cnt, W, b, n, coef, AsmTables{}, status, nsub);
     count_launch();
   }
   return cudaGetLastError();

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_resid_rows(const double* __restrict__ K
   }
   const int i0 = cnt[3 * s] + cnt[3 * s + 1];
   double ev = F[xv + r] - a;
-  if (r >= i0) {
+  if (r >= i0 && r < i0 + cnt[3 * s + 2]) {  // interface rows (pad rows follow them)
     const int li = r - i0;
     ev += u[(size_t)rh * ng + ifc_dof[(size_t)s * mgld + li]];
     z[((size_t)rh * N + s) * mgld + li] = -(ev + b);

@@ -50,6 +50,7 @@ FLAG_FP64_SIMT = 1
 FLAG_SCHUR_CG = 2
 FLAG_DIRECT_ASSEMBLY = 4
 FLAG_MIXED = 8
+FLAG_NEURONS_PER_SUB = 16
 OP_POISSON, OP_VARCOEF = 0, 1
 
 
@@ -134,7 +135,9 @@ class Solver:
 
     def __init__(self, geom, n_neurons: int, max_rhs: int = 1, stream=None, fp64_simt: bool = False,
                  schur_cg: bool = False, op: int = OP_POISSON, direct_assembly: bool = False,
-                 mixed: bool = False):
+                 mixed: bool = False, neurons=None):
+        """neurons: None (n_neurons in every subdomain) or int [N] per-subdomain counts <= n_neurons
+        (ELM_DDM_FLAG_NEURONS_PER_SUB)."""
         import torch
         self.lib = load()
         ga = geom if isinstance(geom, GeometryArrays) else GeometryArrays.from_geometry(geom)
@@ -143,11 +146,17 @@ class Solver:
         self.max_rhs = max_rhs
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         flags = ((FLAG_FP64_SIMT if fp64_simt else 0) | (FLAG_SCHUR_CG if schur_cg else 0) |
-                 (FLAG_DIRECT_ASSEMBLY if direct_assembly else 0) | (FLAG_MIXED if mixed else 0))
+                 (FLAG_DIRECT_ASSEMBLY if direct_assembly else 0) | (FLAG_MIXED if mixed else 0) |
+                 (FLAG_NEURONS_PER_SUB if neurons is not None else 0))
         desc = Desc(N, self.n, m_max, ga.n_gamma, op, max_rhs, flags)
         h = ctypes.c_void_p()
         self._keep = ga
-        rc = self.lib.elm_ddm_setup(ctypes.byref(desc), ga.counts.ctypes.data, ga.xy.ctypes.data,
+        counts = ga.counts
+        if neurons is not None:
+            counts = np.ascontiguousarray(np.concatenate([ga.counts, np.asarray(neurons, np.int32)[:, None]], 1),
+                                          np.int32)
+        self._counts_arg = counts
+        rc = self.lib.elm_ddm_setup(ctypes.byref(desc), counts.ctypes.data, ga.xy.ctypes.data,
                                     ga.nrm.ctypes.data, ga.dof.ctypes.data,
                                     ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
         if rc != OK:
@@ -257,8 +266,9 @@ class Solver:
 
     def _export_shape(self, what, s):
         mi, mb, mg = (int(v) for v in self._keep.counts[s])
+        pad = self.n - int(self._counts_arg[s, 3]) if self._counts_arg.shape[1] == 4 else 0
         if what == BUF_K:
-            return mi + mb + mg, self.n + mg
+            return mi + mb + mg + pad, self.n + mg
         if what == BUF_A:
             return mg, self.n
         if what in (BUF_D, BUF_M):

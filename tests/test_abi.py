@@ -62,7 +62,7 @@ G = wl.make_geometry(3, 2, 4, 4, 3, 3)
     (dict(n_neurons=10_000), "8192"),
     (dict(n_neurons=40), "fewer rows than neurons"),
     (dict(n_gamma=G.n_gamma + 1), "not shared by exactly two"),
-    (dict(flags=16), "unknown flags"),
+    (dict(flags=32), "unknown flags"),
     (dict(flags=E.FLAG_MIXED | E.FLAG_FP64_SIMT), "tensor-core back end"),
     (dict(flags=E.FLAG_MIXED | E.FLAG_SCHUR_CG), "direct Schur solve"),
 ])
@@ -119,3 +119,15 @@ def test_new_entry_points_reject_null_handles():
     lib = E.load()
     assert lib.elm_ddm_get_points(None, 0, None, None) == E.ERR_ARG
     assert lib.elm_ddm_set_wait_limit(None, 1.0, 0) == E.ERR_ARG
+
+
+def test_setup_checks_per_subdomain_neuron_counts():
+    c, xy, nrm, dof = _arrays(G)
+    lib = E.load()
+    for ns, msg in [(0, "not in 1..n_neurons"), (9, "not in 1..n_neurons")]:
+        c4 = np.ascontiguousarray(np.concatenate([c, np.full((G.n_sub, 1), ns, np.int32)], 1))
+        h = ctypes.c_void_p()
+        d = _desc(G, 8, flags=E.FLAG_NEURONS_PER_SUB)
+        rc = lib.elm_ddm_setup(ctypes.byref(d), c4.ctypes.data, xy.ctypes.data, nrm.ctypes.data,
+                               dof.ctypes.data, None, ctypes.byref(h))
+        assert rc == E.ERR_ARG and msg in lib.elm_ddm_last_error(None).decode()

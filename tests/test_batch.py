@@ -61,13 +61,63 @@ def test_stacked_interface_map_has_two_owners_per_unknown():
 
 
 def test_plan_groups_by_neurons_and_caps_the_interface():
-    ws = B.serving_instances(12, (20, 30), seed=7)
-    groups = B.plan(ws, max_gamma=700)
+    ws = B.serving_instances(12, (20, 24, 30), seed=7)
+    groups = B.plan(ws, max_gamma=700, max_pad=0.0)
     assert sorted(i for g in groups for i in g) == list(range(12))
     for g in groups:
         assert len({ws[i].n_neurons for i in g}) == 1
         ng = sum(ws[i].geom.n_gamma for i in g)
         assert ng <= 700 or len(g) == 1
-    with pytest.raises(ValueError):
-        B.combine([ws[i] for i in range(12) if ws[i].n_neurons == 20][:1] +
-                  [ws[i] for i in range(12) if ws[i].n_neurons == 30][:1])
+    # with padding allowed, neuron counts within the factor share batches
+    groups = B.plan(ws, max_gamma=10 ** 6, max_pad=0.25)
+    for g in groups:
+        ns = [ws[i].n_neurons for i in g]
+        assert max(ns) <= 1.25 * min(ns)
+    assert any(len({ws[i].n_neurons for i in g}) > 1 for g in groups)
+
+
+def test_padded_neurons_leave_the_solution_unchanged():
+    """The library's per-subdomain neuron counts (identity columns on extra pad rows,
+    Section 3's K^s otherwise unchanged): the oracle's factorisation of the padded K^s
+    gives the unpadded interface solution, the same weights for the real neurons and zero
+    weights for the pad ones.  (The oracle takes the interface rows last, so the pad rows
+    go before them here; a least-squares solution does not depend on the row order.)"""
+    w = wl.build(2, 2, 14, 6, 6, 5, 5, theta="paper", theta_seed=3, source="sinsin", c=0.5, n_test_side=10)
+    g = w.geom
+    pad = 5
+    ref = O.solve(g, w.W, w.b, w.rhs)
+    locs, qs = [], []
+    for s in range(g.n_sub):
+        mi, mb, mg = (int(v) for v in g.counts[s])
+        K, A = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s])
+        m, n = K.shape
+        i0 = mi + mb
+        Kp = np.zeros((m + pad, n + pad))
+        Kp[:i0, :n] = K[:i0]
+        Kp[i0:i0 + pad, n:] = np.eye(pad)     # pad rows (no collocation point)
+        Kp[i0 + pad:, :n] = K[i0:]            # interface rows last
+        Ap = np.zeros((A.shape[0], n + pad))
+        Ap[:, :n] = A
+        L = O.factor_local(Kp, Ap, g.dof[s, mi + mb:mi + mb + mg].astype(np.int64), i0 + pad)
+        F = np.zeros(m + pad)
+        F[:i0] = O.rhs_local(w.rhs[s], g.counts[s])[:i0]
+        locs.append(L)
+        qs.append(L.Q.T @ F)
+    S, M = O.schur_matrix(locs, g.n_gamma)
+    r = O.schur_rhs(locs, qs, M, g.n_gamma)
+    u = np.linalg.solve(S, r)
+    c = np.stack([O.back_solve(L, q, u) for L, q in zip(locs, qs)])
+    assert np.linalg.norm(u - ref.u_gamma) <= 1e-10 * np.linalg.norm(ref.u_gamma)
+    np.testing.assert_allclose(c[:, :w.n_neurons], ref.c, rtol=1e-8, atol=1e-8 * np.abs(ref.c).max())
+    assert np.abs(c[:, w.n_neurons:]).max() <= 1e-12 * np.abs(ref.c).max()
+
+
+def test_combine_pads_smaller_networks():
+    ws = B.serving_instances(4, (20, 30), seed=11)
+    bt = B.combine(ws)
+    assert bt.n_neurons == max(w.n_neurons for w in ws)
+    for i, w in enumerate(ws):
+        s0, s1 = bt.sub_off[i], bt.sub_off[i + 1]
+        assert np.all(bt.neurons[s0:s1] == w.n_neurons)
+        assert np.array_equal(bt.W[s0:s1, :w.n_neurons], w.W)
+        assert not bt.W[s0:s1, w.n_neurons:].any() and not bt.b[s0:s1, w.n_neurons:].any()

@@ -65,3 +65,26 @@ def test_graph_replay_equals_eager_and_oracle():
         res = O.solve(w.geom, w.W, w.b, w.rhs, coef=w.coef_rows)
         u1, _ = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
         assert np.linalg.norm(u_b - u1) <= 1e-8 * np.linalg.norm(u1)
+
+
+def test_uneven_neuron_counts_in_one_launch_sequence():
+    """Instances with different networks (20 .. 30 neurons per subdomain, variable
+    coefficient, mixed grids) in one batch: the per-subdomain neuron counts pad the smaller
+    networks, and every instance still matches its own oracle solution."""
+    ws = B.serving_instances(5, (20, 24, 30), seed=12)
+    assert len({w.n_neurons for w in ws}) > 1
+    bt = B.combine(ws)
+    bs = B.BatchSolver(bt)
+    ug, c, u = bs.run()
+    bs.solver.check()
+    ug, c, u = ug.cpu().numpy(), c.cpu().numpy(), u.cpu().numpy()
+    for w, (ug_b, c_b, u_b) in zip(ws, B.split(bt, ug, c, u)):
+        res = O.solve(w.geom, w.W, w.b, w.rhs, coef=w.coef_rows)
+        u1, _ = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
+        assert np.linalg.norm(u_b - u1) <= 1e-8 * np.linalg.norm(u1)
+        assert np.linalg.norm(ug_b - res.u_gamma) <= 1e-8 * np.linalg.norm(res.u_gamma)
+        assert c_b.shape[1] == w.n_neurons
+    # the pad neurons' weights are zero
+    for i, w in enumerate(ws):
+        s0, s1 = bt.sub_off[i], bt.sub_off[i + 1]
+        assert np.abs(c[s0:s1, w.n_neurons:]).max(initial=0.0) <= 1e-12 * max(np.abs(c[s0:s1]).max(), 1.0)
