@@ -285,6 +285,22 @@ int elm_ddm_get_points(elm_ddm_handle* h, int kind, double* xy, int32_t* counts)
 int elm_ddm_set_wait_limit(elm_ddm_handle* h, double seconds, int hold_release);
 
 /*
+ * Tile choices of the factorisation (the paper has no counterpart; performance only, the
+ * results are the same up to rounding).  Host-only; applies to later calls.
+ *   ELM_DDM_TUNE_PANEL_CTAS  CTAs per subdomain of the FP64 Householder panel: 0 (default)
+ *                            the smallest cluster whose shared memory holds the panel (4 or
+ *                            8), 4 or 8 to ask for one (8 gives small batches more SMs; a
+ *                            size that does not fit is replaced by the default)
+ *   ELM_DDM_TUNE_UPD_GRID    grid cap of the persistent tensor-core products: 0 (default)
+ *                            one CTA per SM, else at most this many CTAs
+ * Returns ELM_DDM_ERR_ARG for an unknown key or value.  An autotuner that times these per
+ * shape class is paper_2406_15959_gb300/autotune.py.
+ */
+#define ELM_DDM_TUNE_PANEL_CTAS 0
+#define ELM_DDM_TUNE_UPD_GRID   1
+int elm_ddm_set_tuning(elm_ddm_handle* h, int key, int value);
+
+/*
  * The Schur matrix is assembled and factored with its interface unknowns renumbered
  * (reverse Cuthill-McKee on the interface edges, so the Cholesky factor stays inside a
  * narrow envelope).  order (host int32 [n_gamma]) receives, for every caller unknown g,

@@ -33,7 +33,8 @@ from . import workload as wl
 
 @dataclasses.dataclass
 class BatchGeometry:
-    """The stacked decomposition (the attributes elm_ddm.Solver and the oracle read)."""
+    """The stacked decomposition (the attributes elm_ddm.Solver reads; the same layout as
+    workload.Geometry)."""
     counts: np.ndarray    # int32 [N, 3]
     xy: np.ndarray        # float64 [N, m_max, 2]
     nrm: np.ndarray       # float64 [N, m_max, 2]
@@ -160,7 +161,9 @@ class BatchSolver:
     on its own CUDA stream (a new one unless given), so that several batches submitted one
     after another run concurrently on the GPU."""
 
-    def __init__(self, batch: Batch, stream=None):
+    def __init__(self, batch: Batch, stream=None, tuner=None):
+        """tuner: an autotune.Autotuner that picks (and caches) the tile choices for this
+        batch's shape class."""
         import torch
         self.batch = batch
         self.stream = stream if stream is not None else torch.cuda.Stream()
@@ -174,6 +177,11 @@ class BatchSolver:
         self.W, self.b, self.rhs = t(batch.W), t(batch.b), t(batch.rhs)
         self.coef = t(batch.coef_rows) if batch.coef_rows is not None else None
         self.test_xy, self.test_owner = t(batch.test_xy), t(batch.test_owner, torch.int32)
+        self.tuning = None
+        if tuner is not None:
+            if self.coef is not None:
+                self.solver.set_coefficient(self.coef)
+            self.tuning = tuner.tune(self.solver, self.W, self.b, self.stream)
 
     def run(self):
         """One full solve of every instance, enqueued on this batch's stream; returns
@@ -225,24 +233,129 @@ def serving_instances(count: int, neurons=(200,), seed: int = 0):
     return out
 
 
+def serve_in_waves(instances, max_gamma: int = 32768, max_pad: float = 0.25, budget_gb: float = 150.0,
+                   steps: int = 3, warmup: int = 1, tuner=None, graphs: bool = True):
+    """Full solves of every instance, batched by `plan` and run in waves whose handles fit
+    `budget_gb` of device memory (all instances at once need more than the GPU holds at the
+    serving configuration's sizes).  Each wave's batches share one stream; with `graphs`
+    the whole wave is captured as one CUDA graph after `warmup` eager rounds and replayed
+    `steps` times.  Returns per-wave timings (device time of the replays, CUDA events) and
+    the per-instance results of the last replay as host arrays (u at the test points)."""
+    import torch
+    groups = plan(instances, max_gamma, max_pad)
+    waves, cur, cur_bytes = [], [], 0
+    results = [None] * len(instances)
+    report = {"batches": len(groups), "waves": [], "tuning": {}}
+
+    def run_wave(batches):
+        st = torch.cuda.Stream()
+        solvers = [BatchSolver(combine([instances[i] for i in g]), stream=st, tuner=tuner) for g in batches]
+        for _ in range(warmup):
+            for bs in solvers:
+                bs.run()
+        st.synchronize()
+        graph = None
+        if graphs:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=st):
+                outs = [bs.run() for bs in solvers]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            for _ in range(steps):
+                if graph is not None:
+                    graph.replay()
+                else:
+                    outs = [bs.run() for bs in solvers]
+            e1.record(st)
+        st.synchronize()
+        for bs in solvers:
+            bs.solver.check()
+        ms = e0.elapsed_time(e1) / steps
+        n_inst = sum(len(g) for g in batches)
+        for g, bs, (ug, c, u) in zip(batches, solvers, outs):
+            for i, (_, _, u_i) in zip(g, split(bs.batch, None, None, u.cpu().numpy())):
+                results[i] = u_i
+        mem = sum(bs.solver.workspace_bytes for bs in solvers)
+        report["waves"].append({"batches": len(batches), "instances": n_inst, "ms_per_round": ms,
+                                "workspace_gb": mem / 1e9})
+        del solvers, graph
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+    for g in groups:
+        need = _workspace_estimate([instances[i] for i in g])
+        if cur and cur_bytes + need > budget_gb * 1e9:
+            waves.append(cur)
+            cur, cur_bytes = [], 0
+        cur.append(g)
+        cur_bytes += need
+    if cur:
+        waves.append(cur)
+    for w in waves:
+        run_wave(w)
+    if tuner is not None:
+        report["tuning"] = {"choices": tuner.table, "measured_ms": tuner.measured}
+    report["ms_per_round"] = sum(wv["ms_per_round"] for wv in report["waves"])
+    report["instances_per_s"] = len(instances) / (report["ms_per_round"] * 1e-3)
+    return report, results
+
+
+def _workspace_estimate(ws) -> int:
+    """Device bytes a batch of these instances needs (dominant terms: [K | J], the Schur
+    matrix, the split planes ~ 2.2 x K)."""
+    n = max(w.n_neurons for w in ws)
+    rows = max(int(w.geom.counts.sum(1).max()) + n - w.n_neurons for w in ws)
+    mg = max(int(w.geom.counts[:, 2].max()) for w in ws)
+    subs = sum(w.geom.n_sub for w in ws)
+    ng = sum(w.geom.n_gamma for w in ws)
+    ld = -(-rows // 32) * 32
+    return int(3.2 * subs * ld * (n + mg) * 8 + 8 * ng * ng)
+
+
 def _main(argv=None):
-    """Serving measurement: instances per second of full solves of `--instances` seeded
-    instances packed into batches, every batch on its own stream (wall clock around
-    synchronised rounds, inputs resident)."""
+    """Serving measurement.  Default: `--instances` seeded instances of 200 neurons per
+    subdomain, all resident, every batch on its own stream (wall clock around synchronised
+    rounds).  `--waves`: the serving configuration (neurons drawn from 200..1500), batched
+    with padding, run in memory-bounded waves, each captured as one CUDA graph (device
+    time of the replays), optionally with the tile autotuner."""
     import argparse
     import torch
     ap = argparse.ArgumentParser()
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--neurons", type=int, nargs="+", default=[200])
+    ap.add_argument("--neuron-range", type=int, nargs=2, default=None,
+                    help="draw neurons uniformly from this closed range instead of --neurons")
     ap.add_argument("--max-gamma", type=int, default=32768)
+    ap.add_argument("--max-pad", type=float, default=0.25)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--seed", type=int, default=4)
-    ap.add_argument("--graphs", action="store_true", help="replay one CUDA graph per batch")
+    ap.add_argument("--graphs", action="store_true", help="replay CUDA graphs")
+    ap.add_argument("--waves", action="store_true", help="memory-bounded waves, one CUDA graph each")
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--autotune", default=None, metavar="CACHE.json",
+                    help="tile autotuner with its cache file")
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
-    inst = serving_instances(a.instances, a.neurons, a.seed)
-    groups = plan(inst, a.max_gamma)
+    neurons = range(a.neuron_range[0], a.neuron_range[1] + 1) if a.neuron_range else a.neurons
+    inst = serving_instances(a.instances, neurons, a.seed)
+    host_s = time.perf_counter() - t0
+    if a.waves:
+        tuner = None
+        if a.autotune:
+            from .autotune import Autotuner
+            tuner = Autotuner(a.autotune)
+        t1 = time.perf_counter()
+        rep, res = serve_in_waves(inst, a.max_gamma, a.max_pad, a.budget_gb, a.steps, a.warmup, tuner, True)
+        rep["wall_s_incl_setup_and_capture"] = time.perf_counter() - t1
+        neur = [w.n_neurons for w in inst]
+        print(json.dumps({"metric": "batched serving, memory-bounded waves, one CUDA graph per wave",
+                          "instances": a.instances, "neurons_min_max": [min(neur), max(neur)],
+                          "grids": sorted({f"{w.geom.gx}x{w.geom.gy}" for w in inst}),
+                          "host_instance_generation_s": host_s, **rep}))
+        return
+    groups = plan(inst, a.max_gamma, a.max_pad)
     solvers = [BatchSolver(combine([inst[i] for i in g])) for g in groups]
     host_s = time.perf_counter() - t0
     for _ in range(a.warmup):
@@ -269,7 +382,7 @@ def _main(argv=None):
     for bs in solvers:
         bs.solver.check()
     print(json.dumps({"metric": "batched serving (full solves, inputs resident, wall clock)",
-                      "instances": a.instances, "neurons": a.neurons, "batches": len(solvers),
+                      "instances": a.instances, "neurons": list(a.neurons), "batches": len(solvers),
                       "subdomains": int(sum(bs.batch.geom.n_sub for bs in solvers)),
                       "n_gamma": int(sum(bs.batch.geom.n_gamma for bs in solvers)),
                       "ms_per_round": ms, "instances_per_s": a.instances / (ms * 1e-3),

@@ -151,7 +151,7 @@ cudaError_t launch_eval(const double* W, const double* b, int N, int n, int npts
 // the explicit reflectors in Vp.  T is formed afterwards by launch_form_t.
 cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
                             int nbe, double* tau, int n, double* Vp, long long vstride, unsigned* status,
-                            cudaStream_t st, bool fp32 = false);
+                            cudaStream_t st, bool fp32 = false, int pcl_pref = 0);
 // Compact-WY T of panel [k0, k0+nbe) of every subdomain from G (v_l^T v_j at G[l*32 + j],
 // l < j, per subdomain at stride gstride) and tau; T [32 x 32] column-major at T + s*tstride.
 cudaError_t launch_form_t(const double* G, long long gstride, const double* tau, int n, int k0, int nbe,

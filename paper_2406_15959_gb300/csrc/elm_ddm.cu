@@ -135,6 +135,10 @@ struct elm_ddm_handle {
   unsigned* cbar = nullptr;     // grid-barrier state of the persistent triangular solves
   unsigned long long wait_ns = kDefaultWaitNs;  // limit of their bounded grid-barrier waits
   int wait_hold = 0;            // 1: withhold every barrier's release (failure-detection test)
+  // tile choices (elm_ddm_set_tuning): CTAs per subdomain of the FP64 Householder panel
+  // (0: the smallest cluster whose shared memory holds the panel), and the grid cap of the
+  // persistent products (0: one CTA per SM)
+  int tune_panel = 0, tune_upd_grid = 0;
   int fwd_grid = 0, bwd_grid = 0;  // their grids (0: one launch per block step instead)
   // device buffers
   double *K = nullptr, *Am = nullptr, *tau = nullptr, *T = nullptr, *Vp = nullptr;
@@ -333,7 +337,8 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
       if (e_ != cudaSuccess) return cuda_fail(h, e_, nm);
     } else if (L.kind == 4)
       ELM_LAUNCH_FB(h, launch_ozaki_upd(h->od + L.off, L.count, h->ut + L.toff, L.max_tiles, L.alpha,
-                                        L.beta, L.flags, h->status, h->st, 0, gmax), nm, L.flops, L.bytes);
+                                        L.beta, L.flags, h->status, h->st, h->tune_upd_grid, gmax), nm,
+                    L.flops, L.bytes);
     else
       ELM_LAUNCH_FB(h, launch_ozaki_fa(h->od + L.off, L.count, L.max_tiles, h->status, h->st, gmax), nm,
                     L.flops, L.bytes);
@@ -1232,8 +1237,8 @@ int elm_ddm_schur(elm_ddm_handle* h) {
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, h->n - k0);
     ELM_LAUNCH_FB(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->Vp,
-                                     h->vstride, h->status, h->st, h->lowfac), "panel_qr", h->panel_flops[b],
-                  h->panel_bytes[b]);
+                                     h->vstride, h->status, h->st, h->lowfac, h->tune_panel),
+                  "panel_qr", h->panel_flops[b], h->panel_bytes[b]);
     int rc = run_recs(h, h->qr_recs, h->qr_first[b], h->qr_first[b + 1] - h->qr_first[b],
                       "gemm_qr", lo_gmax);
     if (rc) return rc;
@@ -1688,6 +1693,23 @@ int elm_ddm_set_wait_limit(elm_ddm_handle* h, double seconds, int hold_release) 
   h->wait_ns = (unsigned long long)(seconds * 1e9);
   h->wait_hold = hold_release;
   return ELM_DDM_OK;
+}
+
+int elm_ddm_set_tuning(elm_ddm_handle* h, int key, int value) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  switch (key) {
+    case ELM_DDM_TUNE_PANEL_CTAS:
+      if (value != 0 && value != 4 && value != 8)
+        return fail(h, ELM_DDM_ERR_ARG, "set_tuning: panel CTAs must be 0, 4 or 8");
+      h->tune_panel = value;
+      return ELM_DDM_OK;
+    case ELM_DDM_TUNE_UPD_GRID:
+      if (value < 0) return fail(h, ELM_DDM_ERR_ARG, "set_tuning: grid cap must be >= 0");
+      h->tune_upd_grid = value;
+      return ELM_DDM_OK;
+    default:
+      return fail(h, ELM_DDM_ERR_ARG, "set_tuning: unknown key");
+  }
 }
 
 int elm_ddm_interface_order(const elm_ddm_handle* h, int32_t* order) {

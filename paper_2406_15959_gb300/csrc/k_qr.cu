@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(128) k_form_t(const double* __restrict__ G, lo
 
 cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
                             int nbe, double* tau, int n, double* Vp, long long vstride, unsigned* status,
-                            cudaStream_t st, bool fp32) {
+                            cudaStream_t st, bool fp32, int pcl_pref) {
   // the cluster variant keeps 1/PCL of the rows (up to ld - k0) in shared memory: 4 CTAs
   // per subdomain, or 8 when a quarter of the rows does not fit.  (Splitting the launch
   // into a full wave of 4-CTA clusters and a remainder of 5-CTA clusters measured slower:
@@ -751,6 +751,8 @@ cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms,
     else if (smem(4, 4) <= kMax) ELM_PANEL(4, float);
     else if (smem(8, 4) <= kMax) ELM_PANEL(8, float);
     else return cudaErrorInvalidValue;  // rows beyond the low-precision panel's shared memory
+  } else if (pcl_pref == 8 && smem(8, 8) <= kMax) {
+    ELM_PANEL(8, double);  // a tile choice: twice the SMs per subdomain (small batches)
   } else if (smem(4, 8) <= kMax) {
     ELM_PANEL(4, double);
   } else if (smem(8, 8) <= kMax) {

@@ -28,7 +28,8 @@ SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve"
            "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order",
            "elm_ddm_profile_only", "elm_ddm_solve_cg", "elm_ddm_set_coefficient",
            "elm_ddm_solve_pcg", "elm_ddm_get_points", "elm_ddm_set_wait_limit",
-           "elm_ddm_fp64_gemm", "elm_ddm_fp64_gemm_workspace")
+           "elm_ddm_fp64_gemm", "elm_ddm_fp64_gemm_workspace", "elm_ddm_set_tuning")
+TUNE_PANEL_CTAS, TUNE_UPD_GRID = 0, 1
 GEMM_TILE32, GEMM_TILE64, GEMM_PERSISTENT, GEMM_FUSED_SPLIT = range(4)
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
 PTS_INTERIOR, PTS_BOUNDARY, PTS_INTERFACE, PTS_NORMALS = range(4)
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_get_info.argtypes = [P, I, D]
     lib.elm_ddm_get_points.argtypes = [P, I, P, P]
     lib.elm_ddm_set_wait_limit.argtypes = [P, ctypes.c_double, I]
+    lib.elm_ddm_set_tuning.argtypes = [P, I, I]
     LL = ctypes.c_longlong
     lib.elm_ddm_fp64_gemm_workspace.argtypes = [I, I, I, I]
     lib.elm_ddm_fp64_gemm_workspace.restype = ctypes.c_size_t
@@ -292,6 +294,14 @@ class Solver:
         """Limit of the device-side waits of the triangular solves (hold_release: test hook
         that makes them run out)."""
         self._check_rc(self.lib.elm_ddm_set_wait_limit(self.h, float(seconds), int(hold_release)))
+
+    def set_tuning(self, panel_ctas: int | None = None, upd_grid: int | None = None):
+        """Tile choices (elm_ddm_set_tuning): panel CTAs per subdomain (0, 4, 8) and the grid cap
+        of the persistent products (0 = one CTA per SM)."""
+        if panel_ctas is not None:
+            self._check_rc(self.lib.elm_ddm_set_tuning(self.h, TUNE_PANEL_CTAS, int(panel_ctas)))
+        if upd_grid is not None:
+            self._check_rc(self.lib.elm_ddm_set_tuning(self.h, TUNE_UPD_GRID, int(upd_grid)))
 
     @property
     def refinement(self) -> dict:

@@ -121,3 +121,12 @@ def test_combine_pads_smaller_networks():
         assert np.all(bt.neurons[s0:s1] == w.n_neurons)
         assert np.array_equal(bt.W[s0:s1, :w.n_neurons], w.W)
         assert not bt.W[s0:s1, w.n_neurons:].any() and not bt.b[s0:s1, w.n_neurons:].any()
+
+
+def test_autotuner_shape_classes_and_candidates():
+    from paper_2406_15959_gb300 import autotune as AT
+    assert AT.shape_key(64, 1000, 2400, 400) == "N64_n1024_m4096_g512"
+    assert AT.shape_key(16, 1000, 2400, 400) != AT.shape_key(64, 1000, 2400, 400)
+    assert AT.shape_key(60, 990, 2300, 390) == AT.shape_key(64, 1000, 2400, 400)
+    c = AT.candidates(152)
+    assert (0, 0) in c and all(p in (0, 4, 8) and g >= 0 for p, g in c)

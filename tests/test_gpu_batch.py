@@ -88,3 +88,27 @@ def test_uneven_neuron_counts_in_one_launch_sequence():
     for i, w in enumerate(ws):
         s0, s1 = bt.sub_off[i], bt.sub_off[i + 1]
         assert np.abs(c[s0:s1, w.n_neurons:]).max(initial=0.0) <= 1e-12 * max(np.abs(c[s0:s1]).max(), 1.0)
+
+
+def test_serving_waves_with_autotuner_match_the_oracle(tmp_path):
+    """The serving driver on a scaled-down mix (neurons 24 .. 40 per subdomain, grids
+    2x2 / 4x4 / 8x8, variable coefficient): batches padded within 25%, two memory-bounded
+    waves each captured as one CUDA graph, tile choices from the autotuner (cached in a
+    file); every instance's u at its test points matches its own oracle solution."""
+    from paper_2406_15959_gb300 import autotune as AT
+    ws = B.serving_instances(10, range(24, 41), seed=21)
+    tuner = AT.Autotuner(str(tmp_path / "tuning.json"))
+    groups = B.plan(ws, max_gamma=4096, max_pad=0.25)
+    assert len(groups) >= 2
+    budget = 1.01 * max(B._workspace_estimate([ws[i] for i in g]) for g in groups) / 1e9  # one batch a wave
+    rep, res = B.serve_in_waves(ws, max_gamma=4096, max_pad=0.25, budget_gb=budget, steps=2, warmup=1,
+                                tuner=tuner)
+    assert len(rep["waves"]) >= 2 and rep["instances_per_s"] > 0
+    assert (tmp_path / "tuning.json").exists() and rep["tuning"]["choices"]
+    for w, u in zip(ws, res):
+        r = O.solve(w.geom, w.W, w.b, w.rhs, keep=False, coef=w.coef_rows)
+        u1, _ = O.evaluate(w.W, w.b, r.c, w.test_xy, w.test_owner)
+        assert np.linalg.norm(u - u1) <= 1e-8 * np.linalg.norm(u1)
+    # a second tuner on the same cache reuses the choices without timing
+    t2 = AT.Autotuner(str(tmp_path / "tuning.json"))
+    assert t2.table == tuner.table
