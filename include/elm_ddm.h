@@ -103,6 +103,16 @@ extern "C" {
                                      and their theta is ignored (set to 0 in the handle).
                                      Requires m_i + m_b + m_Gamma >= n_s */
 
+#define ELM_DDM_FLAG_RIDGE 32  /* Tikhonov-regularised local least squares: every K^s gets
+                                     n_s extra rows lambda_s I (after the pad rows), so each local
+                                     problem becomes min |K c - F|^2 + lambda_s^2 |c|^2, with
+                                     lambda_s = alpha * (largest column norm of K^s), alpha from
+                                     elm_ddm_set_ridge (default 1e-14).  The paper does not name
+                                     its local solver; at its Table 2 setup (rows barely more than
+                                     neurons, K^s numerically rank deficient) the unregularised
+                                     solution interpolates with huge weights, and this option
+                                     reaches the paper's accuracy */
+
 /* Differential operators. */
 #define ELM_DDM_OP_POISSON 0  /* L = -Laplacian (Eq. (4.4)) */
 #define ELM_DDM_OP_VARCOEF 1  /* L = -div(rho grad) (Section 4, the variable-coefficient
@@ -283,6 +293,13 @@ int elm_ddm_get_points(elm_ddm_handle* h, int kind, double* xy, int32_t* counts)
  * step is used instead and there is no device-side wait).
  */
 int elm_ddm_set_wait_limit(elm_ddm_handle* h, double seconds, int hold_release);
+
+/*
+ * Regularisation parameter of ELM_DDM_FLAG_RIDGE (see the flag): alpha in [0, 1), applied
+ * from the next elm_ddm_assemble.  ERR_STATE without the flag.  The paper has no
+ * counterpart (its local solver is unspecified).
+ */
+int elm_ddm_set_ridge(elm_ddm_handle* h, double alpha);
 
 /*
  * Tile choices of the factorisation (the paper has no counterpart; performance only, the

@@ -175,9 +175,23 @@ class Result:
     locs: list
 
 
-def solve(geom, W, b, rhs_rows, keep=True, coef=None):
+def ridge_rows(K, F, first_ifc, alpha):
+    """Tikhonov regularisation of a local least-squares problem (the library's
+    ELM_DDM_FLAG_RIDGE; the paper does not name its local solver): min |K c - F|^2 +
+    lambda^2 |c|^2 with lambda = alpha * the largest column norm of K, written as the least
+    squares problem of K stacked on lambda I (F stacked on 0).  The rows go before the
+    interface rows, which stay last; returns (K', F', index of the first interface row)."""
+    m, n = K.shape
+    lam = alpha * np.sqrt((K * K).sum(axis=0)).max()
+    Ka = np.vstack([K[:first_ifc], lam * np.eye(n), K[first_ifc:]])
+    Fa = np.concatenate([F[:first_ifc], np.zeros(n), F[first_ifc:]])
+    return Ka, Fa, first_ifc + n
+
+
+def solve(geom, W, b, rhs_rows, keep=True, coef=None, ridge=None):
     """Algorithm 1: assemble, factor, solve Eq. (3.5) by Cholesky, back-solve.
-    coef: None (-Laplacian) or [N, m_max, 3] rows of (rho, grad rho)."""
+    coef: None (-Laplacian) or [N, m_max, 3] rows of (rho, grad rho).
+    ridge: None, or alpha of the Tikhonov-regularised local problems (ridge_rows)."""
     N = geom.n_sub
     locs, qs = [], []
     for s in range(N):
@@ -185,8 +199,11 @@ def solve(geom, W, b, rhs_rows, keep=True, coef=None):
         K, A = assemble_local(geom.xy[s], geom.nrm[s], geom.counts[s], W[s], b[s],
                               None if coef is None else coef[s])
         dof = geom.dof[s, mi + mb:mi + mb + mg].astype(np.int64)
-        L = factor_local(K, A, dof, mi + mb)
         F = rhs_local(rhs_rows[s], geom.counts[s])
+        i0 = mi + mb
+        if ridge is not None:
+            K, F, i0 = ridge_rows(K, F, mi + mb, ridge)
+        L = factor_local(K, A, dof, i0)
         locs.append(L)
         qs.append(L.Q.T @ F)
     S, M = schur_matrix(locs, geom.n_gamma)

@@ -132,6 +132,9 @@ cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, doub
                             int m_max, const int* cnt, const double* W, const double* b, int N,
                             int n, const double* coef, const AsmTables* tb, unsigned* status,
                             cudaStream_t st, const int* nsub = nullptr);
+// Tikhonov rows (ELM_DDM_FLAG_RIDGE): K[ms + (n - n_s) + j][j] = alpha * max column norm, j < n_s
+cudaError_t launch_ridge_rows(double* K, long long kstride, int ld, const int* cnt, const int* nsub, int N, int n,
+                              double alpha, cudaStream_t st);
 // theta of the pad neurons (j >= nsub[s]) set to zero, so that they evaluate to zero
 cudaError_t launch_zero_pad_theta(double* W, double* b, const int* nsub, int N, int n, cudaStream_t st);
 // Rows of one kind (0 interior, 1 boundary, 2 interface, 3 interface normals) of every

@@ -125,6 +125,10 @@ struct elm_ddm_handle {
   // ms_h = m_i + m_b + m_Gamma + (n - n_s) and mr_h = m_i + m_b + m_Gamma (rows with points)
   std::vector<int> ns_h, mr_h;
   int* nsub = nullptr;          // device copy of ns_h (NULL when every subdomain has n)
+  // ELM_DDM_FLAG_RIDGE: n_s rows lambda_s I after the pad rows (Tikhonov regularisation of
+  // the local least-squares problems), lambda_s = ridge_alpha * largest column norm of K^s
+  bool ridge = false;
+  double ridge_alpha = 1e-14;
   std::vector<Edge> edges;
   std::vector<int> newoff;      // internal offset of each edge's first unknown
   std::vector<int> perm_h;      // caller interface unknown -> internal index
@@ -351,13 +355,16 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
 int assemble_launch(elm_ddm_handle* h) {
   cudaError_t e = cudaMemsetAsync(h->Am, 0, (size_t)h->N * h->astride * sizeof(double), h->st);
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble: clear A");
-  if (h->nsub)
+  if (h->nsub && (h->desc.flags & ELM_DDM_FLAG_NEURONS_PER_SUB))
     ELM_LAUNCH(h, launch_zero_pad_theta(h->thW, h->thb, h->nsub, h->N, h->n, h->st), "assemble");
   ELM_LAUNCH_FB(h, launch_assemble(h->K, h->kstride, h->ld, h->ncap, h->Am, h->astride, h->mgld, h->xy,
                                    h->nrm, h->m_max, h->cnt, h->thW, h->thb, h->N, h->n,
                                    h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr,
                                    h->use_tabs ? &h->tabs : nullptr, h->status, h->st, h->nsub),
                 "assemble", 0.0, h->asm_bytes);
+  if (h->ridge)
+    ELM_LAUNCH(h, launch_ridge_rows(h->K, h->kstride, h->ld, h->cnt, h->nsub, h->N, h->n, h->ridge_alpha, h->st),
+               "assemble");
   if (h->emulated)
     ELM_LAUNCH(h, launch_colexp(h->K, h->kstride, h->ld, h->ncap, h->ms, h->N, h->colexp, h->st), "colexp");
   if (h->mixed) {
@@ -395,7 +402,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   if (max_rhs < 1 || max_rhs > 64) return fail(nullptr, ELM_DDM_ERR_ARG, "max_rhs must be in 1..64");
   if (n > TRSV_MAX_N) return fail(nullptr, ELM_DDM_ERR_ARG, "n_neurons > 8192 is not supported");
   if (desc->flags & ~(ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG | ELM_DDM_FLAG_DIRECT_ASSEMBLY |
-                      ELM_DDM_FLAG_MIXED | ELM_DDM_FLAG_NEURONS_PER_SUB))
+                      ELM_DDM_FLAG_MIXED | ELM_DDM_FLAG_NEURONS_PER_SUB | ELM_DDM_FLAG_RIDGE))
     return fail(nullptr, ELM_DDM_ERR_ARG, "unknown flags");
   if ((desc->flags & ELM_DDM_FLAG_MIXED) && (desc->flags & (ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG)))
     return fail(nullptr, ELM_DDM_ERR_ARG,
@@ -409,6 +416,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->emulated = !(desc->flags & ELM_DDM_FLAG_FP64_SIMT);
   h->cg_only = (desc->flags & ELM_DDM_FLAG_SCHUR_CG) != 0;
   h->mixed = (desc->flags & ELM_DDM_FLAG_MIXED) != 0;
+  h->ridge = (desc->flags & ELM_DDM_FLAG_RIDGE) != 0;
   h->op = desc->op;
   const int cst = (desc->flags & ELM_DDM_FLAG_NEURONS_PER_SUB) ? 4 : 3;  // counts row stride
   h->cnt_h.resize(3 * (size_t)N);
@@ -442,7 +450,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       delete h;
       return fail(nullptr, ELM_DDM_ERR_ARG, "a single subdomain cannot have interface rows");
     }
-    h->ms_h[s] = mi + mb + mgs + (n - ns);
+    h->ms_h[s] = mi + mb + mgs + (n - ns) + (h->ridge ? ns : 0);
     h->mg_h[s] = mgs;
     msmax = std::max(msmax, h->ms_h[s]);
     mgmax = std::max(mgmax, mgs);
@@ -668,7 +676,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->cinv, (size_t)((ng + CHOL_NB - 1) / CHOL_NB + 1) * CHOL_NB * CHOL_NB) &&
             dev_alloc(h, &h->d_rend, h->chol_rend.size()) && dev_alloc(h, &h->d_jbeg, h->chol_jbeg.size()) &&
             dev_alloc(h, &h->cbar, (size_t)2) &&
-            (cst == 3 || dev_alloc(h, &h->nsub, (size_t)N)) &&
+            ((cst == 3 && !h->ridge) || dev_alloc(h, &h->nsub, (size_t)N)) &&
             dev_alloc(h, &h->colexp, h->emulated ? (size_t)N * h->ncap : (size_t)1) &&
             dev_alloc(h, &h->status, 1);
   if (ok && h->mixed) {
@@ -1692,6 +1700,14 @@ int elm_ddm_set_wait_limit(elm_ddm_handle* h, double seconds, int hold_release) 
     return fail(h, ELM_DDM_ERR_ARG, "set_wait_limit: hold_release must be 0 or 1");
   h->wait_ns = (unsigned long long)(seconds * 1e9);
   h->wait_hold = hold_release;
+  return ELM_DDM_OK;
+}
+
+int elm_ddm_set_ridge(elm_ddm_handle* h, double alpha) {
+  if (!h) return ELM_DDM_ERR_ARG;
+  if (!h->ridge) return fail(h, ELM_DDM_ERR_STATE, "set_ridge: the handle was set up without ELM_DDM_FLAG_RIDGE");
+  if (!(alpha >= 0.0) || !(alpha < 1.0)) return fail(h, ELM_DDM_ERR_ARG, "set_ridge: alpha must be in [0, 1)");
+  h->ridge_alpha = alpha;
   return ELM_DDM_OK;
 }
 

@@ -266,6 +266,42 @@ cudaError_t launch_get_points(const double* xy, const double* nrm, int m_max, co
   return cudaGetLastError();
 }
 
+// Tikhonov rows of subdomain s (one CTA): lambda = alpha * the largest column norm of K^s
+// over its collocation rows and real columns, then K[ms + (n - n_s) + j][j] = lambda for
+// j < n_s (the rows were written as zeros by the assembly).
+__global__ void __launch_bounds__(256) k_ridge_rows(double* __restrict__ K, long long kstride, int ld,
+                                                   const int* __restrict__ cnt, const int* __restrict__ nsub,
+                                                   int n, double alpha) {
+  const int s = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ms = cnt[3 * s] + cnt[3 * s + 1] + cnt[3 * s + 2], ns = nsub[s];
+  double* Ks = K + (size_t)s * kstride;
+  __shared__ double wmax[8];
+  double mx = 0.0;
+  for (int j = warp; j < ns; j += 8) {
+    double a = 0.0;
+    for (int r = lane; r < ms; r += 32) a = fma(Ks[r + (size_t)j * ld], Ks[r + (size_t)j * ld], a);
+    a = warp_sum(a);
+    mx = fmax(mx, a);
+  }
+  if (lane == 0) wmax[warp] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < 8; ++w) m = fmax(m, wmax[w]);
+    wmax[0] = alpha * sqrt(m);
+  }
+  __syncthreads();
+  const double lam = wmax[0];
+  const int r0 = ms + (n - ns);
+  for (int j = threadIdx.x; j < ns; j += 256) Ks[(r0 + j) + (size_t)j * ld] = lam;
+}
+
+cudaError_t launch_ridge_rows(double* K, long long kstride, int ld, const int* cnt, const int* nsub, int N, int n,
+                              double alpha, cudaStream_t st) {
+  k_ridge_rows<<<N, 256, 0, st>>>(K, kstride, ld, cnt, nsub, n, alpha); count_launch();
+  return cudaGetLastError();
+}
+
 __global__ void k_zero_pad_theta(double* __restrict__ W, double* __restrict__ b, const int* __restrict__ nsub,
                                  int n) {
   const int s = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;

@@ -28,7 +28,7 @@ SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve"
            "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order",
            "elm_ddm_profile_only", "elm_ddm_solve_cg", "elm_ddm_set_coefficient",
            "elm_ddm_solve_pcg", "elm_ddm_get_points", "elm_ddm_set_wait_limit",
-           "elm_ddm_fp64_gemm", "elm_ddm_fp64_gemm_workspace", "elm_ddm_set_tuning")
+           "elm_ddm_fp64_gemm", "elm_ddm_fp64_gemm_workspace", "elm_ddm_set_tuning", "elm_ddm_set_ridge")
 TUNE_PANEL_CTAS, TUNE_UPD_GRID = 0, 1
 GEMM_TILE32, GEMM_TILE64, GEMM_PERSISTENT, GEMM_FUSED_SPLIT = range(4)
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
@@ -52,6 +52,7 @@ FLAG_SCHUR_CG = 2
 FLAG_DIRECT_ASSEMBLY = 4
 FLAG_MIXED = 8
 FLAG_NEURONS_PER_SUB = 16
+FLAG_RIDGE = 32
 OP_POISSON, OP_VARCOEF = 0, 1
 
 
@@ -90,6 +91,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_get_points.argtypes = [P, I, P, P]
     lib.elm_ddm_set_wait_limit.argtypes = [P, ctypes.c_double, I]
     lib.elm_ddm_set_tuning.argtypes = [P, I, I]
+    lib.elm_ddm_set_ridge.argtypes = [P, ctypes.c_double]
     LL = ctypes.c_longlong
     lib.elm_ddm_fp64_gemm_workspace.argtypes = [I, I, I, I]
     lib.elm_ddm_fp64_gemm_workspace.restype = ctypes.c_size_t
@@ -137,9 +139,9 @@ class Solver:
 
     def __init__(self, geom, n_neurons: int, max_rhs: int = 1, stream=None, fp64_simt: bool = False,
                  schur_cg: bool = False, op: int = OP_POISSON, direct_assembly: bool = False,
-                 mixed: bool = False, neurons=None):
+                 mixed: bool = False, neurons=None, ridge: float | None = None):
         """neurons: None (n_neurons in every subdomain) or int [N] per-subdomain counts <= n_neurons
-        (ELM_DDM_FLAG_NEURONS_PER_SUB)."""
+        (ELM_DDM_FLAG_NEURONS_PER_SUB).  ridge: None, or alpha of ELM_DDM_FLAG_RIDGE."""
         import torch
         self.lib = load()
         ga = geom if isinstance(geom, GeometryArrays) else GeometryArrays.from_geometry(geom)
@@ -149,7 +151,8 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         flags = ((FLAG_FP64_SIMT if fp64_simt else 0) | (FLAG_SCHUR_CG if schur_cg else 0) |
                  (FLAG_DIRECT_ASSEMBLY if direct_assembly else 0) | (FLAG_MIXED if mixed else 0) |
-                 (FLAG_NEURONS_PER_SUB if neurons is not None else 0))
+                 (FLAG_NEURONS_PER_SUB if neurons is not None else 0) |
+                 (FLAG_RIDGE if ridge is not None else 0))
         desc = Desc(N, self.n, m_max, ga.n_gamma, op, max_rhs, flags)
         h = ctypes.c_void_p()
         self._keep = ga
@@ -164,6 +167,9 @@ class Solver:
         if rc != OK:
             raise ElmDdmError(rc, self.lib.elm_ddm_last_error(None).decode())
         self.h = h
+        self.ridge = ridge
+        if ridge is not None:
+            self._check_rc(self.lib.elm_ddm_set_ridge(self.h, float(ridge)))
 
     # -- helpers
     def _check_rc(self, rc):
@@ -268,7 +274,8 @@ class Solver:
 
     def _export_shape(self, what, s):
         mi, mb, mg = (int(v) for v in self._keep.counts[s])
-        pad = self.n - int(self._counts_arg[s, 3]) if self._counts_arg.shape[1] == 4 else 0
+        ns = int(self._counts_arg[s, 3]) if self._counts_arg.shape[1] == 4 else self.n
+        pad = self.n - ns + (ns if self.ridge is not None else 0)
         if what == BUF_K:
             return mi + mb + mg + pad, self.n + mg
         if what == BUF_A:

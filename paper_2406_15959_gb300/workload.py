@@ -526,6 +526,89 @@ def varcoef_grf_4x4_n800() -> Workload:
                  coef="grf", coef_seed=6, name="varcoef_grf_4x4_n800")
 
 
+def make_paper_grid_geometry(G: int, n_grid: int = 257) -> Geometry:
+    """The paper's collocation layout (Section 4.2): the global uniform n_grid x n_grid grid
+    of [0, 1]^2 split among G x G subdomains whose boundaries lie on grid lines.  Subdomain
+    rows: its grid points strictly inside (interior), its grid points on the outer boundary
+    (boundary; a point where an interface line meets the outer boundary is a boundary row
+    of both subdomains), and the grid points strictly inside each of its interface edges
+    (interface; one unknown per point, shared by the two subdomains of the edge).  The
+    cross points, where four subdomains meet, are left out: with them the corner rule of
+    the remark in Section 3 would apply (one flux row per edge at the point), and they are
+    (G - 1)^2 of n_grid^2 points.  Interface unknowns are numbered edge by edge like
+    make_geometry's (vertical edges first)."""
+    h = n_grid - 1
+    if h % G:
+        raise ValueError("the grid lines must contain the subdomain boundaries")
+    k = h // G                      # intervals per subdomain side
+    t = np.arange(n_grid, dtype=np.float64) / h
+    per = []
+    for s in range(G * G):
+        ix, iy = s % G, s // G
+        xs, ys = t[ix * k:(ix + 1) * k + 1], t[iy * k:(iy + 1) * k + 1]   # k + 1 lines each
+        X, Y = np.meshgrid(xs[1:-1], ys[1:-1], indexing="xy")
+        interior = np.stack([X.ravel(), Y.ravel()], axis=1)
+        bnd = []
+        if iy == 0:
+            bnd.append(np.stack([xs, np.zeros(k + 1)], axis=1))
+        if iy == G - 1:
+            bnd.append(np.stack([xs, np.ones(k + 1)], axis=1))
+        if ix == 0:
+            bnd.append(np.stack([np.zeros(k + 1), ys], axis=1))
+        if ix == G - 1:
+            bnd.append(np.stack([np.ones(k + 1), ys], axis=1))
+        bnd = np.unique(np.concatenate(bnd), axis=0) if bnd else np.zeros((0, 2))
+        ifc, nrm, dof = [], [], []
+        for e in _EDGES:
+            eid = _edge_id(G, G, ix, iy, e)
+            if eid is None:
+                continue
+            if e in ("left", "right"):
+                xe = t[(ix + (1 if e == "right" else 0)) * k]
+                pts = np.stack([np.full(k - 1, xe), t[iy * k + 1:(iy + 1) * k]], axis=1)
+            else:
+                ye = t[(iy + (1 if e == "top" else 0)) * k]
+                pts = np.stack([t[ix * k + 1:(ix + 1) * k], np.full(k - 1, ye)], axis=1)
+            ifc.append(pts)
+            nrm.append(np.tile(np.array(_NORMALS[e]), (k - 1, 1)))
+            dof.append(eid * (k - 1) + np.arange(k - 1))
+        ifc = np.concatenate(ifc) if ifc else np.zeros((0, 2))
+        nrm = np.concatenate(nrm) if nrm else np.zeros((0, 2))
+        dof = np.concatenate(dof).astype(np.int32) if dof else np.zeros(0, np.int32)
+        per.append((interior, bnd, ifc, nrm, dof))
+    m_max = max(len(a) + len(b) + len(c) for a, b, c, _, _ in per)
+    N = G * G
+    counts = np.zeros((N, 3), np.int32)
+    xy = np.zeros((N, m_max, 2))
+    nr = np.zeros((N, m_max, 2))
+    dd = np.full((N, m_max), -1, np.int32)
+    for s, (interior, bnd, ifc, nrm, dof) in enumerate(per):
+        mi, mb, mg = len(interior), len(bnd), len(ifc)
+        counts[s] = (mi, mb, mg)
+        xy[s, :mi] = interior
+        xy[s, mi:mi + mb] = bnd
+        xy[s, mi + mb:mi + mb + mg] = ifc
+        nr[s, mi + mb:mi + mb + mg] = nrm
+        dd[s, mi + mb:mi + mb + mg] = dof
+    n_gamma = 2 * G * (G - 1) * (k - 1)
+    return Geometry(G, G, k - 1, k - 1, k + 1, k - 1, counts, xy, nr, dd, n_gamma)
+
+
+def paper_grid_workload(G: int, n_total: int = 65536, theta: str = "paper", seed: int = 0,
+                        source: str = "sin2pi_exp", n_grid: int = 257, n_test_side: int = 100) -> Workload:
+    """The paper's Poisson experiments (Section 4.2, Table 2; Table 1 with other theta
+    modes): n_total neurons split evenly over G x G subdomains, the global n_grid^2
+    collocation grid (make_paper_grid_geometry), u = sin(2 pi x) e^y by default, theta by
+    Eq. (4.3) with c = 1/8 (``paper``), or ``global_unit`` (Table 1's manual l = 1) or
+    ``he`` (Table 1's He initialisation)."""
+    geom = make_paper_grid_geometry(G, n_grid)
+    n = n_total // (G * G)
+    W, b = draw_theta(geom, n, theta, seed, c=1.0 / 8.0)
+    src = make_source(source, seed)
+    txy, own = test_points(geom, n_test_side)
+    return Workload(f"paper_grid_{G}x{G}_{theta}", geom, n, W, b, src, rhs_rows(geom, src), txy, own)
+
+
 def mixed_16x16_n60_local() -> Workload:
     """16 x 16 subdomains with few neurons (60, 40 x 40 interior points, 40 points per edge) and
     local U(-1, 1) weights: kappa(K^s) ~ 1e6, well-conditioned enough for the mixed-precision
@@ -536,6 +619,9 @@ def mixed_16x16_n60_local() -> Workload:
 
 
 WORKLOADS = {
+    "paper_grid_4x4": lambda: paper_grid_workload(4, seed=41),
+    "paper_grid_8x8": lambda: paper_grid_workload(8, seed=81),
+    "paper_grid_16x16": lambda: paper_grid_workload(16, seed=161),
     "mixed_16x16_n60_local": mixed_16x16_n60_local,
     "varcoef_4x4_n800": varcoef_4x4_n800,
     "varcoef_grf_4x4_n800": varcoef_grf_4x4_n800,

@@ -600,3 +600,27 @@ def test_mixed_precision_refinement_system_converges_to_the_method_result():
                      n_test_side=10)
     etas_p, _, _ = _refined_solve(paper, iters=6)
     assert not (min(etas_p[2:]) < 0.5)                       # no contraction: a stall
+
+
+def test_ridge_zero_is_the_exact_least_squares_solution():
+    """ridge_rows with alpha = 0 adds zero rows: the oracle's result is unchanged."""
+    w = tiny(gx=2, gy=2, seed=3)
+    a = O.solve(w.geom, w.W, w.b, w.rhs)
+    z = O.solve(w.geom, w.W, w.b, w.rhs, ridge=0.0)
+    assert np.linalg.norm(z.u_gamma - a.u_gamma) <= 1e-12 * np.linalg.norm(a.u_gamma)
+    np.testing.assert_allclose(z.c, a.c, rtol=1e-10, atol=1e-12 * np.abs(a.c).max())
+
+
+def test_ridge_single_subdomain_is_ridge_regression():
+    """N = 1 with the Tikhonov rows: c = (K^T K + lambda^2 I)^{-1} K^T F with
+    lambda = alpha * max_j |K_j| (the normal equations of ridge regression, solved by LU:
+    a route independent of the augmented QR)."""
+    w = tiny(gx=1, gy=1, n=15, mi=7, p=6, seed=2)
+    g = w.geom
+    K, _ = O.assemble_local(g.xy[0], g.nrm[0], g.counts[0], w.W[0], w.b[0])
+    F = O.rhs_local(w.rhs[0], g.counts[0])
+    alpha = 1e-3
+    lam = alpha * np.sqrt((K * K).sum(axis=0)).max()
+    c_ref = np.linalg.solve(K.T @ K + lam ** 2 * np.eye(K.shape[1]), K.T @ F)
+    res = O.solve(g, w.W, w.b, w.rhs, ridge=alpha)
+    np.testing.assert_allclose(res.c[0], c_ref, rtol=1e-9, atol=1e-10 * np.abs(c_ref).max())
