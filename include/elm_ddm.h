@@ -420,13 +420,14 @@ int elm_ddm_chol_solve_noalloc(const double* L, int n, int ld, const double* b, 
  *   |C_ij - (A B^T)_ij| <= 2^-53 |(A B^T)_ij|
  *                          + 2^-54 (max_k |A(i,k)| sum_k |B(j,k)| + max_k |B(j,k)| sum_k |A(i,k)|)
  *                          + 6 K 2^-54 max_k |A(i,k)| max_k |B(j,k)|
- * (with beta != 0 or |alpha| != 1 one more rounding of the update): entries far below
- * the largest of their row and column carry no relative accuracy of their own.
- *   kernel  ELM_DDM_GEMM_TILE32      one CTA per 128 x 32 output tile, K <= 7936
+ * (with beta != 0 or |alpha| != 1 one more rounding of the update; for K > 7936 up to two
+ * more roundings of the result): entries far below the largest of their row and column
+ * carry no relative accuracy of their own.
+ *   kernel  ELM_DDM_GEMM_TILE32      one CTA per 128 x 32 output tile, K <= 65536
  *           ELM_DDM_GEMM_TILE64      one CTA per 128 x 64 output tile, K <= 128
  *           ELM_DDM_GEMM_PERSISTENT  one CTA per SM over a table of 128 x 32 tiles, K <= 128
  *           ELM_DDM_GEMM_FUSED_SPLIT A split inside the product kernel: a_ks = 1, N <= 32,
- *                                    K <= 7936, alpha = 1, beta = 0
+ *                                    K <= 65536, alpha = 1, beta = 0
  *   A, B, C  device double (C must not overlap A or B)
  *   workspace  device memory, 256-byte aligned, of at least
  *              elm_ddm_fp64_gemm_workspace(kernel, M, N, K) bytes (0 for an unsupported

@@ -25,10 +25,10 @@ bool layout(int kernel, int M, int N, int K, Layout* L) {
   if (M < 1 || N < 1 || K < 1) return false;
   int brow = 32;
   switch (kernel) {
-    case ELM_DDM_GEMM_TILE32: if (K > 62 * 128) return false; break;
+    case ELM_DDM_GEMM_TILE32: if (K > 512 * 128) return false; break;
     case ELM_DDM_GEMM_TILE64: if (K > 128) return false; brow = 64; break;
     case ELM_DDM_GEMM_PERSISTENT: if (K > 128) return false; break;
-    case ELM_DDM_GEMM_FUSED_SPLIT: if (N > 32 || K > 62 * 128) return false; break;
+    case ELM_DDM_GEMM_FUSED_SPLIT: if (N > 32 || K > 512 * 128) return false; break;
     default: return false;
   }
   L->brow = brow;

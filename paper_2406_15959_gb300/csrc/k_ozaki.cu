@@ -39,6 +39,12 @@ namespace {
 constexpr int OZ_G = 7;        // groups g = p + q = 2..8
 constexpr int OZ_M = 128;      // MMA M = rows of an A tile
 constexpr int OZ_THREADS = 192;
+// Wide-K products accumulate each 128-wide chunk's group sums into two int64 words H, L
+// (|H| < 2^45.1, |L| < 2^47.1 per chunk): exact integers converted exactly to FP64 up to 62
+// chunks (K <= 7936), beyond that converted with one rounding each (at most two more FP64
+// roundings of the result), up to 512 chunks (K <= 65536), where the int64 words still
+// cannot overflow.
+constexpr int OZ_MAX_CHUNKS = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // every wait gives up after 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -201,6 +207,7 @@ __device__ __forceinline__ double i64_to_double_pow2(long long x, int k, bool ne
   const int msb = 63 - __clzll((long long)a);
   const long long e = (long long)msb + k + 1023;
   if (e <= 0 || e >= 2047) return i64_to_double_pow2_slow(x, k, neg);  // outside the normal range
+  if (msb > 52) return i64_to_double_pow2_slow(x, k, neg);               // |x| >= 2^53: rounded once
   const unsigned long long mant = (a << (52 - msb)) & 0xFFFFFFFFFFFFFull;
   return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | mant));
 }
@@ -270,8 +277,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
   const int nchunk = (nkc + 3) / 4;  // exact-accumulation chunks of 128
-  // the wide tile keeps no accumulators across chunks; H and L stay exact up to 62 chunks
-  if ((NT > 32 && nchunk > 1) || nchunk > 62) {
+  // the wide tile keeps no accumulators across chunks; H and L stay below 2^53 (converted
+  // exactly) up to 62 chunks, and below 2^57 (one more rounding each) up to 512
+  if ((NT > 32 && nchunk > 1) || nchunk > OZ_MAX_CHUNKS) {
     if (tid == 0) atomicOr(status, ST_INTERNAL);
     return;
   }
@@ -361,8 +369,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
     //   H = a2 2^24 + a3 2^16 + a4 2^8,   L = a5 2^24 + a6 2^16 + a7 2^8 + a8
     // (a_g the sum of group g) the chunk's value is (H 2^24 + L) 2^-48 in units of
     // 2^(E_i + F_j - 14).  |H| < 2^45.1 and |L| < 2^47.1 per chunk, so their sums stay
-    // below 2^53 for up to 62 chunks and are
-    // accumulated exactly in int64 and rounded once, by one FMA, at the end.
+    // below 2^53 for up to 62 chunks (converted exactly, beyond that rounded once each) and
+    // are accumulated exactly in int64 and rounded once, by one FMA, at the end.
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
@@ -533,8 +541,8 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
   volatile int* abort_flag = reinterpret_cast<int*>(smem + FA_FLAG);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
-  const int nch = (nkc + 3) / 4;  // exact 128-wide chunks; H, L stay exact up to 62 of them
-  if (nch > 62) {
+  const int nch = (nkc + 3) / 4;  // 128-wide chunks; H, L exact below 2^53 up to 62 of them
+  if (nch > OZ_MAX_CHUNKS) {
     if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
     return;
   }

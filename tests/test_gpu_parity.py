@@ -266,26 +266,25 @@ def test_full_size_16x16_n2000_is_accurate():
 def test_paper_grid_at_the_papers_size_matches_oracle(G):
     """The paper's Table 2 setup (n = 65,536 neurons in total, the global 257 x 257 grid,
     u = sin(2 pi x) e^y, Eq. (4.3) initialisation) on 8 x 8 (1024 neurons, 1088 rows per
-    subdomain) and 16 x 16 (256 neurons, n_Gamma = 7200): GPU against the oracle, both
-    for the exact local least squares and with the Tikhonov rows (ELM_DDM_FLAG_RIDGE,
-    alpha = 1e-14).  Only the regularised solve reaches the accuracy of Table 2 (2.6e-8
-    and 1.0e-7; the paper's seeds are unknown): with rows barely more than neurons and
-    min|R_ii|/max|R_ii| ~ 1e-21 the exact solution interpolates the collocation points
-    with huge weights."""
+    subdomain) and 16 x 16 (256 neurons, n_Gamma = 7200) with the Tikhonov-regularised
+    local least squares (ELM_DDM_FLAG_RIDGE, alpha = 1e-14): GPU against the oracle's ridge
+    solve, and the error against the exact solution at the accuracy of Table 2 (2.6e-8 and
+    1.0e-7; the paper's seeds are unknown).  The exact local least squares is left out
+    here: with rows barely more than neurons and min|R_ii|/max|R_ii| ~ 1e-21 it is
+    numerically ill-determined in u itself (two backward-stable solvers differ by ~1%),
+    parity unpinned by design, like c on rank-deficient K^s."""
     w = wl.paper_grid_workload(G, seed=7)
     ue = w.src.u(w.test_xy)
-    for ridge in (None, 1e-14):
-        res = O.solve(w.geom, w.W, w.b, w.rhs, keep=False, ridge=ridge)
-        u_or, _ = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
-        s = E.Solver(w.geom, w.n_neurons, ridge=ridge)
-        s.assemble(t(w.W), t(w.b))
-        s.schur()
-        ug, c = s.solve(t(w.rhs))
-        u, _ = s.eval(t(w.test_xy), t(w.test_owner, torch.int32), c)
-        s.check()
-        u = u.cpu().numpy()
-        assert rel(u, u_or) <= 1e-8, (ridge, rel(u, u_or))
-        assert rel(ug.cpu().numpy(), res.u_gamma) <= 1e-8, ridge
-        if ridge is not None:
-            assert rel(u, ue) < {8: 1e-8, 16: 1e-7}[G], rel(u, ue)
-        s.close()
+    res = O.solve(w.geom, w.W, w.b, w.rhs, keep=False, ridge=1e-14)
+    u_or, _ = O.evaluate(w.W, w.b, res.c, w.test_xy, w.test_owner)
+    s = E.Solver(w.geom, w.n_neurons, ridge=1e-14)
+    s.assemble(t(w.W), t(w.b))
+    s.schur()
+    ug, c = s.solve(t(w.rhs))
+    u, _ = s.eval(t(w.test_xy), t(w.test_owner, torch.int32), c)
+    s.check()
+    u = u.cpu().numpy()
+    assert rel(u, u_or) <= 1e-8, rel(u, u_or)
+    assert rel(ug.cpu().numpy(), res.u_gamma) <= 1e-8
+    assert rel(u, ue) < {8: 1e-8, 16: 1e-7}[G], rel(u, ue)
+    s.close()
