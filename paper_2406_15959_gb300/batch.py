@@ -303,14 +303,17 @@ def serve_in_waves(instances, max_gamma: int = 32768, max_pad: float = 0.25, bud
 
 def _workspace_estimate(ws) -> int:
     """Device bytes a batch of these instances needs (dominant terms: [K | J], the Schur
-    matrix, the split planes ~ 2.2 x K)."""
+    matrix, the split planes ~ 2.2 x K with 32-column QR operands, plus what the outer QR
+    blocks of up to 128 columns add: the explicit reflectors, W1, W2 and their digit
+    planes, nbo (36 ld + 44 (n + m_Gamma)) bytes per subdomain for nbo = 128 - 32)."""
     n = max(w.n_neurons for w in ws)
     rows = max(int(w.geom.counts.sum(1).max()) + n - w.n_neurons for w in ws)
     mg = max(int(w.geom.counts[:, 2].max()) for w in ws)
     subs = sum(w.geom.n_sub for w in ws)
     ng = sum(w.geom.n_gamma for w in ws)
     ld = -(-rows // 32) * 32
-    return int(3.2 * subs * ld * (n + mg) * 8 + 8 * ng * ng)
+    nbo = max(0, min(128, -(-n // 32) * 32) - 32)
+    return int(subs * (3.2 * ld * (n + mg) * 8 + nbo * (36 * ld + 44 * (n + mg))) + 8 * ng * ng)
 
 
 def _main(argv=None):

@@ -69,7 +69,8 @@ struct OzDesc {
   int lower_off = 0;
   // fused-split launches: rows i < lead of A are read from At2 (same row stride a_rs) and
   // take their exponent bounds from Ae2, instead of At and Ae, so one product can stack
-  // two FP64 operands with equal leading dimension
+  // two FP64 operands with equal leading dimension (for the B-split launch these three
+  // describe the leading rows of B)
   const void* At2 = nullptr;
   const int* Ae2 = nullptr;
   int lead = 0;
@@ -104,6 +105,11 @@ cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int 
 // C = A B^T with the FP64 A split inside the kernel (At = FP64 A, a_rs its row stride, K
 // contiguous; Ae its row exponents), B split as usual with row_tile 32, N <= 32, beta = 0.
 cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned* status,
+                            cudaStream_t st, int gmax = 8);
+// C = A B^T with A already split (M <= 128: one row tile) and the FP64 B operand split
+// inside the kernel: B row j at Bt + j * a_rs with exponent bound Be[j], or, for j < lead,
+// at At2 + j * a_rs with Ae2[j].  One CTA per 32 rows of B (max_tiles = the most tiles).
+cudaError_t launch_ozaki_fb(const OzDesc* d, int count, int max_tiles, unsigned* status,
                             cudaStream_t st, int gmax = 8);
 cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_tiles,
                         double alpha, double beta, int flags, cudaStream_t st);
@@ -151,14 +157,23 @@ cudaError_t launch_eval(const double* W, const double* b, int N, int n, int npts
                         double* grad, cudaStream_t st);
 
 // Householder panel [k0, k0+nbe) of every subdomain: R and the reflectors in place, tau,
-// the explicit reflectors in Vp.  T is formed afterwards by launch_form_t.
+// the explicit reflectors in Vp (column j at Vp + s*vstride + j*ld, rows k0 .. m_s - 1, and
+// rows vrow0 .. k0 - 1 zeroed).  T is formed afterwards by launch_form_t.
 cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
                             int nbe, double* tau, int n, double* Vp, long long vstride, unsigned* status,
-                            cudaStream_t st, bool fp32 = false, int pcl_pref = 0);
+                            cudaStream_t st, bool fp32, int pcl_pref, int vrow0);
 // Compact-WY T of panel [k0, k0+nbe) of every subdomain from G (v_l^T v_j at G[l*32 + j],
 // l < j, per subdomain at stride gstride) and tau; T [32 x 32] column-major at T + s*tstride.
 cudaError_t launch_form_t(const double* G, long long gstride, const double* tau, int n, int k0, int nbe,
                           int N, double* T, long long tstride, cudaStream_t st);
+// Compact-WY T of a block of w <= 128 columns [k0, k0+w) (several panels) from its Gram
+// matrix G (v_l^T v_j at G[j*gld + l], l < j, per subdomain at stride gstride): T [w x w]
+// column-major with leading dimension tld at Tw + s*twstride; its diagonal 32-block
+// starting at column dcol (the block's last panel) is also written to Td + s*tdstride
+// (column-major, 32 x 32).
+cudaError_t launch_form_t_wide(const double* G, long long gstride, int gld, const double* tau, int n,
+                               int k0, int w, int N, double* Tw, long long twstride, int tld,
+                               double* Td, long long tdstride, int dcol, cudaStream_t st);
 cudaError_t launch_trsm_y(double* Y, long long ystride, int mgld, const double* K,
                           long long kstride, int ld, const int* mg, int mgmax, int N, int n,
                           cudaStream_t st);

@@ -27,7 +27,10 @@ struct LaunchRec {
              // 4 = persistent tensor-core digit GEMM for K <= 64 (max_tiles = total tiles),
              // 5 = tensor-core digit GEMM with the FP64 A operand split in the kernel,
              // 6 = diagonal step of the blocked Y = A R^{-1} (off = first column, nt = width),
-             // 7 = compact-WY T of QR panel `off` from the Gram rows of its W1 product
+             // 7 = compact-WY T of QR panel `off` from the Gram rows of its W1 product,
+             // 8 = compact-WY T of the outer QR block of nt columns from column toff, whose
+             //     last panel is `off`,
+             // 9 = tensor-core digit GEMM with the FP64 B operand split in the kernel
   int off, count, max_tiles;  // split: max_tiles = blocks of k_split, nt = max rows
   bool ta, tb;
   double alpha, beta;
@@ -57,6 +60,18 @@ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 // Digit groups g = p + q of the low-precision local products (the 10 leading digit pairs:
 // an error below about 2^-28 of the row and column maxima, against the FP32 panels' 2^-24).
 constexpr int LO_GMAX = 5;
+
+// Two-level blocking of the tensor-core QR: 32-column Householder panels inside outer
+// blocks of QR_NBO columns.  Each panel updates only the rest of its outer block; the
+// columns beyond it are updated once per outer block, with the block's aggregated
+// compact-WY factor (K = QR_NBO in the update product instead of 32), so the trailing
+// matrix is read and written n / QR_NBO times instead of n / 32.
+#ifndef ELM_QR_NBO
+#define ELM_QR_NBO 128
+#endif
+constexpr int QR_NBO = ELM_QR_NBO;
+static_assert(QR_NBO % QR_NB == 0 && QR_NBO >= QR_NB && QR_NBO <= 128,
+              "outer QR block: a multiple of the panel width, at most 128 (one product chunk)");
 
 std::string g_setup_error;
 
@@ -146,6 +161,10 @@ struct elm_ddm_handle {
   int fwd_grid = 0, bwd_grid = 0;  // their grids (0: one launch per block step instead)
   // device buffers
   double *K = nullptr, *Am = nullptr, *tau = nullptr, *T = nullptr, *Vp = nullptr;
+  // two-level QR (tensor-core path): compact-WY T of each outer block of QR_NBO columns,
+  // [N][QR_NBO][QR_NBO] column-major, and where each panel writes its explicit reflectors
+  double* Tab = nullptr;
+  std::vector<int> panel_vcol, panel_vrow0;  // per panel: column of Vp, first zeroed row
   double *W1 = nullptr, *W2 = nullptr, *D = nullptr, *M = nullptr, *S = nullptr;
   double *Mdiag = nullptr, *thW = nullptr, *thb = nullptr, *xy = nullptr, *nrm = nullptr;
   double* cinv = nullptr;             // inverses of the Cholesky diagonal blocks, one per step
@@ -327,6 +346,11 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
     else if (L.kind == 7)
       ELM_LAUNCH(h, launch_form_t(h->W1, h->wstride, h->tau, h->n, L.off * QR_NB, L.nt, h->N,
                                   h->T + (size_t)L.off * QR_NB * QR_NB, h->tstride, h->st), "form_t");
+    else if (L.kind == 8)
+      ELM_LAUNCH(h, launch_form_t_wide(h->W1, h->wstride, QR_NBO, h->tau, h->n, L.toff, L.nt, h->N, h->Tab,
+                                       (long long)QR_NBO * QR_NBO, QR_NBO,
+                                       h->T + (size_t)L.off * QR_NB * QR_NB, h->tstride,
+                                       L.off * QR_NB - L.toff, h->st), "form_t");
     else if (L.kind == 6)
       ELM_LAUNCH_F(h, launch_trsm_y_diag(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg,
                                          h->mgmax, h->N, h->n, L.off, h->st), nm, L.flops);
@@ -342,6 +366,9 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
     } else if (L.kind == 4)
       ELM_LAUNCH_FB(h, launch_ozaki_upd(h->od + L.off, L.count, h->ut + L.toff, L.max_tiles, L.alpha,
                                         L.beta, L.flags, h->status, h->st, h->tune_upd_grid, gmax), nm,
+                    L.flops, L.bytes);
+    else if (L.kind == 9)
+      ELM_LAUNCH_FB(h, launch_ozaki_fb(h->od + L.off, L.count, L.max_tiles, h->status, h->st, gmax), nm,
                     L.flops, L.bytes);
     else
       ELM_LAUNCH_FB(h, launch_ozaki_fa(h->od + L.off, L.count, L.max_tiles, h->status, h->st, gmax), nm,
@@ -575,8 +602,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->astride = (long long)h->mgld * n;
   h->mstride = (long long)h->mgld * h->mgld;
   h->tstride = (long long)h->nblk * QR_NB * QR_NB;
-  h->vstride = (long long)h->ld * QR_NB;
-  h->wstride = (long long)QR_NB * h->ncap;
+  h->vstride = (long long)h->ld * QR_NBO;
+  h->wstride = (long long)QR_NBO * h->ncap;
   for (const Edge& e : h->edges) h->mdiag_elems += (size_t)e.len * e.len;
   for (int s = 0; s < N; ++s)
     h->asm_bytes += 8.0 * ((double)h->ms_h[s] * (n + h->mg_h[s]) + (double)h->mg_h[s] * n);
@@ -650,6 +677,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->Am, (size_t)N * h->astride) &&
             dev_alloc(h, &h->tau, (size_t)N * n) && dev_alloc(h, &h->T, (size_t)N * h->tstride) &&
             dev_alloc(h, &h->Vp, (size_t)N * h->vstride) &&
+            dev_alloc(h, &h->Tab, (size_t)N * QR_NBO * QR_NBO) &&
             dev_alloc(h, &h->W1, (size_t)N * h->wstride) &&
             dev_alloc(h, &h->W2, (size_t)N * h->wstride) &&
             dev_alloc(h, &h->D, (size_t)N * h->mstride) &&
@@ -716,9 +744,11 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   // (A2^T is split inside the fused product kernel: only its row exponents are stored)
   const size_t s1 = 0, e1 = 0;  // (unused region)
-  const size_t s2 = al(oz_split_elems(QR_NB, mpmax, 32) * 2), e2 = al((size_t)QR_NB * 4);
-  const size_t s3 = al(oz_split_elems(mpmax, QR_NB, 128) * 2), e3 = al((size_t)mpmax * 4);
-  const size_t s4 = al(oz_split_elems(n2max, QR_NB, 32) * 2), e4 = al((size_t)n2max * 4);
+  // (QR operands for an outer block of up to min(QR_NBO, n) reflectors)
+  const int nbo = std::min(QR_NBO, round_up(n, QR_NB));
+  const size_t s2 = al(oz_split_elems(nbo, mpmax, 128) * 2), e2 = al((size_t)nbo * 4);
+  const size_t s3 = al(oz_split_elems(mpmax, nbo, 128) * 2), e3 = al((size_t)mpmax * 4);
+  const size_t s4 = al(oz_split_elems(n2max, nbo, 32) * 2), e4 = al((size_t)n2max * 4);
   // D_s / M_s products: Q_G as both operands, Y as the left operand (K = n_N)
   const int mgm = std::max(mgmax, 1);
   const size_t s5 = al(oz_split_elems(mgm, n, 128) * 2), e5 = al((size_t)mgm * 4);
@@ -727,8 +757,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   // Y = A R^{-1} updates: the 64-row block of R to the right of the diagonal (Y_b reuses s7)
   const size_t s8 = al(oz_split_elems(n, 64, 32) * 2), e8 = al((size_t)n * 4);
   // W2^T = W1^T T per QR panel: W1^T (rows = trailing columns) and T^T
-  const size_t s9 = al(oz_split_elems(n2max, QR_NB, 128) * 2), e9 = al((size_t)n2max * 4);
-  const size_t s10 = al(oz_split_elems(QR_NB, QR_NB, 32) * 2), e10 = al((size_t)QR_NB * 4);
+  const size_t s9 = al(oz_split_elems(n2max, nbo, 128) * 2), e9 = al((size_t)n2max * 4);
+  const size_t s10 = al(oz_split_elems(nbo, nbo, 32) * 2), e10 = al((size_t)nbo * 4);
   const size_t per_sub = s1 + e1 + s2 + e2 + s3 + e3 + s4 + e4 + s5 + e5 + s6 + e6 + s7 + e7 + s8 + e8 +
                          s9 + e9 + s10 + e10;
   const size_t c1 = al(oz_split_elems(std::max(restmax, 1), CHOL_NB, 128) * 2);
@@ -861,6 +891,20 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
     recs.push_back(L);
   };
+  // C = A B^T with B = FP64 operand split inside the kernel (M <= 128, beta = 0)
+  auto add_fb_rec = [&](std::vector<LaunchRec>& recs, const std::vector<OzDesc>& batch, const char* name) {
+    LaunchRec L{9, (int)ods.size(), 0, 0, false, false, 1.0, 0.0, 0, 0.0, 0};
+    L.name = name;
+    for (const OzDesc& d : batch) {
+      if (d.M <= 0 || d.N <= 0) continue;
+      ods.push_back(d);
+      L.count++;
+      L.max_tiles = std::max(L.max_tiles, (d.N + 31) / 32);
+      L.flops += 2.0 * d.M * d.N * d.K;
+      L.bytes += 8.0 * ((double)d.M * d.K + (double)d.N * d.K + (double)d.M * d.N);
+    }
+    recs.push_back(L);
+  };
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, n - k0);
     double pf = 0.0, pb = 0.0;
@@ -871,65 +915,86 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
     h->panel_flops.push_back(pf);
     h->panel_bytes.push_back(pb);
-    // W1 = V^T [V | A2]: its first nbe rows of W1^T are v_l^T v_j (what T needs,
-    // launch_form_t), the rest V^T A2 (the FP64 back end takes V^T [P | A2], P the panel's
-    // stored columns, whose rows give the same v_l^T v_j for l < j exactly).  Then
-    // W2 = T^T W1 and A2 -= V W2 on the trailing columns only.  With the tensor-core back
-    // end W1^T = [P | A2]^T V and A2 -= V W2 are digit-split products (W2 too, K = 32).
-    std::vector<GemmDesc> g1, g2, g3;
+    h->qr_first.push_back((int)h->qr_recs.size());
+    LaunchRec FT{7, b, 1, 0, false, false, 0.0, 0.0, 0, 0.0, nbe};
+    FT.name = "form_t";
+    if (!h->emulated) {
+      // FP64 back end, one level: W1 = V^T [P | A2] (P the panel's stored columns, whose
+      // rows give v_l^T v_j for l < j exactly: what T needs, launch_form_t), then
+      // W2 = T^T W1 and A2 -= V W2 on the trailing columns
+      h->panel_vcol.push_back(0);
+      h->panel_vrow0.push_back(k0);
+      std::vector<GemmDesc> g1, g2, g3;
+      for (int s = 0; s < N; ++s) {
+        const int n2 = n + h->mg_h[s] - (k0 + nbe), mp = h->ms_h[s] - k0;
+        if (mp <= 0) continue;
+        double* Ks = h->K + (size_t)s * h->kstride;
+        const double* V = h->Vp + (size_t)s * h->vstride + k0;
+        double* PA2 = Ks + k0 + (size_t)k0 * ld;
+        double* w1 = h->W1 + (size_t)s * h->wstride;
+        double* w2 = h->W2 + (size_t)s * h->wstride;
+        const double* Tb = h->T + (size_t)s * h->tstride + (size_t)b * QR_NB * QR_NB;
+        g1.push_back({V, PA2, w1, nbe, n2 + nbe, mp, ld, ld, QR_NB});
+        if (n2 > 0) {
+          g2.push_back({Tb, w1 + (size_t)nbe * QR_NB, w2, nbe, n2, nbe, QR_NB, QR_NB, QR_NB});
+          g3.push_back({V, w2, PA2 + (size_t)nbe * ld, mp, n2, nbe, ld, QR_NB, ld});
+        }
+      }
+      add_gemm_rec(h->qr_recs, g1, true, false, 1.0, 0.0, 0);
+      h->qr_recs.push_back(FT);
+      add_gemm_rec(h->qr_recs, g2, true, false, 1.0, 0.0, 0);
+      add_gemm_rec(h->qr_recs, g3, false, false, -1.0, 1.0, 0);
+      continue;
+    }
+    // Tensor-core back end, two levels.  Panel b is panel j of the outer block of wo columns
+    // from k0o; its explicit reflectors go to column j * 32 of Vp, with rows k0o .. k0 - 1
+    // zeroed, so that columns 0 .. wo - 1 of Vp from row k0o are the block's V.
+    const int k0o = k0 / QR_NBO * QR_NBO, wo = std::min(QR_NBO, n - k0o);
+    const int np = (wo + QR_NB - 1) / QR_NB, j = (k0 - k0o) / QR_NB;
+    h->panel_vcol.push_back(j * QR_NB);
+    h->panel_vrow0.push_back(k0o);
     std::vector<SplitDesc> sp1, sp3, spt;
     std::vector<OzDesc> o1, o3, ot;
-    for (int s = 0; s < N; ++s) {
-      // the W1 product runs for every panel (T needs its Gram rows even when no trailing
-      // column is left); W2 and the update only when there are trailing columns
-      const int n2 = n + h->mg_h[s] - (k0 + nbe), mp = h->ms_h[s] - k0;
-      if (mp <= 0) continue;
-      double* Ks = h->K + (size_t)s * h->kstride;
-      const double* V = h->Vp + (size_t)s * h->vstride + k0;
-      double* PA2 = Ks + k0 + (size_t)k0 * ld;           // [P | A2], n2 + nbe columns
-      double* A2 = PA2 + (size_t)nbe * ld;
-      double* w1 = h->W1 + (size_t)s * h->wstride;
-      double* w1t = w1 + (size_t)nbe * QR_NB;             // rows of W1^T for the trailing columns
-      double* w2 = h->W2 + (size_t)s * h->wstride;
-      const double* Tb = h->T + (size_t)s * h->tstride + (size_t)b * QR_NB * QR_NB;
-      g1.push_back({V, PA2, w1, nbe, n2 + nbe, mp, ld, ld, QR_NB});
-      if (n2 > 0) {
-        g2.push_back({Tb, w1t, w2, nbe, n2, nbe, QR_NB, QR_NB, QR_NB});
-        g3.push_back({V, w2, A2, mp, n2, nbe, ld, QR_NB, ld});
-      }
-      if (h->emulated) {
+    if (j < np - 1) {
+      // Inner step: the rest of the outer block (n2i columns) takes this panel's reflectors.
+      // W1^T = [V | A2]^T V (A split inside the product: the first nbe rows are the Gram
+      // rows v_l^T v_j that T needs, from the explicit reflectors (|v| <= 1 with a unit
+      // diagonal, so the digit split keeps them to FP64 accuracy, where the stored panel
+      // columns would be truncated relative to R's entries); the rows of A2^T take the
+      // exponent bounds of their columns' original norms, which no orthogonal update of
+      // the column can exceed), T from the Gram rows, W2^T = W1^T T, A2 -= V W2 (K = 32).
+      const int n2i = k0o + wo - (k0 + nbe);
+      for (int s = 0; s < N; ++s) {
+        const int mp = h->ms_h[s] - k0;
+        if (mp <= 0) continue;
+        double* Ks = h->K + (size_t)s * h->kstride;
+        const double* V = h->Vp + (size_t)s * h->vstride + (size_t)j * QR_NB * ld + k0;
+        double* PA2 = Ks + k0 + (size_t)k0 * ld;           // [P | A2], n2i + nbe columns
+        double* A2 = PA2 + (size_t)nbe * ld;
+        double* w1 = h->W1 + (size_t)s * h->wstride;       // W1^T, row stride 32
+        double* w1t = w1 + (size_t)nbe * QR_NB;
+        double* w2 = h->W2 + (size_t)s * h->wstride;
+        const double* Tb = h->T + (size_t)s * h->tstride + (size_t)b * QR_NB * QR_NB;
         void* t2 = sub_region(s, 2); int* x2 = (int*)sub_region(s, 3);
         void* t3 = sub_region(s, 4); int* x3 = (int*)sub_region(s, 5);
         void* t4 = sub_region(s, 6); int* x4 = (int*)sub_region(s, 7);
-        // A = [V | A2]^T, split inside the product: the Gram rows from the explicit
-        // reflectors (|v| <= 1 with a unit diagonal, so the digit split keeps them to FP64
-        // accuracy, where the stored panel columns would be truncated relative to R's
-        // entries), with V's row exponents from its split as the B operand; the rows of
-        // A2^T take the exponent bounds of their columns' original norms, which no
-        // orthogonal update of the column can exceed (no pass over A2 per panel)
+        void* t9 = sub_region(s, 16); int* x9 = (int*)sub_region(s, 17);
+        void* t10 = sub_region(s, 18); int* x10 = (int*)sub_region(s, 19);
         sp1.push_back({V, ld, 1, nbe, mp, x2, t2, 32});              // V^T: rows = panel columns
-        OzDesc ow{PA2, h->colexp + (size_t)s * h->ncap + k0, t2, x2, w1, QR_NB, 1, n2 + nbe, nbe, mp, 0, ld};
+        OzDesc ow{PA2, h->colexp + (size_t)s * h->ncap + k0, t2, x2, w1, QR_NB, 1, n2i + nbe, nbe, mp, 0, ld};
         ow.At2 = V;   // rows i < nbe at V + i * ld, rows i >= nbe at PA2 + i * ld = A2
         ow.Ae2 = x2;
         ow.lead = nbe;
         o1.push_back(ow);
-        if (n2 <= 0) continue;
-        void* t9 = sub_region(s, 16); int* x9 = (int*)sub_region(s, 17);
-        void* t10 = sub_region(s, 18); int* x10 = (int*)sub_region(s, 19);
-        // W2^T = W1^T T as a tensor-core product: A = W1^T (row j = trailing column j,
-        // 32 contiguous values), B = T^T (row i = column i of the column-major T)
-        spt.push_back({w1t, QR_NB, 1, n2, nbe, x9, t9, 128});
+        // W2^T = W1^T T: A = W1^T (row r = column r of A2, 32 contiguous values), B = T^T
+        // (row i = column i of the column-major T)
+        spt.push_back({w1t, QR_NB, 1, n2i, nbe, x9, t9, 128});
         spt.push_back({Tb, QR_NB, 1, nbe, nbe, x10, t10, 32});
         spt.push_back({V, 1, ld, mp, nbe, x3, t3, 128});     // V: rows = matrix rows
-        ot.push_back({t9, x9, t10, x10, w2, QR_NB, 1, n2, nbe, nbe, 0});
-        sp3.push_back({w2, QR_NB, 1, n2, nbe, x4, t4, 32});  // W2^T: rows = trailing columns
-        o3.push_back({t3, x3, t4, x4, A2, 1, ld, mp, n2, nbe, 0});
+        ot.push_back({t9, x9, t10, x10, w2, QR_NB, 1, n2i, nbe, nbe, 0});
+        sp3.push_back({w2, QR_NB, 1, n2i, nbe, x4, t4, 32});  // W2^T: rows = columns of A2
+        o3.push_back({t3, x3, t4, x4, A2, 1, ld, mp, n2i, nbe, 0});
       }
-    }
-    h->qr_first.push_back((int)h->qr_recs.size());
-    LaunchRec FT{7, b, 1, 0, false, false, 0.0, 0.0, 0, 0.0, nbe};
-    FT.name = "form_t";
-    if (h->emulated) {
       add_split_rec(h->qr_recs, sp1, "split_qr_w");
       add_fa_rec(h->qr_recs, o1, "oz_qr_w");
       h->qr_recs.push_back(FT);
@@ -937,12 +1002,55 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       add_oz_rec(h->qr_recs, ot, 0, 1.0, 0.0, 0, "oz_qr_t");
       add_split_rec(h->qr_recs, sp3, "split_qr_update");
       add_oz_rec(h->qr_recs, o3, 0, -1.0, 1.0, 0, "oz_qr_update");
-    } else {
-      add_gemm_rec(h->qr_recs, g1, true, false, 1.0, 0.0, 0);
-      h->qr_recs.push_back(FT);
-      add_gemm_rec(h->qr_recs, g2, true, false, 1.0, 0.0, 0);
-      add_gemm_rec(h->qr_recs, g3, false, false, -1.0, 1.0, 0);
+      continue;
     }
+    // Outer step, after the block's last panel: W1 = V_o^T [V_o | A2] over the trailing
+    // columns, as one product whose A operand is V_o^T (all wo reflectors, split once) and
+    // whose B operand, the block's explicit reflectors then the trailing columns, is split
+    // inside the kernel (each trailing column once per outer block); its first wo columns
+    // are the block's Gram matrix.  Then T_o of the whole block (its last diagonal 32-block
+    // is this panel's T), W2^T = W1^T T_o and A2 -= V_o W2 (K = wo).
+    for (int s = 0; s < N; ++s) {
+      const int mpo = h->ms_h[s] - k0o, n2o = n + h->mg_h[s] - (k0o + wo);
+      if (mpo <= 0) continue;
+      double* Ks = h->K + (size_t)s * h->kstride;
+      const double* Vo = h->Vp + (size_t)s * h->vstride + k0o;  // wo columns from row k0o
+      double* Ao = Ks + k0o + (size_t)k0o * ld;                  // [P_o | A2], wo + n2o columns
+      double* A2 = Ao + (size_t)wo * ld;
+      double* w1 = h->W1 + (size_t)s * h->wstride;               // W1^T, row stride QR_NBO
+      double* w1t = w1 + (size_t)wo * QR_NBO;
+      double* w2 = h->W2 + (size_t)s * h->wstride;
+      const double* To = h->Tab + (size_t)s * QR_NBO * QR_NBO;
+      void* t2 = sub_region(s, 2); int* x2 = (int*)sub_region(s, 3);
+      void* t3 = sub_region(s, 4); int* x3 = (int*)sub_region(s, 5);
+      void* t4 = sub_region(s, 6); int* x4 = (int*)sub_region(s, 7);
+      void* t9 = sub_region(s, 16); int* x9 = (int*)sub_region(s, 17);
+      void* t10 = sub_region(s, 18); int* x10 = (int*)sub_region(s, 19);
+      sp1.push_back({Vo, ld, 1, wo, mpo, x2, t2, 128});            // V_o^T: rows = block columns
+      // C[i, j] = W1^T[j][i] at w1 + j * QR_NBO + i
+      OzDesc ob{t2, x2, Ao, h->colexp + (size_t)s * h->ncap + k0o, w1, 1, QR_NBO, wo, wo + n2o, mpo, 0, ld};
+      ob.At2 = Vo;  // B rows j < wo at Vo + j * ld (explicit reflectors), j >= wo at Ao + j * ld = A2
+      ob.Ae2 = x2;
+      ob.lead = wo;
+      o1.push_back(ob);
+      if (n2o <= 0) continue;
+      spt.push_back({w1t, QR_NBO, 1, n2o, wo, x9, t9, 128});
+      spt.push_back({To, QR_NBO, 1, wo, wo, x10, t10, 32});
+      spt.push_back({Vo, 1, ld, mpo, wo, x3, t3, 128});
+      ot.push_back({t9, x9, t10, x10, w2, QR_NBO, 1, n2o, wo, wo, 0});
+      sp3.push_back({w2, QR_NBO, 1, n2o, wo, x4, t4, 32});
+      o3.push_back({t3, x3, t4, x4, A2, 1, ld, mpo, n2o, wo, 0});
+    }
+    LaunchRec FW{8, b, 1, 0, false, false, 0.0, 0.0, 0, 0.0, wo};
+    FW.toff = k0o;
+    FW.name = "form_t";
+    add_split_rec(h->qr_recs, sp1, "split_qr_w");
+    add_fb_rec(h->qr_recs, o1, "oz_qr_w");
+    h->qr_recs.push_back(FW);
+    add_split_rec(h->qr_recs, spt, "split_qr_t");
+    add_oz_rec(h->qr_recs, ot, 0, 1.0, 0.0, 0, "oz_qr_t");
+    add_split_rec(h->qr_recs, sp3, "split_qr_update");
+    add_oz_rec(h->qr_recs, o3, 0, -1.0, 1.0, 0, "oz_qr_update");
   }
   h->qr_first.push_back((int)h->qr_recs.size());
   // Y = A R^{-1}, blocked by 64 columns: substitution on the diagonal block of R, then the
@@ -1244,8 +1352,9 @@ int elm_ddm_schur(elm_ddm_handle* h) {
   // (b) blocked Householder QR of [K^s | J]
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, h->n - k0);
-    ELM_LAUNCH_FB(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n, h->Vp,
-                                     h->vstride, h->status, h->st, h->lowfac, h->tune_panel),
+    ELM_LAUNCH_FB(h, launch_panel_qr(h->K, h->kstride, h->ld, h->ms, h->N, k0, nbe, h->tau, h->n,
+                                     h->Vp + (size_t)h->panel_vcol[b] * h->ld, h->vstride, h->status,
+                                     h->st, h->lowfac, h->tune_panel, h->panel_vrow0[b]),
                   "panel_qr", h->panel_flops[b], h->panel_bytes[b]);
     int rc = run_recs(h, h->qr_recs, h->qr_first[b], h->qr_first[b + 1] - h->qr_first[b],
                       "gemm_qr", lo_gmax);

@@ -29,6 +29,7 @@ bool layout(int kernel, int M, int N, int K, Layout* L) {
     case ELM_DDM_GEMM_TILE64: if (K > 128) return false; brow = 64; break;
     case ELM_DDM_GEMM_PERSISTENT: if (K > 128) return false; break;
     case ELM_DDM_GEMM_FUSED_SPLIT: if (N > 32 || K > 512 * 128) return false; break;
+    case ELM_DDM_GEMM_FUSED_SPLIT_B: if (M > 128 || K > 512 * 128) return false; break;
     default: return false;
   }
   L->brow = brow;
@@ -41,7 +42,7 @@ bool layout(int kernel, int M, int N, int K, Layout* L) {
   L->ea = o; o += al256((size_t)M * 4);
   L->eb = o; o += al256((size_t)N * 4);
   L->ta = o; o += kernel == ELM_DDM_GEMM_FUSED_SPLIT ? 0 : al256(oz_split_elems(M, K, 128) * 2);
-  L->tb = o; o += al256(oz_split_elems(N, K, brow) * 2);
+  L->tb = o; o += kernel == ELM_DDM_GEMM_FUSED_SPLIT_B ? 0 : al256(oz_split_elems(N, K, brow) * 2);
   L->total = o;
   return true;
 }
@@ -63,16 +64,19 @@ extern "C" int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, 
   if (((uintptr_t)workspace & 255) != 0) return ELM_DDM_ERR_ARG;
   if (kernel == ELM_DDM_GEMM_FUSED_SPLIT && (a_ks != 1 || alpha != 1.0 || beta != 0.0))
     return ELM_DDM_ERR_ARG;
+  if (kernel == ELM_DDM_GEMM_FUSED_SPLIT_B && (b_ks != 1 || alpha != 1.0 || beta != 0.0))
+    return ELM_DDM_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
   unsigned* status = reinterpret_cast<unsigned*>(ws + L.status);
   int* ea = reinterpret_cast<int*>(ws + L.ea);
   int* eb = reinterpret_cast<int*>(ws + L.eb);
-  const bool fused = kernel == ELM_DDM_GEMM_FUSED_SPLIT;
+  const bool fused = kernel == ELM_DDM_GEMM_FUSED_SPLIT, fused_b = kernel == ELM_DDM_GEMM_FUSED_SPLIT_B;
   SplitDesc sd[2] = {{A, a_rs, a_ks, M, K, ea, fused ? nullptr : ws + L.ta, 128},
-                     {B, b_rs, b_ks, N, K, eb, ws + L.tb, L.brow}};
-  OzDesc od{fused ? (const void*)A : (const void*)(ws + L.ta), ea, ws + L.tb, eb, C, c_rs, c_cs, M, N, K,
-            0, fused ? a_rs : 0};
+                     {B, b_rs, b_ks, N, K, eb, fused_b ? nullptr : ws + L.tb, L.brow}};
+  OzDesc od{fused ? (const void*)A : (const void*)(ws + L.ta), ea,
+            fused_b ? (const void*)B : (const void*)(ws + L.tb), eb, C, c_rs, c_cs, M, N, K,
+            0, fused ? a_rs : (fused_b ? b_rs : 0)};
   std::vector<int4> tiles;
   if (kernel == ELM_DDM_GEMM_PERSISTENT) {
     tiles.resize(L.tiles);
@@ -97,6 +101,7 @@ extern "C" int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, 
         e = launch_ozaki_upd(dod, 1, reinterpret_cast<const int4*>(ws + L.ut), L.tiles, alpha, beta, 0, status,
                              st);
         break;
+      case ELM_DDM_GEMM_FUSED_SPLIT_B: e = launch_ozaki_fb(dod, 1, (N + 31) / 32, status, st); break;
       default: e = launch_ozaki_fa(dod, 1, (M + 127) / 128, status, st); break;
     }
   }

@@ -26,6 +26,7 @@
 //               cp.async.bulk, warp 1 issues the 28 digit-pair MMAs per 16-wide k-step
 //               into 7 TMEM accumulators (one per g), warps 2..5 drain TMEM and write C
 //   k_ozaki_fa  wide-K product whose FP64 A operand is split inside the kernel
+//   k_ozaki_fb  wide-K product whose FP64 B operand is split inside the kernel
 //   k_ozaki_upd persistent product for K <= 128 over a table of output tiles
 #include "common.cuh"
 #include "digits.cuh"
@@ -733,6 +734,251 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
 }
 
 // ---------------------------------------------------------------------------------------
+// Wide-K product with the digit split of the FP64 B operand fused in: C = A B^T with A
+// (M <= 128 rows, one row tile) already split, and B (N rows, element (j, k) at
+// B[j * a_rs + k], K contiguous; rows j < lead from At2 with exponent bounds Ae2) read
+// from HBM once and split in the kernel.  One CTA per 32-row tile of B.  This is the
+// orientation of the outer-block W1 product of the two-level QR: A = V_o^T (all the
+// block's reflectors, M = the block width) and B = the trailing columns, so every trailing
+// column is split once per outer block, where the A-operand form would split it once per
+// 32-column slice of V_o.  Warp 0 streams the A planes of each 32-wide K step with
+// cp.async.bulk into a 3-stage ring; the 16 worker warps form 4 groups, group g splitting
+// the B tile of the K steps kc = g mod 4 into its own buffer (one 8-wide k group of one
+// row per thread, the group's next step prefetched); one thread of warp 1 issues the 28
+// digit-pair MMAs per 16-wide k-step into one of two TMEM accumulator sets; and all 16
+// worker warps drain each 128-wide chunk into exact int64 words while the MMAs of the
+// next one run.  Every mbarrier is waited on one phase at a time by each waiter (the A
+// ring in step order by the producer and the MMA thread, each B buffer by its own group
+// and the MMA thread), so the parity waits cannot alias a phase two steps away.
+constexpr int FB_WORKERS = 16;
+constexpr int FB_THREADS = 32 * (2 + FB_WORKERS);
+constexpr int FB_NS = 3;                           // A stages
+constexpr int FB_A = OZ_S * OZ_M * OZ_KC * 2;     // 57344 B of A planes per stage
+constexpr int FB_B = OZ_S * 32 * OZ_KC * 2;       // 14336 B of B planes per group buffer
+constexpr int FB_BOFF = FB_NS * FB_A;
+constexpr int FB_BAR = FB_BOFF + 4 * FB_B;        // AFULL[3] AEMPTY[3] BFULL[4] BEMPTY[4] TFULL[2] TEMPTY[2] DONE
+constexpr int FB_SLOT = FB_BAR + 160;
+constexpr int FB_FLAG = FB_SLOT + 16;
+constexpr int FB_SMEM = FB_FLAG + 16 + 1024;
+static_assert(FB_SMEM <= 227 * 1024, "B-split product exceeds the shared memory of one CTA");
+
+__global__ void __launch_bounds__(FB_THREADS, 1) k_ozaki_fb(const OzDesc* __restrict__ descs,
+                                                           unsigned* status, int gmax) {
+  const OzDesc d = descs[blockIdx.y];
+  const int tiles_n = (d.N + 31) / 32;
+  if ((int)blockIdx.x >= tiles_n) return;
+  if (d.M > OZ_M) {
+    if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
+    return;
+  }
+  const int bj = blockIdx.x;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar = sbase + FB_BAR;
+  const uint32_t AFULL = bar, AEMPTY = bar + 24, BFULL = bar + 48, BEMPTY = bar + 80, TFULL = bar + 112,
+                 TEMPTY = bar + 128, DONE = bar + 144;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + FB_SLOT);
+  volatile int* abort_flag = reinterpret_cast<int*>(smem + FB_FLAG);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
+  const int nch = (nkc + 3) / 4;
+  if (nch > OZ_MAX_CHUNKS) {
+    if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
+    return;
+  }
+
+  if (tid == 0) {
+    for (int i = 0; i < FB_NS; ++i) {
+      mbar_init(AFULL + 8 * i, 1);
+      mbar_init(AEMPTY + 8 * i, 1);
+    }
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(BFULL + 8 * i, 128);   // the 4 warps of group i
+      mbar_init(BEMPTY + 8 * i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(TFULL + 8 * i, 1);
+      mbar_init(TEMPTY + 8 * i, 32 * FB_WORKERS);
+    }
+    mbar_init(DONE, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *slot;
+
+  if (warp == 0) {
+    // ---------------- A planes (the single 128-row tile), in step order
+    if (lane == 0) {
+      int issued = 0;
+      for (int kc = 0; kc < nkc && !*abort_flag; ++kc) {
+        const int s = kc % FB_NS, use = kc / FB_NS;
+        if (!mbar_wait(AEMPTY + 8 * s, (use & 1) ^ 1)) { *abort_flag = 1; break; }
+        mbar_expect_tx(AFULL + 8 * s, FB_A);
+        const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(d.At) + (size_t)kc * OZ_S * OZ_M * OZ_KC;
+        bulk_g2s(sbase + s * FB_A, src, FB_A, AFULL + 8 * s);
+        issued = kc + 1;
+      }
+      for (int kc = (issued > FB_NS ? issued - FB_NS : 0); kc < issued; ++kc)
+        mbar_wait(AFULL + 8 * (kc % FB_NS), (kc / FB_NS) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(OZ_M, 32);
+      for (int kc = 0; kc < nkc && !*abort_flag; ++kc) {
+        const int s = kc % FB_NS, use = kc / FB_NS, c = kc >> 2, buf = c & 1, gb = kc & 3;
+        const bool chunk_start = (kc & 3) == 0;
+        if (chunk_start && !mbar_wait(TEMPTY + 8 * buf, ((c >> 1) & 1) ^ 1)) { *abort_flag = 1; break; }
+        if (!mbar_wait(AFULL + 8 * s, use & 1) || !mbar_wait(BFULL + 8 * gb, (kc >> 2) & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = sbase + s * FB_A, b0 = sbase + FB_BOFF + gb * FB_B;
+        const uint32_t dbase = tmem + buf * (OZ_G * 32);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+#pragma unroll
+          for (int g = 2; g <= OZ_S + 1; ++g) {
+            if (g > gmax) continue;  // digit groups beyond gmax are not formed
+#pragma unroll
+            for (int p = 1; p <= OZ_S; ++p) {
+              const int q = g - p;
+              if (q < 1 || q > OZ_S) continue;
+              const uint32_t first = (chunk_start && t == 0 && p == (g - 1 < OZ_S ? 1 : g - OZ_S));
+              const uint64_t ad = sdesc(a0 + (p - 1) * (OZ_M * OZ_KC * 2) + t * 256, 128, 512);
+              const uint64_t bd = sdesc(b0 + (q - 1) * (32 * OZ_KC * 2) + t * 256, 128, 512);
+              mma_bf16(dbase + (g - 2) * 32, ad, bd, idesc, first ? 0u : 1u);
+            }
+          }
+        }
+        mma_commit(AEMPTY + 8 * s);
+        mma_commit(BEMPTY + 8 * gb);
+        if ((kc & 3) == 3 || kc == nkc - 1) mma_commit(TFULL + 8 * buf);
+      }
+      mma_commit(DONE);
+      mbar_wait(DONE, 0);
+    }
+  } else {
+    // ---------------- workers: split B (group grp takes the K steps kc = grp mod 4), drain TMEM
+    const int ew = warp - 2, grp = ew >> 2;
+    // split item: tile row r (0..31), 8-wide k group kg; the 8 lanes of each quarter-warp
+    // cover 8 rows of one k group, so their 16-byte digit stores fill 128 contiguous bytes
+    const int r = (ew & 3) * 8 + (lane & 7), kg = lane >> 3;
+    const int gj = bj * 32 + r;
+    const bool row_ok = gj < d.N;
+    const bool lead_row = gj < d.lead;
+    const unsigned emax = row_ok ? (unsigned)(lead_row ? d.Ae2 : d.Be)[gj] : 0u;
+    const double* rowp = static_cast<const double*>(lead_row ? d.At2 : d.Bt) + (row_ok ? (size_t)gj * d.a_rs : 0);
+    const bool vec = ((reinterpret_cast<uintptr_t>(rowp) | (uintptr_t)d.a_rs * 8) & 15) == 0;
+    const int quarter = warp & 3, col0 = (ew >> 2) * 8;  // drain: TMEM lane quarter, 8 columns
+    const int drow = quarter * 32 + lane;                // row of A (and of C)
+    auto load = [&](int kc, double (&x)[8]) {
+      const int k0 = kc * OZ_KC + kg * 8;
+      if (row_ok && vec && k0 + 8 <= d.K) {
+        const double2* p2 = reinterpret_cast<const double2*>(rowp + k0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const double2 v = p2[j];
+          x[2 * j] = v.x;
+          x[2 * j + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = (row_ok && k0 + j < d.K) ? rowp[k0 + j] : 0.0;
+      }
+    };
+    long long H[8], Lw[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { H[j] = 0; Lw[j] = 0; }
+    bool alive = true;
+    auto drain = [&](int c) {
+      const int buf = c & 1;
+      if (!mbar_wait_warp(TFULL + 8 * buf, (c >> 1) & 1)) { alive = false; *abort_flag = 1; return; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t lb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (OZ_G * 32) + col0;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        uint32_t v[OZ_G][4];
+#pragma unroll
+        for (int g = 0; g < OZ_G; ++g) {
+          if (g + 2 <= gmax) tmem_ld4(lb + g * 32 + half * 4, v[g]);
+          else for (int j = 0; j < 4; ++j) v[g][j] = 0u;
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (half == 1) {
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(TEMPTY + 8 * buf);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          int a[OZ_G];
+#pragma unroll
+          for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][j]));
+          H[half * 4 + j] += ((long long)a[0] << 24) + ((long long)a[1] << 16) + ((long long)a[2] << 8);
+          Lw[half * 4 + j] +=
+              ((long long)a[3] << 24) + ((long long)a[4] << 16) + ((long long)a[5] << 8) + a[6];
+        }
+      }
+    };
+    double xn[8];
+    if (grp < nkc) load(grp, xn);
+    unsigned char* stB = smem + FB_BOFF + grp * FB_B;  // this group's B buffer
+    for (int kc = 0; kc < nkc && alive; ++kc) {
+      if ((kc & 3) == grp) {
+        uint32_t w[OZ_S][4];
+        split8(xn, emax, w);
+        if (kc + 4 < nkc) load(kc + 4, xn);  // this group's next step, in flight meanwhile
+        // the buffer's previous contents (step kc - 4) have been consumed by the MMAs
+        if (!mbar_wait_warp(BEMPTY + 8 * grp, ((kc >> 2) & 1) ^ 1)) { alive = false; *abort_flag = 1; break; }
+        const int off = tile_off32(r, kg * 8);
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p)
+          *reinterpret_cast<uint4*>(stB + 2 * ((size_t)p * 32 * OZ_KC + off)) =
+              make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(BFULL + 8 * grp);
+      }
+      if (((kc & 3) == 3 || kc == nkc - 1) && (kc >> 2) >= 1) drain((kc >> 2) - 1);
+    }
+    if (alive && nch >= 1) drain(nch - 1);
+    if (alive && drow < d.M) {
+      const int ed = d.Ae[drow];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int gc = bj * 32 + col0 + j;
+        if (gc < d.N) {
+          const int fj = (gc < d.lead ? d.Ae2 : d.Be)[gc];
+          double v = 0.0;
+          if (ed != 0 && fj != 0) {
+            const int k = ed + fj - 2044 - 62;
+            v = i64_to_double_pow2(H[j], k + 24, false) + i64_to_double_pow2(Lw[j], k, false);
+          }
+          d.C[(size_t)drow * d.c_rs + (size_t)gc * d.c_cs] = v;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Persistent update kernel for short products (K <= 128: the rank-32 QR update and the
 // Cholesky SYRK).  One CTA per SM walks the 128 x 32 tiles of the whole batch; two
 // shared-memory stages and two TMEM accumulator sets (7 x 32 columns each) let the loads
@@ -1057,6 +1303,23 @@ cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned*
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
     k_ozaki_fa<<<dim3(max_tiles, c), FA_THREADS, FA_SMEM, st>>>(d + off, status, gmax); count_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ozaki_fb(const OzDesc* d, int count, int max_tiles, unsigned* status,
+                            cudaStream_t st, int gmax) {
+  if (count <= 0 || max_tiles <= 0) return cudaSuccess;
+  if (gmax < 2 || gmax > OZ_S + 1) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_ozaki_fb, cudaFuncAttributeMaxDynamicSharedMemorySize, FB_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  for (int off = 0; off < count; off += 65535) {
+    const int c = count - off < 65535 ? count - off : 65535;
+    k_ozaki_fb<<<dim3(max_tiles, c), FB_THREADS, FB_SMEM, st>>>(d + off, status, gmax); count_launch();
   }
   return cudaGetLastError();
 }

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(256) k_panel_qr(double* __restrict__ K, long l
                                                   const int* __restrict__ ms_arr, int k0, int nbe,
                                                   double* __restrict__ tau_out, int n,
                                                   double* __restrict__ Vp, long long vstride,
-                                                  unsigned* status) {
+                                                  unsigned* status, int vrow0) {
   const int s = blockIdx.x;
   double* A = K + (size_t)s * kstride;
   const int m = ms_arr[s];
@@ -110,6 +110,9 @@ __global__ void __launch_bounds__(256) k_panel_qr(double* __restrict__ K, long l
       V[r + (size_t)j * ld] = v;
     }
   }
+  // rows [vrow0, k0) of these columns of V: zero, for a reflector block that starts above
+  for (int e = tid; e < (k0 - vrow0) * nbe; e += 256)
+    V[vrow0 + e % (k0 - vrow0) + (size_t)(e / (k0 - vrow0)) * ld] = 0.0;
   if (tid == 0 && bits) atomicOr(status, bits);
 }
 
@@ -561,7 +564,7 @@ template <int PCL, typename T>
 __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
     k_panel_qr_cl(double* __restrict__ K, long long kstride, int ld, const int* __restrict__ ms_arr,
                   int k0, int nbe, double* __restrict__ tau_out, int n, double* __restrict__ Vp,
-                  long long vstride, unsigned* status, int s_off) {
+                  long long vstride, unsigned* status, int s_off, int vrow0) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int q = (int)cluster.block_rank();
@@ -676,6 +679,9 @@ __global__ void __cluster_dims__(PCL, 1, 1) __launch_bounds__(256)
     }
   }
   if (q == 0) {
+    // rows [vrow0, k0) of these columns of V: zero, for a reflector block that starts above
+    for (int e = tid; e < (k0 - vrow0) * nbe; e += 256)
+      V[vrow0 + e % (k0 - vrow0) + (size_t)(e / (k0 - vrow0)) * ld] = 0.0;
     if (tid < nbe) tau_out[(size_t)s * n + k0 + tid] = (double)stau[tid];
     if (tid == 0 && bits) atomicOr(status, bits);
   }
@@ -719,11 +725,66 @@ __global__ void __launch_bounds__(128) k_form_t(const double* __restrict__ G, lo
   for (int e = t; e < 32 * 32; e += 128) Tp[e] = T[e & 31][e >> 5];
 }
 
+// Compact-WY factor of a block of w <= 128 columns spanning several panels, for the
+// trailing update of a two-level blocked QR: the same forward recurrence as k_form_t,
+// T(0:j, j) = -tau_j T(0:j, 0:j) g_j, over the block's Gram matrix.  One CTA of 256
+// threads per subdomain keeps T in shared memory; row j of the (symmetric) Gram matrix,
+// v_l^T v_j for l < j, is fetched from global memory one step ahead into a double buffer,
+// and each row i of T is shared by 256 / 128 = 2 threads (4 when w <= 64).
+constexpr int FTW_MAX = 128;
+constexpr int FTW_LD = FTW_MAX + 1;
+constexpr int FTW_SMEM = (FTW_MAX * FTW_LD + 3 * FTW_MAX) * (int)sizeof(double);
+
+__global__ void __launch_bounds__(256) k_form_t_wide(const double* __restrict__ G, long long gstride, int gld,
+                                                    const double* __restrict__ tau, int n, int k0, int w,
+                                                    double* __restrict__ Tw, long long twstride, int tld,
+                                                    double* __restrict__ Td, long long tdstride, int dcol) {
+  extern __shared__ double ftw_smem[];
+  double* Tm = ftw_smem;                 // [FTW_MAX][FTW_LD], row-major
+  double* gs = Tm + FTW_MAX * FTW_LD;    // [2][FTW_MAX]
+  double* ts = gs + 2 * FTW_MAX;         // [FTW_MAX]
+  const int s = blockIdx.x, t = threadIdx.x;
+  const int tpr = w <= 64 ? 4 : 2, i = t / tpr, qd = t % tpr;
+  const double* Gp = G + (size_t)s * gstride;
+  for (int e = t; e < FTW_MAX * FTW_LD; e += 256) Tm[e] = 0.0;
+  if (t < FTW_MAX) ts[t] = t < w ? tau[(size_t)s * n + k0 + t] : 0.0;
+  __syncthreads();
+  for (int j = 0; j < w; ++j) {
+    // row j + 1 of G is loaded while column j is computed, and stored into the buffer that
+    // row j - 1 occupied (last read in the previous step, before its barrier)
+    const bool ld_next = j + 1 < w && t < j + 1;
+    const double gn = ld_next ? Gp[(size_t)(j + 1) * gld + t] : 0.0;
+    const double* g = gs + (j & 1) * FTW_MAX;
+    double p = 0.0;
+    if (i < j)
+      for (int l = i + qd; l < j; l += tpr) p = fma(Tm[i * FTW_LD + l], g[l], p);
+    p += __shfl_xor_sync(0xffffffffu, p, 1);
+    if (tpr == 4) p += __shfl_xor_sync(0xffffffffu, p, 2);
+    if (qd == 0) {
+      if (i < j) Tm[i * FTW_LD + j] = -ts[j] * p;
+      else if (i == j) Tm[j * FTW_LD + j] = ts[j];
+    }
+    if (ld_next) gs[((j + 1) & 1) * FTW_MAX + t] = gn;
+    __syncthreads();
+  }
+  double* Tp = Tw + (size_t)s * twstride;
+  for (int e = t; e < w * w; e += 256) {
+    const int r = e % w, c = e / w;
+    Tp[(size_t)c * tld + r] = Tm[r * FTW_LD + c];
+  }
+  double* Dp = Td + (size_t)s * tdstride;
+  for (int e = t; e < 32 * 32; e += 256) {
+    const int r = e & 31, c = e >> 5;
+    Dp[e] = (dcol + r < FTW_MAX && dcol + c < FTW_MAX) ? Tm[(dcol + r) * FTW_LD + dcol + c] : 0.0;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms, int N, int k0,
                             int nbe, double* tau, int n, double* Vp, long long vstride, unsigned* status,
-                            cudaStream_t st, bool fp32, int pcl_pref) {
+                            cudaStream_t st, bool fp32, int pcl_pref, int vrow0) {
+  if (vrow0 < 0 || vrow0 > k0) return cudaErrorInvalidValue;
   // the cluster variant keeps 1/PCL of the rows (up to ld - k0) in shared memory: 4 CTAs
   // per subdomain, or 8 when a quarter of the rows does not fit.  (Splitting the launch
   // into a full wave of 4-CTA clusters and a remainder of 5-CTA clusters measured slower:
@@ -745,7 +806,7 @@ cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms,
   auto smem = [&](int pcl, size_t bytes) { return (size_t)((ld - k0 + pcl - 1) / pcl) * PLD * bytes; };
 #define ELM_PANEL(PCL_, T_)                                                                          \
   k_panel_qr_cl<PCL_, T_><<<dim3(PCL_, N), 256, smem(PCL_, sizeof(T_)), st>>>(K, kstride, ld, ms, k0, nbe, \
-                                                                          tau, n, Vp, vstride, status, 0)
+                                                                          tau, n, Vp, vstride, status, 0, vrow0)
   if (fp32) {
     if (smem(2, 4) <= kMax) ELM_PANEL(2, float);
     else if (smem(4, 4) <= kMax) ELM_PANEL(4, float);
@@ -758,7 +819,7 @@ cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms,
   } else if (smem(8, 8) <= kMax) {
     ELM_PANEL(8, double);
   } else {
-    k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, Vp, vstride, status);
+    k_panel_qr<<<N, 256, 0, st>>>(K, kstride, ld, ms, k0, nbe, tau, n, Vp, vstride, status, vrow0);
   }
 #undef ELM_PANEL
   count_launch();
@@ -768,6 +829,21 @@ cudaError_t launch_panel_qr(double* K, long long kstride, int ld, const int* ms,
 cudaError_t launch_form_t(const double* G, long long gstride, const double* tau, int n, int k0, int nbe,
                           int N, double* T, long long tstride, cudaStream_t st) {
   k_form_t<<<N, 128, 0, st>>>(G, gstride, tau, n, k0, nbe, T, tstride); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_form_t_wide(const double* G, long long gstride, int gld, const double* tau, int n,
+                               int k0, int w, int N, double* Tw, long long twstride, int tld,
+                               double* Td, long long tdstride, int dcol, cudaStream_t st) {
+  if (w <= 0 || w > FTW_MAX || tld < w || gld < w || dcol < 0 || dcol >= w) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_form_t_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, FTW_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_form_t_wide<<<N, 256, FTW_SMEM, st>>>(G, gstride, gld, tau, n, k0, w, Tw, twstride, tld, Td, tdstride, dcol);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve"
            "elm_ddm_solve_pcg", "elm_ddm_get_points", "elm_ddm_set_wait_limit",
            "elm_ddm_fp64_gemm", "elm_ddm_fp64_gemm_workspace", "elm_ddm_set_tuning", "elm_ddm_set_ridge")
 TUNE_PANEL_CTAS, TUNE_UPD_GRID = 0, 1
-GEMM_TILE32, GEMM_TILE64, GEMM_PERSISTENT, GEMM_FUSED_SPLIT = range(4)
+GEMM_TILE32, GEMM_TILE64, GEMM_PERSISTENT, GEMM_FUSED_SPLIT, GEMM_FUSED_SPLIT_B = range(5)
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
 PTS_INTERIOR, PTS_BOUNDARY, PTS_INTERFACE, PTS_NORMALS = range(4)
 

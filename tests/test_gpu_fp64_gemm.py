@@ -80,9 +80,10 @@ def _wide_rows(M, K, binades=44):
 @pytest.mark.parametrize("kernel,K", [(E.GEMM_TILE32, 300), (E.GEMM_TILE32, 2048),
                                       (E.GEMM_TILE64, 128), (E.GEMM_PERSISTENT, 96),
                                       (E.GEMM_FUSED_SPLIT, 700), (E.GEMM_TILE32, 9000),
-                                      (E.GEMM_FUSED_SPLIT, 9000)])
+                                      (E.GEMM_FUSED_SPLIT, 9000), (E.GEMM_FUSED_SPLIT_B, 700),
+                                      (E.GEMM_FUSED_SPLIT_B, 2400), (E.GEMM_FUSED_SPLIT_B, 9000)])
 def test_random_operands_within_the_bound(kernel, K):
-    M, N = 200, (32 if kernel == E.GEMM_FUSED_SPLIT else 70)
+    M, N = {E.GEMM_FUSED_SPLIT: (200, 32), E.GEMM_FUSED_SPLIT_B: (120, 350)}.get(kernel, (200, 70))
     A, B = RNG.standard_normal((M, K)), RNG.standard_normal((N, K))
     _check(kernel, A, B)
     # the bound is also tight enough to mean FP64 accuracy for well-scaled data
@@ -92,12 +93,15 @@ def test_random_operands_within_the_bound(kernel, K):
     assert np.abs(got.cpu().numpy() - ex).max() <= 1e-14 * np.abs(A).sum(1).max() * np.abs(B).max()
 
 
-@pytest.mark.parametrize("kernel", [E.GEMM_TILE32, E.GEMM_PERSISTENT, E.GEMM_FUSED_SPLIT])
+@pytest.mark.parametrize("kernel", [E.GEMM_TILE32, E.GEMM_PERSISTENT, E.GEMM_FUSED_SPLIT,
+                                    E.GEMM_FUSED_SPLIT_B])
 def test_rows_spanning_forty_binades(kernel):
     K = 128 if kernel == E.GEMM_PERSISTENT else 520
     N = 32 if kernel == E.GEMM_FUSED_SPLIT else 45
-    A, B = _wide_rows(150, K), _wide_rows(N, K)
-    _check(kernel, A, B, a_layout="col" if kernel != E.GEMM_FUSED_SPLIT else "row", b_layout="col")
+    M = 128 if kernel == E.GEMM_FUSED_SPLIT_B else 150
+    A, B = _wide_rows(M, K), _wide_rows(N, K)
+    _check(kernel, A, B, a_layout="col" if kernel != E.GEMM_FUSED_SPLIT else "row",
+           b_layout="row" if kernel == E.GEMM_FUSED_SPLIT_B else "col")
 
 
 def test_upper_triangular_factor_with_kappa_1e14():
@@ -140,6 +144,7 @@ def test_rejects_unsupported_shapes():
     lib = E.load()
     assert lib.elm_ddm_fp64_gemm_workspace(E.GEMM_PERSISTENT, 10, 10, 129) == 0
     assert lib.elm_ddm_fp64_gemm_workspace(E.GEMM_FUSED_SPLIT, 10, 33, 10) == 0
+    assert lib.elm_ddm_fp64_gemm_workspace(E.GEMM_FUSED_SPLIT_B, 129, 10, 10) == 0
     assert lib.elm_ddm_fp64_gemm_workspace(9, 10, 10, 10) == 0
     A = torch.zeros((4, 4), dtype=torch.float64, device=DEV)
     with pytest.raises(E.ElmDdmError):   # fused split needs beta = 0
