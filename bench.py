@@ -42,8 +42,9 @@ KERNEL_OF_CLASS = {
     "panel_qr": "k_panel_qr_cl (Householder panel of 32 columns, 4-CTA cluster per subdomain, FP64 pipe)",
     "potrf": "k_potrf_diag (64x64 diagonal Cholesky, one CTA, FP64 pipe)",
     "trsm_rows": "k_trsm_chol_rows (Cholesky panel solve by substitution in 4-column blocks, 16 rows per CTA, FP64 pipe)",
-    "oz_qr_update": "k_ozaki_upd (persistent tensor-core FP64 product: A2 -= V W2 of every QR panel)",
-    "oz_qr_w": "k_ozaki_fa (tensor-core FP64 product with fused digit split: W1^T = A2^T V of every QR panel)",
+    "oz_qr_update": "k_ozaki_upd (persistent tensor-core FP64 product: A2 -= V_o W2, one K = 128 update per outer QR block)",
+    "oz_qr_w": "k_ozaki_fb (tensor-core FP64 product, B split in the kernel: W1 = V_o^T [V_o | A2] per outer QR block)",
+    "oz_qr_w_in": "k_ozaki_fa (tensor-core FP64 product, A split in the kernel: W1 of the inner panel steps)",
     "oz_syrk": "k_ozaki_upd (persistent tensor-core FP64 product: Schur Cholesky SYRK)",
     "split_qr_w": "k_rowexp + k_split (digit split of A2^T and V^T)",
     "assemble": "k_exp_tables + k_assemble (K^s, J and A^s from theta: factored activation)",
@@ -64,11 +65,27 @@ TRAFFIC_PER_ALGO_BYTE = {
     # first QR panel: 9.880 MB read + 0 B written (the panel stays in L2) for
     # 16 x 2400 x 32 x 8 B read and written once
     "panel_qr": (9.880320e6, 19.6608e6, "profiles/k_panel_qr_cl_poisson_4x4_n1000.md"),
-    # first QR update A2 -= V W2: C read + written, V and W2 once
-    "oz_qr_update": (745.953536e6, 855.90e6, "profiles/k_ozaki_upd_poisson_4x4_n1000.md"),
-    # first W1^T = A2^T V: A2, V, W1 once
-    "oz_qr_w": (410.991872e6, 435.69e6, "profiles/k_ozaki_fa_poisson_4x4_n1000.md"),
+    # first outer-block trailing update A2 -= V_o W2 (K = 128): C read + written, V_o and
+    # W2 once
+    "oz_qr_update": (768.653312e6, 778.600448e6, "profiles/k_ozaki_upd_poisson_4x4_n1000.md"),
+    # first outer-block W1 = V_o^T [V_o | A2]: V_o^T, [V_o | A2] and W1 once
+    "oz_qr_w": (503.213312e6, 459.980800e6, "profiles/k_ozaki_fb_poisson_4x4_n1000.md"),
 }
+
+# Digit pairs a tensor-core FP64 product forms (the p + q <= 8 pairs of the 7 BF16 digit
+# planes of each operand): the BF16 work per FP64-equivalent multiply-add.
+DIGIT_PAIRS = 28
+
+
+def measured_bf16_peak(sustained=True):
+    """Dense BF16 tensor throughput measured on this machine, TFLOP/s (the sustained figure for
+    kernels timed inside a long step), else the recipe fallback."""
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), f"MEASURED_PEAKS.json {key} (of measured)"
+    except (OSError, KeyError, ValueError):
+        return (1700.0 if sustained else 1900.0), "recipe fallback (of fallback)"
 
 
 def measured_hbm_peak():
@@ -297,7 +314,19 @@ def run_ours(args):
     s.profile(False)
     classes = {k: v for k, v in prof1.items() if not k.startswith("_")}
 
+    bf16_peak, bf16_src = measured_bf16_peak(sustained=True)
+
     def roof(k, v, ms):
+        if k.startswith("oz_") and v["flops"] > 0:
+            # tensor-core FP64 product: the 2MNK of the FP64 product times the digit pairs
+            # formed is the BF16 work the tensor cores must do for it
+            # (the low-precision local factorisation forms the 10 leading pairs)
+            pairs = 10 if mixed and k not in ("oz_syrk", "oz_syrk_b", "oz_schur") else DIGIT_PAIRS
+            ach = v["flops"] * pairs / (ms * 1e-3) / 1e12
+            return {"bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
+                    "frac": ach / bf16_peak, "digit_pairs": pairs,
+                    "fp64_equiv_tflops": v["flops"] / (ms * 1e-3) / 1e12,
+                    "hbm_frac": v["bytes"] / (ms * 1e-3) / 1e9 / hbm_peak}
         if k.startswith("oz_") or k.startswith("split") or k == "assemble":
             ach = v["bytes"] / (ms * 1e-3) / 1e9
             return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
@@ -385,8 +414,8 @@ def run_ours(args):
             "avg_launch_us": 1e3 * v["ms"] / max(v["launches"], 1),
             "per_launch": {"flops": v["flops"] / max(v["launches"], 1),
                            "bytes": v["bytes"] / max(v["launches"], 1)},
-            "peak_source": (hbm_src if roofline["bound"] == "hbm" else
-                            "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz (recipe units/clock)")})
+            "peak_source": (hbm_src if roofline["bound"] == "hbm" else bf16_src if roofline["bound"] == "tensor"
+                            else "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz (recipe units/clock)")})
     step_ms_breakdown = {k: round(v["ms"], 3) for k, v in sorted(classes.items())}
 
     # ---- CPU oracle: parity of this result and the timed baseline

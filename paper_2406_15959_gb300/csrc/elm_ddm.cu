@@ -995,13 +995,14 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
         sp3.push_back({w2, QR_NB, 1, n2i, nbe, x4, t4, 32});  // W2^T: rows = columns of A2
         o3.push_back({t3, x3, t4, x4, A2, 1, ld, mp, n2i, nbe, 0});
       }
-      add_split_rec(h->qr_recs, sp1, "split_qr_w");
-      add_fa_rec(h->qr_recs, o1, "oz_qr_w");
+      FT.name = "form_t_in";
+      add_split_rec(h->qr_recs, sp1, "split_qr_in");
+      add_fa_rec(h->qr_recs, o1, "oz_qr_w_in");
       h->qr_recs.push_back(FT);
-      add_split_rec(h->qr_recs, spt, "split_qr_t");
-      add_oz_rec(h->qr_recs, ot, 0, 1.0, 0.0, 0, "oz_qr_t");
-      add_split_rec(h->qr_recs, sp3, "split_qr_update");
-      add_oz_rec(h->qr_recs, o3, 0, -1.0, 1.0, 0, "oz_qr_update");
+      add_split_rec(h->qr_recs, spt, "split_qr_in");
+      add_oz_rec(h->qr_recs, ot, 0, 1.0, 0.0, 0, "oz_qr_t_in");
+      add_split_rec(h->qr_recs, sp3, "split_qr_in");
+      add_oz_rec(h->qr_recs, o3, 0, -1.0, 1.0, 0, "oz_qr_update_in");
       continue;
     }
     // Outer step, after the block's last panel: W1 = V_o^T [V_o | A2] over the trailing

@@ -116,3 +116,15 @@ extern "C" int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, 
   if (bits) return ELM_DDM_ERR_CUDA;
   return ELM_DDM_OK;
 }
+
+extern "C" int elm_ddm_selftest(int which, const double* x, double* y, int n, void* stream) {
+  if (which != ELM_DDM_SELFTEST_PIVOT_RCP || !x || !y || n < 0) return ELM_DDM_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_rcp_newton(x, y, n, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ELM_DDM_ERR_CUDA;
+  }
+  return ELM_DDM_OK;
+}

@@ -30,6 +30,7 @@ constexpr int NB = CHOL_NB;
 // by one warp in registers measured slower: the whole chain then runs on one
 // sub-partition's quarter of the FP64 pipe.)
 constexpr int POTRF_THREADS = 512;
+
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict__ S, int ld, int k, int nb,
                                                               unsigned* status) {
   __shared__ double a[NB][NB + 1];
@@ -49,12 +50,14 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict
     double rd = 0.0;
     if (lane == 0) {
       double d = a[c][c];
-      if (!(d > 0.0) || !isfinite(d)) {
+      // positive and finite: the sign bit clear, not zero, the exponent below 2047
+      const long long db = __double_as_longlong(d);
+      if (db <= 0 || (db >> 52) >= 0x7FF) {
         bad = 1;
         d = 1.0;
       }
       piv[c] = d;
-      rd = 1.0 / d;
+      rd = rcp_newton(d);
     }
     rd = __shfl_sync(0xffffffffu, rd, 0);
     for (int i = c + 1 + lane; i < nb; i += 32) tcol[c & 1][i] = a[i][c] * rd;
@@ -504,6 +507,12 @@ __global__ void __launch_bounds__(256) k_chol_bwd_all(const double* __restrict__
   }
 }
 
+// y = rcp_newton(x) element by element (the self-test of the pivot reciprocal).
+__global__ void k_rcp_newton(const double* __restrict__ x, double* __restrict__ y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = rcp_newton(x[i]);
+}
+
 }  // namespace
 
 cudaError_t launch_potrf_diag(double* S, int ld, int k, int nb, unsigned* status, cudaStream_t st) {
@@ -521,6 +530,12 @@ cudaError_t launch_tri_inv(const double* S, int ld, int n, double* inv, cudaStre
     attr = true;
   }
   k_tri_inv<<<(n + NB - 1) / NB, NB, smem, st>>>(S, ld, n, inv); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rcp_newton(const double* x, double* y, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_rcp_newton<<<(n + 255) / 256, 256, 0, st>>>(x, y, n); count_launch();
   return cudaGetLastError();
 }
 

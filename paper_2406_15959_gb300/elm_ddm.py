@@ -28,7 +28,9 @@ SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve"
            "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order",
            "elm_ddm_profile_only", "elm_ddm_solve_cg", "elm_ddm_set_coefficient",
            "elm_ddm_solve_pcg", "elm_ddm_get_points", "elm_ddm_set_wait_limit",
-           "elm_ddm_fp64_gemm", "elm_ddm_fp64_gemm_workspace", "elm_ddm_set_tuning", "elm_ddm_set_ridge")
+           "elm_ddm_fp64_gemm", "elm_ddm_fp64_gemm_workspace", "elm_ddm_set_tuning", "elm_ddm_set_ridge",
+           "elm_ddm_selftest")
+SELFTEST_PIVOT_RCP = 0
 TUNE_PANEL_CTAS, TUNE_UPD_GRID = 0, 1
 GEMM_TILE32, GEMM_TILE64, GEMM_PERSISTENT, GEMM_FUSED_SPLIT, GEMM_FUSED_SPLIT_B = range(5)
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
@@ -97,6 +99,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_fp64_gemm_workspace.restype = ctypes.c_size_t
     lib.elm_ddm_fp64_gemm.argtypes = [I, I, I, I, ctypes.c_double, P, LL, LL, P, LL, LL, ctypes.c_double,
                                       P, LL, LL, P, ctypes.c_size_t, P]
+    lib.elm_ddm_selftest.argtypes = [I, P, P, I, P]
     lib.elm_ddm_destroy.argtypes = [P]
     lib.elm_ddm_last_error.argtypes = [P]
     lib.elm_ddm_last_error.restype = ctypes.c_char_p
@@ -378,6 +381,20 @@ def fp64_gemm(A, B, C, alpha: float = 1.0, beta: float = 0.0, kernel: int = GEMM
     if rc != OK:
         raise ElmDdmError(rc, "elm_ddm_fp64_gemm")
     return C
+
+
+def selftest(which: int, x, stream=None):
+    """y = f(x) elementwise for the device routine `which` (elm_ddm_selftest); x a CUDA
+    float64 tensor.  Returns y."""
+    import torch
+    lib = load()
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    st = (stream or torch.cuda.current_stream(x.device)).cuda_stream
+    rc = lib.elm_ddm_selftest(which, x.data_ptr(), y.data_ptr(), x.numel(), st)
+    if rc != OK:
+        raise ElmDdmError(rc, "elm_ddm_selftest")
+    return y
 
 
 def run_workload(w, device="cuda", max_rhs=1):

@@ -149,3 +149,19 @@ def test_rejects_unsupported_shapes():
     A = torch.zeros((4, 4), dtype=torch.float64, device=DEV)
     with pytest.raises(E.ElmDdmError):   # fused split needs beta = 0
         E.fp64_gemm(A, A, A.clone(), 1.0, 1.0, E.GEMM_FUSED_SPLIT)
+
+
+def test_cholesky_pivot_reciprocal_within_two_ulp():
+    """The Schur Cholesky's pivots use a Newton reciprocal from an FP32 seed instead of a
+    division: within two units in the last place of the correctly rounded 1/x over the
+    normal range (and the division itself at the ends of it)."""
+    x = np.concatenate([RNG.uniform(1.0, 2.0, 4000),
+                        2.0 ** RNG.uniform(-1020, 1020, 4000),
+                        np.nextafter(2.0 ** np.arange(-1022, 1023, 7), 0.0),
+                        [1.0, 2.0, 3.0, 1.5, np.nextafter(1.0, 2.0), np.nextafter(2.0, 1.0),
+                         2.0 ** -1021, 2.0 ** -1022, 2.0 ** 1023]])
+    y = E.selftest(E.SELFTEST_PIVOT_RCP, torch.as_tensor(x, device=DEV)).cpu().numpy()
+    ref = 1.0 / x.astype(np.longdouble)
+    ulp = np.spacing(np.abs(ref.astype(np.float64)))
+    err = np.abs((y.astype(np.longdouble) - ref)).astype(np.float64) / ulp
+    assert err.max() <= 2.0, (float(err.max()), x[np.argmax(err)])
