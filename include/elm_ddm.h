@@ -113,6 +113,12 @@ extern "C" {
                                      solution interpolates with huge weights, and this option
                                      reaches the paper's accuracy */
 
+#define ELM_DDM_FLAG_BLOCK_JACOBI 64  /* elm_ddm_schur also inverts S's diagonal block of every
+                                     interface edge (every edge at most 128 unknowns), the
+                                     block-Jacobi preconditioner that elm_ddm_solve_pcg takes with
+                                     jacobi = 2.  Not with ELM_DDM_FLAG_SCHUR_CG or
+                                     ELM_DDM_FLAG_MIXED */
+
 /* Differential operators. */
 #define ELM_DDM_OP_POISSON 0  /* L = -Laplacian (Eq. (4.4)) */
 #define ELM_DDM_OP_VARCOEF 1  /* L = -div(rho grad) (Section 4, the variable-coefficient
@@ -218,7 +224,9 @@ int elm_ddm_solve_cg(elm_ddm_handle* h, const double* rhs, int nrhs, double tol,
  * learned-interface extension):
  *   x0      device double [nrhs][n_gamma] initial u_Gamma in the caller's order, or NULL (zero)
  *   jacobi  1: preconditioner diag(S)^{-1} (needs the assembled S, i.e. not
- *           ELM_DDM_FLAG_SCHUR_CG; ERR_STATE otherwise), 0: none
+ *           ELM_DDM_FLAG_SCHUR_CG; ERR_STATE otherwise); 2: block-Jacobi, the inverse of
+ *           S's diagonal block of every interface edge (needs ELM_DDM_FLAG_BLOCK_JACOBI;
+ *           ERR_STATE otherwise); 0: none.  Other values: ERR_ARG
  * The stopping rule is on the true residual of the recurrence, |r| <= tol |rhs|, checked
  * also at the start (a guess that already meets it takes 0 steps).
  */

@@ -244,6 +244,19 @@ cudaError_t launch_pcg_init(const double* b, const double* q, double* r, double*
                             CgState* state, int ng, int nrhs, int has_x0, double tol2, cudaStream_t st);
 cudaError_t launch_pcg_update(double* x, double* r, double* p, const double* q, const double* dinv,
                               CgState* state, int ng, int nrhs, double tol2, cudaStream_t st);
+// Block-Jacobi preconditioner of the CG solves: the inverse of each interface edge's
+// diagonal block of S (edge e: internal unknowns off[e] .. off[e] + len[e] - 1, len <= 128,
+// inverse row-major at inv + ioff[e]), and its application z = B^{-1} r.
+cudaError_t launch_block_inv(const double* S, int ng, const int* off, const int* len, const long long* ioff,
+                             int nedges, int maxlen, double* inv, unsigned* status, cudaStream_t st);
+cudaError_t launch_bj_apply(const double* inv, const int* off, const int* len, const long long* ioff, int nedges,
+                            const double* r, double* z, int ng, int nrhs, cudaStream_t st);
+// A CG step split around a preconditioner launched in between: step_a (alpha, x, r, r^T r),
+// then z = M^{-1} r, then step_b (r^T z, beta, p; first = 1 at the start: p = z).
+cudaError_t launch_pcg_step_a(double* x, double* r, const double* p, const double* q, CgState* state, int ng,
+                              int nrhs, cudaStream_t st);
+cudaError_t launch_pcg_step_b(const double* r, const double* z, double* p, CgState* state, int ng, int nrhs,
+                              double tol2, int first, cudaStream_t st);
 cudaError_t launch_scatter_perm(const int* idx, int n, const double* src, double* dst, int nrhs,
                                 cudaStream_t st);
 cudaError_t launch_diag_inv(const double* S, int n, double* dinv, cudaStream_t st);

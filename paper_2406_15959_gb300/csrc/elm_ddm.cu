@@ -208,6 +208,12 @@ struct elm_ddm_handle {
   double *cg_p = nullptr, *cg_q = nullptr;  // CG search direction and S p, [max_rhs][ng]
   CgState* cg_st = nullptr;                 // [max_rhs]
   double* sdinv = nullptr;                  // 1 / diag(S), internal order (Jacobi), set by schur
+  // ELM_DDM_FLAG_BLOCK_JACOBI: inverses of S's diagonal block of every edge (set by schur)
+  bool bj = false, has_bj = false;
+  int bj_maxlen = 0;
+  int *bj_off = nullptr, *bj_len = nullptr;
+  long long* bj_ioff = nullptr;
+  double *bj_inv = nullptr, *cg_z = nullptr;
   bool has_sdinv = false;
   void* sp_buf = nullptr;        // digit tiles and row exponents of the split operands
   std::vector<int> qr_first;     // first record of each panel in qr_recs
@@ -429,8 +435,12 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   if (max_rhs < 1 || max_rhs > 64) return fail(nullptr, ELM_DDM_ERR_ARG, "max_rhs must be in 1..64");
   if (n > TRSV_MAX_N) return fail(nullptr, ELM_DDM_ERR_ARG, "n_neurons > 8192 is not supported");
   if (desc->flags & ~(ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG | ELM_DDM_FLAG_DIRECT_ASSEMBLY |
-                      ELM_DDM_FLAG_MIXED | ELM_DDM_FLAG_NEURONS_PER_SUB | ELM_DDM_FLAG_RIDGE))
+                      ELM_DDM_FLAG_MIXED | ELM_DDM_FLAG_NEURONS_PER_SUB | ELM_DDM_FLAG_RIDGE |
+                      ELM_DDM_FLAG_BLOCK_JACOBI))
     return fail(nullptr, ELM_DDM_ERR_ARG, "unknown flags");
+  if ((desc->flags & ELM_DDM_FLAG_BLOCK_JACOBI) && (desc->flags & (ELM_DDM_FLAG_SCHUR_CG | ELM_DDM_FLAG_MIXED)))
+    return fail(nullptr, ELM_DDM_ERR_ARG,
+                "ELM_DDM_FLAG_BLOCK_JACOBI needs the assembled S of the FP64 factorisation");
   if ((desc->flags & ELM_DDM_FLAG_MIXED) && (desc->flags & (ELM_DDM_FLAG_FP64_SIMT | ELM_DDM_FLAG_SCHUR_CG)))
     return fail(nullptr, ELM_DDM_ERR_ARG,
                 "ELM_DDM_FLAG_MIXED needs the tensor-core back end and the direct Schur solve");
@@ -444,6 +454,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->cg_only = (desc->flags & ELM_DDM_FLAG_SCHUR_CG) != 0;
   h->mixed = (desc->flags & ELM_DDM_FLAG_MIXED) != 0;
   h->ridge = (desc->flags & ELM_DDM_FLAG_RIDGE) != 0;
+  h->bj = (desc->flags & ELM_DDM_FLAG_BLOCK_JACOBI) != 0;
   h->op = desc->op;
   const int cst = (desc->flags & ELM_DDM_FLAG_NEURONS_PER_SUB) ? 4 : 3;  // counts row stride
   h->cnt_h.resize(3 * (size_t)N);
@@ -568,6 +579,13 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     h->newoff.assign(ne, 0);
     int off = 0;
     for (int pos = 0; pos < ne; ++pos) { h->newoff[order[pos]] = off; off += h->edges[order[pos]].len; }
+    if (h->bj) {
+      for (const Edge& ed : h->edges) h->bj_maxlen = std::max(h->bj_maxlen, ed.len);
+      if (h->bj_maxlen > 128) {
+        delete h;
+        return fail(nullptr, ELM_DDM_ERR_ARG, "ELM_DDM_FLAG_BLOCK_JACOBI: an interface edge has more than 128 unknowns");
+      }
+    }
     h->perm_h.assign(ng, 0);
     for (int e = 0; e < ne; ++e)
       for (int k = 0; k < h->edges[e].len; ++k) h->perm_h[h->edges[e].g0 + k] = h->newoff[e] + k;
@@ -707,6 +725,20 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             ((cst == 3 && !h->ridge) || dev_alloc(h, &h->nsub, (size_t)N)) &&
             dev_alloc(h, &h->colexp, h->emulated ? (size_t)N * h->ncap : (size_t)1) &&
             dev_alloc(h, &h->status, 1);
+  std::vector<int> bj_len_h;
+  std::vector<long long> bj_ioff_h;
+  if (ok && h->bj) {
+    long long tot = 0;
+    for (const Edge& ed : h->edges) {
+      bj_len_h.push_back(ed.len);
+      bj_ioff_h.push_back(tot);
+      tot += (long long)ed.len * ed.len;
+    }
+    const size_t ne = h->edges.size();
+    ok = dev_alloc(h, &h->bj_off, std::max<size_t>(ne, 1)) && dev_alloc(h, &h->bj_len, std::max<size_t>(ne, 1)) &&
+         dev_alloc(h, &h->bj_ioff, std::max<size_t>(ne, 1)) && dev_alloc(h, &h->bj_inv, (size_t)std::max(tot, 1ll)) &&
+         dev_alloc(h, &h->cg_z, (size_t)max_rhs * std::max(ng, 1));
+  }
   if (ok && h->mixed) {
     const size_t R = (size_t)max_rhs, ngs = (size_t)std::max(ng, 1);
     const size_t xn = R * N * h->ld, cn = R * N * n, gn = R * N * h->mgld;
@@ -1292,6 +1324,11 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   cp(h->perm, h->perm_h.data(), h->perm_h.size() * sizeof(int));
   cp(h->d_rend, h->chol_rend.data(), h->chol_rend.size() * sizeof(int));
   cp(h->d_jbeg, h->chol_jbeg.data(), h->chol_jbeg.size() * sizeof(int));
+  if (h->bj && !h->edges.empty()) {
+    cp(h->bj_off, h->newoff.data(), h->newoff.size() * sizeof(int));
+    cp(h->bj_len, bj_len_h.data(), bj_len_h.size() * sizeof(int));
+    cp(h->bj_ioff, bj_ioff_h.data(), bj_ioff_h.size() * sizeof(long long));
+  }
   {
     int rows = 0, cols = 0;
     for (size_t st = 0; st < h->chol_rend.size(); ++st) {
@@ -1385,6 +1422,11 @@ int elm_ddm_schur(elm_ddm_handle* h) {
     // Jacobi preconditioner of the CG solves, taken before the factorisation overwrites S
     ELM_LAUNCH(h, launch_diag_inv(h->S, h->ng, h->sdinv, h->st), "diag_inv");
     h->has_sdinv = true;
+    if (h->bj) {
+      ELM_LAUNCH(h, launch_block_inv(h->S, h->ng, h->bj_off, h->bj_len, h->bj_ioff, (int)h->edges.size(),
+                                     h->bj_maxlen, h->bj_inv, h->status, h->st), "block_inv");
+      h->has_bj = true;
+    }
     // Look-ahead (tensor-core back end): part B of step k's SYRK (columns beyond the next
     // block column) runs on st2 while st factors and solves that column.  st2 starts B
     // after st's panel solve of step k, which writes the split operands (evS); st waits
@@ -1646,8 +1688,11 @@ static int solve_cg_impl(elm_ddm_handle* h, const double* rhs, int nrhs, const d
   if (nrhs < 1 || nrhs > h->max_rhs) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: nrhs out of range");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: tol must be > 0");
   if (maxit < 1) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: maxit must be >= 1");
-  if (jacobi && !h->has_sdinv)
+  if (jacobi < 0 || jacobi > 2) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: preconditioner must be 0, 1 or 2");
+  if (jacobi == 1 && !h->has_sdinv)
     return fail(h, ELM_DDM_ERR_STATE, "solve_cg: Jacobi needs the assembled S (not ELM_DDM_FLAG_SCHUR_CG)");
+  if (jacobi == 2 && !h->has_bj)
+    return fail(h, ELM_DDM_ERR_STATE, "solve_cg: block-Jacobi needs ELM_DDM_FLAG_BLOCK_JACOBI and elm_ddm_schur");
   const int N = h->N, n = h->n, ng = h->ng;
   ELM_LAUNCH(h, launch_load_rhs(h->X, rhs, N, h->m_max, h->ld, h->cnt, nrhs, h->status, h->st),
              "load_rhs");
@@ -1666,7 +1711,9 @@ static int solve_cg_impl(elm_ddm_handle* h, const double* rhs, int nrhs, const d
     ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
     // CG: x in uv, r in yv; gq / hq / hv are free now and serve as the operator's scratch
     const double tol2 = tol * tol;
-    const double* dinv = jacobi ? h->sdinv : nullptr;
+    const double* dinv = jacobi == 1 ? h->sdinv : nullptr;
+    const bool block = jacobi == 2;
+    const int nedges = (int)h->edges.size();
     if (x0) {  // start from the caller's guess: x = x0 (internal order), q = S x
       ELM_LAUNCH(h, launch_scatter_perm(h->perm, ng, x0, h->uv, nrhs, h->st), "cg_x0");
       ELM_LAUNCH(h, launch_schur_apply(h->D, h->M, h->mstride, h->mgld, h->mg, h->mgmax, h->ifc_dof,
@@ -1678,6 +1725,11 @@ static int solve_cg_impl(elm_ddm_handle* h, const double* rhs, int nrhs, const d
     }
     ELM_LAUNCH(h, launch_pcg_init(h->rv, h->cg_q, h->yv, h->cg_p, dinv, h->cg_st, ng, nrhs, x0 ? 1 : 0,
                                   tol2, h->st), "cg_init");
+    if (block) {  // z = B^{-1} r, p = z, rz = r^T z
+      ELM_LAUNCH(h, launch_bj_apply(h->bj_inv, h->bj_off, h->bj_len, h->bj_ioff, nedges, h->yv, h->cg_z, ng,
+                                    nrhs, h->st), "cg_prec");
+      ELM_LAUNCH(h, launch_pcg_step_b(h->yv, h->cg_z, h->cg_p, h->cg_st, ng, nrhs, tol2, 1, h->st), "cg_update");
+    }
     std::vector<CgState> hs(nrhs);
     {
       cudaError_t e = cudaMemcpyAsync(hs.data(), h->cg_st, nrhs * sizeof(CgState), cudaMemcpyDeviceToHost,
@@ -1693,8 +1745,17 @@ static int solve_cg_impl(elm_ddm_handle* h, const double* rhs, int nrhs, const d
         ELM_LAUNCH(h, launch_schur_apply(h->D, h->M, h->mstride, h->mgld, h->mg, h->mgmax, h->ifc_dof,
                                          h->dofmap, h->cg_p, h->cg_q, h->gq, h->hq, h->hv, ng, N, nrhs,
                                          h->st), "cg_apply");
-        ELM_LAUNCH(h, launch_pcg_update(h->uv, h->yv, h->cg_p, h->cg_q, dinv, h->cg_st, ng, nrhs, tol2,
-                                        h->st), "cg_update");
+        if (block) {
+          ELM_LAUNCH(h, launch_pcg_step_a(h->uv, h->yv, h->cg_p, h->cg_q, h->cg_st, ng, nrhs, h->st),
+                     "cg_update");
+          ELM_LAUNCH(h, launch_bj_apply(h->bj_inv, h->bj_off, h->bj_len, h->bj_ioff, nedges, h->yv, h->cg_z, ng,
+                                        nrhs, h->st), "cg_prec");
+          ELM_LAUNCH(h, launch_pcg_step_b(h->yv, h->cg_z, h->cg_p, h->cg_st, ng, nrhs, tol2, 0, h->st),
+                     "cg_update");
+        } else {
+          ELM_LAUNCH(h, launch_pcg_update(h->uv, h->yv, h->cg_p, h->cg_q, dinv, h->cg_st, ng, nrhs, tol2,
+                                          h->st), "cg_update");
+        }
       }
       it += chunk;
       cudaError_t e = cudaMemcpyAsync(hs.data(), h->cg_st, nrhs * sizeof(CgState), cudaMemcpyDeviceToHost,

@@ -168,6 +168,126 @@ __global__ void k_diag_inv(const double* __restrict__ S, int n, double* __restri
   if (i < n) dinv[i] = 1.0 / S[i + (size_t)i * n];
 }
 
+// ---- block-Jacobi preconditioner: the inverse of S's diagonal block of every interface
+// edge (the unknowns of one edge are consecutive in the internal order) ----
+
+// Inverse of one edge's diagonal block (len <= BJ_MAX), from the lower triangle of S, by
+// Gauss-Jordan elimination in place without pivoting (S is SPD, so every pivot of its
+// principal blocks is positive): for every k, row k is divided by the pivot and column k
+// eliminated from every other row, the identity's column k built in its place.  One CTA
+// per edge, the block in shared memory.  A pivot that is not positive flags ST_NOT_SPD.
+constexpr int BJ_MAX = 128;
+__global__ void __launch_bounds__(256) k_block_inv(const double* __restrict__ S, int ng,
+                                                   const int* __restrict__ off, const int* __restrict__ len,
+                                                   const long long* __restrict__ ioff, double* __restrict__ inv,
+                                                   unsigned* status) {
+  extern __shared__ double bj_smem[];
+  const int e = blockIdx.x, t = threadIdx.x;
+  const int o = off[e], n = len[e], ld = n + 1;
+  double* a = bj_smem;  // [n][n + 1]
+  __shared__ double prow[BJ_MAX + 1], pcol[BJ_MAX + 1];
+  __shared__ int bad;
+  for (int q = t; q < n * n; q += 256) {
+    const int i = q / n, j = q % n;
+    const int r = max(i, j), c = min(i, j);
+    a[i * ld + j] = S[(o + r) + (size_t)(o + c) * ng];
+  }
+  if (t == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const double piv = a[k * ld + k];
+    if (t == 0 && !(piv > 0.0)) bad = 1;
+    const double rp = piv > 0.0 ? 1.0 / piv : 0.0;
+    // pivot row scaled (the identity's entry at k becomes 1 / piv) and column k saved
+    for (int j = t; j < n; j += 256) {
+      prow[j] = j == k ? rp : a[k * ld + j] * rp;
+      pcol[j] = a[j * ld + k];
+    }
+    __syncthreads();
+    for (int q = t; q < n * n; q += 256) {
+      const int i = q / n, j = q % n;
+      if (i == k) a[i * ld + j] = prow[j];
+      else a[i * ld + j] = (j == k ? 0.0 : a[i * ld + j]) - pcol[i] * prow[j];
+    }
+    __syncthreads();
+  }
+  double* out = inv + ioff[e];
+  for (int q = t; q < n * n; q += 256) out[q] = a[(q / n) * ld + q % n];
+  if (t == 0 && bad) atomicOr(status, ST_NOT_SPD);
+}
+
+// z = B^{-1} r on every edge's unknowns, B the block-diagonal part of S.  Block (edge,
+// right-hand side), one thread per row of the edge's inverse (row-major, contiguous).
+__global__ void __launch_bounds__(BJ_MAX) k_bj_apply(const double* __restrict__ inv, const int* __restrict__ off,
+                                                    const int* __restrict__ len,
+                                                    const long long* __restrict__ ioff,
+                                                    const double* __restrict__ r, double* __restrict__ z, int ng) {
+  __shared__ double rs[BJ_MAX];
+  const int e = blockIdx.x, rh = blockIdx.y, t = threadIdx.x;
+  const int o = off[e], n = len[e];
+  const double* rr = r + (size_t)rh * ng + o;
+  if (t < n) rs[t] = rr[t];
+  __syncthreads();
+  if (t < n) {
+    const double* row = inv + ioff[e] + (size_t)t * n;
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc = fma(row[j], rs[j], acc);
+    z[(size_t)rh * ng + o + t] = acc;
+  }
+}
+
+// First half of a CG step with a preconditioner applied by separate launches:
+// alpha = rz / p^T q, x += alpha p, r -= alpha q, rr = r^T r.
+__global__ void __launch_bounds__(1024) k_pcg_step_a(double* __restrict__ x, double* __restrict__ r,
+                                                     const double* __restrict__ p, const double* __restrict__ q,
+                                                     CgState* __restrict__ st, int ng) {
+  __shared__ double red[33];
+  const int rh = blockIdx.x, tid = threadIdx.x;
+  if (st[rh].done) return;
+  const size_t o = (size_t)rh * ng;
+  double pq = 0.0;
+  for (int g = tid; g < ng; g += blockDim.x) pq = fma(p[o + g], q[o + g], pq);
+  pq = block_sum(pq, red);
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    if (tid == 0) st[rh].done = 2;
+    return;
+  }
+  const double alpha = st[rh].rz / pq;
+  double rr = 0.0;
+  for (int g = tid; g < ng; g += blockDim.x) {
+    x[o + g] = fma(alpha, p[o + g], x[o + g]);
+    const double rg = fma(-alpha, q[o + g], r[o + g]);
+    r[o + g] = rg;
+    rr = fma(rg, rg, rr);
+  }
+  rr = block_sum(rr, red);
+  if (tid == 0) st[rh].rr = rr;
+}
+
+// Second half, with z = M^{-1} r already formed: beta = r^T z / rz, p = z + beta p (and at
+// the start, first = 1: p = z); the stopping rule and the breakdown flags as in
+// k_pcg_update.
+__global__ void __launch_bounds__(1024) k_pcg_step_b(const double* __restrict__ r, const double* __restrict__ z,
+                                                     double* __restrict__ p, CgState* __restrict__ st, int ng,
+                                                     double tol2, int first) {
+  __shared__ double red[33];
+  const int rh = blockIdx.x, tid = threadIdx.x;
+  if (st[rh].done) return;
+  const size_t o = (size_t)rh * ng;
+  double rz = 0.0;
+  for (int g = tid; g < ng; g += blockDim.x) rz = fma(r[o + g], z[o + g], rz);
+  rz = block_sum(rz, red);
+  const double beta = first ? 0.0 : rz / st[rh].rz;
+  for (int g = tid; g < ng; g += blockDim.x) p[o + g] = first ? z[o + g] : fma(beta, p[o + g], z[o + g]);
+  if (tid == 0) {
+    const double rr = st[rh].rr, bb = st[rh].bb;
+    st[rh].rz = rz;
+    if (!first) st[rh].iters += 1;
+    if (!isfinite(rr) || !isfinite(rz)) st[rh].done = 2;
+    else if (rr <= tol2 * bb) st[rh].done = 1;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_schur_apply(const double* D, const double* M, long long mstride, int mgld,
@@ -196,6 +316,41 @@ cudaError_t launch_pcg_init(const double* b, const double* q, double* r, double*
 cudaError_t launch_pcg_update(double* x, double* r, double* p, const double* q, const double* dinv,
                               CgState* state, int ng, int nrhs, double tol2, cudaStream_t st) {
   k_pcg_update<<<nrhs, 1024, 0, st>>>(x, r, p, q, dinv, state, ng, tol2); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_inv(const double* S, int ng, const int* off, const int* len, const long long* ioff,
+                             int nedges, int maxlen, double* inv, unsigned* status, cudaStream_t st) {
+  if (nedges <= 0) return cudaSuccess;
+  if (maxlen > BJ_MAX) return cudaErrorInvalidValue;
+  const int smem = maxlen * (maxlen + 1) * (int)sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_block_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         BJ_MAX * (BJ_MAX + 1) * (int)sizeof(double));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_block_inv<<<nedges, 256, smem, st>>>(S, ng, off, len, ioff, inv, status); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bj_apply(const double* inv, const int* off, const int* len, const long long* ioff, int nedges,
+                            const double* r, double* z, int ng, int nrhs, cudaStream_t st) {
+  if (nedges <= 0) return cudaSuccess;
+  k_bj_apply<<<dim3(nedges, nrhs), BJ_MAX, 0, st>>>(inv, off, len, ioff, r, z, ng); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_step_a(double* x, double* r, const double* p, const double* q, CgState* state, int ng,
+                              int nrhs, cudaStream_t st) {
+  k_pcg_step_a<<<nrhs, 1024, 0, st>>>(x, r, p, q, state, ng); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_step_b(const double* r, const double* z, double* p, CgState* state, int ng, int nrhs,
+                              double tol2, int first, cudaStream_t st) {
+  k_pcg_step_b<<<nrhs, 1024, 0, st>>>(r, z, p, state, ng, tol2, first); count_launch();
   return cudaGetLastError();
 }
 

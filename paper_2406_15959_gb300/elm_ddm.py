@@ -55,6 +55,7 @@ FLAG_DIRECT_ASSEMBLY = 4
 FLAG_MIXED = 8
 FLAG_NEURONS_PER_SUB = 16
 FLAG_RIDGE = 32
+FLAG_BLOCK_JACOBI = 64
 OP_POISSON, OP_VARCOEF = 0, 1
 
 
@@ -142,9 +143,11 @@ class Solver:
 
     def __init__(self, geom, n_neurons: int, max_rhs: int = 1, stream=None, fp64_simt: bool = False,
                  schur_cg: bool = False, op: int = OP_POISSON, direct_assembly: bool = False,
-                 mixed: bool = False, neurons=None, ridge: float | None = None):
+                 mixed: bool = False, neurons=None, ridge: float | None = None,
+                 block_jacobi: bool = False):
         """neurons: None (n_neurons in every subdomain) or int [N] per-subdomain counts <= n_neurons
-        (ELM_DDM_FLAG_NEURONS_PER_SUB).  ridge: None, or alpha of ELM_DDM_FLAG_RIDGE."""
+        (ELM_DDM_FLAG_NEURONS_PER_SUB).  ridge: None, or alpha of ELM_DDM_FLAG_RIDGE.
+        block_jacobi: ELM_DDM_FLAG_BLOCK_JACOBI (the per-edge block preconditioner of solve_cg)."""
         import torch
         self.lib = load()
         ga = geom if isinstance(geom, GeometryArrays) else GeometryArrays.from_geometry(geom)
@@ -155,7 +158,7 @@ class Solver:
         flags = ((FLAG_FP64_SIMT if fp64_simt else 0) | (FLAG_SCHUR_CG if schur_cg else 0) |
                  (FLAG_DIRECT_ASSEMBLY if direct_assembly else 0) | (FLAG_MIXED if mixed else 0) |
                  (FLAG_NEURONS_PER_SUB if neurons is not None else 0) |
-                 (FLAG_RIDGE if ridge is not None else 0))
+                 (FLAG_RIDGE if ridge is not None else 0) | (FLAG_BLOCK_JACOBI if block_jacobi else 0))
         desc = Desc(N, self.n, m_max, ga.n_gamma, op, max_rhs, flags)
         h = ctypes.c_void_p()
         self._keep = ga
@@ -225,9 +228,10 @@ class Solver:
         return u_gamma, c
 
     def solve_cg(self, rhs, tol: float = 1e-9, maxit: int = 10000, u_gamma=None, c=None,
-                 require_convergence: bool = True, x0=None, jacobi: bool = False):
+                 require_convergence: bool = True, x0=None, jacobi=False):
         """As solve(), with the interface system solved by CG to relative residual tol
-        (from x0 [nrhs, n_gamma] if given, Jacobi-preconditioned if asked).
+        (from x0 [nrhs, n_gamma] if given; jacobi: False / True (diagonal) / "block" (the
+        per-edge blocks, needs block_jacobi=True at construction)).
         Returns (u_gamma, c, iterations)."""
         import torch
         squeeze = rhs.dim() == 2
@@ -247,7 +251,8 @@ class Solver:
             rc = self.lib.elm_ddm_solve_cg(self.h, _ptr(r.contiguous()), nrhs, float(tol), int(maxit), ugp,
                                            _ptr(c), ctypes.byref(it))
         else:
-            rc = self.lib.elm_ddm_solve_pcg(self.h, _ptr(r.contiguous()), nrhs, x0p, int(bool(jacobi)),
+            prec = 2 if jacobi == "block" else int(bool(jacobi))
+            rc = self.lib.elm_ddm_solve_pcg(self.h, _ptr(r.contiguous()), nrhs, x0p, prec,
                                             float(tol), int(maxit), ugp, _ptr(c), ctypes.byref(it))
         if rc != ERR_NOCONV or require_convergence:
             self._check_rc(rc)

@@ -1,7 +1,8 @@
 """Learned interface warm start: an MLP maps the coefficients a of a source
 f = sum a_kl sin(k pi x) sin(l pi y) to the interface variable u_Gamma of Eq. (3.5), and
-its prediction starts the (Jacobi-preconditioned) CG interface solve; the direct solve
-of the same handle is the fallback and the reference for the error.
+its prediction starts the preconditioned CG interface solve (diagonal or per-edge
+block-Jacobi); the direct solve of the same handle is the fallback and the reference for
+the error, and its RHS-only time the bar the warm start is measured against.
 
 The training set is generated by the method itself: one factorisation, then batches of
 right-hand sides through the direct solve.  Network, loss and Adam run in the library's
@@ -81,25 +82,56 @@ class WarmStart:
         return torch.cat(out) * self.sd + self.mu
 
 
+PRECONDITIONERS = {"none": False, "jacobi": True, "block": "block"}
+
+
 def evaluate(solver, ws: WarmStart, basis: np.ndarray, A: np.ndarray, tol: float = 1e-9,
-             maxit: int = 100000, jacobi: bool = True):
-    """Per held-out sample: CG steps from zero and from the prediction (both with or both
-    without the Jacobi preconditioner), the prediction's relative error, and the warm
-    result's distance to the direct solve."""
+             maxit: int = 100000, jacobi=True, precs=None):
+    """Per held-out sample: the direct RHS-only solve (time, the reference), and for every
+    preconditioner in `precs` (names of PRECONDITIONERS; default: the one `jacobi` selects)
+    the CG steps and wall time from zero and from the prediction, and the warm result's
+    distance to the direct solve; plus the prediction's relative error.  Times are wall
+    clock around each call (the CG entry points poll their convergence from the host)."""
     import torch
+    if precs is None:
+        precs = ["block" if jacobi == "block" else ("jacobi" if jacobi else "none")]
     flat = basis.reshape(basis.shape[0], -1)
     pred = ws.predict(A)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, 1e3 * (time.perf_counter() - t0)
+
     rows = []
     for i in range(A.shape[0]):
         rhs = torch.as_tensor((A[i] @ flat).reshape(1, solver.N, solver.m_max), device="cuda")
-        ud, _ = solver.solve(rhs)
-        _, _, it0 = solver.solve_cg(rhs, tol=tol, maxit=maxit, jacobi=jacobi)
-        ug1, _, it1 = solver.solve_cg(rhs, tol=tol, maxit=maxit, jacobi=jacobi, x0=pred[i:i + 1])
+        (ud, _), t_direct = timed(lambda: solver.solve(rhs))
         nd = float(torch.linalg.norm(ud))
-        rows.append({"cold_steps": it0, "warm_steps": it1,
-                     "prediction_rel_err": float(torch.linalg.norm(pred[i] - ud[0])) / nd,
-                     "warm_rel_err_vs_direct": float(torch.linalg.norm(ug1 - ud)) / nd})
+        row = {"direct_ms": t_direct, "prediction_rel_err": float(torch.linalg.norm(pred[i] - ud[0])) / nd}
+        for name in precs:
+            pj = PRECONDITIONERS[name]
+            (_, _, it0), t0 = timed(lambda: solver.solve_cg(rhs, tol=tol, maxit=maxit, jacobi=pj))
+            (ug1, _, it1), t1 = timed(lambda: solver.solve_cg(rhs, tol=tol, maxit=maxit, jacobi=pj,
+                                                              x0=pred[i:i + 1]))
+            row[name] = {"cold_steps": it0, "cold_ms": t0, "warm_steps": it1, "warm_ms": t1,
+                         "warm_rel_err_vs_direct": float(torch.linalg.norm(ug1 - ud)) / nd}
+        if len(precs) == 1:  # flat keys for a single preconditioner
+            row.update(row[precs[0]])
+        rows.append(row)
     return rows
+
+
+def summarise(rows, precs):
+    out = {"direct_ms_mean": float(np.mean([r["direct_ms"] for r in rows])),
+           "prediction_rel_err_mean": float(np.mean([r["prediction_rel_err"] for r in rows]))}
+    for name in precs:
+        out[name] = {k: float(np.mean([r[name][k] for r in rows]))
+                     for k in ("cold_steps", "cold_ms", "warm_steps", "warm_ms")}
+        out[name]["warm_rel_err_vs_direct_max"] = float(np.max([r[name]["warm_rel_err_vs_direct"] for r in rows]))
+    return out
 
 
 def main(argv=None):
@@ -112,7 +144,7 @@ def main(argv=None):
     ap.add_argument("--test", type=int, default=16)
     args = ap.parse_args(argv)
     w = wl.WORKLOADS[args.workload]()
-    s = E.Solver(w.geom, w.n_neurons, max_rhs=64)
+    s = E.Solver(w.geom, w.n_neurons, max_rhs=64, block_jacobi=True)
     s.assemble(torch.as_tensor(w.W, device="cuda"), torch.as_tensor(w.b, device="cuda"))
     s.schur()
     basis = wl.fourier_basis_rows(w.geom, args.modes)
@@ -126,20 +158,13 @@ def main(argv=None):
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
     At = np.random.default_rng(99).standard_normal((args.test, args.modes * args.modes))
-    out = {}
-    for jac in (False, True):
-        rows = evaluate(s, ws, basis, At, jacobi=jac)
-        key = "jacobi" if jac else "plain"
-        out[key] = {"cold_steps_mean": float(np.mean([r["cold_steps"] for r in rows])),
-                    "warm_steps_mean": float(np.mean([r["warm_steps"] for r in rows])),
-                    "warm_rel_err_vs_direct_max": float(np.max([r["warm_rel_err_vs_direct"]
-                                                                for r in rows]))}
+    precs = list(PRECONDITIONERS)
+    rows = evaluate(s, ws, basis, At, precs=precs)
     print(json.dumps({
         "workload": args.workload, "n_gamma": w.geom.n_gamma, "samples": args.samples,
         "generate_s": t_gen, "train_s": t_fit, "epochs": args.epochs,
         "final_train_loss": losses[-1], "test_samples": args.test,
-        "prediction_rel_err_mean": float(np.mean([r["prediction_rel_err"] for r in rows])),
-        "cg": out,
+        **summarise(rows, precs),
     }))
 
 

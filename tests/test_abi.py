@@ -62,7 +62,9 @@ G = wl.make_geometry(3, 2, 4, 4, 3, 3)
     (dict(n_neurons=10_000), "8192"),
     (dict(n_neurons=40), "fewer rows than neurons"),
     (dict(n_gamma=G.n_gamma + 1), "not shared by exactly two"),
-    (dict(flags=64), "unknown flags"),
+    (dict(flags=128), "unknown flags"),
+    (dict(flags=E.FLAG_BLOCK_JACOBI | E.FLAG_SCHUR_CG), "assembled S"),
+    (dict(flags=E.FLAG_BLOCK_JACOBI | E.FLAG_MIXED), "assembled S"),
     (dict(flags=E.FLAG_MIXED | E.FLAG_FP64_SIMT), "tensor-core back end"),
     (dict(flags=E.FLAG_MIXED | E.FLAG_SCHUR_CG), "direct Schur solve"),
 ])

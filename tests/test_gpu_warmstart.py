@@ -86,11 +86,13 @@ def test_mlp_rejects_bad_arguments():
 
 def test_warm_start_saves_cg_steps():
     """4x4 subdomains (n_Gamma = 2400), sources with 4 x 4 sine modes: 2048 method-generated
-    solves train the network; on held-out sources the Jacobi-preconditioned CG started at
-    its prediction needs clearly fewer steps than from zero, and both end within the
-    tolerance's reach of the direct solution."""
+    solves train the network; on held-out sources the preconditioned CG (diagonal and
+    per-edge block-Jacobi) started at its prediction needs clearly fewer steps than from
+    zero, and ends within the tolerance's reach of the direct solution.  The direct
+    RHS-only solve of the same handle is timed beside it: it is the bar a warm-started
+    iterative solve has to beat, and the test records (does not assert) how far off it is."""
     w = wl.poisson_4x4_n1000()
-    s = E.Solver(w.geom, w.n_neurons, max_rhs=64)
+    s = E.Solver(w.geom, w.n_neurons, max_rhs=64, block_jacobi=True)
     s.assemble(torch.as_tensor(w.W, device="cuda"), torch.as_tensor(w.b, device="cuda"))
     s.schur()
     basis = wl.fourier_basis_rows(w.geom, 4)
@@ -99,14 +101,18 @@ def test_warm_start_saves_cg_steps():
     losses = ws.fit(A, U, epochs=60, batch=128, lr=2e-3)
     assert losses[-1] < 0.05 * losses[0]
     At = np.random.default_rng(42).standard_normal((4, 16))
-    rows = WS.evaluate(s, ws, basis, At, tol=1e-9)
-    cold = np.mean([r["cold_steps"] for r in rows])
-    warm = np.mean([r["warm_steps"] for r in rows])
-    # the step counts move with the rounding of D_s and M_s (S is determined by the data only
-    # to a few percent at this initialisation), so the bar is a 10% saving, not a ratio
-    # tuned to one build
-    assert warm < 0.9 * cold, (warm, cold)
+    precs = ["jacobi", "block"]
+    rows = WS.evaluate(s, ws, basis, At, tol=1e-9, precs=precs)
+    summ = WS.summarise(rows, precs)
+    print("warm start:", summ)
+    for name in precs:
+        cold, warm = summ[name]["cold_steps"], summ[name]["warm_steps"]
+        # the step counts move with the rounding of D_s and M_s (S is determined by the data
+        # only to a few percent at this initialisation), so the bar is a 10% saving, not a
+        # ratio tuned to one build
+        assert warm < 0.9 * cold, (name, warm, cold)
+        # CG error bound kappa_M * tol with kappa_M <= kappa(S) = 2.9e5 at this size
+        assert summ[name]["warm_rel_err_vs_direct_max"] < 1e-3, (name, summ[name])
+    assert summ["block"]["cold_steps"] <= summ["jacobi"]["cold_steps"], summ
     assert max(r["prediction_rel_err"] for r in rows) < 0.1
-    # CG error bound kappa_J * tol with kappa_J <= kappa(S) = 2.9e5 at this size
-    assert max(r["warm_rel_err_vs_direct"] for r in rows) < 1e-3
     s.check()
