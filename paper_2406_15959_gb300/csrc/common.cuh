@@ -13,6 +13,7 @@ inline void count_launch(int k = 1) { g_kernel_launches.fetch_add(k, std::memory
 
 constexpr int QR_NB = 32;     // panel width of the blocked Householder QR
 constexpr int CHOL_NB = 64;   // block size of the Schur-matrix Cholesky
+constexpr int OZ_HL_TILE = 128 * 32 * 2;  // int64 words of one split-K accumulator tile
 constexpr int TRSV_MAX_N = 8192;  // largest n_neurons the back-solve keeps in shared memory
 
 // Bits of the device status word.
@@ -74,6 +75,9 @@ struct OzDesc {
   const void* At2 = nullptr;
   const int* Ae2 = nullptr;
   int lead = 0;
+  // split-K A-split launches (one 128-row tile): [128][32][2] int64 accumulator of the
+  // exact digit sums, zero before the launch (the conversion clears it again)
+  long long* hl = nullptr;
 };
 
 // Per right-hand side state of the CG solve of the Schur system (k_cg.cu).
@@ -105,7 +109,7 @@ cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int 
 // C = A B^T with the FP64 A split inside the kernel (At = FP64 A, a_rs its row stride, K
 // contiguous; Ae its row exponents), B split as usual with row_tile 32, N <= 32, beta = 0.
 cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned* status,
-                            cudaStream_t st, int gmax = 8);
+                            cudaStream_t st, int gmax = 8, int ksplit = 1);
 // C = A B^T with A already split (M <= 128: one row tile) and the FP64 B operand split
 // inside the kernel: B row j at Bt + j * a_rs with exponent bound Be[j], or, for j < lead,
 // at At2 + j * a_rs with Ae2[j].  One CTA per 32 rows of B (max_tiles = the most tiles).

@@ -164,6 +164,7 @@ struct elm_ddm_handle {
   // two-level QR (tensor-core path): compact-WY T of each outer block of QR_NBO columns,
   // [N][QR_NBO][QR_NBO] column-major, and where each panel writes its explicit reflectors
   double* Tab = nullptr;
+  long long* hlbuf = nullptr;   // [N][OZ_HL_TILE] split-K accumulators of the inner W1 products
   std::vector<int> panel_vcol, panel_vrow0;  // per panel: column of Vp, first zeroed row
   double *W1 = nullptr, *W2 = nullptr, *D = nullptr, *M = nullptr, *S = nullptr;
   double *Mdiag = nullptr, *thW = nullptr, *thb = nullptr, *xy = nullptr, *nrm = nullptr;
@@ -351,12 +352,12 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
                                     L.flags, h->status, h->st, gmax), nm, L.flops, L.bytes);
     else if (L.kind == 7)
       ELM_LAUNCH(h, launch_form_t(h->W1, h->wstride, h->tau, h->n, L.off * QR_NB, L.nt, h->N,
-                                  h->T + (size_t)L.off * QR_NB * QR_NB, h->tstride, h->st), "form_t");
+                                  h->T + (size_t)L.off * QR_NB * QR_NB, h->tstride, h->st), nm);
     else if (L.kind == 8)
       ELM_LAUNCH(h, launch_form_t_wide(h->W1, h->wstride, QR_NBO, h->tau, h->n, L.toff, L.nt, h->N, h->Tab,
                                        (long long)QR_NBO * QR_NBO, QR_NBO,
                                        h->T + (size_t)L.off * QR_NB * QR_NB, h->tstride,
-                                       L.off * QR_NB - L.toff, h->st), "form_t");
+                                       L.off * QR_NB - L.toff, h->st), nm);
     else if (L.kind == 6)
       ELM_LAUNCH_F(h, launch_trsm_y_diag(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg,
                                          h->mgmax, h->N, h->n, L.off, h->st), nm, L.flops);
@@ -377,8 +378,8 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
       ELM_LAUNCH_FB(h, launch_ozaki_fb(h->od + L.off, L.count, L.max_tiles, h->status, h->st, gmax), nm,
                     L.flops, L.bytes);
     else
-      ELM_LAUNCH_FB(h, launch_ozaki_fa(h->od + L.off, L.count, L.max_tiles, h->status, h->st, gmax), nm,
-                    L.flops, L.bytes);
+      ELM_LAUNCH_FB(h, launch_ozaki_fa(h->od + L.off, L.count, L.max_tiles, h->status, h->st, gmax,
+                                       L.nt > 1 ? L.nt : 1), nm, L.flops, L.bytes);
   }
   return ELM_DDM_OK;
 }
@@ -696,6 +697,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->tau, (size_t)N * n) && dev_alloc(h, &h->T, (size_t)N * h->tstride) &&
             dev_alloc(h, &h->Vp, (size_t)N * h->vstride) &&
             dev_alloc(h, &h->Tab, (size_t)N * QR_NBO * QR_NBO) &&
+            dev_alloc(h, &h->hlbuf, h->emulated ? (size_t)N * OZ_HL_TILE : (size_t)1) &&
             dev_alloc(h, &h->W1, (size_t)N * h->wstride) &&
             dev_alloc(h, &h->W2, (size_t)N * h->wstride) &&
             dev_alloc(h, &h->D, (size_t)N * h->mstride) &&
@@ -909,9 +911,11 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
     recs.push_back(L);
   };
-  // C = A B^T with A = FP64 operand split inside the kernel (N <= 32, beta = 0)
-  auto add_fa_rec = [&](std::vector<LaunchRec>& recs, const std::vector<OzDesc>& batch, const char* name) {
-    LaunchRec L{5, (int)ods.size(), 0, 0, false, false, 1.0, 0.0, 0, 0.0, 0};
+  // C = A B^T with A = FP64 operand split inside the kernel (N <= 32, beta = 0); ksplit > 1:
+  // K split over that many CTAs per tile (one 128-row tile, the descriptors' hl set)
+  auto add_fa_rec = [&](std::vector<LaunchRec>& recs, const std::vector<OzDesc>& batch, const char* name,
+                        int ksplit = 1) {
+    LaunchRec L{5, (int)ods.size(), 0, 0, false, false, 1.0, 0.0, 0, 0.0, ksplit};
     L.name = name;
     for (const OzDesc& d : batch) {
       if (d.M <= 0 || d.N <= 0) continue;
@@ -937,6 +941,9 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
     recs.push_back(L);
   };
+  // the inner steps' W1 products are one 128-row tile per subdomain: split their K over
+  // the CTAs the GPU has beyond one per subdomain (at most 4)
+  const int inner_ksplit = h->emulated ? std::max(1, std::min(4, h->sms / std::max(N, 1))) : 1;
   for (int b = 0; b < h->nblk; ++b) {
     const int k0 = b * QR_NB, nbe = std::min(QR_NB, n - k0);
     double pf = 0.0, pb = 0.0;
@@ -1017,6 +1024,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
         ow.At2 = V;   // rows i < nbe at V + i * ld, rows i >= nbe at PA2 + i * ld = A2
         ow.Ae2 = x2;
         ow.lead = nbe;
+        if (inner_ksplit > 1) ow.hl = h->hlbuf + (size_t)s * OZ_HL_TILE;
         o1.push_back(ow);
         // W2^T = W1^T T: A = W1^T (row r = column r of A2, 32 contiguous values), B = T^T
         // (row i = column i of the column-major T)
@@ -1029,7 +1037,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       }
       FT.name = "form_t_in";
       add_split_rec(h->qr_recs, sp1, "split_qr_in");
-      add_fa_rec(h->qr_recs, o1, "oz_qr_w_in");
+      add_fa_rec(h->qr_recs, o1, "oz_qr_w_in", inner_ksplit);
       h->qr_recs.push_back(FT);
       add_split_rec(h->qr_recs, spt, "split_qr_in");
       add_oz_rec(h->qr_recs, ot, 0, 1.0, 0.0, 0, "oz_qr_t_in");
@@ -1324,6 +1332,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   cp(h->perm, h->perm_h.data(), h->perm_h.size() * sizeof(int));
   cp(h->d_rend, h->chol_rend.data(), h->chol_rend.size() * sizeof(int));
   cp(h->d_jbeg, h->chol_jbeg.data(), h->chol_jbeg.size() * sizeof(int));
+  if (e == cudaSuccess && h->emulated) e = cudaMemset(h->hlbuf, 0, (size_t)N * OZ_HL_TILE * sizeof(long long));
   if (h->bj && !h->edges.empty()) {
     cp(h->bj_off, h->newoff.data(), h->newoff.size() * sizeof(int));
     cp(h->bj_len, bj_len_h.data(), bj_len_h.size() * sizeof(int));

@@ -6,6 +6,7 @@
 #include "common.cuh"
 #include "digits.cuh"
 
+#include <algorithm>
 #include <vector>
 
 using namespace elmddm;
@@ -17,8 +18,8 @@ size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 // Workspace layout: status word | split descriptors | product descriptor | tile table |
 // row exponents of A and B | digit planes of A and B.
 struct Layout {
-  size_t status, sd, od, ut, ea, eb, ta, tb, total;
-  int brow, tiles;
+  size_t status, sd, od, ut, ea, eb, ta, tb, hl, total;
+  int brow, tiles, ksplit;
 };
 
 bool layout(int kernel, int M, int N, int K, Layout* L) {
@@ -33,6 +34,9 @@ bool layout(int kernel, int M, int N, int K, Layout* L) {
     default: return false;
   }
   L->brow = brow;
+  // the fused A-split product of a single 128-row tile splits K over up to 4 CTAs (exact
+  // int64 accumulation, the same bits as one CTA)
+  L->ksplit = (kernel == ELM_DDM_GEMM_FUSED_SPLIT && M <= 128) ? std::min(4, (K + 511) / 512) : 1;
   L->tiles = kernel == ELM_DDM_GEMM_PERSISTENT ? ((M + 127) / 128) * ((N + 31) / 32) : 0;
   size_t o = 0;
   L->status = o; o += 256;
@@ -43,6 +47,7 @@ bool layout(int kernel, int M, int N, int K, Layout* L) {
   L->eb = o; o += al256((size_t)N * 4);
   L->ta = o; o += kernel == ELM_DDM_GEMM_FUSED_SPLIT ? 0 : al256(oz_split_elems(M, K, 128) * 2);
   L->tb = o; o += kernel == ELM_DDM_GEMM_FUSED_SPLIT_B ? 0 : al256(oz_split_elems(N, K, brow) * 2);
+  L->hl = o; o += L->ksplit > 1 ? al256((size_t)OZ_HL_TILE * sizeof(long long)) : 0;
   L->total = o;
   return true;
 }
@@ -77,12 +82,14 @@ extern "C" int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, 
   OzDesc od{fused ? (const void*)A : (const void*)(ws + L.ta), ea,
             fused_b ? (const void*)B : (const void*)(ws + L.tb), eb, C, c_rs, c_cs, M, N, K,
             0, fused ? a_rs : (fused_b ? b_rs : 0)};
+  if (L.ksplit > 1) od.hl = reinterpret_cast<long long*>(ws + L.hl);
   std::vector<int4> tiles;
   if (kernel == ELM_DDM_GEMM_PERSISTENT) {
     tiles.resize(L.tiles);
     oz_upd_tile_table(&od, 1, 0, tiles.data());
   }
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess && L.ksplit > 1) e = cudaMemsetAsync(ws + L.hl, 0, OZ_HL_TILE * sizeof(long long), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ws + L.sd, sd, sizeof sd, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ws + L.od, &od, sizeof od, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !tiles.empty())
@@ -102,7 +109,7 @@ extern "C" int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, 
                              st);
         break;
       case ELM_DDM_GEMM_FUSED_SPLIT_B: e = launch_ozaki_fb(dod, 1, (N + 31) / 32, status, st); break;
-      default: e = launch_ozaki_fa(dod, 1, (M + 127) / 128, status, st); break;
+      default: e = launch_ozaki_fa(dod, 1, (M + 127) / 128, status, st, 8, L.ksplit); break;
     }
   }
   unsigned bits = 0;

@@ -541,12 +541,20 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + FA_SLOT);
   volatile int* abort_flag = reinterpret_cast<int*>(smem + FA_FLAG);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
-  const int nch = (nkc + 3) / 4;  // 128-wide chunks; H, L exact below 2^53 up to 62 of them
-  if (nch > OZ_MAX_CHUNKS) {
+  const int nkc_all = (d.K + OZ_KC - 1) / OZ_KC;
+  const int nch_all = (nkc_all + 3) / 4;  // 128-wide chunks; H, L exact below 2^53 up to 62 of them
+  if (nch_all > OZ_MAX_CHUNKS || (d.hl && tiles_m > 1)) {
     if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
     return;
   }
+  // split K (gridDim.z > 1, with the int64 accumulator d.hl): this CTA takes the chunks
+  // [c0, c1); below, kc and the chunk counts are local to that range, kb its first step
+  const int per = (nch_all + gridDim.z - 1) / gridDim.z;
+  const int c0 = (int)blockIdx.z * per, c1 = min(nch_all, c0 + per);
+  if (c0 >= c1) return;
+  const int kb = c0 * 4;
+  const int nkc = min(nkc_all, c1 * 4) - kb;
+  const int nch = (nkc + 3) / 4;
 
   if (tid == 0) {
     for (int i = 0; i < FA_NS; ++i) {
@@ -581,7 +589,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
         const int s = kc % FA_NS, use = kc / FA_NS;
         if (!mbar_wait(EMPTY + 8 * s, (use & 1) ^ 1)) { *abort_flag = 1; break; }
         mbar_expect_tx(BFULL + 8 * s, FA_B);
-        const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(d.Bt) + (size_t)kc * OZ_S * 32 * OZ_KC;
+        const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(d.Bt) + (size_t)(kb + kc) * OZ_S * 32 * OZ_KC;
         bulk_g2s(sbase + s * FA_STAGE + FA_A, src, FA_B, BFULL + 8 * s);
         issued = kc + 1;
       }
@@ -641,7 +649,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
     const int quarter = warp & 3, col0 = (ew >> 2) * 8;  // drain: TMEM lane quarter, 8 columns
     const int drow = bi * OZ_M + quarter * 32 + lane;
     auto load = [&](int kc, double (&x)[8]) {
-      const int k0 = kc * OZ_KC + kg * 8;
+      const int k0 = (kb + kc) * OZ_KC + kg * 8;
       if (row_ok && vec && k0 + 8 <= d.K) {
         const double2* p2 = reinterpret_cast<const double2*>(rowp + k0);
 #pragma unroll
@@ -707,7 +715,17 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
       if (((kc & 3) == 3 || kc == nkc - 1) && (kc >> 2) >= 1) drain((kc >> 2) - 1);
     }
     if (alive && nch >= 1) drain(nch - 1);
-    if (alive && drow < d.M) {
+    if (alive && drow < d.M && d.hl) {
+      // split K: the exact integer words go to the accumulator (one 128 x 32 tile), added in
+      // any order with the same result; k_hl_convert builds C from them
+      unsigned long long* hp = reinterpret_cast<unsigned long long*>(d.hl) + ((size_t)drow * 32 + col0) * 2;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (col0 + j < d.N) {
+          atomicAdd(hp + 2 * j, (unsigned long long)H[j]);
+          atomicAdd(hp + 2 * j + 1, (unsigned long long)Lw[j]);
+        }
+    } else if (alive && drow < d.M) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int gj = col0 + j;
@@ -730,6 +748,30 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// C from the split-K accumulator of k_ozaki_fa: the two exact int64 words of every element
+// (summed over the K ranges by integer atomics, so in any order the same), converted with
+// the fa epilogue's arithmetic, and the accumulator cleared for the next product.
+__global__ void __launch_bounds__(256) k_hl_convert(const OzDesc* __restrict__ descs) {
+  const OzDesc d = descs[blockIdx.y];
+  long long* hl = d.hl;
+  for (int e = blockIdx.x * 256 + threadIdx.x; e < d.M * 32; e += gridDim.x * 256) {
+    const int row = e >> 5, col = e & 31;
+    if (col >= d.N) continue;
+    long long* hp = hl + 2 * (size_t)e;
+    const long long H = hp[0], Lw = hp[1];
+    hp[0] = 0;
+    hp[1] = 0;
+    const int ed = (row < d.lead ? d.Ae2 : d.Ae)[row];
+    const int fj = d.Be[col];
+    double v = 0.0;
+    if (ed != 0 && fj != 0) {
+      const int k = ed + fj - 2044 - 62;
+      v = i64_to_double_pow2(H, k + 24, false) + i64_to_double_pow2(Lw, k, false);
+    }
+    d.C[(size_t)row * d.c_rs + (size_t)col * d.c_cs] = v;
   }
 }
 
@@ -1291,9 +1333,9 @@ cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int 
 }
 
 cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned* status,
-                            cudaStream_t st, int gmax) {
+                            cudaStream_t st, int gmax, int ksplit) {
   if (count <= 0 || max_tiles <= 0) return cudaSuccess;
-  if (gmax < 2 || gmax > OZ_S + 1) return cudaErrorInvalidValue;
+  if (gmax < 2 || gmax > OZ_S + 1 || ksplit < 1 || (ksplit > 1 && max_tiles > 1)) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_ozaki_fa, cudaFuncAttributeMaxDynamicSharedMemorySize, FA_SMEM);
@@ -1302,7 +1344,10 @@ cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned*
   }
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
-    k_ozaki_fa<<<dim3(max_tiles, c), FA_THREADS, FA_SMEM, st>>>(d + off, status, gmax); count_launch();
+    k_ozaki_fa<<<dim3(max_tiles, c, ksplit), FA_THREADS, FA_SMEM, st>>>(d + off, status, gmax); count_launch();
+    if (ksplit > 1) {
+      k_hl_convert<<<dim3(4, c), 256, 0, st>>>(d + off); count_launch();
+    }
   }
   return cudaGetLastError();
 }

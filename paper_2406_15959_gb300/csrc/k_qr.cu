@@ -726,56 +726,74 @@ __global__ void __launch_bounds__(128) k_form_t(const double* __restrict__ G, lo
 }
 
 // Compact-WY factor of a block of w <= 128 columns spanning several panels, for the
-// trailing update of a two-level blocked QR: the same forward recurrence as k_form_t,
-// T(0:j, j) = -tau_j T(0:j, 0:j) g_j, over the block's Gram matrix.  One CTA of 256
-// threads per subdomain keeps T in shared memory; row j of the (symmetric) Gram matrix,
-// v_l^T v_j for l < j, is fetched from global memory one step ahead into a double buffer,
-// and each row i of T is shared by 256 / 128 = 2 threads (4 when w <= 64).
+// trailing update of a two-level blocked QR: the forward recurrence of k_form_t,
+// T(i, j) = -tau_j sum_{l=i}^{j-1} T(i, l) g_j(l) for j > i, T(i, i) = tau_i, over the
+// block's Gram matrix (g_j(l) = v_l^T v_j = G[j][l]).  Row i of T needs only row i's
+// earlier entries, so rows are independent: the 8-row groups of a subdomain are dealt
+// round-robin to FTW_RS CTAs (the heavy first rows spread over both), a warp owns one
+// group with 4 threads per row (each summing every fourth term, 2 shuffles per entry; the
+// groups are paired heavy with light on each SM sub-partition), and
+// no block barrier is needed after G is staged.  The FP64 work, w^3 / 6 per subdomain, is
+// what bounds it; a warp's rows differ by at most 7 in length, so its lanes stay busy.
 constexpr int FTW_MAX = 128;
-constexpr int FTW_LD = FTW_MAX + 1;
-constexpr int FTW_SMEM = (FTW_MAX * FTW_LD + 3 * FTW_MAX) * (int)sizeof(double);
+constexpr int FTW_RS = 2;                      // CTAs per subdomain
+constexpr int FTW_GLD = FTW_MAX + 1;           // padded row of the staged Gram matrix
+constexpr int FTW_ROWS = FTW_MAX / FTW_RS;     // rows of T per CTA
+constexpr int FTW_SMEM = (FTW_MAX * FTW_GLD + FTW_ROWS * FTW_MAX + FTW_MAX) * (int)sizeof(double);
+static_assert(FTW_ROWS == 64, "8 warps x 8 rows per CTA");
 
 __global__ void __launch_bounds__(256) k_form_t_wide(const double* __restrict__ G, long long gstride, int gld,
                                                     const double* __restrict__ tau, int n, int k0, int w,
                                                     double* __restrict__ Tw, long long twstride, int tld,
                                                     double* __restrict__ Td, long long tdstride, int dcol) {
   extern __shared__ double ftw_smem[];
-  double* Tm = ftw_smem;                 // [FTW_MAX][FTW_LD], row-major
-  double* gs = Tm + FTW_MAX * FTW_LD;    // [2][FTW_MAX]
-  double* ts = gs + 2 * FTW_MAX;         // [FTW_MAX]
-  const int s = blockIdx.x, t = threadIdx.x;
-  const int tpr = w <= 64 ? 4 : 2, i = t / tpr, qd = t % tpr;
+  double* Gs = ftw_smem;                        // [w][FTW_GLD]: row j holds g_j
+  double* Tr = Gs + FTW_MAX * FTW_GLD;          // [FTW_ROWS][FTW_MAX]: this CTA's rows of T
+  double* ts = Tr + FTW_ROWS * FTW_MAX;         // [FTW_MAX]
+  const int s = blockIdx.x, q = blockIdx.y, t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const double* Gp = G + (size_t)s * gstride;
-  for (int e = t; e < FTW_MAX * FTW_LD; e += 256) Tm[e] = 0.0;
+  for (int e = t; e < w * w; e += 256) {
+    const int j = e / w, l = e % w;
+    Gs[j * FTW_GLD + l] = Gp[(size_t)j * gld + l];
+  }
   if (t < FTW_MAX) ts[t] = t < w ? tau[(size_t)s * n + k0 + t] : 0.0;
   __syncthreads();
-  for (int j = 0; j < w; ++j) {
-    // row j + 1 of G is loaded while column j is computed, and stored into the buffer that
-    // row j - 1 occupied (last read in the previous step, before its barrier)
-    const bool ld_next = j + 1 < w && t < j + 1;
-    const double gn = ld_next ? Gp[(size_t)(j + 1) * gld + t] : 0.0;
-    const double* g = gs + (j & 1) * FTW_MAX;
-    double p = 0.0;
-    if (i < j)
-      for (int l = i + qd; l < j; l += tpr) p = fma(Tm[i * FTW_LD + l], g[l], p);
-    p += __shfl_xor_sync(0xffffffffu, p, 1);
-    if (tpr == 4) p += __shfl_xor_sync(0xffffffffu, p, 2);
-    if (qd == 0) {
-      if (i < j) Tm[i * FTW_LD + j] = -ts[j] * p;
-      else if (i == j) Tm[j * FTW_LD + j] = ts[j];
+  // warp -> 8-row group, 4 threads per row.  This CTA's groups are q, q + FTW_RS, ...
+  // (heaviest first); warps w and w + 4 share an SM sub-partition's quarter of the FP64
+  // pipe, so warp w < 4 takes the w-th heaviest and warp w + 4 the w-th lightest group.
+  const int rank = warp < 4 ? warp : 11 - warp;
+  const int grp = rank * FTW_RS + q, r8 = lane >> 2, qd = lane & 3;
+  const int i = grp * 8 + r8, slot = warp * 8 + r8;
+  double* Ti = Tr + slot * FTW_MAX;
+  const bool live = i < w;
+  if (live && qd == 0) Ti[i] = ts[i];
+  __syncwarp();
+  const int j0 = grp * 8 + 1;                   // first j any row of the group needs
+  for (int j = j0; j < w; ++j) {
+    double acc = 0.0;
+    if (live)
+      for (int l = i + qd; l < j; l += 4) acc = fma(Ti[l], Gs[j * FTW_GLD + l], acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (live && j > i && qd == 0) Ti[j] = -ts[j] * acc;
+    __syncwarp();
+  }
+  if (live) {
+    double* Tp = Tw + (size_t)s * twstride;
+    for (int j = qd; j < w; j += 4) Tp[(size_t)j * tld + i] = j < i ? 0.0 : Ti[j];
+    // the last panel's diagonal 32-block (rows and columns dcol .. dcol + 31)
+    if (i >= dcol && i < dcol + 32) {
+      double* Dp = Td + (size_t)s * tdstride;
+      for (int c = qd; c < 32; c += 4) {
+        const int j = dcol + c;
+        Dp[(size_t)c * 32 + (i - dcol)] = (j < w && j >= i) ? Ti[j] : 0.0;
+      }
     }
-    if (ld_next) gs[((j + 1) & 1) * FTW_MAX + t] = gn;
-    __syncthreads();
   }
-  double* Tp = Tw + (size_t)s * twstride;
-  for (int e = t; e < w * w; e += 256) {
-    const int r = e % w, c = e / w;
-    Tp[(size_t)c * tld + r] = Tm[r * FTW_LD + c];
-  }
-  double* Dp = Td + (size_t)s * tdstride;
-  for (int e = t; e < 32 * 32; e += 256) {
-    const int r = e & 31, c = e >> 5;
-    Dp[e] = (dcol + r < FTW_MAX && dcol + c < FTW_MAX) ? Tm[(dcol + r) * FTW_LD + dcol + c] : 0.0;
+  // rows of the diagonal block beyond w (a last panel narrower than 32): zero
+  if (q == 0 && t < 32 && dcol + t >= w) {
+    double* Dp = Td + (size_t)s * tdstride;
+    for (int c = 0; c < 32; ++c) Dp[(size_t)c * 32 + t] = 0.0;
   }
 }
 
@@ -842,7 +860,8 @@ cudaError_t launch_form_t_wide(const double* G, long long gstride, int gld, cons
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_form_t_wide<<<N, 256, FTW_SMEM, st>>>(G, gstride, gld, tau, n, k0, w, Tw, twstride, tld, Td, tdstride, dcol);
+  k_form_t_wide<<<dim3(N, FTW_RS), 256, FTW_SMEM, st>>>(G, gstride, gld, tau, n, k0, w, Tw, twstride, tld, Td,
+                                                        tdstride, dcol);
   count_launch();
   return cudaGetLastError();
 }

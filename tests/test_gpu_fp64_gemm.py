@@ -80,10 +80,13 @@ def _wide_rows(M, K, binades=44):
 @pytest.mark.parametrize("kernel,K", [(E.GEMM_TILE32, 300), (E.GEMM_TILE32, 2048),
                                       (E.GEMM_TILE64, 128), (E.GEMM_PERSISTENT, 96),
                                       (E.GEMM_FUSED_SPLIT, 700), (E.GEMM_TILE32, 9000),
-                                      (E.GEMM_FUSED_SPLIT, 9000), (E.GEMM_FUSED_SPLIT_B, 700),
+                                      (E.GEMM_FUSED_SPLIT, 9000), (E.GEMM_FUSED_SPLIT, 2400),
+                                      (E.GEMM_FUSED_SPLIT_B, 700),
                                       (E.GEMM_FUSED_SPLIT_B, 2400), (E.GEMM_FUSED_SPLIT_B, 9000)])
 def test_random_operands_within_the_bound(kernel, K):
-    M, N = {E.GEMM_FUSED_SPLIT: (200, 32), E.GEMM_FUSED_SPLIT_B: (120, 350)}.get(kernel, (200, 70))
+    # (M <= 128 for the fused A split at K = 2400: one tile, K split over 4 CTAs)
+    M, N = {E.GEMM_FUSED_SPLIT: (120 if K == 2400 else 200, 32),
+            E.GEMM_FUSED_SPLIT_B: (120, 350)}.get(kernel, (200, 70))
     A, B = RNG.standard_normal((M, K)), RNG.standard_normal((N, K))
     _check(kernel, A, B)
     # the bound is also tight enough to mean FP64 accuracy for well-scaled data
