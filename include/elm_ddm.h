@@ -438,6 +438,8 @@ int elm_ddm_chol_solve_noalloc(const double* L, int n, int ld, const double* b, 
  *                                    K <= 65536, alpha = 1, beta = 0
  *           ELM_DDM_GEMM_FUSED_SPLIT_B  B split inside the product kernel: b_ks = 1,
  *                                    M <= 128, K <= 65536, alpha = 1, beta = 0
+ *           ELM_DDM_GEMM_PERSISTENT_WIDE  one CTA per SM over 128 x 64 tiles (the QR's
+ *                                    outer-block update): K <= 128, alpha = +-1, beta = 1
  *   A, B, C  device double (C must not overlap A or B)
  *   workspace  device memory, 256-byte aligned, of at least
  *              elm_ddm_fp64_gemm_workspace(kernel, M, N, K) bytes (0 for an unsupported
@@ -452,6 +454,7 @@ int elm_ddm_chol_solve_noalloc(const double* L, int n, int ld, const double* b, 
 #define ELM_DDM_GEMM_PERSISTENT  2
 #define ELM_DDM_GEMM_FUSED_SPLIT 3
 #define ELM_DDM_GEMM_FUSED_SPLIT_B 4
+#define ELM_DDM_GEMM_PERSISTENT_WIDE 5
 size_t elm_ddm_fp64_gemm_workspace(int kernel, int M, int N, int K);
 int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, const double* A,
                       long long a_rs, long long a_ks, const double* B, long long b_rs,

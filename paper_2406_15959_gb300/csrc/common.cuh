@@ -101,7 +101,12 @@ cudaError_t launch_ozaki(int nt, const OzDesc* d, int count, int max_tiles, doub
 // column tile) over all 128 x 32 output tiles of the batch.  oz_upd_tile_table (host)
 // writes that table (out may be null to count) and skips the tiles above the diagonal of
 // a GEMM_LOWER product; it returns the number of tiles.
-int oz_upd_tile_table(const OzDesc* descs, int count, int flags, int4* out);
+int oz_upd_tile_table(const OzDesc* descs, int count, int flags, int4* out, int nt = 32);
+// C += alpha A B^T, alpha = +-1, K <= 128, over 128 x 64 output tiles (tile table with
+// nt = UPW_TILE_N; B split with row_tile 64): the wide persistent update.
+constexpr int UPW_TILE_N = 64;
+cudaError_t launch_ozaki_updw(const OzDesc* d, int count, const int4* tiles, int total_tiles, double alpha,
+                              unsigned* status, cudaStream_t st, int max_grid = 0, int gmax = 8);
 // max_grid > 0 caps the persistent grid (SMs left to work on another stream).
 cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int total_tiles,
                              double alpha, double beta, int flags, unsigned* status,
@@ -112,9 +117,10 @@ cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned*
                             cudaStream_t st, int gmax = 8, int ksplit = 1);
 // C = A B^T with A already split (M <= 128: one row tile) and the FP64 B operand split
 // inside the kernel: B row j at Bt + j * a_rs with exponent bound Be[j], or, for j < lead,
-// at At2 + j * a_rs with Ae2[j].  One CTA per 32 rows of B (max_tiles = the most tiles).
+// at At2 + j * a_rs with Ae2[j].  One CTA per nbc (32 or 64) rows of B (max_tiles = the
+// most tiles).
 cudaError_t launch_ozaki_fb(const OzDesc* d, int count, int max_tiles, unsigned* status,
-                            cudaStream_t st, int gmax = 8);
+                            cudaStream_t st, int gmax = 8, int nbc = 32);
 cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_tiles,
                         double alpha, double beta, int flags, cudaStream_t st);
 cudaError_t launch_add_blocks(const AddDesc* d, int count, int max_elems, cudaStream_t st);

@@ -30,7 +30,8 @@ struct LaunchRec {
              // 7 = compact-WY T of QR panel `off` from the Gram rows of its W1 product,
              // 8 = compact-WY T of the outer QR block of nt columns from column toff, whose
              //     last panel is `off`,
-             // 9 = tensor-core digit GEMM with the FP64 B operand split in the kernel
+             // 9 = tensor-core digit GEMM with the FP64 B operand split in the kernel,
+             // 10 = wide persistent tensor-core digit update (128 x 64 tiles, K <= 128)
   int off, count, max_tiles;  // split: max_tiles = blocks of k_split, nt = max rows
   bool ta, tb;
   double alpha, beta;
@@ -374,8 +375,11 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
       ELM_LAUNCH_FB(h, launch_ozaki_upd(h->od + L.off, L.count, h->ut + L.toff, L.max_tiles, L.alpha,
                                         L.beta, L.flags, h->status, h->st, h->tune_upd_grid, gmax), nm,
                     L.flops, L.bytes);
+    else if (L.kind == 10)
+      ELM_LAUNCH_FB(h, launch_ozaki_updw(h->od + L.off, L.count, h->ut + L.toff, L.max_tiles, L.alpha, h->status,
+                                         h->st, h->tune_upd_grid, gmax), nm, L.flops, L.bytes);
     else if (L.kind == 9)
-      ELM_LAUNCH_FB(h, launch_ozaki_fb(h->od + L.off, L.count, L.max_tiles, h->status, h->st, gmax), nm,
+      ELM_LAUNCH_FB(h, launch_ozaki_fb(h->od + L.off, L.count, L.max_tiles, h->status, h->st, gmax, L.nt), nm,
                     L.flops, L.bytes);
     else
       ELM_LAUNCH_FB(h, launch_ozaki_fa(h->od + L.off, L.count, L.max_tiles, h->status, h->st, gmax,
@@ -782,7 +786,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const int nbo = std::min(QR_NBO, round_up(n, QR_NB));
   const size_t s2 = al(oz_split_elems(nbo, mpmax, 128) * 2), e2 = al((size_t)nbo * 4);
   const size_t s3 = al(oz_split_elems(mpmax, nbo, 128) * 2), e3 = al((size_t)mpmax * 4);
-  const size_t s4 = al(oz_split_elems(n2max, nbo, 32) * 2), e4 = al((size_t)n2max * 4);
+  const size_t s4 = al(oz_split_elems(n2max, nbo, 64) * 2), e4 = al((size_t)n2max * 4);  // (64-row tiles)
   // D_s / M_s products: Q_G as both operands, Y as the left operand (K = n_N)
   const int mgm = std::max(mgmax, 1);
   const size_t s5 = al(oz_split_elems(mgm, n, 128) * 2), e5 = al((size_t)mgm * 4);
@@ -911,6 +915,26 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
     recs.push_back(L);
   };
+  // C += alpha A B^T (alpha = +-1) over 128 x 64 tiles: the wide persistent update
+  auto add_updw_rec = [&](std::vector<LaunchRec>& recs, const std::vector<OzDesc>& batch, double alpha,
+                          const char* name) {
+    LaunchRec L{10, (int)ods.size(), 0, 0, false, false, alpha, 1.0, 0, 0.0, 64};
+    L.name = name;
+    for (const OzDesc& d : batch) {
+      if (d.M <= 0 || d.N <= 0) continue;
+      ods.push_back(d);
+      L.count++;
+      L.flops += 2.0 * d.M * d.N * d.K;
+      L.bytes += 8.0 * ((double)d.M * d.K + (double)d.N * d.K) + 16.0 * d.M * d.N;
+    }
+    if (L.count > 0) {
+      L.toff = (int)uts.size();
+      L.max_tiles = oz_upd_tile_table(ods.data() + L.off, L.count, 0, nullptr, UPW_TILE_N);
+      uts.resize(uts.size() + L.max_tiles);
+      oz_upd_tile_table(ods.data() + L.off, L.count, 0, uts.data() + L.toff, UPW_TILE_N);
+    }
+    recs.push_back(L);
+  };
   // C = A B^T with A = FP64 operand split inside the kernel (N <= 32, beta = 0); ksplit > 1:
   // K split over that many CTAs per tile (one 128-row tile, the descriptors' hl set)
   auto add_fa_rec = [&](std::vector<LaunchRec>& recs, const std::vector<OzDesc>& batch, const char* name,
@@ -928,14 +952,17 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     recs.push_back(L);
   };
   // C = A B^T with B = FP64 operand split inside the kernel (M <= 128, beta = 0)
+  // (64 rows of B per CTA when some descriptor has that many: N = 64 MMAs)
   auto add_fb_rec = [&](std::vector<LaunchRec>& recs, const std::vector<OzDesc>& batch, const char* name) {
-    LaunchRec L{9, (int)ods.size(), 0, 0, false, false, 1.0, 0.0, 0, 0.0, 0};
+    int nbc = 32;
+    for (const OzDesc& d : batch) if (d.N >= 64) nbc = 64;
+    LaunchRec L{9, (int)ods.size(), 0, 0, false, false, 1.0, 0.0, 0, 0.0, nbc};
     L.name = name;
     for (const OzDesc& d : batch) {
       if (d.M <= 0 || d.N <= 0) continue;
       ods.push_back(d);
       L.count++;
-      L.max_tiles = std::max(L.max_tiles, (d.N + 31) / 32);
+      L.max_tiles = std::max(L.max_tiles, (d.N + nbc - 1) / nbc);
       L.flops += 2.0 * d.M * d.N * d.K;
       L.bytes += 8.0 * ((double)d.M * d.K + (double)d.N * d.K + (double)d.M * d.N);
     }
@@ -1079,7 +1106,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       spt.push_back({To, QR_NBO, 1, wo, wo, x10, t10, 32});
       spt.push_back({Vo, 1, ld, mpo, wo, x3, t3, 128});
       ot.push_back({t9, x9, t10, x10, w2, QR_NBO, 1, n2o, wo, wo, 0});
-      sp3.push_back({w2, QR_NBO, 1, n2o, wo, x4, t4, 32});
+      sp3.push_back({w2, QR_NBO, 1, n2o, wo, x4, t4, 64});  // 64-row tiles for the wide update
       o3.push_back({t3, x3, t4, x4, A2, 1, ld, mpo, n2o, wo, 0});
     }
     LaunchRec FW{8, b, 1, 0, false, false, 0.0, 0.0, 0, 0.0, wo};
@@ -1091,7 +1118,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     add_split_rec(h->qr_recs, spt, "split_qr_t");
     add_oz_rec(h->qr_recs, ot, 0, 1.0, 0.0, 0, "oz_qr_t");
     add_split_rec(h->qr_recs, sp3, "split_qr_update");
-    add_oz_rec(h->qr_recs, o3, 0, -1.0, 1.0, 0, "oz_qr_update");
+    add_updw_rec(h->qr_recs, o3, -1.0, "oz_qr_update");
   }
   h->qr_first.push_back((int)h->qr_recs.size());
   // Y = A R^{-1}, blocked by 64 columns: substitution on the diagonal block of R, then the

@@ -29,6 +29,7 @@ bool layout(int kernel, int M, int N, int K, Layout* L) {
     case ELM_DDM_GEMM_TILE32: if (K > 512 * 128) return false; break;
     case ELM_DDM_GEMM_TILE64: if (K > 128) return false; brow = 64; break;
     case ELM_DDM_GEMM_PERSISTENT: if (K > 128) return false; break;
+    case ELM_DDM_GEMM_PERSISTENT_WIDE: if (K > 128) return false; brow = 64; break;
     case ELM_DDM_GEMM_FUSED_SPLIT: if (N > 32 || K > 512 * 128) return false; break;
     case ELM_DDM_GEMM_FUSED_SPLIT_B: if (M > 128 || K > 512 * 128) return false; break;
     default: return false;
@@ -37,7 +38,9 @@ bool layout(int kernel, int M, int N, int K, Layout* L) {
   // the fused A-split product of a single 128-row tile splits K over up to 4 CTAs (exact
   // int64 accumulation, the same bits as one CTA)
   L->ksplit = (kernel == ELM_DDM_GEMM_FUSED_SPLIT && M <= 128) ? std::min(4, (K + 511) / 512) : 1;
-  L->tiles = kernel == ELM_DDM_GEMM_PERSISTENT ? ((M + 127) / 128) * ((N + 31) / 32) : 0;
+  L->tiles = kernel == ELM_DDM_GEMM_PERSISTENT        ? ((M + 127) / 128) * ((N + 31) / 32)
+             : kernel == ELM_DDM_GEMM_PERSISTENT_WIDE ? ((M + 127) / 128) * ((N + 63) / 64)
+                                                      : 0;
   size_t o = 0;
   L->status = o; o += 256;
   L->sd = o; o += al256(2 * sizeof(SplitDesc));
@@ -71,6 +74,8 @@ extern "C" int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, 
     return ELM_DDM_ERR_ARG;
   if (kernel == ELM_DDM_GEMM_FUSED_SPLIT_B && (b_ks != 1 || alpha != 1.0 || beta != 0.0))
     return ELM_DDM_ERR_ARG;
+  if (kernel == ELM_DDM_GEMM_PERSISTENT_WIDE && ((alpha != 1.0 && alpha != -1.0) || beta != 1.0))
+    return ELM_DDM_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
   unsigned* status = reinterpret_cast<unsigned*>(ws + L.status);
@@ -84,9 +89,9 @@ extern "C" int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, 
             0, fused ? a_rs : (fused_b ? b_rs : 0)};
   if (L.ksplit > 1) od.hl = reinterpret_cast<long long*>(ws + L.hl);
   std::vector<int4> tiles;
-  if (kernel == ELM_DDM_GEMM_PERSISTENT) {
+  if (kernel == ELM_DDM_GEMM_PERSISTENT || kernel == ELM_DDM_GEMM_PERSISTENT_WIDE) {
     tiles.resize(L.tiles);
-    oz_upd_tile_table(&od, 1, 0, tiles.data());
+    oz_upd_tile_table(&od, 1, 0, tiles.data(), kernel == ELM_DDM_GEMM_PERSISTENT ? 32 : UPW_TILE_N);
   }
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
   if (e == cudaSuccess && L.ksplit > 1) e = cudaMemsetAsync(ws + L.hl, 0, OZ_HL_TILE * sizeof(long long), st);
@@ -108,7 +113,14 @@ extern "C" int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, 
         e = launch_ozaki_upd(dod, 1, reinterpret_cast<const int4*>(ws + L.ut), L.tiles, alpha, beta, 0, status,
                              st);
         break;
-      case ELM_DDM_GEMM_FUSED_SPLIT_B: e = launch_ozaki_fb(dod, 1, (N + 31) / 32, status, st); break;
+      case ELM_DDM_GEMM_PERSISTENT_WIDE:
+        e = launch_ozaki_updw(dod, 1, reinterpret_cast<const int4*>(ws + L.ut), L.tiles, alpha, status, st);
+        break;
+      case ELM_DDM_GEMM_FUSED_SPLIT_B: {
+        const int nbc = N >= 64 ? 64 : 32;  // as the solver's outer W1 products
+        e = launch_ozaki_fb(dod, 1, (N + nbc - 1) / nbc, status, st, 8, nbc);
+        break;
+      }
       default: e = launch_ozaki_fa(dod, 1, (M + 127) / 128, status, st, 8, L.ksplit); break;
     }
   }

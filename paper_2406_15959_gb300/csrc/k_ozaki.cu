@@ -125,6 +125,12 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&v)[2]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
+               : "=r"(v[0]), "=r"(v[1])
+               : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
@@ -792,22 +798,42 @@ __global__ void __launch_bounds__(256) k_hl_convert(const OzDesc* __restrict__ d
 // next one run.  Every mbarrier is waited on one phase at a time by each waiter (the A
 // ring in step order by the producer and the MMA thread, each B buffer by its own group
 // and the MMA thread), so the parity waits cannot alias a phase two steps away.
-constexpr int FB_WORKERS = 16;
-constexpr int FB_THREADS = 32 * (2 + FB_WORKERS);
 constexpr int FB_NS = 3;                           // A stages
 constexpr int FB_A = OZ_S * OZ_M * OZ_KC * 2;     // 57344 B of A planes per stage
-constexpr int FB_B = OZ_S * 32 * OZ_KC * 2;       // 14336 B of B planes per group buffer
-constexpr int FB_BOFF = FB_NS * FB_A;
-constexpr int FB_BAR = FB_BOFF + 4 * FB_B;        // AFULL[3] AEMPTY[3] BFULL[4] BEMPTY[4] TFULL[2] TEMPTY[2] DONE
-constexpr int FB_SLOT = FB_BAR + 160;
-constexpr int FB_FLAG = FB_SLOT + 16;
-constexpr int FB_SMEM = FB_FLAG + 16 + 1024;
-static_assert(FB_SMEM <= 227 * 1024, "B-split product exceeds the shared memory of one CTA");
+// NBC columns of C (rows of B) per CTA:
+//   32: 16 worker warps in 4 splitting groups (group g splits the K steps g mod 4 into its
+//       own B buffer), two TMEM accumulator sets (the drain of one chunk overlaps the MMAs
+//       of the next), 8 columns per drain thread;
+//   64: 8 worker warps splitting every step into a ring of 2 B buffers, one accumulator set
+//       (the 7 group accumulators of a 128 x 64 tile take 448 of the 512 TMEM columns), 32
+//       columns per drain thread (registers allow it with 10 warps per CTA); its N = 64 MMAs
+//       read each A plane once for twice the columns.
+template <int NBC>
+struct FbCfg {
+  static constexpr int WORKERS = NBC == 32 ? 16 : 8;
+  static constexpr int THREADS = 32 * (2 + WORKERS);
+  static constexpr int NGRP = NBC == 32 ? 4 : 1;          // splitting groups
+  static constexpr int GW = WORKERS / NGRP;               // warps per group
+  static constexpr int NBB = NGRP == 1 ? 2 : NGRP;        // B buffers
+  static constexpr int NBUF = NBC == 32 ? 2 : 1;          // TMEM accumulator sets
+  static constexpr int B = OZ_S * NBC * OZ_KC * 2;        // B planes per buffer
+  static constexpr int BOFF = FB_NS * FB_A;
+  static constexpr int BAR = BOFF + NBB * B;              // AFULL[3] AEMPTY[3] BFULL[4] BEMPTY[4] TFULL[2] TEMPTY[2] DONE
+  static constexpr int SLOT = BAR + 160;
+  static constexpr int FLAG = SLOT + 16;
+  static constexpr int SMEM = FLAG + 16 + 1024;
+  static constexpr int DCOLS = NBC / (WORKERS / 4);       // columns each drain thread owns
+  static_assert(SMEM <= 227 * 1024, "B-split product exceeds the shared memory of one CTA");
+  static_assert(GW * 32 == NBC * 4, "one splitting thread per (row, 8-wide k group)");
+  static_assert(NBB <= 4, "four B barrier pairs");
+};
 
-__global__ void __launch_bounds__(FB_THREADS, 1) k_ozaki_fb(const OzDesc* __restrict__ descs,
+template <int NBC>
+__global__ void __launch_bounds__(FbCfg<NBC>::THREADS, 1) k_ozaki_fb(const OzDesc* __restrict__ descs,
                                                            unsigned* status, int gmax) {
+  using C = FbCfg<NBC>;
   const OzDesc d = descs[blockIdx.y];
-  const int tiles_n = (d.N + 31) / 32;
+  const int tiles_n = (d.N + NBC - 1) / NBC;
   if ((int)blockIdx.x >= tiles_n) return;
   if (d.M > OZ_M) {
     if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
@@ -817,11 +843,11 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_ozaki_fb(const OzDesc* __rest
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sbase = smem_u32(smem);
-  const uint32_t bar = sbase + FB_BAR;
+  const uint32_t bar = sbase + C::BAR;
   const uint32_t AFULL = bar, AEMPTY = bar + 24, BFULL = bar + 48, BEMPTY = bar + 80, TFULL = bar + 112,
                  TEMPTY = bar + 128, DONE = bar + 144;
-  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + FB_SLOT);
-  volatile int* abort_flag = reinterpret_cast<int*>(smem + FB_FLAG);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + C::SLOT);
+  volatile int* abort_flag = reinterpret_cast<int*>(smem + C::FLAG);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
   const int nch = (nkc + 3) / 4;
@@ -835,13 +861,13 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_ozaki_fb(const OzDesc* __rest
       mbar_init(AFULL + 8 * i, 1);
       mbar_init(AEMPTY + 8 * i, 1);
     }
-    for (int i = 0; i < 4; ++i) {
-      mbar_init(BFULL + 8 * i, 128);   // the 4 warps of group i
+    for (int i = 0; i < C::NBB; ++i) {
+      mbar_init(BFULL + 8 * i, 32 * C::GW);   // the warps of the group that fills buffer i
       mbar_init(BEMPTY + 8 * i, 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < C::NBUF; ++i) {
       mbar_init(TFULL + 8 * i, 1);
-      mbar_init(TEMPTY + 8 * i, 32 * FB_WORKERS);
+      mbar_init(TEMPTY + 8 * i, 32 * C::WORKERS);
     }
     mbar_init(DONE, 1);
     *abort_flag = 0;
@@ -876,18 +902,19 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_ozaki_fb(const OzDesc* __rest
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(OZ_M, 32);
+      const uint32_t idesc = idesc_bf16(OZ_M, NBC);
       for (int kc = 0; kc < nkc && !*abort_flag; ++kc) {
-        const int s = kc % FB_NS, use = kc / FB_NS, c = kc >> 2, buf = c & 1, gb = kc & 3;
+        const int s = kc % FB_NS, use = kc / FB_NS, c = kc >> 2, gb = kc % C::NBB;
+        const int buf = C::NBUF == 2 ? (c & 1) : 0, tuse = C::NBUF == 2 ? (c >> 1) : c;
         const bool chunk_start = (kc & 3) == 0;
-        if (chunk_start && !mbar_wait(TEMPTY + 8 * buf, ((c >> 1) & 1) ^ 1)) { *abort_flag = 1; break; }
-        if (!mbar_wait(AFULL + 8 * s, use & 1) || !mbar_wait(BFULL + 8 * gb, (kc >> 2) & 1)) {
+        if (chunk_start && !mbar_wait(TEMPTY + 8 * buf, (tuse & 1) ^ 1)) { *abort_flag = 1; break; }
+        if (!mbar_wait(AFULL + 8 * s, use & 1) || !mbar_wait(BFULL + 8 * gb, (kc / C::NBB) & 1)) {
           *abort_flag = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a0 = sbase + s * FB_A, b0 = sbase + FB_BOFF + gb * FB_B;
-        const uint32_t dbase = tmem + buf * (OZ_G * 32);
+        const uint32_t a0 = sbase + s * FB_A, b0 = sbase + C::BOFF + gb * C::B;
+        const uint32_t dbase = tmem + buf * (OZ_G * NBC);
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
 #pragma unroll
@@ -899,8 +926,8 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_ozaki_fb(const OzDesc* __rest
               if (q < 1 || q > OZ_S) continue;
               const uint32_t first = (chunk_start && t == 0 && p == (g - 1 < OZ_S ? 1 : g - OZ_S));
               const uint64_t ad = sdesc(a0 + (p - 1) * (OZ_M * OZ_KC * 2) + t * 256, 128, 512);
-              const uint64_t bd = sdesc(b0 + (q - 1) * (32 * OZ_KC * 2) + t * 256, 128, 512);
-              mma_bf16(dbase + (g - 2) * 32, ad, bd, idesc, first ? 0u : 1u);
+              const uint64_t bd = sdesc(b0 + (q - 1) * (NBC * OZ_KC * 2) + t * 256, 128, 512);
+              mma_bf16(dbase + (g - 2) * NBC, ad, bd, idesc, first ? 0u : 1u);
             }
           }
         }
@@ -912,19 +939,20 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_ozaki_fb(const OzDesc* __rest
       mbar_wait(DONE, 0);
     }
   } else {
-    // ---------------- workers: split B (group grp takes the K steps kc = grp mod 4), drain TMEM
-    const int ew = warp - 2, grp = ew >> 2;
-    // split item: tile row r (0..31), 8-wide k group kg; the 8 lanes of each quarter-warp
-    // cover 8 rows of one k group, so their 16-byte digit stores fill 128 contiguous bytes
-    const int r = (ew & 3) * 8 + (lane & 7), kg = lane >> 3;
-    const int gj = bj * 32 + r;
+    // ---------------- workers: split B (group grp takes the K steps kc = grp mod NGRP, into
+    // buffer kc mod NBB, in step order), drain TMEM
+    const int ew = warp - 2, grp = ew / C::GW;
+    // split item: tile row r, 8-wide k group kg; the 8 lanes of each quarter-warp cover 8
+    // rows of one k group, so their 16-byte digit stores fill 128 contiguous bytes
+    const int r = (ew % C::GW) * 8 + (lane & 7), kg = lane >> 3;
+    const int gj = bj * NBC + r;
     const bool row_ok = gj < d.N;
     const bool lead_row = gj < d.lead;
     const unsigned emax = row_ok ? (unsigned)(lead_row ? d.Ae2 : d.Be)[gj] : 0u;
     const double* rowp = static_cast<const double*>(lead_row ? d.At2 : d.Bt) + (row_ok ? (size_t)gj * d.a_rs : 0);
     const bool vec = ((reinterpret_cast<uintptr_t>(rowp) | (uintptr_t)d.a_rs * 8) & 15) == 0;
-    const int quarter = warp & 3, col0 = (ew >> 2) * 8;  // drain: TMEM lane quarter, 8 columns
-    const int drow = quarter * 32 + lane;                // row of A (and of C)
+    const int quarter = warp & 3, col0 = (ew >> 2) * C::DCOLS;  // drain: TMEM lane quarter, DCOLS columns
+    const int drow = quarter * 32 + lane;                       // row of A (and of C)
     auto load = [&](int kc, double (&x)[8]) {
       const int k0 = kc * OZ_KC + kg * 8;
       if (row_ok && vec && k0 + 8 <= d.K) {
@@ -940,71 +968,91 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_ozaki_fb(const OzDesc* __rest
         for (int j = 0; j < 8; ++j) x[j] = (row_ok && k0 + j < d.K) ? rowp[k0 + j] : 0.0;
       }
     };
-    long long H[8], Lw[8];
+    // the exact sum of element j is H[j] 2^24 + Lw[j]; after every chunk the part of Lw at
+    // and above 2^24 moves into H, so Lw stays in [0, 2^24) and fits 32 bits
+    long long H[C::DCOLS];
+    int Lw[C::DCOLS];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) { H[j] = 0; Lw[j] = 0; }
+    for (int j = 0; j < C::DCOLS; ++j) { H[j] = 0; Lw[j] = 0; }
     bool alive = true;
     auto drain = [&](int c) {
-      const int buf = c & 1;
-      if (!mbar_wait_warp(TFULL + 8 * buf, (c >> 1) & 1)) { alive = false; *abort_flag = 1; return; }
+      const int buf = C::NBUF == 2 ? (c & 1) : 0, tuse = C::NBUF == 2 ? (c >> 1) : c;
+      if (!mbar_wait_warp(TFULL + 8 * buf, tuse & 1)) { alive = false; *abort_flag = 1; return; }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t lb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (OZ_G * 32) + col0;
+      const uint32_t lb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (OZ_G * NBC) + col0;
+      // columns in groups of CW (2 for the wide tile, keeping the TMEM copies at 14 registers)
+      constexpr int CW = NBC == 32 ? 4 : 2;
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        uint32_t v[OZ_G][4];
+      for (int cb = 0; cb < C::DCOLS / CW; ++cb) {
+        uint32_t v[OZ_G][CW];
 #pragma unroll
         for (int g = 0; g < OZ_G; ++g) {
-          if (g + 2 <= gmax) tmem_ld4(lb + g * 32 + half * 4, v[g]);
-          else for (int j = 0; j < 4; ++j) v[g][j] = 0u;
+          if (g + 2 <= gmax) {
+            if constexpr (CW == 4) tmem_ld4(lb + g * NBC + cb * CW, v[g]);
+            else tmem_ld2(lb + g * NBC + cb * CW, v[g]);
+          } else {
+            for (int j = 0; j < CW; ++j) v[g][j] = 0u;
+          }
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (half == 1) {
+        if (cb == C::DCOLS / CW - 1) {
           asm volatile("tcgen05.fence::before_thread_sync;");
           mbar_arrive(TEMPTY + 8 * buf);
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < CW; ++j) {
           int a[OZ_G];
 #pragma unroll
           for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][j]));
-          H[half * 4 + j] += ((long long)a[0] << 24) + ((long long)a[1] << 16) + ((long long)a[2] << 8);
-          Lw[half * 4 + j] +=
-              ((long long)a[3] << 24) + ((long long)a[4] << 16) + ((long long)a[5] << 8) + a[6];
+          const long long l = (long long)Lw[cb * CW + j] + ((long long)a[3] << 24) + ((long long)a[4] << 16) +
+                              ((long long)a[5] << 8) + a[6];
+          const long long carry = l >> 24;  // floor
+          H[cb * CW + j] += ((long long)a[0] << 24) + ((long long)a[1] << 16) + ((long long)a[2] << 8) + carry;
+          Lw[cb * CW + j] = (int)(l - (carry << 24));
         }
       }
     };
     double xn[8];
     if (grp < nkc) load(grp, xn);
-    unsigned char* stB = smem + FB_BOFF + grp * FB_B;  // this group's B buffer
     for (int kc = 0; kc < nkc && alive; ++kc) {
-      if ((kc & 3) == grp) {
+      if (kc % C::NGRP == grp) {
+        const int bb = kc % C::NBB;
+        unsigned char* stB = smem + C::BOFF + bb * C::B;
         uint32_t w[OZ_S][4];
         split8(xn, emax, w);
-        if (kc + 4 < nkc) load(kc + 4, xn);  // this group's next step, in flight meanwhile
-        // the buffer's previous contents (step kc - 4) have been consumed by the MMAs
-        if (!mbar_wait_warp(BEMPTY + 8 * grp, ((kc >> 2) & 1) ^ 1)) { alive = false; *abort_flag = 1; break; }
+        if (kc + C::NGRP < nkc) load(kc + C::NGRP, xn);  // this group's next step, in flight meanwhile
+        // the buffer's previous contents (step kc - NBB) have been consumed by the MMAs
+        if (!mbar_wait_warp(BEMPTY + 8 * bb, ((kc / C::NBB) & 1) ^ 1)) { alive = false; *abort_flag = 1; break; }
         const int off = tile_off32(r, kg * 8);
 #pragma unroll
         for (int p = 0; p < OZ_S; ++p)
-          *reinterpret_cast<uint4*>(stB + 2 * ((size_t)p * 32 * OZ_KC + off)) =
+          *reinterpret_cast<uint4*>(stB + 2 * ((size_t)p * NBC * OZ_KC + off)) =
               make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(BFULL + 8 * grp);
+        mbar_arrive(BFULL + 8 * bb);
       }
-      if (((kc & 3) == 3 || kc == nkc - 1) && (kc >> 2) >= 1) drain((kc >> 2) - 1);
+      if ((kc & 3) == 3 || kc == nkc - 1) {
+        // two accumulator sets: drain the previous chunk while this one's MMAs run; one set:
+        // drain this chunk now, the next chunk's MMAs wait for its TMEM to be read
+        if (C::NBUF == 2) {
+          if ((kc >> 2) >= 1) drain((kc >> 2) - 1);
+        } else {
+          drain(kc >> 2);
+        }
+      }
     }
-    if (alive && nch >= 1) drain(nch - 1);
+    if (C::NBUF == 2 && alive && nch >= 1) drain(nch - 1);
     if (alive && drow < d.M) {
       const int ed = d.Ae[drow];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int gc = bj * 32 + col0 + j;
+      for (int j = 0; j < C::DCOLS; ++j) {
+        const int gc = bj * NBC + col0 + j;
         if (gc < d.N) {
           const int fj = (gc < d.lead ? d.Ae2 : d.Be)[gc];
           double v = 0.0;
           if (ed != 0 && fj != 0) {
             const int k = ed + fj - 2044 - 62;
-            v = i64_to_double_pow2(H[j], k + 24, false) + i64_to_double_pow2(Lw[j], k, false);
+            v = i64_to_double_pow2(H[j], k + 24, false) + i64_to_double_pow2((long long)Lw[j], k, false);
           }
           d.C[(size_t)drow * d.c_rs + (size_t)gc * d.c_cs] = v;
         }
@@ -1245,6 +1293,189 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Wide persistent update C += s A B^T (s = +-1, K <= 128) over 128 x 64 output tiles: the
+// QR's outer-block trailing update.  An N = 64 MMA reads each A plane from shared memory
+// once for 64 columns (the N = 32 kernel reads it twice), so the operand traffic per
+// output halves.  The 7 group accumulators of a 128 x 64 tile take 448 of the 512 TMEM
+// columns: one set, so the next tile's MMAs wait until the epilogue has read it (its C
+// values are requested before that wait and arrive meanwhile).  B is split with 64-row
+// tiles (one bulk copy per stage).  Warp roles as in k_ozaki_upd; 16 epilogue warps, each
+// thread 16 columns of one row.
+constexpr int UPW_NT = 64;
+constexpr int UPW_EPI_WARPS = 16;
+constexpr int UPW_COLS = UPW_NT / (UPW_EPI_WARPS / 4);
+constexpr int UPW_THREADS = 32 * (2 + UPW_EPI_WARPS);
+constexpr int UPW_A = OZ_S * OZ_M * OZ_KC * 2;       // 57344 B
+constexpr int UPW_B = OZ_S * UPW_NT * OZ_KC * 2;     // 28672 B
+constexpr int UPW_STAGE = UPW_A + UPW_B;
+constexpr int UPW_BAR = 2 * UPW_STAGE;               // FULL[2] EMPTY[2] TFULL TEMPTY
+constexpr int UPW_SLOT = UPW_BAR + 64;
+constexpr int UPW_FLAG = UPW_SLOT + 16;
+constexpr int UPW_SMEM = UPW_FLAG + 16 + 1024;
+static_assert(UPW_SMEM <= 227 * 1024, "wide persistent product exceeds the shared memory of one CTA");
+
+template <bool NEG>
+__global__ void __launch_bounds__(UPW_THREADS, 1) k_ozaki_updw(const OzDesc* __restrict__ descs,
+                                                              const int4* __restrict__ tiles, int total_tiles,
+                                                              unsigned* status, int gmax) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar = sbase + UPW_BAR;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + UPW_SLOT);
+  volatile int* abort_flag = reinterpret_cast<int*>(smem + UPW_FLAG);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t FULL = bar, EMPTY = bar + 16, TFULL = bar + 32, TEMPTY = bar + 40;
+
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(FULL + 8 * i, 1);
+      mbar_init(EMPTY + 8 * i, 1);
+    }
+    mbar_init(TFULL, 1);
+    mbar_init(TEMPTY, 32 * UPW_EPI_WARPS);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int sc = 0;  // stage counter
+      for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
+        const int4 r = tiles[t];  // (entry, row tile, column tile)
+        const OzDesc& d = descs[r.x];
+        const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
+        for (int kc = 0; kc < nkc; ++kc, ++sc) {
+          const int s = sc & 1, use = sc >> 1;
+          if (!mbar_wait(EMPTY + 8 * s, (use & 1) ^ 1)) { *abort_flag = 1; break; }
+          mbar_expect_tx(FULL + 8 * s, UPW_STAGE);
+          const __nv_bfloat16* srcA =
+              static_cast<const __nv_bfloat16*>(d.At) + (size_t)(r.y * nkc + kc) * OZ_S * OZ_M * OZ_KC;
+          const __nv_bfloat16* srcB =
+              static_cast<const __nv_bfloat16*>(d.Bt) + (size_t)(r.z * nkc + kc) * OZ_S * UPW_NT * OZ_KC;
+          const uint32_t dst = sbase + s * UPW_STAGE;
+          bulk_g2s(dst, srcA, UPW_A, FULL + 8 * s);
+          bulk_g2s(dst + UPW_A, srcB, UPW_B, FULL + 8 * s);
+        }
+      }
+      for (int q = (sc > 2 ? sc - 2 : 0); q < sc; ++q) mbar_wait(FULL + 8 * (q & 1), (q >> 1) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(OZ_M, UPW_NT);
+      int sc = 0, tc = 0;
+      for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
+        const OzDesc& d = descs[tiles[t].x];
+        const int nkc = (d.K + OZ_KC - 1) / OZ_KC;
+        // the accumulators of the previous tile have been read by the epilogue
+        if (!mbar_wait(TEMPTY, (tc & 1) ^ 1)) { *abort_flag = 1; break; }
+        bool fail = false;
+        for (int kc = 0; kc < nkc; ++kc, ++sc) {
+          const int s = sc & 1, use = sc >> 1;
+          if (!mbar_wait(FULL + 8 * s, use & 1)) { fail = true; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t a0 = sbase + s * UPW_STAGE, b0 = a0 + UPW_A;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+#pragma unroll
+            for (int g = 2; g <= OZ_S + 1; ++g) {
+              if (g > gmax) continue;  // digit groups beyond gmax are not formed
+#pragma unroll
+              for (int p = 1; p <= OZ_S; ++p) {
+                const int q = g - p;
+                if (q < 1 || q > OZ_S) continue;
+                const uint32_t first = (kc == 0 && k == 0 && p == 1);
+                const uint64_t ad = sdesc(a0 + (p - 1) * (OZ_M * OZ_KC * 2) + k * 256, 128, 512);
+                const uint64_t bd = sdesc(b0 + (q - 1) * (UPW_NT * OZ_KC * 2) + k * 256, 128, 512);
+                mma_bf16(tmem + (g - 2) * UPW_NT, ad, bd, idesc, first ? 0u : 1u);
+              }
+            }
+          }
+          mma_commit(EMPTY + 8 * s);
+        }
+        if (fail) { *abort_flag = 1; break; }
+        mma_commit(TFULL);
+        ++tc;
+      }
+    }
+  } else {
+    const int ew = warp - 2, quarter = warp & 3, part = ew >> 2;
+    const int row = quarter * 32 + lane;
+    const int col0 = part * UPW_COLS;
+    int tc = 0;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++tc) {
+      const int4 r = tiles[t];
+      const OzDesc& d = descs[r.x];
+      const int gi = r.y * OZ_M + row, gj0 = r.z * UPW_NT + col0;
+      const bool rok = gi < d.M;
+      const int ei = rok ? d.Ae[gi] : 0;
+      double* cp = d.C + (size_t)(rok ? gi : 0) * d.c_rs + (size_t)gj0 * d.c_cs;
+      // C in rounds of 4 columns, each round's values requested one round ahead (the first
+      // before the accumulators are waited for)
+      auto load_c = [&](int cb, double (&x)[4]) {
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int j = cb * 4 + jj;
+          x[jj] = (rok && gj0 + j < d.N) ? cp[(size_t)j * d.c_cs] : 0.0;
+        }
+      };
+      double cvn[4];
+      load_c(0, cvn);
+      if (!mbar_wait_warp(TFULL, tc & 1)) { *abort_flag = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t lb = tmem + ((uint32_t)(quarter * 32) << 16) + col0;
+#pragma unroll
+      for (int cb = 0; cb < UPW_COLS / 4; ++cb) {
+        double cv[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) cv[jj] = cvn[jj];
+        if (cb + 1 < UPW_COLS / 4) load_c(cb + 1, cvn);
+        uint32_t v[OZ_G][4];
+#pragma unroll
+        for (int g = 0; g < OZ_G; ++g) {
+          if (g + 2 <= gmax) tmem_ld4(lb + g * UPW_NT + cb * 4, v[g]);
+          else for (int j = 0; j < 4; ++j) v[g][j] = 0u;
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (cb == UPW_COLS / 4 - 1) {
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(TEMPTY);  // accumulators copied: the MMAs of the next tile may start
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int j = cb * 4 + jj;
+          if (rok && gj0 + j < d.N) {
+            int a[OZ_G];
+#pragma unroll
+            for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][jj]));
+            const int fj = d.Be[gj0 + j];
+            const double pv = (ei != 0 && fj != 0) ? groups_to_double(a, ei + fj - 2044 - 62, NEG) : 0.0;
+            cp[(size_t)j * d.c_cs] = cv[jj] + pv;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
 template <int NT>
 cudaError_t launch_oz(const OzDesc* d, int count, int max_tiles, double alpha, double beta,
                       int flags, unsigned* status, cudaStream_t st, int gmax) {
@@ -1282,14 +1513,14 @@ cudaError_t launch_split(const SplitDesc* d, int count, int max_rows, int max_sp
   return cudaGetLastError();
 }
 
-int oz_upd_tile_table(const OzDesc* descs, int count, int flags, int4* out) {
+int oz_upd_tile_table(const OzDesc* descs, int count, int flags, int4* out, int nt) {
   int n = 0;
   for (int e = 0; e < count; ++e) {
     const OzDesc& d = descs[e];
-    const int tm = (d.M + OZ_M - 1) / OZ_M, tn = (d.N + UPD_NT - 1) / UPD_NT;
+    const int tm = (d.M + OZ_M - 1) / OZ_M, tn = (d.N + nt - 1) / nt;
     for (int bj = 0; bj < tn; ++bj)
       for (int bi = 0; bi < tm; ++bi) {
-        if ((flags & GEMM_LOWER) && bj * UPD_NT + d.lower_off > bi * OZ_M + OZ_M - 1) continue;  // above the diagonal
+        if ((flags & GEMM_LOWER) && bj * nt + d.lower_off > bi * OZ_M + OZ_M - 1) continue;  // above the diagonal
         if (out) out[n] = make_int4(e, bi, bj, 0);
         ++n;
       }
@@ -1332,6 +1563,30 @@ cudaError_t launch_ozaki_upd(const OzDesc* d, int count, const int4* tiles, int 
   return cudaGetLastError();
 }
 
+cudaError_t launch_ozaki_updw(const OzDesc* d, int count, const int4* tiles, int total_tiles, double alpha,
+                              unsigned* status, cudaStream_t st, int max_grid, int gmax) {
+  if (count <= 0 || total_tiles <= 0) return cudaSuccess;
+  if (gmax < 2 || gmax > OZ_S + 1 || (alpha != 1.0 && alpha != -1.0)) return cudaErrorInvalidValue;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaFuncSetAttribute(k_ozaki_updw<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, UPW_SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_ozaki_updw<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, UPW_SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  int grid = total_tiles < sms ? total_tiles : sms;
+  if (max_grid > 0 && grid > max_grid) grid = max_grid;
+  if (alpha < 0.0)
+    k_ozaki_updw<true><<<grid, UPW_THREADS, UPW_SMEM, st>>>(d, tiles, total_tiles, status, gmax);
+  else
+    k_ozaki_updw<false><<<grid, UPW_THREADS, UPW_SMEM, st>>>(d, tiles, total_tiles, status, gmax);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned* status,
                             cudaStream_t st, int gmax, int ksplit) {
   if (count <= 0 || max_tiles <= 0) return cudaSuccess;
@@ -1353,18 +1608,25 @@ cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned*
 }
 
 cudaError_t launch_ozaki_fb(const OzDesc* d, int count, int max_tiles, unsigned* status,
-                            cudaStream_t st, int gmax) {
+                            cudaStream_t st, int gmax, int nbc) {
   if (count <= 0 || max_tiles <= 0) return cudaSuccess;
-  if (gmax < 2 || gmax > OZ_S + 1) return cudaErrorInvalidValue;
+  if (gmax < 2 || gmax > OZ_S + 1 || (nbc != 32 && nbc != 64)) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_ozaki_fb, cudaFuncAttributeMaxDynamicSharedMemorySize, FB_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_ozaki_fb<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         FbCfg<32>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_ozaki_fb<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, FbCfg<64>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
-    k_ozaki_fb<<<dim3(max_tiles, c), FB_THREADS, FB_SMEM, st>>>(d + off, status, gmax); count_launch();
+    if (nbc == 64)
+      k_ozaki_fb<64><<<dim3(max_tiles, c), FbCfg<64>::THREADS, FbCfg<64>::SMEM, st>>>(d + off, status, gmax);
+    else
+      k_ozaki_fb<32><<<dim3(max_tiles, c), FbCfg<32>::THREADS, FbCfg<32>::SMEM, st>>>(d + off, status, gmax);
+    count_launch();
   }
   return cudaGetLastError();
 }

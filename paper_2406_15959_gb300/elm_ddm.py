@@ -32,7 +32,7 @@ SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve"
            "elm_ddm_selftest")
 SELFTEST_PIVOT_RCP = 0
 TUNE_PANEL_CTAS, TUNE_UPD_GRID = 0, 1
-GEMM_TILE32, GEMM_TILE64, GEMM_PERSISTENT, GEMM_FUSED_SPLIT, GEMM_FUSED_SPLIT_B = range(5)
+GEMM_TILE32, GEMM_TILE64, GEMM_PERSISTENT, GEMM_FUSED_SPLIT, GEMM_FUSED_SPLIT_B, GEMM_PERSISTENT_WIDE = range(6)
 BUF_K, BUF_A, BUF_D, BUF_M, BUF_L = range(5)
 PTS_INTERIOR, PTS_BOUNDARY, PTS_INTERFACE, PTS_NORMALS = range(4)
 

@@ -123,9 +123,11 @@ def test_upper_triangular_factor_with_kappa_1e14():
 
 
 @pytest.mark.parametrize("kernel,alpha,beta", [(E.GEMM_TILE32, -1.0, 1.0), (E.GEMM_PERSISTENT, -1.0, 1.0),
-                                               (E.GEMM_PERSISTENT, 0.75, -2.0), (E.GEMM_TILE32, 1.0, 0.0)])
+                                               (E.GEMM_PERSISTENT, 0.75, -2.0), (E.GEMM_TILE32, 1.0, 0.0),
+                                               (E.GEMM_PERSISTENT_WIDE, -1.0, 1.0),
+                                               (E.GEMM_PERSISTENT_WIDE, 1.0, 1.0)])
 def test_alpha_beta_update(kernel, alpha, beta):
-    M, N, K = 260, 66, 64
+    M, N, K = (300, 150, 128) if kernel == E.GEMM_PERSISTENT_WIDE else (260, 66, 64)
     A, B = RNG.standard_normal((M, K)), RNG.standard_normal((N, K))
     C0 = RNG.standard_normal((M, N))
     _check(kernel, A, B, alpha, beta, C0)
@@ -141,6 +143,7 @@ def test_zero_and_subnormal_rows():
     B[0] = 0.0
     _check(E.GEMM_TILE32, A, B)
     _check(E.GEMM_PERSISTENT, A, B)
+    _check(E.GEMM_PERSISTENT_WIDE, A, B, beta=1.0, C0=RNG.standard_normal((140, 33)))
 
 
 def test_rejects_unsupported_shapes():
@@ -148,7 +151,12 @@ def test_rejects_unsupported_shapes():
     assert lib.elm_ddm_fp64_gemm_workspace(E.GEMM_PERSISTENT, 10, 10, 129) == 0
     assert lib.elm_ddm_fp64_gemm_workspace(E.GEMM_FUSED_SPLIT, 10, 33, 10) == 0
     assert lib.elm_ddm_fp64_gemm_workspace(E.GEMM_FUSED_SPLIT_B, 129, 10, 10) == 0
+    assert lib.elm_ddm_fp64_gemm_workspace(E.GEMM_PERSISTENT_WIDE, 10, 10, 129) == 0
     assert lib.elm_ddm_fp64_gemm_workspace(9, 10, 10, 10) == 0
+    with pytest.raises(E.ElmDdmError):   # the wide update is C += +-A B^T
+        E.fp64_gemm(torch.zeros((4, 4), dtype=torch.float64, device=DEV),
+                    torch.zeros((4, 4), dtype=torch.float64, device=DEV),
+                    torch.zeros((4, 4), dtype=torch.float64, device=DEV), 0.5, 1.0, E.GEMM_PERSISTENT_WIDE)
     A = torch.zeros((4, 4), dtype=torch.float64, device=DEV)
     with pytest.raises(E.ElmDdmError):   # fused split needs beta = 0
         E.fp64_gemm(A, A, A.clone(), 1.0, 1.0, E.GEMM_FUSED_SPLIT)
