@@ -40,13 +40,14 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07
 SINGLE_CTA_CLASSES = ("potrf",)
 KERNEL_OF_CLASS = {
     "panel_qr": "k_panel_qr_cl (Householder panel of 32 columns, 4-CTA cluster per subdomain, FP64 pipe)",
+    "oz_qr_update_in": "k_ozaki_upd (persistent tensor-core FP64 product: the inner QR steps' updates of the rest of an outer block)",
     "potrf": "k_potrf_diag (64x64 diagonal Cholesky, one CTA, FP64 pipe)",
     "trsm_rows": "k_trsm_chol_rows (Cholesky panel solve by substitution in 4-column blocks, 16 rows per CTA, FP64 pipe)",
-    "oz_qr_update": "k_ozaki_upd (persistent tensor-core FP64 product: A2 -= V_o W2, one K = 128 update per outer QR block)",
-    "oz_qr_w": "k_ozaki_fb (tensor-core FP64 product, B split in the kernel: W1 = V_o^T [V_o | A2] per outer QR block)",
+    "oz_qr_update": "k_ozaki_updw (wide persistent tensor-core FP64 product, 128 x 64 tiles: A2 -= V_o W2, one K = 128 update per outer QR block)",
+    "oz_qr_w": "k_ozaki_fb<64> (tensor-core FP64 product, B split in the kernel, 64-column tiles: W1 = V_o^T [V_o | A2] per outer QR block)",
     "oz_qr_w_in": "k_ozaki_fa (tensor-core FP64 product, A split in the kernel: W1 of the inner panel steps)",
     "oz_syrk": "k_ozaki_upd (persistent tensor-core FP64 product: Schur Cholesky SYRK)",
-    "split_qr_w": "k_rowexp + k_split (digit split of A2^T and V^T)",
+    "split_qr_w": "k_rowexp + k_split (digit split of the outer block's V_o^T)",
     "assemble": "k_exp_tables + k_assemble (K^s, J and A^s from theta: factored activation)",
     "split_qr_update": "k_rowexp + k_split (digit split of V and W2^T)",
     "gemm_qr": "k_gemm (FP64 pipe: QR trailing updates)",
@@ -62,14 +63,14 @@ KERNEL_OF_CLASS = {
 # bench's per-launch traffic is this ratio times its per-launch algorithmic bytes.
 TRAFFIC_PER_ALGO_BYTE = {
     # class: (DRAM bytes of the captured launch, its algorithmic bytes, summary)
-    # first QR panel: 9.880 MB read + 0 B written (the panel stays in L2) for
+    # first QR panel: 9.859 MB read + 5.6 KB written (the panel's writes stay in L2) for
     # 16 x 2400 x 32 x 8 B read and written once
-    "panel_qr": (9.880320e6, 19.6608e6, "profiles/k_panel_qr_cl_poisson_4x4_n1000.md"),
-    # first outer-block trailing update A2 -= V_o W2 (K = 128): C read + written, V_o and
-    # W2 once
-    "oz_qr_update": (768.653312e6, 778.600448e6, "profiles/k_ozaki_upd_poisson_4x4_n1000.md"),
-    # first outer-block W1 = V_o^T [V_o | A2]: V_o^T, [V_o | A2] and W1 once
-    "oz_qr_w": (503.213312e6, 459.980800e6, "profiles/k_ozaki_fb_poisson_4x4_n1000.md"),
+    "panel_qr": (9.864704e6, 19.6608e6, "profiles/k_panel_qr_cl_poisson_4x4_n1000.md"),
+    # first outer-block trailing update A2 -= V_o W2 (K = 128, 128 x 64 tiles): C read +
+    # written, V_o and W2 once
+    "oz_qr_update": (770.483712e6, 778.600448e6, "profiles/k_ozaki_updw_poisson_4x4_n1000.md"),
+    # first outer-block W1 = V_o^T [V_o | A2] (64-column tiles): V_o^T, [V_o | A2] and W1 once
+    "oz_qr_w": (490.386176e6, 459.980800e6, "profiles/k_ozaki_fb_poisson_4x4_n1000.md"),
 }
 
 # Digit pairs a tensor-core FP64 product forms (the p + q <= 8 pairs of the 7 BF16 digit
