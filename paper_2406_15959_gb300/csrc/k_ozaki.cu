@@ -147,9 +147,21 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Warp per row: E[r] = largest biased exponent in row r (0 for an all-zero row).
+// E[r] = largest biased exponent in row r (0 for an all-zero row).  A warp per row,
+// lanes over k; but short rows of a column-major operand (rs == 1, K <= 256): a thread per
+// row looping over k, so that a warp reads 32 consecutive rows of one column at a time
+// (the grid, sized for 8 rows per block, has blocks to spare).
 __global__ void __launch_bounds__(256) k_rowexp(const SplitDesc* __restrict__ descs) {
   const SplitDesc d = descs[blockIdx.y];
+  if (d.rs == 1 && d.ks != 1 && d.K <= 256) {
+    const int r = blockIdx.x * 256 + threadIdx.x;
+    if (r >= d.R) return;
+    unsigned mx = 0;
+    const double* x = d.X + r;
+    for (int k = 0; k < d.K; ++k) mx = max(mx, biased_exp(x[(long long)k * d.ks]));
+    d.E[r] = (int)mx;
+    return;
+  }
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (r >= d.R) return;
