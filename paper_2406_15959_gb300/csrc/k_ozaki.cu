@@ -125,12 +125,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&v)[2]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
-               : "=r"(v[0]), "=r"(v[1])
-               : "r"(taddr));
-}
-
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
@@ -992,16 +986,15 @@ __global__ void __launch_bounds__(FbCfg<NBC>::THREADS, 1) k_ozaki_fb(const OzDes
       if (!mbar_wait_warp(TFULL + 8 * buf, tuse & 1)) { alive = false; *abort_flag = 1; return; }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t lb = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (OZ_G * NBC) + col0;
-      // columns in groups of CW (2 for the wide tile, keeping the TMEM copies at 14 registers)
-      constexpr int CW = NBC == 32 ? 4 : 2;
+      // columns in groups of CW = 4 (the TMEM copies of one group take 28 registers)
+      constexpr int CW = 4;
 #pragma unroll
       for (int cb = 0; cb < C::DCOLS / CW; ++cb) {
         uint32_t v[OZ_G][CW];
 #pragma unroll
         for (int g = 0; g < OZ_G; ++g) {
           if (g + 2 <= gmax) {
-            if constexpr (CW == 4) tmem_ld4(lb + g * NBC + cb * CW, v[g]);
-            else tmem_ld2(lb + g * NBC + cb * CW, v[g]);
+            tmem_ld4(lb + g * NBC + cb * CW, v[g]);
           } else {
             for (int j = 0; j < CW; ++j) v[g][j] = 0u;
           }
