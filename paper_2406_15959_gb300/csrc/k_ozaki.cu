@@ -237,13 +237,29 @@ __device__ __forceinline__ double i64_to_double_pow2(long long x, int k, bool ne
 // result as two exact conversions of P 2^32 and Q and one FP64 addition.  The FP64 pipe
 // (2 operations per clock per SM) is the scarce unit of this epilogue, and the remaining
 // FP64 addition is the one with C.  Outside the normal range the slow path rounds twice.
-__device__ __forceinline__ double groups_to_double(const int (&a)[OZ_G], int k, bool neg) {
+// The integer part: the 63-bit X (sticky bit folded in) and its shift t in {0, 7, 13}.
+__device__ __forceinline__ long long groups_to_x(const int (&a)[OZ_G], int& t) {
   const long long P = (long long)a[0] * 65536 + (long long)a[1] * 256 + a[2];
   const long long Q = (long long)a[3] * 16777216 + (long long)a[4] * 65536 + (long long)a[5] * 256 + a[6];
   const unsigned long long ap = P < 0 ? 0ull - (unsigned long long)P : (unsigned long long)P;
-  const int t = ap < (1ull << 30) ? 0 : (ap < (1ull << 36) ? 7 : 13);
+  t = ap < (1ull << 30) ? 0 : (ap < (1ull << 36) ? 7 : 13);
   long long X = (long long)((unsigned long long)P << (32 - t)) + (Q >> t);
   if (Q & ((1ll << t) - 1)) X |= 1;
+  return X;
+}
+// The floating-point part: X 2^(k + t) with its sign flipped when neg.
+__device__ __forceinline__ double x_to_double(long long X, int kt, bool neg) {
+  if (X == 0) return 0.0;
+  long long b = __double_as_longlong(__ll2double_rn(X));
+  const int e = (int)((b >> 52) & 0x7FF) + kt;
+  if (e <= 0 || e >= 2047) return i64_to_double_pow2_slow(X, kt, neg);
+  b += (long long)kt * (1ll << 52);
+  if (neg) b ^= (long long)(1ull << 63);
+  return __longlong_as_double(b);
+}
+__device__ __forceinline__ double groups_to_double(const int (&a)[OZ_G], int k, bool neg) {
+  int t;
+  const long long X = groups_to_x(a, t);
   if (X == 0) return 0.0;
   // X -> double rounds to nearest (the second rounding); 2^(k + t) and the sign go into
   // the bit pattern
@@ -1304,11 +1320,14 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_ozaki_upd(const OzDesc* __re
 // once for 64 columns (the N = 32 kernel reads it twice), so the operand traffic per
 // output halves.  The 7 group accumulators of a 128 x 64 tile take 448 of the 512 TMEM
 // columns: one set, so the next tile's MMAs wait until the epilogue has read it (its C
-// values are requested before that wait and arrive meanwhile).  B is split with 64-row
-// tiles (one bulk copy per stage).  Warp roles as in k_ozaki_upd; 16 epilogue warps, each
-// thread 16 columns of one row.
+// values are requested before that wait and arrive meanwhile).  The epilogue turns the
+// accumulators into exact integers first and releases the TMEM before its FP64 work (the
+// conversion and the add to C, one FP64-pipe operation each per element), which then
+// overlaps the next tile's MMAs.  B is split with 64-row tiles (one bulk copy per stage).
+// Warp roles as in k_ozaki_upd; 8 epilogue warps (10 warps per CTA leave registers for the
+// 32 exact integers each epilogue thread holds), each thread 32 columns of one row.
 constexpr int UPW_NT = 64;
-constexpr int UPW_EPI_WARPS = 16;
+constexpr int UPW_EPI_WARPS = 8;
 constexpr int UPW_COLS = UPW_NT / (UPW_EPI_WARPS / 4);
 constexpr int UPW_THREADS = 32 * (2 + UPW_EPI_WARPS);
 constexpr int UPW_A = OZ_S * OZ_M * OZ_KC * 2;       // 57344 B
@@ -1440,12 +1459,12 @@ __global__ void __launch_bounds__(UPW_THREADS, 1) k_ozaki_updw(const OzDesc* __r
       if (!mbar_wait_warp(TFULL, tc & 1)) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t lb = tmem + ((uint32_t)(quarter * 32) << 16) + col0;
+      // 1) the accumulators to exact integers (integer work only), then the TMEM is released
+      //    for the next tile's MMAs; 2) the FP64 conversions and C updates meanwhile
+      long long X[UPW_COLS];
+      unsigned long long tcode = 0;  // the shift t of element j in bits 2j, 2j+1 (0, 7, 13 -> 0, 1, 2)
 #pragma unroll
       for (int cb = 0; cb < UPW_COLS / 4; ++cb) {
-        double cv[4];
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) cv[jj] = cvn[jj];
-        if (cb + 1 < UPW_COLS / 4) load_c(cb + 1, cvn);
         uint32_t v[OZ_G][4];
 #pragma unroll
         for (int g = 0; g < OZ_G; ++g) {
@@ -1453,19 +1472,31 @@ __global__ void __launch_bounds__(UPW_THREADS, 1) k_ozaki_updw(const OzDesc* __r
           else for (int j = 0; j < 4; ++j) v[g][j] = 0u;
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (cb == UPW_COLS / 4 - 1) {
-          asm volatile("tcgen05.fence::before_thread_sync;");
-          mbar_arrive(TEMPTY);  // accumulators copied: the MMAs of the next tile may start
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          int a[OZ_G];
+#pragma unroll
+          for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][jj]));
+          int sh;
+          X[cb * 4 + jj] = groups_to_x(a, sh);
+          tcode |= (unsigned long long)(sh == 0 ? 0 : (sh == 7 ? 1 : 2)) << (2 * (cb * 4 + jj));
         }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      mbar_arrive(TEMPTY);  // accumulators copied: the MMAs of the next tile may start
+#pragma unroll
+      for (int cb = 0; cb < UPW_COLS / 4; ++cb) {
+        double cv[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) cv[jj] = cvn[jj];
+        if (cb + 1 < UPW_COLS / 4) load_c(cb + 1, cvn);
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
           const int j = cb * 4 + jj;
           if (rok && gj0 + j < d.N) {
-            int a[OZ_G];
-#pragma unroll
-            for (int g = 0; g < OZ_G; ++g) a[g] = __float2int_rn(__uint_as_float(v[g][jj]));
             const int fj = d.Be[gj0 + j];
-            const double pv = (ei != 0 && fj != 0) ? groups_to_double(a, ei + fj - 2044 - 62, NEG) : 0.0;
+            const int code = (int)(tcode >> (2 * j)) & 3, sh = code == 0 ? 0 : (code == 1 ? 7 : 13);
+            const double pv = (ei != 0 && fj != 0) ? x_to_double(X[j], ei + fj - 2044 - 62 + sh, NEG) : 0.0;
             cp[(size_t)j * d.c_cs] = cv[jj] + pv;
           }
         }
