@@ -68,9 +68,9 @@ TRAFFIC_PER_ALGO_BYTE = {
     "panel_qr": (9.864704e6, 19.6608e6, "profiles/k_panel_qr_cl_poisson_4x4_n1000.md"),
     # first outer-block trailing update A2 -= V_o W2 (K = 128, 128 x 64 tiles): C read +
     # written, V_o and W2 once
-    "oz_qr_update": (770.483712e6, 778.600448e6, "profiles/k_ozaki_updw_poisson_4x4_n1000.md"),
+    "oz_qr_update": (769.099008e6, 778.600448e6, "profiles/k_ozaki_updw_poisson_4x4_n1000.md"),
     # first outer-block W1 = V_o^T [V_o | A2] (64-column tiles): V_o^T, [V_o | A2] and W1 once
-    "oz_qr_w": (490.386176e6, 459.980800e6, "profiles/k_ozaki_fb_poisson_4x4_n1000.md"),
+    "oz_qr_w": (489.178368e6, 459.980800e6, "profiles/k_ozaki_fb_poisson_4x4_n1000.md"),
 }
 
 # Digit pairs a tensor-core FP64 product forms (the p + q <= 8 pairs of the 7 BF16 digit
