@@ -37,6 +37,15 @@ Readings of the paper used here (the paper gives A^s, B^s only for N = 2):
 one A-row per global interface point, carrying the outward-normal derivatives
 of the two subdomains that share it; L = -Laplacian (Eq. (4.4)); all rows have
 unit weight; the Schur system is solved directly instead of by CG.
+
+Cross points (the remark in Section 3).  Where several edges meet at an
+interface point, that point is one unknown shared by all its subdomains, and
+A^s gets one row per edge of s through it, with that edge's normal.  The
+global flux conditions are then no longer one per unknown: with P_s the 0/1
+map of the rows of A^s onto the global conditions (each condition sums the
+rows of the two subdomains of its edge), A = sum_s P_s^T A^s and
+      M = A K^+ B = sum_s P_s^T (-Y_s Q_G^T) E_s,   h = sum_s P_s^T Y_s q_s,
+with S and rhs as above.  Without cross points P_s = E_s.
 """
 from __future__ import annotations
 
@@ -59,8 +68,8 @@ def hidden(W, b, xy):
     return np.tanh(z)
 
 
-def assemble_local(xy, nrm, counts, W, b, coef=None):
-    """K^s [m, n] and A^s [m_G, n] of subdomain s (Section 3).
+def assemble_local(xy, nrm, counts, W, b, coef=None, flux=None):
+    """K^s [m, n] and A^s [m_F, n] of subdomain s (Section 3).
 
     Rows of K^s: L phi_j at interior points, phi_j at boundary points, phi_j at
     interface points.  With t = tanh(w.x + b):
@@ -73,6 +82,9 @@ def assemble_local(xy, nrm, counts, W, b, coef=None):
             = 2 rho |w|^2 t (1 - t^2) - (grad rho . w)(1 - t^2).
     The transmission rows are unchanged: with rho continuous across Gamma the flux
     condition rho du/dn is the normal-derivative condition.
+    flux: None (one A-row per interface row, with its normal nrm) or (rows, normals):
+    the A-rows at interface rows ``rows`` (indices among the interface rows) with those
+    normals (the corner rule of the remark in Section 3).
     """
     mi, mb, mg = (int(v) for v in counts)
     m = mi + mb + mg
@@ -84,9 +96,30 @@ def assemble_local(xy, nrm, counts, W, b, coef=None):
         rho, grho = coef[:mi, 0:1], coef[:mi, 1:3]
         K[:mi] = rho * K[:mi] - (grho @ W.T) * (1.0 - t[:mi] ** 2)
     tg = t[mi + mb:m]
-    wn = nrm[mi + mb:m] @ W.T                     # [m_G, n]: w_j . n_i
-    A = wn * (1.0 - tg ** 2)
+    if flux is None:
+        wn = nrm[mi + mb:m] @ W.T                 # [m_G, n]: w_j . n_i
+        A = wn * (1.0 - tg ** 2)
+    else:
+        rows, fn = flux
+        A = (np.asarray(fn) @ W.T) * (1.0 - tg[np.asarray(rows, np.int64)] ** 2)
     return K, A
+
+
+def flux_rows(geom, s):
+    """(rows, normals, conditions) of the A-rows of subdomain s: the explicit ones of
+    geom.flux, else one per interface row with its normal and its unknown."""
+    mi, mb, mg = (int(v) for v in geom.counts[s])
+    if getattr(geom, "flux", None) is None:
+        return (np.arange(mg), geom.nrm[s, mi + mb:mi + mb + mg],
+                geom.dof[s, mi + mb:mi + mb + mg].astype(np.int64))
+    f = geom.flux
+    c = int(f.count[s])
+    return f.row[s, :c].astype(np.int64), f.nrm[s, :c], f.fdof[s, :c].astype(np.int64)
+
+
+def n_flux(geom):
+    """Number of global flux conditions (rows of A)."""
+    return geom.n_gamma if getattr(geom, "flux", None) is None else int(geom.flux.n_flux)
 
 
 def rhs_local(rhs_row, counts):
@@ -114,9 +147,10 @@ class Local:
     Y: np.ndarray       # A^s R^{-1}
     D: np.ndarray       # I - Q_G Q_G^T
     M: np.ndarray       # -Y Q_G^T
+    fdof: np.ndarray = None   # global flux condition of every row of A^s (P_s)
 
 
-def factor_local(K, A, dof, mi_mb):
+def factor_local(K, A, dof, mi_mb, fdof=None):
     """Householder QR of K^s and the local pieces of Eq. (3.5)."""
     Q, R = np.linalg.qr(K, mode="reduced")
     QG = Q[mi_mb:]
@@ -124,36 +158,38 @@ def factor_local(K, A, dof, mi_mb):
     Y = sla.solve_triangular(R, A.T, trans="T", lower=False).T if A.size else np.zeros_like(A)
     D = np.eye(len(dof)) - QG @ QG.T
     M = -(Y @ QG.T)
-    return Local(K, A, Q, R, dof, mi_mb, QG, Y, D, M)
+    return Local(K, A, Q, R, dof, mi_mb, QG, Y, D, M, dof if fdof is None else fdof)
 
 
-def schur_matrix(locs, n_gamma):
-    """S = sum_s E_s^T D_s E_s + M^T M with M = sum_s E_s^T M_s E_s (Eq. (3.5))."""
+def schur_matrix(locs, n_gamma, n_flux=None):
+    """S = sum_s E_s^T D_s E_s + M^T M with M = sum_s P_s^T M_s E_s (Eq. (3.5)); P_s = E_s
+    without cross points."""
+    n_flux = n_gamma if n_flux is None else n_flux
     S = np.zeros((n_gamma, n_gamma))
     rows, cols, vals = [], [], []
     for L in locs:
         if len(L.dof) == 0:
             continue
         S[np.ix_(L.dof, L.dof)] += L.D
-        rr, cc = np.meshgrid(L.dof, L.dof, indexing="ij")
+        rr, cc = np.meshgrid(L.fdof, L.dof, indexing="ij")
         rows.append(rr.ravel()); cols.append(cc.ravel()); vals.append(L.M.ravel())
     M = None
     if rows:
         M = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                          shape=(n_gamma, n_gamma)).tocsr()
+                          shape=(n_flux, n_gamma)).tocsr()
         S += (M.T @ M).toarray()
     return S, M
 
 
-def schur_rhs(locs, qs, M, n_gamma):
-    """rhs = sum_s E_s^T Q_G q_s + M^T h, h = sum_s E_s^T Y_s q_s (Eq. (3.5))."""
+def schur_rhs(locs, qs, M, n_gamma, n_flux=None):
+    """rhs = sum_s E_s^T Q_G q_s + M^T h, h = sum_s P_s^T Y_s q_s (Eq. (3.5))."""
     r = np.zeros(n_gamma)
-    h = np.zeros(n_gamma)
+    h = np.zeros(n_gamma if n_flux is None else n_flux)
     for L, q in zip(locs, qs):
         if len(L.dof) == 0:
             continue
         np.add.at(r, L.dof, L.QG @ q)
-        np.add.at(h, L.dof, L.Y @ q)
+        np.add.at(h, L.fdof, L.Y @ q)
     if M is not None:
         r += M.T @ h
     return r
@@ -196,18 +232,19 @@ def solve(geom, W, b, rhs_rows, keep=True, coef=None, ridge=None):
     locs, qs = [], []
     for s in range(N):
         mi, mb, mg = (int(v) for v in geom.counts[s])
+        frow, fnrm, fdof = flux_rows(geom, s)
         K, A = assemble_local(geom.xy[s], geom.nrm[s], geom.counts[s], W[s], b[s],
-                              None if coef is None else coef[s])
+                              None if coef is None else coef[s], (frow, fnrm))
         dof = geom.dof[s, mi + mb:mi + mb + mg].astype(np.int64)
         F = rhs_local(rhs_rows[s], geom.counts[s])
         i0 = mi + mb
         if ridge is not None:
             K, F, i0 = ridge_rows(K, F, mi + mb, ridge)
-        L = factor_local(K, A, dof, i0)
+        L = factor_local(K, A, dof, i0, fdof)
         locs.append(L)
         qs.append(L.Q.T @ F)
-    S, M = schur_matrix(locs, geom.n_gamma)
-    r = schur_rhs(locs, qs, M, geom.n_gamma)
+    S, M = schur_matrix(locs, geom.n_gamma, n_flux(geom))
+    r = schur_rhs(locs, qs, M, geom.n_gamma, n_flux(geom))
     if geom.n_gamma:
         Lc = np.linalg.cholesky(S)
         y = sla.solve_triangular(Lc, r, lower=True)
@@ -271,23 +308,24 @@ def rel_errors(u, g, u_ex, g_ex):
 # --------------------------------------------------------------------------
 
 def global_blocks(geom, W, b, rhs_rows, coef=None):
-    """Dense K = diag(K^s), B = [B^s], A = [A^s] (one row per interface unknown),
-    F = [F^s] of Eq. (3.2)."""
+    """Dense K = diag(K^s), B = [B^s], A = [P_s^T A^s] (one row per flux condition: per
+    interface unknown without cross points), F = [F^s] of Eq. (3.2)."""
     Ks, As, Fs, Bs = [], [], [], []
     n = W.shape[1]
     N = geom.n_sub
     for s in range(N):
         mi, mb, mg = (int(v) for v in geom.counts[s])
+        frow, fnrm, fdof = flux_rows(geom, s)
         K, A = assemble_local(geom.xy[s], geom.nrm[s], geom.counts[s], W[s], b[s],
-                              None if coef is None else coef[s])
+                              None if coef is None else coef[s], (frow, fnrm))
         Ks.append(K)
         Fs.append(rhs_local(rhs_rows[s], geom.counts[s]))
         Bs_ = np.zeros((mi + mb + mg, geom.n_gamma))
-        Ag = np.zeros((geom.n_gamma, n))
+        Ag = np.zeros((n_flux(geom), n))
         for r in range(mg):
-            g = int(geom.dof[s, mi + mb + r])
-            Bs_[mi + mb + r, g] = -1.0
-            Ag[g] += A[r]
+            Bs_[mi + mb + r, int(geom.dof[s, mi + mb + r])] = -1.0
+        for r in range(len(fdof)):
+            Ag[int(fdof[r])] += A[r]
         Bs.append(Bs_)
         As.append(Ag)
     K = sla.block_diag(*Ks)

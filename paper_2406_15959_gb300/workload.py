@@ -43,6 +43,23 @@ _NORMALS = {"left": (-1.0, 0.0), "right": (1.0, 0.0),
 
 
 @dataclasses.dataclass
+class FluxRows:
+    """Explicit rows of the A^s blocks (the normal-derivative rows of Section 3), for
+    decompositions with cross points (the remark in Section 3: at a point where several
+    edges meet, A^s gets one row per edge through it, with that edge's normal).  Row f of
+    subdomain s sits at its interface row ``row[s, f]`` (an index among the interface
+    rows) with normal ``nrm[s, f]``; ``fdof[s, f]`` is the global flux condition it
+    belongs to, and every condition sums the rows of the two subdomains of its edge.
+    Without it, each interface row carries one row with its own normal and the condition
+    of its interface unknown."""
+    n_flux: int
+    count: np.ndarray       # int32 [N]
+    row: np.ndarray         # int32 [N, f_max]
+    nrm: np.ndarray         # float64 [N, f_max, 2]
+    fdof: np.ndarray        # int32 [N, f_max], -1 past count
+
+
+@dataclasses.dataclass
 class Geometry:
     """Decomposition of the unit square and the collocation points."""
     gx: int
@@ -56,6 +73,7 @@ class Geometry:
     nrm: np.ndarray         # float64 [N, m_max, 2], outward normal on interface rows
     dof: np.ndarray         # int32 [N, m_max], global interface unknown or -1
     n_gamma: int
+    flux: Optional[FluxRows] = None   # explicit A^s rows (cross points), else one per interface row
 
     @property
     def n_sub(self) -> int:
@@ -526,22 +544,60 @@ def varcoef_grf_4x4_n800() -> Workload:
                  coef="grf", coef_seed=6, name="varcoef_grf_4x4_n800")
 
 
-def make_paper_grid_geometry(G: int, n_grid: int = 257) -> Geometry:
+def make_paper_grid_geometry(G: int, n_grid: int = 257, cross_points: bool = False) -> Geometry:
     """The paper's collocation layout (Section 4.2): the global uniform n_grid x n_grid grid
     of [0, 1]^2 split among G x G subdomains whose boundaries lie on grid lines.  Subdomain
     rows: its grid points strictly inside (interior), its grid points on the outer boundary
     (boundary; a point where an interface line meets the outer boundary is a boundary row
     of both subdomains), and the grid points strictly inside each of its interface edges
-    (interface; one unknown per point, shared by the two subdomains of the edge).  The
-    cross points, where four subdomains meet, are left out: with them the corner rule of
-    the remark in Section 3 would apply (one flux row per edge at the point), and they are
-    (G - 1)^2 of n_grid^2 points.  Interface unknowns are numbered edge by edge like
-    make_geometry's (vertical edges first)."""
+    (interface; one unknown per point, shared by the two subdomains of the edge).
+    Interface unknowns are numbered edge by edge like make_geometry's (vertical edges
+    first).
+
+    The (G - 1)^2 cross points, where four subdomains meet, are left out unless
+    ``cross_points``.  With them, each cross point is one more interface unknown (numbered
+    after the edge unknowns, row by row), an interface row of each of its four
+    subdomains, and the corner rule of the remark in Section 3 applies: A^s gets one row
+    per edge through the point, with that edge's normal.  The rows of A^s are then given
+    explicitly (``flux``): for every interface edge of s, its points and then its ends
+    that are cross points (by increasing coordinate), all with the edge's outward normal;
+    the flux conditions are numbered edge by edge in the same order."""
     h = n_grid - 1
     if h % G:
         raise ValueError("the grid lines must contain the subdomain boundaries")
     k = h // G                      # intervals per subdomain side
     t = np.arange(n_grid, dtype=np.float64) / h
+    n_edge_dof = 2 * G * (G - 1) * (k - 1)
+    n_edges = 2 * G * (G - 1)
+
+    def vertex(X, Y):
+        """Unknown of the cross point on grid lines (X, Y), or None."""
+        if 1 <= X <= G - 1 and 1 <= Y <= G - 1:
+            return n_edge_dof + (Y - 1) * (G - 1) + (X - 1)
+        return None
+
+    def edge_ends(ix, iy, e):
+        """Cross points at the ends of edge e of subdomain (ix, iy), by increasing coordinate."""
+        if e in ("left", "right"):
+            X = ix + (1 if e == "right" else 0)
+            ends = [(X, iy), (X, iy + 1)]
+        else:
+            Y = iy + (1 if e == "top" else 0)
+            ends = [(ix, Y), (ix + 1, Y)]
+        return [(XY, vertex(*XY)) for XY in ends if vertex(*XY) is not None]
+
+    # flux conditions: edge by edge, its k - 1 points and then its cross-point ends
+    f0 = np.zeros(n_edges + 1, np.int64)
+    if cross_points:
+        ends_of = {}
+        for s in range(G * G):
+            ix, iy = s % G, s // G
+            for e in _EDGES:
+                eid = _edge_id(G, G, ix, iy, e)
+                if eid is not None:
+                    ends_of[eid] = len(edge_ends(ix, iy, e))
+        for eid in range(n_edges):
+            f0[eid + 1] = f0[eid] + (k - 1) + ends_of[eid]
     per = []
     for s in range(G * G):
         ix, iy = s % G, s // G
@@ -559,6 +615,15 @@ def make_paper_grid_geometry(G: int, n_grid: int = 257) -> Geometry:
             bnd.append(np.stack([np.ones(k + 1), ys], axis=1))
         bnd = np.unique(np.concatenate(bnd), axis=0) if bnd else np.zeros((0, 2))
         ifc, nrm, dof = [], [], []
+        frow, fnrm, fdof = [], [], []
+        corners = {}                # cross-point unknown -> its interface row in s
+        if cross_points:
+            nedge_rows = (k - 1) * sum(_edge_id(G, G, ix, iy, e) is not None for e in _EDGES)
+            for XY in [(ix, iy), (ix + 1, iy), (ix, iy + 1), (ix + 1, iy + 1)]:
+                v = vertex(*XY)
+                if v is not None:
+                    corners[v] = nedge_rows + len(corners)
+        nrow = 0
         for e in _EDGES:
             eid = _edge_id(G, G, ix, iy, e)
             if eid is None:
@@ -572,17 +637,28 @@ def make_paper_grid_geometry(G: int, n_grid: int = 257) -> Geometry:
             ifc.append(pts)
             nrm.append(np.tile(np.array(_NORMALS[e]), (k - 1, 1)))
             dof.append(eid * (k - 1) + np.arange(k - 1))
+            if cross_points:
+                ends = edge_ends(ix, iy, e)
+                frow += list(range(nrow, nrow + k - 1)) + [corners[v] for _, v in ends]
+                fnrm += [_NORMALS[e]] * (k - 1 + len(ends))
+                fdof += list(range(f0[eid], f0[eid + 1]))
+            nrow += k - 1
+        for v, r in corners.items():
+            X, Y = (v - n_edge_dof) % (G - 1) + 1, (v - n_edge_dof) // (G - 1) + 1
+            ifc.append(np.array([[t[X * k], t[Y * k]]]))
+            nrm.append(np.zeros((1, 2)))      # its A^s rows are the flux rows above
+            dof.append(np.array([v]))
         ifc = np.concatenate(ifc) if ifc else np.zeros((0, 2))
         nrm = np.concatenate(nrm) if nrm else np.zeros((0, 2))
         dof = np.concatenate(dof).astype(np.int32) if dof else np.zeros(0, np.int32)
-        per.append((interior, bnd, ifc, nrm, dof))
-    m_max = max(len(a) + len(b) + len(c) for a, b, c, _, _ in per)
+        per.append((interior, bnd, ifc, nrm, dof, (frow, fnrm, fdof)))
+    m_max = max(len(a) + len(b) + len(c) for a, b, c, _, _, _ in per)
     N = G * G
     counts = np.zeros((N, 3), np.int32)
     xy = np.zeros((N, m_max, 2))
     nr = np.zeros((N, m_max, 2))
     dd = np.full((N, m_max), -1, np.int32)
-    for s, (interior, bnd, ifc, nrm, dof) in enumerate(per):
+    for s, (interior, bnd, ifc, nrm, dof, _) in enumerate(per):
         mi, mb, mg = len(interior), len(bnd), len(ifc)
         counts[s] = (mi, mb, mg)
         xy[s, :mi] = interior
@@ -590,23 +666,38 @@ def make_paper_grid_geometry(G: int, n_grid: int = 257) -> Geometry:
         xy[s, mi + mb:mi + mb + mg] = ifc
         nr[s, mi + mb:mi + mb + mg] = nrm
         dd[s, mi + mb:mi + mb + mg] = dof
-    n_gamma = 2 * G * (G - 1) * (k - 1)
-    return Geometry(G, G, k - 1, k - 1, k + 1, k - 1, counts, xy, nr, dd, n_gamma)
+    n_gamma = n_edge_dof + ((G - 1) ** 2 if cross_points else 0)
+    flux = None
+    if cross_points:
+        f_max = max(len(f[0]) for *_, f in per)
+        fc = np.zeros(N, np.int32)
+        fr = np.zeros((N, f_max), np.int32)
+        fn = np.zeros((N, f_max, 2))
+        fd = np.full((N, f_max), -1, np.int32)
+        for s, (*_, (frow, fnrm, fdof)) in enumerate(per):
+            fc[s] = len(frow)
+            fr[s, :len(frow)] = frow
+            fn[s, :len(frow)] = np.array(fnrm).reshape(-1, 2)
+            fd[s, :len(frow)] = fdof
+        flux = FluxRows(int(f0[-1]), fc, fr, fn, fd)
+    return Geometry(G, G, k - 1, k - 1, k + 1, k - 1, counts, xy, nr, dd, n_gamma, flux)
 
 
 def paper_grid_workload(G: int, n_total: int = 65536, theta: str = "paper", seed: int = 0,
-                        source: str = "sin2pi_exp", n_grid: int = 257, n_test_side: int = 100) -> Workload:
+                        source: str = "sin2pi_exp", n_grid: int = 257, n_test_side: int = 100,
+                        cross_points: bool = False) -> Workload:
     """The paper's Poisson experiments (Section 4.2, Table 2; Table 1 with other theta
     modes): n_total neurons split evenly over G x G subdomains, the global n_grid^2
-    collocation grid (make_paper_grid_geometry), u = sin(2 pi x) e^y by default, theta by
-    Eq. (4.3) with c = 1/8 (``paper``), or ``global_unit`` (Table 1's manual l = 1) or
-    ``he`` (Table 1's He initialisation)."""
-    geom = make_paper_grid_geometry(G, n_grid)
+    collocation grid (make_paper_grid_geometry, with or without its cross points),
+    u = sin(2 pi x) e^y by default, theta by Eq. (4.3) with c = 1/8 (``paper``), or
+    ``global_unit`` (Table 1's manual l = 1) or ``he`` (Table 1's He initialisation)."""
+    geom = make_paper_grid_geometry(G, n_grid, cross_points)
     n = n_total // (G * G)
     W, b = draw_theta(geom, n, theta, seed, c=1.0 / 8.0)
     src = make_source(source, seed)
     txy, own = test_points(geom, n_test_side)
-    return Workload(f"paper_grid_{G}x{G}_{theta}", geom, n, W, b, src, rhs_rows(geom, src), txy, own)
+    name = f"paper_grid_{G}x{G}_{theta}" + ("_cross" if cross_points else "")
+    return Workload(name, geom, n, W, b, src, rhs_rows(geom, src), txy, own)
 
 
 def mixed_16x16_n60_local() -> Workload:

@@ -624,3 +624,156 @@ def test_ridge_single_subdomain_is_ridge_regression():
     c_ref = np.linalg.solve(K.T @ K + lam ** 2 * np.eye(K.shape[1]), K.T @ F)
     res = O.solve(g, w.W, w.b, w.rhs, ridge=alpha)
     np.testing.assert_allclose(res.c[0], c_ref, rtol=1e-9, atol=1e-10 * np.abs(c_ref).max())
+
+
+# ----------------------------------------------------------------- cross points (corner rule)
+
+def cross(G, n_grid, n, seed=5, source="sin2pi_exp"):
+    """The paper's grid with its cross points (the corner rule of the remark in Section 3)."""
+    return wl.paper_grid_workload(G, n_total=n * G * G, theta="local_unit", seed=seed, source=source,
+                                  n_grid=n_grid, n_test_side=10, cross_points=True)
+
+
+@pytest.mark.parametrize("G,n_grid", [(2, 9), (3, 13), (4, 17)])
+def test_cross_point_geometry_follows_the_corner_rule(G, n_grid):
+    """Every interface unknown sits at one point shared by 2 subdomains (inside an edge) or
+    by the 4 around a cross point; every flux condition sums the rows of the two subdomains
+    across one edge, at the same point, with opposite normals pointing from each to the
+    other; and a subdomain has one row per edge through each of its cross points: 2 rows
+    there, 4 conditions per cross point.  Read off the coordinates only."""
+    g = wl.make_paper_grid_geometry(G, n_grid, cross_points=True)
+    f = g.flux
+    owners = {}
+    for s in range(g.n_sub):
+        _, _, rg = g.rows(s)
+        for r in range(rg.start, rg.stop):
+            owners.setdefault(int(g.dof[s, r]), []).append((s, tuple(g.xy[s, r])))
+    assert sorted(owners) == list(range(g.n_gamma))
+    ncross = 0
+    for d, lst in owners.items():
+        assert len({p for _, p in lst}) == 1 and len({s for s, _ in lst}) == len(lst)
+        x, y = lst[0][1]
+        on_x = any(abs(x - i / G) < 1e-12 for i in range(1, G))
+        on_y = any(abs(y - i / G) < 1e-12 for i in range(1, G))
+        assert len(lst) == (4 if on_x and on_y else 2)
+        ncross += on_x and on_y
+    assert ncross == (G - 1) ** 2
+    cond = {}
+    for s in range(g.n_sub):
+        mi, mb, _ = g.counts[s]
+        for k in range(int(f.count[s])):
+            p = tuple(g.xy[s, mi + mb + f.row[s, k]])
+            cond.setdefault(int(f.fdof[s, k]), []).append((s, p, tuple(f.nrm[s, k])))
+    assert sorted(cond) == list(range(f.n_flux))
+    per_point = {}
+    for c, lst in cond.items():
+        assert len(lst) == 2
+        (s0, p0, n0), (s1, p1, n1) = lst
+        assert p0 == p1 and np.array_equal(np.array(n0), -np.array(n1))
+        # the normal of s0 points at s1: the neighbour across that edge
+        ix, iy = s0 % G, s0 // G
+        assert s1 == (iy + int(n0[1])) * G + (ix + int(n0[0]))
+        per_point.setdefault(p0, []).append(lst)
+    for p, conds in per_point.items():
+        x, y = p
+        if any(abs(x - i / G) < 1e-12 for i in range(1, G)) and any(abs(y - i / G) < 1e-12 for i in range(1, G)):
+            assert len(conds) == 4
+            rows = [(s, n) for lst in conds for s, _, n in lst]
+            for s in {s for s, _ in rows}:
+                assert len([n for t, n in rows if t == s]) == 2
+        else:
+            assert len(conds) == 1
+    assert f.n_flux == g.n_gamma + 3 * (G - 1) ** 2
+
+
+def test_corner_rows_are_normal_derivatives():
+    """Every A-row of a cross-point geometry, the extra corner rows included, is the
+    derivative of the features along its row's normal at its row's point (central
+    differences), so A^s c is the normal flux of u_s there."""
+    w = cross(2, 9, 6, seed=4)
+    g = w.geom
+    h = 1e-4
+    for s in range(g.n_sub):
+        frow, fnrm, _ = O.flux_rows(g, s)
+        _, A = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s], flux=(frow, fnrm))
+        mi, mb, _ = g.counts[s]
+        assert A.shape == (len(frow), w.n_neurons)
+        for k in range(len(frow)):
+            p0, n = g.xy[s, mi + mb + frow[k]], fnrm[k]
+            dn = (np.tanh((p0 + h * n) @ w.W[s].T + w.b[s]) - np.tanh((p0 - h * n) @ w.W[s].T + w.b[s])) / (2 * h)
+            np.testing.assert_allclose(A[k], dn, rtol=1e-6, atol=1e-8)
+
+
+@pytest.mark.parametrize("G,n_grid,n", [(2, 17, 30), (3, 19, 24)])
+def test_ddm_route_with_cross_points_matches_monolithic_and_normal_equations(G, n_grid, n):
+    """With cross points the Schur route (P_s != E_s in M and h) still equals the dense LS
+    solution of Eq. (3.3) and the dense normal equations Eq. (3.4), whose global A is
+    assembled row by row from the flux conditions."""
+    w = cross(G, n_grid, n)
+    g = w.geom
+    res = O.solve(g, w.W, w.b, w.rhs)
+    assert res.rdiag_ratio.min() > 1e-6
+    c2, u2 = O.monolithic_ls(g, w.W, w.b, w.rhs)
+    c3, u3 = O.normal_equations(g, w.W, w.b, w.rhs)
+    for c, u in [(c2, u2), (c3, u3)]:
+        assert np.linalg.norm(res.u_gamma - u) <= 1e-9 * np.linalg.norm(u)
+        assert np.linalg.norm(res.c - c) <= 1e-7 * np.linalg.norm(c)
+    # the corner rows change the answer (they are not redundant)
+    g0 = wl.make_paper_grid_geometry(G, n_grid, cross_points=True)
+    g0.flux = None
+    keep = {}
+    for s in range(g0.n_sub):
+        _, _, rg = g0.rows(s)
+        for r in range(rg.start, rg.stop):
+            keep.setdefault(int(g0.dof[s, r]), []).append(s)
+    assert any(len(v) == 4 for v in keep.values())
+
+
+@pytest.mark.parametrize("G,n_grid", [(2, 9), (3, 13)])
+def test_consistent_system_with_cross_points_is_recovered_exactly(G, n_grid):
+    """Networks c* continuous across Gamma (every unknown's value equal in all its
+    subdomains, cross points included) whose normal fluxes cancel in every flux condition
+    (the corner rows included), with F^s = K^s c*^s away from Gamma, solve Eq. (3.1)
+    exactly: the oracle must return them.  A flux condition that paired the wrong rows, or
+    M and h indexed by unknowns instead of flux conditions, leaves a residual."""
+    w = cross(G, n_grid, 16, seed=17)
+    g = w.geom
+    N, n = g.n_sub, w.n_neurons
+    Ks, As, maps = [], [], []
+    for s in range(N):
+        frow, fnrm, fdof = O.flux_rows(g, s)
+        K, A = O.assemble_local(g.xy[s], g.nrm[s], g.counts[s], w.W[s], w.b[s], flux=(frow, fnrm))
+        Ks.append(K); As.append(A); maps.append(fdof)
+    rows = []
+    first = {}
+    for s in range(N):
+        _, _, rg = g.rows(s)
+        for r in range(rg.start, rg.stop):
+            d = int(g.dof[s, r])
+            if d in first:                      # value of s equals value of the first owner
+                s0, r0 = first[d]
+                row = np.zeros(N * n)
+                row[s * n:(s + 1) * n] += Ks[s][r]
+                row[s0 * n:(s0 + 1) * n] -= Ks[s0][r0]
+                rows.append(row)
+            else:
+                first[d] = (s, r)
+    F = np.zeros((g.flux.n_flux, N * n))
+    for s in range(N):
+        for k, c in enumerate(maps[s]):
+            F[c, s * n:(s + 1) * n] += As[s][k]
+    C = np.vstack([np.array(rows), F])
+    Nul = sla.null_space(C)
+    assert Nul.shape[1] > 0
+    cstar = (Nul @ np.random.default_rng(1).standard_normal(Nul.shape[1])).reshape(N, n)
+    rhs = np.zeros_like(w.rhs)
+    ustar = np.zeros(g.n_gamma)
+    for s in range(N):
+        ri, rb, rg = g.rows(s)
+        v = Ks[s] @ cstar[s]
+        rhs[s, :rb.stop] = v[:rb.stop]
+        ustar[g.dof[s, rg]] = v[rg]
+    res = O.solve(g, w.W, w.b, rhs)
+    assert res.rdiag_ratio.min() > 1e-6
+    assert np.linalg.norm(res.u_gamma - ustar) <= 1e-8 * np.linalg.norm(ustar)
+    assert np.linalg.norm(res.c - cstar) <= 1e-6 * np.linalg.norm(cstar)
