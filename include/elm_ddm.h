@@ -6,7 +6,8 @@
  * network per subdomain, u_s(x) = sum_j c^s_j tanh(w^s_j . x + b^s_j), joined by an
  * interface unknown u_Gamma.  The entry points follow Algorithm 1:
  *
- *   elm_ddm_setup     geometry of the decomposition (points, normals, interface map)
+ *   elm_ddm_setup     geometry of the decomposition (points, normals, interface map);
+ *                     elm_ddm_setup_flux also takes explicit rows of A^s (cross points)
  *   elm_ddm_assemble  step (a): K^s, A^s of Eq. (3.1) from the hidden parameters theta^s
  *   elm_ddm_schur     step (b): local Householder QR of K^s, and the RHS-independent
  *                     part of step (c): assembly and Cholesky factorisation of the
@@ -22,10 +23,11 @@
  * - Subdomain s has rows ordered [interior | boundary | interface] (the row blocks of
  *   K^s in Section 3); counts[s] = {m_i, m_b, m_Gamma}; per-row arrays have a row
  *   stride of desc->m_max.
- * - Every interface unknown must be shared by exactly two subdomains.  Interface rows
- *   are grouped into "edges": maximal runs of a subdomain's interface rows with
- *   consecutive global unknowns and the same neighbouring subdomain.  Each edge must
- *   appear, with the same unknowns in the same order, in both subdomains.
+ * - Every interface unknown must be shared by exactly two subdomains (elm_ddm_setup), or
+ *   by two to four (elm_ddm_setup_flux: a cross point, where several edges meet).
+ *   Interface rows are grouped into "edges": maximal runs of a subdomain's interface rows
+ *   with consecutive global unknowns and the same set of sharing subdomains.  Each edge
+ *   must appear, with the same unknowns in the same order, in all those subdomains.
  * - Pointers documented "host" are read during the call only.  Pointers documented
  *   "device" are borrowed for the duration of the call (the kernels they feed are
  *   enqueued on the handle's stream; the caller keeps them alive and unmodified until
@@ -157,6 +159,46 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
                   const double* nrm, const int32_t* dof, void* stream, elm_ddm_handle** out);
 
 /*
+ * Explicit rows of A^s, for decompositions with cross points (the remark in Section 3:
+ * at an interface point where several edges meet, A^s gets one row per edge through the
+ * point, with that edge's normal n_s).  The global flux conditions (rows of the global A)
+ * are numbered 0 .. n_flux-1; each is the sum of exactly two rows, of the two subdomains
+ * of its edge, and the method's pieces become M = A K^+ B = sum_s P_s^T M_s E_s and
+ * h = sum_s P_s^T Y_s q_s, with P_s the map of the rows of A^s onto the conditions
+ * (S and the right-hand side as in elm_ddm_schur / elm_ddm_solve).  elm_ddm_setup is the
+ * case of one row per interface row, with that row's normal and its unknown's condition.
+ *   n_flux  number of global flux conditions (>= 1 when n_gamma > 0)
+ *   f_max   row stride of row, nrm, fdof (>= every count[s])
+ *   count   host int32  [N]           rows of A^s
+ *   row     host int32  [N][f_max]    interface row each A-row sits at, as an index among
+ *                                     the subdomain's interface rows (0 <= row < m_Gamma)
+ *   nrm     host double [N][f_max][2] its unit normal
+ *   fdof    host int32  [N][f_max]    its flux condition, in [0, n_flux)
+ * Rows of A^s are grouped like the interface rows: maximal runs with consecutive
+ * conditions and the same other subdomain, appearing identically in both subdomains.
+ */
+typedef struct elm_ddm_flux_rows {
+  int32_t n_flux;
+  int32_t f_max;
+  const int32_t* count;
+  const int32_t* row;
+  const double* nrm;
+  const int32_t* fdof;
+} elm_ddm_flux_rows;
+
+/*
+ * elm_ddm_setup with explicit rows of A^s (flux: see elm_ddm_flux_rows; NULL is
+ * elm_ddm_setup itself).  With flux rows the per-row normals nrm are not read, interface
+ * unknowns may be shared by up to four subdomains, ELM_DDM_BUF_A / _M export m_F x n_N /
+ * m_F x m_Gamma (m_F = count[s]), and the CG interface solves are not available:
+ * ELM_DDM_FLAG_SCHUR_CG, ELM_DDM_FLAG_MIXED and ELM_DDM_FLAG_BLOCK_JACOBI give ERR_ARG,
+ * elm_ddm_solve_cg / elm_ddm_solve_pcg give ERR_STATE.
+ */
+int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const double* xy,
+                       const double* nrm, const int32_t* dof, const elm_ddm_flux_rows* flux,
+                       void* stream, elm_ddm_handle** out);
+
+/*
  * Step (a) of Algorithm 1 (Section 3, definitions of K^s and A^s): with
  * t = tanh(w.x + b), interior rows get L phi = 2|w|^2 t (1 - t^2), boundary and
  * interface rows get phi = t, and A^s rows get d phi/d n = (w.n)(1 - t^2).
@@ -257,9 +299,10 @@ int elm_ddm_check(elm_ddm_handle* h);
 #define ELM_DDM_BUF_K 0  /* m_s x (n_N + m_Gamma): [K^s | J] after assemble; after schur the
                             Householder factors: R on and above the diagonal, reflectors
                             below it, Q_G^T in rows 0..n_N-1 of the last m_Gamma columns */
-#define ELM_DDM_BUF_A 1  /* m_Gamma x n_N: A^s after assemble, Y_s = A^s R_s^{-1} after schur */
+#define ELM_DDM_BUF_A 1  /* m_F x n_N: A^s after assemble, Y_s = A^s R_s^{-1} after schur
+                            (m_F = m_Gamma, or the explicit rows of elm_ddm_setup_flux) */
 #define ELM_DDM_BUF_D 2  /* m_Gamma x m_Gamma: D_s = I - Q_G Q_G^T (after schur) */
-#define ELM_DDM_BUF_M 3  /* m_Gamma x m_Gamma: M_s = -Y_s Q_G^T (after schur) */
+#define ELM_DDM_BUF_M 3  /* m_F x m_Gamma: M_s = -Y_s Q_G^T (after schur) */
 #define ELM_DDM_BUF_L 4  /* n_gamma x n_gamma: lower Cholesky factor of S in the internal
                             interface order (elm_ddm_interface_order), after schur; s ignored;
                             the strict upper triangle is unspecified */

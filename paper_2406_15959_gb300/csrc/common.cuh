@@ -13,6 +13,7 @@ inline void count_launch(int k = 1) { g_kernel_launches.fetch_add(k, std::memory
 
 constexpr int QR_NB = 32;     // panel width of the blocked Householder QR
 constexpr int CHOL_NB = 64;   // block size of the Schur-matrix Cholesky
+constexpr int GRP_MAX = 4;    // most subdomains one interface unknown is shared by (a cross point)
 constexpr int OZ_HL_TILE = 128 * 32 * 2;  // int64 words of one split-K accumulator tile
 constexpr int TRSV_MAX_N = 8192;  // largest n_neurons the back-solve keeps in shared memory
 
@@ -197,14 +198,27 @@ cudaError_t launch_load_rhs(double* X, const double* rhs, int N, int m_max, int 
 cudaError_t launch_apply_qt(double* X, const double* K, long long kstride, int ld,
                             const int* ms, int N, int n, const double* T, long long tstride,
                             int nrhs, cudaStream_t st);
+// gq_s = Q_G q_s (m_Gamma rows, stride mgld) and hq_s = Y_s q_s (rows of A^s, stride mfld).
 cudaError_t launch_iface_vecs(const double* X, const double* K, long long kstride, int ld,
-                              const double* Y, long long ystride, int mgld, const int* mg,
-                              int N, int n, int nrhs, double* gq, double* hq, cudaStream_t st);
-cudaError_t launch_gather2(const int* dofmap, int n_gamma, int mgld, int N, const double* a,
+                              const double* Y, long long ystride, int mgld, const int* mg, int mfld,
+                              const int* mf, int N, int n, int nrhs, double* gq, double* hq,
+                              cudaStream_t st);
+// out[i] (+)= sum of a[s][l] over the (s, l) pairs of entry i: map [n][2 kmax], a list
+// shorter than kmax ends at s = -1 (its first two pairs are always present).
+cudaError_t launch_gather2(const int* map, int kmax, int n, int ldv, int N, const double* a,
                            double* out, int accumulate, int nrhs, cudaStream_t st);
-cudaError_t launch_mt_h(const double* M, long long mstride, int mgld, const int* mg,
-                        const int* ifc_dof, const double* h, int n_gamma, int N, int nrhs,
+// z_s = M_s^T (P_s h): M_s has mf[s] rows (ld mfld) and mg[s] columns; row k of M_s reads
+// h[ffd[s][k]] (h of length n_flux); z has stride mgld.
+cudaError_t launch_mt_h(const double* M, long long mstride, int mfld, const int* mf, const int* mg,
+                        const int* ffd, const double* h, int n_flux, int N, int mgld, int nrhs,
                         double* z, cudaStream_t st);
+// A-rows at explicit (collocation row, normal) pairs: A[s][f][c] = (w_c . n_f)(1 - t^2),
+// t = tanh(w_c . x + b_c) at x = xy[s][frow[s][f]] (the corner rule of the remark in
+// Section 3); columns of pad neurons (c >= nsub[s]) stay zero.
+cudaError_t launch_flux_rows(double* A, long long astride, int mfld, const int* mf, int mfmax,
+                             const int* frow, const double* fnrm, const double* xy, int m_max,
+                             const double* W, const double* b, int N, int n, const int* nsub,
+                             unsigned* status, cudaStream_t st);
 cudaError_t launch_backsolve(const double* X, const double* K, long long kstride, int ld,
                              const int* mg, const int* ifc_dof, int mgld, const double* u,
                              int n_gamma, int N, int n, int nrhs, double* c, cudaStream_t st);

@@ -51,9 +51,20 @@ struct ProfRec {
   double flops, bytes;
 };
 
+// An interface group ("edge"): a maximal run of consecutive interface unknowns held by
+// the same k subdomains s[q], at local interface rows i[q] .. i[q] + len - 1 (k = 2 inside
+// an edge, up to GRP_MAX at a cross point of the corner rule in Section 3).
 struct Edge {
-  int g0, len;
-  int s[2], i[2];  // owning subdomains and local interface-row offsets
+  int g0, len, k = 2;
+  int s[GRP_MAX], i[GRP_MAX];  // owning subdomains and local interface-row offsets
+};
+
+// A flux group: a maximal run of consecutive flux conditions (rows of the global A) carried
+// by the same two subdomains s[q], at rows i[q] .. i[q] + len - 1 of A^{s[q]}.  Without
+// explicit flux rows the flux groups are the edges.
+struct FGroup {
+  int f0, len;
+  int s[2], i[2];
 };
 
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -146,6 +157,18 @@ struct elm_ddm_handle {
   bool ridge = false;
   double ridge_alpha = 1e-14;
   std::vector<Edge> edges;
+  std::vector<FGroup> fgroups;
+  // rows of A^s (flux rows): one per interface row, or the explicit rows of
+  // elm_ddm_setup_flux; n_flux global flux conditions (internal order: the unknowns' without
+  // explicit rows, the caller's with them)
+  std::vector<int> mf_h;
+  int mfmax = 0, mfld = 0, n_flux = 0;
+  bool explicit_flux = false;
+  int* mf = nullptr;            // device copy of mf_h
+  int* fluxmap = nullptr;       // [n_flux][4]: (subdomain, row of A^s) of both rows of a condition
+  int* ffd = nullptr;           // [N][mfld]: flux condition of every row of A^s
+  int* frow = nullptr;          // [N][mfld]: collocation row of every explicit row of A^s
+  double* fnrm = nullptr;       // [N][mfld][2]: its normal
   std::vector<int> newoff;      // internal offset of each edge's first unknown
   std::vector<int> perm_h;      // caller interface unknown -> internal index
   std::vector<int> chol_rend;   // per Cholesky block step: end of the envelope rows
@@ -360,8 +383,8 @@ int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first
                                        h->T + (size_t)L.off * QR_NB * QR_NB, h->tstride,
                                        L.off * QR_NB - L.toff, h->st), nm);
     else if (L.kind == 6)
-      ELM_LAUNCH_F(h, launch_trsm_y_diag(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg,
-                                         h->mgmax, h->N, h->n, L.off, h->st), nm, L.flops);
+      ELM_LAUNCH_F(h, launch_trsm_y_diag(h->Am, h->astride, h->mfld, h->K, h->kstride, h->ld, h->mf,
+                                         h->mfmax, h->N, h->n, L.off, h->st), nm, L.flops);
     else if (L.kind == 4 && L.side) {
       cudaError_t e_;
       {
@@ -395,11 +418,17 @@ int assemble_launch(elm_ddm_handle* h) {
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble: clear A");
   if (h->nsub && (h->desc.flags & ELM_DDM_FLAG_NEURONS_PER_SUB))
     ELM_LAUNCH(h, launch_zero_pad_theta(h->thW, h->thb, h->nsub, h->N, h->n, h->st), "assemble");
-  ELM_LAUNCH_FB(h, launch_assemble(h->K, h->kstride, h->ld, h->ncap, h->Am, h->astride, h->mgld, h->xy,
-                                   h->nrm, h->m_max, h->cnt, h->thW, h->thb, h->N, h->n,
-                                   h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr,
+  // A^s: with the interface rows (one row per interface row, its normal), or from the
+  // explicit rows
+  ELM_LAUNCH_FB(h, launch_assemble(h->K, h->kstride, h->ld, h->ncap, h->explicit_flux ? nullptr : h->Am,
+                                   h->astride, h->mfld, h->xy, h->nrm, h->m_max, h->cnt, h->thW, h->thb,
+                                   h->N, h->n, h->op == ELM_DDM_OP_VARCOEF ? h->coef : nullptr,
                                    h->use_tabs ? &h->tabs : nullptr, h->status, h->st, h->nsub),
                 "assemble", 0.0, h->asm_bytes);
+  if (h->explicit_flux)
+    ELM_LAUNCH(h, launch_flux_rows(h->Am, h->astride, h->mfld, h->mf, h->mfmax, h->frow, h->fnrm, h->xy,
+                                   h->m_max, h->thW, h->thb, h->N, h->n, h->nsub, h->status, h->st),
+               "assemble");
   if (h->ridge)
     ELM_LAUNCH(h, launch_ridge_rows(h->K, h->kstride, h->ld, h->cnt, h->nsub, h->N, h->n, h->ridge_alpha, h->st),
                "assemble");
@@ -427,6 +456,12 @@ extern "C" {
 
 int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double* xy,
                   const double* nrm, const int32_t* dof, void* stream, elm_ddm_handle** out) {
+  return elm_ddm_setup_flux(desc, counts, xy, nrm, dof, nullptr, stream, out);
+}
+
+int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const double* xy,
+                       const double* nrm, const int32_t* dof, const elm_ddm_flux_rows* flux,
+                       void* stream, elm_ddm_handle** out) {
   if (!out) return fail(nullptr, ELM_DDM_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!desc || !counts || !xy || !nrm || !dof)
@@ -450,6 +485,14 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     return fail(nullptr, ELM_DDM_ERR_ARG,
                 "ELM_DDM_FLAG_MIXED needs the tensor-core back end and the direct Schur solve");
   if ((long long)N * m_max > (1ll << 31)) return fail(nullptr, ELM_DDM_ERR_ARG, "geometry too large");
+  if (flux) {
+    if (desc->flags & (ELM_DDM_FLAG_SCHUR_CG | ELM_DDM_FLAG_MIXED | ELM_DDM_FLAG_BLOCK_JACOBI))
+      return fail(nullptr, ELM_DDM_ERR_ARG,
+                  "explicit flux rows: not with ELM_DDM_FLAG_SCHUR_CG, _MIXED or _BLOCK_JACOBI");
+    if (!flux->count || !flux->row || !flux->nrm || !flux->fdof || flux->f_max < 1 || flux->n_flux < 0 ||
+        (ng > 0 && flux->n_flux < 1) || (long long)N * flux->f_max > (1ll << 31))
+      return fail(nullptr, ELM_DDM_ERR_ARG, "explicit flux rows: NULL array or bad n_flux / f_max");
+  }
 
   auto h = new elm_ddm_handle();
   h->desc = *desc;
@@ -518,17 +561,27 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
       owners[g].push_back({s, i});
     }
   }
+  const size_t kmax_own = flux ? GRP_MAX : 2;
   for (int g = 0; g < ng; ++g) {
-    if (owners[g].size() != 2 || owners[g][0].first == owners[g][1].first) {
+    std::vector<int> ss;
+    for (auto& o : owners[g]) ss.push_back(o.first);
+    std::sort(ss.begin(), ss.end());
+    if (owners[g].size() < 2 || owners[g].size() > kmax_own ||
+        std::unique(ss.begin(), ss.end()) != ss.end()) {
       delete h;
       return fail(nullptr, ELM_DDM_ERR_ARG,
-                  "interface unknown " + std::to_string(g) + " is not shared by exactly two subdomains");
+                  "interface unknown " + std::to_string(g) +
+                      (flux ? " is not shared by two to four subdomains" : " is not shared by exactly two subdomains"));
     }
+    std::sort(owners[g].begin(), owners[g].end());
   }
-  auto other = [&](int g, int s) {
-    return owners[g][0].first == s ? owners[g][1].first : owners[g][0].first;
+  auto same_owners = [&](int g1, int g2) {
+    if (owners[g1].size() != owners[g2].size()) return false;
+    for (size_t q = 0; q < owners[g1].size(); ++q)
+      if (owners[g1][q].first != owners[g2][q].first) return false;
+    return true;
   };
-  // segments: maximal runs with consecutive unknowns and the same neighbour
+  // segments: maximal runs with consecutive unknowns and the same sharing subdomains
   std::map<int, std::vector<std::array<int, 3>>> segs;  // g0 -> list of {s, i0, len}
   for (int s = 0; s < N; ++s) {
     const int r0 = h->cnt_h[3 * s] + h->cnt_h[3 * s + 1];
@@ -536,21 +589,26 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     int i = 0;
     while (i < h->mg_h[s]) {
       int j = i + 1;
-      while (j < h->mg_h[s] && d[j] == d[j - 1] + 1 && other(d[j], s) == other(d[i], s)) ++j;
+      while (j < h->mg_h[s] && d[j] == d[j - 1] + 1 && same_owners(d[j], d[i])) ++j;
       segs[d[i]].push_back({s, i, j - i});
       i = j;
     }
   }
   int covered = 0;
   for (auto& kv : segs) {
-    if (kv.second.size() != 2 || kv.second[0][2] != kv.second[1][2]) {
+    const size_t k = owners[kv.first].size();
+    bool okk = kv.second.size() == k;
+    for (size_t q = 1; okk && q < k; ++q) okk = kv.second[q][2] == kv.second[0][2];
+    if (!okk) {
       delete h;
       return fail(nullptr, ELM_DDM_ERR_ARG, "interface rows do not form matching edges");
     }
     Edge e;
     e.g0 = kv.first;
     e.len = kv.second[0][2];
-    for (int q = 0; q < 2; ++q) { e.s[q] = kv.second[q][0]; e.i[q] = kv.second[q][1]; }
+    e.k = (int)k;
+    std::sort(kv.second.begin(), kv.second.end());
+    for (size_t q = 0; q < k; ++q) { e.s[q] = kv.second[q][0]; e.i[q] = kv.second[q][1]; }
     if (e.g0 != covered) {
       delete h;
       return fail(nullptr, ELM_DDM_ERR_ARG, "interface edges overlap or leave gaps");
@@ -563,21 +621,122 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     return fail(nullptr, ELM_DDM_ERR_ARG, "interface edges do not cover all unknowns");
   }
 
+  // ---- rows of A^s and the flux conditions they belong to ----
+  // Without explicit rows: one per interface row (its point and normal), condition = its
+  // unknown.  fr_h / fd_h: per subdomain the interface-row index and condition of each row.
+  h->explicit_flux = flux != nullptr;
+  h->n_flux = flux ? flux->n_flux : ng;
+  h->mf_h.assign(N, 0);
+  std::vector<std::vector<int>> fr_h(N), fd_h(N);
+  std::vector<std::vector<double>> fn_h(N);
+  for (int s = 0; s < N; ++s) {
+    const int r0 = h->cnt_h[3 * s] + h->cnt_h[3 * s + 1];
+    if (!flux) {
+      h->mf_h[s] = h->mg_h[s];
+      for (int i = 0; i < h->mg_h[s]; ++i) {
+        fr_h[s].push_back(i);
+        fd_h[s].push_back(dof[(size_t)s * m_max + r0 + i]);
+      }
+      continue;
+    }
+    const int c = flux->count[s];
+    if (c < 0 || c > flux->f_max || (c > 0 && h->mg_h[s] == 0)) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_ARG, "flux rows of subdomain " + std::to_string(s) + ": bad count");
+    }
+    h->mf_h[s] = c;
+    for (int f = 0; f < c; ++f) {
+      const size_t q = (size_t)s * flux->f_max + f;
+      const int r = flux->row[q], cd = flux->fdof[q];
+      const double nx = flux->nrm[2 * q], ny = flux->nrm[2 * q + 1];
+      if (r < 0 || r >= h->mg_h[s] || cd < 0 || cd >= flux->n_flux) {
+        delete h;
+        return fail(nullptr, ELM_DDM_ERR_ARG, "flux rows of subdomain " + std::to_string(s) + ": row or condition out of range");
+      }
+      if (!std::isfinite(nx) || !std::isfinite(ny)) {
+        delete h;
+        return fail(nullptr, ELM_DDM_ERR_NONFINITE, "non-finite flux-row normal");
+      }
+      fr_h[s].push_back(r);
+      fd_h[s].push_back(cd);
+      fn_h[s].push_back(nx);
+      fn_h[s].push_back(ny);
+    }
+  }
+  for (int s = 0; s < N; ++s) h->mfmax = std::max(h->mfmax, h->mf_h[s]);
+  std::vector<std::vector<std::pair<int, int>>> fown(h->n_flux);
+  for (int s = 0; s < N; ++s)
+    for (int f = 0; f < h->mf_h[s]; ++f) fown[fd_h[s][f]].push_back({s, f});
+  for (int c = 0; c < h->n_flux; ++c) {
+    if (fown[c].size() != 2 || fown[c][0].first == fown[c][1].first) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_ARG,
+                  "flux condition " + std::to_string(c) + " is not carried by rows of exactly two subdomains");
+    }
+    std::sort(fown[c].begin(), fown[c].end());
+  }
+  {
+    auto partner = [&](int c, int s) { return fown[c][0].first == s ? fown[c][1].first : fown[c][0].first; };
+    std::map<int, std::vector<std::array<int, 3>>> fsegs;  // f0 -> {s, first row, len}
+    for (int s = 0; s < N; ++s) {
+      const std::vector<int>& d = fd_h[s];
+      int i = 0;
+      while (i < h->mf_h[s]) {
+        int j = i + 1;
+        while (j < h->mf_h[s] && d[j] == d[j - 1] + 1 && partner(d[j], s) == partner(d[i], s)) ++j;
+        fsegs[d[i]].push_back({s, i, j - i});
+        i = j;
+      }
+    }
+    int fcov = 0;
+    for (auto& kv : fsegs) {
+      if (kv.second.size() != 2 || kv.second[0][2] != kv.second[1][2] || kv.first != fcov) {
+        delete h;
+        return fail(nullptr, ELM_DDM_ERR_ARG, "flux rows do not form matching groups");
+      }
+      std::sort(kv.second.begin(), kv.second.end());
+      FGroup F;
+      F.f0 = kv.first;
+      F.len = kv.second[0][2];
+      for (int q = 0; q < 2; ++q) { F.s[q] = kv.second[q][0]; F.i[q] = kv.second[q][1]; }
+      fcov += F.len;
+      h->fgroups.push_back(F);
+    }
+    if (fcov != h->n_flux) {
+      delete h;
+      return fail(nullptr, ELM_DDM_ERR_ARG, "flux rows do not cover all conditions");
+    }
+  }
+
   // ---- Schur-matrix block pattern, interface ordering and Cholesky envelope ----
-  // Edges e1, e2 couple in S when some edge shares a subdomain with both (the M^T M term);
-  // that includes every pair sharing a subdomain (the D term).
-  const int ne = (int)h->edges.size();
-  std::vector<std::vector<int>> sub_edges(N), nbr(ne), spat(ne);
-  for (int e = 0; e < ne; ++e) for (int q = 0; q < 2; ++q) sub_edges[h->edges[e].s[q]].push_back(e);
+  // Edges e1, e2 couple in S when they share a subdomain (the D term) or some flux group
+  // shares a subdomain with both (the M^T M term).  nbr[e]: edges sharing a subdomain with
+  // e; fnbr[f]: edges sharing a subdomain with flux group f; efl[e]: flux groups sharing a
+  // subdomain with edge e.
+  const int ne = (int)h->edges.size(), nfg = (int)h->fgroups.size();
+  std::vector<std::vector<int>> sub_edges(N), sub_fg(N), nbr(ne), spat(ne), fnbr(nfg), efl(ne);
+  auto uniq = [](std::vector<int>& v) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  };
+  for (int e = 0; e < ne; ++e) for (int q = 0; q < h->edges[e].k; ++q) sub_edges[h->edges[e].s[q]].push_back(e);
+  for (int f = 0; f < nfg; ++f) for (int q = 0; q < 2; ++q) sub_fg[h->fgroups[f].s[q]].push_back(f);
   for (int e = 0; e < ne; ++e) {
-    for (int q = 0; q < 2; ++q) for (int e2 : sub_edges[h->edges[e].s[q]]) nbr[e].push_back(e2);
-    std::sort(nbr[e].begin(), nbr[e].end());
-    nbr[e].erase(std::unique(nbr[e].begin(), nbr[e].end()), nbr[e].end());
+    for (int q = 0; q < h->edges[e].k; ++q) {
+      for (int e2 : sub_edges[h->edges[e].s[q]]) nbr[e].push_back(e2);
+      for (int f : sub_fg[h->edges[e].s[q]]) efl[e].push_back(f);
+    }
+    uniq(nbr[e]);
+    uniq(efl[e]);
+  }
+  for (int f = 0; f < nfg; ++f) {
+    for (int q = 0; q < 2; ++q) for (int e2 : sub_edges[h->fgroups[f].s[q]]) fnbr[f].push_back(e2);
+    uniq(fnbr[f]);
   }
   for (int e1 = 0; e1 < ne; ++e1) {
-    for (int e : nbr[e1]) for (int e2 : nbr[e]) spat[e1].push_back(e2);
-    std::sort(spat[e1].begin(), spat[e1].end());
-    spat[e1].erase(std::unique(spat[e1].begin(), spat[e1].end()), spat[e1].end());
+    spat[e1] = nbr[e1];
+    for (int f : efl[e1]) for (int e2 : fnbr[f]) spat[e1].push_back(e2);
+    uniq(spat[e1]);
   }
   {
     const std::vector<int> order = rcm_order(spat);
@@ -622,14 +781,29 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->ncap = n + mgmax;
   h->nblk = (n + QR_NB - 1) / QR_NB;
   h->kstride = (long long)h->ld * h->ncap;
-  h->astride = (long long)h->mgld * n;
-  h->mstride = (long long)h->mgld * h->mgld;
+  h->mfld = round_up(std::max(h->mfmax, 1), 32);
+  h->astride = (long long)h->mfld * n;
+  h->mstride = (long long)std::max(h->mfld, h->mgld) * h->mgld;
   h->tstride = (long long)h->nblk * QR_NB * QR_NB;
   h->vstride = (long long)h->ld * QR_NBO;
   h->wstride = (long long)QR_NBO * h->ncap;
-  for (const Edge& e : h->edges) h->mdiag_elems += (size_t)e.len * e.len;
+  // M blocks that two subdomains contribute to (a flux group and an edge both subdomains
+  // of the group hold): summed once into Mdiag before the M^T M products
+  std::map<std::pair<int, int>, size_t> msum_off;
+  for (int f = 0; f < nfg; ++f)
+    for (int e : fnbr[f]) {
+      const FGroup& F = h->fgroups[f];
+      const Edge& E = h->edges[e];
+      int common = 0;
+      for (int q = 0; q < 2; ++q)
+        for (int p = 0; p < E.k; ++p) common += E.s[p] == F.s[q];
+      if (common == 2) {
+        msum_off[{f, e}] = h->mdiag_elems;
+        h->mdiag_elems += (size_t)F.len * E.len;
+      }
+    }
   for (int s = 0; s < N; ++s)
-    h->asm_bytes += 8.0 * ((double)h->ms_h[s] * (n + h->mg_h[s]) + (double)h->mg_h[s] * n);
+    h->asm_bytes += 8.0 * ((double)h->ms_h[s] * (n + h->mg_h[s]) + (double)h->mf_h[s] * n);
 
   // ---- distinct coordinates of each subdomain's rows (factored activation) ----
   std::vector<double> txs, tys, tctr(2 * (size_t)N);
@@ -718,12 +892,16 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
             dev_alloc(h, &h->nrm, (size_t)N * m_max * 2) &&
             dev_alloc(h, &h->X, (size_t)max_rhs * N * h->ld) &&
             dev_alloc(h, &h->gq, (size_t)max_rhs * N * h->mgld) &&
-            dev_alloc(h, &h->hq, (size_t)max_rhs * N * h->mgld) &&
+            dev_alloc(h, &h->hq, (size_t)max_rhs * N * h->mfld) &&
             dev_alloc(h, &h->zv, (size_t)max_rhs * N * h->mgld) &&
-            dev_alloc(h, &h->rv, (size_t)max_rhs * ng) && dev_alloc(h, &h->hv, (size_t)max_rhs * ng) &&
+            dev_alloc(h, &h->rv, (size_t)max_rhs * ng) && dev_alloc(h, &h->hv, (size_t)max_rhs * h->n_flux) &&
             dev_alloc(h, &h->yv, (size_t)max_rhs * ng) && dev_alloc(h, &h->uv, (size_t)max_rhs * ng) &&
             dev_alloc(h, &h->cnt, (size_t)N * 3) && dev_alloc(h, &h->ms, (size_t)N) &&
-            dev_alloc(h, &h->mg, (size_t)N) && dev_alloc(h, &h->dofmap, (size_t)ng * 4) &&
+            dev_alloc(h, &h->mg, (size_t)N) && dev_alloc(h, &h->dofmap, (size_t)ng * 2 * GRP_MAX) &&
+            dev_alloc(h, &h->mf, (size_t)N) && dev_alloc(h, &h->fluxmap, (size_t)h->n_flux * 4) &&
+            dev_alloc(h, &h->ffd, (size_t)N * h->mfld) &&
+            (!h->explicit_flux || (dev_alloc(h, &h->frow, (size_t)N * h->mfld) &&
+                                   dev_alloc(h, &h->fnrm, (size_t)N * h->mfld * 2))) &&
             dev_alloc(h, &h->ifc_dof, (size_t)N * h->mgld) && dev_alloc(h, &h->perm, (size_t)ng) &&
             dev_alloc(h, &h->cinv, (size_t)((ng + CHOL_NB - 1) / CHOL_NB + 1) * CHOL_NB * CHOL_NB) &&
             dev_alloc(h, &h->d_rend, h->chol_rend.size()) && dev_alloc(h, &h->d_jbeg, h->chol_jbeg.size()) &&
@@ -791,7 +969,8 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   const int mgm = std::max(mgmax, 1);
   const size_t s5 = al(oz_split_elems(mgm, n, 128) * 2), e5 = al((size_t)mgm * 4);
   const size_t s6 = al(oz_split_elems(mgm, n, 32) * 2), e6 = al((size_t)mgm * 4);
-  const size_t s7 = al(oz_split_elems(mgm, n, 128) * 2), e7 = al((size_t)mgm * 4);
+  const int mfm = std::max(h->mfmax, 1);  // Y_s rows (rows of A^s)
+  const size_t s7 = al(oz_split_elems(mfm, n, 128) * 2), e7 = al((size_t)mfm * 4);
   // Y = A R^{-1} updates: the 64-row block of R to the right of the diagonal (Y_b reuses s7)
   const size_t s8 = al(oz_split_elems(n, 64, 32) * 2), e8 = al((size_t)n * 4);
   // W2^T = W1^T T per QR panel: W1^T (rows = trailing columns) and T^T
@@ -824,18 +1003,44 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->creg_ce = ce;
 
   // ---- geometry tables ----
-  std::vector<int> dofmap((size_t)ng * 4), ifc((size_t)N * h->mgld, -1);
+  // dofmap: the (subdomain, interface row) pairs of every unknown in internal order
+  // (subdomain -1 ends a list shorter than GRP_MAX); fluxmap: the two (subdomain, A-row)
+  // pairs of every flux condition in internal order (the unknowns' order without explicit
+  // flux rows, so that h lines up with u_Gamma there)
+  std::vector<int> dofmap((size_t)ng * 2 * GRP_MAX, -1), ifc((size_t)N * h->mgld, -1);
   for (int g = 0; g < ng; ++g) {
-    auto a = owners[g][0], b = owners[g][1];
-    if (a.first > b.first) std::swap(a, b);
     const size_t gi = (size_t)h->perm_h[g];
-    dofmap[4 * gi] = a.first; dofmap[4 * gi + 1] = a.second;
-    dofmap[4 * gi + 2] = b.first; dofmap[4 * gi + 3] = b.second;
+    for (size_t q = 0; q < owners[g].size(); ++q) {
+      dofmap[2 * GRP_MAX * gi + 2 * q] = owners[g][q].first;
+      dofmap[2 * GRP_MAX * gi + 2 * q + 1] = owners[g][q].second;
+    }
   }
   for (int s = 0; s < N; ++s) {
     const int r0 = h->cnt_h[3 * s] + h->cnt_h[3 * s + 1];
     for (int i = 0; i < h->mg_h[s]; ++i)
       ifc[(size_t)s * h->mgld + i] = h->perm_h[dof[(size_t)s * m_max + r0 + i]];
+  }
+  auto fint = [&](int c) { return h->explicit_flux ? c : h->perm_h[c]; };
+  std::vector<int> fluxmap((size_t)h->n_flux * 4), ffd((size_t)N * h->mfld, 0), frow_d;
+  std::vector<double> fnrm_d;
+  for (int c = 0; c < h->n_flux; ++c)
+    for (int q = 0; q < 2; ++q) {
+      fluxmap[4 * (size_t)fint(c) + 2 * q] = fown[c][q].first;
+      fluxmap[4 * (size_t)fint(c) + 2 * q + 1] = fown[c][q].second;
+    }
+  for (int s = 0; s < N; ++s)
+    for (int f = 0; f < h->mf_h[s]; ++f) ffd[(size_t)s * h->mfld + f] = fint(fd_h[s][f]);
+  if (h->explicit_flux) {
+    frow_d.assign((size_t)N * h->mfld, 0);
+    fnrm_d.assign((size_t)N * h->mfld * 2, 0.0);
+    for (int s = 0; s < N; ++s) {
+      const int r0 = h->cnt_h[3 * s] + h->cnt_h[3 * s + 1];
+      for (int f = 0; f < h->mf_h[s]; ++f) {
+        frow_d[(size_t)s * h->mfld + f] = r0 + fr_h[s][f];
+        fnrm_d[2 * ((size_t)s * h->mfld + f)] = fn_h[s][2 * f];
+        fnrm_d[2 * ((size_t)s * h->mfld + f) + 1] = fn_h[s][2 * f + 1];
+      }
+    }
   }
 
   // ---- launch plans ----
@@ -1123,26 +1328,26 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   h->qr_first.push_back((int)h->qr_recs.size());
   // Y = A R^{-1}, blocked by 64 columns: substitution on the diagonal block of R, then the
   // columns to its right take Y_b R[b, >b] off as a digit-split product (K = 64).
-  if (h->emulated && mgmax > 0) {
+  if (h->emulated && h->mfmax > 0) {
     for (int c0 = 0; c0 < n; c0 += 64) {
       const int nbe = std::min(64, n - c0), nrest = n - c0 - nbe;
       LaunchRec D{6, c0, 1, 0, false, false, 0.0, 0.0, 0, 0.0, nbe};
-      for (int s = 0; s < N; ++s) D.flops += (double)h->mg_h[s] * nbe * nbe;
+      for (int s = 0; s < N; ++s) D.flops += (double)h->mf_h[s] * nbe * nbe;
       D.name = "trsm_y";
       h->ty_recs.push_back(D);
       if (nrest <= 0) continue;
       std::vector<SplitDesc> sp;
       std::vector<OzDesc> od;
       for (int s = 0; s < N; ++s) {
-        const int mgs = h->mg_h[s];
-        if (mgs == 0) continue;
+        const int mfs = h->mf_h[s];
+        if (mfs == 0) continue;
         double* Ys = h->Am + (size_t)s * h->astride;
         const double* Rb = h->K + (size_t)s * h->kstride + c0 + (size_t)(c0 + nbe) * ld;
         void* ty = sub_region(s, 12); int* xy = (int*)sub_region(s, 13);
         void* tr = sub_region(s, 14); int* xr = (int*)sub_region(s, 15);
-        sp.push_back({Ys + (size_t)c0 * h->mgld, 1, h->mgld, mgs, nbe, xy, ty, 128});
+        sp.push_back({Ys + (size_t)c0 * h->mfld, 1, h->mfld, mfs, nbe, xy, ty, 128});
         sp.push_back({Rb, ld, 1, nrest, nbe, xr, tr, 32});
-        od.push_back({ty, xy, tr, xr, Ys + (size_t)(c0 + nbe) * h->mgld, 1, h->mgld, mgs, nrest, nbe, 0});
+        od.push_back({ty, xy, tr, xr, Ys + (size_t)(c0 + nbe) * h->mfld, 1, h->mfld, mfs, nrest, nbe, 0});
       }
       add_split_rec(h->ty_recs, sp, "split_trsm_y");
       add_oz_rec(h->ty_recs, od, 0, -1.0, 1.0, 0, "oz_trsm_y");
@@ -1157,21 +1362,22 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     for (int s = 0; s < N; ++s) {
       const int mgs = h->mg_h[s];
       if (mgs == 0) continue;
+      const int mfs = h->mf_h[s];
       const double* QGt = h->K + (size_t)s * h->kstride + (size_t)n * ld;
       double* Ds = h->D + (size_t)s * h->mstride;
       double* Ms = h->M + (size_t)s * h->mstride;
       const double* Ys = h->Am + (size_t)s * h->astride;
       gD.push_back({QGt, QGt, Ds, mgs, mgs, n, ld, ld, h->mgld});
-      gM.push_back({Ys, QGt, Ms, mgs, mgs, n, h->mgld, ld, h->mgld});
+      if (mfs > 0) gM.push_back({Ys, QGt, Ms, mfs, mgs, n, h->mfld, ld, h->mfld});
       if (h->emulated) {
         void* t5 = sub_region(s, 8); int* x5 = (int*)sub_region(s, 9);
         void* t6 = sub_region(s, 10); int* x6 = (int*)sub_region(s, 11);
         void* t7 = sub_region(s, 12); int* x7 = (int*)sub_region(s, 13);
         sp.push_back({QGt, ld, 1, mgs, n, x5, t5, 128});   // Q_G, left operand
         sp.push_back({QGt, ld, 1, mgs, n, x6, t6, 32});    // Q_G, right operand
-        sp.push_back({Ys, 1, h->mgld, mgs, n, x7, t7, 128});  // Y_s, left operand
+        if (mfs > 0) sp.push_back({Ys, 1, h->mfld, mfs, n, x7, t7, 128});  // Y_s, left operand
         oD.push_back({t5, x5, t6, x6, Ds, 1, h->mgld, mgs, mgs, n, 0});
-        oM.push_back({t7, x7, t6, x6, Ms, 1, h->mgld, mgs, mgs, n, 0});
+        if (mfs > 0) oM.push_back({t7, x7, t6, x6, Ms, 1, h->mfld, mfs, mgs, n, 0});
       }
     }
     if (h->emulated) {
@@ -1184,34 +1390,37 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
     }
   }
   // Schur matrix (lower edge blocks, internal order): S[e1,e2] = sum of D blocks +
-  // sum_e Mblk(e,e1)^T Mblk(e,e2), each output block written once per round.  Not
-  // formed at all when the interface problem is solved by CG.
+  // sum_f Mblk(f,e1)^T Mblk(f,e2) over the flux groups f, each output block written once per
+  // round.  Not formed at all when the interface problem is solved by CG.
   if (ng > 0 && !h->cg_only) {
-    std::vector<size_t> mdoff(ne);
-    size_t acc = 0;
-    for (int e = 0; e < ne; ++e) { mdoff[e] = acc; acc += (size_t)h->edges[e].len * h->edges[e].len; }
-    auto local = [&](int e, int s) -> int {
+    auto local = [&](int e, int s) -> int {  // first interface row of edge e in subdomain s, or -1
       const Edge& E = h->edges[e];
-      return E.s[0] == s ? E.i[0] : (E.s[1] == s ? E.i[1] : -1);
+      for (int q = 0; q < E.k; ++q)
+        if (E.s[q] == s) return E.i[q];
+      return -1;
     };
-    // Mdiag[e] = M_{s0}[e,e] + M_{s1}[e,e]
+    // Mdiag[(f, e)] = M_{s0}[f, e] + M_{s1}[f, e] where both subdomains of flux group f hold
+    // edge e (without explicit flux rows: f = e)
     for (int q = 0; q < 2; ++q) {
       std::vector<AddDesc> batch;
-      for (int e = 0; e < ne; ++e) {
-        const Edge& E = h->edges[e];
-        const double* src = h->M + (size_t)E.s[q] * h->mstride + E.i[q] + (size_t)E.i[q] * h->mgld;
-        batch.push_back({src, h->Mdiag + mdoff[e], E.len, E.len, h->mgld, E.len});
+      for (const auto& kv : msum_off) {
+        const FGroup& F = h->fgroups[kv.first.first];
+        const int e = kv.first.second, s = F.s[q];
+        const double* src = h->M + (size_t)s * h->mstride + F.i[q] + (size_t)local(e, s) * h->mfld;
+        batch.push_back({src, h->Mdiag + kv.second, F.len, h->edges[e].len, h->mfld, F.len});
       }
       add_add_rec(h->s_recs, batch);
     }
-    auto mblk = [&](int e, int e2, const double** p, int* ldp) {
-      if (e == e2) { *p = h->Mdiag + mdoff[e]; *ldp = h->edges[e].len; return; }
-      const Edge& E = h->edges[e];
+    // the block of M in flux group f's rows and edge e's columns
+    auto mblk = [&](int f, int e, const double** p, int* ldp) {
+      const auto it = msum_off.find({f, e});
+      if (it != msum_off.end()) { *p = h->Mdiag + it->second; *ldp = h->fgroups[f].len; return; }
+      const FGroup& F = h->fgroups[f];
       for (int q = 0; q < 2; ++q) {
-        const int s = E.s[q], l2 = local(e2, s);
+        const int s = F.s[q], l2 = local(e, s);
         if (l2 >= 0) {
-          *p = h->M + (size_t)s * h->mstride + E.i[q] + (size_t)l2 * h->mgld;
-          *ldp = h->mgld;
+          *p = h->M + (size_t)s * h->mstride + F.i[q] + (size_t)l2 * h->mfld;
+          *ldp = h->mfld;
           return;
         }
       }
@@ -1226,7 +1435,7 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
         const Edge& E2 = h->edges[e2];
         double* dst = h->S + h->newoff[e1] + (size_t)h->newoff[e2] * ng;
         int r = 0;
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < E1.k; ++q) {
           const int s = E1.s[q], l2 = local(e2, s);
           if (l2 < 0) continue;
           if ((int)drounds.size() <= r) drounds.emplace_back();
@@ -1234,24 +1443,24 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
                                   E1.len, E2.len, h->mgld, ng});
         }
         r = 0;
-        for (int e : nbr[e1]) {
-          if (!std::binary_search(nbr[e].begin(), nbr[e].end(), e2)) continue;
+        for (int f : efl[e1]) {
+          if (!std::binary_search(fnbr[f].begin(), fnbr[f].end(), e2)) continue;
           const double *pa, *pb;
           int la, lb;
-          mblk(e, e1, &pa, &la);
-          mblk(e, e2, &pb, &lb);
+          mblk(f, e1, &pa, &la);
+          mblk(f, e2, &pb, &lb);
           if (!pa || !pb) continue;
           if ((int)mrounds.size() <= r) mrounds.emplace_back();
-          mrounds[r++].push_back({pa, pb, dst, E1.len, E2.len, h->edges[e].len, la, lb, ng});
+          mrounds[r++].push_back({pa, pb, dst, E1.len, E2.len, h->fgroups[f].len, la, lb, ng});
         }
       }
     }
     for (auto& b : drounds) add_add_rec(h->s_recs, b);
     // M^T M blocks: with the tensor-core path every distinct M block is split once (as a
     // 128-row A operand and a 32-row B operand; rows = the block's columns, K = its rows)
-    // and each round is one persistent product launch (K = edge length <= 128).
-    int maxlen = 0;
-    for (const Edge& E : h->edges) maxlen = std::max(maxlen, E.len);
+    // and each round is one persistent product launch (K = flux-group length <= 128).
+    int maxlen = 0;  // K of the M^T M products: the flux groups' rows
+    for (const FGroup& F : h->fgroups) maxlen = std::max(maxlen, F.len);
     if (h->emulated && maxlen <= 128) {
       struct MB { const double* p; int ld, rows, K; size_t ta, tb, ea, eb; };
       std::vector<MB> blocks;
@@ -1355,6 +1564,13 @@ int elm_ddm_setup(const elm_ddm_desc* desc, const int32_t* counts, const double*
   cp(h->ms, h->ms_h.data(), (size_t)N * sizeof(int));
   cp(h->mg, h->mg_h.data(), (size_t)N * sizeof(int));
   cp(h->dofmap, dofmap.data(), dofmap.size() * sizeof(int));
+  cp(h->mf, h->mf_h.data(), (size_t)N * sizeof(int));
+  cp(h->fluxmap, fluxmap.data(), fluxmap.size() * sizeof(int));
+  cp(h->ffd, ffd.data(), ffd.size() * sizeof(int));
+  if (h->explicit_flux) {
+    cp(h->frow, frow_d.data(), frow_d.size() * sizeof(int));
+    cp(h->fnrm, fnrm_d.data(), fnrm_d.size() * sizeof(double));
+  }
   cp(h->ifc_dof, ifc.data(), ifc.size() * sizeof(int));
   cp(h->perm, h->perm_h.data(), h->perm_h.size() * sizeof(int));
   cp(h->d_rend, h->chol_rend.data(), h->chol_rend.size() * sizeof(int));
@@ -1441,7 +1657,7 @@ int elm_ddm_schur(elm_ddm_handle* h) {
       rc = run_recs(h, h->ty_recs, 0, h->ty_recs.size(), "trsm_y", lo_gmax);
       if (rc) return rc;
     } else {
-      ELM_LAUNCH(h, launch_trsm_y(h->Am, h->astride, h->mgld, h->K, h->kstride, h->ld, h->mg, h->mgmax,
+      ELM_LAUNCH(h, launch_trsm_y(h->Am, h->astride, h->mfld, h->K, h->kstride, h->ld, h->mf, h->mfmax,
                                   h->N, h->n, h->st), "trsm_y");
     }
     rc = run_recs(h, h->dm_recs, 0, h->dm_recs.size(), "gemm_dm", lo_gmax);
@@ -1547,12 +1763,13 @@ int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
                                 h->st), "apply_qt");
   if (ng > 0) {
     ELM_LAUNCH(h, launch_iface_vecs(h->X, h->K, h->kstride, h->ld, h->Am, h->astride, h->mgld, h->mg,
-                                    N, n, nrhs, h->gq, h->hq, h->st), "iface_vecs");
-    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->gq, h->rv, 0, nrhs, h->st), "gather_r");
-    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->hq, h->hv, 0, nrhs, h->st), "gather_h");
-    ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, h->mgld, h->mg, h->ifc_dof, h->hv, ng, N, nrhs, h->zv,
-                              h->st), "mt_h");
-    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
+                                    h->mfld, h->mf, N, n, nrhs, h->gq, h->hq, h->st), "iface_vecs");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, h->mgld, N, h->gq, h->rv, 0, nrhs, h->st), "gather_r");
+    ELM_LAUNCH(h, launch_gather2(h->fluxmap, 2, h->n_flux, h->mfld, N, h->hq, h->hv, 0, nrhs, h->st),
+               "gather_h");
+    ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, h->mfld, h->mf, h->mg, h->ffd, h->hv, h->n_flux, N, h->mgld,
+                              nrhs, h->zv, h->st), "mt_h");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
     const int rc = chol_solves(h, nrhs);
     if (rc) return rc;
   }
@@ -1636,7 +1853,7 @@ int solve_refined(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
     if (ng > 0) {
       ELM_LAUNCH(h, launch_amul(h->A64, h->astride, mgld, h->mg, h->mgmax, n, h->cit, N, nrhs, h->Acl, h->st),
                  "refine_resid");
-      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->Acl, h->Acg, 0, nrhs, h->st), "refine_resid");
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, mgld, N, h->Acl, h->Acg, 0, nrhs, h->st), "refine_resid");
     }
     ELM_LAUNCH(h, launch_atmul(h->A64, h->astride, mgld, h->mg, h->ifc_dof, n, ng > 0 ? h->Acg : h->zero_ng, ng,
                                h->tb, -1.0, h->r1b, N, nrhs, h->r3b, h->r13b, h->st), "refine_resid");
@@ -1646,14 +1863,14 @@ int solve_refined(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
                "refine_rt");
     if (ng > 0) {
       const size_t gslot = (size_t)nrhs * N * mgld;
-      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->zb, h->rv, 0, nrhs, h->st), "gather_r");
-      ELM_LAUNCH(h, launch_iface_vecs(h->Pb, h->K, h->kstride, ld, h->Am, h->astride, mgld, h->mg, N, n, 2 * nrhs,
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, mgld, N, h->zb, h->rv, 0, nrhs, h->st), "gather_r");
+      ELM_LAUNCH(h, launch_iface_vecs(h->Pb, h->K, h->kstride, ld, h->Am, h->astride, mgld, h->mg, mgld, h->mg, N, n, 2 * nrhs,
                                       h->gq2, h->hq2, h->st), "iface_vecs");
-      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->gq2 + gslot, h->rv, 1, nrhs, h->st), "gather_r");
-      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->hq2, h->hv, 0, nrhs, h->st), "gather_h");
-      ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, mgld, h->mg, h->ifc_dof, h->hv, ng, N, nrhs, h->zv, h->st),
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, mgld, N, h->gq2 + gslot, h->rv, 1, nrhs, h->st), "gather_r");
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, mgld, N, h->hq2, h->hv, 0, nrhs, h->st), "gather_h");
+      ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, mgld, h->mg, h->mg, h->ifc_dof, h->hv, ng, N, mgld, nrhs, h->zv, h->st),
                  "mt_h");
-      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
       const int rc = chol_solves(h, nrhs);
       if (rc) return rc;
     }
@@ -1662,7 +1879,7 @@ int solve_refined(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
     if (ng > 0) {
       ELM_LAUNCH(h, launch_amul(h->A64, h->astride, mgld, h->mg, h->mgmax, n, h->dcv, N, nrhs, h->Acl, h->st),
                  "refine_resid");
-      ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, mgld, N, h->Acl, h->Acg, 0, nrhs, h->st), "refine_resid");
+      ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, mgld, N, h->Acl, h->Acg, 0, nrhs, h->st), "refine_resid");
     }
     ELM_LAUNCH(h, launch_atmul(h->A64, h->astride, mgld, h->mg, h->ifc_dof, n, ng > 0 ? h->Acg : h->zero_ng, ng,
                                h->r3b, 1.0, nullptr, N, nrhs, h->r13b, nullptr, h->st), "refine_resid");
@@ -1720,6 +1937,8 @@ static int solve_cg_impl(elm_ddm_handle* h, const double* rhs, int nrhs, const d
   if (h->state != 2) return fail(h, ELM_DDM_ERR_STATE, "solve_cg: call elm_ddm_schur first");
   if (h->lowfac)
     return fail(h, ELM_DDM_ERR_STATE, "solve_cg: the factorisation is the low-precision one (ELM_DDM_FLAG_MIXED)");
+  if (h->explicit_flux)
+    return fail(h, ELM_DDM_ERR_STATE, "solve_cg: not with explicit flux rows (elm_ddm_setup_flux)");
   if (!rhs || !c) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: NULL rhs or c");
   if (nrhs < 1 || nrhs > h->max_rhs) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: nrhs out of range");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(h, ELM_DDM_ERR_ARG, "solve_cg: tol must be > 0");
@@ -1739,12 +1958,13 @@ static int solve_cg_impl(elm_ddm_handle* h, const double* rhs, int nrhs, const d
   if (ng > 0) {
     // right-hand side of Eq. (3.5), as in elm_ddm_solve
     ELM_LAUNCH(h, launch_iface_vecs(h->X, h->K, h->kstride, h->ld, h->Am, h->astride, h->mgld, h->mg,
-                                    N, n, nrhs, h->gq, h->hq, h->st), "iface_vecs");
-    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->gq, h->rv, 0, nrhs, h->st), "gather_r");
-    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->hq, h->hv, 0, nrhs, h->st), "gather_h");
-    ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, h->mgld, h->mg, h->ifc_dof, h->hv, ng, N, nrhs, h->zv,
-                              h->st), "mt_h");
-    ELM_LAUNCH(h, launch_gather2(h->dofmap, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
+                                    h->mfld, h->mf, N, n, nrhs, h->gq, h->hq, h->st), "iface_vecs");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, h->mgld, N, h->gq, h->rv, 0, nrhs, h->st), "gather_r");
+    ELM_LAUNCH(h, launch_gather2(h->fluxmap, 2, h->n_flux, h->mfld, N, h->hq, h->hv, 0, nrhs, h->st),
+               "gather_h");
+    ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, h->mfld, h->mf, h->mg, h->ffd, h->hv, h->n_flux, N, h->mgld,
+                              nrhs, h->zv, h->st), "mt_h");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
     // CG: x in uv, r in yv; gq / hq / hv are free now and serve as the operator's scratch
     const double tol2 = tol * tol;
     const double* dinv = jacobi == 1 ? h->sdinv : nullptr;
@@ -1848,11 +2068,11 @@ int elm_ddm_export(elm_ddm_handle* h, int what, int s, double* dst, int ld_dst) 
     case ELM_DDM_BUF_K:
       src = h->K + (size_t)s * h->kstride; rows = h->ms_h[s]; cols = h->n + h->mg_h[s]; lds = h->ld; break;
     case ELM_DDM_BUF_A:
-      src = h->Am + (size_t)s * h->astride; rows = h->mg_h[s]; cols = h->n; lds = h->mgld; break;
+      src = h->Am + (size_t)s * h->astride; rows = h->mf_h[s]; cols = h->n; lds = h->mfld; break;
     case ELM_DDM_BUF_D:
       src = h->D + (size_t)s * h->mstride; rows = cols = h->mg_h[s]; lds = h->mgld; break;
     case ELM_DDM_BUF_M:
-      src = h->M + (size_t)s * h->mstride; rows = cols = h->mg_h[s]; lds = h->mgld; break;
+      src = h->M + (size_t)s * h->mstride; rows = h->mf_h[s]; cols = h->mg_h[s]; lds = h->mfld; break;
     case ELM_DDM_BUF_L:
       if (h->cg_only) return fail(h, ELM_DDM_ERR_STATE, "export: S is not formed (ELM_DDM_FLAG_SCHUR_CG)");
       src = h->S; rows = cols = h->ng; lds = h->ng; break;

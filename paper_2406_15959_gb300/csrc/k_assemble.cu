@@ -164,12 +164,43 @@ __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long l
         } else {
           v = t;
         }
-        if (r >= row0g) As[(r - row0g) + (size_t)c * mgld] = fma(wx, nx, wy * ny) * d1;
+        if (Amat && r >= row0g) As[(r - row0g) + (size_t)c * mgld] = fma(wx, nx, wy * ny) * d1;
       }
     } else if (c - n < mg) {
       v = (r == row0g + (c - n)) ? 1.0 : 0.0;
     }
     Ks[r + (size_t)c * ld] = v;
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+// Explicit A-rows (the corner rule of the remark in Section 3: one row per edge through a
+// cross point, with that edge's normal): row f of A^s sits at collocation row frow[s][f]
+// with normal fnrm[s][f]; A[f][c] = (w_c . n)(1 - t^2), t = tanh(w_c . x + b_c).  A thread
+// per (row, 8 columns), rows fastest so the column-major stores coalesce.
+__global__ void __launch_bounds__(256) k_flux_rows(double* __restrict__ A, long long astride, int mfld,
+                                                   const int* __restrict__ mf, const int* __restrict__ frow,
+                                                   const double* __restrict__ fnrm,
+                                                   const double* __restrict__ xy, int m_max,
+                                                   const double* __restrict__ W,
+                                                   const double* __restrict__ bias, int n,
+                                                   const int* __restrict__ nsub, unsigned* status) {
+  const int s = blockIdx.z;
+  const int f = blockIdx.x * 32 + threadIdx.x;
+  if (f >= mf[s]) return;
+  const int ns = nsub ? nsub[s] : n;
+  const size_t q = (size_t)s * mfld + f;
+  const int r = frow[q];
+  const double px = xy[((size_t)s * m_max + r) * 2], py = xy[((size_t)s * m_max + r) * 2 + 1];
+  const double nx = fnrm[2 * q], ny = fnrm[2 * q + 1];
+  double* As = A + (size_t)s * astride;
+  bool bad = false;
+  for (int c = blockIdx.y * 64 + threadIdx.y; c < min(ns, (int)(blockIdx.y + 1) * 64); c += 8) {
+    const double wx = W[((size_t)s * n + c) * 2], wy = W[((size_t)s * n + c) * 2 + 1];
+    const double z = fma(wx, px, fma(wy, py, bias[(size_t)s * n + c]));
+    const double t = tanh(z);
+    bad |= !isfinite(z);
+    As[f + (size_t)c * mfld] = fma(wx, nx, wy * ny) * (1.0 - t * t);
   }
   if (bad) atomicOr(status, ST_NONFINITE);
 }
@@ -336,6 +367,17 @@ cudaError_t launch_assemble(double* K, long long kstride, int ld, int ncap, doub
                                                     m_max, cnt, W, b, n, coef, AsmTables{}, status, nsub);
     count_launch();
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flux_rows(double* A, long long astride, int mfld, const int* mf, int mfmax,
+                             const int* frow, const double* fnrm, const double* xy, int m_max,
+                             const double* W, const double* b, int N, int n, const int* nsub,
+                             unsigned* status, cudaStream_t st) {
+  if (mfmax <= 0 || N <= 0) return cudaSuccess;
+  k_flux_rows<<<dim3((mfmax + 31) / 32, (n + 63) / 64, N), dim3(32, 8), 0, st>>>(
+      A, astride, mfld, mf, frow, fnrm, xy, m_max, W, b, n, nsub, status);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -298,13 +298,13 @@ cudaError_t launch_schur_apply(const double* D, const double* M, long long mstri
   const size_t smem = (size_t)mgld * sizeof(double);
   k_schur_apply1<<<dim3((mgmax + 63) / 64, N, nrhs), 256, smem, st>>>(D, M, mstride, mgld, mg, ifc_dof,
                                                                      p, ng, N, zl, wl); count_launch();
-  cudaError_t e = launch_gather2(dofmap, ng, mgld, N, wl, wg, 0, nrhs, st);
+  cudaError_t e = launch_gather2(dofmap, GRP_MAX, ng, mgld, N, wl, wg, 0, nrhs, st);
   if (e != cudaSuccess) return e;
   k_schur_apply2<<<dim3((mgmax + 15) / 16, N, nrhs), 256, smem, st>>>(M, mstride, mgld, mg, ifc_dof, wg,
                                                                      ng, N, zl); count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_gather2(dofmap, ng, mgld, N, zl, q, 0, nrhs, st);
+  return launch_gather2(dofmap, GRP_MAX, ng, mgld, N, zl, q, 0, nrhs, st);
 }
 
 cudaError_t launch_pcg_init(const double* b, const double* q, double* r, double* p, const double* dinv,

@@ -352,39 +352,41 @@ __global__ void __launch_bounds__(256) k_iface_vecs(const double* __restrict__ X
                                                     const double* __restrict__ K, long long kstride,
                                                     int ld, const double* __restrict__ Y,
                                                     long long ystride, int mgld,
-                                                    const int* __restrict__ mg_arr, int N, int n,
+                                                    const int* __restrict__ mg_arr, int mfld,
+                                                    const int* __restrict__ mf_arr, int N, int n,
                                                     double* __restrict__ gq,
                                                     double* __restrict__ hq) {
   const int s = blockIdx.x, rh = blockIdx.y;
-  const int mg = mg_arr[s];
+  const int mg = mg_arr[s], mf = mf_arr[s];
   const double* q = X + ((size_t)rh * N + s) * ld;
   const double* QGt = K + (size_t)s * kstride + (size_t)n * ld;
   const double* Ys = Y + (size_t)s * ystride;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = warp; i < mg; i += 8) {
+  for (int i = warp; i < max(mg, mf); i += 8) {
     double a = 0.0, b = 0.0;
     for (int j = lane; j < n; j += 32) {
       const double qj = q[j];
-      a = fma(QGt[j + (size_t)i * ld], qj, a);
-      b = fma(Ys[i + (size_t)j * mgld], qj, b);
+      if (i < mg) a = fma(QGt[j + (size_t)i * ld], qj, a);
+      if (i < mf) b = fma(Ys[i + (size_t)j * mfld], qj, b);
     }
     a = warp_sum(a);
     b = warp_sum(b);
     if (lane == 0) {
-      gq[((size_t)rh * N + s) * mgld + i] = a;
-      hq[((size_t)rh * N + s) * mgld + i] = b;
+      if (i < mg) gq[((size_t)rh * N + s) * mgld + i] = a;
+      if (i < mf) hq[((size_t)rh * N + s) * mfld + i] = b;
     }
   }
 }
 
-// out[g] (+)= a[s0][l0] + a[s1][l1] for every interface unknown g.
-__global__ void k_gather2(const int* __restrict__ dofmap, int n_gamma, int mgld, int N,
+// out[g] (+)= the sum of a[s][l] over the (s, l) pairs of entry g (2 to kmax of them).
+__global__ void k_gather2(const int* __restrict__ map, int kmax, int n, int ldv, int N,
                           const double* __restrict__ a, double* __restrict__ out, int accumulate) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x, rh = blockIdx.y;
-  if (g >= n_gamma) return;
-  const int s0 = dofmap[4 * g], l0 = dofmap[4 * g + 1], s1 = dofmap[4 * g + 2], l1 = dofmap[4 * g + 3];
-  const double v = a[((size_t)rh * N + s0) * mgld + l0] + a[((size_t)rh * N + s1) * mgld + l1];
-  double* o = out + (size_t)rh * n_gamma + g;
+  if (g >= n) return;
+  const int* m = map + (size_t)2 * kmax * g;
+  double v = a[((size_t)rh * N + m[0]) * ldv + m[1]] + a[((size_t)rh * N + m[2]) * ldv + m[3]];
+  for (int q = 2; q < kmax && m[2 * q] >= 0; ++q) v += a[((size_t)rh * N + m[2 * q]) * ldv + m[2 * q + 1]];
+  double* o = out + (size_t)rh * n + g;
   *o = accumulate ? *o + v : v;
 }
 
@@ -395,21 +397,22 @@ __global__ void k_gather_perm(const int* __restrict__ idx, int n, const double* 
   if (g < n) dst[(size_t)rh * n + g] = src[(size_t)rh * n + idx[g]];
 }
 
-// z_s = M_s^T (E_s h) (warp per column of M_s).
-__global__ void __launch_bounds__(256) k_mt_h(const double* __restrict__ M, long long mstride, int mgld,
+// z_s = M_s^T (P_s h) (warp per column of M_s; P_s = E_s without explicit flux rows).
+__global__ void __launch_bounds__(256) k_mt_h(const double* __restrict__ M, long long mstride, int mfld,
+                                              const int* __restrict__ mf_arr,
                                               const int* __restrict__ mg_arr,
-                                              const int* __restrict__ ifc_dof,
-                                              const double* __restrict__ h, int n_gamma, int N,
+                                              const int* __restrict__ ffd,
+                                              const double* __restrict__ h, int n_flux, int N, int mgld,
                                               double* __restrict__ z) {
   const int s = blockIdx.x, rh = blockIdx.y;
-  const int mg = mg_arr[s];
+  const int mg = mg_arr[s], mf = mf_arr[s];
   const double* Ms = M + (size_t)s * mstride;
-  const int* dofs = ifc_dof + (size_t)s * mgld;
-  const double* hh = h + (size_t)rh * n_gamma;
+  const int* fds = ffd + (size_t)s * mfld;
+  const double* hh = h + (size_t)rh * n_flux;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = warp; i < mg; i += 8) {
     double a = 0.0;
-    for (int k = lane; k < mg; k += 32) a = fma(Ms[k + (size_t)i * mgld], hh[dofs[k]], a);
+    for (int k = lane; k < mf; k += 32) a = fma(Ms[k + (size_t)i * mfld], hh[fds[k]], a);
     a = warp_sum(a);
     if (lane == 0) z[((size_t)rh * N + s) * mgld + i] = a;
   }
@@ -903,18 +906,20 @@ cudaError_t launch_apply_qt(double* X, const double* K, long long kstride, int l
 }
 
 cudaError_t launch_iface_vecs(const double* X, const double* K, long long kstride, int ld,
-                              const double* Y, long long ystride, int mgld, const int* mg,
-                              int N, int n, int nrhs, double* gq, double* hq, cudaStream_t st) {
-  k_iface_vecs<<<dim3(N, nrhs), 256, 0, st>>>(X, K, kstride, ld, Y, ystride, mgld, mg, N, n, gq,
+                              const double* Y, long long ystride, int mgld, const int* mg, int mfld,
+                              const int* mf, int N, int n, int nrhs, double* gq, double* hq,
+                              cudaStream_t st) {
+  k_iface_vecs<<<dim3(N, nrhs), 256, 0, st>>>(X, K, kstride, ld, Y, ystride, mgld, mg, mfld, mf, N, n, gq,
                                               hq); count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather2(const int* dofmap, int n_gamma, int mgld, int N, const double* a,
+cudaError_t launch_gather2(const int* map, int kmax, int n, int ldv, int N, const double* a,
                            double* out, int accumulate, int nrhs, cudaStream_t st) {
-  if (n_gamma <= 0) return cudaSuccess;
-  k_gather2<<<dim3((n_gamma + 255) / 256, nrhs), 256, 0, st>>>(dofmap, n_gamma, mgld, N, a, out,
-                                                               accumulate); count_launch();
+  if (n <= 0) return cudaSuccess;
+  if (kmax < 2) return cudaErrorInvalidValue;
+  k_gather2<<<dim3((n + 255) / 256, nrhs), 256, 0, st>>>(map, kmax, n, ldv, N, a, out,
+                                                         accumulate); count_launch();
   return cudaGetLastError();
 }
 
@@ -925,10 +930,10 @@ cudaError_t launch_gather_perm(const int* idx, int n, const double* src, double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_mt_h(const double* M, long long mstride, int mgld, const int* mg,
-                        const int* ifc_dof, const double* h, int n_gamma, int N, int nrhs,
+cudaError_t launch_mt_h(const double* M, long long mstride, int mfld, const int* mf, const int* mg,
+                        const int* ffd, const double* h, int n_flux, int N, int mgld, int nrhs,
                         double* z, cudaStream_t st) {
-  k_mt_h<<<dim3(N, nrhs), 256, 0, st>>>(M, mstride, mgld, mg, ifc_dof, h, n_gamma, N, z); count_launch();
+  k_mt_h<<<dim3(N, nrhs), 256, 0, st>>>(M, mstride, mfld, mf, mg, ffd, h, n_flux, N, mgld, z); count_launch();
   return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ ERROR_NAMES = {ERR_ARG: "ERR_ARG", ERR_STATE: "ERR_STATE", ERR_CUDA: "ERR_CUDA",
                ERR_TIMEOUT: "ERR_TIMEOUT"}
 
 # Every symbol the header declares.
-SYMBOLS = ("elm_ddm_setup", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve",
+SYMBOLS = ("elm_ddm_setup", "elm_ddm_setup_flux", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve",
            "elm_ddm_eval", "elm_ddm_export", "elm_ddm_check", "elm_ddm_get_info",
            "elm_ddm_profile", "elm_ddm_profile_report", "elm_ddm_destroy",
            "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order",
@@ -47,6 +47,12 @@ class Desc(ctypes.Structure):
     _fields_ = [("n_sub", ctypes.c_int32), ("n_neurons", ctypes.c_int32),
                 ("m_max", ctypes.c_int32), ("n_gamma", ctypes.c_int32),
                 ("op", ctypes.c_int32), ("max_rhs", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class FluxRowsDesc(ctypes.Structure):
+    """elm_ddm_flux_rows: explicit rows of A^s (cross points)."""
+    _fields_ = [("n_flux", ctypes.c_int32), ("f_max", ctypes.c_int32), ("count", ctypes.c_void_p),
+                ("row", ctypes.c_void_p), ("nrm", ctypes.c_void_p), ("fdof", ctypes.c_void_p)]
 
 
 FLAG_FP64_SIMT = 1
@@ -77,6 +83,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib = ctypes.CDLL(path)
     P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
     lib.elm_ddm_setup.argtypes = [ctypes.POINTER(Desc), P, P, P, P, P, ctypes.POINTER(P)]
+    lib.elm_ddm_setup_flux.argtypes = [ctypes.POINTER(Desc), P, P, P, P, ctypes.POINTER(FluxRowsDesc), P,
+                                       ctypes.POINTER(P)]
     lib.elm_ddm_assemble.argtypes = [P, P, P]
     lib.elm_ddm_schur.argtypes = [P]
     lib.elm_ddm_solve.argtypes = [P, P, I, P, P]
@@ -130,12 +138,17 @@ class GeometryArrays:
     nrm: np.ndarray      # float64 [N, m_max, 2]
     dof: np.ndarray      # int32 [N, m_max]
     n_gamma: int
+    flux: object = None  # workload.FluxRows (explicit A-rows at cross points) or None
 
     @classmethod
     def from_geometry(cls, g):
+        f = getattr(g, "flux", None)
+        if f is not None:
+            f = type(f)(int(f.n_flux), np.ascontiguousarray(f.count, np.int32), np.ascontiguousarray(f.row, np.int32),
+                        np.ascontiguousarray(f.nrm, np.float64), np.ascontiguousarray(f.fdof, np.int32))
         return cls(np.ascontiguousarray(g.counts, np.int32), np.ascontiguousarray(g.xy, np.float64),
                    np.ascontiguousarray(g.nrm, np.float64), np.ascontiguousarray(g.dof, np.int32),
-                   int(g.n_gamma))
+                   int(g.n_gamma), f)
 
 
 class Solver:
@@ -167,9 +180,17 @@ class Solver:
             counts = np.ascontiguousarray(np.concatenate([ga.counts, np.asarray(neurons, np.int32)[:, None]], 1),
                                           np.int32)
         self._counts_arg = counts
-        rc = self.lib.elm_ddm_setup(ctypes.byref(desc), counts.ctypes.data, ga.xy.ctypes.data,
-                                    ga.nrm.ctypes.data, ga.dof.ctypes.data,
-                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if ga.flux is None:
+            rc = self.lib.elm_ddm_setup(ctypes.byref(desc), counts.ctypes.data, ga.xy.ctypes.data,
+                                        ga.nrm.ctypes.data, ga.dof.ctypes.data,
+                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        else:
+            f = ga.flux
+            fd = FluxRowsDesc(int(f.n_flux), int(f.row.shape[1]), f.count.ctypes.data, f.row.ctypes.data,
+                              f.nrm.ctypes.data, f.fdof.ctypes.data)
+            rc = self.lib.elm_ddm_setup_flux(ctypes.byref(desc), counts.ctypes.data, ga.xy.ctypes.data,
+                                             ga.nrm.ctypes.data, ga.dof.ctypes.data, ctypes.byref(fd),
+                                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
         if rc != OK:
             raise ElmDdmError(rc, self.lib.elm_ddm_last_error(None).decode())
         self.h = h
@@ -286,10 +307,13 @@ class Solver:
         pad = self.n - ns + (ns if self.ridge is not None else 0)
         if what == BUF_K:
             return mi + mb + mg + pad, self.n + mg
+        mf = mg if self._keep.flux is None else int(self._keep.flux.count[s])   # rows of A^s
         if what == BUF_A:
-            return mg, self.n
-        if what in (BUF_D, BUF_M):
+            return mf, self.n
+        if what == BUF_D:
             return mg, mg
+        if what == BUF_M:
+            return mf, mg
         if what == BUF_L:
             return self.n_gamma, self.n_gamma
         raise ValueError(what)

@@ -133,3 +133,60 @@ def test_setup_checks_per_subdomain_neuron_counts():
         rc = lib.elm_ddm_setup(ctypes.byref(d), c4.ctypes.data, xy.ctypes.data, nrm.ctypes.data,
                                dof.ctypes.data, None, ctypes.byref(h))
         assert rc == E.ERR_ARG and msg in lib.elm_ddm_last_error(None).decode()
+
+
+# ---- explicit A-rows (elm_ddm_setup_flux; the corner rule at cross points) ----
+
+GX = wl.make_paper_grid_geometry(3, 13, cross_points=True)
+
+
+def _setup_flux(desc, g, flux):
+    lib = E.load()
+    ga = E.GeometryArrays.from_geometry(g)
+    f = flux
+    fd = E.FluxRowsDesc(int(f.n_flux), int(f.row.shape[1]), f.count.ctypes.data, f.row.ctypes.data,
+                        f.nrm.ctypes.data, f.fdof.ctypes.data)
+    h = ctypes.c_void_p()
+    rc = lib.elm_ddm_setup_flux(ctypes.byref(desc), ga.counts.ctypes.data, ga.xy.ctypes.data,
+                                ga.nrm.ctypes.data, ga.dof.ctypes.data, ctypes.byref(fd), None, ctypes.byref(h))
+    return rc, lib.elm_ddm_last_error(None).decode(), h
+
+
+def _flux_copy(g):
+    f = g.flux
+    return type(f)(f.n_flux, f.count.copy(), f.row.copy(), f.nrm.copy(), f.fdof.copy())
+
+
+def test_cross_points_need_explicit_flux_rows():
+    """Unknowns shared by four subdomains: elm_ddm_setup (one A-row per interface row)
+    rejects them before any CUDA call."""
+    c, xy, nrm, dof = _arrays(GX)
+    rc, err, h = _setup(_desc(GX, 8), c, xy, nrm, dof)
+    assert rc == E.ERR_ARG and "exactly two" in err and not h.value
+
+
+@pytest.mark.parametrize("flags", [E.FLAG_SCHUR_CG, E.FLAG_MIXED, E.FLAG_BLOCK_JACOBI])
+def test_setup_flux_rejects_the_cg_and_mixed_modes(flags):
+    rc, err, h = _setup_flux(_desc(GX, 8, flags=flags), GX, _flux_copy(GX))
+    assert rc == E.ERR_ARG and "explicit flux rows" in err and not h.value
+
+
+def test_setup_flux_rejects_bad_rows():
+    f = _flux_copy(GX)
+    f.row[4, 0] = GX.counts[4, 2]                      # past the interface rows
+    rc, err, _ = _setup_flux(_desc(GX, 8), GX, f)
+    assert rc == E.ERR_ARG and "out of range" in err
+    f = _flux_copy(GX)
+    f.fdof[4, 0] = f.fdof[4, 1]                        # one condition with three rows, one with one
+    rc, err, _ = _setup_flux(_desc(GX, 8), GX, f)
+    assert rc == E.ERR_ARG and "exactly two" in err
+    f = _flux_copy(GX)
+    k = int(f.count[0])
+    f.fdof[0, :k] = f.fdof[0, :k][::-1].copy()           # same conditions, mismatched order
+    f.row[0, :k] = f.row[0, :k][::-1].copy()
+    rc, err, _ = _setup_flux(_desc(GX, 8), GX, f)
+    assert rc == E.ERR_ARG and "matching groups" in err
+    f = _flux_copy(GX)
+    f.nrm[2, 3, 1] = np.inf
+    rc, err, _ = _setup_flux(_desc(GX, 8), GX, f)
+    assert rc == E.ERR_NONFINITE
