@@ -364,10 +364,16 @@ __global__ void __launch_bounds__(256) k_iface_vecs(const double* __restrict__ X
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = warp; i < max(mg, mf); i += 8) {
     double a = 0.0, b = 0.0;
-    for (int j = lane; j < n; j += 32) {
-      const double qj = q[j];
-      if (i < mg) a = fma(QGt[j + (size_t)i * ld], qj, a);
-      if (i < mf) b = fma(Ys[i + (size_t)j * mfld], qj, b);
+    if (i < mg && i < mf) {
+      for (int j = lane; j < n; j += 32) {
+        const double qj = q[j];
+        a = fma(QGt[j + (size_t)i * ld], qj, a);
+        b = fma(Ys[i + (size_t)j * mfld], qj, b);
+      }
+    } else if (i < mg) {
+      for (int j = lane; j < n; j += 32) a = fma(QGt[j + (size_t)i * ld], q[j], a);
+    } else {
+      for (int j = lane; j < n; j += 32) b = fma(Ys[i + (size_t)j * mfld], q[j], b);
     }
     a = warp_sum(a);
     b = warp_sum(b);

@@ -2,7 +2,7 @@
 neurons in total, the global 257 x 257 collocation grid, u = sin(2 pi x) e^y, on G x G
 subdomains, solved on the GPU through the library (FP64 path).
 
-  python -m paper_2406_15959_gb300.tables [--grids 4 8 16] [--table1]
+  python -m paper_2406_15959_gb300.tables [--grids 4 8 16] [--table1] [--no-cross-points]
 
 Table 2 rows: relative L2 and H1 errors at 100 x 100 test points against the exact
 solution, and the wall-clock of one full solve (setup, assembly, factorisation, the
@@ -16,9 +16,13 @@ weights (relative L2 errors ~3e-2 at 8 x 8), while a regularised or rank-truncat
 reaches the paper's accuracy.  Table 1 rows (--table1): the RMSE of u_Gamma against the exact
 solution at the interface points for the paper's initialisation (Eq. (4.3), c = 1/8, i.e.
 l = sqrt(n / 64)), the manual l = 1 and He's.  The paper's seeds are unknown, so the
-errors agree in order of magnitude, not digit for digit.  The cross points of the grid
-are left out (make_paper_grid_geometry); 2 x 2 and 1 x 1 need 16,384 and 65,536 neurons
-per subdomain, beyond the panel's shared memory and the back-solve's limits.
+errors agree in order of magnitude, not digit for digit.  The grid's (G - 1)^2 cross points
+are interface unknowns of their four subdomains with the corner rule of the remark in
+Section 3 (one A-row per edge through the point; make_paper_grid_geometry with
+cross_points, elm_ddm_setup_flux); --no-cross-points leaves them out, and --cg does too
+(the CG interface solve takes one flux condition per unknown).  2 x 2 and 1 x 1 need
+16,384 and 65,536 neurons per subdomain, beyond the panel's shared memory and the
+back-solve's limits.
 """
 from __future__ import annotations
 
@@ -38,9 +42,10 @@ PAPER_TABLE2 = {4: (1.6192e-08, 3.2441e-08, 19.46), 8: (2.6392e-08, 8.1948e-08, 
 PAPER_TABLE1 = {4: (7.5946e-10, 4.09e-9, 1.72e-4), 8: (2.9894e-09, 6.58e-8, 1.15e-5)}
 
 
-def run(G: int, theta: str = "paper", seed: int = 0, ridge: float | None = 1e-14, direct: bool = True):
+def run(G: int, theta: str = "paper", seed: int = 0, ridge: float | None = 1e-14, direct: bool = True,
+        cross_points: bool = True):
     import torch
-    w = wl.paper_grid_workload(G, theta=theta, seed=seed)
+    w = wl.paper_grid_workload(G, theta=theta, seed=seed, cross_points=cross_points and direct)
     dev = torch.device("cuda")
     t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), device=dev, dtype=dt)
     W, b, rhs = t(w.W), t(w.b), t(w.rhs)
@@ -77,6 +82,7 @@ def run(G: int, theta: str = "paper", seed: int = 0, ridge: float | None = 1e-14
             "local_solve": "exact least squares" if ridge is None else f"Tikhonov rows, alpha = {ridge:g}",
             "interface_solve": "direct (Cholesky)" if direct else "CG to 1e-9 (the paper's)", "cg_steps": steps,
             "rows_per_subdomain": int(geo.counts.sum(1).max()), "n_gamma": geo.n_gamma,
+            "cross_points": geo.flux is not None,
             "rel_l2": l2, "rel_h1": h1, "rmse_u_gamma": rmse, "seconds": times[-1]}
 
 
@@ -90,17 +96,20 @@ def main(argv=None):
                          "local solves the Schur system is too ill-conditioned for plain CG)")
     ap.add_argument("--ridge", type=float, default=1e-14,
                     help="alpha of the Tikhonov rows (negative: the exact local least squares)")
+    ap.add_argument("--no-cross-points", action="store_true",
+                    help="leave the grid's cross points out (no corner rule)")
     a = ap.parse_args(argv)
     ridge = None if a.ridge < 0 else a.ridge
+    cross = not a.no_cross_points
     for G in a.grids:
-        r = run(G, "paper", a.seed, ridge, not a.cg)
+        r = run(G, "paper", a.seed, ridge, not a.cg, cross)
         p = PAPER_TABLE2.get(G)
         r["paper_table2"] = {"rel_l2": p[0], "rel_h1": p[1], "seconds_cpu": p[2]} if p else None
         print(json.dumps({"table": 2, **r}), flush=True)
     if a.table1:
         for G in [g for g in a.grids if g in PAPER_TABLE1]:
             for k, theta in enumerate(("paper", "global_unit", "he")):
-                r = run(G, theta, a.seed, ridge, not a.cg)
+                r = run(G, theta, a.seed, ridge, not a.cg, cross)
                 print(json.dumps({"table": 1, **r, "paper_rmse_u_gamma": PAPER_TABLE1[G][k]}), flush=True)
 
 
