@@ -286,12 +286,12 @@ def run_ours(args):
 
     def step(Wt, bt, rt):
         s.assemble(Wt, bt)
+        s.schur()
         if cg:  # the paper's interface solve: CG to a relative residual of 1e-9
-            s.schur()
             _, _, it = s.solve_cg(rt.unsqueeze(0), tol=CG_TOL, maxit=100000, u_gamma=ug_dev, c=c_dev)
             cg_steps.append(it)
-        else:  # factorisation and solve in one call: the RHS work overlaps the Cholesky
-            s.schur_solve(rt.unsqueeze(0), ug_dev, c_dev)
+        else:
+            s.solve(rt.unsqueeze(0), ug_dev, c_dev)
         s.eval(txy, own, c_dev[0], u_dev, g_dev)
 
     from paper_2406_15959_gb300 import replicas as R

@@ -244,18 +244,6 @@ int elm_ddm_schur(elm_ddm_handle* h);
 int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c);
 
 /*
- * elm_ddm_schur followed by elm_ddm_solve, in one call (arguments and errors as theirs).
- * Because rhs is known when the factorisation is enqueued, the right-hand side's part of
- * the solve (q_s = Q_s^T F^s, the interface vectors, M^T h) runs on a second internal stream
- * as soon as the local factors are final, beside the Schur assembly and Cholesky
- * factorisation; the call's work is still ordered on the handle's stream as a whole (it
- * starts after the work enqueued before it and the outputs are complete when the stream
- * passes it).  Same results, bit for bit, as the two calls.  With ELM_DDM_FLAG_MIXED or no
- * interface it is the two calls.
- */
-int elm_ddm_schur_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c);
-
-/*
  * The paper's interface solve (Section 4: the Schur system of Eq. (3.5) by conjugate
  * gradients to a relative residual): as elm_ddm_solve, but u_Gamma comes from
  * unpreconditioned CG started at zero, with S applied from the stored local pieces,

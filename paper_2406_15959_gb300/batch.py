@@ -192,7 +192,8 @@ class BatchSolver:
             if self.coef is not None:
                 s.set_coefficient(self.coef)
             s.assemble(self.W, self.b)
-            ug, c = s.schur_solve(self.rhs)
+            s.schur()
+            ug, c = s.solve(self.rhs)
             u, _ = s.eval(self.test_xy, self.test_owner, c)
         return ug, c, u
 

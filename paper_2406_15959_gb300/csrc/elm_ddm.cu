@@ -143,11 +143,6 @@ struct elm_ddm_handle {
   size_t creg_c1 = 0, creg_c2 = 0, creg_ce = 0;
   cudaStream_t st2 = nullptr;
   cudaEvent_t evS = nullptr, evB = nullptr;
-  // elm_ddm_schur_solve: the right-hand-side work (Q^T F, the interface vectors, M^T h) runs
-  // on st3 once the local pieces are final (evQ), beside the Schur assembly and Cholesky
-  // on st, which waits for it (evR) before the triangular solves
-  cudaStream_t st3 = nullptr;
-  cudaEvent_t evQ = nullptr, evR = nullptr;
   int N = 0, n = 0, m_max = 0, ld = 0, ncap = 0, mgmax = 0, mgld = 0, ng = 0, nblk = 0;
   int max_rhs = 1;
   long long kstride = 0, astride = 0, mstride = 0, tstride = 0, vstride = 0, wstride = 0;
@@ -304,9 +299,6 @@ void free_all(elm_ddm_handle* h) {
   if (h->st2) { cudaStreamSynchronize(h->st2); cudaStreamDestroy(h->st2); h->st2 = nullptr; }
   if (h->evS) { cudaEventDestroy(h->evS); h->evS = nullptr; }
   if (h->evB) { cudaEventDestroy(h->evB); h->evB = nullptr; }
-  if (h->st3) { cudaStreamSynchronize(h->st3); cudaStreamDestroy(h->st3); h->st3 = nullptr; }
-  if (h->evQ) { cudaEventDestroy(h->evQ); h->evQ = nullptr; }
-  if (h->evR) { cudaEventDestroy(h->evR); h->evR = nullptr; }
 }
 
 cudaEvent_t next_event(elm_ddm_handle* h) {
@@ -364,16 +356,6 @@ struct ProfScope {
     if (e_ != cudaSuccess) return cuda_fail((h), e_, where); \
   } while (0)
 #define ELM_LAUNCH(h, expr, where) ELM_LAUNCH_F(h, expr, where, 0.0)
-#define ELM_LAUNCH_ON(h, stream, expr, where)                \
-  do {                                                       \
-    cudaError_t e_;                                          \
-    {                                                        \
-      ProfScope ps_((h), (where), 0.0, 0.0, (stream));       \
-      e_ = (expr);                                           \
-    }                                                        \
-    (h)->launches++;                                         \
-    if (e_ != cudaSuccess) return cuda_fail((h), e_, where); \
-  } while (0)
 
 int run_recs(elm_ddm_handle* h, const std::vector<LaunchRec>& recs, size_t first, size_t cnt,
              const char* gemm_name, int gmax = 8) {
@@ -467,9 +449,6 @@ int assemble_launch(elm_ddm_handle* h) {
 
 int solve_refined(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c);
 int chol_solves(elm_ddm_handle* h, int nrhs);
-int schur_impl(elm_ddm_handle* h, const double* fork_rhs, int fork_nrhs);
-int solve_rhs(elm_ddm_handle* h, const double* rhs, int nrhs, cudaStream_t sr);
-int solve_finish(elm_ddm_handle* h, int nrhs, double* u_gamma, double* c);
 
 }  // namespace
 
@@ -880,17 +859,11 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->evS, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->evB, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&h->st3, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->evQ, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->evR, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->evB, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       if (h->st2) cudaStreamDestroy(h->st2);
       if (h->evS) cudaEventDestroy(h->evS);
       if (h->evB) cudaEventDestroy(h->evB);
-      if (h->st3) cudaStreamDestroy(h->st3);
-      if (h->evQ) cudaEventDestroy(h->evQ);
-      if (h->evR) cudaEventDestroy(h->evR);
       delete h;
       return fail(nullptr, ELM_DDM_ERR_CUDA, "setup: second stream");
     }
@@ -1663,32 +1636,6 @@ int elm_ddm_assemble(elm_ddm_handle* h, const double* W, const double* b) {
 int elm_ddm_schur(elm_ddm_handle* h) {
   if (!h) return ELM_DDM_ERR_ARG;
   if (h->state != 1) return fail(h, ELM_DDM_ERR_STATE, "schur: call elm_ddm_assemble first");
-  return schur_impl(h, nullptr, 0);
-}
-
-int elm_ddm_schur_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c) {
-  if (!h) return ELM_DDM_ERR_ARG;
-  if (h->state != 1) return fail(h, ELM_DDM_ERR_STATE, "schur_solve: call elm_ddm_assemble first");
-  if (h->cg_only)
-    return fail(h, ELM_DDM_ERR_STATE, "schur_solve: S is not factored (ELM_DDM_FLAG_SCHUR_CG); use elm_ddm_solve_cg");
-  if (!rhs || !c) return fail(h, ELM_DDM_ERR_ARG, "schur_solve: NULL rhs or c");
-  if (nrhs < 1 || nrhs > h->max_rhs) return fail(h, ELM_DDM_ERR_ARG, "schur_solve: nrhs out of range");
-  if (h->lowfac || h->ng == 0) {  // refinement, or no interface: the two calls in sequence
-    const int rc = elm_ddm_schur(h);
-    return rc ? rc : elm_ddm_solve(h, rhs, nrhs, u_gamma, c);
-  }
-  const int rc = schur_impl(h, rhs, nrhs);
-  return rc ? rc : solve_finish(h, nrhs, u_gamma, c);
-}
-
-}  // extern "C"
-
-namespace {
-
-// Steps (b) and (c) without the right-hand side: the local QR, Y, D_s, M_s, then S and its
-// Cholesky factor.  With fork_rhs (elm_ddm_schur_solve) the right-hand side's part of the
-// solve runs on st3 as soon as the local pieces are final, and st waits for it at the end.
-int schur_impl(elm_ddm_handle* h, const double* fork_rhs, int fork_nrhs) {
   // digit groups of the local products (QR, Y, D_s, M_s): all of them, or the leading ones of
   // the low-precision factorisation; the Schur matrix's M^T M and Cholesky stay FP64
   const int lo_gmax = h->lowfac ? LO_GMAX : 8;
@@ -1715,15 +1662,6 @@ int schur_impl(elm_ddm_handle* h, const double* fork_rhs, int fork_nrhs) {
     }
     rc = run_recs(h, h->dm_recs, 0, h->dm_recs.size(), "gemm_dm", lo_gmax);
     if (rc) return rc;
-    if (fork_rhs) {  // Q^T F, the interface vectors and M^T h beside the assembly of S
-      cudaError_t e = cudaEventRecord(h->evQ, h->st);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st3, h->evQ, 0);
-      if (e != cudaSuccess) return cuda_fail(h, e, "schur_solve: fork");
-      rc = solve_rhs(h, fork_rhs, fork_nrhs, h->st3);
-      if (rc) return rc;
-      e = cudaEventRecord(h->evR, h->st3);
-      if (e != cudaSuccess) return cuda_fail(h, e, "schur_solve: fork");
-    }
     if (h->cg_only) {  // D_s and M_s are all that elm_ddm_solve_cg needs
       h->state = 2;
       return ELM_DDM_OK;
@@ -1801,55 +1739,10 @@ int schur_impl(elm_ddm_handle* h, const double* fork_rhs, int fork_nrhs) {
     }
     // inverses of the diagonal blocks for the triangular solves of the solve phase
     ELM_LAUNCH(h, launch_tri_inv(h->S, h->ng, h->ng, h->cinv, h->st), "tri_inv");
-    if (fork_rhs) {
-      const cudaError_t e = cudaStreamWaitEvent(h->st, h->evR, 0);
-      if (e != cudaSuccess) return cuda_fail(h, e, "schur_solve: join");
-    }
   }
   h->state = 2;
   return ELM_DDM_OK;
 }
-
-// The right-hand side's part of a solve, on stream sr: F into X, q_s = Q_s^T F^s, and the
-// right-hand side of Eq. (3.5) rv = sum_s E_s^T Q_G q_s + M^T h, h = sum_s P_s^T Y_s q_s.
-int solve_rhs(elm_ddm_handle* h, const double* rhs, int nrhs, cudaStream_t sr) {
-  const int N = h->N, n = h->n, ng = h->ng;
-  ELM_LAUNCH_ON(h, sr, launch_load_rhs(h->X, rhs, N, h->m_max, h->ld, h->cnt, nrhs, h->status, sr), "load_rhs");
-  ELM_LAUNCH_ON(h, sr, launch_apply_qt(h->X, h->K, h->kstride, h->ld, h->ms, N, n, h->T, h->tstride, nrhs, sr),
-                "apply_qt");
-  if (ng > 0) {
-    ELM_LAUNCH_ON(h, sr, launch_iface_vecs(h->X, h->K, h->kstride, h->ld, h->Am, h->astride, h->mgld, h->mg,
-                                           h->mfld, h->mf, N, n, nrhs, h->gq, h->hq, sr), "iface_vecs");
-    ELM_LAUNCH_ON(h, sr, launch_gather2(h->dofmap, GRP_MAX, ng, h->mgld, N, h->gq, h->rv, 0, nrhs, sr),
-                  "gather_r");
-    ELM_LAUNCH_ON(h, sr, launch_gather2(h->fluxmap, 2, h->n_flux, h->mfld, N, h->hq, h->hv, 0, nrhs, sr),
-                  "gather_h");
-    ELM_LAUNCH_ON(h, sr, launch_mt_h(h->M, h->mstride, h->mfld, h->mf, h->mg, h->ffd, h->hv, h->n_flux, N,
-                                     h->mgld, nrhs, h->zv, sr), "mt_h");
-    ELM_LAUNCH_ON(h, sr, launch_gather2(h->dofmap, GRP_MAX, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, sr),
-                  "gather_z");
-  }
-  return ELM_DDM_OK;
-}
-
-// The rest of a solve on st: u_Gamma = S^{-1} rv by the Cholesky factor, the back-solves
-// c^s = R^{-1}(q_s + Q_G^T E_s u_Gamma), u_Gamma in the caller's order.
-int solve_finish(elm_ddm_handle* h, int nrhs, double* u_gamma, double* c) {
-  const int N = h->N, n = h->n, ng = h->ng;
-  if (ng > 0) {
-    const int rc = chol_solves(h, nrhs);
-    if (rc) return rc;
-  }
-  ELM_LAUNCH(h, launch_backsolve(h->X, h->K, h->kstride, h->ld, h->mg, h->ifc_dof, h->mgld,
-                                 ng > 0 ? h->uv : h->rv, ng, N, n, nrhs, c, h->st), "backsolve");
-  if (u_gamma && ng > 0)
-    ELM_LAUNCH(h, launch_gather_perm(h->perm, ng, h->uv, u_gamma, nrhs, h->st), "gather_u");
-  return ELM_DDM_OK;
-}
-
-}  // namespace
-
-extern "C" {
 
 int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamma, double* c) {
   if (!h) return ELM_DDM_ERR_ARG;
@@ -1863,8 +1756,28 @@ int elm_ddm_solve(elm_ddm_handle* h, const double* rhs, int nrhs, double* u_gamm
     return fail(h, ELM_DDM_ERR_STATE, "solve: S is not factored (ELM_DDM_FLAG_SCHUR_CG); use elm_ddm_solve_cg");
   if (!rhs || !c) return fail(h, ELM_DDM_ERR_ARG, "solve: NULL rhs or c");
   if (nrhs < 1 || nrhs > h->max_rhs) return fail(h, ELM_DDM_ERR_ARG, "solve: nrhs out of range");
-  const int rc = solve_rhs(h, rhs, nrhs, h->st);
-  return rc ? rc : solve_finish(h, nrhs, u_gamma, c);
+  const int N = h->N, n = h->n, ng = h->ng;
+  ELM_LAUNCH(h, launch_load_rhs(h->X, rhs, N, h->m_max, h->ld, h->cnt, nrhs, h->status, h->st),
+             "load_rhs");
+  ELM_LAUNCH(h, launch_apply_qt(h->X, h->K, h->kstride, h->ld, h->ms, N, n, h->T, h->tstride, nrhs,
+                                h->st), "apply_qt");
+  if (ng > 0) {
+    ELM_LAUNCH(h, launch_iface_vecs(h->X, h->K, h->kstride, h->ld, h->Am, h->astride, h->mgld, h->mg,
+                                    h->mfld, h->mf, N, n, nrhs, h->gq, h->hq, h->st), "iface_vecs");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, h->mgld, N, h->gq, h->rv, 0, nrhs, h->st), "gather_r");
+    ELM_LAUNCH(h, launch_gather2(h->fluxmap, 2, h->n_flux, h->mfld, N, h->hq, h->hv, 0, nrhs, h->st),
+               "gather_h");
+    ELM_LAUNCH(h, launch_mt_h(h->M, h->mstride, h->mfld, h->mf, h->mg, h->ffd, h->hv, h->n_flux, N, h->mgld,
+                              nrhs, h->zv, h->st), "mt_h");
+    ELM_LAUNCH(h, launch_gather2(h->dofmap, GRP_MAX, ng, h->mgld, N, h->zv, h->rv, 1, nrhs, h->st), "gather_z");
+    const int rc = chol_solves(h, nrhs);
+    if (rc) return rc;
+  }
+  ELM_LAUNCH(h, launch_backsolve(h->X, h->K, h->kstride, h->ld, h->mg, h->ifc_dof, h->mgld,
+                                 ng > 0 ? h->uv : h->rv, ng, N, n, nrhs, c, h->st), "backsolve");
+  if (u_gamma && ng > 0)
+    ELM_LAUNCH(h, launch_gather_perm(h->perm, ng, h->uv, u_gamma, nrhs, h->st), "gather_u");
+  return ELM_DDM_OK;
 }
 
 }  // extern "C"

@@ -23,7 +23,6 @@ ERROR_NAMES = {ERR_ARG: "ERR_ARG", ERR_STATE: "ERR_STATE", ERR_CUDA: "ERR_CUDA",
 
 # Every symbol the header declares.
 SYMBOLS = ("elm_ddm_setup", "elm_ddm_setup_flux", "elm_ddm_assemble", "elm_ddm_schur", "elm_ddm_solve",
-           "elm_ddm_schur_solve",
            "elm_ddm_eval", "elm_ddm_export", "elm_ddm_check", "elm_ddm_get_info",
            "elm_ddm_profile", "elm_ddm_profile_report", "elm_ddm_destroy",
            "elm_ddm_last_error", "elm_ddm_chol_solve_noalloc", "elm_ddm_interface_order",
@@ -89,7 +88,6 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.elm_ddm_assemble.argtypes = [P, P, P]
     lib.elm_ddm_schur.argtypes = [P]
     lib.elm_ddm_solve.argtypes = [P, P, I, P, P]
-    lib.elm_ddm_schur_solve.argtypes = [P, P, I, P, P]
     lib.elm_ddm_eval.argtypes = [P, I, P, P, P, P, P]
     lib.elm_ddm_export.argtypes = [P, I, I, P, I]
     lib.elm_ddm_check.argtypes = [P]
@@ -234,7 +232,7 @@ class Solver:
     def schur(self):
         self._check_rc(self.lib.elm_ddm_schur(self.h))
 
-    def solve(self, rhs, u_gamma=None, c=None, _entry="elm_ddm_solve"):
+    def solve(self, rhs, u_gamma=None, c=None):
         """rhs: CUDA float64 [nrhs, N, m_max] or [N, m_max].  Returns (u_gamma, c)."""
         import torch
         squeeze = rhs.dim() == 2
@@ -244,16 +242,11 @@ class Solver:
             c = torch.empty((nrhs, self.N, self.n), dtype=torch.float64, device=rhs.device)
         if u_gamma is None and self.n_gamma > 0:
             u_gamma = torch.empty((nrhs, self.n_gamma), dtype=torch.float64, device=rhs.device)
-        self._check_rc(getattr(self.lib, _entry)(self.h, _ptr(r.contiguous()), nrhs,
-                                                 _ptr(u_gamma) if self.n_gamma > 0 else None, _ptr(c)))
+        self._check_rc(self.lib.elm_ddm_solve(self.h, _ptr(r.contiguous()), nrhs,
+                                              _ptr(u_gamma) if self.n_gamma > 0 else None, _ptr(c)))
         if squeeze:
             return (u_gamma[0] if u_gamma is not None else None), c[0]
         return u_gamma, c
-
-    def schur_solve(self, rhs, u_gamma=None, c=None):
-        """schur() and solve(rhs) in one call (elm_ddm_schur_solve: the right-hand side's
-        work overlaps the Schur factorisation)."""
-        return self.solve(rhs, u_gamma, c, _entry="elm_ddm_schur_solve")
 
     def solve_cg(self, rhs, tol: float = 1e-9, maxit: int = 10000, u_gamma=None, c=None,
                  require_convergence: bool = True, x0=None, jacobi=False):

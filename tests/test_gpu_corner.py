@@ -115,16 +115,6 @@ def test_corner_rule_factor_pieces_match_oracle(fp64_simt):
     s.close()
 
 
-def test_corner_rule_schur_solve_matches_the_two_calls():
-    w, res, _, _ = get("3x3_k12")
-    s = E.Solver(w.geom, w.n_neurons)
-    s.assemble(t(w.W), t(w.b))
-    ug, c = s.schur_solve(t(w.rhs))
-    s.check()
-    assert rel(ug.cpu().numpy(), res.u_gamma) <= 1e-8
-    s.close()
-
-
 def test_corner_rule_has_no_cg_interface_solve():
     w, _, _, _ = get("2x2_k16")
     s, *_ = run(w)

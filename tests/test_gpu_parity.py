@@ -288,30 +288,3 @@ def test_paper_grid_at_the_papers_size_matches_oracle(G):
     assert rel(ug.cpu().numpy(), res.u_gamma) <= 1e-8
     assert rel(u, ue) < {8: 1e-8, 16: 1e-7}[G], rel(u, ue)
     s.close()
-
-
-@pytest.mark.parametrize("fp64_simt", [False, True], ids=["tensor-core", "fp64-pipe"])
-@pytest.mark.parametrize("name", ["3x3_ragged", "5x3_edges70"])
-def test_schur_solve_equals_schur_then_solve(name, fp64_simt):
-    """elm_ddm_schur_solve (the right-hand side's work on a second stream beside the Schur
-    factorisation) gives the two calls' results bit for bit, for several right-hand sides,
-    and stays ordered after work enqueued before it on the handle's stream."""
-    w, res, _, _ = get(name)
-    rng = np.random.default_rng(3)
-    rhs = np.stack([w.rhs, w.rhs * rng.uniform(0.5, 2.0, size=w.rhs.shape)])
-    outs = []
-    for fused in (False, True):
-        s = E.Solver(w.geom, w.n_neurons, max_rhs=2, fp64_simt=fp64_simt)
-        s.assemble(t(w.W), t(w.b))
-        r = torch.zeros((2,) + w.rhs.shape, dtype=torch.float64, device=DEV)
-        r.copy_(t(rhs))                   # enqueued before the call on the same stream
-        if fused:
-            ug, c = s.schur_solve(r)
-        else:
-            s.schur()
-            ug, c = s.solve(r)
-        s.check()
-        outs.append((ug.cpu().numpy(), c.cpu().numpy()))
-        s.close()
-    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
-    assert rel(outs[1][0][0], res.u_gamma) <= 1e-8
