@@ -19,17 +19,25 @@ constexpr int NB = CHOL_NB;
 // at the end l_jj = sqrt(d_j) and l_ij = a_ij / l_jj.
 //
 // FP64 arithmetic is the scarce resource (2 FMA per clock per SM, a quarter of that for
-// the warps of one SM sub-partition, and a warp-wide FMA occupies the pipe whatever its
-// active lanes), and the pivot reciprocal is a long dependent chain.  So step j is split
-// between a look-ahead warp and the rest:
-//   warp 0:      updates column j+1 (the next pivot column), forms d_{j+1}, its
-//                reciprocal and the next multipliers t^(j+1) (double-buffered);
-//   warps 1..15: the rest of the trailing triangle (columns > j+1), flattened into one
-//                index range so every warp-wide FMA has 32 active lanes.
-// The reciprocal's latency hides behind the bulk update.  (Panels of 8 columns factored
-// by one warp in registers measured slower: the whole chain then runs on one
-// sub-partition's quarter of the FP64 pipe.)
+// the warps of one SM sub-partition), and the pivot reciprocal is a long dependent chain.
+// So step j is split between a look-ahead warp and the rest:
+//   warp 0:      makes column c = j+1 final (applies column j to it), forms d_c, its
+//                reciprocal and the multipliers t^(c) (double-buffered in shared memory);
+//                it keeps column j and t^(j) in registers (lane l: rows l and l + 32), so
+//                its chain reads shared memory once per step (the new column);
+//   warps 1..15: the trailing triangle (columns >= 2) in registers, about four entries per
+//                thread dealt round-robin over the column-major enumeration (so the active
+//                entries stay spread over all threads as the triangle shrinks); step j
+//                applies column j to the entries of columns >= j+2 and writes column j+2's
+//                entries to shared memory, where warp 0 takes it as the next look-ahead.
+// Every entry sees the same FMAs in the same order as in the plain right-looking
+// elimination.  The reciprocal's latency hides behind the bulk update.  (Panels of 8
+// columns factored by one warp in registers measured slower: the whole chain then runs on
+// one sub-partition's quarter of the FP64 pipe; two pivots per barrier too.)
 constexpr int POTRF_THREADS = 512;
+constexpr int POTRF_BULK = POTRF_THREADS - 32;
+constexpr int POTRF_E = (NB - 2) * (NB - 1) / 2;                     // entries (i, k), 2 <= k <= i < NB
+constexpr int POTRF_PER = (POTRF_E + POTRF_BULK - 1) / POTRF_BULK;   // per bulk thread
 
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict__ S, int ld, int k, int nb,
                                                               unsigned* status) {
@@ -37,55 +45,80 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(double* __restrict
   __shared__ double piv[NB], rl[NB], tcol[2][NB];  // d_j, 1/sqrt(d_j), t^(j) (by parity of j)
   __shared__ int bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int BULK = POTRF_THREADS - 32;
   for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
     const int i = e % NB, j = e / NB;
     a[i][j] = (i < nb && j < nb && i >= j) ? S[(k + i) + (size_t)(k + j) * ld] : 0.0;
   }
   if (tid == 0) bad = 0;
   __syncthreads();
-  // warp 0: pivot d_c (column c already final), its multipliers into tcol[c & 1].  A pivot
-  // that is not positive (not SPD) is flagged and replaced by 1 so the loop ends.
-  auto pivot_column = [&](int c) {
-    double rd = 0.0;
-    if (lane == 0) {
-      double d = a[c][c];
-      // positive and finite: the sign bit clear, not zero, the exponent below 2047
-      const long long db = __double_as_longlong(d);
-      if (db <= 0 || (db >> 52) >= 0x7FF) {
-        bad = 1;
-        d = 1.0;
-      }
-      piv[c] = d;
-      rd = rcp_newton(d);
+  // a pivot that is not positive (not SPD) is flagged and replaced by 1 so the loop ends
+  auto checked = [&](double d) {
+    const long long db = __double_as_longlong(d);
+    if (db <= 0 || (db >> 52) >= 0x7FF) {  // positive and finite: sign clear, not zero, exponent < 2047
+      if (lane == 0) bad = 1;
+      return 1.0;
     }
-    rd = __shfl_sync(0xffffffffu, rd, 0);
-    for (int i = c + 1 + lane; i < nb; i += 32) tcol[c & 1][i] = a[i][c] * rd;
+    return d;
   };
-  if (warp == 0 && nb > 0) pivot_column(0);
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    const double* t = tcol[j & 1];
-    const int m = nb - j - 1;
-    if (warp == 0) {
-      if (m > 0) {
-        for (int i = j + 1 + lane; i < nb; i += 32) a[i][j + 1] = fma(-t[i], a[j + 1][j], a[i][j + 1]);
-        __syncwarp();
-        pivot_column(j + 1);
-      }
-    } else {
-      // triangle of columns j+2.. (size m-1)
-      const int tri = m > 0 ? (m - 1) * m / 2 : 0;
-      for (int e = tid - 32; e < tri; e += BULK) {
-        int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-        if ((r + 1) * (r + 2) / 2 <= e) ++r;
-        if (r * (r + 1) / 2 > e) --r;
-        const int c = e - r * (r + 1) / 2;
-        const int i = j + 2 + r, kk = j + 2 + c;
-        a[i][kk] = fma(-t[i], a[kk][j], a[i][kk]);
+  if (warp == 0) {
+    const int r0 = lane, r1 = lane + 32;
+    double tj0 = 0.0, tj1 = 0.0, cj0 = 0.0, cj1 = 0.0;  // t^(j), column j at rows r0, r1
+    if (nb > 0) {  // column 0
+      cj0 = a[r0][0];
+      cj1 = a[r1][0];
+      const double d = checked(__shfl_sync(0xffffffffu, cj0, 0));
+      if (lane == 0) piv[0] = d;
+      const double rd = rcp_newton(d);
+      if (r0 > 0 && r0 < nb) { tj0 = cj0 * rd; tcol[0][r0] = tj0; }
+      if (r1 < nb) { tj1 = cj1 * rd; tcol[0][r1] = tj1; }
+    }
+    for (int j = 0; j + 1 < nb; ++j) {
+      const int c = j + 1;
+      double x0 = (r0 >= c && r0 < nb) ? a[r0][c] : 0.0;
+      double x1 = (r1 >= c && r1 < nb) ? a[r1][c] : 0.0;
+      const double acj = __shfl_sync(0xffffffffu, c < 32 ? cj0 : cj1, c & 31);
+      if (r0 >= c && r0 < nb) x0 = fma(-tj0, acj, x0);
+      if (r1 >= c && r1 < nb) x1 = fma(-tj1, acj, x1);
+      const double d = checked(__shfl_sync(0xffffffffu, c < 32 ? x0 : x1, c & 31));
+      const double rd = rcp_newton(d);
+      double* tn = tcol[c & 1];
+      if (r0 > c && r0 < nb) { tj0 = x0 * rd; tn[r0] = tj0; }
+      if (r1 > c && r1 < nb) { tj1 = x1 * rd; tn[r1] = tj1; }
+      if (r0 >= c && r0 < nb) a[r0][c] = x0;
+      if (r1 >= c && r1 < nb) a[r1][c] = x1;
+      if (lane == 0) piv[c] = d;
+      cj0 = x0;
+      cj1 = x1;
+      __syncthreads();
+    }
+  } else {
+    const int bt = tid - 32;
+    int ei[POTRF_PER], ek[POTRF_PER];
+    double v[POTRF_PER];
+#pragma unroll
+    for (int q = 0; q < POTRF_PER; ++q) {
+      const int e = bt + POTRF_BULK * q;
+      ei[q] = -1;
+      ek[q] = NB;
+      v[q] = 0.0;
+      if (e < POTRF_E) {  // column-major over k = 2 .. NB-1, rows i = k .. NB-1
+        int kk = 2, base = 0;
+        while (base + (NB - kk) <= e) { base += NB - kk; ++kk; }
+        const int i = kk + (e - base);
+        if (i < nb && kk < nb) { ei[q] = i; ek[q] = kk; v[q] = a[i][kk]; }
       }
     }
-    __syncthreads();
+    for (int j = 0; j + 1 < nb; ++j) {
+      const double* t = tcol[j & 1];
+#pragma unroll
+      for (int q = 0; q < POTRF_PER; ++q) {
+        if (ei[q] >= 0 && ek[q] >= j + 2) {
+          v[q] = fma(-t[ei[q]], a[ek[q]][j], v[q]);
+          if (ek[q] == j + 2) a[ei[q]][ek[q]] = v[q];
+        }
+      }
+      __syncthreads();
+    }
   }
   if (tid < nb) rl[tid] = 1.0 / sqrt(piv[tid]);
   __syncthreads();
