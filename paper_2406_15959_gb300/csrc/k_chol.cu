@@ -167,13 +167,16 @@ __global__ void __launch_bounds__(NB) k_tri_inv(const double* __restrict__ S, in
 // update of the row's remaining columns spread over all threads, so the FP64 pipe sees
 // independent FMAs instead of one long dependent chain.  Same operations as the
 // unblocked solve up to summation order, hence its backward stability.  TRC_ROWS rows per
-// block keep about one block per SM on the envelopes of interest.
+// block keep about one block per SM on the envelopes of interest; 256 threads spread the
+// rank-4 updates thin enough that the 4-column triangles set the pace (128 threads
+// measured 14% slower, 384 and 512 no faster).
 //
 // With split outputs (tensor-core back end) the block also writes the finished rows as
 // the SYRK's operands, so no separate split launch follows: each row's largest biased
 // exponent (the 8 threads of a row reduce it) into eA and eB, and its 7 digit planes into
 // tA (128-row tiles) and tB (32-row tiles), the layout k_split writes for K = nb.
-constexpr int TRC_ROWS = 16, TRC_THREADS = 128, TRC_BW = 4;
+constexpr int TRC_ROWS = 16, TRC_THREADS = 256, TRC_BW = 4;
+constexpr int TRC_SPLIT = TRC_ROWS * NB / 8;  // threads of the split: one per 8 entries of the rows
 __global__ void __launch_bounds__(TRC_THREADS) k_trsm_chol_rows(double* __restrict__ S, int ld, int k, int nb,
                                                                 int row_end, void* tA, void* tB, int* eA,
                                                                 int* eB) {
@@ -220,8 +223,8 @@ __global__ void __launch_bounds__(TRC_THREADS) k_trsm_chol_rows(double* __restri
     const int r = e % TRC_ROWS, j = e / TRC_ROWS;
     if (r0 + r < row_end && j < nb) S[(r0 + r) + (size_t)(k + j) * ld] = X[r][j];
   }
-  if (tA) {  // 128 threads = 16 rows x 8 groups of 8 k
-    static_assert(TRC_THREADS == TRC_ROWS * NB / 8, "one thread per 8 entries of the block's rows");
+  if (tA && t < TRC_SPLIT) {  // 128 threads = 16 rows x 8 groups of 8 k (whole warps)
+    static_assert(TRC_SPLIT <= TRC_THREADS && TRC_SPLIT % 32 == 0, "one thread per 8 entries of the block's rows");
     const int r = t >> 3, g8 = t & 7, kc = g8 >> 2, kg = g8 & 3;
     const int gr = blockIdx.x * TRC_ROWS + r;  // row of L21
     const bool valid = r0 + r < row_end;
