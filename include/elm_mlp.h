@@ -2,8 +2,9 @@
  * libelmddm: the learned interface warm start.
  *
  * A small multilayer perceptron y = W3^T g(W2^T g(W1^T x + b1) + b2) + b3 with
- * g = GELU (exact, 0.5 z (1 + erf(z / sqrt 2))), trained by the library's own FP32
- * forward, backward and Adam kernels.  It maps the coefficients of a source term to the
+ * g = GELU (exact, 0.5 z (1 + erf(z / sqrt 2))), trained by the library's own forward,
+ * backward and Adam kernels: FP32 parameters and activations, the layers' products on the
+ * tensor cores at FP32 accuracy (three TF32 products of a hi/lo split of each operand).  It maps the coefficients of a source term to the
  * interface variable u_Gamma of the Schur system of Eq. (3.5), whose prediction starts
  * the conjugate-gradient interface solve (elm_ddm_solve_pcg).  The paper has no
  * counterpart: it is an extension of its iterative interface solve (Section 4).
@@ -43,6 +44,9 @@ int elm_mlp_gradient(elm_mlp* m, const float* x, const float* target, int batch,
  * batch; loss (device scalar, may be NULL) receives the loss before the update. */
 int elm_mlp_train_step(elm_mlp* m, const float* x, const float* target, int batch, float lr,
                        float* loss);
+/* Synchronises the stream; ELM_DDM_ERR_TIMEOUT when a bounded wait of a GEMM kernel gave up
+ * since the previous check (the affected outputs are not valid), else ELM_DDM_OK. */
+int elm_mlp_check(elm_mlp* m);
 int elm_mlp_destroy(elm_mlp* m);
 const char* elm_mlp_last_error(const elm_mlp* m);
 

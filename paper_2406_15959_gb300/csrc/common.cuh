@@ -120,6 +120,16 @@ cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned*
 // inside the kernel: B row j at Bt + j * a_rs with exponent bound Be[j], or, for j < lead,
 // at At2 + j * a_rs with Ae2[j].  One CTA per nbc (32 or 64) rows of B (max_tiles = the
 // most tiles).
+// FP32 C (M x N, row-major, ldc) = op(A) op(B) on the tensor cores at FP32 accuracy (three
+// TF32 products of a hi/lo split, k_ozaki.cu), with the warm-start network's epilogues:
+// epi 0: C = AB; 1: Z = AB + bias, C = gelu(Z); 2: C = AB + bias; 3: C = AB * gelu'(Z).
+// op(A): element (i, k) at A[i a_rs + k a_ks]; op(B): element (k, j) at B[j b_ns + k b_ks].
+// work: 16-byte aligned device scratch of tf32x3_work_floats(M, N, K) floats (the split planes).
+size_t tf32x3_work_floats(int M, int N, int K);
+cudaError_t launch_tf32x3_gemm(int M, int N, int K, const float* A, long long a_rs, long long a_ks,
+                               const float* B, long long b_ns, long long b_ks, float* C, int ldc, int epi,
+                               const float* bias, float* Z, int ldz, float* work, size_t work_floats,
+                               unsigned* status, cudaStream_t st);
 cudaError_t launch_ozaki_fb(const OzDesc* d, int count, int max_tiles, unsigned* status,
                             cudaStream_t st, int gmax = 8, int nbc = 32);
 cudaError_t launch_gemm(bool ta, bool tb, const GemmDesc* d, int count, int max_tiles,

@@ -1,12 +1,13 @@
 // The learned interface warm start (include/elm_mlp.h): an MLP with GELU activations,
-// trained by FP32 kernels of our own (tiled GEMM with fused epilogues, column sums, a
-// deterministic MSE reduction, Adam).  Sizes are small (64 -> 512 -> 512 -> n_Gamma,
-// batches of a few hundred), so a 64x64-tile SIMT GEMM on the FP32 pipe (~70 TFLOP/s)
-// keeps an epoch at tens of milliseconds.
+// trained by kernels of our own: the layers' GEMMs with their fused epilogues on the tensor
+// cores at FP32 accuracy (three TF32 products of a hi/lo split, launch_tf32x3_gemm in
+// k_ozaki.cu), column sums, a deterministic MSE reduction, Adam.  Sizes are small
+// (64 -> 512 -> 512 -> n_Gamma, batches of a few hundred).
 #include "elm_ddm.h"
 #include "elm_mlp.h"
 #include "common.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <random>
 #include <string>
@@ -15,90 +16,6 @@
 namespace elmddm {
 
 namespace {
-
-constexpr int GT = 64;  // output tile
-constexpr int GK = 16;  // k step
-
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
-}
-
-// C (M x N) = op(A) op(B) with a fused epilogue; row-major, op(A) M x K, op(B) K x N.
-//   EPI 0: C = AB           EPI 1: Z = AB + bias, C = gelu(Z)
-//   EPI 2: C = AB + bias    EPI 3: C = AB * gelu'(Z)
-template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda,
-                                               const float* __restrict__ B, int ldb, float* __restrict__ C,
-                                               int ldc, const float* __restrict__ bias, float* __restrict__ Z,
-                                               int ldz) {
-  __shared__ float As[GK][GT + 4];
-  __shared__ float Bs[GK][GT + 4];
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
-  float acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += GK) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = t + 256 * q;
-      int i, k;
-      if (TA) { i = e & 63; k = e >> 6; } else { k = e & 15; i = e >> 4; }
-      const int gi = i0 + i, gk = k0 + k;
-      float v = 0.f;
-      if (gi < M && gk < K) v = TA ? A[(size_t)gk * lda + gi] : A[(size_t)gi * lda + gk];
-      As[k][i] = v;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = t + 256 * q;
-      int j, k;
-      if (TB) { k = e & 15; j = e >> 4; } else { j = e & 63; k = e >> 6; }
-      const int gj = j0 + j, gk = k0 + k;
-      float v = 0.f;
-      if (gj < N && gk < K) v = TB ? B[(size_t)gj * ldb + gk] : B[(size_t)gk * ldb + gj];
-      Bs[k][j] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < GK; ++k) {
-      float av[4], bv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[k][ty + 16 * a];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[k][tx + 16 * b];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int gi = i0 + ty + 16 * a;
-    if (gi >= M) continue;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int gj = j0 + tx + 16 * b;
-      if (gj >= N) continue;
-      float v = acc[a][b];
-      if (EPI == 1) {
-        v += bias[gj];
-        Z[(size_t)gi * ldz + gj] = v;
-        v = gelu(v);
-      } else if (EPI == 2) {
-        v += bias[gj];
-      } else if (EPI == 3) {
-        v *= gelu_grad(Z[(size_t)gi * ldz + gj]);
-      }
-      C[(size_t)gi * ldc + gj] = v;
-    }
-  }
-}
 
 // db[j] = sum_i D[i][j] (D rows x cols, row-major): one thread per column, fixed order.
 __global__ void k_colsum(const float* __restrict__ D, int rows, int cols, float* __restrict__ db) {
@@ -150,13 +67,6 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
   }
 }
 
-template <bool TA, bool TB, int EPI>
-void sgemm(cudaStream_t st, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
-           int ldc, const float* bias = nullptr, float* Z = nullptr, int ldz = 0) {
-  dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
-  k_sgemm<TA, TB, EPI><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, ldz); count_launch();
-}
-
 constexpr int MSE_BLOCKS = 256;
 
 }  // namespace
@@ -171,6 +81,9 @@ struct elm_mlp {
   float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
   float *z1 = nullptr, *a1 = nullptr, *z2 = nullptr, *a2 = nullptr, *y = nullptr;
   float *dy = nullptr, *d2 = nullptr, *d1 = nullptr, *part = nullptr, *loss = nullptr;
+  float* work = nullptr;        // split planes of the tensor-core GEMMs
+  size_t work_floats = 0;
+  unsigned* status = nullptr;   // bounded waits of the GEMM kernels (ST_TIMEOUT)
   int step = 0;
   std::vector<void*> allocs;
   std::string err;
@@ -204,15 +117,35 @@ int check_launch(elm_mlp* m, const char* where) {
   return ELM_DDM_OK;
 }
 
+// C (M x N, row-major) = op(A) op(B) with the layer epilogue epi: A, B row-major with leading
+// dimensions lda, ldb, transposed when ta / tb (op(A) M x K, op(B) K x N).
+cudaError_t gemm(elm_mlp* m, bool ta, bool tb, int epi, int M, int N, int K, const float* A, int lda,
+                 const float* B, int ldb, float* C, int ldc, const float* bias = nullptr, float* Z = nullptr,
+                 int ldz = 0) {
+  return launch_tf32x3_gemm(M, N, K, A, ta ? 1 : lda, ta ? lda : 1, B, tb ? ldb : 1, tb ? 1 : ldb, C, ldc, epi,
+                            bias, Z, ldz, m->work, m->work_floats, m->status, m->st);
+}
+
+// the largest split workspace of the layers' GEMMs at batch size B
+size_t gemm_work(int din, int dh, int dout, int B) {
+  const int shapes[8][3] = {{B, dh, din}, {B, dh, dh}, {B, dout, dh}, {dh, dout, B},
+                            {B, dh, dout}, {dh, dh, B}, {B, dh, dh}, {din, dh, B}};
+  size_t w = 0;
+  for (const auto& sh : shapes) w = std::max(w, tf32x3_work_floats(sh[0], sh[1], sh[2]));
+  return w;
+}
+
 // forward through the three layers; keeps z1, a1, z2, a2 for the backward pass
-void forward(elm_mlp* m, const float* x, int B, float* y) {
-  sgemm<false, false, 1>(m->st, B, m->dh, m->din, x, m->din, m->W1, m->dh, m->a1, m->dh, m->b1, m->z1, m->dh);
-  sgemm<false, false, 1>(m->st, B, m->dh, m->dh, m->a1, m->dh, m->W2, m->dh, m->a2, m->dh, m->b2, m->z2, m->dh);
-  sgemm<false, false, 2>(m->st, B, m->dout, m->dh, m->a2, m->dh, m->W3, m->dout, y, m->dout, m->b3);
+cudaError_t forward(elm_mlp* m, const float* x, int B, float* y) {
+  cudaError_t e = gemm(m, false, false, 1, B, m->dh, m->din, x, m->din, m->W1, m->dh, m->a1, m->dh, m->b1, m->z1, m->dh);
+  if (e == cudaSuccess)
+    e = gemm(m, false, false, 1, B, m->dh, m->dh, m->a1, m->dh, m->W2, m->dh, m->a2, m->dh, m->b2, m->z2, m->dh);
+  if (e == cudaSuccess) e = gemm(m, false, false, 2, B, m->dout, m->dh, m->a2, m->dh, m->W3, m->dout, y, m->dout, m->b3);
+  return e;
 }
 
 // loss and gradients of the MSE with respect to every parameter (into m->grads)
-void backward(elm_mlp* m, const float* x, const float* t, int B) {
+cudaError_t backward(elm_mlp* m, const float* x, const float* t, int B) {
   const long long n = (long long)B * m->dout;
   k_mse<<<MSE_BLOCKS, 256, 0, m->st>>>(m->y, t, n, m->dy, m->part); count_launch();
   k_sum_parts<<<1, 32, 0, m->st>>>(m->part, MSE_BLOCKS, m->loss); count_launch();
@@ -223,16 +156,19 @@ void backward(elm_mlp* m, const float* x, const float* t, int B) {
   float* gW3 = gb2 + m->dh;
   float* gb3 = gW3 + (size_t)m->dh * m->dout;
   // layer 3: dW3 = a2^T dy, db3 = colsum(dy), d2 = (dy W3^T) * g'(z2)
-  sgemm<true, false, 0>(m->st, m->dh, m->dout, B, m->a2, m->dh, m->dy, m->dout, gW3, m->dout);
+  cudaError_t e = gemm(m, true, false, 0, m->dh, m->dout, B, m->a2, m->dh, m->dy, m->dout, gW3, m->dout);
   k_colsum<<<(m->dout + 255) / 256, 256, 0, m->st>>>(m->dy, B, m->dout, gb3); count_launch();
-  sgemm<false, true, 3>(m->st, B, m->dh, m->dout, m->dy, m->dout, m->W3, m->dout, m->d2, m->dh, nullptr, m->z2, m->dh);
+  if (e == cudaSuccess)
+    e = gemm(m, false, true, 3, B, m->dh, m->dout, m->dy, m->dout, m->W3, m->dout, m->d2, m->dh, nullptr, m->z2, m->dh);
   // layer 2
-  sgemm<true, false, 0>(m->st, m->dh, m->dh, B, m->a1, m->dh, m->d2, m->dh, gW2, m->dh);
+  if (e == cudaSuccess) e = gemm(m, true, false, 0, m->dh, m->dh, B, m->a1, m->dh, m->d2, m->dh, gW2, m->dh);
   k_colsum<<<(m->dh + 255) / 256, 256, 0, m->st>>>(m->d2, B, m->dh, gb2); count_launch();
-  sgemm<false, true, 3>(m->st, B, m->dh, m->dh, m->d2, m->dh, m->W2, m->dh, m->d1, m->dh, nullptr, m->z1, m->dh);
+  if (e == cudaSuccess)
+    e = gemm(m, false, true, 3, B, m->dh, m->dh, m->d2, m->dh, m->W2, m->dh, m->d1, m->dh, nullptr, m->z1, m->dh);
   // layer 1
-  sgemm<true, false, 0>(m->st, m->din, m->dh, B, x, m->din, m->d1, m->dh, gW1, m->dh);
+  if (e == cudaSuccess) e = gemm(m, true, false, 0, m->din, m->dh, B, x, m->din, m->d1, m->dh, gW1, m->dh);
   k_colsum<<<(m->dh + 255) / 256, 256, 0, m->st>>>(m->d1, B, m->dh, gb1); count_launch();
+  return e;
 }
 
 }  // namespace
@@ -256,6 +192,8 @@ int elm_mlp_create(int d_in, int d_hidden, int d_out, int max_batch, uint64_t se
             malloc_f(m, &m->z2, hb) && malloc_f(m, &m->a2, hb) && malloc_f(m, &m->y, ob) &&
             malloc_f(m, &m->dy, ob) && malloc_f(m, &m->d2, hb) && malloc_f(m, &m->d1, hb) &&
             malloc_f(m, &m->part, MSE_BLOCKS) && malloc_f(m, &m->loss, 1);
+  m->work_floats = gemm_work(d_in, d_hidden, d_out, max_batch);
+  ok = ok && malloc_f(m, &m->work, m->work_floats) && malloc_f(m, reinterpret_cast<float**>(&m->status), 1);
   if (!ok) {
     for (void* p : m->allocs) cudaFree(p);
     delete m;
@@ -281,6 +219,7 @@ int elm_mlp_create(int d_in, int d_hidden, int d_out, int max_batch, uint64_t se
   cudaError_t e = cudaMemcpy(m->params, h.data(), m->np * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->am, 0, m->np * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->av, 0, m->np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
     for (void* p : m->allocs) cudaFree(p);
     delete m;
@@ -314,7 +253,8 @@ int elm_mlp_forward(elm_mlp* m, const float* x, int batch, float* y) {
   if (!m) return ELM_DDM_ERR_ARG;
   if (!x || !y) return mfail(m, ELM_DDM_ERR_ARG, "forward: NULL pointer");
   if (batch < 1 || batch > m->max_batch) return mfail(m, ELM_DDM_ERR_ARG, "forward: batch out of range");
-  forward(m, x, batch, y);
+  const cudaError_t e = forward(m, x, batch, y);
+  if (e != cudaSuccess) return mfail(m, ELM_DDM_ERR_CUDA, std::string("forward: ") + cudaGetErrorString(e));
   return check_launch(m, "forward");
 }
 
@@ -322,9 +262,9 @@ int elm_mlp_gradient(elm_mlp* m, const float* x, const float* target, int batch,
   if (!m) return ELM_DDM_ERR_ARG;
   if (!x || !target) return mfail(m, ELM_DDM_ERR_ARG, "gradient: NULL pointer");
   if (batch < 1 || batch > m->max_batch) return mfail(m, ELM_DDM_ERR_ARG, "gradient: batch out of range");
-  forward(m, x, batch, m->y);
-  backward(m, x, target, batch);
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = forward(m, x, batch, m->y);
+  if (e == cudaSuccess) e = backward(m, x, target, batch);
+  if (e != cudaSuccess) return mfail(m, ELM_DDM_ERR_CUDA, std::string("gradient: ") + cudaGetErrorString(e));
   if (loss) e = cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, m->st);
   if (e == cudaSuccess && grad)
     e = cudaMemcpyAsync(grad, m->grads, m->np * sizeof(float), cudaMemcpyDeviceToDevice, m->st);
@@ -343,6 +283,17 @@ int elm_mlp_train_step(elm_mlp* m, const float* x, const float* target, int batc
   const int blocks = (int)std::min<int64_t>((m->np + 255) / 256, 4096);
   k_adam<<<blocks, 256, 0, m->st>>>(m->params, m->grads, m->am, m->av, m->np, lr_t, b1, b2, 1e-8f); count_launch();
   return check_launch(m, "train_step");
+}
+
+int elm_mlp_check(elm_mlp* m) {
+  if (!m) return ELM_DDM_ERR_ARG;
+  unsigned st = 0;
+  cudaError_t e = cudaStreamSynchronize(m->st);
+  if (e == cudaSuccess) e = cudaMemcpy(&st, m->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && st) e = cudaMemset(m->status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return mfail(m, ELM_DDM_ERR_CUDA, cudaGetErrorString(e));
+  if (st) return mfail(m, ELM_DDM_ERR_TIMEOUT, "a tensor-core GEMM wait gave up (its results are not valid)");
+  return ELM_DDM_OK;
 }
 
 int elm_mlp_destroy(elm_mlp* m) {

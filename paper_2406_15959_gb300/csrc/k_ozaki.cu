@@ -524,6 +524,208 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki(const OzDesc* __restric
 
 
 // ---------------------------------------------------------------------------------------
+// FP32 GEMM on the tensor cores at FP32 accuracy (the warm-start network's layers):
+// C = op(A) op(B) as three TF32 products of a hi/lo split of both operands, x = hi + lo with
+// hi the TF32 value nearest x (sign, exponent, 10 mantissa bits) and lo = x - hi (exact in
+// FP32, |lo| <= 2^-11 |hi|):  A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi.  The dropped A_lo B_lo
+// and the TF32 reading of lo leave a relative error of about 2^-21 per product term, against
+// 2^-24 for an FP32 FMA chain.  k_tf32_split writes both planes of an operand in the tcgen05
+// K-major no-swizzle canonical layout (the digit planes' byte geometry: 16 floats of K per
+// 64-byte row segment, tiles [row tile][k chunk]); k_tf32x3 computes one 128 x 64 tile of C
+// per CTA: warp 0 streams the stages of both operands (4-deep ring) with cp.async.bulk, one
+// thread of warp 1 issues the 6 MMAs (kind::tf32, 128 x 64 x 8) of each 16-wide K chunk into
+// one TMEM accumulator, and warps 2..5 read it back (a row per thread) and apply the
+// layer's epilogue: C = AB; Z = AB + bias, C = gelu(Z); C = AB + bias; C = AB gelu'(Z).
+constexpr int TF_KC = 16;                       // floats of K per stage
+constexpr int TF_M = 128, TF_N = 64;
+constexpr int TF_PA = TF_M * TF_KC;             // floats of one plane of an A stage
+constexpr int TF_PB = TF_N * TF_KC;
+constexpr int TF_A = 2 * TF_PA * 4;             // bytes of the A stage (hi, lo): 16 KB
+constexpr int TF_B = 2 * TF_PB * 4;             // 8 KB
+constexpr int TF_STAGE = TF_A + TF_B;
+constexpr int TF_NS = 4;
+constexpr int TF_BAR = TF_NS * TF_STAGE;        // FULL[4] EMPTY[4] TFULL
+constexpr int TF_SLOT = TF_BAR + 80;
+constexpr int TF_FLAG = TF_SLOT + 16;
+constexpr int TF_SMEM = TF_FLAG + 16 + 1024;
+static_assert(TF_SMEM <= 227 * 1024, "TF32 product exceeds the shared memory of one CTA");
+
+// Float offset of (r, k) in an R x 16 tile: [r/8][k/4][r%8][k%4] (8 x 16-byte core matrices).
+__device__ __forceinline__ int tf_off(int r, int k) {
+  return (((r >> 3) * 4 + (k >> 2)) << 5) + ((r & 7) << 2) + (k & 3);
+}
+// kind::tf32 instruction descriptor: FP32 accumulator, TF32 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+struct TfSplit {
+  const float* X;
+  long long rs, ks;  // element (r, k) at X[r * rs + k * ks]
+  int R, K, TR;      // rows, K, rows per tile
+  float* tiles;
+};
+
+// One block per (row tile, 16-wide K chunk) of each of the two operands (blockIdx.y).
+__global__ void __launch_bounds__(256) k_tf32_split(const TfSplit a, const TfSplit b) {
+  const TfSplit d = blockIdx.y == 0 ? a : b;
+  const int nkc = (d.K + TF_KC - 1) / TF_KC, ntr = (d.R + d.TR - 1) / d.TR;
+  if ((int)blockIdx.x >= ntr * nkc) return;
+  const int rt = blockIdx.x / nkc, kc = blockIdx.x % nkc;
+  float* hi = d.tiles + (size_t)(rt * nkc + kc) * 2 * d.TR * TF_KC;
+  float* lo = hi + (size_t)d.TR * TF_KC;
+  for (int it = threadIdx.x; it < 4 * d.TR; it += blockDim.x) {
+    int r, kg;  // row, 4-wide k group; consecutive threads along the operand's contiguous index
+    if (d.ks == 1) { r = it >> 2; kg = it & 3; } else { r = it % d.TR; kg = it / d.TR; }
+    const int gr = rt * d.TR + r;
+    float h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = kc * TF_KC + kg * 4 + j;
+      const float x = (gr < d.R && k < d.K) ? d.X[(long long)gr * d.rs + (long long)k * d.ks] : 0.0f;
+      h[j] = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);  // nearest TF32 (ties up)
+      l[j] = x - h[j];
+    }
+    const int off = tf_off(r, kg * 4);
+    *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+struct TfGemm {
+  const float *At, *Bt;  // split planes of op(A) (M x K, 128-row tiles) and op(B)^T (N x K, 64-row tiles)
+  float* C;
+  int ldc, M, N, K;
+  const float* bias;
+  float* Z;
+  int ldz;
+};
+
+__device__ __forceinline__ float tf_gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float tf_gelu_grad(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(192, 1) k_tf32x3(const TfGemm g, unsigned* status) {
+  const int tiles_m = (g.M + TF_M - 1) / TF_M;
+  const int bi = blockIdx.x % tiles_m, bj = blockIdx.x / tiles_m;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t FULL = sbase + TF_BAR, EMPTY = FULL + 8 * TF_NS, TFULL = EMPTY + 8 * TF_NS;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + TF_SLOT);
+  volatile int* abort_flag = reinterpret_cast<int*>(smem + TF_FLAG);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nkc = (g.K + TF_KC - 1) / TF_KC;
+  if (tid == 0) {
+    for (int i = 0; i < TF_NS; ++i) {
+      mbar_init(FULL + 8 * i, 1);
+      mbar_init(EMPTY + 8 * i, 1);
+    }
+    mbar_init(TFULL, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(TF_N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *slot;
+
+  if (warp == 0) {
+    // ---------------- producer: one stage (both planes of both operands) per K chunk
+    if (lane == 0) {
+      int issued = 0;
+      for (int kc = 0; kc < nkc && !*abort_flag; ++kc) {
+        const int s = kc % TF_NS, use = kc / TF_NS;
+        if (!mbar_wait(EMPTY + 8 * s, (use & 1) ^ 1)) { *abort_flag = 1; break; }
+        mbar_expect_tx(FULL + 8 * s, TF_STAGE);
+        const uint32_t dst = sbase + s * TF_STAGE;
+        bulk_g2s(dst, g.At + (size_t)(bi * nkc + kc) * 2 * TF_PA, TF_A, FULL + 8 * s);
+        bulk_g2s(dst + TF_A, g.Bt + (size_t)(bj * nkc + kc) * 2 * TF_PB, TF_B, FULL + 8 * s);
+        issued = kc + 1;
+      }
+      // never leave copies in flight: wait (bounded) for the last issued stages to land
+      for (int kc = (issued > TF_NS ? issued - TF_NS : 0); kc < issued; ++kc)
+        mbar_wait(FULL + 8 * (kc % TF_NS), (kc / TF_NS) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(TF_M, TF_N);
+      for (int kc = 0; kc < nkc && !*abort_flag; ++kc) {
+        const int s = kc % TF_NS, use = kc / TF_NS;
+        if (!mbar_wait(FULL + 8 * s, use & 1)) { *abort_flag = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t ahi = sbase + s * TF_STAGE, alo = ahi + TF_PA * 4;
+        const uint32_t bhi = ahi + TF_A, blo = bhi + TF_PB * 4;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {  // two 8-wide k-steps: 2 core matrices (32 bytes) each
+          const uint64_t ah = sdesc(ahi + t * 256, 128, 512), al = sdesc(alo + t * 256, 128, 512);
+          const uint64_t bh = sdesc(bhi + t * 256, 128, 512), bl = sdesc(blo + t * 256, 128, 512);
+          mma_tf32(tmem, ah, bh, idesc, (kc > 0 || t > 0) ? 1u : 0u);
+          mma_tf32(tmem, ah, bl, idesc, 1u);
+          mma_tf32(tmem, al, bh, idesc, 1u);
+        }
+        mma_commit(EMPTY + 8 * s);  // stage s may be refilled
+      }
+      mma_commit(TFULL);
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 own TMEM lanes 32*(warp%4) .. (rows of the tile)
+    const int quarter = warp & 3, row = quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int gi = bi * TF_M + row;
+    if (!mbar_wait_warp(TFULL, 0)) {
+      *abort_flag = 1;
+    } else if (!*abort_flag) {  // warp-uniform (the flag is read after the barrier completed)
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll 1
+      for (int cb = 0; cb < TF_N / 8; ++cb) {
+        uint32_t v[8];
+        tmem_ld8(lane_base + cb * 8, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int gj = bj * TF_N + cb * 8 + j;
+          if (gi >= g.M || gj >= g.N) continue;
+          float x = __uint_as_float(v[j]);
+          if (EPI == 1) {
+            x += g.bias[gj];
+            g.Z[(size_t)gi * g.ldz + gj] = x;
+            x = tf_gelu(x);
+          } else if (EPI == 2) {
+            x += g.bias[gj];
+          } else if (EPI == 3) {
+            x *= tf_gelu_grad(g.Z[(size_t)gi * g.ldz + gj]);
+          }
+          g.C[(size_t)gi * g.ldc + gj] = x;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TF_N));
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Wide-K product with the digit split of the FP64 A operand fused in: C = A B^T with A
 // (M x K, element (i, k) at A[i * a_rs + k], K contiguous) read from HBM once, and B
 // (N <= 32) already split.  One CTA per 128-row tile of A.  Sixteen worker warps load the
@@ -1664,6 +1866,43 @@ cudaError_t launch_ozaki_fb(const OzDesc* d, int count, int max_tiles, unsigned*
       k_ozaki_fb<32><<<dim3(max_tiles, c), FbCfg<32>::THREADS, FbCfg<32>::SMEM, st>>>(d + off, status, gmax);
     count_launch();
   }
+  return cudaGetLastError();
+}
+
+size_t tf32x3_work_floats(int M, int N, int K) {
+  const size_t kp = (size_t)((K + TF_KC - 1) / TF_KC) * TF_KC;
+  return 2 * kp * ((size_t)((M + TF_M - 1) / TF_M) * TF_M + (size_t)((N + TF_N - 1) / TF_N) * TF_N);
+}
+
+cudaError_t launch_tf32x3_gemm(int M, int N, int K, const float* A, long long a_rs, long long a_ks,
+                               const float* B, long long b_ns, long long b_ks, float* C, int ldc, int epi,
+                               const float* bias, float* Z, int ldz, float* work, size_t work_floats,
+                               unsigned* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K <= 0 || epi < 0 || epi > 3 || work_floats < tf32x3_work_floats(M, N, K)) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(work) & 15) != 0) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaSuccess;
+    e = cudaFuncSetAttribute(k_tf32x3<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tf32x3<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tf32x3<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tf32x3<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TF_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int nkc = (K + TF_KC - 1) / TF_KC, tm = (M + TF_M - 1) / TF_M, tn = (N + TF_N - 1) / TF_N;
+  float* At = work;
+  float* Bt = work + (size_t)2 * tm * TF_M * nkc * TF_KC;
+  const TfSplit sa{A, a_rs, a_ks, M, K, TF_M, At}, sb{B, b_ns, b_ks, N, K, TF_N, Bt};
+  k_tf32_split<<<dim3(std::max(tm, tn) * nkc, 2), 256, 0, st>>>(sa, sb); count_launch();
+  const TfGemm g{At, Bt, C, ldc, M, N, K, bias, Z, ldz};
+  const dim3 grid(tm * tn);
+  if (epi == 0) k_tf32x3<0><<<grid, 192, TF_SMEM, st>>>(g, status);
+  else if (epi == 1) k_tf32x3<1><<<grid, 192, TF_SMEM, st>>>(g, status);
+  else if (epi == 2) k_tf32x3<2><<<grid, 192, TF_SMEM, st>>>(g, status);
+  else k_tf32x3<3><<<grid, 192, TF_SMEM, st>>>(g, status);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 """Python binding of the learned interface warm start (include/elm_mlp.h): argument
-marshalling only; forward, backward and Adam run in the library's CUDA kernels."""
+marshalling only; forward, backward and Adam run in the library's CUDA kernels (the layers'
+products on the tensor cores at FP32 accuracy)."""
 from __future__ import annotations
 
 import ctypes
@@ -7,8 +8,8 @@ import ctypes
 from . import elm_ddm as _E
 
 SYMBOLS = ("elm_mlp_create", "elm_mlp_param_count", "elm_mlp_get_params", "elm_mlp_set_params",
-           "elm_mlp_forward", "elm_mlp_gradient", "elm_mlp_train_step", "elm_mlp_destroy",
-           "elm_mlp_last_error")
+           "elm_mlp_forward", "elm_mlp_gradient", "elm_mlp_train_step", "elm_mlp_check",
+           "elm_mlp_destroy", "elm_mlp_last_error")
 
 _bound = False
 
@@ -25,6 +26,7 @@ def _lib():
         lib.elm_mlp_forward.argtypes = [P, P, I, P]
         lib.elm_mlp_gradient.argtypes = [P, P, P, I, P, P]
         lib.elm_mlp_train_step.argtypes = [P, P, P, I, ctypes.c_float, P]
+        lib.elm_mlp_check.argtypes = [P]
         lib.elm_mlp_destroy.argtypes = [P]
         lib.elm_mlp_last_error.argtypes = [P]
         lib.elm_mlp_last_error.restype = ctypes.c_char_p
@@ -39,7 +41,8 @@ def _ptr(t):
 
 
 class MLP:
-    """d_in -> d_hidden -> d_hidden -> d_out with GELU, FP32, on one CUDA stream."""
+    """d_in -> d_hidden -> d_hidden -> d_out with GELU, FP32 (products at FP32 accuracy on the
+    tensor cores), on one CUDA stream."""
 
     def __init__(self, d_in: int, d_hidden: int, d_out: int, max_batch: int, seed: int = 0, stream=None):
         import torch
@@ -89,6 +92,10 @@ class MLP:
         self._rc(self.lib.elm_mlp_train_step(self.h, _ptr(x), _ptr(target), x.shape[0], float(lr),
                                              _ptr(self._loss)))
         return self._loss
+
+    def check(self):
+        """Synchronise; raise if a bounded wait of a GEMM kernel gave up since the last check."""
+        self._rc(self.lib.elm_mlp_check(self.h))
 
     def close(self):
         if getattr(self, "h", None):

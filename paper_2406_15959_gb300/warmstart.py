@@ -71,6 +71,7 @@ class WarmStart:
                 nb += 1
             losses.append(float(tot / max(nb, 1)))
             lr *= lr_decay
+        self.net.check()
         return losses
 
     def predict(self, A: np.ndarray):

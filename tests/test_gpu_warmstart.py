@@ -3,11 +3,14 @@ and Adam step against the FP64 oracle (oracle/mlp_oracle.py, itself pinned by fi
 differences), and the gain of the trained network as the initial guess of the CG
 interface solve, with the direct solve as the reference for the error.
 
-Tolerances: the library computes in FP32.  A forward value or gradient entry is a sum of
-at most a few hundred FP32 products (relative rounding <= K * 2^-24 ~ 3e-5 for K = 512),
-so forward and gradients are compared at 1e-4 relative to each block's norm; one Adam
-step moves every parameter by about lr, so parameters after a step are compared at 1e-3 lr
-absolute (the gradient's relative error enters the step only through m / sqrt(v)).
+Tolerances: the library computes in FP32, its layer products on the tensor cores as three
+TF32 products of a hi/lo split (about 2^-21 relative per product term instead of an FP32
+FMA's 2^-24).  A forward value or gradient entry is a sum of at most a few hundred such
+products (relative error <= K * 2^-21 ~ 2.4e-4 for K = 512 in the worst case, about
+sqrt(K) * 2^-21 ~ 1e-5 for terms of random sign), so forward values are compared at 1e-5
+and gradients at 1e-4 relative to each block's norm; one Adam step moves every parameter
+by about lr, so parameters after a step are compared at 1e-3 lr absolute (the gradient's
+relative error enters the step only through m / sqrt(v)).
 """
 import numpy as np
 import pytest
@@ -53,6 +56,30 @@ def test_mlp_forward_and_gradient_match_oracle():
     assert abs(float(loss) - l_or) <= 1e-5 * l_or
     for gb, ob in zip(blocks(g.cpu().numpy()), blocks(g_or)):
         assert np.linalg.norm(gb - ob) <= 1e-4 * np.linalg.norm(ob)
+
+
+@pytest.mark.parametrize("dims", [(64, 300, 700, 200), (33, 129, 257, 129)])
+def test_mlp_spanning_several_tiles_matches_oracle(dims):
+    """Layer products over several 128 x 64 output tiles and 16-wide K chunks, ragged in
+    every dimension, against the FP64 oracle."""
+    d_in, d_h, d_out, b = dims
+    rng = np.random.default_rng(11)
+    net = M.MLP(d_in, d_h, d_out, b, seed=4)
+    X = torch.as_tensor(rng.standard_normal((b, d_in)), dtype=torch.float32, device="cuda")
+    T = torch.as_tensor(rng.standard_normal((b, d_out)), dtype=torch.float32, device="cuda")
+    p = net.params().cpu().numpy().astype(np.float64)
+    Xn, Tn = X.cpu().numpy().astype(np.float64), T.cpu().numpy().astype(np.float64)
+    y_or, _ = MO.forward(p, Xn, d_in, d_h, d_out)
+    y = net.forward(X).cpu().numpy()
+    assert np.linalg.norm(y - y_or) <= 1e-5 * np.linalg.norm(y_or)
+    _, g = net.gradient(X, T)
+    _, g_or = MO.loss_and_grad(p, Xn, Tn, d_in, d_h, d_out)
+    sizes = [d_in * d_h, d_h, d_h * d_h, d_h, d_h * d_out, d_out]
+    for gb, ob in zip(np.split(g.cpu().numpy().astype(np.float64), np.cumsum(sizes)[:-1]),
+                      np.split(g_or, np.cumsum(sizes)[:-1])):
+        assert np.linalg.norm(gb - ob) <= 1e-4 * np.linalg.norm(ob)
+    net.check()
+    net.close()
 
 
 def test_adam_step_matches_oracle():
