@@ -64,10 +64,11 @@ struct OzDesc {
   double* C;
   long long c_rs, c_cs;
   int M, N, K;
-  int tile0;  // unused (kept zero)
+  int tile0;  // B-split product (k_ozaki_fb): bit 0 negates, bit 1 adds the identity; else zero
   long long a_rs;  // fused-split launches: At is the FP64 A, element (i, k) at At[i * a_rs + k]
   // persistent product with GEMM_LOWER: column j of this C is column j + lower_off of the
-  // symmetric matrix, so a tile is kept when its first column is on or below the diagonal
+  // symmetric matrix, so a tile is kept when its first column is on or below the diagonal;
+  // B-split product with the identity flag: row i of this C is row i + lower_off
   int lower_off = 0;
   // fused-split launches: rows i < lead of A are read from At2 (same row stride a_rs) and
   // take their exponent bounds from Ae2, instead of At and Ae, so one product can stack

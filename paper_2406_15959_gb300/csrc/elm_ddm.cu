@@ -1353,8 +1353,10 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
       add_oz_rec(h->ty_recs, od, 0, -1.0, 1.0, 0, "oz_trsm_y");
     }
   }
-  // D_s = I - (Q_G^T)^T Q_G^T and M_s = -Y_s Q_G^T (K = n_N): tensor-core products that
-  // share the digit split of Q_G, or FP64 GEMMs.
+  // D_s = I - (Q_G^T)^T Q_G^T and M_s = -Y_s Q_G^T (K = n_N): tensor-core products whose
+  // left operands (Q_G, Y_s) are split in 128-row tiles and whose right operand, the columns
+  // of Q_G^T, is split inside the B-split kernel (64 columns per CTA, one descriptor per left
+  // row tile), or FP64 GEMMs.
   {
     std::vector<GemmDesc> gD, gM;
     std::vector<SplitDesc> sp;
@@ -1371,19 +1373,28 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
       if (mfs > 0) gM.push_back({Ys, QGt, Ms, mfs, mgs, n, h->mfld, ld, h->mfld});
       if (h->emulated) {
         void* t5 = sub_region(s, 8); int* x5 = (int*)sub_region(s, 9);
-        void* t6 = sub_region(s, 10); int* x6 = (int*)sub_region(s, 11);
+        int* x6 = (int*)sub_region(s, 11);
         void* t7 = sub_region(s, 12); int* x7 = (int*)sub_region(s, 13);
-        sp.push_back({QGt, ld, 1, mgs, n, x5, t5, 128});   // Q_G, left operand
-        sp.push_back({QGt, ld, 1, mgs, n, x6, t6, 32});    // Q_G, right operand
+        sp.push_back({QGt, ld, 1, mgs, n, x5, t5, 128});        // Q_G, left operand
+        sp.push_back({QGt, ld, 1, mgs, n, x6, nullptr, 128});   // Q_G^T columns: exponent bounds only
         if (mfs > 0) sp.push_back({Ys, 1, h->mfld, mfs, n, x7, t7, 128});  // Y_s, left operand
-        oD.push_back({t5, x5, t6, x6, Ds, 1, h->mgld, mgs, mgs, n, 0});
-        if (mfs > 0) oM.push_back({t7, x7, t6, x6, Ms, 1, h->mfld, mfs, mgs, n, 0});
+        const size_t tile = oz_split_elems(128, n, 128) * 2;    // bytes of one 128-row tile's planes
+        for (int r0 = 0; r0 < mgs; r0 += 128) {
+          OzDesc od{(char*)t5 + (size_t)(r0 / 128) * tile, x5 + r0, QGt, x6, Ds + r0, 1, h->mgld,
+                    std::min(128, mgs - r0), mgs, n, 3, ld};  // -(Q_G Q_G^T) + I
+          od.lower_off = r0;
+          oD.push_back(od);
+        }
+        for (int r0 = 0; r0 < mfs; r0 += 128)
+          oM.push_back({(char*)t7 + (size_t)(r0 / 128) * tile, x7 + r0, QGt, x6, Ms + r0, 1, h->mfld,
+                        std::min(128, mfs - r0), mgs, n, 1, ld});  // -(Y_s Q_G^T)
       }
     }
     if (h->emulated) {
       add_split_rec(h->dm_recs, sp, "split_dm");
-      add_oz_rec(h->dm_recs, oD, 32, -1.0, 0.0, GEMM_ADD_IDENTITY, "oz_dm");
-      add_oz_rec(h->dm_recs, oM, 32, -1.0, 0.0, 0, "oz_dm");
+      std::vector<OzDesc> odm(oD);
+      odm.insert(odm.end(), oM.begin(), oM.end());
+      add_fb_rec(h->dm_recs, odm, "oz_dm");
     } else {
       add_gemm_rec(h->dm_recs, gD, true, false, -1.0, 0.0, GEMM_ADD_IDENTITY);
       add_gemm_rec(h->dm_recs, gM, false, false, -1.0, 0.0, 0);

@@ -1006,10 +1006,11 @@ __global__ void __launch_bounds__(256) k_hl_convert(const OzDesc* __restrict__ d
 }
 
 // ---------------------------------------------------------------------------------------
-// Wide-K product with the digit split of the FP64 B operand fused in: C = A B^T with A
-// (M <= 128 rows, one row tile) already split, and B (N rows, element (j, k) at
-// B[j * a_rs + k], K contiguous; rows j < lead from At2 with exponent bounds Ae2) read
-// from HBM once and split in the kernel.  One CTA per 32-row tile of B.  This is the
+// Wide-K product with the digit split of the FP64 B operand fused in: C = A B^T (or its
+// negation, optionally plus the identity: descriptor flags in tile0) with A (M <= 128
+// rows, one row tile) already split, and B (N rows, element (j, k) at B[j * a_rs + k], K
+// contiguous; rows j < lead from At2 with exponent bounds Ae2) read from HBM once and split
+// in the kernel.  One CTA per 32-row tile of B.  This is the
 // orientation of the outer-block W1 product of the two-level QR: A = V_o^T (all the
 // block's reflectors, M = the block width) and B = the trailing columns, so every trailing
 // column is split once per outer block, where the A-operand form would split it once per
@@ -1267,6 +1268,9 @@ __global__ void __launch_bounds__(FbCfg<NBC>::THREADS, 1) k_ozaki_fb(const OzDes
     if (C::NBUF == 2 && alive && nch >= 1) drain(nch - 1);
     if (alive && drow < d.M) {
       const int ed = d.Ae[drow];
+      // tile0 flags: bit 0 negates the product, bit 1 adds the identity (C row drow +
+      // lower_off is the diagonal's row)
+      const bool neg = (d.tile0 & 1) != 0, ident = (d.tile0 & 2) != 0;
 #pragma unroll
       for (int j = 0; j < C::DCOLS; ++j) {
         const int gc = bj * NBC + col0 + j;
@@ -1275,8 +1279,9 @@ __global__ void __launch_bounds__(FbCfg<NBC>::THREADS, 1) k_ozaki_fb(const OzDes
           double v = 0.0;
           if (ed != 0 && fj != 0) {
             const int k = ed + fj - 2044 - 62;
-            v = i64_to_double_pow2(H[j], k + 24, false) + i64_to_double_pow2((long long)Lw[j], k, false);
+            v = i64_to_double_pow2(H[j], k + 24, neg) + i64_to_double_pow2((long long)Lw[j], k, neg);
           }
+          if (ident && drow + d.lower_off == gc) v += 1.0;
           d.C[(size_t)drow * d.c_rs + (size_t)gc * d.c_cs] = v;
         }
       }
