@@ -1468,8 +1468,9 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
     }
     for (auto& b : drounds) add_add_rec(h->s_recs, b);
     // M^T M blocks: with the tensor-core path every distinct M block is split once (as a
-    // 128-row A operand and a 32-row B operand; rows = the block's columns, K = its rows)
-    // and each round is one persistent product launch (K = flux-group length <= 128).
+    // 128-row A operand and a 64-row B operand; rows = the block's columns, K = its rows)
+    // and each round is one launch of the wide persistent product (128 x 64 tiles,
+    // K = flux-group length <= 128).
     int maxlen = 0;  // K of the M^T M products: the flux groups' rows
     for (const FGroup& F : h->fgroups) maxlen = std::max(maxlen, F.len);
     if (h->emulated && maxlen <= 128) {
@@ -1484,7 +1485,7 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
             if (idx.count(ptr)) continue;
             MB m{ptr, side ? g.ldb : g.lda, side ? g.n : g.m, g.k, 0, 0, 0, 0};
             m.ta = bytes; bytes += al(oz_split_elems(m.rows, m.K, 128) * 2);
-            m.tb = bytes; bytes += al(oz_split_elems(m.rows, m.K, 32) * 2);
+            m.tb = bytes; bytes += al(oz_split_elems(m.rows, m.K, 64) * 2);
             m.ea = bytes; bytes += al((size_t)m.rows * 4);
             m.eb = bytes; bytes += al((size_t)m.rows * 4);
             idx[ptr] = (int)blocks.size();
@@ -1499,7 +1500,7 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
       std::vector<SplitDesc> sp;
       for (const MB& m : blocks) {
         sp.push_back({m.p, m.ld, 1, m.rows, m.K, (int*)(mbase + m.ea), mbase + m.ta, 128});
-        sp.push_back({m.p, m.ld, 1, m.rows, m.K, (int*)(mbase + m.eb), mbase + m.tb, 32});
+        sp.push_back({m.p, m.ld, 1, m.rows, m.K, (int*)(mbase + m.eb), mbase + m.tb, 64});
       }
       add_split_rec(h->s_recs, sp, "split_schur");
       for (auto& b : mrounds) {
@@ -1510,7 +1511,7 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
           od.push_back({mbase + A.ta, (int*)(mbase + A.ea), mbase + B.tb, (int*)(mbase + B.eb), g.C, 1,
                         g.ldc, g.m, g.n, g.k, 0});
         }
-        add_oz_rec(h->s_recs, od, 0, 1.0, 1.0, 0, "oz_schur");
+        add_updw_rec(h->s_recs, od, 1.0, "oz_schur");
       }
     } else {
       for (auto& b : mrounds) add_gemm_rec(h->s_recs, b, true, false, 1.0, 1.0, 0);
