@@ -507,8 +507,8 @@ int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, const doubl
 /* Numerical self-test of a device routine the solver uses, element by element:
  * y[i] = f(x[i]) for 0 <= i < n, x and y device double arrays (caller-owned).
  *   which  ELM_DDM_SELFTEST_PIVOT_RCP: the reciprocal of the Schur Cholesky's pivots
- *          (Newton's iteration from an FP32 seed; defined for positive normal x, within
- *          two units in the last place of 1/x)
+ *          (one third-order iteration from an FP32 seed; defined for positive normal x,
+ *          within two units in the last place of 1/x)
  * Synchronises the stream.  Returns ELM_DDM_ERR_ARG for an unknown `which`, NULL arrays or
  * n < 0; ELM_DDM_ERR_CUDA. */
 #define ELM_DDM_SELFTEST_PIVOT_RCP 0

@@ -360,12 +360,13 @@ __device__ __forceinline__ double warp_transpose_sum32(double (&a)[32]) {
 }
 #endif
 
-// Reciprocal of a positive normal double by Newton's iteration r <- r + r (1 - d r), whose
-// relative error squares at every step, from an FP32 seed: d = m 2^(e - 1023) with m in
-// [1, 2) truncated to 24 bits, r0 = 2^(1023 - e) / m (FP32 reciprocal, relative error
-// below 2^-22 against 1/d), then two steps (below 2^-44, then at the rounding level).
-// Four dependent FP64 FMAs on the pivot chain instead of a division; d outside
-// [2^-1020, 2^1020] takes the division.
+// Reciprocal of a positive normal double from an FP32 seed: d = m 2^(e - 1023) with m in
+// [1, 2) truncated to 24 bits, r0 = 2^(1023 - e) / m (FP32 reciprocal, relative error below
+// 2^-22 against 1/d), then one step of the third-order iteration for 1/d: with
+// eps = 1 - d r0, 1/d = r0 / (1 - eps) = r0 (1 + eps + eps^2 + ...), so r0 (1 + eps + eps^2)
+// has relative error about eps^3 < 2^-66, below the final rounding (Newton's second-order
+// step r <- r + r (1 - d r) would need two steps).  Three dependent FP64 FMAs on the pivot
+// chain instead of a division; d outside [2^-1020, 2^1020] takes the division.
 __device__ __forceinline__ double rcp_newton(double d) {
   const long long b = __double_as_longlong(d);
   const int e = (int)((b >> 52) & 0x7FF);
@@ -373,10 +374,9 @@ __device__ __forceinline__ double rcp_newton(double d) {
   const float rf = __frcp_rn(__int_as_float(0x3F800000 | (int)((b >> 29) & 0x7FFFFF)));  // in (0.5, 1]
   const int fb = __float_as_int(rf);
   const long long rb = ((long long)(((fb >> 23) & 0xFF) - 127 + 2046 - e) << 52) | ((long long)(fb & 0x7FFFFF) << 29);
-  double r = __longlong_as_double(rb);
-  r = fma(r, fma(-d, r, 1.0), r);
-  r = fma(r, fma(-d, r, 1.0), r);
-  return r;
+  const double r = __longlong_as_double(rb);
+  const double eps = fma(-d, r, 1.0);
+  return fma(r, fma(eps, eps, eps), r);
 }
 
 // y[i] = rcp_newton(x[i]) (self-test of the Cholesky pivots' reciprocal).

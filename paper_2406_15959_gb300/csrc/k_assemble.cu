@@ -19,8 +19,8 @@
 // factors into per-neuron tables over those coordinates (k_exp_tables).  Then with
 // r = 1 / (E + 1)
 //   t = (E - 1) r,   1 - t^2 = 4 E r^2,
-// one product and one reciprocal per entry instead of a tanh (the reciprocal by Newton's
-// iteration from an FP32 seed, rcp_newton: four FP64 FMAs, within 2 ulp).  Accuracy: E carries the
+// one product and one reciprocal per entry instead of a tanh (the reciprocal by a
+// third-order iteration from an FP32 seed, rcp_newton: three FP64 FMAs, within 2 ulp).  Accuracy: E carries the
 // relative error of the two factors (a few ulp plus the rounding of their centred
 // arguments), E - 1 is exact near E = 1, so t has an absolute error of a few ulp times
 // the argument's magnitude -- no more than tanh(w . x + b) itself, whose argument rounds
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) k_assemble(double* __restrict__ K, long l
           const double b = tb.Ty[((size_t)s * n + c) * tb.nymax + iy];
           const double E = a * b;
           if (E < 1e300) {
-            const double rr = rcp_newton(E + 1.0);  // E + 1 in [1, 1e300]: Newton's fast path
+            const double rr = rcp_newton(E + 1.0);  // E + 1 in [1, 1e300]: the iteration's fast path
             t = (E - 1.0) * rr;
             d1 = 4.0 * rr * (E * rr);
           } else if (E >= 1e300) {
