@@ -77,6 +77,8 @@ def combine(workloads) -> Batch:
     ws = list(workloads)
     if not ws:
         raise ValueError("no instances")
+    if any(getattr(w.geom, "flux", None) is not None for w in ws):
+        raise ValueError("instances with explicit flux rows (cross points) are not batched")
     n = max(w.n_neurons for w in ws)
     m_max = max(w.geom.m_max for w in ws)
     N = sum(w.geom.n_sub for w in ws)

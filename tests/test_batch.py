@@ -130,3 +130,12 @@ def test_autotuner_shape_classes_and_candidates():
     assert AT.shape_key(60, 990, 2300, 390) == AT.shape_key(64, 1000, 2400, 400)
     c = AT.candidates(152)
     assert (0, 0) in c and all(p in (0, 4, 8) and g >= 0 for p, g in c)
+
+
+def test_combine_rejects_cross_point_geometries():
+    """Batching stacks one A-row per interface row; geometries with explicit flux rows (the
+    corner rule) are refused instead of losing their corner rows."""
+    w = wl.paper_grid_workload(2, n_total=4 * 30, theta="local_unit", n_grid=17, n_test_side=10,
+                               cross_points=True)
+    with pytest.raises(ValueError):
+        B.combine([w])
