@@ -14,7 +14,10 @@ inline void count_launch(int k = 1) { g_kernel_launches.fetch_add(k, std::memory
 constexpr int QR_NB = 32;     // panel width of the blocked Householder QR
 constexpr int CHOL_NB = 64;   // block size of the Schur-matrix Cholesky
 constexpr int GRP_MAX = 4;    // most subdomains one interface unknown is shared by (a cross point)
-constexpr int OZ_HL_TILE = 128 * 32 * 2;  // int64 words of one split-K accumulator tile
+// int64 words of one split-K accumulator tile: 128 x 32 elements x 2 words, then the count
+// of the tile's CTAs that have added their part (the last one converts and clears)
+constexpr int OZ_HL_WORDS = 128 * 32 * 2;
+constexpr int OZ_HL_TILE = OZ_HL_WORDS + 2;
 constexpr int TRSV_MAX_N = 8192;  // largest n_neurons the back-solve keeps in shared memory
 
 // Bits of the device status word.

@@ -750,6 +750,37 @@ constexpr int FA_SMEM = FA_FLAG + 16 + 1024;
 static_assert(FA_SMEM <= 227 * 1024, "fused product exceeds the shared memory of one CTA");
 static_assert(FA_WORKERS * 32 == 4 * OZ_M, "one worker thread per (row, 8-wide k group)");
 
+// Split K: every CTA of a tile counts itself once it has added its part (or had no K range);
+// the last one builds C from the accumulator (the two exact int64 words of every element,
+// summed by integer atomics, so in any order the same) with the epilogue's arithmetic, and
+// clears the accumulator and the count for the next product.  All threads of the CTA call it.
+__device__ __forceinline__ void fa_splitk_finish(const OzDesc& d, int tid) {
+  __shared__ int is_last;
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(d.hl) + OZ_HL_WORDS;
+  if (tid == 0) is_last = atomicAdd(cnt, 1ull) == (unsigned long long)(gridDim.z - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  long long* hl = d.hl;
+  for (int e = tid; e < d.M * 32; e += FA_THREADS) {
+    const int row = e >> 5, col = e & 31;
+    if (col >= d.N) continue;
+    long long* hp = hl + 2 * (size_t)e;
+    const long long H = __ldcg(hp), Lw = __ldcg(hp + 1);
+    hp[0] = 0;
+    hp[1] = 0;
+    const int ed = (row < d.lead ? d.Ae2 : d.Ae)[row];
+    const int fj = d.Be[col];
+    double v = 0.0;
+    if (ed != 0 && fj != 0) {
+      const int k = ed + fj - 2044 - 62;
+      v = i64_to_double_pow2(H, k + 24, false) + i64_to_double_pow2(Lw, k, false);
+    }
+    d.C[(size_t)row * d.c_rs + (size_t)col * d.c_cs] = v;
+  }
+  if (tid == 0) *cnt = 0ull;
+}
+
 __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __restrict__ descs,
                                                            unsigned* status, int gmax) {
   const OzDesc d = descs[blockIdx.y];
@@ -781,7 +812,10 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
   // [c0, c1); below, kc and the chunk counts are local to that range, kb its first step
   const int per = (nch_all + gridDim.z - 1) / gridDim.z;
   const int c0 = (int)blockIdx.z * per, c1 = min(nch_all, c0 + per);
-  if (c0 >= c1) return;
+  if (c0 >= c1) {  // no K range here: only counted
+    if (d.hl && gridDim.z > 1) fa_splitk_finish(d, threadIdx.x);
+    return;
+  }
   const int kb = c0 * 4;
   const int nkc = min(nkc_all, c1 * 4) - kb;
   const int nch = (nkc + 3) / 4;
@@ -947,7 +981,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
     if (alive && nch >= 1) drain(nch - 1);
     if (alive && drow < d.M && d.hl) {
       // split K: the exact integer words go to the accumulator (one 128 x 32 tile), added in
-      // any order with the same result; k_hl_convert builds C from them
+      // any order with the same result; the tile's last CTA builds C from them (below)
       unsigned long long* hp = reinterpret_cast<unsigned long long*>(d.hl) + ((size_t)drow * 32 + col0) * 2;
 #pragma unroll
       for (int j = 0; j < 8; ++j)
@@ -955,6 +989,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
           atomicAdd(hp + 2 * j, (unsigned long long)H[j]);
           atomicAdd(hp + 2 * j + 1, (unsigned long long)Lw[j]);
         }
+      __threadfence();  // the additions are visible before this CTA is counted
     } else if (alive && drow < d.M) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -979,30 +1014,7 @@ __global__ void __launch_bounds__(FA_THREADS, 1) k_ozaki_fa(const OzDesc* __rest
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
-}
-
-// C from the split-K accumulator of k_ozaki_fa: the two exact int64 words of every element
-// (summed over the K ranges by integer atomics, so in any order the same), converted with
-// the fa epilogue's arithmetic, and the accumulator cleared for the next product.
-__global__ void __launch_bounds__(256) k_hl_convert(const OzDesc* __restrict__ descs) {
-  const OzDesc d = descs[blockIdx.y];
-  long long* hl = d.hl;
-  for (int e = blockIdx.x * 256 + threadIdx.x; e < d.M * 32; e += gridDim.x * 256) {
-    const int row = e >> 5, col = e & 31;
-    if (col >= d.N) continue;
-    long long* hp = hl + 2 * (size_t)e;
-    const long long H = hp[0], Lw = hp[1];
-    hp[0] = 0;
-    hp[1] = 0;
-    const int ed = (row < d.lead ? d.Ae2 : d.Ae)[row];
-    const int fj = d.Be[col];
-    double v = 0.0;
-    if (ed != 0 && fj != 0) {
-      const int k = ed + fj - 2044 - 62;
-      v = i64_to_double_pow2(H, k + 24, false) + i64_to_double_pow2(Lw, k, false);
-    }
-    d.C[(size_t)row * d.c_rs + (size_t)col * d.c_cs] = v;
-  }
+  if (d.hl && gridDim.z > 1) fa_splitk_finish(d, tid);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1843,9 +1855,6 @@ cudaError_t launch_ozaki_fa(const OzDesc* d, int count, int max_tiles, unsigned*
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
     k_ozaki_fa<<<dim3(max_tiles, c, ksplit), FA_THREADS, FA_SMEM, st>>>(d + off, status, gmax); count_launch();
-    if (ksplit > 1) {
-      k_hl_convert<<<dim3(4, c), 256, 0, st>>>(d + off); count_launch();
-    }
   }
   return cudaGetLastError();
 }
