@@ -95,7 +95,10 @@ struct CgState {
 // ---- launchers (return cudaGetLastError after the launch) ----
 int oz_tiles(int m, int n, int nt);
 size_t oz_split_elems(int R, int K, int row_tile);
-cudaError_t launch_split(const SplitDesc* d, int count, int max_rows, int max_split_blocks,
+// blocks of k_rowexp that descriptor d needs (a warp per row, or a thread per row for
+// short rows of a column-major operand); a split launch takes the largest over its batch
+int oz_rowexp_blocks(const SplitDesc& d);
+cudaError_t launch_split(const SplitDesc* d, int count, int rowexp_blocks, int max_split_blocks,
                          cudaStream_t st);
 // gmax (2..8): the digit pairs formed are those with p + q <= gmax; 8 (all 28 pairs of
 // weight >= 2^-62) is the FP64-accurate product, smaller values a lower-precision one

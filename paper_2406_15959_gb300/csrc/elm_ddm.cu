@@ -32,12 +32,12 @@ struct LaunchRec {
              //     last panel is `off`,
              // 9 = tensor-core digit GEMM with the FP64 B operand split in the kernel,
              // 10 = wide persistent tensor-core digit update (128 x 64 tiles, K <= 128)
-  int off, count, max_tiles;  // split: max_tiles = blocks of k_split, nt = max rows
+  int off, count, max_tiles;  // split: max_tiles = blocks of k_split, nt = blocks of k_rowexp
   bool ta, tb;
   double alpha, beta;
   int flags;
   double flops;  // algorithmic flops of the launch (2mnk per GEMM; m(m+1)k for a lower SYRK)
-  int nt;        // tensor-core GEMM: tile width (32 or 64); split: largest row count
+  int nt;        // tensor-core GEMM: tile width (32 or 64); split: k_rowexp blocks
   double bytes = 0.0;          // algorithmic HBM bytes (FP64 operands read, C read/written)
   const char* name = nullptr;  // kernel class for profiling (nullptr: the caller's name)
   int toff = 0;                // persistent launches: offset of the tile table
@@ -1086,7 +1086,7 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
       if (d.R <= 0 || d.K <= 0) continue;
       sds.push_back(d);
       L.count++;
-      L.nt = std::max(L.nt, d.R);
+      L.nt = std::max(L.nt, oz_rowexp_blocks(d));
       if (!d.tiles) {  // row exponents only
         L.bytes += 8.0 * d.R * d.K;
         continue;
@@ -1252,6 +1252,9 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
         void* t9 = sub_region(s, 16); int* x9 = (int*)sub_region(s, 17);
         void* t10 = sub_region(s, 18); int* x10 = (int*)sub_region(s, 19);
         sp1.push_back({V, ld, 1, nbe, mp, x2, t2, 32});              // V^T: rows = panel columns
+        // V itself (the update's left operand) is ready once the panel is: split in the
+        // same launch as V^T rather than after the W1 product
+        sp1.push_back({V, 1, ld, mp, nbe, x3, t3, 128});             // V: rows = matrix rows
         OzDesc ow{PA2, h->colexp + (size_t)s * h->ncap + k0, t2, x2, w1, QR_NB, 1, n2i + nbe, nbe, mp, 0, ld};
         ow.At2 = V;   // rows i < nbe at V + i * ld, rows i >= nbe at PA2 + i * ld = A2
         ow.Ae2 = x2;
@@ -1262,7 +1265,6 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
         // (row i = column i of the column-major T)
         spt.push_back({w1t, QR_NB, 1, n2i, nbe, x9, t9, 128});
         spt.push_back({Tb, QR_NB, 1, nbe, nbe, x10, t10, 32});
-        spt.push_back({V, 1, ld, mp, nbe, x3, t3, 128});     // V: rows = matrix rows
         ot.push_back({t9, x9, t10, x10, w2, QR_NB, 1, n2i, nbe, nbe, 0});
         sp3.push_back({w2, QR_NB, 1, n2i, nbe, x4, t4, 32});  // W2^T: rows = columns of A2
         o3.push_back({t3, x3, t4, x4, A2, 1, ld, mp, n2i, nbe, 0});
@@ -1300,6 +1302,7 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
       void* t9 = sub_region(s, 16); int* x9 = (int*)sub_region(s, 17);
       void* t10 = sub_region(s, 18); int* x10 = (int*)sub_region(s, 19);
       sp1.push_back({Vo, ld, 1, wo, mpo, x2, t2, 128});            // V_o^T: rows = block columns
+      if (n2o > 0) sp1.push_back({Vo, 1, ld, mpo, wo, x3, t3, 128});  // V_o: rows = matrix rows
       // C[i, j] = W1^T[j][i] at w1 + j * QR_NBO + i
       OzDesc ob{t2, x2, Ao, h->colexp + (size_t)s * h->ncap + k0o, w1, 1, QR_NBO, wo, wo + n2o, mpo, 0, ld};
       ob.At2 = Vo;  // B rows j < wo at Vo + j * ld (explicit reflectors), j >= wo at Ao + j * ld = A2
@@ -1309,7 +1312,6 @@ int elm_ddm_setup_flux(const elm_ddm_desc* desc, const int32_t* counts, const do
       if (n2o <= 0) continue;
       spt.push_back({w1t, QR_NBO, 1, n2o, wo, x9, t9, 128});
       spt.push_back({To, QR_NBO, 1, wo, wo, x10, t10, 32});
-      spt.push_back({Vo, 1, ld, mpo, wo, x3, t3, 128});
       ot.push_back({t9, x9, t10, x10, w2, QR_NBO, 1, n2o, wo, wo, 0});
       sp3.push_back({w2, QR_NBO, 1, n2o, wo, x4, t4, 64});  // 64-row tiles for the wide update
       o3.push_back({t3, x3, t4, x4, A2, 1, ld, mpo, n2o, wo, 0});

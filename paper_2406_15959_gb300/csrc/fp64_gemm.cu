@@ -101,10 +101,10 @@ extern "C" int elm_ddm_fp64_gemm(int kernel, int M, int N, int K, double alpha, 
     e = cudaMemcpyAsync(ws + L.ut, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
   const SplitDesc* dsd = reinterpret_cast<const SplitDesc*>(ws + L.sd);
   const OzDesc* dod = reinterpret_cast<const OzDesc*>(ws + L.od);
-  const int rows = M > N ? M : N;
+  const int rx_blocks = std::max(oz_rowexp_blocks(sd[0]), oz_rowexp_blocks(sd[1]));
   const int ta_tiles = (M + 127) / 128, tb_tiles = (N + L.brow - 1) / L.brow;
   const int blocks = (ta_tiles > tb_tiles ? ta_tiles : tb_tiles) * ((K + OZ_KC - 1) / OZ_KC);
-  if (e == cudaSuccess) e = launch_split(dsd, 2, rows, blocks, st);
+  if (e == cudaSuccess) e = launch_split(dsd, 2, rx_blocks, blocks, st);
   if (e == cudaSuccess) {
     switch (kernel) {
       case ELM_DDM_GEMM_TILE32: e = launch_ozaki(32, dod, 1, oz_tiles(M, N, 32), alpha, beta, 0, status, st); break;

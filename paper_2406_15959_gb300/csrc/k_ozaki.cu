@@ -144,15 +144,29 @@ __device__ __forceinline__ void cp_async_wait() {
 // E[r] = largest biased exponent in row r (0 for an all-zero row).  A warp per row,
 // lanes over k; but short rows of a column-major operand (rs == 1, K <= 256): a thread per
 // row looping over k, so that a warp reads 32 consecutive rows of one column at a time
-// (the grid, sized for 8 rows per block, has blocks to spare).
+// (the grid, sized for 8 rows per block, has blocks to spare).  Both loops issue RX_UNROLL
+// loads before the first maximum, so that a long row (a panel's V^T, K up to the local
+// row count) waits for one memory latency per RX_UNROLL elements, not per element.
+constexpr int RX_UNROLL = 8;
+__host__ __device__ inline bool rowexp_by_thread(long long rs, long long ks, int K) {
+  return rs == 1 && ks != 1 && K <= 256;
+}
 __global__ void __launch_bounds__(256) k_rowexp(const SplitDesc* __restrict__ descs) {
   const SplitDesc d = descs[blockIdx.y];
-  if (d.rs == 1 && d.ks != 1 && d.K <= 256) {
+  if (rowexp_by_thread(d.rs, d.ks, d.K)) {
     const int r = blockIdx.x * 256 + threadIdx.x;
     if (r >= d.R) return;
     unsigned mx = 0;
     const double* x = d.X + r;
-    for (int k = 0; k < d.K; ++k) mx = max(mx, biased_exp(x[(long long)k * d.ks]));
+    int k = 0;
+    for (; k + RX_UNROLL <= d.K; k += RX_UNROLL) {
+      double v[RX_UNROLL];
+#pragma unroll
+      for (int u = 0; u < RX_UNROLL; ++u) v[u] = x[(long long)(k + u) * d.ks];
+#pragma unroll
+      for (int u = 0; u < RX_UNROLL; ++u) mx = max(mx, biased_exp(v[u]));
+    }
+    for (; k < d.K; ++k) mx = max(mx, biased_exp(x[(long long)k * d.ks]));
     d.E[r] = (int)mx;
     return;
   }
@@ -160,8 +174,16 @@ __global__ void __launch_bounds__(256) k_rowexp(const SplitDesc* __restrict__ de
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (r >= d.R) return;
   unsigned mx = 0;
-  for (int k = lane; k < d.K; k += 32)
-    mx = max(mx, biased_exp(d.X[(long long)r * d.rs + (long long)k * d.ks]));
+  const double* x = d.X + (long long)r * d.rs;
+  int k = lane;
+  for (; k + 32 * (RX_UNROLL - 1) < d.K; k += 32 * RX_UNROLL) {
+    double v[RX_UNROLL];
+#pragma unroll
+    for (int u = 0; u < RX_UNROLL; ++u) v[u] = x[(long long)(k + 32 * u) * d.ks];
+#pragma unroll
+    for (int u = 0; u < RX_UNROLL; ++u) mx = max(mx, biased_exp(v[u]));
+  }
+  for (; k < d.K; k += 32) mx = max(mx, biased_exp(x[(long long)k * d.ks]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) d.E[r] = (int)mx;
@@ -1757,12 +1779,17 @@ size_t oz_split_elems(int R, int K, int row_tile) {
   return (size_t)((R + row_tile - 1) / row_tile) * ((K + OZ_KC - 1) / OZ_KC) * OZ_S * row_tile * OZ_KC;
 }
 
-cudaError_t launch_split(const SplitDesc* d, int count, int max_rows, int max_split_blocks,
+int oz_rowexp_blocks(const SplitDesc& d) {
+  if (d.R <= 0) return 0;
+  return rowexp_by_thread(d.rs, d.ks, d.K) ? (d.R + 255) / 256 : (d.R + 7) / 8;
+}
+
+cudaError_t launch_split(const SplitDesc* d, int count, int rowexp_blocks, int max_split_blocks,
                          cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   for (int off = 0; off < count; off += 65535) {
     const int c = count - off < 65535 ? count - off : 65535;
-    k_rowexp<<<dim3((max_rows + 7) / 8, c), 256, 0, st>>>(d + off); count_launch();
+    if (rowexp_blocks > 0) { k_rowexp<<<dim3(rowexp_blocks, c), 256, 0, st>>>(d + off); count_launch(); }
     k_split<<<dim3(max_split_blocks, c), 256, 0, st>>>(d + off); count_launch();
   }
   return cudaGetLastError();
