@@ -347,7 +347,13 @@ __global__ void __cluster_dims__(AQ_CL, 1, 1) __launch_bounds__(256)
   cluster.sync();  // no CTA leaves while another may still read its partials
 }
 
-// gq = Q_G q and hq = Y q for one subdomain / right-hand side (warp per interface row).
+// gq = Q_G q and hq = Y q for each subdomain / right-hand side.  A block takes IV_GROWS
+// rows of gq, a warp each with lanes over the contiguous columns of Q_G^T, and IV_HROWS
+// rows of hq, a lane each (Y is column-major, so a warp reads 32 consecutive rows of one
+// column) with the n columns split over the 8 warps and summed in shared memory.  Both
+// loops issue 4 loads before their first FMA.
+constexpr int IV_GROWS = 8;
+constexpr int IV_HROWS = 32;
 __global__ void __launch_bounds__(256) k_iface_vecs(const double* __restrict__ X,
                                                     const double* __restrict__ K, long long kstride,
                                                     int ld, const double* __restrict__ Y,
@@ -356,31 +362,52 @@ __global__ void __launch_bounds__(256) k_iface_vecs(const double* __restrict__ X
                                                     const int* __restrict__ mf_arr, int N, int n,
                                                     double* __restrict__ gq,
                                                     double* __restrict__ hq) {
-  const int s = blockIdx.x, rh = blockIdx.y;
+  __shared__ double part[8][IV_HROWS];
+  const int s = blockIdx.x, rh = blockIdx.y, b = blockIdx.z;
   const int mg = mg_arr[s], mf = mf_arr[s];
   const double* q = X + ((size_t)rh * N + s) * ld;
-  const double* QGt = K + (size_t)s * kstride + (size_t)n * ld;
-  const double* Ys = Y + (size_t)s * ystride;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = warp; i < max(mg, mf); i += 8) {
-    double a = 0.0, b = 0.0;
-    if (i < mg && i < mf) {
-      for (int j = lane; j < n; j += 32) {
-        const double qj = q[j];
-        a = fma(QGt[j + (size_t)i * ld], qj, a);
-        b = fma(Ys[i + (size_t)j * mfld], qj, b);
-      }
-    } else if (i < mg) {
-      for (int j = lane; j < n; j += 32) a = fma(QGt[j + (size_t)i * ld], q[j], a);
-    } else {
-      for (int j = lane; j < n; j += 32) b = fma(Ys[i + (size_t)j * mfld], q[j], b);
+  const int i = b * IV_GROWS + warp;
+  if (i < mg) {
+    const double* row = K + (size_t)s * kstride + (size_t)n * ld + (size_t)i * ld;  // row i of Q_G
+    double a = 0.0;
+    int j = lane;
+    for (; j + 96 < n; j += 128) {
+      const double r0 = row[j], r1 = row[j + 32], r2 = row[j + 64], r3 = row[j + 96];
+      const double q0 = q[j], q1 = q[j + 32], q2 = q[j + 64], q3 = q[j + 96];
+      a = fma(r0, q0, a);
+      a = fma(r1, q1, a);
+      a = fma(r2, q2, a);
+      a = fma(r3, q3, a);
     }
+    for (; j < n; j += 32) a = fma(row[j], q[j], a);
     a = warp_sum(a);
-    b = warp_sum(b);
-    if (lane == 0) {
-      if (i < mg) gq[((size_t)rh * N + s) * mgld + i] = a;
-      if (i < mf) hq[((size_t)rh * N + s) * mfld + i] = b;
+    if (lane == 0) gq[((size_t)rh * N + s) * mgld + i] = a;
+  }
+  if (b * IV_HROWS >= mf) return;  // uniform over the block
+  const int r = b * IV_HROWS + lane;
+  double acc = 0.0;
+  if (r < mf) {
+    const double* col = Y + (size_t)s * ystride + r;
+    const int j1 = (int)(((long long)n * (warp + 1)) / 8);
+    int j = (int)(((long long)n * warp) / 8);
+    for (; j + 3 < j1; j += 4) {
+      const double y0 = col[(size_t)j * mfld], y1 = col[(size_t)(j + 1) * mfld];
+      const double y2 = col[(size_t)(j + 2) * mfld], y3 = col[(size_t)(j + 3) * mfld];
+      acc = fma(y0, q[j], acc);
+      acc = fma(y1, q[j + 1], acc);
+      acc = fma(y2, q[j + 2], acc);
+      acc = fma(y3, q[j + 3], acc);
     }
+    for (; j < j1; ++j) acc = fma(col[(size_t)j * mfld], q[j], acc);
+  }
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && r < mf) {
+    double t = part[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) t += part[w][lane];
+    hq[((size_t)rh * N + s) * mfld + r] = t;
   }
 }
 
@@ -412,16 +439,25 @@ __global__ void __launch_bounds__(256) k_mt_h(const double* __restrict__ M, long
                                               double* __restrict__ z) {
   const int s = blockIdx.x, rh = blockIdx.y;
   const int mg = mg_arr[s], mf = mf_arr[s];
-  const double* Ms = M + (size_t)s * mstride;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.z * 8 + warp;
+  if (i >= mg) return;
+  const double* col = M + (size_t)s * mstride + (size_t)i * mfld;  // column i of M_s
   const int* fds = ffd + (size_t)s * mfld;
   const double* hh = h + (size_t)rh * n_flux;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = warp; i < mg; i += 8) {
-    double a = 0.0;
-    for (int k = lane; k < mf; k += 32) a = fma(Ms[k + (size_t)i * mfld], hh[fds[k]], a);
-    a = warp_sum(a);
-    if (lane == 0) z[((size_t)rh * N + s) * mgld + i] = a;
+  double a = 0.0;
+  int k = lane;
+  for (; k + 96 < mf; k += 128) {  // 4 loads in flight, summed in the same order
+    const double m0 = col[k], m1 = col[k + 32], m2 = col[k + 64], m3 = col[k + 96];
+    const int f0 = fds[k], f1 = fds[k + 32], f2 = fds[k + 64], f3 = fds[k + 96];
+    a = fma(m0, hh[f0], a);
+    a = fma(m1, hh[f1], a);
+    a = fma(m2, hh[f2], a);
+    a = fma(m3, hh[f3], a);
   }
+  for (; k < mf; k += 32) a = fma(col[k], hh[fds[k]], a);
+  a = warp_sum(a);
+  if (lane == 0) z[((size_t)rh * N + s) * mgld + i] = a;
 }
 
 // c^s = R^{-1} (q + Q_G^T E_s u), one block per (subdomain, right-hand side).
@@ -915,8 +951,11 @@ cudaError_t launch_iface_vecs(const double* X, const double* K, long long kstrid
                               const double* Y, long long ystride, int mgld, const int* mg, int mfld,
                               const int* mf, int N, int n, int nrhs, double* gq, double* hq,
                               cudaStream_t st) {
-  k_iface_vecs<<<dim3(N, nrhs), 256, 0, st>>>(X, K, kstride, ld, Y, ystride, mgld, mg, mfld, mf, N, n, gq,
-                                              hq); count_launch();
+  const int zg = (mgld + IV_GROWS - 1) / IV_GROWS, zh = (mfld + IV_HROWS - 1) / IV_HROWS;
+  const int zb = zg > zh ? zg : zh;
+  if (N <= 0 || nrhs <= 0 || zb <= 0) return cudaSuccess;
+  k_iface_vecs<<<dim3(N, nrhs, zb), 256, 0, st>>>(X, K, kstride, ld, Y, ystride, mgld, mg, mfld, mf, N, n,
+                                                  gq, hq); count_launch();
   return cudaGetLastError();
 }
 
@@ -939,7 +978,9 @@ cudaError_t launch_gather_perm(const int* idx, int n, const double* src, double*
 cudaError_t launch_mt_h(const double* M, long long mstride, int mfld, const int* mf, const int* mg,
                         const int* ffd, const double* h, int n_flux, int N, int mgld, int nrhs,
                         double* z, cudaStream_t st) {
-  k_mt_h<<<dim3(N, nrhs), 256, 0, st>>>(M, mstride, mfld, mf, mg, ffd, h, n_flux, N, mgld, z); count_launch();
+  if (N <= 0 || nrhs <= 0 || mgld <= 0) return cudaSuccess;
+  k_mt_h<<<dim3(N, nrhs, (mgld + 7) / 8), 256, 0, st>>>(M, mstride, mfld, mf, mg, ffd, h, n_flux, N, mgld, z);
+  count_launch();
   return cudaGetLastError();
 }
 
